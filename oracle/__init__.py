@@ -1,0 +1,247 @@
+"""Serial CPU oracle of IPLS (arxiv 2208.06902) -- test infrastructure only.
+
+Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product library never does, and
+the oracle never imports the product library: the two share no code.
+
+The oracle itself is plain serial C++ (``ipls_oracle.cpp``); this module
+builds it with g++ and wraps its C entry points with ctypes.  Every function
+cites the passage of the paper it follows; the C++ file lists the readings
+taken where the paper is silent.
+
+Parity status of each function (what pins it, in ``tests/test_oracle_pins.py``):
+  * ``sort``                  -- std::sort under totalOrder, brute force over
+                                 all permutations (n <= 7), multiset hash.
+  * ``classify``              -- the worked example of Ch.4 (golden file),
+                                 monotonicity property, NaN/inf/-0 cases.
+  * ``fmcd``                  -- brute-force smallest-D search from the
+                                 definition, closed form on arithmetic
+                                 progressions, conflict-degree bound.
+  * ``partition_pass``        -- histogram sums, permutation, bucket ordering,
+                                 the splitter fallback's progress guarantee.
+  * ``sample_indices``        -- parity unpinned by the paper (it names no
+                                 random generator); pinned only against the
+                                 published SplitMix64 reference outputs.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ipls_oracle.cpp")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "libipls_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+F64, F32, U64, U32 = 0, 1, 2, 3
+_NP = {F64: np.float64, F32: np.float32, U64: np.uint64, U32: np.uint32}
+_CODE = {np.dtype(np.float64): F64, np.dtype(np.float32): F32,
+         np.dtype(np.uint64): U64, np.dtype(np.uint32): U32}
+
+KIND_LINEAR, KIND_SPLITTER = 0, 1
+
+
+class Cfg(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("cutoff", ctypes.c_int32),
+                ("root_sample", ctypes.c_int64), ("seed", ctypes.c_uint64)]
+
+
+class Model(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("capped", ctypes.c_int32),
+                ("S", ctypes.c_int64), ("D", ctypes.c_int64),
+                ("A", ctypes.c_double), ("Bc", ctypes.c_double),
+                ("xlo", ctypes.c_double), ("xlo_bits", ctypes.c_uint64),
+                ("B", ctypes.c_double), ("ud", ctypes.c_double),
+                ("nsplit", ctypes.c_int32), ("nbuckets", ctypes.c_int32),
+                ("split", ctypes.c_uint64 * 128)]
+
+
+class Trace(ctypes.Structure):
+    _fields_ = [("off", ctypes.c_int64), ("n", ctypes.c_int64),
+                ("level", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("model", Model), ("counts", ctypes.c_int64 * 512)]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with g++ (no FMA contraction, no fast-math)."""
+    with _lock:
+        if (not force and os.path.exists(_LIB)
+                and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+            return _LIB
+        os.makedirs(_BUILD, exist_ok=True)
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math",
+               "-fPIC", "-shared", "-o", tmp, _SRC]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+        return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = ctypes.CDLL(build())
+        c = ctypes
+        L.oracle_record_sizes.argtypes = [c.POINTER(c.c_int64), c.POINTER(c.c_int64)]
+        L.oracle_mix64.restype = c.c_uint64
+        L.oracle_mix64.argtypes = [c.c_uint64]
+        L.oracle_sample_indices.restype = None
+        L.oracle_sample_indices.argtypes = [c.c_uint64, c.c_int64, c.c_int64, c.c_int32,
+                                            c.c_int64, c.c_void_p]
+        L.oracle_sample_size.restype = c.c_int64
+        L.oracle_sample_size.argtypes = [c.c_int64, c.c_int32, c.c_int32, c.c_int64]
+        L.oracle_total_order.argtypes = [c.c_int, c.c_void_p, c.c_int64, c.c_void_p]
+        L.oracle_fmcd.argtypes = [c.c_int, c.c_void_p, c.c_int64, c.c_int32, c.POINTER(Model)]
+        L.oracle_fmcd_bruteforce.argtypes = [c.c_int, c.c_void_p, c.c_int64, c.c_int32,
+                                             c.POINTER(Model)]
+        L.oracle_classify.argtypes = [c.c_int, c.c_void_p, c.c_int64, c.POINTER(Model),
+                                      c.c_void_p]
+        L.oracle_partition_with_model.argtypes = [c.c_int, c.c_void_p, c.c_int64,
+                                                  c.POINTER(Model), c.c_void_p, c.c_void_p]
+        L.oracle_partition_pass.argtypes = [c.c_int, c.c_void_p, c.c_int64, c.c_int64,
+                                            c.c_int32, c.POINTER(Cfg), c.c_void_p,
+                                            c.c_void_p, c.POINTER(Model)]
+        L.oracle_sort.argtypes = [c.c_int, c.c_void_p, c.c_int64, c.POINTER(Cfg),
+                                  c.POINTER(Trace), c.c_int64, c.POINTER(c.c_int64),
+                                  c.POINTER(c.c_int32)]
+        L.oracle_std_sort.argtypes = [c.c_int, c.c_void_p, c.c_int64]
+        L.oracle_multiset_hash.restype = None
+        L.oracle_multiset_hash.argtypes = [c.c_int, c.c_void_p, c.c_int64,
+                                           c.POINTER(c.c_uint64), c.POINTER(c.c_uint64)]
+        mb, tb = c.c_int64(), c.c_int64()
+        L.oracle_record_sizes(c.byref(mb), c.byref(tb))
+        if mb.value != c.sizeof(Model) or tb.value != c.sizeof(Trace):
+            raise RuntimeError("oracle record layout mismatch")
+        _lib = L
+    return _lib
+
+
+def _code(a: np.ndarray) -> int:
+    return _CODE[a.dtype]
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def cfg(k: int = 256, cutoff: int = 32, root_sample: int = 0, seed: int = 0) -> Cfg:
+    return Cfg(k, cutoff, root_sample, seed)
+
+
+def mix64(z: int) -> int:
+    """SplitMix64 finaliser (Steele, Lea and Flood 2014)."""
+    return int(lib().oracle_mix64(ctypes.c_uint64(z & (2**64 - 1))))
+
+
+def sample_size(n: int, level: int, k: int = 256, root_sample: int = 0) -> int:
+    """S = alpha*k - 1 with alpha = 0.2*floor(log2 n) (Ch.4), at least 3."""
+    return int(lib().oracle_sample_size(n, level, k, root_sample))
+
+
+def sample_indices(seed: int, off: int, n: int, level: int, S: int) -> np.ndarray:
+    """Sampling phase (Ch.2 IPS4o; Ch.3): S indices in [off, off+n), with replacement."""
+    out = np.empty(S, np.int64)
+    lib().oracle_sample_indices(seed, off, n, level, S, _ptr(out))
+    return out
+
+
+def total_order(keys: np.ndarray) -> np.ndarray:
+    keys = np.ascontiguousarray(keys)
+    out = np.empty(keys.size, np.uint64)
+    lib().oracle_total_order(_code(keys), _ptr(keys), keys.size, _ptr(out))
+    return out
+
+
+def fmcd(sorted_sample: np.ndarray, K: int = 256) -> Model:
+    """FMCD, the loop of Listing 1 (Ch.3), binary64."""
+    s = np.ascontiguousarray(sorted_sample)
+    m = Model()
+    if lib().oracle_fmcd(_code(s), _ptr(s), s.size, K, ctypes.byref(m)) != 0:
+        raise ValueError("FMCD needs N >= 3 and K >= 3")
+    return m
+
+
+def fmcd_bruteforce(sorted_sample: np.ndarray, K: int = 256) -> Model:
+    """FMCD's result recomputed from its definition (smallest D with P(D))."""
+    s = np.ascontiguousarray(sorted_sample)
+    m = Model()
+    if lib().oracle_fmcd_bruteforce(_code(s), _ptr(s), s.size, K, ctypes.byref(m)) != 0:
+        raise ValueError("FMCD needs N >= 3 and K >= 3")
+    return m
+
+
+def linear_model(A: float, Bc: float, k: int, xlo_bits: int = 0) -> Model:
+    """A linear partition model given directly (kind 0)."""
+    m = Model()
+    m.kind, m.A, m.Bc, m.nbuckets, m.xlo_bits = KIND_LINEAR, A, Bc, k, xlo_bits
+    return m
+
+
+def classify(keys: np.ndarray, m: Model) -> np.ndarray:
+    """Bucket of every key: the model equation of Ch.3 (or the splitter tree)."""
+    keys = np.ascontiguousarray(keys)
+    out = np.empty(keys.size, np.int32)
+    lib().oracle_classify(_code(keys), _ptr(keys), keys.size, ctypes.byref(m), _ptr(out))
+    return out
+
+
+def partition_with_model(keys: np.ndarray, m: Model):
+    keys = np.ascontiguousarray(keys)
+    dst = np.empty_like(keys)
+    counts = np.zeros(m.nbuckets, np.int64)
+    lib().oracle_partition_with_model(_code(keys), _ptr(keys), keys.size, ctypes.byref(m),
+                                      _ptr(dst), _ptr(counts))
+    return dst, counts
+
+
+def partition_pass(keys: np.ndarray, off: int = 0, level: int = 0, k: int = 256,
+                   root_sample: int = 0, seed: int = 0):
+    """One IPLS pass: sample, sort, FMCD, classify, scan, stable scatter."""
+    keys = np.ascontiguousarray(keys)
+    dst = np.empty_like(keys)
+    counts = np.zeros(512, np.int64)
+    m = Model()
+    c = Cfg(k, 1, root_sample, seed)
+    rc = lib().oracle_partition_pass(_code(keys), _ptr(keys), keys.size, off, level,
+                                     ctypes.byref(c), _ptr(dst), _ptr(counts),
+                                     ctypes.byref(m))
+    if rc != 0:
+        raise ValueError(f"partition_pass failed ({rc})")
+    return dst, counts[: m.nbuckets].copy(), m
+
+
+def sort(keys: np.ndarray, k: int = 256, cutoff: int = 32, root_sample: int = 0,
+         seed: int = 0, trace_cap: int = 0):
+    """Whole IPLS sort (returns a sorted copy, the trace records and the depth)."""
+    out = np.array(keys, copy=True)
+    c = Cfg(k, cutoff, root_sample, seed)
+    tr = (Trace * trace_cap)() if trace_cap > 0 else None
+    cnt = ctypes.c_int64(0)
+    lv = ctypes.c_int32(0)
+    rc = lib().oracle_sort(_code(out), _ptr(out), out.size, ctypes.byref(c), tr, trace_cap,
+                           ctypes.byref(cnt), ctypes.byref(lv))
+    if rc != 0:
+        raise RuntimeError(f"oracle_sort failed ({rc})")
+    recs = list(tr[: cnt.value]) if tr is not None else []
+    return out, recs, lv.value
+
+
+def std_sort(keys: np.ndarray) -> np.ndarray:
+    """std::sort under IEEE totalOrder (the plain definition of the result)."""
+    out = np.array(keys, copy=True)
+    lib().oracle_std_sort(_code(out), _ptr(out), out.size)
+    return out
+
+
+def multiset_hash(keys: np.ndarray):
+    keys = np.ascontiguousarray(keys)
+    s, x = ctypes.c_uint64(), ctypes.c_uint64()
+    lib().oracle_multiset_hash(_code(keys), _ptr(keys), keys.size, ctypes.byref(s),
+                               ctypes.byref(x))
+    return int(s.value), int(x.value)

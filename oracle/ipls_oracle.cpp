@@ -1,0 +1,576 @@
+// Serial CPU oracle of In-Place Parallel Learned Sort (IPLS), arxiv 2208.06902.
+//
+// TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or
+// call this file; only the test suite, the smoke check and the timed CPU
+// baseline of bench.py do.  It shares no code, header, table or constant
+// generator with the CUDA library: every formula below is written out again
+// from the paper.
+//
+// What it computes, and where the paper defines it:
+//   * the partition model F(x) = clamp(floor(a*x + b), 0, k-1)
+//       (Ch.3 "Linear Models", the model equation and the clamping rule);
+//   * FMCD, the Fastest Minimum Conflict Degree fit, literally as the loop of
+//       Listing 1 (Ch.3 "Linear Models"), in binary64;
+//   * the IPLS pass: sample alpha*k-1 random keys with alpha = 0.2 log N and
+//       k = 256, sort the sample, train FMCD, predict the bucket of every key
+//       and move the keys into contiguous bucket regions (Ch.2 IPS4o section,
+//       Ch.3 four phases, Ch.4 "Proposed Algorithm");
+//   * recursion into every bucket as an independent subproblem, with a base
+//       case below a size cutoff (Ch.2 IPS4o, Ch.4);
+//   * the sampled-splitter decision tree with equality buckets (Ch.3
+//       "Decision Trees") as the fallback when the linear model cannot split.
+//
+// Readings where the paper is silent or ambiguous (each one is listed, with
+// its reason, in the design notes of the repository):
+//   R1  FMCD arithmetic is binary64, not long double.
+//   R2  The stale u_d at the 3D > N break is kept exactly as the loop has it.
+//   R3  The model is evaluated in the centred form
+//         b(x) = clamp(floor(fma(A, x (-) x_lo, Bc)), 0, k-1),
+//       x_lo = x[D], Bc = (K - A*(x[N-1-D] (-) x[D])) / 2, which equals
+//       A*x + B of the listing in exact arithmetic; (-) is a binary64
+//       subtraction for float keys and the exact integer difference rounded
+//       once to binary64 for integer keys.
+//   R4  One correctly rounded fma, then floor, then the clamp in binary64,
+//       then the conversion to an integer bucket.  NaN keys go to bucket 0
+//       when their sign bit is set and to bucket k-1 otherwise.
+//   R5  alpha = 0.2*floor(log2 n): S = max(3, floor(floor(log2 n)*k/5) - 1);
+//       the root may override S.
+//   R6  k is the same at every level.
+//   R7  Duplicates: a sample whose extremes are equal or not finite, a
+//       degenerate FMCD result (u_d <= 0 or not finite, A not finite), or a
+//       linear pass that puts every key into one bucket, re-partitions the
+//       subproblem with the splitter tree with equality buckets built from
+//       the same sorted sample.  An equality bucket is homogeneous and done.
+//   R8  Keys keep their input order inside a bucket (stable scatter).
+//   R9  Samples are drawn with replacement from a counter-based SplitMix64
+//       stream keyed by (seed, offset, size, level); see sample_indices().
+//
+// Keys are ordered by IEEE 754 totalOrder for floats (-NaN < -inf < ... <
+// -0 < +0 < ... < +inf < +NaN) and naturally for integers.
+//
+// Build: g++ -O2 -ffp-contract=off -fPIC -shared (no fast-math, no FMA
+// contraction: every rounding is the one written here).
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+namespace {
+
+enum { OR_F64 = 0, OR_F32 = 1, OR_U64 = 2, OR_U32 = 3 };
+
+// ---------------------------------------------------------------------------
+// Configuration, model record and trace record (oracle-private layouts).
+// ---------------------------------------------------------------------------
+struct OracleCfg {
+  int32_t k;            // buckets per pass (paper: 256, Ch.4)
+  int32_t cutoff;       // subproblems of at most this many keys are base-cased
+  int64_t root_sample;  // sample size at level 0; 0 = the alpha*k-1 formula
+  uint64_t seed;        // seed of the sampling stream
+};
+
+struct OracleModel {
+  int32_t kind;     // 0 = FMCD linear model, 1 = splitter tree, 2 = homogeneous
+  int32_t capped;   // FMCD left its loop at the 3D > N break (stale u_d)
+  int64_t S;        // sample size
+  int64_t D;        // conflict-degree parameter returned by FMCD
+  double A;         // slope 1/u_d
+  double Bc;        // centred intercept (K - A*span)/2
+  double xlo;       // x[D]: the centre of the centred form (as binary64)
+  uint64_t xlo_bits;  // x[D] as raw key bits (integer keys: the exact key)
+  double B;         // the listing's own intercept (K - A*(x_hi + x_lo))/2
+  double ud;        // the u_d the slope came from
+  int32_t nsplit;   // splitter count (kind 1)
+  int32_t nbuckets; // buckets of this pass: k, or 2*nsplit+1 for splitters
+  uint64_t split[128];  // splitters as totalOrder bits, ascending, unique
+};
+
+struct OracleTrace {
+  int64_t off, n;
+  int32_t level, pad;
+  OracleModel model;
+  int64_t counts[512];
+};
+
+// ---------------------------------------------------------------------------
+// SplitMix64 (Steele, Lea and Flood, OOPSLA 2014): golden-gamma increment
+// followed by the 64-bit finaliser.  Used as a counter-based generator.
+// ---------------------------------------------------------------------------
+const uint64_t kGamma = 0x9e3779b97f4a7c15ULL;
+
+uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+  return z ^ (z >> 31);
+}
+
+uint64_t mulhi64(uint64_t a, uint64_t b) {
+  return (uint64_t)(((unsigned __int128)a * (unsigned __int128)b) >> 64);
+}
+
+// The stream of one subproblem: seed, offset, size and level folded in, one
+// finaliser per field.  Sample j is the (j+1)-th SplitMix64 output of that
+// stream, reduced to [0, n) by a multiply-high.
+uint64_t stream_key(uint64_t seed, int64_t off, int64_t n, int32_t level) {
+  uint64_t t = mix64(seed + kGamma);
+  t = mix64((t ^ (uint64_t)off) + kGamma);
+  t = mix64((t ^ (uint64_t)n) + kGamma);
+  t = mix64((t ^ (uint64_t)(uint32_t)level) + kGamma);
+  return t;
+}
+
+void sample_indices(uint64_t seed, int64_t off, int64_t n, int32_t level,
+                    int64_t S, int64_t* idx) {
+  uint64_t t = stream_key(seed, off, n, level);
+  for (int64_t j = 0; j < S; ++j) {
+    uint64_t r = mix64(t + (uint64_t)(j + 1) * kGamma);
+    idx[j] = off + (int64_t)mulhi64(r, (uint64_t)n);
+  }
+}
+
+// Sample size, reading R5 of alpha = 0.2 log N, S = alpha*k - 1 (Ch.4).
+int64_t sample_size(int64_t n, int32_t level, const OracleCfg& cfg) {
+  if (level == 0 && cfg.root_sample > 0) return cfg.root_sample;
+  int64_t L = 0;
+  while ((int64_t(1) << (L + 1)) <= n) ++L;  // floor(log2 n)
+  int64_t S = (L * cfg.k) / 5 - 1;
+  return S < 3 ? 3 : S;
+}
+
+// ---------------------------------------------------------------------------
+// Key traits: totalOrder bits, value as binary64, exact difference.
+// ---------------------------------------------------------------------------
+template <class T> struct Key;
+
+template <> struct Key<double> {
+  static uint64_t ord(double x) {
+    uint64_t b; std::memcpy(&b, &x, 8);
+    return (b >> 63) ? ~b : (b | (uint64_t(1) << 63));
+  }
+  static uint64_t bits(double x) { uint64_t b; std::memcpy(&b, &x, 8); return b; }
+  static double val(double x) { return x; }
+  static bool is_nan(double x) { return std::isnan(x); }
+  static bool neg_sign(double x) { return std::signbit(x); }
+  static bool finite(double x) { return std::isfinite(x); }
+  // a (-) b: one binary64 subtraction.
+  static double diff(double a, double b) { return a - b; }
+};
+
+template <> struct Key<float> {
+  static uint64_t ord(float x) {
+    uint32_t b; std::memcpy(&b, &x, 4);
+    return (b >> 31) ? (uint32_t)~b : (b | 0x80000000u);
+  }
+  static uint64_t bits(float x) { uint32_t b; std::memcpy(&b, &x, 4); return b; }
+  static double val(float x) { return (double)x; }   // exact promotion
+  static bool is_nan(float x) { return std::isnan(x); }
+  static bool neg_sign(float x) { return std::signbit(x); }
+  static bool finite(float x) { return std::isfinite(x); }
+  static double diff(float a, float b) { return (double)a - (double)b; }
+};
+
+template <class U> struct IntKey {
+  static uint64_t ord(U x) { return (uint64_t)x; }
+  static uint64_t bits(U x) { return (uint64_t)x; }
+  static double val(U x) { return (double)x; }
+  static bool is_nan(U) { return false; }
+  static bool neg_sign(U) { return false; }
+  static bool finite(U) { return true; }
+  // Exact integer difference, rounded once to binary64 (reading R3).
+  static double diff(U a, U b) {
+    return a >= b ? (double)(uint64_t)(a - b) : -(double)(uint64_t)(b - a);
+  }
+};
+template <> struct Key<uint64_t> : IntKey<uint64_t> {};
+template <> struct Key<uint32_t> : IntKey<uint32_t> {};
+
+// ---------------------------------------------------------------------------
+// FMCD, the loop of Listing 1 (Ch.3), in binary64 (reading R1).
+// x[0..N) is the sorted sample; K the number of buckets.
+// ---------------------------------------------------------------------------
+template <class T>
+void fmcd_listing(const T* x, int64_t N, int32_t K, OracleModel* m) {
+  typedef Key<T> KT;
+  const double km2 = (double)(K - 2);
+  int64_t i = 0, D = 1;
+  double ud = KT::diff(x[N - 1 - D], x[D]) / km2;
+  int capped = 0;
+  while (i <= N - 1 - D) {
+    while (i + D < N && KT::diff(x[i + D], x[i]) >= ud) ++i;
+    if (i + D >= N) break;
+    D += 1;
+    if (D * 3 > N) { capped = 1; break; }
+    ud = KT::diff(x[N - 1 - D], x[D]) / km2;
+  }
+  const double A = 1.0 / ud;
+  const double span = KT::diff(x[N - 1 - D], x[D]);
+  const double prod = A * span;
+  const double Bc = ((double)K - prod) / 2.0;
+  const double sum = KT::val(x[N - 1 - D]) + KT::val(x[D]);
+  const double prod2 = A * sum;
+  m->kind = 0;
+  m->capped = capped;
+  m->S = N;
+  m->D = D;
+  m->ud = ud;
+  m->A = A;
+  m->Bc = Bc;
+  m->B = ((double)K - prod2) / 2.0;
+  m->xlo = KT::val(x[D]);
+  m->xlo_bits = KT::bits(x[D]);
+  m->nsplit = 0;
+  m->nbuckets = K;
+}
+
+// The same result found from the definition rather than the loop: the
+// smallest D >= 1 with 3D <= N such that every window of D+1 consecutive
+// sample points spans at least u_d(D); if no such D exists, the first D with
+// 3D > N, with u_d taken at D-1.  (Equivalence: gap(i,D) grows with D and
+// u_d(D) shrinks with D, so the loop never has to move i backwards.)
+template <class T>
+void fmcd_bruteforce(const T* x, int64_t N, int32_t K, OracleModel* m) {
+  typedef Key<T> KT;
+  const double km2 = (double)(K - 2);
+  int64_t Dcap = N / 3 + 1;   // smallest D with 3D > N
+  int64_t D = -1;
+  for (int64_t d = 1; d < Dcap; ++d) {
+    double ud = KT::diff(x[N - 1 - d], x[d]) / km2;
+    bool ok = true;
+    for (int64_t i = 0; i + d < N; ++i)
+      if (!(KT::diff(x[i + d], x[i]) >= ud)) { ok = false; break; }
+    if (ok) { D = d; break; }
+  }
+  int capped = 0;
+  double ud;
+  if (D < 0) {
+    capped = 1;
+    D = Dcap;
+    ud = KT::diff(x[N - 1 - (Dcap - 1)], x[Dcap - 1]) / km2;
+  } else {
+    ud = KT::diff(x[N - 1 - D], x[D]) / km2;
+  }
+  const double A = 1.0 / ud;
+  const double span = KT::diff(x[N - 1 - D], x[D]);
+  const double prod = A * span;
+  m->kind = 0; m->capped = capped; m->S = N; m->D = D; m->ud = ud; m->A = A;
+  m->Bc = ((double)K - prod) / 2.0;
+  const double sum = KT::val(x[N - 1 - D]) + KT::val(x[D]);
+  const double prod2 = A * sum;
+  m->B = ((double)K - prod2) / 2.0;
+  m->xlo = KT::val(x[D]); m->xlo_bits = KT::bits(x[D]);
+  m->nsplit = 0; m->nbuckets = K;
+}
+
+// Model equation of Ch.3 "Linear Models" in the centred form (R3, R4).
+template <class T>
+int32_t linear_bucket(T x, const OracleModel& m, T xlo) {
+  typedef Key<T> KT;
+  const int32_t k = m.nbuckets;
+  if (KT::is_nan(x)) return KT::neg_sign(x) ? 0 : k - 1;
+  const double d = KT::diff(x, xlo);
+  double v = std::fma(m.A, d, m.Bc);
+  v = std::floor(v);
+  if (v < 0.0) return 0;
+  if (v >= (double)k) return k - 1;
+  return (int32_t)v;
+}
+
+// Splitter tree with equality buckets (Ch.3 "Decision Trees"): with unique
+// splitters s_1 < ... < s_m, bucket 2p for keys strictly between s_p and
+// s_{p+1}, bucket 2p-1 for keys equal to s_p.
+int32_t splitter_bucket(uint64_t u, const OracleModel& m) {
+  int32_t p = 0;
+  while (p < m.nsplit && m.split[p] <= u) ++p;   // p = #{s_i <= u}
+  if (p > 0 && m.split[p - 1] == u) return 2 * p - 1;
+  return 2 * p;
+}
+
+template <class T>
+void build_splitters(const T* samp, int64_t S, int32_t k, OracleModel* m) {
+  typedef Key<T> KT;
+  const int64_t want = (k - 1) / 2;
+  int32_t cnt = 0;
+  for (int64_t i = 0; i < want; ++i) {
+    uint64_t u = KT::ord(samp[(i + 1) * S / (want + 1)]);
+    if (cnt == 0 || m->split[cnt - 1] != u) m->split[cnt++] = u;
+  }
+  m->kind = 1;
+  m->nsplit = cnt;
+  m->nbuckets = 2 * cnt + 1;
+}
+
+template <class T>
+int32_t bucket_of(T x, const OracleModel& m, T xlo) {
+  if (m.kind == 0) return linear_bucket<T>(x, m, xlo);
+  return splitter_bucket(Key<T>::ord(x), m);
+}
+
+// One IPLS partition pass on src[0..n) (the subproblem at offset `off` of the
+// whole array, at recursion level `level`): sample, sort the sample, fit,
+// classify, histogram, exclusive scan, stable scatter into dst[0..n).
+template <class T>
+void partition_pass(const T* src, int64_t n, int64_t off, int32_t level,
+                    const OracleCfg& cfg, T* dst, int64_t* counts,
+                    OracleModel* m) {
+  typedef Key<T> KT;
+  const int64_t S = sample_size(n, level, cfg);
+  std::vector<int64_t> idx(S);
+  sample_indices(cfg.seed, off, n, level, S, idx.data());
+  std::vector<T> samp(S);
+  for (int64_t j = 0; j < S; ++j) samp[j] = src[idx[j] - off];
+  std::stable_sort(samp.begin(), samp.end(),
+                   [](T a, T b) { return KT::ord(a) < KT::ord(b); });
+  std::memset(m, 0, sizeof(*m));
+  m->S = S;
+  bool linear = KT::ord(samp[0]) != KT::ord(samp[S - 1]) &&
+                KT::finite(samp[0]) && KT::finite(samp[S - 1]);
+  T xlo = samp[0];
+  if (linear) {
+    fmcd_listing<T>(samp.data(), S, cfg.k, m);
+    const bool ok = std::isfinite(m->ud) && m->ud > 0.0 &&
+                    std::isfinite(m->A) && std::isfinite(m->Bc);
+    if (ok) xlo = samp[m->D]; else linear = false;
+  }
+  std::vector<int32_t> b(n);
+  if (linear) {
+    std::fill(counts, counts + m->nbuckets, 0);
+    for (int64_t i = 0; i < n; ++i) counts[b[i] = linear_bucket<T>(src[i], *m, xlo)]++;
+    bool all_one = false;
+    for (int32_t j = 0; j < m->nbuckets; ++j) if (counts[j] == n) all_one = true;
+    if (all_one) linear = false;      // no progress: splitter fallback (R7)
+  }
+  if (!linear) {
+    OracleModel keep = *m;
+    build_splitters<T>(samp.data(), S, cfg.k, m);
+    m->S = S; m->D = keep.D; m->capped = keep.capped; m->A = keep.A;
+    m->Bc = keep.Bc; m->B = keep.B; m->ud = keep.ud; m->xlo = keep.xlo;
+    m->xlo_bits = keep.xlo_bits;
+    std::fill(counts, counts + m->nbuckets, 0);
+    for (int64_t i = 0; i < n; ++i) counts[b[i] = splitter_bucket(KT::ord(src[i]), *m)]++;
+  }
+  std::vector<int64_t> base(m->nbuckets + 1, 0);
+  for (int32_t j = 0; j < m->nbuckets; ++j) base[j + 1] = base[j] + counts[j];
+  for (int64_t i = 0; i < n; ++i) dst[base[b[i]]++] = src[i];
+}
+
+// Base case: insertion sort by totalOrder (the paper uses SkaSort for
+// n <= 2^12, Ch.4; any exact sort gives the same, unique result).
+template <class T>
+void base_sort(T* a, int64_t n) {
+  typedef Key<T> KT;
+  for (int64_t i = 1; i < n; ++i) {
+    T v = a[i];
+    int64_t j = i - 1;
+    while (j >= 0 && KT::ord(a[j]) > KT::ord(v)) { a[j + 1] = a[j]; --j; }
+    a[j + 1] = v;
+  }
+}
+
+struct Sub { int64_t off, n; };
+
+// IPLS by levels: every subproblem at level L lives in buffer L%2 (0 = keys,
+// 1 = scratch); a pass writes its buckets into the other buffer; buckets
+// become level L+1 subproblems (Ch.2 IPS4o recursion; Ch.4).
+template <class T>
+int ipls_sort(T* keys, int64_t n, const OracleCfg& cfg, OracleTrace* trace,
+              int64_t trace_cap, int64_t* trace_count, int32_t* levels_out) {
+  if (trace_count) *trace_count = 0;
+  if (n <= 1) { if (levels_out) *levels_out = 0; return 0; }
+  if (cfg.k < 3 || cfg.k > 256 || cfg.cutoff < 1) return -1;
+  std::vector<T> scratch(n);
+  T* buf[2] = {keys, scratch.data()};
+  std::vector<Sub> cur(1, Sub{0, n}), next;
+  int32_t level = 0;
+  std::vector<int64_t> counts(512);
+  OracleModel m;
+  while (!cur.empty()) {
+    if (level > 4096) return -6;
+    next.clear();
+    T* src = buf[level & 1];
+    T* dst = buf[(level + 1) & 1];
+    for (const Sub& s : cur) {
+      if (s.n <= cfg.cutoff) {
+        if (src != keys) std::memcpy(keys + s.off, src + s.off, s.n * sizeof(T));
+        base_sort<T>(keys + s.off, s.n);
+        continue;
+      }
+      partition_pass<T>(src + s.off, s.n, s.off, level, cfg, dst + s.off,
+                        counts.data(), &m);
+      if (trace && trace_count && *trace_count < trace_cap) {
+        OracleTrace& t = trace[(*trace_count)++];
+        t.off = s.off; t.n = s.n; t.level = level; t.pad = 0; t.model = m;
+        std::memset(t.counts, 0, sizeof(t.counts));
+        std::copy(counts.begin(), counts.begin() + m.nbuckets, t.counts);
+      }
+      int64_t pos = s.off;
+      for (int32_t j = 0; j < m.nbuckets; ++j) {
+        const int64_t c = counts[j];
+        if (c == 0) continue;
+        const bool equal_bucket = (m.kind == 1) && (j & 1);
+        if (equal_bucket) {
+          if (dst != keys) std::memcpy(keys + pos, dst + pos, c * sizeof(T));
+        } else {
+          next.push_back(Sub{pos, c});
+        }
+        pos += c;
+      }
+    }
+    cur.swap(next);
+    ++level;
+  }
+  if (levels_out) *levels_out = level;
+  return 0;
+}
+
+template <class F>
+int dispatch(int dtype, F f) {
+  switch (dtype) {
+    case OR_F64: return f((double*)nullptr);
+    case OR_F32: return f((float*)nullptr);
+    case OR_U64: return f((uint64_t*)nullptr);
+    case OR_U32: return f((uint32_t*)nullptr);
+  }
+  return -1;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C entry points (loaded by the tests through ctypes).
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int oracle_record_sizes(int64_t* model_bytes, int64_t* trace_bytes) {
+  *model_bytes = sizeof(OracleModel);
+  *trace_bytes = sizeof(OracleTrace);
+  return 0;
+}
+
+uint64_t oracle_mix64(uint64_t z) { return mix64(z); }
+
+void oracle_sample_indices(uint64_t seed, int64_t off, int64_t n, int32_t level,
+                           int64_t S, int64_t* idx) {
+  sample_indices(seed, off, n, level, S, idx);
+}
+
+int64_t oracle_sample_size(int64_t n, int32_t level, int32_t k, int64_t root_sample) {
+  OracleCfg c{k, 1, root_sample, 0};
+  return sample_size(n, level, c);
+}
+
+int oracle_total_order(int dtype, const void* keys, int64_t n, uint64_t* out) {
+  return dispatch(dtype, [&](auto* tag) {
+    typedef std::remove_pointer_t<decltype(tag)> T;
+    const T* k = (const T*)keys;
+    for (int64_t i = 0; i < n; ++i) out[i] = Key<T>::ord(k[i]);
+    return 0;
+  });
+}
+
+// FMCD on an already sorted sample (the loop of Listing 1).
+int oracle_fmcd(int dtype, const void* sorted, int64_t N, int32_t K, OracleModel* m) {
+  if (N < 3 || K < 3) return -1;
+  std::memset(m, 0, sizeof(*m));
+  return dispatch(dtype, [&](auto* tag) {
+    typedef std::remove_pointer_t<decltype(tag)> T;
+    fmcd_listing<T>((const T*)sorted, N, K, m);
+    return 0;
+  });
+}
+
+int oracle_fmcd_bruteforce(int dtype, const void* sorted, int64_t N, int32_t K, OracleModel* m) {
+  if (N < 3 || K < 3) return -1;
+  std::memset(m, 0, sizeof(*m));
+  return dispatch(dtype, [&](auto* tag) {
+    typedef std::remove_pointer_t<decltype(tag)> T;
+    fmcd_bruteforce<T>((const T*)sorted, N, K, m);
+    return 0;
+  });
+}
+
+// Bucket of every key under a given model (kind 0 uses A, Bc and the key
+// whose raw bits are xlo_bits; kind 1 uses the splitters).
+int oracle_classify(int dtype, const void* keys, int64_t n, const OracleModel* m,
+                    int32_t* out) {
+  return dispatch(dtype, [&](auto* tag) {
+    typedef std::remove_pointer_t<decltype(tag)> T;
+    T xlo;
+    uint64_t b = m->xlo_bits;
+    if (sizeof(T) == 8) std::memcpy(&xlo, &b, 8);
+    else { uint32_t b32 = (uint32_t)b; std::memcpy(&xlo, &b32, 4); }
+    const T* k = (const T*)keys;
+    for (int64_t i = 0; i < n; ++i) out[i] = bucket_of<T>(k[i], *m, xlo);
+    return 0;
+  });
+}
+
+// Partition keys[0..n) by a given model: stable scatter into dst, counts out.
+int oracle_partition_with_model(int dtype, const void* keys, int64_t n,
+                                const OracleModel* m, void* dst, int64_t* counts) {
+  std::vector<int32_t> b(n);
+  int rc = oracle_classify(dtype, keys, n, m, b.data());
+  if (rc) return rc;
+  std::fill(counts, counts + m->nbuckets, 0);
+  for (int64_t i = 0; i < n; ++i) counts[b[i]]++;
+  return dispatch(dtype, [&](auto* tag) {
+    typedef std::remove_pointer_t<decltype(tag)> T;
+    std::vector<int64_t> base(m->nbuckets + 1, 0);
+    for (int32_t j = 0; j < m->nbuckets; ++j) base[j + 1] = base[j] + counts[j];
+    const T* s = (const T*)keys;
+    T* d = (T*)dst;
+    for (int64_t i = 0; i < n; ++i) d[base[b[i]]++] = s[i];
+    return 0;
+  });
+}
+
+// One full IPLS pass (sample, sort, fit, classify, scan, stable scatter) on
+// the subproblem src[0..n) that sits at `off` of the whole array, `level`.
+int oracle_partition_pass(int dtype, const void* src, int64_t n, int64_t off,
+                          int32_t level, const OracleCfg* cfg, void* dst,
+                          int64_t* counts, OracleModel* m) {
+  if (n < 2 || cfg->k < 3 || cfg->k > 256) return -1;
+  return dispatch(dtype, [&](auto* tag) {
+    typedef std::remove_pointer_t<decltype(tag)> T;
+    partition_pass<T>((const T*)src, n, off, level, *cfg, (T*)dst, counts, m);
+    return 0;
+  });
+}
+
+// Whole IPLS sort, in place.  Returns 0, or a negative status.
+int oracle_sort(int dtype, void* keys, int64_t n, const OracleCfg* cfg,
+                OracleTrace* trace, int64_t trace_cap, int64_t* trace_count,
+                int32_t* levels) {
+  return dispatch(dtype, [&](auto* tag) {
+    typedef std::remove_pointer_t<decltype(tag)> T;
+    return ipls_sort<T>((T*)keys, n, *cfg, trace, trace_cap, trace_count, levels);
+  });
+}
+
+// Reference sort for the pins: std::sort under totalOrder.
+int oracle_std_sort(int dtype, void* keys, int64_t n) {
+  return dispatch(dtype, [&](auto* tag) {
+    typedef std::remove_pointer_t<decltype(tag)> T;
+    T* k = (T*)keys;
+    std::sort(k, k + n, [](T a, T b) { return Key<T>::ord(a) < Key<T>::ord(b); });
+    return 0;
+  });
+}
+
+// Multiset fingerprint: sum and xor of mix64 over the raw bits of every key.
+void oracle_multiset_hash(int dtype, const void* keys, int64_t n, uint64_t* sum_out,
+                          uint64_t* xor_out) {
+  uint64_t s = 0, x = 0;
+  const int w = (dtype == OR_F64 || dtype == OR_U64) ? 8 : 4;
+  const unsigned char* p = (const unsigned char*)keys;
+  for (int64_t i = 0; i < n; ++i) {
+    uint64_t b = 0;
+    std::memcpy(&b, p + i * w, w);
+    uint64_t h = mix64(b + kGamma);
+    s += h; x ^= h;
+  }
+  *sum_out = s; *xor_out = x;
+}
+
+}  // extern "C"
