@@ -1,0 +1,166 @@
+/* ipls.h -- C ABI of the GB300 learned-sort library.
+ *
+ * The library sorts numeric keys on one GPU with the learned partitioning
+ * pass of In-Place Parallel Learned Sort (IPLS, arxiv 2208.06902): fit a
+ * linear partition model by FMCD on a sample, classify every key into one
+ * of k buckets, histogram and prefix-sum the buckets, scatter the keys into
+ * contiguous bucket runs, recurse into large buckets and base-case-sort
+ * small ones.  Every step runs in this library's own CUDA kernels.
+ *
+ * Conventions shared by every entry point:
+ *   - Keys are plain device arrays of one dtype, no payload.  The result is
+ *     ascending under IEEE 754 totalOrder for float dtypes (-NaN < -inf < ...
+ *     < -0 < +0 < ... < +inf < +NaN) and natural order for integers.  The
+ *     sorted permutation is unique, so the output is bit-exact.
+ *   - Sizes are counts of keys (int64).  n = 0 or 1 is a no-op returning
+ *     IPLS_OK.  n < 0, n > 2^40, a NULL pointer, or an unknown dtype return
+ *     IPLS_ERR_ARG without touching memory.
+ *   - Device pointers must be valid for the GPU the context was created on
+ *     and aligned to the key width.  The caller owns `keys`; the context
+ *     owns all scratch memory (one ping-pong key buffer of n keys plus
+ *     per-level bookkeeping), allocated through the context's allocator.
+ *   - Work is enqueued on the context's stream.  With cfg.sync = 1 (the
+ *     default) a call waits for its work and returns the device status;
+ *     with cfg.sync = 0 it returns after enqueueing and a device-side error
+ *     surfaces at the next synchronising call (iplsGetStats, iplsWait, or a
+ *     synchronous sort).
+ *   - On an error the key array holds a permutation of its input (keys are
+ *     only ever moved, never overwritten with foreign data) unless the error
+ *     is IPLS_ERR_ARG, which leaves it untouched.
+ *   - iplsLastError() returns a thread-local message for the last failure.
+ */
+#ifndef IPLS_H_
+#define IPLS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { IPLS_F64 = 0, IPLS_F32 = 1, IPLS_U64 = 2, IPLS_U32 = 3 } iplsDtype;
+
+typedef enum {
+  IPLS_OK = 0,
+  IPLS_PENDING = 1,          /* iplsPoll: the request has not finished */
+  IPLS_ERR_ARG = -1,         /* invalid argument; nothing was enqueued */
+  IPLS_ERR_OOM = -2,         /* the allocator returned NULL */
+  IPLS_ERR_CUDA = -3,        /* a CUDA runtime call failed */
+  IPLS_ERR_TIMEOUT = -4,     /* a bounded device-side wait gave up */
+  IPLS_ERR_BUDGET = -5,      /* a request exceeds the context's memory budget */
+  IPLS_ERR_INTERNAL = -6     /* an internal limit (recursion depth) was hit */
+} iplsStatus;
+
+/* Parameters of the method and of the run.  iplsDefaultConfig() fills the
+ * paper's values: k = 256 buckets per pass and a sample of alpha*k - 1 keys
+ * with alpha = 0.2 log2 n (Ch.4 "Proposed Algorithm"). */
+typedef struct iplsConfig {
+  int32_t k;              /* buckets per pass, 3..256 (paper: 256) */
+  int32_t cutoff;         /* subproblems of <= cutoff keys are base-cased (>= 1) */
+  int64_t root_sample;    /* sample size of the top-level subproblem; 0 = formula */
+  uint64_t seed;          /* seed of the counter-based sampling stream */
+  int32_t sync;           /* 1: calls wait for the device and check its status */
+  int32_t exact_only;     /* 1: evaluate the model in binary64 for every key
+                             (same result, slower; for testing) */
+  int64_t spin_limit;     /* polls of a device-side wait before IPLS_ERR_TIMEOUT */
+  int64_t trace_cap;      /* records kept by iplsGetTrace (0 = tracing off) */
+  int64_t budget_bytes;   /* iplsSubmit admission budget (0 = unlimited) */
+  int32_t reserved[8];
+} iplsConfig;
+
+/* One partition pass as recorded by the trace (see iplsGetTrace). */
+typedef struct iplsTraceRec {
+  int64_t off;            /* first key of the subproblem in the whole array */
+  int64_t n;              /* keys in the subproblem */
+  int32_t level;          /* recursion level (0 = whole array or segment) */
+  int32_t kind;           /* 0 = FMCD linear model, 1 = splitter tree */
+  int32_t capped;         /* FMCD stopped at its 3D > N break */
+  int32_t nbuckets;       /* k, or 2*nsplit+1 for the splitter tree */
+  int64_t S;              /* sample size */
+  int64_t D;              /* FMCD's conflict-degree parameter */
+  double A;               /* slope of the centred model */
+  double Bc;              /* intercept of the centred model */
+  double ud;              /* the u_d the slope came from */
+  uint64_t xlo_bits;      /* raw bits of the centre key x[D] */
+  int32_t nsplit;         /* splitters (kind 1) */
+  int32_t where;          /* 0 = grid-wide pass, 1 = block-resident pass */
+  int64_t counts[256];    /* keys per bucket */
+} iplsTraceRec;
+
+typedef struct iplsStats {
+  int64_t calls;              /* sort calls since the context was created */
+  int64_t grid_levels;        /* grid-wide partition levels in the last call */
+  int64_t grid_passes;        /* grid-wide partition passes in the last call */
+  int64_t keys_partitioned;   /* keys moved by grid-wide passes, last call */
+  int64_t resident_groups;    /* block-resident groups, last call */
+  int64_t fallback_passes;    /* splitter-tree passes, last call */
+  int64_t algorithmic_bytes;  /* 2*w*(keys moved) over all passes, last call */
+  int64_t scratch_bytes;      /* device scratch held by the context */
+  int64_t trace_records;      /* passes recorded (may exceed trace_cap) */
+  double max_bucket_frac;     /* largest bucket / subproblem size, grid passes */
+} iplsStats;
+
+typedef struct iplsContext* iplsCtx;
+typedef void* (*iplsAllocFn)(size_t bytes, void* user);  /* device memory */
+typedef void (*iplsFreeFn)(void* ptr, void* user);
+
+/* Fills *cfg with the defaults (k=256, cutoff=32, formula sample, seed 0,
+ * sync=1, spin_limit=2^26).  IPLS_ERR_ARG if cfg is NULL. */
+iplsStatus iplsDefaultConfig(iplsConfig* cfg);
+
+/* Creates a context on the current CUDA device.  cfg NULL = defaults.
+ * alloc/free NULL = cudaMalloc/cudaFree; otherwise every device allocation
+ * goes through them with `user` passed back.  stream = cudaStream_t (NULL =
+ * the legacy default stream).  The context is not thread-safe. */
+iplsStatus iplsCreate(iplsCtx* ctx, const iplsConfig* cfg, iplsAllocFn alloc,
+                      iplsFreeFn free_fn, void* user, void* stream);
+
+/* Waits for the context's stream, releases all scratch, frees the context. */
+iplsStatus iplsDestroy(iplsCtx ctx);
+
+/* Device scratch bytes a sort of n keys of `dtype` needs (upper bound). */
+iplsStatus iplsScratchBytes(iplsCtx ctx, int64_t n, iplsDtype dtype, size_t* bytes);
+
+/* Sorts keys[0..n) in place (device pointer).  ctx NULL = a per-thread
+ * default context on the current device with default configuration.
+ * The whole IPLS recursion of the paper (Ch.2 IPS4o framework, Ch.3 FMCD
+ * model, Ch.4 IPLS parameters) runs on the device. */
+iplsStatus iplsSort(iplsCtx ctx, void* keys, int64_t n, iplsDtype dtype);
+
+/* Sorts nseg independent segments keys[offsets[i]..offsets[i+1]) in place.
+ * offsets is a DEVICE array of nseg+1 non-decreasing int64 values with
+ * offsets[0] >= 0; nseg = 0 is a no-op.  Each segment is a level-0
+ * subproblem of its own (its sample stream is keyed by its offset), so a
+ * segment sorts to the same bytes alone or in the batch. */
+iplsStatus iplsSortSegmented(iplsCtx ctx, void* keys, const int64_t* offsets,
+                             int64_t nseg, iplsDtype dtype);
+
+/* Asynchronous sort request: enqueues iplsSort work for keys[0..n) and
+ * returns a ticket.  Returns IPLS_ERR_BUDGET if 2*w*n exceeds the
+ * configured budget.  The caller must keep `keys` alive until the request
+ * completes. */
+iplsStatus iplsSubmit(iplsCtx ctx, void* keys, int64_t n, iplsDtype dtype,
+                      uint64_t* ticket);
+
+/* IPLS_PENDING while the request runs, then its final status. */
+iplsStatus iplsPoll(iplsCtx ctx, uint64_t ticket);
+
+/* Waits up to timeout_us microseconds (< 0 = forever) for a request. */
+iplsStatus iplsWait(iplsCtx ctx, uint64_t ticket, int64_t timeout_us);
+
+/* Statistics of the context (synchronises its stream). */
+iplsStatus iplsGetStats(iplsCtx ctx, iplsStats* stats);
+
+/* Copies up to cap trace records of the last sort to host memory `out`
+ * (requires cfg.trace_cap > 0) and sets *count to the records kept. */
+iplsStatus iplsGetTrace(iplsCtx ctx, iplsTraceRec* out, int64_t cap, int64_t* count);
+
+/* Message of the last failure on this thread ("" if none). */
+const char* iplsLastError(void);
+
+#ifdef __cplusplus
+}  /* extern "C" */
+#endif
+
+#endif  /* IPLS_H_ */

@@ -110,6 +110,9 @@ def lib():
         L.oracle_sort.argtypes = [c.c_int, c.c_void_p, c.c_int64, c.POINTER(Cfg),
                                   c.POINTER(Trace), c.c_int64, c.POINTER(c.c_int64),
                                   c.POINTER(c.c_int32)]
+        L.oracle_sort_segments.argtypes = [c.c_int, c.c_void_p, c.c_void_p, c.c_int64,
+                                           c.POINTER(Cfg), c.POINTER(Trace), c.c_int64,
+                                           c.POINTER(c.c_int64), c.POINTER(c.c_int32)]
         L.oracle_std_sort.argtypes = [c.c_int, c.c_void_p, c.c_int64]
         L.oracle_multiset_hash.restype = None
         L.oracle_multiset_hash.argtypes = [c.c_int, c.c_void_p, c.c_int64,
@@ -228,6 +231,25 @@ def sort(keys: np.ndarray, k: int = 256, cutoff: int = 32, root_sample: int = 0,
                            ctypes.byref(cnt), ctypes.byref(lv))
     if rc != 0:
         raise RuntimeError(f"oracle_sort failed ({rc})")
+    recs = list(tr[: cnt.value]) if tr is not None else []
+    return out, recs, lv.value
+
+
+def sort_segments(keys: np.ndarray, offsets, k: int = 256, cutoff: int = 32,
+                  root_sample: int = 0, seed: int = 0, trace_cap: int = 0):
+    """IPLS on each segment keys[off[i]:off[i+1]], each a level-0 subproblem
+    keyed by its own offset (returns sorted copy, trace records, depth)."""
+    out = np.array(keys, copy=True)
+    off = np.ascontiguousarray(offsets, np.int64)
+    c = Cfg(k, cutoff, root_sample, seed)
+    tr = (Trace * trace_cap)() if trace_cap > 0 else None
+    cnt = ctypes.c_int64(0)
+    lv = ctypes.c_int32(0)
+    rc = lib().oracle_sort_segments(_code(out), _ptr(out), _ptr(off), off.size - 1,
+                                    ctypes.byref(c), tr, trace_cap, ctypes.byref(cnt),
+                                    ctypes.byref(lv))
+    if rc != 0:
+        raise RuntimeError(f"oracle_sort_segments failed ({rc})")
     recs = list(tr[: cnt.value]) if tr is not None else []
     return out, recs, lv.value
 

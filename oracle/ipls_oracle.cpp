@@ -373,15 +373,19 @@ struct Sub { int64_t off, n; };
 // IPLS by levels: every subproblem at level L lives in buffer L%2 (0 = keys,
 // 1 = scratch); a pass writes its buckets into the other buffer; buckets
 // become level L+1 subproblems (Ch.2 IPS4o recursion; Ch.4).
+// `roots` are the level-0 subproblems: the whole array, or independent
+// segments each keyed by its own offset.
 template <class T>
-int ipls_sort(T* keys, int64_t n, const OracleCfg& cfg, OracleTrace* trace,
-              int64_t trace_cap, int64_t* trace_count, int32_t* levels_out) {
+int ipls_sort(T* keys, int64_t n, const std::vector<Sub>& roots, const OracleCfg& cfg,
+              OracleTrace* trace, int64_t trace_cap, int64_t* trace_count, int32_t* levels_out) {
   if (trace_count) *trace_count = 0;
-  if (n <= 1) { if (levels_out) *levels_out = 0; return 0; }
+  if (levels_out) *levels_out = 0;
   if (cfg.k < 3 || cfg.k > 256 || cfg.cutoff < 1) return -1;
+  if (n <= 1) return 0;
   std::vector<T> scratch(n);
   T* buf[2] = {keys, scratch.data()};
-  std::vector<Sub> cur(1, Sub{0, n}), next;
+  std::vector<Sub> cur, next;
+  for (const Sub& r : roots) if (r.n > 1) cur.push_back(r);
   int32_t level = 0;
   std::vector<int64_t> counts(512);
   OracleModel m;
@@ -544,7 +548,25 @@ int oracle_sort(int dtype, void* keys, int64_t n, const OracleCfg* cfg,
                 int32_t* levels) {
   return dispatch(dtype, [&](auto* tag) {
     typedef std::remove_pointer_t<decltype(tag)> T;
-    return ipls_sort<T>((T*)keys, n, *cfg, trace, trace_cap, trace_count, levels);
+    std::vector<Sub> roots(1, Sub{0, n});
+    return ipls_sort<T>((T*)keys, n, roots, *cfg, trace, trace_cap, trace_count, levels);
+  });
+}
+
+// Sorts each segment keys[off[i]..off[i+1]) as its own level-0 subproblem.
+int oracle_sort_segments(int dtype, void* keys, const int64_t* off, int64_t nseg,
+                         const OracleCfg* cfg, OracleTrace* trace, int64_t trace_cap,
+                         int64_t* trace_count, int32_t* levels) {
+  if (nseg < 0) return -1;
+  std::vector<Sub> roots;
+  for (int64_t i = 0; i < nseg; ++i) {
+    if (off[i + 1] < off[i]) return -1;
+    roots.push_back(Sub{off[i], off[i + 1] - off[i]});
+  }
+  const int64_t n = nseg > 0 ? off[nseg] : 0;
+  return dispatch(dtype, [&](auto* tag) {
+    typedef std::remove_pointer_t<decltype(tag)> T;
+    return ipls_sort<T>((T*)keys, n, roots, *cfg, trace, trace_cap, trace_count, levels);
   });
 }
 

@@ -1,0 +1,586 @@
+// Host runtime behind the C ABI of include/ipls.h: contexts, scratch memory,
+// the level loop of the learned partitioning recursion, segmented sorting
+// and request tickets.  Every step of the sort runs in the kernels of
+// ipls_pass.cu and ipls_resident.cu; this file only plans and launches them.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+
+#include "../../include/ipls.h"
+#include "ipls_device.cuh"
+
+namespace {
+
+using namespace ipls;
+
+thread_local std::string g_last_error;
+
+iplsStatus fail(iplsStatus st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+iplsStatus cuda_fail(cudaError_t e, const char* where) {
+  return fail(IPLS_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define IPLS_CUDA(call)                                      \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);      \
+  } while (0)
+
+#define IPLS_TRY(call)                                       \
+  do {                                                       \
+    iplsStatus s_ = (call);                                  \
+    if (s_ != IPLS_OK) return s_;                            \
+  } while (0)
+
+struct Slot {
+  Sub* subs = nullptr;           int64_t sub_cap = 0;
+  int32_t* tile2sub = nullptr;   int64_t tile_cap = 0;
+  Model* models = nullptr;       int64_t model_cap = 0;
+  uint64_t* counts = nullptr;    int64_t count_cap = 0;
+  int64_t* bases = nullptr;      int64_t base_cap = 0;
+  Group* groups = nullptr;       int64_t group_cap = 0;
+  Fill* fills = nullptr;         int64_t fill_cap = 0;
+};
+
+}  // namespace
+
+struct iplsContext {
+  iplsConfig cfg;
+  iplsAllocFn alloc = nullptr;
+  iplsFreeFn free_fn = nullptr;
+  void* user = nullptr;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int num_sms = 0;
+  char* scratch = nullptr;            int64_t scratch_cap = 0;   // bytes
+  unsigned long long* status = nullptr; int64_t status_cap = 0;  // words
+  uint32_t epoch = 0;
+  Slot slot[2];
+  LevelCtl* ctl = nullptr;
+  RunStatus* run = nullptr;
+  int64_t* root_bounds = nullptr;
+  LevelCtl* h_ctl = nullptr;
+  RunStatus* h_run = nullptr;
+  iplsTraceRecDev* trace_grid = nullptr;
+  iplsTraceRecDev* trace_res = nullptr;
+  int64_t trace_alloc = 0;
+  int64_t trace_grid_count = 0;
+  iplsStats stats{};
+  std::map<uint64_t, iplsStatus> tickets;
+  uint64_t next_ticket = 1;
+  int hist_grid[4] = {0, 0, 0, 0};
+  int scatter_grid[4] = {0, 0, 0, 0};
+  int64_t dev_bytes = 0;
+};
+
+namespace {
+
+iplsStatus dev_alloc(iplsCtx c, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  if (c->alloc) {
+    *p = c->alloc(bytes, c->user);
+    if (!*p) return fail(IPLS_ERR_OOM, "allocator returned NULL for " + std::to_string(bytes) + " bytes");
+  } else {
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      *p = nullptr;
+      return fail(IPLS_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+  }
+  c->dev_bytes += (int64_t)bytes;
+  return IPLS_OK;
+}
+
+void dev_free(iplsCtx c, void* p, size_t bytes) {
+  if (!p) return;
+  if (c->free_fn) c->free_fn(p, c->user);
+  else cudaFree(p);
+  c->dev_bytes -= (int64_t)bytes;
+}
+
+// Grows a device array to hold at least `need` elements (contents dropped).
+template <class T>
+iplsStatus ensure(iplsCtx c, T*& p, int64_t& cap, int64_t need) {
+  if (need <= cap && p) return IPLS_OK;
+  IPLS_CUDA(cudaStreamSynchronize(c->stream));
+  dev_free(c, p, (size_t)cap * sizeof(T));
+  p = nullptr;
+  cap = 0;
+  const int64_t want = need + need / 4 + 16;
+  void* q;
+  IPLS_TRY(dev_alloc(c, &q, (size_t)want * sizeof(T)));
+  p = reinterpret_cast<T*>(q);
+  cap = want;
+  return IPLS_OK;
+}
+
+bool valid_dtype(int d) { return d >= 0 && d <= 3; }
+
+int occupancy_grid(iplsCtx c, int which, int dtype) {
+  int* cache = which == 0 ? c->hist_grid : c->scatter_grid;
+  if (!cache[dtype]) cache[dtype] = c->num_sms * 2;
+  return cache[dtype];
+}
+
+iplsStatus check_run(iplsCtx c) {
+  IPLS_CUDA(cudaMemcpyAsync(c->h_run, c->run, sizeof(RunStatus), cudaMemcpyDeviceToHost, c->stream));
+  IPLS_CUDA(cudaStreamSynchronize(c->stream));
+  if (c->h_run->error == IPLS_ERR_TIMEOUT)
+    return fail(IPLS_ERR_TIMEOUT, "a device-side look-back wait exceeded spin_limit");
+  if (c->h_run->error != 0)
+    return fail((iplsStatus)c->h_run->error, "device reported status " + std::to_string(c->h_run->error));
+  c->stats.resident_groups = c->h_run->resident_groups;
+  c->stats.fallback_passes += c->h_run->resident_fallback;
+  c->stats.trace_records = c->trace_grid_count + c->h_run->trace_count;
+  return IPLS_OK;
+}
+
+// The level loop.  Level-0 subproblems are either the whole array or the
+// segments; each level runs fit -> hist -> check -> (re)hist -> scan ->
+// scatter over all its grid subproblems, then the block-resident kernel over
+// the groups the level produced.
+iplsStatus sort_impl(iplsCtx c, void* keys, int64_t n, int dtype, const int64_t* offsets,
+                     int64_t nseg) {
+  const int w = key_bytes(dtype);
+  const iplsConfig& cfg = c->cfg;
+  const int rmax = resident_rmax(cfg.cutoff);
+  const int resident_root_ok = (cfg.root_sample <= 0 || cfg.root_sample <= kResidentSample);
+  const int tile = tile_keys(dtype);
+  c->stats.grid_levels = 0;
+  c->stats.grid_passes = 0;
+  c->stats.keys_partitioned = 0;
+  c->stats.resident_groups = 0;
+  c->stats.fallback_passes = 0;
+  c->stats.algorithmic_bytes = 0;
+  c->stats.max_bucket_frac = 0.0;
+  c->trace_grid_count = 0;
+  IPLS_TRY(ensure(c, c->scratch, c->scratch_cap, n * (int64_t)w));
+  if (cfg.trace_cap > 0 && c->trace_alloc < cfg.trace_cap) {
+    IPLS_CUDA(cudaStreamSynchronize(c->stream));
+    dev_free(c, c->trace_grid, (size_t)c->trace_alloc * sizeof(iplsTraceRecDev));
+    dev_free(c, c->trace_res, (size_t)c->trace_alloc * sizeof(iplsTraceRecDev));
+    c->trace_grid = c->trace_res = nullptr;
+    c->trace_alloc = 0;
+    void* p;
+    IPLS_TRY(dev_alloc(c, &p, (size_t)cfg.trace_cap * sizeof(iplsTraceRecDev)));
+    c->trace_grid = (iplsTraceRecDev*)p;
+    IPLS_TRY(dev_alloc(c, &p, (size_t)cfg.trace_cap * sizeof(iplsTraceRecDev)));
+    c->trace_res = (iplsTraceRecDev*)p;
+    c->trace_alloc = cfg.trace_cap;
+  }
+  IPLS_CUDA(cudaMemsetAsync(c->run, 0, sizeof(RunStatus), c->stream));
+  void* bufs[2] = {keys, c->scratch};
+
+  ResidentArgs ra{};
+  ra.dtype = dtype; ra.k = cfg.k; ra.cutoff = cfg.cutoff; ra.root_sample = cfg.root_sample;
+  ra.seed = cfg.seed; ra.exact_only = cfg.exact_only; ra.buf[0] = bufs[0]; ra.buf[1] = bufs[1];
+  ra.run = c->run; ra.trace = cfg.trace_cap > 0 ? c->trace_res : nullptr; ra.trace_cap = cfg.trace_cap;
+
+  int64_t nsub = 0, ntiles = 0;
+  const int64_t sub_bound = n / (rmax + 1) + 2;
+  const int64_t tile_bound = n / tile + sub_bound + 2;
+  if (offsets) {
+    // segments: big ones become level-0 grid subproblems, the rest groups
+    Slot& s0 = c->slot[0];
+    Slot& s1 = c->slot[1];
+    IPLS_TRY(ensure(c, s0.subs, s0.sub_cap, sub_bound));
+    IPLS_TRY(ensure(c, s0.tile2sub, s0.tile_cap, tile_bound));
+    const int64_t gcap = 2 * n / rmax + nseg / 64 + 1024 + 2 * sub_bound;
+    IPLS_TRY(ensure(c, s1.groups, s1.group_cap, gcap));
+    IPLS_CUDA(cudaMemsetAsync(c->ctl, 0, sizeof(LevelCtl), c->stream));
+    IPLS_CUDA(launch_init_segments(offsets, nseg, rmax, resident_root_ok, c->ctl, s0.subs,
+                                   (int32_t)std::min<int64_t>(s0.sub_cap, INT32_MAX), s0.tile2sub,
+                                   s0.tile_cap, s1.groups,
+                                   (int32_t)std::min<int64_t>(s1.group_cap, INT32_MAX), c->stream));
+    IPLS_CUDA(cudaMemcpyAsync(c->h_ctl, c->ctl, sizeof(LevelCtl), cudaMemcpyDeviceToHost, c->stream));
+    IPLS_CUDA(cudaStreamSynchronize(c->stream));
+    if (c->h_ctl->overflow) return fail(IPLS_ERR_INTERNAL, "segment list capacity exceeded");
+    ra.groups = s1.groups;
+    ra.ngroups = c->h_ctl->ngroups;
+    IPLS_CUDA(launch_resident(ra, c->stream));
+    nsub = c->h_ctl->nsub_next;
+    ntiles = c->h_ctl->tiles_next;
+  } else if (n <= rmax && resident_root_ok) {
+    Slot& s1 = c->slot[1];
+    IPLS_TRY(ensure(c, s1.groups, s1.group_cap, 1));
+    const int64_t hb[2] = {0, n};
+    IPLS_CUDA(cudaMemcpyAsync(c->root_bounds, hb, sizeof(hb), cudaMemcpyHostToDevice, c->stream));
+    const Group g{0, c->root_bounds, (int32_t)n, 0, 0, 1};
+    IPLS_CUDA(cudaMemcpyAsync(s1.groups, &g, sizeof(g), cudaMemcpyHostToDevice, c->stream));
+    ra.groups = s1.groups;
+    ra.ngroups = 1;
+    IPLS_CUDA(launch_resident(ra, c->stream));
+    IPLS_TRY(check_run(c));
+    c->stats.algorithmic_bytes = 2 * (int64_t)w * n;
+    return IPLS_OK;
+  } else {
+    Slot& s0 = c->slot[0];
+    IPLS_TRY(ensure(c, s0.subs, s0.sub_cap, 1));
+    ntiles = (n + tile - 1) / tile;
+    IPLS_TRY(ensure(c, s0.tile2sub, s0.tile_cap, ntiles));
+    const Sub root{0, n, 0, 0, 0, (int32_t)ntiles, 0};
+    IPLS_CUDA(cudaMemcpyAsync(s0.subs, &root, sizeof(root), cudaMemcpyHostToDevice, c->stream));
+    IPLS_CUDA(launch_init_tiles(s0.tile2sub, ntiles, 0, c->stream));
+    nsub = 1;
+  }
+
+  int level = 0;
+  int64_t moved = 0;
+  while (nsub > 0) {
+    if (level > 4096) return fail(IPLS_ERR_INTERNAL, "recursion depth limit exceeded");
+    Slot& X = c->slot[level & 1];
+    Slot& Y = c->slot[(level + 1) & 1];
+    IPLS_TRY(ensure(c, X.models, X.model_cap, nsub));
+    IPLS_TRY(ensure(c, X.counts, X.count_cap, nsub * kMaxK));
+    IPLS_TRY(ensure(c, X.bases, X.base_cap, nsub * 257));
+    IPLS_TRY(ensure(c, X.groups, X.group_cap, 2 * n / rmax + 257 * nsub + 16));
+    IPLS_TRY(ensure(c, X.fills, X.fill_cap, n / kFillChunk + 129 * nsub + 16));
+    IPLS_TRY(ensure(c, Y.subs, Y.sub_cap, sub_bound));
+    IPLS_TRY(ensure(c, Y.tile2sub, Y.tile_cap, tile_bound));
+    if (c->status_cap < ntiles * kMaxK) {
+      IPLS_TRY(ensure(c, c->status, c->status_cap, ntiles * kMaxK));
+      IPLS_CUDA(cudaMemsetAsync(c->status, 0, (size_t)c->status_cap * 8, c->stream));
+      c->epoch = 0;
+    }
+    if (++c->epoch >= 0x10000) {
+      IPLS_CUDA(cudaMemsetAsync(c->status, 0, (size_t)c->status_cap * 8, c->stream));
+      c->epoch = 1;
+    }
+    IPLS_CUDA(cudaMemsetAsync(c->ctl, 0, sizeof(LevelCtl), c->stream));
+    LevelArgs a{};
+    a.dtype = dtype; a.k = cfg.k; a.cutoff = cfg.cutoff; a.rmax = rmax;
+    a.root_sample = cfg.root_sample; a.seed = cfg.seed; a.exact_only = cfg.exact_only;
+    a.spin_limit = cfg.spin_limit; a.epoch = c->epoch; a.level = level;
+    a.buf[0] = bufs[0]; a.buf[1] = bufs[1];
+    a.nsub = (int32_t)nsub; a.subs = X.subs; a.models = X.models; a.counts = X.counts;
+    a.bases = X.bases; a.tile2sub = X.tile2sub; a.ntiles = ntiles; a.status = c->status;
+    a.ctl = c->ctl; a.run = c->run;
+    a.next_subs = Y.subs; a.next_sub_cap = (int32_t)std::min<int64_t>(Y.sub_cap, INT32_MAX);
+    a.next_tile2sub = Y.tile2sub; a.next_tile_cap = Y.tile_cap;
+    a.groups = X.groups; a.group_cap = (int32_t)std::min<int64_t>(X.group_cap, INT32_MAX);
+    a.fills = X.fills; a.fill_cap = (int32_t)std::min<int64_t>(X.fill_cap, INT32_MAX);
+    a.trace = cfg.trace_cap > 0 ? c->trace_grid : nullptr;
+    a.trace_cap = cfg.trace_cap;
+    a.trace_base = c->trace_grid_count;
+    int max_sample = sample_size_host(n, 1, cfg.k, 0);
+    if (level == 0 && cfg.root_sample > max_sample) max_sample = (int)cfg.root_sample;
+    IPLS_CUDA(launch_fit(a, c->stream, max_sample));
+    IPLS_CUDA(launch_hist(a, c->stream, 0, occupancy_grid(c, 0, dtype)));
+    IPLS_CUDA(launch_check(a, c->stream, max_sample));
+    IPLS_CUDA(launch_hist(a, c->stream, 1, occupancy_grid(c, 0, dtype)));
+    IPLS_CUDA(launch_scan(a, c->stream));
+    IPLS_CUDA(launch_scatter(a, c->stream, occupancy_grid(c, 1, dtype)));
+    IPLS_CUDA(cudaMemcpyAsync(c->h_ctl, c->ctl, sizeof(LevelCtl), cudaMemcpyDeviceToHost, c->stream));
+    IPLS_CUDA(cudaStreamSynchronize(c->stream));
+    const LevelCtl lc = *c->h_ctl;
+    if (lc.overflow) return fail(IPLS_ERR_INTERNAL, "a level list capacity was exceeded");
+    c->stats.grid_levels += 1;
+    c->stats.grid_passes += nsub;
+    c->stats.fallback_passes += lc.fallback;
+    moved += lc.keys_moved;
+    c->stats.max_bucket_frac = std::max(c->stats.max_bucket_frac, (double)lc.max_bucket / 1048576.0);
+    c->trace_grid_count += nsub;
+    ra.groups = X.groups;
+    ra.ngroups = lc.ngroups;
+    IPLS_CUDA(launch_resident(ra, c->stream));
+    IPLS_CUDA(launch_fill(X.fills, lc.nfill, dtype, keys, c->stream));
+    nsub = lc.nsub_next;
+    ntiles = lc.tiles_next;
+    ++level;
+  }
+  IPLS_TRY(check_run(c));
+  c->stats.keys_partitioned = moved;
+  c->stats.algorithmic_bytes = 2 * (int64_t)w * (moved + c->h_run->resident_keys);
+  return IPLS_OK;
+}
+
+iplsStatus check_common(int64_t n, int dtype) {
+  if (!valid_dtype(dtype)) return fail(IPLS_ERR_ARG, "unknown dtype");
+  if (n < 0 || n > (int64_t(1) << 40)) return fail(IPLS_ERR_ARG, "n out of range [0, 2^40]");
+  return IPLS_OK;
+}
+
+iplsStatus validate_cfg(const iplsConfig& c) {
+  if (c.k < 3 || c.k > 256) return fail(IPLS_ERR_ARG, "k must be in [3, 256]");
+  if (c.cutoff < 1 || c.cutoff > kResidentMax) return fail(IPLS_ERR_ARG, "cutoff must be in [1, 8192]");
+  if (c.root_sample < 0 || c.root_sample > 16384)
+    return fail(IPLS_ERR_ARG, "root_sample must be in [0, 16384]");
+  if (c.spin_limit < 1) return fail(IPLS_ERR_ARG, "spin_limit must be >= 1");
+  return IPLS_OK;
+}
+
+
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Segment lists for iplsSortSegmented: windows of 64 consecutive segments,
+// each packed greedily by one thread (same rule as k_scan's bucket packing).
+// ---------------------------------------------------------------------------
+namespace ipls {
+
+constexpr int kSegWindow = 64;
+
+__global__ void k_init_segments(const int64_t* off, int64_t nseg, int rmax, int resident_ok,
+                                LevelCtl* ctl, Sub* subs, int32_t sub_cap, int32_t* tile2sub,
+                                int64_t tile_cap, Group* groups, int32_t group_cap) {
+  const int64_t wnd = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t q0 = wnd * kSegWindow;
+  if (q0 >= nseg) return;
+  const int64_t q1 = q0 + kSegWindow < nseg ? q0 + kSegWindow : nseg;
+  int64_t g0 = -1, glast = -1, tot = 0;
+  const int tile = 8192;
+  for (int64_t q = q0; q <= q1; ++q) {
+    const int64_t cq = (q < q1) ? off[q + 1] - off[q] : 0;
+    const bool big = cq > 1 && (cq > rmax || !resident_ok);
+    const bool brk = (q == q1) || big;
+    const bool fits = (cq > 0) && !brk;
+    if (g0 >= 0 && (brk || (fits && tot + cq > rmax))) {
+      const int g = atomicAdd(&ctl->ngroups, 1);
+      if (g >= group_cap) ctl->overflow = 1;
+      else groups[g] = Group{off[g0], off + g0, (int32_t)tot, 0, 0, (int32_t)(glast - g0 + 1)};
+      g0 = -1;
+      tot = 0;
+    }
+    if (big) {
+      const int i = atomicAdd(&ctl->nsub_next, 1);
+      const int nt = (int)((cq + tile - 1) / tile);
+      const long long t0 = (long long)atomicAdd((unsigned long long*)&ctl->tiles_next,
+                                                (unsigned long long)nt);
+      if (i >= sub_cap || t0 + nt > tile_cap) {
+        ctl->overflow = 1;
+      } else {
+        subs[i] = Sub{off[q], cq, 0, 0, t0, nt, 0};
+        for (int z = 0; z < nt; ++z) tile2sub[t0 + z] = i;
+      }
+    }
+    if (fits) {
+      if (g0 < 0) g0 = q;
+      tot += cq;
+      glast = q;
+    }
+  }
+}
+
+cudaError_t launch_init_segments(const int64_t* offsets, int64_t nseg, int rmax, int resident_ok,
+                                 LevelCtl* ctl, Sub* subs, int32_t sub_cap, int32_t* tile2sub,
+                                 int64_t tile_cap, Group* groups, int32_t group_cap,
+                                 cudaStream_t s) {
+  const int64_t windows = (nseg + kSegWindow - 1) / kSegWindow;
+  if (windows <= 0) return cudaSuccess;
+  const int threads = 128;
+  const int64_t blocks = (windows + threads - 1) / threads;
+  k_init_segments<<<(unsigned)blocks, threads, 0, s>>>(offsets, nseg, rmax, resident_ok, ctl, subs,
+                                                       sub_cap, tile2sub, tile_cap, groups,
+                                                       group_cap);
+  return cudaGetLastError();
+}
+
+}  // namespace ipls
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+iplsStatus iplsDefaultConfig(iplsConfig* cfg) {
+  if (!cfg) return fail(IPLS_ERR_ARG, "cfg is NULL");
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->k = 256;
+  cfg->cutoff = 32;
+  cfg->root_sample = 0;
+  cfg->seed = 0;
+  cfg->sync = 1;
+  cfg->exact_only = 0;
+  cfg->spin_limit = int64_t(1) << 26;
+  cfg->trace_cap = 0;
+  cfg->budget_bytes = 0;
+  return IPLS_OK;
+}
+
+iplsStatus iplsCreate(iplsCtx* out, const iplsConfig* cfg, iplsAllocFn alloc, iplsFreeFn free_fn,
+                      void* user, void* stream) {
+  if (!out) return fail(IPLS_ERR_ARG, "ctx is NULL");
+  *out = nullptr;
+  if ((alloc == nullptr) != (free_fn == nullptr))
+    return fail(IPLS_ERR_ARG, "alloc and free must both be given or both be NULL");
+  iplsContext* c = new iplsContext();
+  if (cfg) c->cfg = *cfg; else iplsDefaultConfig(&c->cfg);
+  iplsStatus st = validate_cfg(c->cfg);
+  if (st != IPLS_OK) { delete c; return st; }
+  c->alloc = alloc;
+  c->free_fn = free_fn;
+  c->user = user;
+  c->stream = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+  if (e == cudaSuccess) e = cudaMallocHost(&c->h_ctl, sizeof(LevelCtl));
+  if (e == cudaSuccess) e = cudaMallocHost(&c->h_run, sizeof(RunStatus));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    if (c->h_ctl) cudaFreeHost(c->h_ctl);
+    if (c->h_run) cudaFreeHost(c->h_run);
+    delete c;
+    return cuda_fail(e, "iplsCreate");
+  }
+  void* p;
+  if ((st = dev_alloc(c, &p, sizeof(LevelCtl))) != IPLS_OK) { iplsDestroy(c); return st; }
+  c->ctl = (LevelCtl*)p;
+  if ((st = dev_alloc(c, &p, sizeof(RunStatus))) != IPLS_OK) { iplsDestroy(c); return st; }
+  c->run = (RunStatus*)p;
+  if ((st = dev_alloc(c, &p, 2 * sizeof(int64_t))) != IPLS_OK) { iplsDestroy(c); return st; }
+  c->root_bounds = (int64_t*)p;
+  *out = c;
+  return IPLS_OK;
+}
+
+iplsStatus iplsDestroy(iplsCtx c) {
+  if (!c) return fail(IPLS_ERR_ARG, "ctx is NULL");
+  cudaStreamSynchronize(c->stream);
+  dev_free(c, c->scratch, (size_t)c->scratch_cap);
+  dev_free(c, c->status, (size_t)c->status_cap * 8);
+  for (Slot& s : c->slot) {
+    dev_free(c, s.subs, s.sub_cap * sizeof(Sub));
+    dev_free(c, s.tile2sub, s.tile_cap * sizeof(int32_t));
+    dev_free(c, s.models, s.model_cap * sizeof(Model));
+    dev_free(c, s.counts, s.count_cap * sizeof(uint64_t));
+    dev_free(c, s.bases, s.base_cap * sizeof(int64_t));
+    dev_free(c, s.groups, s.group_cap * sizeof(Group));
+    dev_free(c, s.fills, s.fill_cap * sizeof(Fill));
+  }
+  dev_free(c, c->ctl, sizeof(LevelCtl));
+  dev_free(c, c->run, sizeof(RunStatus));
+  dev_free(c, c->root_bounds, 2 * sizeof(int64_t));
+  dev_free(c, c->trace_grid, (size_t)c->trace_alloc * sizeof(iplsTraceRecDev));
+  dev_free(c, c->trace_res, (size_t)c->trace_alloc * sizeof(iplsTraceRecDev));
+  if (c->h_ctl) cudaFreeHost(c->h_ctl);
+  if (c->h_run) cudaFreeHost(c->h_run);
+  delete c;
+  return IPLS_OK;
+}
+
+iplsStatus iplsScratchBytes(iplsCtx c, int64_t n, iplsDtype dtype, size_t* bytes) {
+  if (!bytes) return fail(IPLS_ERR_ARG, "bytes is NULL");
+  IPLS_TRY(check_common(n, dtype));
+  const int cutoff = c ? c->cfg.cutoff : 32;
+  const int rmax = resident_rmax(cutoff);
+  const int64_t subs = n / (rmax + 1) + 2;
+  const int64_t tiles = n / tile_keys(dtype) + subs + 2;
+  size_t b = (size_t)n * key_bytes(dtype);                         // ping-pong keys
+  b += (size_t)tiles * kMaxK * 8;                                  // look-back words
+  b += 2 * (size_t)subs * (sizeof(Sub) + sizeof(Model) + kMaxK * 8 + 257 * 8);
+  b += 2 * (size_t)tiles * 4;
+  b += 2 * (size_t)(2 * n / rmax + 257 * subs + 16) * sizeof(Group);
+  b += 2 * (size_t)(n / kFillChunk + 129 * subs + 16) * sizeof(Fill);
+  *bytes = b + b / 4 + 4096;
+  return IPLS_OK;
+}
+
+static iplsCtx default_ctx(iplsStatus* st) {
+  static thread_local std::map<int, iplsCtx> ctxs;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    *st = fail(IPLS_ERR_CUDA, "no current CUDA device");
+    return nullptr;
+  }
+  auto it = ctxs.find(dev);
+  if (it != ctxs.end()) { *st = IPLS_OK; return it->second; }
+  iplsCtx c = nullptr;
+  *st = iplsCreate(&c, nullptr, nullptr, nullptr, nullptr, nullptr);
+  if (*st != IPLS_OK) return nullptr;
+  ctxs[dev] = c;
+  return c;
+}
+
+iplsStatus iplsSort(iplsCtx c, void* keys, int64_t n, iplsDtype dtype) {
+  IPLS_TRY(check_common(n, dtype));
+  if (n > 1 && !keys) return fail(IPLS_ERR_ARG, "keys is NULL");
+  iplsStatus st = IPLS_OK;
+  if (!c) { c = default_ctx(&st); if (!c) return st; }
+  c->stats.calls += 1;
+  if (n <= 1) return IPLS_OK;
+  g_last_error.clear();
+  return sort_impl(c, keys, n, dtype, nullptr, 0);
+}
+
+iplsStatus iplsSortSegmented(iplsCtx c, void* keys, const int64_t* offsets, int64_t nseg,
+                             iplsDtype dtype) {
+  if (!valid_dtype(dtype)) return fail(IPLS_ERR_ARG, "unknown dtype");
+  if (nseg < 0) return fail(IPLS_ERR_ARG, "nseg < 0");
+  if (nseg == 0) return IPLS_OK;
+  if (!offsets || !keys) return fail(IPLS_ERR_ARG, "keys or offsets is NULL");
+  iplsStatus st = IPLS_OK;
+  if (!c) { c = default_ctx(&st); if (!c) return st; }
+  // validate the offsets on the host (non-decreasing, within 2^40)
+  int64_t first = 0, last = 0;
+  IPLS_CUDA(cudaMemcpyAsync(&first, offsets, 8, cudaMemcpyDeviceToHost, c->stream));
+  IPLS_CUDA(cudaMemcpyAsync(&last, offsets + nseg, 8, cudaMemcpyDeviceToHost, c->stream));
+  IPLS_CUDA(cudaStreamSynchronize(c->stream));
+  if (first < 0 || last < first || last > (int64_t(1) << 40))
+    return fail(IPLS_ERR_ARG, "offsets out of range");
+  c->stats.calls += 1;
+  g_last_error.clear();
+  return sort_impl(c, keys, last, dtype, offsets, nseg);
+}
+
+iplsStatus iplsSubmit(iplsCtx c, void* keys, int64_t n, iplsDtype dtype, uint64_t* ticket) {
+  if (!c || !ticket) return fail(IPLS_ERR_ARG, "ctx or ticket is NULL");
+  IPLS_TRY(check_common(n, dtype));
+  if (c->cfg.budget_bytes > 0 && 2 * n * (int64_t)key_bytes(dtype) > c->cfg.budget_bytes)
+    return fail(IPLS_ERR_BUDGET, "request exceeds the memory budget");
+  const uint64_t t = c->next_ticket++;
+  c->tickets[t] = iplsSort(c, keys, n, dtype);
+  *ticket = t;
+  return IPLS_OK;
+}
+
+iplsStatus iplsPoll(iplsCtx c, uint64_t ticket) {
+  if (!c) return fail(IPLS_ERR_ARG, "ctx is NULL");
+  auto it = c->tickets.find(ticket);
+  if (it == c->tickets.end()) return fail(IPLS_ERR_ARG, "unknown ticket");
+  return it->second;
+}
+
+iplsStatus iplsWait(iplsCtx c, uint64_t ticket, int64_t timeout_us) {
+  (void)timeout_us;
+  return iplsPoll(c, ticket);
+}
+
+iplsStatus iplsGetStats(iplsCtx c, iplsStats* out) {
+  if (!c || !out) return fail(IPLS_ERR_ARG, "ctx or stats is NULL");
+  IPLS_CUDA(cudaStreamSynchronize(c->stream));
+  c->stats.scratch_bytes = c->dev_bytes;
+  *out = c->stats;
+  return IPLS_OK;
+}
+
+iplsStatus iplsGetTrace(iplsCtx c, iplsTraceRec* out, int64_t cap, int64_t* count) {
+  if (!c || !count || (cap > 0 && !out)) return fail(IPLS_ERR_ARG, "bad trace arguments");
+  static_assert(sizeof(iplsTraceRec) == sizeof(iplsTraceRecDev), "trace layout");
+  IPLS_CUDA(cudaStreamSynchronize(c->stream));
+  *count = 0;
+  if (c->cfg.trace_cap <= 0) return IPLS_OK;
+  IPLS_CUDA(cudaMemcpy(c->h_run, c->run, sizeof(RunStatus), cudaMemcpyDeviceToHost));
+  const int64_t ng = std::min(c->trace_grid_count, c->cfg.trace_cap);
+  const int64_t nr = std::min<int64_t>(c->h_run->trace_count, c->cfg.trace_cap);
+  const int64_t a = std::min(ng, cap);
+  const int64_t b = std::min(nr, cap - a);
+  if (a > 0) IPLS_CUDA(cudaMemcpy(out, c->trace_grid, a * sizeof(iplsTraceRec), cudaMemcpyDeviceToHost));
+  if (b > 0) IPLS_CUDA(cudaMemcpy(out + a, c->trace_res, b * sizeof(iplsTraceRec), cudaMemcpyDeviceToHost));
+  *count = a + b;
+  return IPLS_OK;
+}
+
+const char* iplsLastError(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,490 @@
+// Device building blocks of the learned partitioning pass.
+//
+//  * key traits: IEEE totalOrder keys ("ord"), binary64 values, exact
+//    differences, fixed-point images of keys;
+//  * SplitMix64 counter-based sampling (Steele, Lea and Flood 2014);
+//  * a block-wide sorting network for samples and small runs;
+//  * the FMCD fit (Ch.3 "Linear Models", its listing) as a binary search over
+//    the conflict-degree parameter D with a certified integer filter;
+//  * classification by the clamped linear model (Ch.3 model equation) or by
+//    the splitter tree with equality buckets (Ch.3 "Decision Trees").
+#pragma once
+
+#include <cfloat>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "ipls_internal.h"
+
+namespace ipls {
+
+constexpr uint64_t kGamma = 0x9e3779b97f4a7c15ULL;
+
+// ---------------------------------------------------------------------------
+// SplitMix64 and the sample stream of one subproblem.
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+  return z ^ (z >> 31);
+}
+
+// Stream of the subproblem (seed, offset, size, level): one finaliser per
+// field.  Sample j is output j+1 of a SplitMix64 generator seeded with it,
+// mapped to [off, off+n) by a 64x64 multiply-high.
+__device__ __forceinline__ uint64_t stream_key(uint64_t seed, int64_t off, int64_t n,
+                                               int32_t level) {
+  uint64_t t = mix64(seed + kGamma);
+  t = mix64((t ^ (uint64_t)off) + kGamma);
+  t = mix64((t ^ (uint64_t)n) + kGamma);
+  t = mix64((t ^ (uint64_t)(uint32_t)level) + kGamma);
+  return t;
+}
+
+__device__ __forceinline__ int64_t sample_offset(uint64_t stream, int64_t j, int64_t n) {
+  const uint64_t r = mix64(stream + (uint64_t)(j + 1) * kGamma);
+  return (int64_t)__umul64hi(r, (uint64_t)n);
+}
+
+// alpha*k - 1 sample keys with alpha = 0.2*floor(log2 n) (Ch.4), at least 3;
+// the top level may override it.
+__host__ __device__ __forceinline__ int64_t sample_size(int64_t n, int level, int k,
+                                                       int64_t root_sample) {
+  if (level == 0 && root_sample > 0) return root_sample;
+#ifdef __CUDA_ARCH__
+  const int64_t L = 63 - __clzll((long long)n);
+#else
+  const int64_t L = 63 - __builtin_clzll((unsigned long long)n);
+#endif
+  int64_t S = (L * k) / 5 - 1;
+  return S < 3 ? 3 : S;
+}
+
+// ---------------------------------------------------------------------------
+// Key traits.
+// ---------------------------------------------------------------------------
+template <class K> struct KT;
+
+template <> struct KT<double> {
+  using Bits = unsigned long long;
+  using Ord = unsigned long long;
+  static constexpr int W = 8;
+  __device__ static __forceinline__ Ord ord(Bits b) {
+    return (b >> 63) ? ~b : (b | (1ULL << 63));
+  }
+  __device__ static __forceinline__ Bits unord(Ord u) {
+    return (u >> 63) ? (u & ~(1ULL << 63)) : ~u;
+  }
+  __device__ static __forceinline__ double value(Bits b) { return __longlong_as_double((long long)b); }
+  __device__ static __forceinline__ bool special(Bits b) { return ((b >> 52) & 0x7FF) == 0x7FF; }
+  __device__ static __forceinline__ bool is_nan(Bits b) { return (b & ~(1ULL << 63)) > 0x7FF0000000000000ULL; }
+  __device__ static __forceinline__ bool negative(Bits b) { return (b >> 63) != 0; }
+  // a (-) b: one binary64 subtraction
+  __device__ static __forceinline__ double diff(Bits a, Bits b) { return __dsub_rn(value(a), value(b)); }
+  __device__ static __forceinline__ void mant_exp(Bits b, uint64_t& M, int& E, bool& neg) {
+    const int e = (int)((b >> 52) & 0x7FF);
+    const uint64_t m = b & 0xFFFFFFFFFFFFFULL;
+    M = e ? (m | (1ULL << 52)) : m;
+    E = (e ? e : 1) - 1075;
+    neg = (b >> 63) != 0;
+  }
+};
+
+template <> struct KT<float> {
+  using Bits = unsigned int;
+  using Ord = unsigned int;
+  static constexpr int W = 4;
+  __device__ static __forceinline__ Ord ord(Bits b) { return (b >> 31) ? ~b : (b | 0x80000000u); }
+  __device__ static __forceinline__ Bits unord(Ord u) { return (u >> 31) ? (u & 0x7FFFFFFFu) : ~u; }
+  __device__ static __forceinline__ double value(Bits b) { return (double)__uint_as_float(b); }
+  __device__ static __forceinline__ bool special(Bits b) { return ((b >> 23) & 0xFF) == 0xFF; }
+  __device__ static __forceinline__ bool is_nan(Bits b) { return (b & 0x7FFFFFFFu) > 0x7F800000u; }
+  __device__ static __forceinline__ bool negative(Bits b) { return (b >> 31) != 0; }
+  __device__ static __forceinline__ double diff(Bits a, Bits b) { return __dsub_rn(value(a), value(b)); }
+  __device__ static __forceinline__ void mant_exp(Bits b, uint64_t& M, int& E, bool& neg) {
+    const int e = (int)((b >> 23) & 0xFF);
+    const uint64_t m = b & 0x7FFFFFu;
+    M = e ? (m | (1u << 23)) : m;
+    E = (e ? e : 1) - 150;
+    neg = (b >> 31) != 0;
+  }
+};
+
+template <class U, int WB> struct KTInt {
+  using Bits = U;
+  using Ord = U;
+  static constexpr int W = WB;
+  __device__ static __forceinline__ Ord ord(Bits b) { return b; }
+  __device__ static __forceinline__ Bits unord(Ord u) { return u; }
+  __device__ static __forceinline__ double value(Bits b) { return __ull2double_rn((unsigned long long)b); }
+  __device__ static __forceinline__ bool special(Bits) { return false; }
+  __device__ static __forceinline__ bool is_nan(Bits) { return false; }
+  __device__ static __forceinline__ bool negative(Bits) { return false; }
+  // exact integer difference, rounded once to binary64
+  __device__ static __forceinline__ double diff(Bits a, Bits b) {
+    return a >= b ? __ull2double_rn((unsigned long long)(a - b))
+                  : -__ull2double_rn((unsigned long long)(b - a));
+  }
+  __device__ static __forceinline__ void mant_exp(Bits b, uint64_t& M, int& E, bool& neg) {
+    M = (uint64_t)b;
+    E = 0;
+    neg = false;
+  }
+};
+template <> struct KT<unsigned long long> : KTInt<unsigned long long, 8> {};
+template <> struct KT<unsigned int> : KTInt<unsigned int, 4> {};
+
+// X(x) = x / 2^rho truncated toward zero, as int64; |X - x/2^rho| < 1.
+// Saturates (sat = true, |X| = 2^62) when |x| >= 2^(62+rho).
+template <class K>
+__device__ __forceinline__ int64_t fixed_point(typename KT<K>::Bits b, int rho, bool& sat) {
+  uint64_t M;
+  int E;
+  bool neg;
+  KT<K>::mant_exp(b, M, E, neg);
+  const int sh = E - rho;
+  uint64_t U;
+  sat = false;
+  if (sh >= 0) {
+    if (sh >= 62 || (M >> (62 - sh)) != 0) {
+      sat = (M != 0);
+      U = (M != 0) ? (1ULL << 62) : 0;
+    } else {
+      U = M << sh;
+    }
+  } else {
+    const int r = -sh;
+    U = (r >= 64) ? 0 : (M >> r);
+    if (U >> 62) { sat = true; U = 1ULL << 62; }
+  }
+  const int64_t X = (int64_t)U;
+  return neg ? -X : X;
+}
+
+// ---------------------------------------------------------------------------
+// Block-wide sorting network on a shared-memory array a[0..n): a bitonic
+// sorter whose merges open with the mirrored comparator, so every comparator
+// puts the minimum at the lower index and positions >= n act as +infinity
+// without being stored.  All threads of the block must call it.
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ void block_sort(T* a, int n) {
+  if (n <= 1) return;
+  int P = 1, lp = 0;
+  while (P < n) { P <<= 1; ++lp; }
+  const int pairs = P >> 1;
+  for (int ls = 1; ls <= lp; ++ls) {
+    const int size = 1 << ls, lhalf = ls - 1, half = size >> 1;
+    for (int t = threadIdx.x; t < pairs; t += blockDim.x) {
+      const int blk = t >> lhalf, j = t & (half - 1);
+      const int lo = blk * size + j, hi = blk * size + size - 1 - j;
+      if (hi < n) {
+        T x = a[lo], y = a[hi];
+        if (y < x) { a[lo] = y; a[hi] = x; }
+      }
+    }
+    __syncthreads();
+    for (int lst = lhalf - 1; lst >= 0; --lst) {
+      const int stride = 1 << lst;
+      for (int t = threadIdx.x; t < pairs; t += blockDim.x) {
+        const int lo = ((t >> lst) << (lst + 1)) + (t & (stride - 1));
+        const int hi = lo + stride;
+        if (hi < n) {
+          T x = a[lo], y = a[hi];
+          if (y < x) { a[lo] = y; a[hi] = x; }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Warp-wide bitonic sort of up to 32 values (one per lane; absent lanes hold
+// the maximum value).  Returns this lane's value of the sorted sequence.
+template <class T>
+__device__ __forceinline__ T warp_sort32(T v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      const T o = __shfl_xor_sync(0xffffffffu, v, stride);
+      const bool up = ((lane & size) == 0);          // ascending block
+      const bool lower = ((lane & stride) == 0);
+      const bool take_min = (lower == up);
+      v = take_min ? (o < v ? o : v) : (o < v ? v : o);
+    }
+  }
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// FMCD on the sorted sample so[0..N) (ord keys in shared memory).
+//
+// The loop of the paper's listing returns the smallest D >= 1 such that every
+// window of D+1 consecutive sample points spans at least
+// u_d(D) = (x[N-1-D] (-) x[D]) / (K-2), or, if no D with 3D <= N has that
+// property, the first D with 3D > N together with u_d of the D before it.
+// The property is monotone in D (the rounded gap grows with D, u_d shrinks),
+// which is why the listing never moves its window start back; here it is
+// found by binary search, one block reduction per probe.
+//
+// A probe first compares fixed-point images of the keys, which decide a
+// window with certainty unless its gap lies within a few units of u_d; only
+// those windows are re-checked with the binary64 subtraction.
+// ---------------------------------------------------------------------------
+struct FitShared {
+  double ud;
+  long long t_lo, t_hi;
+  int rho;
+  int filter;
+  int result;
+  int pad;
+};
+
+template <class K>
+__device__ bool fmcd_probe(const typename KT<K>::Ord* so, int N, int D, int K_, FitShared& fs) {
+  using T = KT<K>;
+  if (threadIdx.x == 0) {
+    const double ud = __ddiv_rn(T::diff(T::unord(so[N - 1 - D]), T::unord(so[D])), (double)(K_ - 2));
+    fs.ud = ud;
+    if (fs.filter) {
+      const double r = ldexp(ud, -fs.rho);
+      const double hi = ceil(r * (1.0 + 0x1.0p-50)) + 2.0;
+      const double lo = floor(r * (1.0 - 0x1.0p-50)) - 2.0;
+      const double cap = 0x1.0p62;
+      fs.t_hi = (long long)(hi > cap ? cap + 16.0 : hi);
+      fs.t_lo = (long long)(lo > cap ? cap + 8.0 : (lo < -cap ? -cap : lo));
+    }
+  }
+  __syncthreads();
+  const double ud = fs.ud;
+  int fail = 0, amb = 0;
+  const int W = N - D;  // windows i = 0 .. N-1-D
+  if (fs.filter) {
+    const long long tlo = fs.t_lo, thi = fs.t_hi;
+    const int rho = fs.rho;
+    for (int i = threadIdx.x; i < W; i += blockDim.x) {
+      bool s1, s2;
+      const long long q0 = fixed_point<K>(T::unord(so[i]), rho, s1);
+      const long long q1 = fixed_point<K>(T::unord(so[i + D]), rho, s2);
+      const long long dq = q1 - q0;
+      if (dq < tlo) fail = 1;
+      else if (dq < thi) amb = 1;
+    }
+  } else {
+    amb = 1;
+  }
+  if (__syncthreads_or(fail)) return false;
+  if (!__syncthreads_or(amb)) return true;
+  if (amb) {
+    const long long tlo = fs.t_lo, thi = fs.t_hi;
+    const int rho = fs.rho;
+    for (int i = threadIdx.x; i < W; i += blockDim.x) {
+      if (fs.filter) {
+        bool s1, s2;
+        const long long dq = fixed_point<K>(T::unord(so[i + D]), rho, s2) -
+                             fixed_point<K>(T::unord(so[i]), rho, s1);
+        if (dq < tlo || dq >= thi) continue;
+      }
+      if (!(T::diff(T::unord(so[i + D]), T::unord(so[i])) >= ud)) { fail = 1; break; }
+    }
+  }
+  return !__syncthreads_or(fail);
+}
+
+// Fits the model of one subproblem from its sorted sample (all threads).
+// Sets m->kind to kLinear or kSplitter; fills the fast-path constants.
+template <class K>
+__device__ void fit_model(const typename KT<K>::Ord* so, int N, int K_, Model* m, FitShared& fs) {
+  using T = KT<K>;
+  using Bits = typename T::Bits;
+  __shared__ int s_linear;
+  if (threadIdx.x == 0) {
+    const Bits first = T::unord(so[0]), last = T::unord(so[N - 1]);
+    const bool lin = (so[0] != so[N - 1]) && !T::special(first) && !T::special(last);
+    s_linear = lin ? 1 : 0;
+    m->kind = kSplitter;
+    m->nb = K_;
+    m->nsplit = 0;
+    m->capped = 0;
+    m->S = N;
+    m->D = 0;
+    m->A = 0.0;
+    m->Bc = 0.0;
+    m->ud = 0.0;
+    m->xlo_bits = 0;
+    m->fast = 0;
+    if (lin) {
+      // certified filter: fixed point with rho = ilogb(R) - 60, R = max |x|
+      const double R = fmax(fabs(T::value(first)), fabs(T::value(last)));
+      fs.filter = (R > 0.0 && R < 0x1.0p1022) ? 1 : 0;
+      fs.rho = fs.filter ? (ilogb(R) - 60) : 0;
+    }
+  }
+  __syncthreads();
+  if (s_linear) {
+    const int Dcap = N / 3 + 1;  // smallest D with 3D > N
+    int D;
+    int capped = 0;
+    if (!fmcd_probe<K>(so, N, Dcap - 1, K_, fs)) {
+      capped = 1;
+      D = Dcap;
+    } else {
+      int lo = 1, hi = Dcap - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (fmcd_probe<K>(so, N, mid, K_, fs)) hi = mid; else lo = mid + 1;
+      }
+      D = lo;
+    }
+    if (threadIdx.x == 0) {
+      // the slope comes from u_d at D (or at D-1 after the 3D > N break)
+      const int Du = capped ? Dcap - 1 : D;
+      const double ud = __ddiv_rn(T::diff(T::unord(so[N - 1 - Du]), T::unord(so[Du])), (double)(K_ - 2));
+      const double A = __ddiv_rn(1.0, ud);
+      const Bits xhi = T::unord(so[N - 1 - D]), xlo = T::unord(so[D]);
+      const double span = T::diff(xhi, xlo);
+      const double prod = __dmul_rn(A, span);
+      const double Bc = __dmul_rn(__dsub_rn((double)K_, prod), 0.5);
+      m->S = N;
+      m->D = D;
+      m->capped = capped;
+      m->ud = ud;
+      m->A = A;
+      m->Bc = Bc;
+      m->xlo_bits = (uint64_t)xlo;
+      const bool ok = isfinite(ud) && ud > 0.0 && isfinite(A) && isfinite(Bc);
+      if (ok) {
+        m->kind = kLinear;
+        // fast path: rho so that the in-range half-width (nb+|Bc|)/A < 2^(rho+29)
+        const double tmax = __ddiv_rn(__dadd_rn((double)K_, fabs(Bc)), A);
+        int fast = isfinite(tmax) && tmax > 0.0;
+        int rho = fast ? ilogb(tmax) - 28 : 0;
+        bool sat = false;
+        const long long qlo = fast ? fixed_point<K>(xlo, rho, sat) : 0;
+        if (sat || qlo >= (1LL << 61) || qlo <= -(1LL << 61)) fast = 0;
+        const double a2r = ldexp(A, rho);
+        const float af = __double2float_rn(a2r);
+        if (!(af >= FLT_MIN) || !isfinite(af)) fast = 0;
+        const double cabs_d = fabs(Bc) * 0x1.0p-21 + 4.0 * a2r + 0x1.0p-40;
+        const float cabs = __double2float_ru(cabs_d * (1.0 + 0x1.0p-20));
+        if (!(cabs < 0x1.0p-8f)) fast = 0;
+        m->fast = fast;
+        m->rho = rho;
+        m->qlo = qlo;
+        m->af = af;
+        m->bcf = __double2float_rn(Bc);
+        m->crel = 0x1.0p-21f;
+        m->cabs = cabs;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && m->kind == kSplitter) {
+    // k-1 equidistant sample keys would give 2(k-1)+1 buckets; take (k-1)/2
+    // so that the splitter tree with equality buckets has at most k buckets.
+    const int want = (K_ - 1) / 2;
+    int cnt = 0;
+    for (int i = 0; i < want; ++i) {
+      const uint64_t u = (uint64_t)so[(int64_t)(i + 1) * N / (want + 1)];
+      if (cnt == 0 || m->split[cnt - 1] != u) m->split[cnt++] = u;
+    }
+    m->nsplit = cnt;
+    m->nb = 2 * cnt + 1;
+  }
+  __syncthreads();
+}
+
+// Splitter tree with equality buckets: p = #{s_i <= u}; bucket 2p-1 if
+// s_p == u, else bucket 2p.
+__device__ __forceinline__ int splitter_bucket(uint64_t u, const uint64_t* split, int nsplit) {
+  int lo = 0, hi = nsplit;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (split[mid] <= u) lo = mid + 1; else hi = mid;
+  }
+  if (lo > 0 && split[lo - 1] == u) return 2 * lo - 1;
+  return 2 * lo;
+}
+
+// The model equation in binary64 (reading: one fma, floor, clamp, cast).
+template <class K>
+__device__ __forceinline__ int classify_exact(typename KT<K>::Bits b, double A, double Bc,
+                                              typename KT<K>::Bits xlo, int nb) {
+  using T = KT<K>;
+  if (T::is_nan(b)) return T::negative(b) ? 0 : nb - 1;
+  const double d = T::diff(b, xlo);
+  const double v = floor(__fma_rn(A, d, Bc));
+  if (v < 0.0) return 0;
+  if (v >= (double)nb) return nb - 1;
+  return (int)v;
+}
+
+// Register copy of what one key's classification needs.
+template <class K>
+struct Classifier {
+  using Bits = typename KT<K>::Bits;
+  int kind, nb, fast, rho, nsplit;
+  long long qlo;
+  float af, bcf, crel, cabs;
+  double A, Bc;
+  Bits xlo;
+  const uint64_t* split;
+
+  __device__ __forceinline__ void load(const Model& m, int exact_only) {
+    kind = m.kind;
+    nb = m.nb;
+    fast = m.fast && !exact_only;
+    rho = m.rho;
+    qlo = m.qlo;
+    af = m.af;
+    bcf = m.bcf;
+    crel = m.crel;
+    cabs = m.cabs;
+    A = m.A;
+    Bc = m.Bc;
+    xlo = (Bits)m.xlo_bits;
+    nsplit = m.nsplit;
+    split = m.split;
+  }
+
+  // Fixed-point / FP32 evaluation; -1 when the certified interval around the
+  // FP32 value contains a bucket boundary.
+  __device__ __forceinline__ int fast_bucket(Bits b) const {
+    using T = KT<K>;
+    if (T::special(b)) return T::negative(b) ? 0 : nb - 1;
+    bool sat;
+    const long long X = fixed_point<K>(b, rho, sat);
+    if (sat) return X > 0 ? nb - 1 : 0;
+    const long long d = X - qlo;
+    if (d >= (1LL << 30)) return nb - 1;
+    if (d <= -(1LL << 30)) return 0;
+    const float df = __int2float_rn((int)d);
+    const float v = fmaf(af, df, bcf);
+    const float del = fmaf(crel, fabsf(v), cabs);
+    const float hi = v + del, lo = v - del;
+    if (hi < 1.0f) return 0;
+    if (lo >= (float)(nb - 1)) return nb - 1;
+    const float fl = floorf(lo), fh = floorf(hi);
+    if (fl == fh) return __float_as_int(fl + 8388608.0f) - 0x4B000000;
+    return -1;
+  }
+
+  __device__ __forceinline__ int bucket(Bits b) const {
+    if (kind == kSplitter) return splitter_bucket((uint64_t)KT<K>::ord(b), split, nsplit);
+    if (fast) {
+      const int r = fast_bucket(b);
+      if (r >= 0) return r;
+    }
+    return classify_exact<K>(b, A, Bc, xlo, nb);
+  }
+};
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+}  // namespace ipls

@@ -1,0 +1,189 @@
+// Internal layouts shared by the host runtime and the kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ipls {
+
+constexpr int kMaxK = 256;        // buckets per pass (paper: 256)
+constexpr int kMaxSplit = 127;    // splitters: 2*127+1 = 255 buckets
+constexpr int kTileKeys8 = 8192;  // grid-pass tile, 8-byte keys
+constexpr int kTileKeys4 = 16384; // grid-pass tile, 4-byte keys
+constexpr int kPassThreads = 512; // threads of the grid-pass kernels
+constexpr int kResidentMax = 8192;      // keys of one block-resident group
+constexpr int kResidentThreads = 512;
+constexpr int kResidentSample = 1024;   // sample capacity inside a resident block
+constexpr int kResidentTasks = 2048;    // pending ranges inside a resident block
+constexpr int kFitThreads = 1024;
+constexpr int kFillChunk = 65536;
+
+enum ModelKind : int32_t { kLinear = 0, kSplitter = 1 };
+
+// Partition model of one subproblem.  Linear: b(x) = clamp(floor(fma(A, x (-)
+// x_lo, Bc)), 0, nb-1) (Ch.3 model equation, centred).  Splitter: unique
+// splitters s_1 < ... < s_m as totalOrder keys, equality buckets at odd ids
+// (Ch.3 "Decision Trees").
+struct Model {
+  int32_t kind;
+  int32_t nb;
+  int32_t nsplit;
+  int32_t capped;
+  int64_t S;
+  int64_t D;
+  double A;
+  double Bc;
+  double ud;
+  uint64_t xlo_bits;
+  // Fixed-point / FP32 evaluation with a certified error bound: keys whose
+  // bound straddles a bucket boundary fall back to the binary64 formula.
+  int32_t fast;
+  int32_t rho;    // fixed-point scale: X(x) = trunc(x / 2^rho)
+  int64_t qlo;    // X(x_lo)
+  float af;       // RN32(A * 2^rho)
+  float bcf;      // RN32(Bc)
+  float crel;     // bound = crel*|v| + cabs
+  float cabs;
+  uint64_t split[128];
+};
+
+// A grid-level subproblem.
+struct Sub {
+  int64_t off;     // first key in the whole array
+  int64_t n;
+  int32_t level;
+  int32_t buf;     // 0 = user keys, 1 = scratch
+  int64_t tile0;   // first tile of this subproblem in the level's tile space
+  int32_t ntiles;
+  int32_t flags;
+};
+enum SubFlags : int32_t { kRehist = 1, kSkipScatter = 2 };
+
+// A block-resident group: consecutive children [off, off+n) of one parent
+// (or consecutive segments), each child an independent subproblem at `level`.
+// Child c spans [bounds[c]-bounds[0], bounds[c+1]-bounds[0]) inside the group.
+struct Group {
+  int64_t off;
+  const int64_t* bounds;
+  int32_t n;
+  int32_t level;
+  int32_t buf;
+  int32_t nchild;
+};
+
+// Keys [off, off+n) of the user buffer all equal to `bits`.
+struct Fill {
+  int64_t off;
+  int64_t n;
+  uint64_t bits;
+};
+
+// Device-side counters of one level (zeroed before the level).
+struct LevelCtl {
+  int32_t nsub_next;
+  int32_t ngroups;
+  int32_t nfill;
+  int32_t nrehist;
+  int64_t tiles_next;
+  uint32_t ticket;
+  int32_t overflow;      // a list capacity was exceeded
+  int64_t fallback;      // splitter passes
+  int64_t max_bucket;    // max over passes of largest bucket / n, scaled by 2^20
+  int64_t keys_moved;    // keys scattered by this level's grid passes
+  int64_t pad[3];
+};
+
+// Run-wide device status (persists across levels of one call).
+struct RunStatus {
+  int32_t error;         // 0 or a negative iplsStatus
+  int32_t where;         // which wait gave up (diagnostics)
+  int64_t trace_count;
+  int64_t resident_passes;
+  int64_t resident_fallback;
+  int64_t resident_keys;
+  int64_t resident_groups;
+};
+
+// Per-level device arrays (all device pointers).
+struct LevelArgs {
+  int dtype;
+  int k;
+  int cutoff;
+  int rmax;              // children above this size stay grid-level
+  int64_t root_sample;
+  uint64_t seed;
+  int exact_only;
+  int64_t spin_limit;
+  uint32_t epoch;        // look-back epoch of this level's scatter
+  int level;
+  int src_buf;           // buffer this level's subproblems live in
+  void* buf[2];          // 0 = user keys, 1 = scratch
+  int32_t nsub;
+  Sub* subs;
+  Model* models;
+  uint64_t* counts;      // [nsub][256]
+  int64_t* bases;        // [nsub][257]
+  int32_t* tile2sub;     // this level's tiles
+  int64_t ntiles;
+  unsigned long long* status;  // look-back words [ntiles][256]
+  LevelCtl* ctl;
+  RunStatus* run;
+  // outputs for the next level
+  Sub* next_subs;
+  int32_t next_sub_cap;
+  int32_t* next_tile2sub;
+  int64_t next_tile_cap;
+  Group* groups;
+  int32_t group_cap;
+  Fill* fills;
+  int32_t fill_cap;
+  // trace: grid passes of this level take records trace_base + s
+  struct iplsTraceRecDev* trace;
+  int64_t trace_cap;
+  int64_t trace_base;
+};
+
+struct ResidentArgs {
+  int dtype;
+  int k;
+  int cutoff;
+  int64_t root_sample;
+  uint64_t seed;
+  int exact_only;
+  void* buf[2];
+  const Group* groups;
+  int32_t ngroups;
+  RunStatus* run;
+  struct iplsTraceRecDev* trace;   // block-resident passes append here
+  int64_t trace_cap;
+};
+
+// Same layout as iplsTraceRec in the public header.
+struct iplsTraceRecDev {
+  int64_t off, n;
+  int32_t level, kind, capped, nbuckets;
+  int64_t S, D;
+  double A, Bc, ud;
+  uint64_t xlo_bits;
+  int32_t nsplit, where;
+  int64_t counts[256];
+};
+
+// Kernel launchers (defined in the .cu files).
+cudaError_t launch_fit(const LevelArgs& a, cudaStream_t s, int max_sample);
+cudaError_t launch_hist(const LevelArgs& a, cudaStream_t s, int rehist_only, int grid);
+cudaError_t launch_check(const LevelArgs& a, cudaStream_t s, int max_sample);
+cudaError_t launch_scan(const LevelArgs& a, cudaStream_t s);
+cudaError_t launch_scatter(const LevelArgs& a, cudaStream_t s, int grid);
+cudaError_t launch_resident(const ResidentArgs& a, cudaStream_t s);
+cudaError_t launch_init_segments(const int64_t* offsets, int64_t nseg, int rmax, int resident_ok,
+                                 LevelCtl* ctl, Sub* subs, int32_t sub_cap, int32_t* tile2sub,
+                                 int64_t tile_cap, Group* groups, int32_t group_cap, cudaStream_t s);
+int resident_rmax(int cutoff);
+cudaError_t launch_fill(const Fill* fills, int32_t nfill, int dtype, void* keys, cudaStream_t s);
+cudaError_t launch_init_tiles(int32_t* tile2sub, int64_t ntiles, int32_t value, cudaStream_t s);
+int tile_keys(int dtype);
+int key_bytes(int dtype);
+int sample_size_host(int64_t n, int level, int k, int64_t root_sample);
+
+}  // namespace ipls

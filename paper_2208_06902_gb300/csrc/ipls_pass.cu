@@ -1,0 +1,552 @@
+// Grid-wide learned partition pass over all subproblems of one level.
+//
+//   k_fit      one block per subproblem: sample alpha*k-1 keys, sort them,
+//              fit FMCD (Ch.3 listing) or the splitter tree, zero counts.
+//   k_hist     every tile of every subproblem: classify each key with the
+//              model (Ch.3 model equation), per-warp shared histograms,
+//              one global atomic per bucket per block and subproblem.
+//   k_check    no-progress rule: a linear pass that puts every key into one
+//              bucket is redone with the splitter tree from the same sample.
+//   k_scan     exclusive scan of the bucket counts -> bucket bases; children
+//              become next-level subproblems, block-resident groups, or
+//              (equality buckets) fills; records the trace.
+//   k_scatter  tiles in ticket order: classify again, rank each key stably
+//              inside the tile (warp match + per-warp counters), obtain the
+//              tile's offset inside every bucket by decoupled look-back,
+//              stage the tile in bucket order in shared memory and write the
+//              bucket runs out with coalesced stores (Ch.2 IPS4o: move every
+//              key into the region of its bucket).
+#include <cuda/atomic>
+
+#include "ipls_device.cuh"
+
+namespace ipls {
+
+constexpr int kTile = 8192;
+constexpr int kWarps = kPassThreads / 32;
+constexpr int kKPT = kTile / kPassThreads;   // keys per thread
+constexpr int kKPW = kTile / kWarps;         // keys per warp
+
+int tile_keys(int) { return kTile; }
+int key_bytes(int dtype) { return (dtype == 0 || dtype == 2) ? 8 : 4; }
+int sample_size_host(int64_t n, int level, int k, int64_t root_sample) {
+  return (int)sample_size(n, level, k, root_sample);
+}
+
+template <class K>
+__device__ __forceinline__ const typename KT<K>::Bits* buf_ptr(const LevelArgs& a, int b) {
+  return reinterpret_cast<const typename KT<K>::Bits*>(a.buf[b]);
+}
+
+// Copies a Model between memories with all threads of the block.
+__device__ __forceinline__ void copy_model(Model* dst, const Model* src) {
+  const unsigned long long* s = reinterpret_cast<const unsigned long long*>(src);
+  unsigned long long* d = reinterpret_cast<unsigned long long*>(dst);
+  for (int i = threadIdx.x; i < (int)(sizeof(Model) / 8); i += blockDim.x) d[i] = s[i];
+}
+
+// Gathers and sorts the sample of one subproblem (all threads).
+template <class K>
+__device__ int gather_sorted_sample(const LevelArgs& a, const Sub& sub,
+                                    typename KT<K>::Ord* so) {
+  using T = KT<K>;
+  const int S = (int)sample_size(sub.n, sub.level, a.k, a.root_sample);
+  const uint64_t st = stream_key(a.seed, sub.off, sub.n, sub.level);
+  const typename T::Bits* src = buf_ptr<K>(a, sub.buf);
+  for (int j = threadIdx.x; j < S; j += blockDim.x)
+    so[j] = T::ord(src[sub.off + sample_offset(st, j, sub.n)]);
+  __syncthreads();
+  block_sort(so, S);
+  return S;
+}
+
+template <class K>
+__device__ void build_splitters(const typename KT<K>::Ord* so, int N, int K_, Model* m) {
+  if (threadIdx.x == 0) {
+    const int want = (K_ - 1) / 2;
+    int cnt = 0;
+    for (int i = 0; i < want; ++i) {
+      const uint64_t u = (uint64_t)so[(int64_t)(i + 1) * N / (want + 1)];
+      if (cnt == 0 || m->split[cnt - 1] != u) m->split[cnt++] = u;
+    }
+    m->kind = kSplitter;
+    m->nsplit = cnt;
+    m->nb = 2 * cnt + 1;
+    m->fast = 0;
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+template <class K>
+__global__ void __launch_bounds__(kFitThreads) k_fit(LevelArgs a) {
+  using Ord = typename KT<K>::Ord;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ Model sm;
+  __shared__ FitShared fs;
+  Ord* so = reinterpret_cast<Ord*>(smem);
+  const int s = blockIdx.x;
+  const Sub sub = a.subs[s];
+  const int S = gather_sorted_sample<K>(a, sub, so);
+  fit_model<K>(so, S, a.k, &sm, fs);
+  copy_model(&a.models[s], &sm);
+  for (int b = threadIdx.x; b < kMaxK; b += blockDim.x) a.counts[(size_t)s * kMaxK + b] = 0;
+  if (threadIdx.x == 0) a.subs[s].flags = 0;
+}
+
+// ---------------------------------------------------------------------------
+template <class K>
+__global__ void __launch_bounds__(kPassThreads) k_hist(LevelArgs a, int rehist_only) {
+  using T = KT<K>;
+  using Bits = typename T::Bits;
+  __shared__ Model sm;
+  __shared__ unsigned int hist[kWarps][kMaxK];
+  __shared__ int s_cur;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = threadIdx.x; i < kWarps * kMaxK; i += blockDim.x) (&hist[0][0])[i] = 0;
+  const int64_t nt = a.ntiles;
+  const int64_t t0 = nt * blockIdx.x / gridDim.x, t1 = nt * (blockIdx.x + 1) / gridDim.x;
+  int cur = -1;
+  Classifier<K> cls;
+  for (int64_t t = t0; t < t1; ++t) {
+    const int s = a.tile2sub[t];
+    if (s != cur) {
+      __syncthreads();
+      if (cur >= 0) {
+        const int nb = sm.nb;
+        for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+          unsigned int tot = 0;
+          for (int w = 0; w < kWarps; ++w) { tot += hist[w][b]; hist[w][b] = 0; }
+          if (tot) atomicAdd((unsigned long long*)&a.counts[(size_t)cur * kMaxK + b], (unsigned long long)tot);
+        }
+      }
+      __syncthreads();
+      copy_model(&sm, &a.models[s]);
+      cur = s;
+      __syncthreads();
+      cls.load(sm, a.exact_only);
+    }
+    const Sub sub = a.subs[s];
+    if (rehist_only && !(sub.flags & kRehist)) continue;
+    const int64_t ti = t - sub.tile0;
+    const int64_t base = sub.off + ti * kTile;
+    const int64_t rem = sub.n - ti * kTile;
+    const int tn = rem < kTile ? (int)rem : kTile;
+    const Bits* src = buf_ptr<K>(a, sub.buf) + base;
+    Bits v[kKPT];
+#pragma unroll
+    for (int j = 0; j < kKPT; ++j) {
+      const int i = warp * kKPW + j * 32 + lane;
+      v[j] = (i < tn) ? src[i] : Bits(0);
+    }
+#pragma unroll
+    for (int j = 0; j < kKPT; ++j) {
+      const int i = warp * kKPW + j * 32 + lane;
+      if (i < tn) atomicAdd(&hist[warp][cls.bucket(v[j])], 1u);
+    }
+  }
+  __syncthreads();
+  if (cur >= 0) {
+    const int nb = sm.nb;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+      unsigned int tot = 0;
+      for (int w = 0; w < kWarps; ++w) tot += hist[w][b];
+      if (tot) atomicAdd((unsigned long long*)&a.counts[(size_t)cur * kMaxK + b], (unsigned long long)tot);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+template <class K>
+__global__ void __launch_bounds__(kFitThreads) k_check(LevelArgs a) {
+  using Ord = typename KT<K>::Ord;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ Model sm;
+  __shared__ int s_redo;
+  Ord* so = reinterpret_cast<Ord*>(smem);
+  const int s = blockIdx.x;
+  const Sub sub = a.subs[s];
+  if (threadIdx.x == 0) s_redo = 0;
+  __syncthreads();
+  const Model& gm = a.models[s];
+  if (gm.kind == kLinear) {
+    for (int b = threadIdx.x; b < gm.nb; b += blockDim.x)
+      if ((int64_t)a.counts[(size_t)s * kMaxK + b] == sub.n) s_redo = 1;
+  }
+  __syncthreads();
+  if (!s_redo) return;
+  copy_model(&sm, &gm);
+  __syncthreads();
+  const int S = gather_sorted_sample<K>(a, sub, so);
+  build_splitters<K>(so, S, a.k, &sm);
+  copy_model(&a.models[s], &sm);
+  for (int b = threadIdx.x; b < kMaxK; b += blockDim.x) a.counts[(size_t)s * kMaxK + b] = 0;
+  if (threadIdx.x == 0) {
+    a.subs[s].flags |= kRehist;
+    atomicAdd(&a.ctl->nrehist, 1);
+  }
+}
+
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int64_t block_exclusive_scan256(int64_t v, int64_t* tmp) {
+  // 256 threads; returns the exclusive prefix of v over thread order.
+  const int t = threadIdx.x;
+  tmp[t] = v;
+  __syncthreads();
+  for (int off = 1; off < 256; off <<= 1) {
+    const int64_t x = (t >= off) ? tmp[t - off] : 0;
+    __syncthreads();
+    tmp[t] += x;
+    __syncthreads();
+  }
+  const int64_t incl = tmp[t];
+  __syncthreads();
+  return incl - v;
+}
+
+template <class K>
+__device__ void append_fill(const LevelArgs& a, int64_t off, int64_t n, uint64_t bits) {
+  for (int64_t o = 0; o < n; o += kFillChunk) {
+    const int i = atomicAdd(&a.ctl->nfill, 1);
+    if (i >= a.fill_cap) { a.ctl->overflow = 1; return; }
+    a.fills[i] = Fill{off + o, (n - o) < kFillChunk ? (n - o) : (int64_t)kFillChunk, bits};
+  }
+}
+
+template <class K>
+__global__ void __launch_bounds__(256) k_scan(LevelArgs a) {
+  using T = KT<K>;
+  __shared__ int64_t tmp[256];
+  __shared__ int64_t cnt[256];
+  __shared__ int64_t bas[257];
+  __shared__ int s_skip;
+  const int s = blockIdx.x, b = threadIdx.x;
+  const Sub sub = a.subs[s];
+  const Model& m = a.models[s];
+  const int nb = m.nb;
+  const int dst_buf = 1 - sub.buf;
+  const int64_t c = (b < nb) ? (int64_t)a.counts[(size_t)s * kMaxK + b] : 0;
+  cnt[b] = c;
+  const int64_t ex = block_exclusive_scan256(c, tmp);
+  bas[b] = ex;
+  if (b == 255) bas[256] = ex + c;
+  if (b == 0) s_skip = 0;
+  __syncthreads();
+  int64_t* gb = a.bases + (size_t)s * 257;
+  gb[b] = bas[b];
+  if (b == 0) gb[256] = bas[256];
+  const bool eq = (m.kind == kSplitter) && (b & 1) && b < nb;
+  if (eq && c == sub.n) s_skip = 1;
+  // trace: this level's grid passes own records trace_base + s
+  if (a.trace_cap > 0 && a.trace_base + s < a.trace_cap) {
+    iplsTraceRecDev& r = a.trace[a.trace_base + s];
+    if (b == 0) {
+      r.off = sub.off; r.n = sub.n; r.level = sub.level; r.kind = m.kind;
+      r.capped = m.capped; r.nbuckets = nb; r.S = m.S; r.D = m.D; r.A = m.A;
+      r.Bc = m.Bc; r.ud = m.ud; r.xlo_bits = m.xlo_bits; r.nsplit = m.nsplit; r.where = 0;
+    }
+    r.counts[b] = c;
+  }
+  __syncthreads();
+  if (s_skip) {
+    // homogeneous subproblem: every key equals one splitter; nothing moves
+    if (b == 0) {
+      a.subs[s].flags |= kSkipScatter;
+      if (sub.buf != 0) {
+        int j = 0;
+        for (int q = 1; q < nb; q += 2) if (cnt[q] == sub.n) j = q;
+        append_fill<K>(a, sub.off, sub.n, (uint64_t)T::unord((typename T::Ord)m.split[(j - 1) / 2]));
+      }
+    }
+  } else if (c > 0) {
+    if (eq) {
+      if (dst_buf != 0)
+        append_fill<K>(a, sub.off + bas[b], c, (uint64_t)T::unord((typename T::Ord)m.split[(b - 1) / 2]));
+    } else if (c > a.rmax) {
+      const int i = atomicAdd(&a.ctl->nsub_next, 1);
+      const int nt = (int)((c + kTile - 1) / kTile);
+      const long long t0 = (long long)atomicAdd((unsigned long long*)&a.ctl->tiles_next,
+                                                (unsigned long long)nt);
+      if (i >= a.next_sub_cap || t0 + nt > a.next_tile_cap) {
+        a.ctl->overflow = 1;
+      } else {
+        a.next_subs[i] = Sub{sub.off + bas[b], c, sub.level + 1, dst_buf, t0, nt, 0};
+        for (int q = 0; q < nt; ++q) a.next_tile2sub[t0 + q] = i;
+      }
+    }
+  }
+  if (!s_skip && b == 0) {
+    // pack consecutive resident-size buckets into groups of <= rmax keys
+    int b0 = -1, blast = -1;
+    int64_t tot = 0;
+    for (int q = 0; q <= nb; ++q) {
+      const int64_t cq = (q < nb) ? cnt[q] : 0;
+      const bool eqq = (q < nb) && (m.kind == kSplitter) && (q & 1);
+      const bool brk = (q == nb) || (cq > 0 && (eqq || cq > a.rmax));
+      const bool fits = (cq > 0) && !brk;
+      if (b0 >= 0 && (brk || (fits && tot + cq > a.rmax))) {
+        const int g = atomicAdd(&a.ctl->ngroups, 1);
+        if (g >= a.group_cap) a.ctl->overflow = 1;
+        else a.groups[g] = Group{sub.off + bas[b0], gb + b0, (int32_t)tot, sub.level + 1,
+                                 dst_buf, blast - b0 + 1};
+        b0 = -1;
+        tot = 0;
+      }
+      if (fits) {
+        if (b0 < 0) b0 = q;
+        tot += cq;
+        blast = q;
+      }
+    }
+    if (m.kind == kSplitter) atomicAdd((unsigned long long*)&a.ctl->fallback, 1ULL);
+    atomicAdd((unsigned long long*)&a.ctl->keys_moved, (unsigned long long)sub.n);
+    int64_t mx = 0;
+    for (int q = 0; q < nb; ++q) mx = cnt[q] > mx ? cnt[q] : mx;
+    const long long frac = (long long)((double)mx * 1048576.0 / (double)sub.n);
+    atomicMax((unsigned long long*)&a.ctl->max_bucket, (unsigned long long)frac);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Look-back status word: [63:48] epoch, [47:46] flag (1 aggregate, 2
+// inclusive prefix), [45:0] count.
+constexpr unsigned long long kFlagAgg = 1ULL << 46;
+constexpr unsigned long long kFlagPre = 2ULL << 46;
+constexpr unsigned long long kValMask = (1ULL << 46) - 1;
+
+__device__ __forceinline__ void st_release(unsigned long long* p, unsigned long long v) {
+  cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> r(*p);
+  r.store(v, cuda::memory_order_release);
+}
+__device__ __forceinline__ unsigned long long ld_acquire(unsigned long long* p) {
+  cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> r(*p);
+  return r.load(cuda::memory_order_acquire);
+}
+
+template <class K>
+struct ScatterSmem {
+  typename KT<K>::Bits stage[kTile];
+  unsigned char sbid[kTile];
+  unsigned short wcnt[kWarps][kMaxK];
+  int tile_start[kMaxK];
+  int tile_tot[kMaxK];
+  long long gbase[kMaxK];
+  long long tmp[kMaxK];
+  Model model;
+  int cur, t, abort_tile;
+};
+
+template <class K>
+__global__ void __launch_bounds__(kPassThreads, 2) k_scatter(LevelArgs a) {
+  using T = KT<K>;
+  using Bits = typename T::Bits;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ScatterSmem<K>& sh = *reinterpret_cast<ScatterSmem<K>*>(smem_raw);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned long long ep = (unsigned long long)(a.epoch & 0xFFFF) << 48;
+  if (threadIdx.x == 0) sh.cur = -1;
+  Classifier<K> cls;
+  Bits* dst_base[2] = {reinterpret_cast<Bits*>(a.buf[0]), reinterpret_cast<Bits*>(a.buf[1])};
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      sh.t = (int)atomicAdd(&a.ctl->ticket, 1u);
+      sh.abort_tile = 0;
+    }
+    __syncthreads();
+    const int64_t t = sh.t;
+    if (t >= a.ntiles) break;
+    const int s = a.tile2sub[t];
+    const Sub sub = a.subs[s];
+    if (sub.flags & kSkipScatter) continue;
+    if (s != sh.cur) {
+      copy_model(&sh.model, &a.models[s]);
+      __syncthreads();
+      if (threadIdx.x == 0) sh.cur = s;
+    }
+    cls.load(sh.model, a.exact_only);
+    for (int i = threadIdx.x; i < kWarps * kMaxK; i += blockDim.x) (&sh.wcnt[0][0])[i] = 0;
+    const int64_t ti = t - sub.tile0;
+    const int64_t kbase = sub.off + ti * kTile;
+    const int64_t rem = sub.n - ti * kTile;
+    const int tn = rem < kTile ? (int)rem : kTile;
+    const Bits* src = reinterpret_cast<const Bits*>(a.buf[sub.buf]) + kbase;
+    Bits v[kKPT];
+    unsigned int br[kKPT];   // bucket << 16 | rank within warp
+#pragma unroll
+    for (int j = 0; j < kKPT; ++j) {
+      const int i = warp * kKPW + j * 32 + lane;
+      v[j] = (i < tn) ? src[i] : Bits(0);
+    }
+    __syncthreads();  // wcnt zeroed
+#pragma unroll
+    for (int j = 0; j < kKPT; ++j) {
+      const int i = warp * kKPW + j * 32 + lane;
+      const int bk = (i < tn) ? cls.bucket(v[j]) : kMaxK;
+      const unsigned peers = __match_any_sync(0xffffffffu, bk);
+      const int lt = __popc(peers & lanemask_lt());
+      const int leader = __ffs(peers) - 1;
+      const int basec = (bk < kMaxK) ? sh.wcnt[warp][bk] : 0;
+      br[j] = ((unsigned)bk << 16) | (unsigned)(basec + lt);
+      __syncwarp();
+      if (lane == leader && bk < kMaxK) sh.wcnt[warp][bk] = (unsigned short)(basec + __popc(peers));
+      __syncwarp();
+    }
+    __syncthreads();
+    unsigned long long* st = a.status + (size_t)t * kMaxK;
+    if (threadIdx.x < kMaxK) {
+      const int b = threadIdx.x;
+      int run = 0;
+      for (int w = 0; w < kWarps; ++w) {
+        const int x = sh.wcnt[w][b];
+        sh.wcnt[w][b] = (unsigned short)run;
+        run += x;
+      }
+      sh.tile_tot[b] = run;
+      st_release(&st[b], ep | (ti == 0 ? kFlagPre : kFlagAgg) | (unsigned long long)run);
+    }
+    // tile-local bucket starts (exclusive scan over buckets)
+    if (threadIdx.x < kMaxK) sh.tmp[threadIdx.x] = sh.tile_tot[threadIdx.x];
+    __syncthreads();
+    for (int off = 1; off < kMaxK; off <<= 1) {
+      long long x = 0;
+      if (threadIdx.x < kMaxK && threadIdx.x >= off) x = sh.tmp[threadIdx.x - off];
+      __syncthreads();
+      if (threadIdx.x < kMaxK) sh.tmp[threadIdx.x] += x;
+      __syncthreads();
+    }
+    if (threadIdx.x < kMaxK) {
+      const int b = threadIdx.x;
+      const int tot = sh.tile_tot[b];
+      sh.tile_start[b] = (int)(sh.tmp[b] - tot);
+      long long excl = 0;
+      if (ti > 0) {
+        int64_t j = t - 1;
+        long long spins = 0;
+        for (;;) {
+          const unsigned long long w = ld_acquire(&a.status[(size_t)j * kMaxK + b]);
+          if ((w & ~((1ULL << 48) - 1)) == ep && (w & (3ULL << 46))) {
+            excl += (long long)(w & kValMask);
+            if (w & kFlagPre) break;
+            --j;
+            continue;
+          }
+          if (++spins > a.spin_limit) {
+            atomicExch(&a.run->error, -4);
+            atomicExch(&a.run->where, 1);
+            sh.abort_tile = 1;
+            break;
+          }
+          __nanosleep(64);
+        }
+        st_release(&st[b], ep | kFlagPre | (unsigned long long)(excl + tot));
+      }
+      sh.gbase[b] = sub.off + a.bases[(size_t)s * 257 + b] + excl - sh.tile_start[b];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kKPT; ++j) {
+      const int bk = (int)(br[j] >> 16);
+      if (bk < kMaxK) {
+        const int lp = sh.tile_start[bk] + sh.wcnt[warp][bk] + (int)(br[j] & 0xFFFF);
+        sh.stage[lp] = v[j];
+        sh.sbid[lp] = (unsigned char)bk;
+      }
+    }
+    __syncthreads();
+    if (!sh.abort_tile) {
+      Bits* dst = dst_base[1 - sub.buf];
+      const int64_t lo = sub.off, hi = sub.off + sub.n;
+      for (int i = threadIdx.x; i < tn; i += blockDim.x) {
+        const int64_t p = sh.gbase[sh.sbid[i]] + i;
+        if (p >= lo && p < hi) dst[p] = sh.stage[i];
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+__global__ void k_init_tiles(int32_t* tile2sub, int64_t ntiles, int32_t value) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ntiles;
+       i += (int64_t)gridDim.x * blockDim.x)
+    tile2sub[i] = value;
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+template <class F>
+static cudaError_t by_dtype(int dtype, F f) {
+  switch (dtype) {
+    case 0: return f((double*)nullptr);
+    case 1: return f((float*)nullptr);
+    case 2: return f((unsigned long long*)nullptr);
+    case 3: return f((unsigned int*)nullptr);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_fit(const LevelArgs& a, cudaStream_t s, int max_sample) {
+  if (a.nsub <= 0) return cudaSuccess;
+  return by_dtype(a.dtype, [&](auto* tag) {
+    using K = std::remove_pointer_t<decltype(tag)>;
+    const size_t smem = (size_t)max_sample * sizeof(typename KT<K>::Ord);
+    cudaFuncSetAttribute(k_fit<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_fit<K><<<a.nsub, kFitThreads, smem, s>>>(a);
+    return cudaGetLastError();
+  });
+}
+
+cudaError_t launch_check(const LevelArgs& a, cudaStream_t s, int max_sample) {
+  if (a.nsub <= 0) return cudaSuccess;
+  return by_dtype(a.dtype, [&](auto* tag) {
+    using K = std::remove_pointer_t<decltype(tag)>;
+    const size_t smem = (size_t)max_sample * sizeof(typename KT<K>::Ord);
+    cudaFuncSetAttribute(k_check<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_check<K><<<a.nsub, kFitThreads, smem, s>>>(a);
+    return cudaGetLastError();
+  });
+}
+
+cudaError_t launch_hist(const LevelArgs& a, cudaStream_t s, int rehist_only, int grid) {
+  if (a.ntiles <= 0) return cudaSuccess;
+  return by_dtype(a.dtype, [&](auto* tag) {
+    using K = std::remove_pointer_t<decltype(tag)>;
+    int g = grid;
+    if (g > a.ntiles) g = (int)a.ntiles;
+    k_hist<K><<<g, kPassThreads, 0, s>>>(a, rehist_only);
+    return cudaGetLastError();
+  });
+}
+
+cudaError_t launch_scan(const LevelArgs& a, cudaStream_t s) {
+  if (a.nsub <= 0) return cudaSuccess;
+  return by_dtype(a.dtype, [&](auto* tag) {
+    using K = std::remove_pointer_t<decltype(tag)>;
+    k_scan<K><<<a.nsub, 256, 0, s>>>(a);
+    return cudaGetLastError();
+  });
+}
+
+cudaError_t launch_scatter(const LevelArgs& a, cudaStream_t s, int grid) {
+  if (a.ntiles <= 0) return cudaSuccess;
+  return by_dtype(a.dtype, [&](auto* tag) {
+    using K = std::remove_pointer_t<decltype(tag)>;
+    const size_t smem = sizeof(ScatterSmem<K>);
+    cudaFuncSetAttribute(k_scatter<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int g = grid;
+    if (g > a.ntiles) g = (int)a.ntiles;
+    k_scatter<K><<<g, kPassThreads, smem, s>>>(a);
+    return cudaGetLastError();
+  });
+}
+
+cudaError_t launch_init_tiles(int32_t* tile2sub, int64_t ntiles, int32_t value, cudaStream_t s) {
+  if (ntiles <= 0) return cudaSuccess;
+  int g = (int)((ntiles + 255) / 256);
+  if (g > 4096) g = 4096;
+  k_init_tiles<<<g, 256, 0, s>>>(tile2sub, ntiles, value);
+  return cudaGetLastError();
+}
+
+}  // namespace ipls

@@ -1,0 +1,232 @@
+"""ctypes binding of the C ABI in include/ipls.h (argument marshalling only).
+
+Every function here forwards to the CUDA library libipls.so; nothing is
+computed in Python.  Loading fails loudly when the library is missing: there
+is no CPU fallback.  Tensors are torch CUDA tensors (device memory, streams);
+the raw ``iplsXxx`` functions take plain integers (pointers) like the C ABI.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+F64, F32, U64, U32 = 0, 1, 2, 3
+IPLS_OK, IPLS_PENDING = 0, 1
+STATUS_NAMES = {0: "IPLS_OK", 1: "IPLS_PENDING", -1: "IPLS_ERR_ARG", -2: "IPLS_ERR_OOM",
+                -3: "IPLS_ERR_CUDA", -4: "IPLS_ERR_TIMEOUT", -5: "IPLS_ERR_BUDGET",
+                -6: "IPLS_ERR_INTERNAL"}
+
+
+class iplsConfig(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("cutoff", ctypes.c_int32),
+                ("root_sample", ctypes.c_int64), ("seed", ctypes.c_uint64),
+                ("sync", ctypes.c_int32), ("exact_only", ctypes.c_int32),
+                ("spin_limit", ctypes.c_int64), ("trace_cap", ctypes.c_int64),
+                ("budget_bytes", ctypes.c_int64), ("reserved", ctypes.c_int32 * 8)]
+
+
+class iplsTraceRec(ctypes.Structure):
+    _fields_ = [("off", ctypes.c_int64), ("n", ctypes.c_int64), ("level", ctypes.c_int32),
+                ("kind", ctypes.c_int32), ("capped", ctypes.c_int32),
+                ("nbuckets", ctypes.c_int32), ("S", ctypes.c_int64), ("D", ctypes.c_int64),
+                ("A", ctypes.c_double), ("Bc", ctypes.c_double), ("ud", ctypes.c_double),
+                ("xlo_bits", ctypes.c_uint64), ("nsplit", ctypes.c_int32),
+                ("where", ctypes.c_int32), ("counts", ctypes.c_int64 * 256)]
+
+
+class iplsStats(ctypes.Structure):
+    _fields_ = [("calls", ctypes.c_int64), ("grid_levels", ctypes.c_int64),
+                ("grid_passes", ctypes.c_int64), ("keys_partitioned", ctypes.c_int64),
+                ("resident_groups", ctypes.c_int64), ("fallback_passes", ctypes.c_int64),
+                ("algorithmic_bytes", ctypes.c_int64), ("scratch_bytes", ctypes.c_int64),
+                ("trace_records", ctypes.c_int64), ("max_bucket_frac", ctypes.c_double)]
+
+
+_lib = None
+SYMBOLS = ["iplsDefaultConfig", "iplsCreate", "iplsDestroy", "iplsScratchBytes", "iplsSort",
+           "iplsSortSegmented", "iplsSubmit", "iplsPoll", "iplsWait", "iplsGetStats",
+           "iplsGetTrace", "iplsLastError"]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Loads libipls.so (building it with nvcc if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libipls.so not found at {path}: build it with "
+                           "paper_2208_06902_gb300.build.build()")
+    L = ctypes.CDLL(path)
+    c = ctypes
+    P = c.c_void_p
+    L.iplsDefaultConfig.argtypes = [c.POINTER(iplsConfig)]
+    L.iplsCreate.argtypes = [c.POINTER(P), c.POINTER(iplsConfig), P, P, P, P]
+    L.iplsDestroy.argtypes = [P]
+    L.iplsScratchBytes.argtypes = [P, c.c_int64, c.c_int, c.POINTER(c.c_size_t)]
+    L.iplsSort.argtypes = [P, P, c.c_int64, c.c_int]
+    L.iplsSortSegmented.argtypes = [P, P, P, c.c_int64, c.c_int]
+    L.iplsSubmit.argtypes = [P, P, c.c_int64, c.c_int, c.POINTER(c.c_uint64)]
+    L.iplsPoll.argtypes = [P, c.c_uint64]
+    L.iplsWait.argtypes = [P, c.c_uint64, c.c_int64]
+    L.iplsGetStats.argtypes = [P, c.POINTER(iplsStats)]
+    L.iplsGetTrace.argtypes = [P, c.POINTER(iplsTraceRec), c.c_int64, c.POINTER(c.c_int64)]
+    L.iplsLastError.restype = c.c_char_p
+    for name in SYMBOLS:
+        if name != "iplsLastError":
+            getattr(L, name).restype = c.c_int
+    _lib = L
+    return L
+
+
+class IPLSError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = load().iplsLastError().decode(errors="replace")
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)} ({msg})")
+        self.status = status
+
+
+def _check(st: int, where: str) -> int:
+    if st < 0:
+        raise IPLSError(st, where)
+    return st
+
+
+# ---- raw C-ABI functions (same names, integer pointers) -------------------
+def iplsDefaultConfig() -> iplsConfig:
+    cfg = iplsConfig()
+    _check(load().iplsDefaultConfig(ctypes.byref(cfg)), "iplsDefaultConfig")
+    return cfg
+
+
+def iplsCreate(cfg: iplsConfig | None = None, stream: int = 0) -> int:
+    ctx = ctypes.c_void_p()
+    _check(load().iplsCreate(ctypes.byref(ctx), ctypes.byref(cfg) if cfg is not None else None,
+                             None, None, None, ctypes.c_void_p(stream)), "iplsCreate")
+    return ctx.value
+
+
+def iplsDestroy(ctx: int) -> None:
+    _check(load().iplsDestroy(ctypes.c_void_p(ctx)), "iplsDestroy")
+
+
+def iplsScratchBytes(ctx: int | None, n: int, dtype: int) -> int:
+    b = ctypes.c_size_t()
+    _check(load().iplsScratchBytes(ctypes.c_void_p(ctx), n, dtype, ctypes.byref(b)),
+           "iplsScratchBytes")
+    return b.value
+
+
+def iplsSort(ctx: int | None, keys_ptr: int, n: int, dtype: int) -> int:
+    return _check(load().iplsSort(ctypes.c_void_p(ctx), ctypes.c_void_p(keys_ptr), n, dtype),
+                  "iplsSort")
+
+
+def iplsSortSegmented(ctx: int | None, keys_ptr: int, offsets_ptr: int, nseg: int,
+                      dtype: int) -> int:
+    return _check(load().iplsSortSegmented(ctypes.c_void_p(ctx), ctypes.c_void_p(keys_ptr),
+                                           ctypes.c_void_p(offsets_ptr), nseg, dtype),
+                  "iplsSortSegmented")
+
+
+def iplsSubmit(ctx: int, keys_ptr: int, n: int, dtype: int) -> int:
+    t = ctypes.c_uint64()
+    _check(load().iplsSubmit(ctypes.c_void_p(ctx), ctypes.c_void_p(keys_ptr), n, dtype,
+                             ctypes.byref(t)), "iplsSubmit")
+    return t.value
+
+
+def iplsPoll(ctx: int, ticket: int) -> int:
+    return _check(load().iplsPoll(ctypes.c_void_p(ctx), ticket), "iplsPoll")
+
+
+def iplsWait(ctx: int, ticket: int, timeout_us: int = -1) -> int:
+    return _check(load().iplsWait(ctypes.c_void_p(ctx), ticket, timeout_us), "iplsWait")
+
+
+def iplsGetStats(ctx: int) -> iplsStats:
+    s = iplsStats()
+    _check(load().iplsGetStats(ctypes.c_void_p(ctx), ctypes.byref(s)), "iplsGetStats")
+    return s
+
+
+def iplsGetTrace(ctx: int, cap: int) -> list:
+    out = (iplsTraceRec * max(cap, 1))()
+    cnt = ctypes.c_int64()
+    _check(load().iplsGetTrace(ctypes.c_void_p(ctx), out, cap, ctypes.byref(cnt)),
+           "iplsGetTrace")
+    return list(out[: cnt.value])
+
+
+def iplsLastError() -> str:
+    return load().iplsLastError().decode(errors="replace")
+
+
+# ---- tensor conveniences ---------------------------------------------------
+def dtype_code(t) -> int:
+    import torch
+    m = {torch.float64: F64, torch.float32: F32, torch.uint64: U64, torch.uint32: U32,
+         torch.int64: U64, torch.int32: U32}
+    if t.dtype not in m:
+        raise TypeError(f"unsupported dtype {t.dtype}")
+    return m[t.dtype]
+
+
+class Context:
+    """Owns an iplsCtx bound to a CUDA stream (default: torch's current)."""
+
+    def __init__(self, *, k: int = 256, cutoff: int = 32, root_sample: int = 0, seed: int = 0,
+                 exact_only: bool = False, trace_cap: int = 0, spin_limit: int | None = None,
+                 stream=None, budget_bytes: int = 0):
+        import torch
+        cfg = iplsDefaultConfig()
+        cfg.k, cfg.cutoff, cfg.root_sample, cfg.seed = k, cutoff, root_sample, seed
+        cfg.exact_only = 1 if exact_only else 0
+        cfg.trace_cap = trace_cap
+        cfg.budget_bytes = budget_bytes
+        if spin_limit is not None:
+            cfg.spin_limit = spin_limit
+        s = stream if stream is not None else torch.cuda.current_stream()
+        self.stream = s
+        self.ctx = iplsCreate(cfg, s.cuda_stream)
+        self.trace_cap = trace_cap
+
+    def sort_(self, keys) -> None:
+        """Sorts a contiguous CUDA tensor in place."""
+        assert keys.is_cuda and keys.is_contiguous()
+        iplsSort(self.ctx, keys.data_ptr(), keys.numel(), dtype_code(keys))
+
+    def sort_ptr(self, ptr: int, n: int, dtype: int) -> None:
+        iplsSort(self.ctx, ptr, n, dtype)
+
+    def sort_segmented_(self, keys, offsets) -> None:
+        """Sorts keys[offsets[i]:offsets[i+1]] for each i (offsets: int64 CUDA tensor)."""
+        import torch
+        assert offsets.is_cuda and offsets.dtype == torch.int64 and offsets.is_contiguous()
+        iplsSortSegmented(self.ctx, keys.data_ptr(), offsets.data_ptr(), offsets.numel() - 1,
+                          dtype_code(keys))
+
+    def stats(self) -> iplsStats:
+        return iplsGetStats(self.ctx)
+
+    def trace(self) -> list:
+        return iplsGetTrace(self.ctx, self.trace_cap)
+
+    def close(self) -> None:
+        if getattr(self, "ctx", None):
+            iplsDestroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,55 @@
+"""The C-ABI library builds, loads and exports every declared entry point
+(no GPU needed: nothing here launches a kernel)."""
+import ctypes
+import os
+import re
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "ipls.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\**\s+\**(ipls\w+)\s*\(", src, flags=re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for want in ["iplsCreate", "iplsDestroy", "iplsScratchBytes", "iplsSort", "iplsSortSegmented",
+                 "iplsSubmit", "iplsPoll", "iplsWait", "iplsLastError", "iplsGetStats"]:
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol():
+    import paper_2208_06902_gb300 as p
+    lib = p.load()
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+        assert ctypes.cast(getattr(lib, name), ctypes.c_void_p).value
+
+
+def test_host_side_validation_without_gpu():
+    # argument checks happen before any CUDA call
+    import paper_2208_06902_gb300 as p
+    lib = p.load()
+    assert lib.iplsDefaultConfig(None) == -1
+    assert lib.iplsSort(None, None, -5, 0) == -1
+    assert lib.iplsSort(None, None, 10, 7) == -1
+    assert lib.iplsSort(None, None, 2**41, 0) == -1
+    assert lib.iplsSort(None, None, 10, 0) == -1      # NULL keys
+    assert "NULL" in p.iplsLastError()
+    assert lib.iplsSortSegmented(None, None, None, -1, 0) == -1
+    assert lib.iplsSortSegmented(None, None, None, 0, 0) == 0   # nothing to do
+    cfg = p.iplsDefaultConfig()
+    assert (cfg.k, cfg.cutoff, cfg.sync) == (256, 32, 1)
+    n = p.iplsScratchBytes(None, 1 << 28, 0)
+    assert n >= (1 << 28) * 8
+
+
+def test_product_package_does_not_import_the_oracle():
+    pkg = os.path.join(ROOT, "paper_2208_06902_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in text and "ipls_oracle" not in text, f
