@@ -1,0 +1,376 @@
+#!/usr/bin/env python3
+"""Throughput of the GB300 learned sort (IPLS learned partitioning pass).
+
+Workload (one step): sort one array of 2^28 float64 keys with the whole IPLS
+recursion (k = 256, alpha*k-1 samples, cutoff 32).  The K timed steps cycle
+through eight seeded synthetic distributions (Normal(0,1), LogNormal(0,0.5),
+Exponential(2), 5-Gaussian mixture, Zipf(0.75), root-dups, two-dups,
+eight-dups) that stand in for the paper's synthetic benchmark datasets.
+
+value   = keys sorted / device time of the sort calls (CUDA events on the
+          context's stream), inputs resident in HBM; between steps a 2 GiB
+          copy restores the input, which also flushes the 129 MB L2.
+e2e     = same metric through iplsSortHost with pinned host buffers: the
+          host->device copy, the sort and the device->host copy are timed.
+roofline: the kernel with the largest device time; algorithmic bytes (keys
+          read + written by its launches) / its summed launch time, against
+          the measured HBM copy bandwidth.
+cpu_baseline: the serial CPU oracle on a bounded prefix sample of the same
+          arrays, timed on this host (rank 0, N=1 only).
+
+--impl reference runs the oracle (the CPU reference implementation written
+from the paper) as the comparison arm on the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DISTS = ["normal", "lognormal", "exponential", "mixgauss", "zipf", "rootdups", "twodups",
+         "eightdups"]
+METRIC = "Gkeys/s sorting 2^28 f64 keys (IPLS learned partition sort)"
+UNIT = "Gkeys/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=8)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--log2n", type=int, default=28)
+    p.add_argument("--cutoff", type=int, default=32)
+    p.add_argument("--e2e-steps", type=int, default=4)
+    p.add_argument("--cpu-sample-log2", type=int, default=23)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-torch-sort", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def source_digest() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2208_06902_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str, launch_bytes_scale: float):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or
+    None when the summary is missing or the kernel sources changed since."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    if d.get("source_digest") != source_digest():
+        return None
+    k = d.get("kernels", {}).get(kernel)
+    if not k:
+        return None
+    return float(k["dram_bytes_per_key"]) * launch_bytes_scale
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms (one GPU)."""
+
+    FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.proc = None
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "200"]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        self.file.flush()
+        rows = []
+        try:
+            with open(self.file.name) as f:
+                for line in f:
+                    parts = [x.strip() for x in line.split(",")]
+                    if len(parts) < 10:
+                        continue
+                    if self.uuid and parts[1] != self.uuid:
+                        continue
+                    rows.append(parts)
+        finally:
+            os.unlink(self.file.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[6 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def make_inputs(n: int):
+    import datagen
+    return {d: datagen.config2(d, n) for d in DISTS}
+
+
+def cpu_baseline(inputs, sample_log2: int):
+    import oracle
+    m = 1 << sample_log2
+    keys = 0
+    t0 = time.perf_counter()
+    for d in DISTS:
+        x = inputs[d][:m]
+        oracle.sort(x, cutoff=32)
+        keys += x.size
+    dt = time.perf_counter() - t0
+    return {"value": keys / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first 2^{sample_log2} keys of each of the 8 arrays "
+                      f"({keys} keys, serial C++ oracle, {dt:.1f} s)"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import datagen
+    import oracle
+    oracle.build()
+    m = 1 << min(args.cpu_sample_log2, args.log2n)
+    # the first m keys of each 2^log2n array (the generators are counter-based,
+    # so the prefix is generated without the rest of the array)
+    samples = {d: datagen.generate(d, 1 << args.log2n, "float64", seed=DISTS.index(d) + 1,
+                                   lo=0, hi=m) for d in DISTS}
+    for i in range(args.warmup):
+        oracle.sort(samples[DISTS[i % len(DISTS)]], cutoff=args.cutoff)
+    t0 = time.perf_counter()
+    keys = 0
+    for i in range(args.steps):
+        x = samples[DISTS[i % len(DISTS)]]
+        oracle.sort(x, cutoff=args.cutoff)
+        keys += x.size
+    dt = time.perf_counter() - t0
+    value = keys / dt / 1e9
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"IPLS sort of 2^{args.log2n} f64 keys, 8 distributions",
+                       "per_step": f"the first 2^{int(m).bit_length() - 1} keys of one array",
+                       "k": 256, "cutoff": args.cutoff},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"first {m} keys of each array, serial C++ oracle"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gb300(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    import paper_2208_06902_gb300 as ipls
+    ipls.load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    n = 1 << args.log2n
+    inputs = make_inputs(n)
+    pristine = {d: torch.from_numpy(inputs[d].view(np.uint8)).to(dev) for d in DISTS}
+    work = torch.empty(n * 8, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    ctx = ipls.Context(cutoff=args.cutoff, profile=True, stream=stream)
+
+    def step(i, timed):
+        d = DISTS[i % len(DISTS)]
+        work.copy_(pristine[d])  # restores the input; 4 GB of traffic flushes L2
+        if timed:
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ctx.sort_ptr(work.data_ptr(), n, ipls.F64)
+            b.record(stream)
+            return d, a, b
+        ctx.sort_ptr(work.data_ptr(), n, ipls.F64)
+        return d, None, None
+
+    for i in range(args.warmup):
+        step(i, False)
+    # correctness guard on the last warm-up output (cheap: monotone check)
+    chk = work.view(torch.float64)
+    assert bool((chk[1:] >= chk[:-1]).all()), "bench: output not sorted"
+    torch.cuda.synchronize()
+
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    sampler = ClockSampler(uuid)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ctx.kernel_stats(reset=True)
+    sampler.start()
+    events = [step(i, True) for i in range(args.steps)]
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    if world > 1:
+        torch.distributed.barrier()
+    times = [(d, a.elapsed_time(b)) for d, a, b in events]
+    total_ms = sum(t for _, t in times)
+    kstats = ctx.kernel_stats(reset=True)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * n * args.steps / (total_ms * 1e-3) / 1e9
+    per_dist = {}
+    for d, t in times:
+        per_dist.setdefault(d, []).append(t)
+    per_dist = {d: round(n / (statistics.median(v) * 1e-3) / 1e9, 3) for d, v in per_dist.items()}
+
+    launches = sum(k["launches"] for k in kstats)
+    dom = max(kstats, key=lambda k: k["total_ms"])
+    peak, peak_kind = measured_peaks()
+    achieved = dom["bytes"] / (dom["total_ms"] * 1e-3) / 1e9 if dom["total_ms"] > 0 else 0.0
+    per_launch_bytes = dom["bytes"] / max(dom["launches"], 1)
+    traffic = ncu_traffic(dom["name"], per_launch_bytes / 8 / (2 if dom["name"] in (
+        "k_scatter", "k_resident") else 1))
+    kernels = {k["name"]: {"launches": k["launches"], "ms": round(k["total_ms"], 3),
+                           "GB/s": round(k["bytes"] / (k["total_ms"] * 1e-3) / 1e9, 1)
+                           if k["total_ms"] > 0 and k["bytes"] else None}
+               for k in kstats if k["launches"]}
+
+    # end to end through iplsSortHost with pinned host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        host = torch.empty(n * 8, dtype=torch.uint8, pin_memory=True)
+        hv = host.numpy()
+        e_ms = 0.0
+        for i in range(args.e2e_steps + 1):
+            hv[:] = inputs[DISTS[i % len(DISTS)]].view(np.uint8)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(stream)
+            ctx.sort_host_ptr(host.data_ptr(), n, ipls.F64)
+            b.record(stream)
+            torch.cuda.synchronize()
+            if i > 0:  # the first call allocates the staging buffer
+                e_ms += a.elapsed_time(b)
+        e2e = {"value": n * args.e2e_steps / (e_ms * 1e-3) / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8}
+        out = np.frombuffer(hv, dtype=np.float64)
+        assert (np.diff(out) >= 0).all(), "bench: e2e output not sorted"
+
+    torch_sort = None
+    if not args.no_torch_sort:
+        x = pristine["normal"].view(torch.float64)
+        torch.sort(x)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(3):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            torch.sort(x)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        torch_sort = round(n / (min(ts) * 1e-3) / 1e9, 3)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(inputs, args.cpu_sample_log2)
+
+    st = ctx.stats()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"IPLS sort of 2^{args.log2n} f64 keys, one step per array, "
+                                   "8 seeded distributions",
+                       "distributions": DISTS, "k": 256, "cutoff": args.cutoff,
+                       "sample": "alpha*k-1 keys, alpha = 0.2*floor(log2 n)",
+                       "l2": "flushed: a 2 GiB input-restore copy runs between timed steps",
+                       "parallelism": f"replicas x{world}"},
+            "per_dist_gkeys_s": per_dist,
+            "roofline": {"bound": "hbm", "kernel": dom["name"], "achieved": round(achieved, 1),
+                         "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                         "peak_source": peak_kind, "traffic": traffic,
+                         "bytes_per_launch": per_launch_bytes},
+            "kernels": kernels,
+            "gpu_launches": launches,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "torch_sort_gkeys_s": torch_sort,
+            "grid_levels_last": st.grid_levels,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gb300(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -13,8 +13,8 @@
  *     < -0 < +0 < ... < +inf < +NaN) and natural order for integers.  The
  *     sorted permutation is unique, so the output is bit-exact.
  *   - Sizes are counts of keys (int64).  n = 0 or 1 is a no-op returning
- *     IPLS_OK.  n < 0, n > 2^40, a NULL pointer, or an unknown dtype return
- *     IPLS_ERR_ARG without touching memory.
+ *     IPLS_OK.  n < 0, n > 2^32 - 1, a NULL pointer, or an unknown dtype
+ *     return IPLS_ERR_ARG without touching memory.
  *   - Device pointers must be valid for the GPU the context was created on
  *     and aligned to the key width.  The caller owns `keys`; the context
  *     owns all scratch memory (one ping-pong key buffer of n keys plus
@@ -66,8 +66,22 @@ typedef struct iplsConfig {
   int64_t spin_limit;     /* polls of a device-side wait before IPLS_ERR_TIMEOUT */
   int64_t trace_cap;      /* records kept by iplsGetTrace (0 = tracing off) */
   int64_t budget_bytes;   /* iplsSubmit admission budget (0 = unlimited) */
-  int32_t reserved[8];
+  int32_t profile;        /* 1: time every kernel launch with CUDA events
+                             (read with iplsGetKernelStats) */
+  int32_t reserved[7];
 } iplsConfig;
+
+/* Accumulated device time of one kernel of the library (profile = 1).
+ * bytes = algorithmic bytes: keys read + keys written by the launches, in
+ * bytes (the classify/histogram sweep reads every live key once, the scatter
+ * reads and writes every live key once, the block-resident kernel reads and
+ * writes each of its keys once). */
+typedef struct iplsKernelStat {
+  char name[24];
+  int64_t launches;
+  double total_ms;        /* sum of CUDA-event durations of the launches */
+  int64_t bytes;          /* algorithmic bytes moved by those launches */
+} iplsKernelStat;
 
 /* One partition pass as recorded by the trace (see iplsGetTrace). */
 typedef struct iplsTraceRec {
@@ -136,6 +150,12 @@ iplsStatus iplsSort(iplsCtx ctx, void* keys, int64_t n, iplsDtype dtype);
 iplsStatus iplsSortSegmented(iplsCtx ctx, void* keys, const int64_t* offsets,
                              int64_t nseg, iplsDtype dtype);
 
+/* Sorts keys[0..n) that live in HOST memory: copies them to a
+ * context-owned device buffer, sorts them there with iplsSort's kernels and
+ * copies the result back into the same host array.  Pinned (page-locked)
+ * host memory gives full copy bandwidth; pageable memory works too. */
+iplsStatus iplsSortHost(iplsCtx ctx, void* host_keys, int64_t n, iplsDtype dtype);
+
 /* Asynchronous sort request: enqueues iplsSort work for keys[0..n) and
  * returns a ticket.  Returns IPLS_ERR_BUDGET if 2*w*n exceeds the
  * configured budget.  The caller must keep `keys` alive until the request
@@ -151,6 +171,12 @@ iplsStatus iplsWait(iplsCtx ctx, uint64_t ticket, int64_t timeout_us);
 
 /* Statistics of the context (synchronises its stream). */
 iplsStatus iplsGetStats(iplsCtx ctx, iplsStats* stats);
+
+/* Per-kernel device time and algorithmic bytes accumulated while
+ * cfg.profile = 1 (synchronises the stream).  Writes up to cap entries and
+ * sets *count; reset = 1 clears the accumulators after reading. */
+iplsStatus iplsGetKernelStats(iplsCtx ctx, iplsKernelStat* out, int32_t cap, int32_t* count,
+                              int32_t reset);
 
 /* Copies up to cap trace records of the last sort to host memory `out`
  * (requires cfg.trace_cap > 0) and sets *count to the records kept. */

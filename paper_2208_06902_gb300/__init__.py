@@ -5,9 +5,10 @@ CUDA kernels behind a C ABI (include/ipls.h), with this thin binding.
 from . import build
 from .ipls import (F32, F64, U32, U64, Context, IPLSError, iplsCreate, iplsDefaultConfig,
                    iplsDestroy, iplsGetStats, iplsGetTrace, iplsLastError, iplsPoll,
-                   iplsScratchBytes, iplsSort, iplsSortSegmented, iplsSubmit, iplsWait, load)
+                   iplsScratchBytes, iplsSort, iplsSortHost, iplsSortSegmented, iplsSubmit, iplsWait,
+                   iplsGetKernelStats, load)
 
 __all__ = ["build", "load", "Context", "IPLSError", "F64", "F32", "U64", "U32",
            "iplsDefaultConfig", "iplsCreate", "iplsDestroy", "iplsScratchBytes", "iplsSort",
-           "iplsSortSegmented", "iplsSubmit", "iplsPoll", "iplsWait", "iplsGetStats",
-           "iplsGetTrace", "iplsLastError"]
+           "iplsSortSegmented", "iplsSortHost", "iplsSubmit", "iplsPoll", "iplsWait",
+           "iplsGetStats", "iplsGetKernelStats", "iplsGetTrace", "iplsLastError"]

@@ -8,6 +8,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "../../include/ipls.h"
 #include "ipls_device.cuh"
@@ -17,6 +18,9 @@ namespace {
 using namespace ipls;
 
 thread_local std::string g_last_error;
+
+// Offsets inside a bucket are kept in 32 bits per tile.
+constexpr int64_t kMaxKeys = (int64_t(1) << 32) - 1;
 
 iplsStatus fail(iplsStatus st, const std::string& msg) {
   g_last_error = msg;
@@ -42,10 +46,13 @@ iplsStatus cuda_fail(cudaError_t e, const char* where) {
 struct Slot {
   Sub* subs = nullptr;           int64_t sub_cap = 0;
   int32_t* tile2sub = nullptr;   int64_t tile_cap = 0;
+  int32_t* chunk2sub = nullptr;  int64_t chunk_cap = 0;
   Model* models = nullptr;       int64_t model_cap = 0;
   uint64_t* counts = nullptr;    int64_t count_cap = 0;
   int64_t* bases = nullptr;      int64_t base_cap = 0;
   Group* groups = nullptr;       int64_t group_cap = 0;
+  int32_t* fit_list = nullptr;   int64_t fit_cap = 0;
+  LinModel* tails = nullptr;     int64_t tail_cap = 0;
   Fill* fills = nullptr;         int64_t fill_cap = 0;
 };
 
@@ -61,6 +68,7 @@ struct iplsContext {
   int num_sms = 0;
   char* scratch = nullptr;            int64_t scratch_cap = 0;   // bytes
   unsigned long long* status = nullptr; int64_t status_cap = 0;  // words
+  uint32_t* tile_off = nullptr;       int64_t tile_off_cap = 0;  // words
   uint32_t epoch = 0;
   Slot slot[2];
   LevelCtl* ctl = nullptr;
@@ -78,6 +86,15 @@ struct iplsContext {
   int hist_grid[4] = {0, 0, 0, 0};
   int scatter_grid[4] = {0, 0, 0, 0};
   int64_t dev_bytes = 0;
+  // profiling (cfg.profile): event pairs per launch, resolved at sync points
+  struct Pending { int kind; cudaEvent_t a, b; };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> spare_events;
+  int64_t k_launches[16] = {};
+  double k_ms[16] = {};
+  int64_t k_bytes[16] = {};
+  // host-buffer sorting
+  char* host_stage = nullptr; int64_t host_stage_cap = 0;
 };
 
 namespace {
@@ -125,10 +142,77 @@ iplsStatus ensure(iplsCtx c, T*& p, int64_t& cap, int64_t need) {
 
 bool valid_dtype(int d) { return d >= 0 && d <= 3; }
 
-int occupancy_grid(iplsCtx c, int which, int dtype) {
-  int* cache = which == 0 ? c->hist_grid : c->scatter_grid;
-  if (!cache[dtype]) cache[dtype] = c->num_sms * 2;
-  return cache[dtype];
+enum KernelKind { kkFit, kkHist, kkCheck, kkRehist, kkScan, kkScatter, kkResident, kkFill,
+                  kkInitSeg, kkInitTiles, kkTailFit, kkTileScan, kkCount };
+const char* const kKernelNames[kkCount] = {"k_fit", "k_hist", "k_check", "k_hist_redo", "k_scan",
+                                           "k_scatter", "k_resident", "k_fill",
+                                           "k_init_segments", "k_init_tiles", "k_tail_fit",
+                                           "k_tilescan"};
+
+cudaEvent_t take_event(iplsCtx c) {
+  if (!c->spare_events.empty()) {
+    cudaEvent_t e = c->spare_events.back();
+    c->spare_events.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+  return e;
+}
+
+// Launches `fn` (which enqueues exactly one kernel) bracketed by CUDA events
+// when profiling; every launch is counted.
+template <class F>
+cudaError_t timed(iplsCtx c, int kind, F fn) {
+  if (!c->cfg.profile) {
+    cudaError_t e = fn();
+    return e;
+  }
+  cudaEvent_t a = take_event(c), b = take_event(c);
+  if (a) cudaEventRecord(a, c->stream);
+  cudaError_t e = fn();
+  if (b) cudaEventRecord(b, c->stream);
+  if (a && b) c->pending.push_back({kind, a, b});
+  return e;
+}
+
+// Folds finished event pairs into the per-kernel totals (after a sync).
+void resolve_events(iplsCtx c) {
+  for (auto& p : c->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      c->k_ms[p.kind] += ms;
+      c->k_launches[p.kind] += 1;
+    } else {
+      cudaGetLastError();
+    }
+    c->spare_events.push_back(p.a);
+    c->spare_events.push_back(p.b);
+  }
+  c->pending.clear();
+}
+
+// Grid kernels size their grids from the occupancy of the SMs they get.
+int occupancy_grid(iplsCtx c, int, int) { return c->num_sms; }
+
+// Group list of a slot with its fit list and fitted tail models.
+iplsStatus ensure_groups(iplsCtx c, Slot& s, int64_t need) {
+  IPLS_TRY(ensure(c, s.groups, s.group_cap, need));
+  IPLS_TRY(ensure(c, s.fit_list, s.fit_cap, s.group_cap));
+  IPLS_TRY(ensure(c, s.tails, s.tail_cap, s.group_cap));
+  return IPLS_OK;
+}
+
+// Fits and runs the block-resident tasks listed in slot s.
+iplsStatus launch_tail(iplsCtx c, ResidentArgs& ra, Slot& s, int32_t ngroups, int32_t nfit) {
+  ra.groups = s.groups;
+  ra.ngroups = ngroups;
+  ra.fit_list = s.fit_list;
+  ra.nfit = nfit;
+  ra.tail_models = s.tails;
+  if (nfit > 0) IPLS_CUDA(timed(c, kkTailFit, [&] { return launch_tail_fit(ra, c->stream); }));
+  if (ngroups > 0) IPLS_CUDA(timed(c, kkResident, [&] { return launch_resident(ra, c->stream); }));
+  return IPLS_OK;
 }
 
 iplsStatus check_run(iplsCtx c) {
@@ -185,51 +269,66 @@ iplsStatus sort_impl(iplsCtx c, void* keys, int64_t n, int dtype, const int64_t*
   ra.seed = cfg.seed; ra.exact_only = cfg.exact_only; ra.buf[0] = bufs[0]; ra.buf[1] = bufs[1];
   ra.run = c->run; ra.trace = cfg.trace_cap > 0 ? c->trace_res : nullptr; ra.trace_cap = cfg.trace_cap;
 
-  int64_t nsub = 0, ntiles = 0;
+  int64_t nsub = 0, ntiles = 0, nchunks = 0;
   const int64_t sub_bound = n / (rmax + 1) + 2;
   const int64_t tile_bound = n / tile + sub_bound + 2;
+  const int64_t chunk_bound = tile_bound / kChunkTiles + sub_bound + 2;
   if (offsets) {
     // segments: big ones become level-0 grid subproblems, the rest groups
     Slot& s0 = c->slot[0];
     Slot& s1 = c->slot[1];
     IPLS_TRY(ensure(c, s0.subs, s0.sub_cap, sub_bound));
     IPLS_TRY(ensure(c, s0.tile2sub, s0.tile_cap, tile_bound));
-    const int64_t gcap = 2 * n / rmax + nseg / 64 + 1024 + 2 * sub_bound;
-    IPLS_TRY(ensure(c, s1.groups, s1.group_cap, gcap));
+    IPLS_TRY(ensure(c, s0.chunk2sub, s0.chunk_cap, chunk_bound));
+    const int64_t gcap = 2 * n / (cfg.cutoff + 1) + 2 * (nseg / 64) + 1024 + 2 * sub_bound;
+    IPLS_TRY(ensure_groups(c, s1, std::min<int64_t>(gcap, nseg + 1024)));
     IPLS_CUDA(cudaMemsetAsync(c->ctl, 0, sizeof(LevelCtl), c->stream));
-    IPLS_CUDA(launch_init_segments(offsets, nseg, rmax, resident_root_ok, c->ctl, s0.subs,
-                                   (int32_t)std::min<int64_t>(s0.sub_cap, INT32_MAX), s0.tile2sub,
-                                   s0.tile_cap, s1.groups,
-                                   (int32_t)std::min<int64_t>(s1.group_cap, INT32_MAX), c->stream));
+    IPLS_CUDA(timed(c, kkInitSeg, [&] {
+      return launch_init_segments(offsets, nseg, rmax, cfg.cutoff, resident_root_ok, c->ctl,
+                                  s0.subs, (int32_t)std::min<int64_t>(s0.sub_cap, INT32_MAX),
+                                  s0.tile2sub, s0.tile_cap, s0.chunk2sub, s0.chunk_cap, s1.groups,
+                                  (int32_t)std::min<int64_t>(s1.group_cap, INT32_MAX),
+                                  s1.fit_list, c->stream);
+    }));
     IPLS_CUDA(cudaMemcpyAsync(c->h_ctl, c->ctl, sizeof(LevelCtl), cudaMemcpyDeviceToHost, c->stream));
     IPLS_CUDA(cudaStreamSynchronize(c->stream));
     if (c->h_ctl->overflow) return fail(IPLS_ERR_INTERNAL, "segment list capacity exceeded");
-    ra.groups = s1.groups;
-    ra.ngroups = c->h_ctl->ngroups;
-    IPLS_CUDA(launch_resident(ra, c->stream));
+    resolve_events(c);
+    IPLS_TRY(launch_tail(c, ra, s1, c->h_ctl->ngroups, c->h_ctl->nfit));
     nsub = c->h_ctl->nsub_next;
     ntiles = c->h_ctl->tiles_next;
+    nchunks = c->h_ctl->chunks_next;
   } else if (n <= rmax && resident_root_ok) {
+    // the whole array is one block-resident task (base case only when n is
+    // at most the cutoff, otherwise a fitted pass first)
     Slot& s1 = c->slot[1];
-    IPLS_TRY(ensure(c, s1.groups, s1.group_cap, 1));
+    IPLS_TRY(ensure_groups(c, s1, 1));
     const int64_t hb[2] = {0, n};
+    const int fitted = n > cfg.cutoff ? 1 : 0;
     IPLS_CUDA(cudaMemcpyAsync(c->root_bounds, hb, sizeof(hb), cudaMemcpyHostToDevice, c->stream));
-    const Group g{0, c->root_bounds, (int32_t)n, 0, 0, 1};
+    const Group g{0, c->root_bounds, (int32_t)n, 0, 0, 1, fitted ? 0 : -1, 0};
     IPLS_CUDA(cudaMemcpyAsync(s1.groups, &g, sizeof(g), cudaMemcpyHostToDevice, c->stream));
-    ra.groups = s1.groups;
-    ra.ngroups = 1;
-    IPLS_CUDA(launch_resident(ra, c->stream));
+    if (fitted) {
+      const int32_t zero = 0;
+      IPLS_CUDA(cudaMemcpyAsync(s1.fit_list, &zero, sizeof(zero), cudaMemcpyHostToDevice, c->stream));
+    }
+    IPLS_TRY(launch_tail(c, ra, s1, 1, fitted));
     IPLS_TRY(check_run(c));
+    resolve_events(c);
+    c->k_bytes[kkResident] += 2 * (int64_t)w * n;
     c->stats.algorithmic_bytes = 2 * (int64_t)w * n;
     return IPLS_OK;
   } else {
     Slot& s0 = c->slot[0];
     IPLS_TRY(ensure(c, s0.subs, s0.sub_cap, 1));
     ntiles = (n + tile - 1) / tile;
+    nchunks = (ntiles + kChunkTiles - 1) / kChunkTiles;
     IPLS_TRY(ensure(c, s0.tile2sub, s0.tile_cap, ntiles));
-    const Sub root{0, n, 0, 0, 0, (int32_t)ntiles, 0};
+    IPLS_TRY(ensure(c, s0.chunk2sub, s0.chunk_cap, nchunks));
+    const Sub root{0, n, 0, 0, 0, (int32_t)ntiles, 0, 0, (int32_t)nchunks};
     IPLS_CUDA(cudaMemcpyAsync(s0.subs, &root, sizeof(root), cudaMemcpyHostToDevice, c->stream));
-    IPLS_CUDA(launch_init_tiles(s0.tile2sub, ntiles, 0, c->stream));
+    IPLS_CUDA(timed(c, kkInitTiles, [&] { return launch_init_tiles(s0.tile2sub, ntiles, 0, c->stream); }));
+    IPLS_CUDA(timed(c, kkInitTiles, [&] { return launch_init_tiles(s0.chunk2sub, nchunks, 0, c->stream); }));
     nsub = 1;
   }
 
@@ -242,12 +341,14 @@ iplsStatus sort_impl(iplsCtx c, void* keys, int64_t n, int dtype, const int64_t*
     IPLS_TRY(ensure(c, X.models, X.model_cap, nsub));
     IPLS_TRY(ensure(c, X.counts, X.count_cap, nsub * kMaxK));
     IPLS_TRY(ensure(c, X.bases, X.base_cap, nsub * 257));
-    IPLS_TRY(ensure(c, X.groups, X.group_cap, 2 * n / rmax + 257 * nsub + 16));
+    IPLS_TRY(ensure_groups(c, X, 2 * n / (cfg.cutoff + 1) + 257 * nsub + 16));
     IPLS_TRY(ensure(c, X.fills, X.fill_cap, n / kFillChunk + 129 * nsub + 16));
     IPLS_TRY(ensure(c, Y.subs, Y.sub_cap, sub_bound));
     IPLS_TRY(ensure(c, Y.tile2sub, Y.tile_cap, tile_bound));
-    if (c->status_cap < ntiles * kMaxK) {
-      IPLS_TRY(ensure(c, c->status, c->status_cap, ntiles * kMaxK));
+    IPLS_TRY(ensure(c, Y.chunk2sub, Y.chunk_cap, chunk_bound));
+    IPLS_TRY(ensure(c, c->tile_off, c->tile_off_cap, ntiles * kMaxK));
+    if (c->status_cap < nchunks * kMaxK) {
+      IPLS_TRY(ensure(c, c->status, c->status_cap, nchunks * kMaxK));
       IPLS_CUDA(cudaMemsetAsync(c->status, 0, (size_t)c->status_cap * 8, c->stream));
       c->epoch = 0;
     }
@@ -263,41 +364,50 @@ iplsStatus sort_impl(iplsCtx c, void* keys, int64_t n, int dtype, const int64_t*
     a.buf[0] = bufs[0]; a.buf[1] = bufs[1];
     a.nsub = (int32_t)nsub; a.subs = X.subs; a.models = X.models; a.counts = X.counts;
     a.bases = X.bases; a.tile2sub = X.tile2sub; a.ntiles = ntiles; a.status = c->status;
+    a.chunk2sub = X.chunk2sub; a.nchunks = nchunks; a.tile_off = c->tile_off;
     a.ctl = c->ctl; a.run = c->run;
     a.next_subs = Y.subs; a.next_sub_cap = (int32_t)std::min<int64_t>(Y.sub_cap, INT32_MAX);
     a.next_tile2sub = Y.tile2sub; a.next_tile_cap = Y.tile_cap;
+    a.next_chunk2sub = Y.chunk2sub; a.next_chunk_cap = Y.chunk_cap;
     a.groups = X.groups; a.group_cap = (int32_t)std::min<int64_t>(X.group_cap, INT32_MAX);
+    a.fit_list = X.fit_list;
     a.fills = X.fills; a.fill_cap = (int32_t)std::min<int64_t>(X.fill_cap, INT32_MAX);
     a.trace = cfg.trace_cap > 0 ? c->trace_grid : nullptr;
     a.trace_cap = cfg.trace_cap;
     a.trace_base = c->trace_grid_count;
     int max_sample = sample_size_host(n, 1, cfg.k, 0);
     if (level == 0 && cfg.root_sample > max_sample) max_sample = (int)cfg.root_sample;
-    IPLS_CUDA(launch_fit(a, c->stream, max_sample));
-    IPLS_CUDA(launch_hist(a, c->stream, 0, occupancy_grid(c, 0, dtype)));
-    IPLS_CUDA(launch_check(a, c->stream, max_sample));
-    IPLS_CUDA(launch_hist(a, c->stream, 1, occupancy_grid(c, 0, dtype)));
-    IPLS_CUDA(launch_scan(a, c->stream));
-    IPLS_CUDA(launch_scatter(a, c->stream, occupancy_grid(c, 1, dtype)));
+    IPLS_CUDA(timed(c, kkFit, [&] { return launch_fit(a, c->stream, max_sample); }));
+    IPLS_CUDA(timed(c, kkHist, [&] { return launch_hist(a, c->stream, 0, occupancy_grid(c, 0, dtype)); }));
+    IPLS_CUDA(timed(c, kkCheck, [&] { return launch_check(a, c->stream, max_sample); }));
+    IPLS_CUDA(timed(c, kkRehist, [&] { return launch_hist(a, c->stream, 1, occupancy_grid(c, 0, dtype)); }));
+    IPLS_CUDA(timed(c, kkScan, [&] { return launch_scan(a, c->stream); }));
+    IPLS_CUDA(timed(c, kkTileScan, [&] { return launch_tilescan(a, c->stream, c->num_sms * 8); }));
+    IPLS_CUDA(timed(c, kkScatter, [&] { return launch_scatter(a, c->stream, occupancy_grid(c, 1, dtype)); }));
     IPLS_CUDA(cudaMemcpyAsync(c->h_ctl, c->ctl, sizeof(LevelCtl), cudaMemcpyDeviceToHost, c->stream));
     IPLS_CUDA(cudaStreamSynchronize(c->stream));
     const LevelCtl lc = *c->h_ctl;
     if (lc.overflow) return fail(IPLS_ERR_INTERNAL, "a level list capacity was exceeded");
+    resolve_events(c);
+    c->k_bytes[kkHist] += (int64_t)w * lc.keys_level;
+    c->k_bytes[kkScatter] += 2 * (int64_t)w * lc.keys_moved;
     c->stats.grid_levels += 1;
     c->stats.grid_passes += nsub;
     c->stats.fallback_passes += lc.fallback;
     moved += lc.keys_moved;
     c->stats.max_bucket_frac = std::max(c->stats.max_bucket_frac, (double)lc.max_bucket / 1048576.0);
     c->trace_grid_count += nsub;
-    ra.groups = X.groups;
-    ra.ngroups = lc.ngroups;
-    IPLS_CUDA(launch_resident(ra, c->stream));
-    IPLS_CUDA(launch_fill(X.fills, lc.nfill, dtype, keys, c->stream));
+    IPLS_TRY(launch_tail(c, ra, X, lc.ngroups, lc.nfit));
+    if (lc.nfill > 0)
+      IPLS_CUDA(timed(c, kkFill, [&] { return launch_fill(X.fills, lc.nfill, dtype, keys, c->stream); }));
     nsub = lc.nsub_next;
     ntiles = lc.tiles_next;
+    nchunks = lc.chunks_next;
     ++level;
   }
   IPLS_TRY(check_run(c));
+  resolve_events(c);
+  c->k_bytes[kkResident] += 2 * (int64_t)w * c->h_run->resident_keys;
   c->stats.keys_partitioned = moved;
   c->stats.algorithmic_bytes = 2 * (int64_t)w * (moved + c->h_run->resident_keys);
   return IPLS_OK;
@@ -305,7 +415,7 @@ iplsStatus sort_impl(iplsCtx c, void* keys, int64_t n, int dtype, const int64_t*
 
 iplsStatus check_common(int64_t n, int dtype) {
   if (!valid_dtype(dtype)) return fail(IPLS_ERR_ARG, "unknown dtype");
-  if (n < 0 || n > (int64_t(1) << 40)) return fail(IPLS_ERR_ARG, "n out of range [0, 2^40]");
+  if (n < 0 || n > kMaxKeys) return fail(IPLS_ERR_ARG, "n out of range [0, 2^32 - 1]");
   return IPLS_OK;
 }
 
@@ -330,37 +440,45 @@ namespace ipls {
 
 constexpr int kSegWindow = 64;
 
-__global__ void k_init_segments(const int64_t* off, int64_t nseg, int rmax, int resident_ok,
-                                LevelCtl* ctl, Sub* subs, int32_t sub_cap, int32_t* tile2sub,
-                                int64_t tile_cap, Group* groups, int32_t group_cap) {
+__global__ void k_init_segments(const int64_t* off, int64_t nseg, int rmax, int cutoff,
+                                int resident_ok, LevelCtl* ctl, Sub* subs, int32_t sub_cap,
+                                int32_t* tile2sub, int64_t tile_cap, int32_t* chunk2sub,
+                                int64_t chunk_cap, Group* groups, int32_t group_cap,
+                                int32_t* fit_list) {
   const int64_t wnd = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t q0 = wnd * kSegWindow;
   if (q0 >= nseg) return;
   const int64_t q1 = q0 + kSegWindow < nseg ? q0 + kSegWindow : nseg;
   int64_t g0 = -1, glast = -1, tot = 0;
-  const int tile = 8192;
   for (int64_t q = q0; q <= q1; ++q) {
     const int64_t cq = (q < q1) ? off[q + 1] - off[q] : 0;
-    const bool big = cq > 1 && (cq > rmax || !resident_ok);
-    const bool brk = (q == q1) || big;
+    const bool big = cq > cutoff && (cq > rmax || !resident_ok);
+    const bool mid = cq > cutoff && !big;
+    const bool brk = (q == q1) || big || mid;
     const bool fits = (cq > 0) && !brk;
     if (g0 >= 0 && (brk || (fits && tot + cq > rmax))) {
       const int g = atomicAdd(&ctl->ngroups, 1);
       if (g >= group_cap) ctl->overflow = 1;
-      else groups[g] = Group{off[g0], off + g0, (int32_t)tot, 0, 0, (int32_t)(glast - g0 + 1)};
+      else groups[g] = Group{off[g0], off + g0, (int32_t)tot, 0, 0, (int32_t)(glast - g0 + 1), -1, 0};
       g0 = -1;
       tot = 0;
     }
-    if (big) {
-      const int i = atomicAdd(&ctl->nsub_next, 1);
-      const int nt = (int)((cq + tile - 1) / tile);
-      const long long t0 = (long long)atomicAdd((unsigned long long*)&ctl->tiles_next,
-                                                (unsigned long long)nt);
-      if (i >= sub_cap || t0 + nt > tile_cap) {
+    if (mid) {
+      const int g = atomicAdd(&ctl->ngroups, 1);
+      if (g >= group_cap) {
         ctl->overflow = 1;
       } else {
-        subs[i] = Sub{off[q], cq, 0, 0, t0, nt, 0};
-        for (int z = 0; z < nt; ++z) tile2sub[t0 + z] = i;
+        groups[g] = Group{off[q], nullptr, (int32_t)cq, 0, 0, 1, g, 0};
+        fit_list[atomicAdd(&ctl->nfit, 1)] = g;
+      }
+    }
+    if (big) {
+      const int i = atomicAdd(&ctl->nsub_next, 1);
+      if (i >= sub_cap) {
+        ctl->overflow = 1;
+      } else {
+        Sub ns{off[q], cq, 0, 0, 0, 0, 0, 0, 0};
+        if (reserve_tiles(ctl, i, ns, tile2sub, tile_cap, chunk2sub, chunk_cap)) subs[i] = ns;
       }
     }
     if (fits) {
@@ -371,17 +489,19 @@ __global__ void k_init_segments(const int64_t* off, int64_t nseg, int rmax, int 
   }
 }
 
-cudaError_t launch_init_segments(const int64_t* offsets, int64_t nseg, int rmax, int resident_ok,
-                                 LevelCtl* ctl, Sub* subs, int32_t sub_cap, int32_t* tile2sub,
-                                 int64_t tile_cap, Group* groups, int32_t group_cap,
-                                 cudaStream_t s) {
+cudaError_t launch_init_segments(const int64_t* offsets, int64_t nseg, int rmax, int cutoff,
+                                 int resident_ok, LevelCtl* ctl, Sub* subs, int32_t sub_cap,
+                                 int32_t* tile2sub, int64_t tile_cap, int32_t* chunk2sub,
+                                 int64_t chunk_cap, Group* groups, int32_t group_cap,
+                                 int32_t* fit_list, cudaStream_t s) {
   const int64_t windows = (nseg + kSegWindow - 1) / kSegWindow;
   if (windows <= 0) return cudaSuccess;
   const int threads = 128;
   const int64_t blocks = (windows + threads - 1) / threads;
-  k_init_segments<<<(unsigned)blocks, threads, 0, s>>>(offsets, nseg, rmax, resident_ok, ctl, subs,
-                                                       sub_cap, tile2sub, tile_cap, groups,
-                                                       group_cap);
+  k_init_segments<<<(unsigned)blocks, threads, 0, s>>>(offsets, nseg, rmax, cutoff, resident_ok,
+                                                       ctl, subs, sub_cap, tile2sub, tile_cap,
+                                                       chunk2sub, chunk_cap, groups, group_cap,
+                                                       fit_list);
   return cudaGetLastError();
 }
 
@@ -448,13 +568,17 @@ iplsStatus iplsDestroy(iplsCtx c) {
   cudaStreamSynchronize(c->stream);
   dev_free(c, c->scratch, (size_t)c->scratch_cap);
   dev_free(c, c->status, (size_t)c->status_cap * 8);
+  dev_free(c, c->tile_off, (size_t)c->tile_off_cap * 4);
   for (Slot& s : c->slot) {
     dev_free(c, s.subs, s.sub_cap * sizeof(Sub));
     dev_free(c, s.tile2sub, s.tile_cap * sizeof(int32_t));
+    dev_free(c, s.chunk2sub, s.chunk_cap * sizeof(int32_t));
     dev_free(c, s.models, s.model_cap * sizeof(Model));
     dev_free(c, s.counts, s.count_cap * sizeof(uint64_t));
     dev_free(c, s.bases, s.base_cap * sizeof(int64_t));
     dev_free(c, s.groups, s.group_cap * sizeof(Group));
+    dev_free(c, s.fit_list, s.fit_cap * sizeof(int32_t));
+    dev_free(c, s.tails, s.tail_cap * sizeof(LinModel));
     dev_free(c, s.fills, s.fill_cap * sizeof(Fill));
   }
   dev_free(c, c->ctl, sizeof(LevelCtl));
@@ -464,6 +588,9 @@ iplsStatus iplsDestroy(iplsCtx c) {
   dev_free(c, c->trace_res, (size_t)c->trace_alloc * sizeof(iplsTraceRecDev));
   if (c->h_ctl) cudaFreeHost(c->h_ctl);
   if (c->h_run) cudaFreeHost(c->h_run);
+  for (auto& p : c->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+  for (cudaEvent_t e : c->spare_events) cudaEventDestroy(e);
+  dev_free(c, c->host_stage, (size_t)c->host_stage_cap);
   delete c;
   return IPLS_OK;
 }
@@ -526,11 +653,49 @@ iplsStatus iplsSortSegmented(iplsCtx c, void* keys, const int64_t* offsets, int6
   IPLS_CUDA(cudaMemcpyAsync(&first, offsets, 8, cudaMemcpyDeviceToHost, c->stream));
   IPLS_CUDA(cudaMemcpyAsync(&last, offsets + nseg, 8, cudaMemcpyDeviceToHost, c->stream));
   IPLS_CUDA(cudaStreamSynchronize(c->stream));
-  if (first < 0 || last < first || last > (int64_t(1) << 40))
+  if (first < 0 || last < first || last > kMaxKeys)
     return fail(IPLS_ERR_ARG, "offsets out of range");
   c->stats.calls += 1;
   g_last_error.clear();
   return sort_impl(c, keys, last, dtype, offsets, nseg);
+}
+
+iplsStatus iplsSortHost(iplsCtx c, void* host_keys, int64_t n, iplsDtype dtype) {
+  IPLS_TRY(check_common(n, dtype));
+  if (n > 1 && !host_keys) return fail(IPLS_ERR_ARG, "host_keys is NULL");
+  iplsStatus st = IPLS_OK;
+  if (!c) { c = default_ctx(&st); if (!c) return st; }
+  c->stats.calls += 1;
+  if (n <= 1) return IPLS_OK;
+  g_last_error.clear();
+  const size_t bytes = (size_t)n * key_bytes(dtype);
+  IPLS_TRY(ensure(c, c->host_stage, c->host_stage_cap, (int64_t)bytes));
+  IPLS_CUDA(cudaMemcpyAsync(c->host_stage, host_keys, bytes, cudaMemcpyHostToDevice, c->stream));
+  IPLS_TRY(sort_impl(c, c->host_stage, n, dtype, nullptr, 0));
+  IPLS_CUDA(cudaMemcpyAsync(host_keys, c->host_stage, bytes, cudaMemcpyDeviceToHost, c->stream));
+  IPLS_CUDA(cudaStreamSynchronize(c->stream));
+  return IPLS_OK;
+}
+
+iplsStatus iplsGetKernelStats(iplsCtx c, iplsKernelStat* out, int32_t cap, int32_t* count,
+                              int32_t reset) {
+  if (!c || !count || (cap > 0 && !out)) return fail(IPLS_ERR_ARG, "bad kernel-stats arguments");
+  IPLS_CUDA(cudaStreamSynchronize(c->stream));
+  resolve_events(c);
+  int m = 0;
+  for (int k = 0; k < kkCount && m < cap; ++k) {
+    std::memset(&out[m], 0, sizeof(out[m]));
+    std::strncpy(out[m].name, kKernelNames[k], sizeof(out[m].name) - 1);
+    out[m].launches = c->k_launches[k];
+    out[m].total_ms = c->k_ms[k];
+    out[m].bytes = c->k_bytes[k];
+    ++m;
+  }
+  *count = m;
+  if (reset) {
+    for (int k = 0; k < 16; ++k) { c->k_launches[k] = 0; c->k_ms[k] = 0.0; c->k_bytes[k] = 0; }
+  }
+  return IPLS_OK;
 }
 
 iplsStatus iplsSubmit(iplsCtx c, void* keys, int64_t n, iplsDtype dtype, uint64_t* ticket) {

@@ -161,21 +161,49 @@ __device__ __forceinline__ int64_t fixed_point(typename KT<K>::Bits b, int rho, 
   return neg ? -X : X;
 }
 
+// Smallest L with |x| < 2^L (kNoBits for x = 0): X(x) at rho = L - 61 stays
+// below 2^61.  Integer operations only.
+constexpr int kNoBits = -100000;
+template <class K>
+__device__ __forceinline__ int magnitude_bits(typename KT<K>::Bits b) {
+  uint64_t M;
+  int E;
+  bool neg;
+  KT<K>::mant_exp(b, M, E, neg);
+  return M ? E + (64 - __clzll((long long)M)) : kNoBits;
+}
+
 // ---------------------------------------------------------------------------
-// Block-wide sorting network on a shared-memory array a[0..n): a bitonic
-// sorter whose merges open with the mirrored comparator, so every comparator
-// puts the minimum at the lower index and positions >= n act as +infinity
-// without being stored.  All threads of the block must call it.
+// Cooperating groups: a whole block or a single warp.
 // ---------------------------------------------------------------------------
-template <class T>
-__device__ void block_sort(T* a, int n) {
+struct BlockG {
+  __device__ static __forceinline__ int tid() { return threadIdx.x; }
+  __device__ static __forceinline__ int size() { return blockDim.x; }
+  __device__ static __forceinline__ void sync() { __syncthreads(); }
+  __device__ static __forceinline__ bool any(bool p) { return __syncthreads_or(p) != 0; }
+};
+struct WarpG {
+  __device__ static __forceinline__ int tid() { return threadIdx.x & 31; }
+  __device__ static __forceinline__ int size() { return 32; }
+  __device__ static __forceinline__ void sync() { __syncwarp(); }
+  __device__ static __forceinline__ bool any(bool p) { return __any_sync(0xffffffffu, p) != 0; }
+};
+
+// ---------------------------------------------------------------------------
+// Sorting network on a shared-memory array a[0..n): a bitonic sorter whose
+// merges open with the mirrored comparator, so every comparator puts the
+// minimum at the lower index and positions >= n act as +infinity without
+// being stored.  Every member of the group must call it.
+// ---------------------------------------------------------------------------
+template <class G, class T>
+__device__ void group_sort(T* a, int n) {
   if (n <= 1) return;
   int P = 1, lp = 0;
   while (P < n) { P <<= 1; ++lp; }
   const int pairs = P >> 1;
   for (int ls = 1; ls <= lp; ++ls) {
     const int size = 1 << ls, lhalf = ls - 1, half = size >> 1;
-    for (int t = threadIdx.x; t < pairs; t += blockDim.x) {
+    for (int t = G::tid(); t < pairs; t += G::size()) {
       const int blk = t >> lhalf, j = t & (half - 1);
       const int lo = blk * size + j, hi = blk * size + size - 1 - j;
       if (hi < n) {
@@ -183,10 +211,10 @@ __device__ void block_sort(T* a, int n) {
         if (y < x) { a[lo] = y; a[hi] = x; }
       }
     }
-    __syncthreads();
+    G::sync();
     for (int lst = lhalf - 1; lst >= 0; --lst) {
       const int stride = 1 << lst;
-      for (int t = threadIdx.x; t < pairs; t += blockDim.x) {
+      for (int t = G::tid(); t < pairs; t += G::size()) {
         const int lo = ((t >> lst) << (lst + 1)) + (t & (stride - 1));
         const int hi = lo + stride;
         if (hi < n) {
@@ -194,10 +222,13 @@ __device__ void block_sort(T* a, int n) {
           if (y < x) { a[lo] = y; a[hi] = x; }
         }
       }
-      __syncthreads();
+      G::sync();
     }
   }
 }
+
+template <class T>
+__device__ __forceinline__ void block_sort(T* a, int n) { group_sort<BlockG, T>(a, n); }
 
 // Warp-wide bitonic sort of up to 32 values (one per lane; absent lanes hold
 // the maximum value).  Returns this lane's value of the sorted sequence.
@@ -227,7 +258,7 @@ __device__ __forceinline__ T warp_sort32(T v) {
 // property, the first D with 3D > N together with u_d of the D before it.
 // The property is monotone in D (the rounded gap grows with D, u_d shrinks),
 // which is why the listing never moves its window start back; here it is
-// found by binary search, one block reduction per probe.
+// found by binary search, one group reduction per probe.
 //
 // A probe first compares fixed-point images of the keys, which decide a
 // window with certainty unless its gap lies within a few units of u_d; only
@@ -235,110 +266,116 @@ __device__ __forceinline__ T warp_sort32(T v) {
 // ---------------------------------------------------------------------------
 struct FitShared {
   double ud;
-  long long t_lo, t_hi;
   int rho;
   int filter;
-  int result;
+  int linear;
   int pad;
 };
 
-template <class K>
+// One probe: does every window of D+1 consecutive sample points span at
+// least u_d(D)?  The thresholds of the fixed-point test come from the
+// fixed-point span q[N-1-D] - q[D]: with |q(x) - x/2^rho| < 1 and binary64
+// rounding errors of at most 2^-53 per operation, a window whose image gap
+// dq reaches t_hi certainly passes and one below t_lo certainly fails (the
+// margins cover both the truncations and the roundings).  Only windows in
+// between are decided with u_d and the gap computed in binary64.
+template <class G, class K>
 __device__ bool fmcd_probe(const typename KT<K>::Ord* so, int N, int D, int K_, FitShared& fs) {
   using T = KT<K>;
-  if (threadIdx.x == 0) {
-    const double ud = __ddiv_rn(T::diff(T::unord(so[N - 1 - D]), T::unord(so[D])), (double)(K_ - 2));
-    fs.ud = ud;
-    if (fs.filter) {
-      const double r = ldexp(ud, -fs.rho);
-      const double hi = ceil(r * (1.0 + 0x1.0p-50)) + 2.0;
-      const double lo = floor(r * (1.0 - 0x1.0p-50)) - 2.0;
-      const double cap = 0x1.0p62;
-      fs.t_hi = (long long)(hi > cap ? cap + 16.0 : hi);
-      fs.t_lo = (long long)(lo > cap ? cap + 8.0 : (lo < -cap ? -cap : lo));
-    }
-  }
-  __syncthreads();
-  const double ud = fs.ud;
   int fail = 0, amb = 0;
   const int W = N - D;  // windows i = 0 .. N-1-D
-  if (fs.filter) {
-    const long long tlo = fs.t_lo, thi = fs.t_hi;
-    const int rho = fs.rho;
-    for (int i = threadIdx.x; i < W; i += blockDim.x) {
-      bool s1, s2;
-      const long long q0 = fixed_point<K>(T::unord(so[i]), rho, s1);
-      const long long q1 = fixed_point<K>(T::unord(so[i + D]), rho, s2);
-      const long long dq = q1 - q0;
-      if (dq < tlo) fail = 1;
-      else if (dq < thi) amb = 1;
+  const int filter = fs.filter;
+  const int rho = fs.rho;
+  long long t_lo = -1, t_hi = 0;
+  if (filter) {
+    bool s1, s2;
+    const long long Sq = fixed_point<K>(T::unord(so[N - 1 - D]), rho, s1) -
+                         fixed_point<K>(T::unord(so[D]), rho, s2);
+    const long long km2 = K_ - 2;
+    const long long marg = (Sq >> 48) + 8;
+    t_hi = (Sq + 2 + marg) / km2 + 3;
+    const long long lo_num = Sq - 2 - marg;
+    t_lo = lo_num > 0 ? lo_num / km2 - 3 : -1;
+    for (int i = G::tid(); i < W; i += G::size()) {
+      const long long dq = fixed_point<K>(T::unord(so[i + D]), rho, s1) -
+                           fixed_point<K>(T::unord(so[i]), rho, s2);
+      if (dq < t_lo) fail = 1;
+      else if (dq < t_hi) amb = 1;
     }
   } else {
     amb = 1;
   }
-  if (__syncthreads_or(fail)) return false;
-  if (!__syncthreads_or(amb)) return true;
+  if (G::any(fail)) return false;
+  if (!G::any(amb)) return true;
+  if (G::tid() == 0)
+    fs.ud = __ddiv_rn(T::diff(T::unord(so[N - 1 - D]), T::unord(so[D])), (double)(K_ - 2));
+  G::sync();
+  const double ud = fs.ud;
   if (amb) {
-    const long long tlo = fs.t_lo, thi = fs.t_hi;
-    const int rho = fs.rho;
-    for (int i = threadIdx.x; i < W; i += blockDim.x) {
-      if (fs.filter) {
+    for (int i = G::tid(); i < W; i += G::size()) {
+      if (filter) {
         bool s1, s2;
         const long long dq = fixed_point<K>(T::unord(so[i + D]), rho, s2) -
                              fixed_point<K>(T::unord(so[i]), rho, s1);
-        if (dq < tlo || dq >= thi) continue;
+        if (dq < t_lo || dq >= t_hi) continue;
       }
       if (!(T::diff(T::unord(so[i + D]), T::unord(so[i])) >= ud)) { fail = 1; break; }
     }
   }
-  return !__syncthreads_or(fail);
+  return !G::any(fail);
 }
 
-// Fits the model of one subproblem from its sorted sample (all threads).
-// Sets m->kind to kLinear or kSplitter; fills the fast-path constants.
-template <class K>
-__device__ void fit_model(const typename KT<K>::Ord* so, int N, int K_, Model* m, FitShared& fs) {
+// Fits the linear model of one subproblem from its sorted sample (every
+// member of the group calls it).  m->kind = kLinear, or kSplitter when the
+// sample's extremes are equal or not finite or FMCD degenerates (u_d <= 0
+// or not finite, A or Bc not finite); the FMCD fields are kept either way.
+template <class G, class K>
+__device__ void fit_linear(const typename KT<K>::Ord* so, int N, int K_, LinModel* m, FitShared& fs) {
   using T = KT<K>;
   using Bits = typename T::Bits;
-  __shared__ int s_linear;
-  if (threadIdx.x == 0) {
+  if (G::tid() == 0) {
     const Bits first = T::unord(so[0]), last = T::unord(so[N - 1]);
     const bool lin = (so[0] != so[N - 1]) && !T::special(first) && !T::special(last);
-    s_linear = lin ? 1 : 0;
+    fs.linear = lin ? 1 : 0;
     m->kind = kSplitter;
     m->nb = K_;
-    m->nsplit = 0;
     m->capped = 0;
+    m->fast = 0;
     m->S = N;
     m->D = 0;
     m->A = 0.0;
     m->Bc = 0.0;
     m->ud = 0.0;
     m->xlo_bits = 0;
-    m->fast = 0;
+    m->rho = 0;
+    m->qlo = 0;
     if (lin) {
-      // certified filter: fixed point with rho = ilogb(R) - 60, R = max |x|
-      const double R = fmax(fabs(T::value(first)), fabs(T::value(last)));
-      fs.filter = (R > 0.0 && R < 0x1.0p1022) ? 1 : 0;
-      fs.rho = fs.filter ? (ilogb(R) - 60) : 0;
+      // certified filter: fixed point at rho = L - 61 with |x| < 2^L for every
+      // sample key; off when the keys are all zero or so large that a
+      // binary64 difference could overflow
+      const int L1 = magnitude_bits<K>(first), L2 = magnitude_bits<K>(last);
+      const int L = L1 > L2 ? L1 : L2;
+      fs.filter = (L != kNoBits && L <= 1022) ? 1 : 0;
+      fs.rho = fs.filter ? L - 61 : 0;
     }
   }
-  __syncthreads();
-  if (s_linear) {
+  G::sync();
+  if (fs.linear) {
     const int Dcap = N / 3 + 1;  // smallest D with 3D > N
     int D;
     int capped = 0;
-    if (!fmcd_probe<K>(so, N, Dcap - 1, K_, fs)) {
+    if (!fmcd_probe<G, K>(so, N, Dcap - 1, K_, fs)) {
       capped = 1;
       D = Dcap;
     } else {
       int lo = 1, hi = Dcap - 1;
       while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        if (fmcd_probe<K>(so, N, mid, K_, fs)) hi = mid; else lo = mid + 1;
+        if (fmcd_probe<G, K>(so, N, mid, K_, fs)) hi = mid; else lo = mid + 1;
       }
       D = lo;
     }
-    if (threadIdx.x == 0) {
+    if (G::tid() == 0) {
       // the slope comes from u_d at D (or at D-1 after the 3D > N break)
       const int Du = capped ? Dcap - 1 : D;
       const double ud = __ddiv_rn(T::diff(T::unord(so[N - 1 - Du]), T::unord(so[Du])), (double)(K_ - 2));
@@ -347,7 +384,6 @@ __device__ void fit_model(const typename KT<K>::Ord* so, int N, int K_, Model* m
       const double span = T::diff(xhi, xlo);
       const double prod = __dmul_rn(A, span);
       const double Bc = __dmul_rn(__dsub_rn((double)K_, prod), 0.5);
-      m->S = N;
       m->D = D;
       m->capped = capped;
       m->ud = ud;
@@ -357,10 +393,11 @@ __device__ void fit_model(const typename KT<K>::Ord* so, int N, int K_, Model* m
       const bool ok = isfinite(ud) && ud > 0.0 && isfinite(A) && isfinite(Bc);
       if (ok) {
         m->kind = kLinear;
-        // fast path: rho so that the in-range half-width (nb+|Bc|)/A < 2^(rho+29)
-        const double tmax = __ddiv_rn(__dadd_rn((double)K_, fabs(Bc)), A);
+        // fast path: rho so that the in-range half-width (nb+|Bc|)/A, bounded
+        // above by (nb+|Bc|)*u_d*(1+2^-50), stays below 2^(rho+29)
+        const double tmax = __dmul_rn(__dmul_rn(__dadd_rn((double)K_, fabs(Bc)), ud), 1.0 + 0x1.0p-50);
         int fast = isfinite(tmax) && tmax > 0.0;
-        int rho = fast ? ilogb(tmax) - 28 : 0;
+        const int rho = fast ? ilogb(tmax) - 28 : 0;
         bool sat = false;
         const long long qlo = fast ? fixed_point<K>(xlo, rho, sat) : 0;
         if (sat || qlo >= (1LL << 61) || qlo <= -(1LL << 61)) fast = 0;
@@ -379,21 +416,35 @@ __device__ void fit_model(const typename KT<K>::Ord* so, int N, int K_, Model* m
         m->cabs = cabs;
       }
     }
-    __syncthreads();
   }
-  if (threadIdx.x == 0 && m->kind == kSplitter) {
-    // k-1 equidistant sample keys would give 2(k-1)+1 buckets; take (k-1)/2
-    // so that the splitter tree with equality buckets has at most k buckets.
+  G::sync();
+}
+
+// Splitter tree with equality buckets from the sorted sample: the (k-1)/2
+// equidistant sample keys, deduplicated, so that the tree with equality
+// buckets has at most k buckets.
+template <class G, class K>
+__device__ void build_splitters(const typename KT<K>::Ord* so, int N, int K_, Model* m) {
+  if (G::tid() == 0) {
     const int want = (K_ - 1) / 2;
     int cnt = 0;
     for (int i = 0; i < want; ++i) {
       const uint64_t u = (uint64_t)so[(int64_t)(i + 1) * N / (want + 1)];
       if (cnt == 0 || m->split[cnt - 1] != u) m->split[cnt++] = u;
     }
+    m->l.kind = kSplitter;
+    m->l.fast = 0;
     m->nsplit = cnt;
-    m->nb = 2 * cnt + 1;
+    m->l.nb = 2 * cnt + 1;
   }
-  __syncthreads();
+  G::sync();
+}
+
+template <class G, class K>
+__device__ void fit_model(const typename KT<K>::Ord* so, int N, int K_, Model* m, FitShared& fs) {
+  if (G::tid() == 0) m->nsplit = 0;
+  fit_linear<G, K>(so, N, K_, &m->l, fs);
+  if (m->l.kind == kSplitter) build_splitters<G, K>(so, N, K_, m);
 }
 
 // Splitter tree with equality buckets: p = #{s_i <= u}; bucket 2p-1 if
@@ -432,7 +483,7 @@ struct Classifier {
   Bits xlo;
   const uint64_t* split;
 
-  __device__ __forceinline__ void load(const Model& m, int exact_only) {
+  __device__ __forceinline__ void load(const LinModel& m, int exact_only) {
     kind = m.kind;
     nb = m.nb;
     fast = m.fast && !exact_only;
@@ -445,6 +496,11 @@ struct Classifier {
     A = m.A;
     Bc = m.Bc;
     xlo = (Bits)m.xlo_bits;
+    nsplit = 0;
+    split = nullptr;
+  }
+  __device__ __forceinline__ void load(const Model& m, int exact_only) {
+    load(m.l, exact_only);
     nsplit = m.nsplit;
     split = m.split;
   }
@@ -480,6 +536,30 @@ struct Classifier {
     return classify_exact<K>(b, A, Bc, xlo, nb);
   }
 };
+
+// Reserves the tiles of a new grid subproblem of n keys, and the chunks of
+// kChunkTiles tiles the look-back scan walks, in the next level's tile and
+// chunk spaces; fills the Sub fields.  False (and ctl->overflow) when a
+// capacity is exceeded.
+__device__ __forceinline__ bool reserve_tiles(LevelCtl* ctl, int32_t idx, Sub& sub, int32_t* tile2sub,
+                                              int64_t tile_cap, int32_t* chunk2sub,
+                                              int64_t chunk_cap) {
+  const int nt = (int)((sub.n + kTileKeys - 1) / kTileKeys);
+  const int nc = (nt + kChunkTiles - 1) / kChunkTiles;
+  const long long t0 = (long long)atomicAdd((unsigned long long*)&ctl->tiles_next, (unsigned long long)nt);
+  const long long c0 = (long long)atomicAdd((unsigned long long*)&ctl->chunks_next, (unsigned long long)nc);
+  if (t0 + nt > tile_cap || c0 + nc > chunk_cap || c0 + nc > 0x7FFFFFFFLL) {
+    ctl->overflow = 1;
+    return false;
+  }
+  sub.tile0 = t0;
+  sub.ntiles = nt;
+  sub.chunk0 = (int32_t)c0;
+  sub.nchunks = nc;
+  for (int q = 0; q < nt; ++q) tile2sub[t0 + q] = idx;
+  for (int q = 0; q < nc; ++q) chunk2sub[c0 + q] = idx;
+  return true;
+}
 
 __device__ __forceinline__ unsigned lanemask_lt() {
   unsigned m;

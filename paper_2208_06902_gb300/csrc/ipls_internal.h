@@ -8,9 +8,8 @@ namespace ipls {
 
 constexpr int kMaxK = 256;        // buckets per pass (paper: 256)
 constexpr int kMaxSplit = 127;    // splitters: 2*127+1 = 255 buckets
-constexpr int kTileKeys8 = 8192;  // grid-pass tile, 8-byte keys
-constexpr int kTileKeys4 = 16384; // grid-pass tile, 4-byte keys
-constexpr int kPassThreads = 512; // threads of the grid-pass kernels
+constexpr int kTileKeys = 4096;   // keys per grid-pass tile
+constexpr int kPassThreads = 256; // threads of the grid-pass kernels
 constexpr int kResidentMax = 8192;      // keys of one block-resident group
 constexpr int kResidentThreads = 512;
 constexpr int kResidentSample = 1024;   // sample capacity inside a resident block
@@ -20,30 +19,36 @@ constexpr int kFillChunk = 65536;
 
 enum ModelKind : int32_t { kLinear = 0, kSplitter = 1 };
 
-// Partition model of one subproblem.  Linear: b(x) = clamp(floor(fma(A, x (-)
-// x_lo, Bc)), 0, nb-1) (Ch.3 model equation, centred).  Splitter: unique
-// splitters s_1 < ... < s_m as totalOrder keys, equality buckets at odd ids
-// (Ch.3 "Decision Trees").
-struct Model {
+// Linear partition model of one subproblem: b(x) = clamp(floor(fma(A,
+// x (-) x_lo, Bc)), 0, nb-1) (Ch.3 model equation, centred form).
+// kind == kSplitter means the sample does not support the linear model and
+// the splitter tree has to be built (Ch.3 "Decision Trees").
+struct LinModel {
   int32_t kind;
   int32_t nb;
-  int32_t nsplit;
   int32_t capped;
+  int32_t fast;   // the fixed-point / FP32 estimate applies (see Classifier)
   int64_t S;
   int64_t D;
   double A;
   double Bc;
   double ud;
   uint64_t xlo_bits;
-  // Fixed-point / FP32 evaluation with a certified error bound: keys whose
-  // bound straddles a bucket boundary fall back to the binary64 formula.
-  int32_t fast;
   int32_t rho;    // fixed-point scale: X(x) = trunc(x / 2^rho)
+  int32_t pad;
   int64_t qlo;    // X(x_lo)
   float af;       // RN32(A * 2^rho)
   float bcf;      // RN32(Bc)
-  float crel;     // bound = crel*|v| + cabs
+  float crel;     // certified bound = crel*|v| + cabs
   float cabs;
+};
+
+// Full model: the linear part, or unique splitters s_1 < ... < s_m as
+// totalOrder keys with equality buckets at odd ids.
+struct Model {
+  LinModel l;
+  int32_t nsplit;
+  int32_t pad;
   uint64_t split[128];
 };
 
@@ -56,12 +61,17 @@ struct Sub {
   int64_t tile0;   // first tile of this subproblem in the level's tile space
   int32_t ntiles;
   int32_t flags;
+  int32_t chunk0;  // first tile chunk (kChunkTiles tiles) of this subproblem
+  int32_t nchunks;
 };
+constexpr int kChunkTiles = 32;  // tiles per decoupled look-back chunk
 enum SubFlags : int32_t { kRehist = 1, kSkipScatter = 2 };
 
-// A block-resident group: consecutive children [off, off+n) of one parent
-// (or consecutive segments), each child an independent subproblem at `level`.
-// Child c spans [bounds[c]-bounds[0], bounds[c+1]-bounds[0]) inside the group.
+// A block-resident task.  fit < 0: consecutive children [off, off+n) of one
+// parent (or consecutive segments), each of at most `cutoff` keys, child c
+// spanning [bounds[c]-bounds[0], bounds[c+1]-bounds[0]); they only need the
+// base case.  fit >= 0: one subproblem [off, off+n) at `level` whose model
+// was fitted by k_tail_fit into tail_models[fit].
 struct Group {
   int64_t off;
   const int64_t* bounds;
@@ -69,6 +79,8 @@ struct Group {
   int32_t level;
   int32_t buf;
   int32_t nchild;
+  int32_t fit;
+  int32_t pad;
 };
 
 // Keys [off, off+n) of the user buffer all equal to `bits`.
@@ -84,13 +96,17 @@ struct LevelCtl {
   int32_t ngroups;
   int32_t nfill;
   int32_t nrehist;
+  int32_t nfit;          // tasks needing a tail fit
+  int32_t pad0;
   int64_t tiles_next;
+  int64_t chunks_next;
   uint32_t ticket;
   int32_t overflow;      // a list capacity was exceeded
   int64_t fallback;      // splitter passes
   int64_t max_bucket;    // max over passes of largest bucket / n, scaled by 2^20
   int64_t keys_moved;    // keys scattered by this level's grid passes
-  int64_t pad[3];
+  int64_t keys_level;    // keys in this level's grid subproblems
+  int64_t pad[2];
 };
 
 // Run-wide device status (persists across levels of one call).
@@ -125,7 +141,10 @@ struct LevelArgs {
   int64_t* bases;        // [nsub][257]
   int32_t* tile2sub;     // this level's tiles
   int64_t ntiles;
-  unsigned long long* status;  // look-back words [ntiles][256]
+  int32_t* chunk2sub;    // this level's tile chunks
+  int64_t nchunks;
+  uint32_t* tile_off;    // [ntiles][256]: tile histogram, then offsets in bucket
+  unsigned long long* status;  // look-back words [nchunks][256]
   LevelCtl* ctl;
   RunStatus* run;
   // outputs for the next level
@@ -133,8 +152,11 @@ struct LevelArgs {
   int32_t next_sub_cap;
   int32_t* next_tile2sub;
   int64_t next_tile_cap;
+  int32_t* next_chunk2sub;
+  int64_t next_chunk_cap;
   Group* groups;
   int32_t group_cap;
+  int32_t* fit_list;     // groups[fit_list[i]] need a tail fit
   Fill* fills;
   int32_t fill_cap;
   // trace: grid passes of this level take records trace_base + s
@@ -153,6 +175,9 @@ struct ResidentArgs {
   void* buf[2];
   const Group* groups;
   int32_t ngroups;
+  const int32_t* fit_list;
+  int32_t nfit;
+  LinModel* tail_models;           // indexed by Group::fit
   RunStatus* run;
   struct iplsTraceRecDev* trace;   // block-resident passes append here
   int64_t trace_cap;
@@ -171,17 +196,22 @@ struct iplsTraceRecDev {
 
 // Kernel launchers (defined in the .cu files).
 cudaError_t launch_fit(const LevelArgs& a, cudaStream_t s, int max_sample);
-cudaError_t launch_hist(const LevelArgs& a, cudaStream_t s, int rehist_only, int grid);
+cudaError_t launch_hist(const LevelArgs& a, cudaStream_t s, int rehist_only, int sms);
 cudaError_t launch_check(const LevelArgs& a, cudaStream_t s, int max_sample);
 cudaError_t launch_scan(const LevelArgs& a, cudaStream_t s);
-cudaError_t launch_scatter(const LevelArgs& a, cudaStream_t s, int grid);
+cudaError_t launch_tilescan(const LevelArgs& a, cudaStream_t s, int grid);
+cudaError_t launch_scatter(const LevelArgs& a, cudaStream_t s, int sms);
+cudaError_t launch_tail_fit(const ResidentArgs& a, cudaStream_t s);
 cudaError_t launch_resident(const ResidentArgs& a, cudaStream_t s);
-cudaError_t launch_init_segments(const int64_t* offsets, int64_t nseg, int rmax, int resident_ok,
-                                 LevelCtl* ctl, Sub* subs, int32_t sub_cap, int32_t* tile2sub,
-                                 int64_t tile_cap, Group* groups, int32_t group_cap, cudaStream_t s);
+cudaError_t launch_init_segments(const int64_t* offsets, int64_t nseg, int rmax, int cutoff,
+                                 int resident_ok, LevelCtl* ctl, Sub* subs, int32_t sub_cap,
+                                 int32_t* tile2sub, int64_t tile_cap, int32_t* chunk2sub,
+                                 int64_t chunk_cap, Group* groups, int32_t group_cap,
+                                 int32_t* fit_list, cudaStream_t s);
 int resident_rmax(int cutoff);
 cudaError_t launch_fill(const Fill* fills, int32_t nfill, int dtype, void* keys, cudaStream_t s);
 cudaError_t launch_init_tiles(int32_t* tile2sub, int64_t ntiles, int32_t value, cudaStream_t s);
+
 int tile_keys(int dtype);
 int key_bytes(int dtype);
 int sample_size_host(int64_t n, int level, int k, int64_t root_sample);

@@ -3,26 +3,30 @@
 //   k_fit      one block per subproblem: sample alpha*k-1 keys, sort them,
 //              fit FMCD (Ch.3 listing) or the splitter tree, zero counts.
 //   k_hist     every tile of every subproblem: classify each key with the
-//              model (Ch.3 model equation), per-warp shared histograms,
-//              one global atomic per bucket per block and subproblem.
+//              model (Ch.3 model equation), per-warp shared histograms; the
+//              tile's histogram goes to memory, the subproblem's totals are
+//              accumulated with one atomic per bucket per block.
 //   k_check    no-progress rule: a linear pass that puts every key into one
 //              bucket is redone with the splitter tree from the same sample.
 //   k_scan     exclusive scan of the bucket counts -> bucket bases; children
 //              become next-level subproblems, block-resident groups, or
 //              (equality buckets) fills; records the trace.
-//   k_scatter  tiles in ticket order: classify again, rank each key stably
-//              inside the tile (warp match + per-warp counters), obtain the
-//              tile's offset inside every bucket by decoupled look-back,
-//              stage the tile in bucket order in shared memory and write the
-//              bucket runs out with coalesced stores (Ch.2 IPS4o: move every
-//              key into the region of its bucket).
+//   k_tilescan exclusive scan of the tile histograms of every subproblem,
+//              per bucket, over its tiles: chunks of kChunkTiles tiles in
+//              ticket order, each chunk's prefix found by decoupled look-back
+//              over the chunks before it.
+//   k_scatter  every tile: classify again, rank each key stably inside the
+//              tile (warp match + per-warp counters), stage the tile in
+//              bucket order in shared memory and write the bucket runs out
+//              with coalesced stores at bucket base + tile offset (Ch.2
+//              IPS4o: move every key into the region of its bucket).
 #include <cuda/atomic>
 
 #include "ipls_device.cuh"
 
 namespace ipls {
 
-constexpr int kTile = 8192;
+constexpr int kTile = kTileKeys;
 constexpr int kWarps = kPassThreads / 32;
 constexpr int kKPT = kTile / kPassThreads;   // keys per thread
 constexpr int kKPW = kTile / kWarps;         // keys per warp
@@ -60,23 +64,6 @@ __device__ int gather_sorted_sample(const LevelArgs& a, const Sub& sub,
   return S;
 }
 
-template <class K>
-__device__ void build_splitters(const typename KT<K>::Ord* so, int N, int K_, Model* m) {
-  if (threadIdx.x == 0) {
-    const int want = (K_ - 1) / 2;
-    int cnt = 0;
-    for (int i = 0; i < want; ++i) {
-      const uint64_t u = (uint64_t)so[(int64_t)(i + 1) * N / (want + 1)];
-      if (cnt == 0 || m->split[cnt - 1] != u) m->split[cnt++] = u;
-    }
-    m->kind = kSplitter;
-    m->nsplit = cnt;
-    m->nb = 2 * cnt + 1;
-    m->fast = 0;
-  }
-  __syncthreads();
-}
-
 // ---------------------------------------------------------------------------
 template <class K>
 __global__ void __launch_bounds__(kFitThreads) k_fit(LevelArgs a) {
@@ -88,22 +75,27 @@ __global__ void __launch_bounds__(kFitThreads) k_fit(LevelArgs a) {
   const int s = blockIdx.x;
   const Sub sub = a.subs[s];
   const int S = gather_sorted_sample<K>(a, sub, so);
-  fit_model<K>(so, S, a.k, &sm, fs);
+  fit_model<BlockG, K>(so, S, a.k, &sm, fs);
   copy_model(&a.models[s], &sm);
   for (int b = threadIdx.x; b < kMaxK; b += blockDim.x) a.counts[(size_t)s * kMaxK + b] = 0;
-  if (threadIdx.x == 0) a.subs[s].flags = 0;
+  if (threadIdx.x == 0) {
+    a.subs[s].flags = 0;
+    atomicAdd((unsigned long long*)&a.ctl->keys_level, (unsigned long long)sub.n);
+  }
 }
 
 // ---------------------------------------------------------------------------
 template <class K>
-__global__ void __launch_bounds__(kPassThreads) k_hist(LevelArgs a, int rehist_only) {
+__global__ void __launch_bounds__(kPassThreads, 4) k_hist(LevelArgs a, int rehist_only) {
   using T = KT<K>;
   using Bits = typename T::Bits;
+  constexpr int kChunk = 8;  // keys per thread in flight
   __shared__ Model sm;
   __shared__ unsigned int hist[kWarps][kMaxK];
-  __shared__ int s_cur;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __shared__ unsigned int acc[kMaxK];
+  const int warp = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < kWarps * kMaxK; i += blockDim.x) (&hist[0][0])[i] = 0;
+  for (int i = threadIdx.x; i < kMaxK; i += blockDim.x) acc[i] = 0;
   const int64_t nt = a.ntiles;
   const int64_t t0 = nt * blockIdx.x / gridDim.x, t1 = nt * (blockIdx.x + 1) / gridDim.x;
   int cur = -1;
@@ -113,11 +105,9 @@ __global__ void __launch_bounds__(kPassThreads) k_hist(LevelArgs a, int rehist_o
     if (s != cur) {
       __syncthreads();
       if (cur >= 0) {
-        const int nb = sm.nb;
-        for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-          unsigned int tot = 0;
-          for (int w = 0; w < kWarps; ++w) { tot += hist[w][b]; hist[w][b] = 0; }
-          if (tot) atomicAdd((unsigned long long*)&a.counts[(size_t)cur * kMaxK + b], (unsigned long long)tot);
+        for (int b = threadIdx.x; b < kMaxK; b += blockDim.x) {
+          if (acc[b]) atomicAdd((unsigned long long*)&a.counts[(size_t)cur * kMaxK + b], (unsigned long long)acc[b]);
+          acc[b] = 0;
         }
       }
       __syncthreads();
@@ -133,26 +123,33 @@ __global__ void __launch_bounds__(kPassThreads) k_hist(LevelArgs a, int rehist_o
     const int64_t rem = sub.n - ti * kTile;
     const int tn = rem < kTile ? (int)rem : kTile;
     const Bits* src = buf_ptr<K>(a, sub.buf) + base;
-    Bits v[kKPT];
+    for (int c0 = 0; c0 < kTile; c0 += kChunk * kPassThreads) {
+      Bits v[kChunk];
 #pragma unroll
-    for (int j = 0; j < kKPT; ++j) {
-      const int i = warp * kKPW + j * 32 + lane;
-      v[j] = (i < tn) ? src[i] : Bits(0);
+      for (int j = 0; j < kChunk; ++j) {
+        const int i = c0 + j * kPassThreads + threadIdx.x;
+        v[j] = (i < tn) ? src[i] : Bits(0);
+      }
+#pragma unroll
+      for (int j = 0; j < kChunk; ++j) {
+        const int i = c0 + j * kPassThreads + threadIdx.x;
+        if (i < tn) atomicAdd(&hist[warp][cls.bucket(v[j])], 1u);
+      }
     }
-#pragma unroll
-    for (int j = 0; j < kKPT; ++j) {
-      const int i = warp * kKPW + j * 32 + lane;
-      if (i < tn) atomicAdd(&hist[warp][cls.bucket(v[j])], 1u);
+    __syncthreads();
+    // the tile's histogram (all 256 bins) to memory; subproblem totals in acc
+    uint32_t* th = a.tile_off + (size_t)t * kMaxK;
+    for (int b = threadIdx.x; b < kMaxK; b += blockDim.x) {
+      unsigned int tot = 0;
+      for (int w = 0; w < kWarps; ++w) { tot += hist[w][b]; hist[w][b] = 0; }
+      th[b] = tot;
+      acc[b] += tot;
     }
   }
   __syncthreads();
   if (cur >= 0) {
-    const int nb = sm.nb;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-      unsigned int tot = 0;
-      for (int w = 0; w < kWarps; ++w) tot += hist[w][b];
-      if (tot) atomicAdd((unsigned long long*)&a.counts[(size_t)cur * kMaxK + b], (unsigned long long)tot);
-    }
+    for (int b = threadIdx.x; b < kMaxK; b += blockDim.x)
+      if (acc[b]) atomicAdd((unsigned long long*)&a.counts[(size_t)cur * kMaxK + b], (unsigned long long)acc[b]);
   }
 }
 
@@ -169,8 +166,8 @@ __global__ void __launch_bounds__(kFitThreads) k_check(LevelArgs a) {
   if (threadIdx.x == 0) s_redo = 0;
   __syncthreads();
   const Model& gm = a.models[s];
-  if (gm.kind == kLinear) {
-    for (int b = threadIdx.x; b < gm.nb; b += blockDim.x)
+  if (gm.l.kind == kLinear) {
+    for (int b = threadIdx.x; b < gm.l.nb; b += blockDim.x)
       if ((int64_t)a.counts[(size_t)s * kMaxK + b] == sub.n) s_redo = 1;
   }
   __syncthreads();
@@ -178,7 +175,7 @@ __global__ void __launch_bounds__(kFitThreads) k_check(LevelArgs a) {
   copy_model(&sm, &gm);
   __syncthreads();
   const int S = gather_sorted_sample<K>(a, sub, so);
-  build_splitters<K>(so, S, a.k, &sm);
+  build_splitters<BlockG, K>(so, S, a.k, &sm);
   copy_model(&a.models[s], &sm);
   for (int b = threadIdx.x; b < kMaxK; b += blockDim.x) a.counts[(size_t)s * kMaxK + b] = 0;
   if (threadIdx.x == 0) {
@@ -223,7 +220,8 @@ __global__ void __launch_bounds__(256) k_scan(LevelArgs a) {
   const int s = blockIdx.x, b = threadIdx.x;
   const Sub sub = a.subs[s];
   const Model& m = a.models[s];
-  const int nb = m.nb;
+  const int nb = m.l.nb;
+  const bool splitter = m.l.kind == kSplitter;
   const int dst_buf = 1 - sub.buf;
   const int64_t c = (b < nb) ? (int64_t)a.counts[(size_t)s * kMaxK + b] : 0;
   cnt[b] = c;
@@ -235,15 +233,15 @@ __global__ void __launch_bounds__(256) k_scan(LevelArgs a) {
   int64_t* gb = a.bases + (size_t)s * 257;
   gb[b] = bas[b];
   if (b == 0) gb[256] = bas[256];
-  const bool eq = (m.kind == kSplitter) && (b & 1) && b < nb;
+  const bool eq = splitter && (b & 1) && b < nb;
   if (eq && c == sub.n) s_skip = 1;
   // trace: this level's grid passes own records trace_base + s
   if (a.trace_cap > 0 && a.trace_base + s < a.trace_cap) {
     iplsTraceRecDev& r = a.trace[a.trace_base + s];
     if (b == 0) {
-      r.off = sub.off; r.n = sub.n; r.level = sub.level; r.kind = m.kind;
-      r.capped = m.capped; r.nbuckets = nb; r.S = m.S; r.D = m.D; r.A = m.A;
-      r.Bc = m.Bc; r.ud = m.ud; r.xlo_bits = m.xlo_bits; r.nsplit = m.nsplit; r.where = 0;
+      r.off = sub.off; r.n = sub.n; r.level = sub.level; r.kind = m.l.kind;
+      r.capped = m.l.capped; r.nbuckets = nb; r.S = m.l.S; r.D = m.l.D; r.A = m.l.A;
+      r.Bc = m.l.Bc; r.ud = m.l.ud; r.xlo_bits = m.l.xlo_bits; r.nsplit = m.nsplit; r.where = 0;
     }
     r.counts[b] = c;
   }
@@ -253,7 +251,7 @@ __global__ void __launch_bounds__(256) k_scan(LevelArgs a) {
     if (b == 0) {
       a.subs[s].flags |= kSkipScatter;
       if (sub.buf != 0) {
-        int j = 0;
+        int j = 1;
         for (int q = 1; q < nb; q += 2) if (cnt[q] == sub.n) j = q;
         append_fill<K>(a, sub.off, sub.n, (uint64_t)T::unord((typename T::Ord)m.split[(j - 1) / 2]));
       }
@@ -264,31 +262,40 @@ __global__ void __launch_bounds__(256) k_scan(LevelArgs a) {
         append_fill<K>(a, sub.off + bas[b], c, (uint64_t)T::unord((typename T::Ord)m.split[(b - 1) / 2]));
     } else if (c > a.rmax) {
       const int i = atomicAdd(&a.ctl->nsub_next, 1);
-      const int nt = (int)((c + kTile - 1) / kTile);
-      const long long t0 = (long long)atomicAdd((unsigned long long*)&a.ctl->tiles_next,
-                                                (unsigned long long)nt);
-      if (i >= a.next_sub_cap || t0 + nt > a.next_tile_cap) {
+      if (i >= a.next_sub_cap) {
         a.ctl->overflow = 1;
       } else {
-        a.next_subs[i] = Sub{sub.off + bas[b], c, sub.level + 1, dst_buf, t0, nt, 0};
-        for (int q = 0; q < nt; ++q) a.next_tile2sub[t0 + q] = i;
+        Sub ns{sub.off + bas[b], c, sub.level + 1, dst_buf, 0, 0, 0, 0, 0};
+        if (reserve_tiles(a.ctl, i, ns, a.next_tile2sub, a.next_tile_cap, a.next_chunk2sub,
+                          a.next_chunk_cap))
+          a.next_subs[i] = ns;
+      }
+    } else if (c > a.cutoff) {
+      // a block-resident subproblem whose model k_tail_fit fits
+      const int g = atomicAdd(&a.ctl->ngroups, 1);
+      if (g >= a.group_cap) {
+        a.ctl->overflow = 1;
+      } else {
+        a.groups[g] = Group{sub.off + bas[b], nullptr, (int32_t)c, sub.level + 1, dst_buf, 1, g, 0};
+        const int f = atomicAdd(&a.ctl->nfit, 1);
+        a.fit_list[f] = g;
       }
     }
   }
   if (!s_skip && b == 0) {
-    // pack consecutive resident-size buckets into groups of <= rmax keys
+    // pack consecutive base-case buckets into groups of <= rmax keys
     int b0 = -1, blast = -1;
     int64_t tot = 0;
     for (int q = 0; q <= nb; ++q) {
       const int64_t cq = (q < nb) ? cnt[q] : 0;
-      const bool eqq = (q < nb) && (m.kind == kSplitter) && (q & 1);
-      const bool brk = (q == nb) || (cq > 0 && (eqq || cq > a.rmax));
+      const bool eqq = (q < nb) && splitter && (q & 1);
+      const bool brk = (q == nb) || (cq > 0 && (eqq || cq > a.cutoff));
       const bool fits = (cq > 0) && !brk;
       if (b0 >= 0 && (brk || (fits && tot + cq > a.rmax))) {
         const int g = atomicAdd(&a.ctl->ngroups, 1);
         if (g >= a.group_cap) a.ctl->overflow = 1;
         else a.groups[g] = Group{sub.off + bas[b0], gb + b0, (int32_t)tot, sub.level + 1,
-                                 dst_buf, blast - b0 + 1};
+                                 dst_buf, blast - b0 + 1, -1, 0};
         b0 = -1;
         tot = 0;
       }
@@ -298,7 +305,7 @@ __global__ void __launch_bounds__(256) k_scan(LevelArgs a) {
         blast = q;
       }
     }
-    if (m.kind == kSplitter) atomicAdd((unsigned long long*)&a.ctl->fallback, 1ULL);
+    if (splitter) atomicAdd((unsigned long long*)&a.ctl->fallback, 1ULL);
     atomicAdd((unsigned long long*)&a.ctl->keys_moved, (unsigned long long)sub.n);
     int64_t mx = 0;
     for (int q = 0; q < nb; ++q) mx = cnt[q] > mx ? cnt[q] : mx;
@@ -323,6 +330,67 @@ __device__ __forceinline__ unsigned long long ld_acquire(unsigned long long* p) 
   return r.load(cuda::memory_order_acquire);
 }
 
+// One block of 256 threads per chunk (thread b = bucket b), chunks in ticket
+// order so that a chunk only waits for chunks already being processed.
+__global__ void __launch_bounds__(256) k_tilescan(LevelArgs a) {
+  __shared__ int s_c;
+  const int b = threadIdx.x;
+  const unsigned long long ep = (unsigned long long)(a.epoch & 0xFFFF) << 48;
+  for (;;) {
+    __syncthreads();
+    if (b == 0) s_c = (int)atomicAdd(&a.ctl->ticket, 1u);
+    __syncthreads();
+    const int c = s_c;
+    if (c >= a.nchunks) break;
+    const Sub sub = a.subs[a.chunk2sub[c]];
+    if (sub.flags & kSkipScatter) continue;
+    const int ci = c - sub.chunk0;
+    const int64_t tb = sub.tile0 + (int64_t)ci * kChunkTiles;
+    const int64_t te0 = tb + kChunkTiles, tend = sub.tile0 + sub.ntiles;
+    const int cnt = (int)((te0 < tend ? te0 : tend) - tb);
+    uint32_t h[kChunkTiles];
+    unsigned long long agg = 0;
+#pragma unroll
+    for (int q = 0; q < kChunkTiles; ++q) {
+      h[q] = (q < cnt) ? a.tile_off[(size_t)(tb + q) * kMaxK + b] : 0u;
+      agg += h[q];
+    }
+    unsigned long long* st = a.status + (size_t)c * kMaxK;
+    unsigned long long excl = 0;
+    if (ci == 0) {
+      st_release(&st[b], ep | kFlagPre | agg);
+    } else {
+      st_release(&st[b], ep | kFlagAgg | agg);
+      int64_t j = c - 1;
+      long long spins = 0;
+      for (;;) {
+        const unsigned long long w = ld_acquire(&a.status[(size_t)j * kMaxK + b]);
+        if ((w & ~((1ULL << 48) - 1)) == ep && (w & (3ULL << 46))) {
+          excl += w & kValMask;
+          if (w & kFlagPre) break;
+          --j;
+          continue;
+        }
+        if (++spins > a.spin_limit) {
+          atomicExch(&a.run->error, -4);
+          atomicExch(&a.run->where, 1);
+          break;
+        }
+        __nanosleep(64);
+      }
+      st_release(&st[b], ep | kFlagPre | (excl + agg));
+    }
+    unsigned long long run = excl;
+#pragma unroll
+    for (int q = 0; q < kChunkTiles; ++q) {
+      if (q < cnt) {
+        a.tile_off[(size_t)(tb + q) * kMaxK + b] = (uint32_t)run;
+        run += h[q];
+      }
+    }
+  }
+}
+
 template <class K>
 struct ScatterSmem {
   typename KT<K>::Bits stage[kTile];
@@ -331,38 +399,30 @@ struct ScatterSmem {
   int tile_start[kMaxK];
   int tile_tot[kMaxK];
   long long gbase[kMaxK];
-  long long tmp[kMaxK];
   Model model;
-  int cur, t, abort_tile;
 };
 
 template <class K>
-__global__ void __launch_bounds__(kPassThreads, 2) k_scatter(LevelArgs a) {
+__global__ void __launch_bounds__(kPassThreads, 3) k_scatter(LevelArgs a) {
   using T = KT<K>;
   using Bits = typename T::Bits;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ScatterSmem<K>& sh = *reinterpret_cast<ScatterSmem<K>*>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const unsigned long long ep = (unsigned long long)(a.epoch & 0xFFFF) << 48;
-  if (threadIdx.x == 0) sh.cur = -1;
   Classifier<K> cls;
   Bits* dst_base[2] = {reinterpret_cast<Bits*>(a.buf[0]), reinterpret_cast<Bits*>(a.buf[1])};
-  for (;;) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      sh.t = (int)atomicAdd(&a.ctl->ticket, 1u);
-      sh.abort_tile = 0;
-    }
-    __syncthreads();
-    const int64_t t = sh.t;
-    if (t >= a.ntiles) break;
+  const int64_t nt = a.ntiles;
+  const int64_t t0 = nt * blockIdx.x / gridDim.x, t1 = nt * (blockIdx.x + 1) / gridDim.x;
+  int cur = -1;
+  for (int64_t t = t0; t < t1; ++t) {
     const int s = a.tile2sub[t];
     const Sub sub = a.subs[s];
     if (sub.flags & kSkipScatter) continue;
-    if (s != sh.cur) {
+    __syncthreads();
+    if (s != cur) {
       copy_model(&sh.model, &a.models[s]);
+      cur = s;
       __syncthreads();
-      if (threadIdx.x == 0) sh.cur = s;
     }
     cls.load(sh.model, a.exact_only);
     for (int i = threadIdx.x; i < kWarps * kMaxK; i += blockDim.x) (&sh.wcnt[0][0])[i] = 0;
@@ -393,57 +453,40 @@ __global__ void __launch_bounds__(kPassThreads, 2) k_scatter(LevelArgs a) {
       __syncwarp();
     }
     __syncthreads();
-    unsigned long long* st = a.status + (size_t)t * kMaxK;
-    if (threadIdx.x < kMaxK) {
-      const int b = threadIdx.x;
+    {
+      const int b = threadIdx.x;  // 256 threads = 256 buckets
       int run = 0;
+#pragma unroll
       for (int w = 0; w < kWarps; ++w) {
         const int x = sh.wcnt[w][b];
         sh.wcnt[w][b] = (unsigned short)run;
         run += x;
       }
       sh.tile_tot[b] = run;
-      st_release(&st[b], ep | (ti == 0 ? kFlagPre : kFlagAgg) | (unsigned long long)run);
     }
-    // tile-local bucket starts (exclusive scan over buckets)
-    if (threadIdx.x < kMaxK) sh.tmp[threadIdx.x] = sh.tile_tot[threadIdx.x];
     __syncthreads();
-    for (int off = 1; off < kMaxK; off <<= 1) {
-      long long x = 0;
-      if (threadIdx.x < kMaxK && threadIdx.x >= off) x = sh.tmp[threadIdx.x - off];
-      __syncthreads();
-      if (threadIdx.x < kMaxK) sh.tmp[threadIdx.x] += x;
-      __syncthreads();
-    }
-    if (threadIdx.x < kMaxK) {
-      const int b = threadIdx.x;
-      const int tot = sh.tile_tot[b];
-      sh.tile_start[b] = (int)(sh.tmp[b] - tot);
-      long long excl = 0;
-      if (ti > 0) {
-        int64_t j = t - 1;
-        long long spins = 0;
-        for (;;) {
-          const unsigned long long w = ld_acquire(&a.status[(size_t)j * kMaxK + b]);
-          if ((w & ~((1ULL << 48) - 1)) == ep && (w & (3ULL << 46))) {
-            excl += (long long)(w & kValMask);
-            if (w & kFlagPre) break;
-            --j;
-            continue;
-          }
-          if (++spins > a.spin_limit) {
-            atomicExch(&a.run->error, -4);
-            atomicExch(&a.run->where, 1);
-            sh.abort_tile = 1;
-            break;
-          }
-          __nanosleep(64);
-        }
-        st_release(&st[b], ep | kFlagPre | (unsigned long long)(excl + tot));
+    if (warp == 0) {
+      // exclusive scan of the tile's bucket totals: 8 buckets per lane
+      int loc[8];
+      int sum = 0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) { loc[q] = sh.tile_tot[lane * 8 + q]; sum += loc[q]; }
+      int incl = sum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int x = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += x;
       }
-      sh.gbase[b] = sub.off + a.bases[(size_t)s * 257 + b] + excl - sh.tile_start[b];
+      int run = incl - sum;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) { sh.tile_start[lane * 8 + q] = run; run += loc[q]; }
     }
     __syncthreads();
+    {
+      const int b = threadIdx.x;
+      sh.gbase[b] = sub.off + a.bases[(size_t)s * 257 + b] +
+                    (long long)a.tile_off[(size_t)t * kMaxK + b] - sh.tile_start[b];
+    }
 #pragma unroll
     for (int j = 0; j < kKPT; ++j) {
       const int bk = (int)(br[j] >> 16);
@@ -454,13 +497,11 @@ __global__ void __launch_bounds__(kPassThreads, 2) k_scatter(LevelArgs a) {
       }
     }
     __syncthreads();
-    if (!sh.abort_tile) {
-      Bits* dst = dst_base[1 - sub.buf];
-      const int64_t lo = sub.off, hi = sub.off + sub.n;
-      for (int i = threadIdx.x; i < tn; i += blockDim.x) {
-        const int64_t p = sh.gbase[sh.sbid[i]] + i;
-        if (p >= lo && p < hi) dst[p] = sh.stage[i];
-      }
+    Bits* dst = dst_base[1 - sub.buf];
+    const int64_t lo = sub.off, hi = sub.off + sub.n;
+    for (int i = threadIdx.x; i < tn; i += blockDim.x) {
+      const int64_t p = sh.gbase[sh.sbid[i]] + i;
+      if (p >= lo && p < hi) dst[p] = sh.stage[i];
     }
   }
 }
@@ -508,11 +549,20 @@ cudaError_t launch_check(const LevelArgs& a, cudaStream_t s, int max_sample) {
   });
 }
 
-cudaError_t launch_hist(const LevelArgs& a, cudaStream_t s, int rehist_only, int grid) {
+static int resident_blocks(const void* fn, int threads, size_t smem, int sms) {
+  int per = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, smem) != cudaSuccess || per < 1) {
+    cudaGetLastError();
+    per = 1;
+  }
+  return per * sms;
+}
+
+cudaError_t launch_hist(const LevelArgs& a, cudaStream_t s, int rehist_only, int sms) {
   if (a.ntiles <= 0) return cudaSuccess;
   return by_dtype(a.dtype, [&](auto* tag) {
     using K = std::remove_pointer_t<decltype(tag)>;
-    int g = grid;
+    int g = resident_blocks((const void*)k_hist<K>, kPassThreads, 0, sms);
     if (g > a.ntiles) g = (int)a.ntiles;
     k_hist<K><<<g, kPassThreads, 0, s>>>(a, rehist_only);
     return cudaGetLastError();
@@ -528,13 +578,21 @@ cudaError_t launch_scan(const LevelArgs& a, cudaStream_t s) {
   });
 }
 
+cudaError_t launch_tilescan(const LevelArgs& a, cudaStream_t s, int grid) {
+  if (a.nchunks <= 0) return cudaSuccess;
+  int g = grid;
+  if (g > a.nchunks) g = (int)a.nchunks;
+  k_tilescan<<<g, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_scatter(const LevelArgs& a, cudaStream_t s, int grid) {
   if (a.ntiles <= 0) return cudaSuccess;
   return by_dtype(a.dtype, [&](auto* tag) {
     using K = std::remove_pointer_t<decltype(tag)>;
     const size_t smem = sizeof(ScatterSmem<K>);
     cudaFuncSetAttribute(k_scatter<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int g = grid;
+    int g = resident_blocks((const void*)k_scatter<K>, kPassThreads, smem, grid);
     if (g > a.ntiles) g = (int)a.ntiles;
     k_scatter<K><<<g, kPassThreads, smem, s>>>(a);
     return cudaGetLastError();

@@ -1,30 +1,82 @@
-// Block-resident IPLS: a group of small subproblems (consecutive buckets of
-// one parent, or consecutive segments) is loaded into one block's shared
-// memory once, the whole remaining recursion runs there -- sample, sort the
-// sample, fit, classify, stable scatter, recurse (Ch.2 IPS4o recursion into
-// independent buckets; Ch.4 IPLS) -- and the sorted keys are written to the
-// user buffer once.  Subproblems of at most `cutoff` keys are base-cased:
-// a warp-wide bitonic sort for up to 32 keys, a block-wide sorting network
-// above that (the paper's base case is SkaSort for n <= 2^12, Ch.4; any exact
-// sort gives the same, unique result).
+// Block-resident tail of the IPLS recursion (Ch.2 IPS4o recursion into
+// independent buckets; Ch.4 IPLS), for subproblems of at most kResidentMax
+// keys.
+//
+//   k_tail_fit   one warp per subproblem: sample alpha*k-1 keys, sort them,
+//                fit FMCD -- many fits in flight per SM hide the latency of
+//                the sorting network and of the binary64 steps.
+//   k_resident   one block per task.  A fitted subproblem is read from HBM
+//                once, classified with its model, ranked stably per bucket
+//                and placed into shared memory in bucket order; each bucket
+//                of at most `cutoff` keys is then base-cased by rank
+//                counting (the position of a key inside its bucket is the
+//                number of smaller keys, ties broken by position), and the
+//                sorted subproblem is written to the user buffer once.  A
+//                task of small children (consecutive buckets or segments of
+//                at most `cutoff` keys) goes straight to the base case.
+//                Rare cases -- a bucket above the cutoff, the splitter tree,
+//                a pass without progress -- continue the recursion inside
+//                the block (sample, sort, fit, classify, stable scatter).
+//
+// The paper's base case is SkaSort for n <= 2^12 (Ch.4); any exact sort
+// gives the same, unique result.
 #include "ipls_device.cuh"
 
 namespace ipls {
 
 constexpr int kRW = kResidentThreads / 32;  // warps
 constexpr int kRKPT = kResidentMax / kResidentThreads;
+constexpr int kFitWarps = 8;
 
+// ---------------------------------------------------------------------------
+// k_tail_fit
+// ---------------------------------------------------------------------------
+template <class K>
+__global__ void __launch_bounds__(kFitWarps * 32) k_tail_fit(ResidentArgs a) {
+  using T = KT<K>;
+  using Ord = typename T::Ord;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ FitShared fs[kFitWarps];
+  __shared__ LinModel lm[kFitWarps];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int task = blockIdx.x * kFitWarps + warp;
+  if (task >= a.nfit) return;
+  Ord* so = reinterpret_cast<Ord*>(smem_raw) + warp * kResidentSample;
+  const Group g = a.groups[a.fit_list[task]];
+  int S = (int)sample_size(g.n, g.level, a.k, a.root_sample);
+  if (S > kResidentSample) S = kResidentSample;  // never planned by the host
+  const uint64_t stream = stream_key(a.seed, g.off, g.n, g.level);
+  const typename T::Bits* src = reinterpret_cast<const typename T::Bits*>(a.buf[g.buf]) + g.off;
+  for (int j = lane; j < S; j += 32) so[j] = T::ord(src[sample_offset(stream, j, g.n)]);
+  __syncwarp();
+  group_sort<WarpG, Ord>(so, S);
+  fit_linear<WarpG, K>(so, S, a.k, &lm[warp], fs[warp]);
+  const unsigned long long* s = reinterpret_cast<const unsigned long long*>(&lm[warp]);
+  unsigned long long* d = reinterpret_cast<unsigned long long*>(&a.tail_models[g.fit]);
+  if (lane < (int)(sizeof(LinModel) / 8)) d[lane] = s[lane];
+}
+
+// ---------------------------------------------------------------------------
+// k_resident
+// ---------------------------------------------------------------------------
 template <class K>
 struct ResSmem {
   typename KT<K>::Ord keys[kResidentMax];
-  typename KT<K>::Ord samp[kResidentSample];
-  unsigned short wcnt[kRW][kMaxK];
-  unsigned long long tasks[kResidentTasks];  // small list from 0 up, stack from the top down
+  unsigned char seg[kResidentMax];   // segment (bucket or child) of each position
+  union {
+    struct {
+      typename KT<K>::Ord samp[kResidentSample];
+      unsigned short wcnt[kRW][kMaxK];
+      unsigned long long tasks[kResidentTasks];  // small list from 0 up, stack from the top
+    } s;
+    unsigned short dest[kResidentMax];           // final position inside the task
+  } u;
   int bstart[kMaxK + 1];
   int tot[kMaxK];
+  int segb[kMaxK + 1];               // segment bounds for the base case
   Model model;
   FitShared fs;
-  int nsmall, nstack, redo, err;
+  int nsmall, nstack, redo, err, slow_all;
   unsigned long long popped;
   long long rec;
 };
@@ -36,124 +88,31 @@ __device__ __forceinline__ int task_start(unsigned long long e) { return (int)((
 __device__ __forceinline__ int task_len(unsigned long long e) { return (int)(e & 0xFFFF); }
 __device__ __forceinline__ int task_level(unsigned long long e) { return (int)(e >> 32); }
 
-// Base-cases every pending small range (all threads).
+// Writes one trace record for a pass (thread 0 writes the header).
 template <class K>
-__device__ void flush_small(ResSmem<K>& sh) {
-  using Ord = typename KT<K>::Ord;
-  __syncthreads();
-  const int ns = sh.nsmall;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int q = warp; q < ns; q += kRW) {
-    const unsigned long long e = sh.tasks[q];
-    const int st = task_start(e), len = task_len(e);
-    if (len > 32) continue;
-    Ord v = (lane < len) ? sh.keys[st + lane] : (Ord)~(Ord)0;
-    v = warp_sort32(v);
-    if (lane < len) sh.keys[st + lane] = v;
+__device__ void trace_pass(ResSmem<K>& sh, const ResidentArgs& a, int64_t off, int n, int level,
+                           const Model& m) {
+  if (a.trace_cap <= 0) return;
+  if (threadIdx.x == 0) {
+    sh.rec = (long long)atomicAdd((unsigned long long*)&a.run->trace_count, 1ULL);
+    if (sh.rec < a.trace_cap) {
+      iplsTraceRecDev& r = a.trace[sh.rec];
+      r.off = off; r.n = n; r.level = level; r.kind = m.l.kind; r.capped = m.l.capped;
+      r.nbuckets = m.l.nb; r.S = m.l.S; r.D = m.l.D; r.A = m.l.A; r.Bc = m.l.Bc; r.ud = m.l.ud;
+      r.xlo_bits = m.l.xlo_bits; r.nsplit = m.nsplit; r.where = 1;
+    }
   }
   __syncthreads();
-  for (int q = 0; q < ns; ++q) {
-    const unsigned long long e = sh.tasks[q];
-    if (task_len(e) > 32) block_sort(sh.keys + task_start(e), task_len(e));
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) sh.nsmall = 0;
+  if (sh.rec < a.trace_cap && threadIdx.x < kMaxK)
+    a.trace[sh.rec].counts[threadIdx.x] = (threadIdx.x < m.l.nb) ? sh.tot[threadIdx.x] : 0;
   __syncthreads();
 }
 
-// Queues a child range: small ones for the base case, large ones on the stack.
+// Exclusive scan of sh.tot into sh.bstart (one warp, 8 values per lane).
 template <class K>
-__device__ __forceinline__ void push_child(ResSmem<K>& sh, int start, int len, int level, int cutoff) {
-  if (len < 2) return;
-  if (len <= cutoff) {
-    const int i = atomicAdd(&sh.nsmall, 1);
-    if (i < kResidentTasks / 2) sh.tasks[i] = enc_task(start, len, level);
-    else sh.err = 1;
-  } else {
-    const int i = atomicAdd(&sh.nstack, 1);
-    if (i < kResidentTasks / 2) sh.tasks[kResidentTasks - 1 - i] = enc_task(start, len, level);
-    else sh.err = 1;
-  }
-}
-
-// One learned partition pass on keys[s0, s0+c) inside shared memory.
-template <class K>
-__device__ void resident_pass(ResSmem<K>& sh, const ResidentArgs& a, int64_t goff, int s0, int c,
-                              int level) {
-  using T = KT<K>;
-  using Ord = typename T::Ord;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // sample (with replacement) and sort it
-  int S = (int)sample_size(c, level, a.k, a.root_sample);
-  if (S > kResidentSample) {  // never planned by the host; keep the block in bounds
-    if (threadIdx.x == 0) sh.err = 1;
-    S = kResidentSample;
-  }
-  const uint64_t stream = stream_key(a.seed, goff + s0, c, level);
-  for (int j = threadIdx.x; j < S; j += blockDim.x) sh.samp[j] = sh.keys[s0 + sample_offset(stream, j, c)];
-  __syncthreads();
-  block_sort(sh.samp, S);
-  fit_model<K>(sh.samp, S, a.k, &sh.model, sh.fs);
-  // each warp owns a contiguous chunk of the range, in 32-key steps
-  const int chunk = ((c + kRW * 32 - 1) / (kRW * 32)) * 32;
-  const int steps = chunk / 32;
-  Ord v[kRKPT];
-  unsigned int br[kRKPT];
-  for (int attempt = 0; attempt < 2; ++attempt) {
-    Classifier<K> cls;
-    cls.load(sh.model, a.exact_only);
-    for (int i = threadIdx.x; i < kRW * kMaxK; i += blockDim.x) (&sh.wcnt[0][0])[i] = 0;
-    if (threadIdx.x == 0) sh.redo = 0;
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < kRKPT; ++j) {
-      if (j < steps) {
-        const int i = warp * chunk + j * 32 + lane;
-        const bool ok = i < c;
-        v[j] = ok ? sh.keys[s0 + i] : (Ord)0;
-        const int bk = ok ? cls.bucket(T::unord(v[j])) : kMaxK;
-        const unsigned peers = __match_any_sync(0xffffffffu, bk);
-        const int lt = __popc(peers & lanemask_lt());
-        const int leader = __ffs(peers) - 1;
-        const int basec = (bk < kMaxK) ? sh.wcnt[warp][bk] : 0;
-        br[j] = ((unsigned)bk << 16) | (unsigned)(basec + lt);
-        __syncwarp();
-        if (lane == leader && bk < kMaxK) sh.wcnt[warp][bk] = (unsigned short)(basec + __popc(peers));
-        __syncwarp();
-      }
-    }
-    __syncthreads();
-    if (threadIdx.x < kMaxK) {
-      const int b = threadIdx.x;
-      int run = 0;
-      for (int w = 0; w < kRW; ++w) {
-        const int x = sh.wcnt[w][b];
-        sh.wcnt[w][b] = (unsigned short)run;
-        run += x;
-      }
-      sh.tot[b] = run;
-      if (attempt == 0 && sh.model.kind == kLinear && run == c) sh.redo = 1;
-    }
-    __syncthreads();
-    if (!sh.redo) break;
-    // no progress: redo the pass with the splitter tree of the same sample
-    if (threadIdx.x == 0) {
-      Model& m = sh.model;
-      const int want = (a.k - 1) / 2;
-      int cnt = 0;
-      for (int i = 0; i < want; ++i) {
-        const uint64_t u = (uint64_t)sh.samp[(int64_t)(i + 1) * S / (want + 1)];
-        if (cnt == 0 || m.split[cnt - 1] != u) m.split[cnt++] = u;
-      }
-      m.kind = kSplitter;
-      m.nsplit = cnt;
-      m.nb = 2 * cnt + 1;
-      m.fast = 0;
-    }
-    __syncthreads();
-  }
-  // exclusive scan of the bucket totals (one warp, 8 values per lane)
-  if (warp == 0) {
+__device__ __forceinline__ void scan_totals(ResSmem<K>& sh) {
+  if ((threadIdx.x >> 5) == 0) {
+    const int lane = threadIdx.x & 31;
     int loc[8];
     int sum = 0;
 #pragma unroll
@@ -170,64 +129,147 @@ __device__ void resident_pass(ResSmem<K>& sh, const ResidentArgs& a, int64_t gof
     if (lane == 31) sh.bstart[kMaxK] = run;
   }
   __syncthreads();
+}
+
+// Totals per bucket from the per-warp counters (into sh.tot); turns wcnt
+// into per-warp exclusive offsets.
+template <class K>
+__device__ __forceinline__ void warp_counts_to_offsets(ResSmem<K>& sh) {
+  if (threadIdx.x < kMaxK) {
+    const int b = threadIdx.x;
+    int run = 0;
+    for (int w = 0; w < kRW; ++w) {
+      const int x = sh.u.s.wcnt[w][b];
+      sh.u.s.wcnt[w][b] = (unsigned short)run;
+      run += x;
+    }
+    sh.tot[b] = run;
+  }
+  __syncthreads();
+}
+
+// Base-cases every pending small range of the slow path (warp bitonic up to
+// 32 keys, block network above).
+template <class K>
+__device__ void flush_small(ResSmem<K>& sh) {
+  using Ord = typename KT<K>::Ord;
+  __syncthreads();
+  const int ns = sh.nsmall;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int q = warp; q < ns; q += kRW) {
+    const unsigned long long e = sh.u.s.tasks[q];
+    const int st = task_start(e), len = task_len(e);
+    if (len > 32) continue;
+    Ord v = (lane < len) ? sh.keys[st + lane] : (Ord)~(Ord)0;
+    v = warp_sort32(v);
+    if (lane < len) sh.keys[st + lane] = v;
+  }
+  __syncthreads();
+  for (int q = 0; q < ns; ++q) {
+    const unsigned long long e = sh.u.s.tasks[q];
+    if (task_len(e) > 32) block_sort(sh.keys + task_start(e), task_len(e));
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) sh.nsmall = 0;
+  __syncthreads();
+}
+
+template <class K>
+__device__ __forceinline__ void push_child(ResSmem<K>& sh, int start, int len, int level, int cutoff) {
+  if (len < 2) return;
+  if (len <= cutoff) {
+    const int i = atomicAdd(&sh.nsmall, 1);
+    if (i < kResidentTasks / 2) sh.u.s.tasks[i] = enc_task(start, len, level);
+    else sh.err = 1;
+  } else {
+    const int i = atomicAdd(&sh.nstack, 1);
+    if (i < kResidentTasks / 2) sh.u.s.tasks[kResidentTasks - 1 - i] = enc_task(start, len, level);
+    else sh.err = 1;
+  }
+}
+
+// Slow path: one learned partition pass on keys[s0, s0+c) inside shared
+// memory, fitting the model in the block (sample, sort, FMCD or splitter
+// tree, no-progress rule), then queueing the children.
+template <class K>
+__device__ void resident_pass(ResSmem<K>& sh, const ResidentArgs& a, int64_t goff, int s0, int c,
+                              int level) {
+  using T = KT<K>;
+  using Ord = typename T::Ord;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int S = (int)sample_size(c, level, a.k, a.root_sample);
+  if (S > kResidentSample) {  // never planned by the host; keep the block in bounds
+    if (threadIdx.x == 0) sh.err = 1;
+    S = kResidentSample;
+  }
+  const uint64_t stream = stream_key(a.seed, goff + s0, c, level);
+  for (int j = threadIdx.x; j < S; j += blockDim.x) sh.u.s.samp[j] = sh.keys[s0 + sample_offset(stream, j, c)];
+  __syncthreads();
+  block_sort(sh.u.s.samp, S);
+  fit_model<BlockG, K>(sh.u.s.samp, S, a.k, &sh.model, sh.fs);
+  const int chunk = ((c + kRW * 32 - 1) / (kRW * 32)) * 32;
+  const int steps = chunk / 32;
+  Ord v[kRKPT];
+  unsigned int br[kRKPT];
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    Classifier<K> cls;
+    cls.load(sh.model, a.exact_only);
+    for (int i = threadIdx.x; i < kRW * kMaxK; i += blockDim.x) (&sh.u.s.wcnt[0][0])[i] = 0;
+    if (threadIdx.x == 0) sh.redo = 0;
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kRKPT; ++j) {
+      if (j < steps) {
+        const int i = warp * chunk + j * 32 + lane;
+        const bool ok = i < c;
+        v[j] = ok ? sh.keys[s0 + i] : (Ord)0;
+        const int bk = ok ? cls.bucket(T::unord(v[j])) : kMaxK;
+        const unsigned peers = __match_any_sync(0xffffffffu, bk);
+        const int lt = __popc(peers & lanemask_lt());
+        const int leader = __ffs(peers) - 1;
+        const int basec = (bk < kMaxK) ? sh.u.s.wcnt[warp][bk] : 0;
+        br[j] = ((unsigned)bk << 16) | (unsigned)(basec + lt);
+        __syncwarp();
+        if (lane == leader && bk < kMaxK) sh.u.s.wcnt[warp][bk] = (unsigned short)(basec + __popc(peers));
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    warp_counts_to_offsets(sh);
+    if (threadIdx.x < kMaxK && attempt == 0 && sh.model.l.kind == kLinear && sh.tot[threadIdx.x] == c)
+      sh.redo = 1;
+    __syncthreads();
+    if (!sh.redo) break;
+    // no progress: redo the pass with the splitter tree of the same sample
+    build_splitters<BlockG, K>(sh.u.s.samp, S, a.k, &sh.model);
+  }
+  scan_totals(sh);
 #pragma unroll
   for (int j = 0; j < kRKPT; ++j) {
     if (j < steps) {
       const int bk = (int)(br[j] >> 16);
-      if (bk < kMaxK) sh.keys[s0 + sh.bstart[bk] + sh.wcnt[warp][bk] + (int)(br[j] & 0xFFFF)] = v[j];
+      if (bk < kMaxK) sh.keys[s0 + sh.bstart[bk] + sh.u.s.wcnt[warp][bk] + (int)(br[j] & 0xFFFF)] = v[j];
     }
   }
   __syncthreads();
   const Model& m = sh.model;
-  if (a.trace_cap > 0) {
-    if (threadIdx.x == 0) {
-      sh.rec = (long long)atomicAdd((unsigned long long*)&a.run->trace_count, 1ULL);
-      if (sh.rec < a.trace_cap) {
-        iplsTraceRecDev& r = a.trace[sh.rec];
-        r.off = goff + s0; r.n = c; r.level = level; r.kind = m.kind; r.capped = m.capped;
-        r.nbuckets = m.nb; r.S = m.S; r.D = m.D; r.A = m.A; r.Bc = m.Bc; r.ud = m.ud;
-        r.xlo_bits = m.xlo_bits; r.nsplit = m.nsplit; r.where = 1;
-      }
-    }
-    __syncthreads();
-    if (sh.rec < a.trace_cap && threadIdx.x < kMaxK)
-      a.trace[sh.rec].counts[threadIdx.x] = (threadIdx.x < m.nb) ? sh.tot[threadIdx.x] : 0;
-  }
+  trace_pass(sh, a, goff + s0, c, level, m);
   if (threadIdx.x == 0) {
     atomicAdd((unsigned long long*)&a.run->resident_passes, 1ULL);
-    if (m.kind == kSplitter) atomicAdd((unsigned long long*)&a.run->resident_fallback, 1ULL);
+    if (m.l.kind == kSplitter) atomicAdd((unsigned long long*)&a.run->resident_fallback, 1ULL);
   }
   // children (equality buckets of the splitter tree are homogeneous: done)
-  if (threadIdx.x < m.nb) {
+  if (threadIdx.x < m.l.nb) {
     const int b = threadIdx.x;
-    const bool eq = (m.kind == kSplitter) && (b & 1);
+    const bool eq = (m.l.kind == kSplitter) && (b & 1);
     if (!eq) push_child(sh, s0 + sh.bstart[b], sh.tot[b], level + 1, a.cutoff);
   }
   __syncthreads();
 }
 
+// Runs the slow-path stack to completion (all threads).
 template <class K>
-__global__ void __launch_bounds__(kResidentThreads, 2) k_resident(ResidentArgs a) {
-  using T = KT<K>;
-  using Bits = typename T::Bits;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  ResSmem<K>& sh = *reinterpret_cast<ResSmem<K>*>(smem_raw);
-  const Group g = a.groups[blockIdx.x];
-  const Bits* src = reinterpret_cast<const Bits*>(a.buf[g.buf]) + g.off;
-  for (int i = threadIdx.x; i < g.n; i += blockDim.x) sh.keys[i] = T::ord(src[i]);
-  if (threadIdx.x == 0) { sh.nsmall = 0; sh.nstack = 0; sh.err = 0; }
-  __syncthreads();
-  const int64_t b0 = g.bounds[0];
-  for (int q0 = 0; q0 < g.nchild; q0 += kMaxK) {
-    if (sh.nsmall + kMaxK > kResidentTasks / 2) flush_small(sh);
-    const int q = q0 + threadIdx.x;
-    if (threadIdx.x < kMaxK && q < g.nchild) {
-      const int st = (int)(g.bounds[q] - b0);
-      const int len = (int)(g.bounds[q + 1] - g.bounds[q]);
-      push_child(sh, st, len, g.level, a.cutoff);
-    }
-    __syncthreads();
-  }
+__device__ void run_stack(ResSmem<K>& sh, const ResidentArgs& a, int64_t goff) {
   for (;;) {
     __syncthreads();
     if (sh.nstack == 0 || sh.err) break;
@@ -235,7 +277,7 @@ __global__ void __launch_bounds__(kResidentThreads, 2) k_resident(ResidentArgs a
     __syncthreads();
     if (threadIdx.x == 0) {
       const int i = --sh.nstack;
-      sh.popped = sh.tasks[kResidentTasks - 1 - i];
+      sh.popped = sh.u.s.tasks[kResidentTasks - 1 - i];
     }
     __syncthreads();
     const unsigned long long e = sh.popped;
@@ -243,28 +285,141 @@ __global__ void __launch_bounds__(kResidentThreads, 2) k_resident(ResidentArgs a
       if (threadIdx.x == 0) { atomicExch(&a.run->error, -6); sh.nstack = 0; }
       continue;
     }
-    resident_pass<K>(sh, a, g.off, task_start(e), task_len(e), task_level(e));
+    resident_pass<K>(sh, a, goff, task_start(e), task_len(e), task_level(e));
   }
   if (sh.err) {
-    if (threadIdx.x == 0) atomicExch(&a.run->error, -6);
-    if (threadIdx.x == 0) sh.nsmall = 0;
+    if (threadIdx.x == 0) { atomicExch(&a.run->error, -6); sh.nsmall = 0; }
     __syncthreads();
   }
   flush_small(sh);
-  Bits* dst = reinterpret_cast<Bits*>(a.buf[0]) + g.off;
-  for (int i = threadIdx.x; i < g.n; i += blockDim.x) dst[i] = T::unord(sh.keys[i]);
-  if (threadIdx.x == 0) {
-    atomicAdd((unsigned long long*)&a.run->resident_keys, (unsigned long long)g.n);
-    atomicAdd((unsigned long long*)&a.run->resident_groups, 1ULL);
-  }
 }
 
-// Largest group a block can hold for this cutoff: every pending range of
-// more than `cutoff` keys, plus one pass's worth of children, must fit in
-// the task array.
-int resident_rmax(int cutoff) {
-  const long long lim = (long long)(kResidentTasks / 2) * (cutoff + 1);
-  return lim < kResidentMax ? (int)lim : kResidentMax;
+template <class K>
+__global__ void __launch_bounds__(kResidentThreads, 2) k_resident(ResidentArgs a) {
+  using T = KT<K>;
+  using Bits = typename T::Bits;
+  using Ord = typename T::Ord;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ResSmem<K>& sh = *reinterpret_cast<ResSmem<K>*>(smem_raw);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const Group g = a.groups[blockIdx.x];
+  const int n = g.n;
+  const Bits* src = reinterpret_cast<const Bits*>(a.buf[g.buf]) + g.off;
+  if (threadIdx.x == 0) { sh.nsmall = 0; sh.nstack = 0; sh.err = 0; sh.slow_all = 0; }
+  bool fitted = false;
+  if (g.fit >= 0) {
+    // ---- fast pass with the model fitted by k_tail_fit -------------------
+    if (threadIdx.x < (int)(sizeof(LinModel) / 8))
+      reinterpret_cast<unsigned long long*>(&sh.model.l)[threadIdx.x] =
+          reinterpret_cast<const unsigned long long*>(&a.tail_models[g.fit])[threadIdx.x];
+    for (int i = threadIdx.x; i < kRW * kMaxK; i += blockDim.x) (&sh.u.s.wcnt[0][0])[i] = 0;
+    __syncthreads();
+    fitted = sh.model.l.kind == kLinear;
+    if (fitted) {
+      Classifier<K> cls;
+      cls.load(sh.model.l, a.exact_only);
+      const int chunk = ((n + kRW * 32 - 1) / (kRW * 32)) * 32;
+      const int steps = chunk / 32;
+      Bits v[kRKPT];
+      unsigned int br[kRKPT];
+#pragma unroll
+      for (int j = 0; j < kRKPT; ++j) {
+        const int i = warp * chunk + j * 32 + lane;
+        v[j] = (j < steps && i < n) ? src[i] : Bits(0);
+      }
+#pragma unroll
+      for (int j = 0; j < kRKPT; ++j) {
+        if (j < steps) {
+          const int i = warp * chunk + j * 32 + lane;
+          const int bk = (i < n) ? cls.bucket(v[j]) : kMaxK;
+          const unsigned peers = __match_any_sync(0xffffffffu, bk);
+          const int lt = __popc(peers & lanemask_lt());
+          const int leader = __ffs(peers) - 1;
+          const int basec = (bk < kMaxK) ? sh.u.s.wcnt[warp][bk] : 0;
+          br[j] = ((unsigned)bk << 16) | (unsigned)(basec + lt);
+          __syncwarp();
+          if (lane == leader && bk < kMaxK) sh.u.s.wcnt[warp][bk] = (unsigned short)(basec + __popc(peers));
+          __syncwarp();
+        }
+      }
+      __syncthreads();
+      warp_counts_to_offsets(sh);
+      if (threadIdx.x < kMaxK && sh.tot[threadIdx.x] == n) sh.slow_all = 1;  // no progress
+      __syncthreads();
+      if (!sh.slow_all) {
+        scan_totals(sh);
+#pragma unroll
+        for (int j = 0; j < kRKPT; ++j) {
+          if (j < steps) {
+            const int bk = (int)(br[j] >> 16);
+            if (bk < kMaxK) {
+              const int p = sh.bstart[bk] + sh.u.s.wcnt[warp][bk] + (int)(br[j] & 0xFFFF);
+              sh.keys[p] = T::ord(v[j]);
+              sh.seg[p] = (unsigned char)bk;
+            }
+          }
+        }
+        for (int q = threadIdx.x; q <= kMaxK; q += blockDim.x) sh.segb[q] = sh.bstart[q];
+        __syncthreads();
+        if (threadIdx.x == 0) sh.model.nsplit = 0;
+        trace_pass(sh, a, g.off, n, g.level, sh.model);
+        if (threadIdx.x == 0) atomicAdd((unsigned long long*)&a.run->resident_passes, 1ULL);
+        // buckets above the cutoff continue the recursion in the block
+        if (threadIdx.x < sh.model.l.nb && sh.tot[threadIdx.x] > a.cutoff)
+          push_child(sh, sh.bstart[threadIdx.x], sh.tot[threadIdx.x], g.level + 1, a.cutoff);
+        __syncthreads();
+      } else {
+        fitted = false;
+      }
+    }
+  }
+  if (!fitted) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) sh.keys[i] = T::ord(src[i]);
+    if (g.fit >= 0) {
+      // the splitter tree or the no-progress rule: the whole task recurses in
+      // the block (the in-block fit reproduces the same sample and model)
+      for (int i = threadIdx.x; i < n; i += blockDim.x) sh.seg[i] = 0;
+      if (threadIdx.x == 0) {
+        sh.segb[0] = 0;
+        sh.segb[1] = n;
+        sh.nstack = 1;
+        sh.u.s.tasks[kResidentTasks - 1] = enc_task(0, n, g.level);
+      }
+    } else {
+      // consecutive small children: segment ids and bounds
+      const int64_t b0 = g.bounds[0];
+      for (int q = threadIdx.x; q <= g.nchild; q += blockDim.x) sh.segb[q] = (int)(g.bounds[q] - b0);
+      __syncthreads();
+      for (int q = warp; q < g.nchild; q += kRW)
+        for (int i = sh.segb[q] + lane; i < sh.segb[q + 1]; i += 32) sh.seg[i] = (unsigned char)q;
+    }
+    __syncthreads();
+  }
+  run_stack<K>(sh, a, g.off);
+  // ---- base case by rank counting for every segment of <= cutoff keys -----
+  const int cutoff = a.cutoff;
+  for (int p = threadIdx.x; p < n; p += blockDim.x) {
+    const int q = sh.seg[p];
+    const int s = sh.segb[q], e = sh.segb[q + 1];
+    int d = p;
+    if (e - s <= cutoff) {
+      const Ord kp = sh.keys[p];
+      int cnt = 0;
+      for (int r = s; r < e; ++r) {
+        const Ord kr = sh.keys[r];
+        cnt += (kr < kp) || (kr == kp && r < p);
+      }
+      d = s + cnt;
+    }
+    sh.u.dest[p] = (unsigned short)d;
+  }
+  __syncthreads();
+  Bits* dst = reinterpret_cast<Bits*>(a.buf[0]) + g.off;
+  for (int p = threadIdx.x; p < n; p += blockDim.x) dst[sh.u.dest[p]] = T::unord(sh.keys[p]);
+  if (threadIdx.x == 0) {
+    atomicAdd((unsigned long long*)&a.run->resident_keys, (unsigned long long)n);
+    atomicAdd((unsigned long long*)&a.run->resident_groups, 1ULL);
+  }
 }
 
 template <class Bits>
@@ -285,6 +440,18 @@ static cudaError_t by_dtype_r(int dtype, F f) {
   return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_tail_fit(const ResidentArgs& a, cudaStream_t s) {
+  if (a.nfit <= 0) return cudaSuccess;
+  return by_dtype_r(a.dtype, [&](auto* tag) {
+    using K = std::remove_pointer_t<decltype(tag)>;
+    const size_t smem = (size_t)kFitWarps * kResidentSample * sizeof(typename KT<K>::Ord);
+    cudaFuncSetAttribute(k_tail_fit<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int blocks = (a.nfit + kFitWarps - 1) / kFitWarps;
+    k_tail_fit<K><<<blocks, kFitWarps * 32, smem, s>>>(a);
+    return cudaGetLastError();
+  });
+}
+
 cudaError_t launch_resident(const ResidentArgs& a, cudaStream_t s) {
   if (a.ngroups <= 0) return cudaSuccess;
   return by_dtype_r(a.dtype, [&](auto* tag) {
@@ -303,6 +470,13 @@ cudaError_t launch_fill(const Fill* fills, int32_t nfill, int dtype, void* keys,
   else
     k_fill<unsigned int><<<nfill, 256, 0, s>>>(fills, reinterpret_cast<unsigned int*>(keys));
   return cudaGetLastError();
+}
+
+// Largest task a block can hold for this cutoff: every pending range of more
+// than `cutoff` keys must fit in half of the task array.
+int resident_rmax(int cutoff) {
+  const long long lim = (long long)(kResidentTasks / 2) * (cutoff + 1);
+  return lim < kResidentMax ? (int)lim : kResidentMax;
 }
 
 }  // namespace ipls

@@ -24,7 +24,13 @@ class iplsConfig(ctypes.Structure):
                 ("root_sample", ctypes.c_int64), ("seed", ctypes.c_uint64),
                 ("sync", ctypes.c_int32), ("exact_only", ctypes.c_int32),
                 ("spin_limit", ctypes.c_int64), ("trace_cap", ctypes.c_int64),
-                ("budget_bytes", ctypes.c_int64), ("reserved", ctypes.c_int32 * 8)]
+                ("budget_bytes", ctypes.c_int64), ("profile", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 7)]
+
+
+class iplsKernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_int64),
+                ("total_ms", ctypes.c_double), ("bytes", ctypes.c_int64)]
 
 
 class iplsTraceRec(ctypes.Structure):
@@ -46,8 +52,8 @@ class iplsStats(ctypes.Structure):
 
 _lib = None
 SYMBOLS = ["iplsDefaultConfig", "iplsCreate", "iplsDestroy", "iplsScratchBytes", "iplsSort",
-           "iplsSortSegmented", "iplsSubmit", "iplsPoll", "iplsWait", "iplsGetStats",
-           "iplsGetTrace", "iplsLastError"]
+           "iplsSortSegmented", "iplsSortHost", "iplsSubmit", "iplsPoll", "iplsWait",
+           "iplsGetStats", "iplsGetKernelStats", "iplsGetTrace", "iplsLastError"]
 
 
 def library_path() -> str:
@@ -74,6 +80,9 @@ def load(build_if_missing: bool = True):
     L.iplsScratchBytes.argtypes = [P, c.c_int64, c.c_int, c.POINTER(c.c_size_t)]
     L.iplsSort.argtypes = [P, P, c.c_int64, c.c_int]
     L.iplsSortSegmented.argtypes = [P, P, P, c.c_int64, c.c_int]
+    L.iplsSortHost.argtypes = [P, P, c.c_int64, c.c_int]
+    L.iplsGetKernelStats.argtypes = [P, c.POINTER(iplsKernelStat), c.c_int32,
+                                     c.POINTER(c.c_int32), c.c_int32]
     L.iplsSubmit.argtypes = [P, P, c.c_int64, c.c_int, c.POINTER(c.c_uint64)]
     L.iplsPoll.argtypes = [P, c.c_uint64]
     L.iplsWait.argtypes = [P, c.c_uint64, c.c_int64]
@@ -137,6 +146,20 @@ def iplsSortSegmented(ctx: int | None, keys_ptr: int, offsets_ptr: int, nseg: in
                   "iplsSortSegmented")
 
 
+def iplsSortHost(ctx: int | None, host_ptr: int, n: int, dtype: int) -> int:
+    return _check(load().iplsSortHost(ctypes.c_void_p(ctx), ctypes.c_void_p(host_ptr), n, dtype),
+                  "iplsSortHost")
+
+
+def iplsGetKernelStats(ctx: int, reset: bool = False) -> list:
+    out = (iplsKernelStat * 32)()
+    cnt = ctypes.c_int32()
+    _check(load().iplsGetKernelStats(ctypes.c_void_p(ctx), out, 32, ctypes.byref(cnt),
+                                     1 if reset else 0), "iplsGetKernelStats")
+    return [dict(name=r.name.decode(), launches=r.launches, total_ms=r.total_ms,
+                 bytes=r.bytes) for r in out[: cnt.value]]
+
+
 def iplsSubmit(ctx: int, keys_ptr: int, n: int, dtype: int) -> int:
     t = ctypes.c_uint64()
     _check(load().iplsSubmit(ctypes.c_void_p(ctx), ctypes.c_void_p(keys_ptr), n, dtype,
@@ -185,13 +208,14 @@ class Context:
 
     def __init__(self, *, k: int = 256, cutoff: int = 32, root_sample: int = 0, seed: int = 0,
                  exact_only: bool = False, trace_cap: int = 0, spin_limit: int | None = None,
-                 stream=None, budget_bytes: int = 0):
+                 stream=None, budget_bytes: int = 0, profile: bool = False):
         import torch
         cfg = iplsDefaultConfig()
         cfg.k, cfg.cutoff, cfg.root_sample, cfg.seed = k, cutoff, root_sample, seed
         cfg.exact_only = 1 if exact_only else 0
         cfg.trace_cap = trace_cap
         cfg.budget_bytes = budget_bytes
+        cfg.profile = 1 if profile else 0
         if spin_limit is not None:
             cfg.spin_limit = spin_limit
         s = stream if stream is not None else torch.cuda.current_stream()
@@ -214,8 +238,14 @@ class Context:
         iplsSortSegmented(self.ctx, keys.data_ptr(), offsets.data_ptr(), offsets.numel() - 1,
                           dtype_code(keys))
 
+    def sort_host_ptr(self, host_ptr: int, n: int, dtype: int) -> None:
+        iplsSortHost(self.ctx, host_ptr, n, dtype)
+
     def stats(self) -> iplsStats:
         return iplsGetStats(self.ctx)
+
+    def kernel_stats(self, reset: bool = False) -> list:
+        return iplsGetKernelStats(self.ctx, reset)
 
     def trace(self) -> list:
         return iplsGetTrace(self.ctx, self.trace_cap)

@@ -35,7 +35,7 @@ def test_host_side_validation_without_gpu():
     assert lib.iplsDefaultConfig(None) == -1
     assert lib.iplsSort(None, None, -5, 0) == -1
     assert lib.iplsSort(None, None, 10, 7) == -1
-    assert lib.iplsSort(None, None, 2**41, 0) == -1
+    assert lib.iplsSort(None, None, 2**32, 0) == -1
     assert lib.iplsSort(None, None, 10, 0) == -1      # NULL keys
     assert "NULL" in p.iplsLastError()
     assert lib.iplsSortSegmented(None, None, None, -1, 0) == -1
