@@ -17,16 +17,19 @@
  *     return IPLS_ERR_ARG without touching memory.
  *   - Device pointers must be valid for the GPU the context was created on
  *     and aligned to the key width.  The caller owns `keys`; the context
- *     owns all scratch memory (one ping-pong key buffer of n keys plus
- *     per-level bookkeeping), allocated through the context's allocator.
+ *     owns all scratch memory (one ping-pong key buffer of n keys, one bucket
+ *     id byte per key, and per-level bookkeeping), allocated through the
+ *     context's allocator.
  *   - Work is enqueued on the context's stream.  With cfg.sync = 1 (the
  *     default) a call waits for its work and returns the device status;
  *     with cfg.sync = 0 it returns after enqueueing and a device-side error
  *     surfaces at the next synchronising call (iplsGetStats, iplsWait, or a
  *     synchronous sort).
- *   - On an error the key array holds a permutation of its input (keys are
- *     only ever moved, never overwritten with foreign data) unless the error
- *     is IPLS_ERR_ARG, which leaves it untouched.
+ *   - IPLS_ERR_ARG and IPLS_ERR_BUDGET leave the key array untouched.  After
+ *     any other error the contents of the key array are unspecified (a
+ *     partition level may have stopped half-way between the array and the
+ *     context's ping-pong buffer); the context stays usable and its next call
+ *     starts from a clean state.
  *   - iplsLastError() returns a thread-local message for the last failure.
  */
 #ifndef IPLS_H_
@@ -68,8 +71,14 @@ typedef struct iplsConfig {
   int64_t budget_bytes;   /* iplsSubmit admission budget (0 = unlimited) */
   int32_t profile;        /* 1: time every kernel launch with CUDA events
                              (read with iplsGetKernelStats) */
-  int32_t reserved[7];
+  int32_t flags;          /* IPLS_FLAG_* bits (tuning switches; results do not change) */
+  int32_t reserved[6];
 } iplsConfig;
+
+/* cfg.flags: classify grid-level passes through the exact threshold index
+ * instead of the certified fixed-point estimate (same buckets, different
+ * speed; off by default). */
+#define IPLS_FLAG_THRESHOLD_INDEX 1
 
 /* Accumulated device time of one kernel of the library (profile = 1).
  * bytes = algorithmic bytes: keys read + keys written by the launches, in

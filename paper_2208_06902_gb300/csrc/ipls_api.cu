@@ -48,6 +48,7 @@ struct Slot {
   int32_t* tile2sub = nullptr;   int64_t tile_cap = 0;
   int32_t* chunk2sub = nullptr;  int64_t chunk_cap = 0;
   Model* models = nullptr;       int64_t model_cap = 0;
+  ThrTable* tabs = nullptr;      int64_t tab_cap = 0;
   uint64_t* counts = nullptr;    int64_t count_cap = 0;
   int64_t* bases = nullptr;      int64_t base_cap = 0;
   Group* groups = nullptr;       int64_t group_cap = 0;
@@ -69,6 +70,7 @@ struct iplsContext {
   char* scratch = nullptr;            int64_t scratch_cap = 0;   // bytes
   unsigned long long* status = nullptr; int64_t status_cap = 0;  // words
   uint32_t* tile_off = nullptr;       int64_t tile_off_cap = 0;  // words
+  uint8_t* bids = nullptr;            int64_t bids_cap = 0;      // bytes
   uint32_t epoch = 0;
   Slot slot[2];
   LevelCtl* ctl = nullptr;
@@ -95,6 +97,9 @@ struct iplsContext {
   int64_t k_bytes[16] = {};
   // host-buffer sorting
   char* host_stage = nullptr; int64_t host_stage_cap = 0;
+  // slow list of the block-resident tail
+  SlowTask* slow = nullptr; int64_t slow_cap = 0;
+  SlowCtl* slow_ctl = nullptr;
 };
 
 namespace {
@@ -143,11 +148,11 @@ iplsStatus ensure(iplsCtx c, T*& p, int64_t& cap, int64_t need) {
 bool valid_dtype(int d) { return d >= 0 && d <= 3; }
 
 enum KernelKind { kkFit, kkHist, kkCheck, kkRehist, kkScan, kkScatter, kkResident, kkFill,
-                  kkInitSeg, kkInitTiles, kkTailFit, kkTileScan, kkCount };
+                  kkInitSeg, kkInitTiles, kkTailFit, kkTileScan, kkSlow, kkCount };
 const char* const kKernelNames[kkCount] = {"k_fit", "k_hist", "k_check", "k_hist_redo", "k_scan",
-                                           "k_scatter", "k_resident", "k_fill",
+                                           "k_scatter", "k_tail", "k_fill",
                                            "k_init_segments", "k_init_tiles", "k_tail_fit",
-                                           "k_tilescan"};
+                                           "k_tilescan", "k_slow"};
 
 cudaEvent_t take_event(iplsCtx c) {
   if (!c->spare_events.empty()) {
@@ -210,8 +215,14 @@ iplsStatus launch_tail(iplsCtx c, ResidentArgs& ra, Slot& s, int32_t ngroups, in
   ra.fit_list = s.fit_list;
   ra.nfit = nfit;
   ra.tail_models = s.tails;
+  ra.slow = c->slow;
+  ra.slow_cap = (int32_t)std::min<int64_t>(c->slow_cap, INT32_MAX);
+  ra.slow_ctl = c->slow_ctl;
+  if (ngroups <= 0) return IPLS_OK;
   if (nfit > 0) IPLS_CUDA(timed(c, kkTailFit, [&] { return launch_tail_fit(ra, c->stream); }));
-  if (ngroups > 0) IPLS_CUDA(timed(c, kkResident, [&] { return launch_resident(ra, c->stream); }));
+  IPLS_CUDA(cudaMemsetAsync(c->slow_ctl, 0, sizeof(SlowCtl), c->stream));
+  IPLS_CUDA(timed(c, kkResident, [&] { return launch_resident(ra, c->stream); }));
+  IPLS_CUDA(timed(c, kkSlow, [&] { return launch_slow(ra, c->stream, c->num_sms); }));
   return IPLS_OK;
 }
 
@@ -248,6 +259,8 @@ iplsStatus sort_impl(iplsCtx c, void* keys, int64_t n, int dtype, const int64_t*
   c->stats.max_bucket_frac = 0.0;
   c->trace_grid_count = 0;
   IPLS_TRY(ensure(c, c->scratch, c->scratch_cap, n * (int64_t)w));
+  IPLS_TRY(ensure(c, c->bids, c->bids_cap, n));
+  IPLS_TRY(ensure(c, c->slow, c->slow_cap, 2 * (n / (cfg.cutoff + 1)) + 4096));
   if (cfg.trace_cap > 0 && c->trace_alloc < cfg.trace_cap) {
     IPLS_CUDA(cudaStreamSynchronize(c->stream));
     dev_free(c, c->trace_grid, (size_t)c->trace_alloc * sizeof(iplsTraceRecDev));
@@ -339,6 +352,7 @@ iplsStatus sort_impl(iplsCtx c, void* keys, int64_t n, int dtype, const int64_t*
     Slot& X = c->slot[level & 1];
     Slot& Y = c->slot[(level + 1) & 1];
     IPLS_TRY(ensure(c, X.models, X.model_cap, nsub));
+    IPLS_TRY(ensure(c, X.tabs, X.tab_cap, nsub));
     IPLS_TRY(ensure(c, X.counts, X.count_cap, nsub * kMaxK));
     IPLS_TRY(ensure(c, X.bases, X.base_cap, nsub * 257));
     IPLS_TRY(ensure_groups(c, X, 2 * n / (cfg.cutoff + 1) + 257 * nsub + 16));
@@ -360,11 +374,14 @@ iplsStatus sort_impl(iplsCtx c, void* keys, int64_t n, int dtype, const int64_t*
     LevelArgs a{};
     a.dtype = dtype; a.k = cfg.k; a.cutoff = cfg.cutoff; a.rmax = rmax;
     a.root_sample = cfg.root_sample; a.seed = cfg.seed; a.exact_only = cfg.exact_only;
+    a.use_tables = (cfg.flags & IPLS_FLAG_THRESHOLD_INDEX) && !cfg.exact_only;
     a.spin_limit = cfg.spin_limit; a.epoch = c->epoch; a.level = level;
     a.buf[0] = bufs[0]; a.buf[1] = bufs[1];
     a.nsub = (int32_t)nsub; a.subs = X.subs; a.models = X.models; a.counts = X.counts;
+    a.tabs = X.tabs;
     a.bases = X.bases; a.tile2sub = X.tile2sub; a.ntiles = ntiles; a.status = c->status;
     a.chunk2sub = X.chunk2sub; a.nchunks = nchunks; a.tile_off = c->tile_off;
+    a.bids = c->bids;
     a.ctl = c->ctl; a.run = c->run;
     a.next_subs = Y.subs; a.next_sub_cap = (int32_t)std::min<int64_t>(Y.sub_cap, INT32_MAX);
     a.next_tile2sub = Y.tile2sub; a.next_tile_cap = Y.tile_cap;
@@ -559,6 +576,8 @@ iplsStatus iplsCreate(iplsCtx* out, const iplsConfig* cfg, iplsAllocFn alloc, ip
   c->run = (RunStatus*)p;
   if ((st = dev_alloc(c, &p, 2 * sizeof(int64_t))) != IPLS_OK) { iplsDestroy(c); return st; }
   c->root_bounds = (int64_t*)p;
+  if ((st = dev_alloc(c, &p, sizeof(SlowCtl))) != IPLS_OK) { iplsDestroy(c); return st; }
+  c->slow_ctl = (SlowCtl*)p;
   *out = c;
   return IPLS_OK;
 }
@@ -569,11 +588,13 @@ iplsStatus iplsDestroy(iplsCtx c) {
   dev_free(c, c->scratch, (size_t)c->scratch_cap);
   dev_free(c, c->status, (size_t)c->status_cap * 8);
   dev_free(c, c->tile_off, (size_t)c->tile_off_cap * 4);
+  dev_free(c, c->bids, (size_t)c->bids_cap);
   for (Slot& s : c->slot) {
     dev_free(c, s.subs, s.sub_cap * sizeof(Sub));
     dev_free(c, s.tile2sub, s.tile_cap * sizeof(int32_t));
     dev_free(c, s.chunk2sub, s.chunk_cap * sizeof(int32_t));
     dev_free(c, s.models, s.model_cap * sizeof(Model));
+    dev_free(c, s.tabs, s.tab_cap * sizeof(ThrTable));
     dev_free(c, s.counts, s.count_cap * sizeof(uint64_t));
     dev_free(c, s.bases, s.base_cap * sizeof(int64_t));
     dev_free(c, s.groups, s.group_cap * sizeof(Group));
@@ -591,6 +612,8 @@ iplsStatus iplsDestroy(iplsCtx c) {
   for (auto& p : c->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
   for (cudaEvent_t e : c->spare_events) cudaEventDestroy(e);
   dev_free(c, c->host_stage, (size_t)c->host_stage_cap);
+  dev_free(c, c->slow, (size_t)c->slow_cap * sizeof(SlowTask));
+  dev_free(c, c->slow_ctl, sizeof(SlowCtl));
   delete c;
   return IPLS_OK;
 }
@@ -603,6 +626,7 @@ iplsStatus iplsScratchBytes(iplsCtx c, int64_t n, iplsDtype dtype, size_t* bytes
   const int64_t subs = n / (rmax + 1) + 2;
   const int64_t tiles = n / tile_keys(dtype) + subs + 2;
   size_t b = (size_t)n * key_bytes(dtype);                         // ping-pong keys
+  b += (size_t)n;                                                  // bucket ids
   b += (size_t)tiles * kMaxK * 8;                                  // look-back words
   b += 2 * (size_t)subs * (sizeof(Sub) + sizeof(Model) + kMaxK * 8 + 257 * 8);
   b += 2 * (size_t)tiles * 4;

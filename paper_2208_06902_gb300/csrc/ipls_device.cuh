@@ -69,6 +69,7 @@ template <> struct KT<double> {
   using Bits = unsigned long long;
   using Ord = unsigned long long;
   static constexpr int W = 8;
+  static constexpr int kMant = 52;   // low ord bits linear inside a binade
   __device__ static __forceinline__ Ord ord(Bits b) {
     return (b >> 63) ? ~b : (b | (1ULL << 63));
   }
@@ -94,6 +95,7 @@ template <> struct KT<float> {
   using Bits = unsigned int;
   using Ord = unsigned int;
   static constexpr int W = 4;
+  static constexpr int kMant = 23;
   __device__ static __forceinline__ Ord ord(Bits b) { return (b >> 31) ? ~b : (b | 0x80000000u); }
   __device__ static __forceinline__ Bits unord(Ord u) { return (u >> 31) ? (u & 0x7FFFFFFFu) : ~u; }
   __device__ static __forceinline__ double value(Bits b) { return (double)__uint_as_float(b); }
@@ -114,6 +116,7 @@ template <class U, int WB> struct KTInt {
   using Bits = U;
   using Ord = U;
   static constexpr int W = WB;
+  static constexpr int kMant = 0;    // integer keys: the value is linear in u
   __device__ static __forceinline__ Ord ord(Bits b) { return b; }
   __device__ static __forceinline__ Bits unord(Ord u) { return u; }
   __device__ static __forceinline__ double value(Bits b) { return __ull2double_rn((unsigned long long)b); }
@@ -537,6 +540,225 @@ struct Classifier {
   }
 };
 
+// ---------------------------------------------------------------------------
+// Exact thresholds of the linear model and the two-level index (ThrTable).
+// ---------------------------------------------------------------------------
+template <class K>
+__device__ __forceinline__ int exact_bucket_ord(typename KT<K>::Ord u, const LinModel& m) {
+  using T = KT<K>;
+  return classify_exact<K>(T::unord(u), m.A, m.Bc, (typename T::Bits)m.xlo_bits, m.nb);
+}
+
+// An ord key near the value x_lo + (j - Bc) * u_d, where the model's value
+// crosses j (a starting point only; the search below is exact).
+template <class K>
+__device__ __forceinline__ typename KT<K>::Ord threshold_estimate(int j, const LinModel& m) {
+  using T = KT<K>;
+  using Ord = typename T::Ord;
+  const double x0 = T::value((typename T::Bits)m.xlo_bits);
+  const double est = __fma_rn(__dsub_rn((double)j, m.Bc), m.ud, x0);
+  if (!(est == est)) return T::ord((typename T::Bits)m.xlo_bits);
+  if (T::kMant == 52) {
+    return (Ord)T::ord((typename T::Bits)__double_as_longlong(est));
+  } else if (T::kMant == 23) {
+    return (Ord)T::ord((typename T::Bits)__float_as_uint(__double2float_rn(est)));
+  } else {
+    const double top = T::W == 8 ? 18446744073709551615.0 : 4294967295.0;
+    if (est <= 0.0) return (Ord)0;
+    if (est >= top) return (Ord)~(Ord)0;
+    return (Ord)__double2ull_rz(est);
+  }
+}
+
+// Smallest ord key u with bucket(u) >= j (1 <= j <= nb-1), by galloping from
+// the estimate and bisection; the bucket map is monotone in u.
+template <class K>
+__device__ typename KT<K>::Ord exact_threshold(int j, const LinModel& m) {
+  using Ord = typename KT<K>::Ord;
+  const Ord top = ~(Ord)0;
+  Ord u0 = threshold_estimate<K>(j, m);
+  Ord lo, hi;
+  if (exact_bucket_ord<K>(u0, m) >= j) {
+    hi = u0;
+    Ord step = 1;
+    for (;;) {
+      if (hi == 0) return 0;
+      const Ord cand = hi > step ? hi - step : (Ord)0;
+      if (exact_bucket_ord<K>(cand, m) < j) { lo = cand; break; }
+      hi = cand;
+      step = step << 1 ? step << 1 : step;
+    }
+  } else {
+    lo = u0;
+    Ord step = 1;
+    for (;;) {
+      if (lo == top) return top;
+      const Ord cand = (Ord)(top - lo) > step ? (Ord)(lo + step) : top;
+      if (exact_bucket_ord<K>(cand, m) >= j) { hi = cand; break; }
+      lo = cand;
+      step = step << 1 ? step << 1 : step;
+    }
+  }
+  while ((Ord)(hi - lo) > 1) {  // bucket(lo) < j <= bucket(hi)
+    const Ord mid = lo + (Ord)((hi - lo) / 2);
+    if (exact_bucket_ord<K>(mid, m) >= j) hi = mid; else lo = mid;
+  }
+  return hi;
+}
+
+// Number of thresholds thr[1..nt] that are <= u (thr ascending).
+__device__ __forceinline__ int count_le(const uint64_t* thr, int nt, uint64_t u) {
+  int lo = 0, hi = nt;  // answer in [0, nt]
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (thr[mid] <= u) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Builds the thresholds and the index of a linear model into `t` (shared
+// memory), with every thread of the block.  t->ok = 0 when the index would
+// not fit (the model is then evaluated directly).
+template <class K>
+__device__ void build_thr_table(const LinModel& m, ThrTable* t, int* scan_tmp) {
+  using T = KT<K>;
+  constexpr int MB = T::kMant;
+  const int nb = m.nb, nt = nb - 1;
+  for (int j = threadIdx.x; j <= kMaxK; j += blockDim.x) {
+    if (j == 0) t->thr[0] = 0;
+    else if (j <= nt) t->thr[j] = (uint64_t)exact_threshold<K>(j, m);
+    else t->thr[j] = ~0ULL;
+  }
+  __syncthreads();
+  __shared__ int s_nl1, s_ok, s_elo;
+  if (threadIdx.x == 0) {
+    s_ok = 1;
+    if (MB > 0) {
+      const int elo = (int)(t->thr[1] >> MB), ehi = (int)(t->thr[nt] >> MB);
+      s_elo = elo;
+      s_nl1 = ehi - elo + 1;
+      if (s_nl1 > kL1Max) s_ok = 0;
+      t->ishift = 0;
+    } else {
+      s_elo = 0;
+      s_nl1 = 1;
+      const uint64_t span = t->thr[nt] - t->thr[1];
+      const int bits = span ? 64 - __clzll((long long)span) : 0;
+      t->ishift = bits > 10 ? bits - 10 : 0;
+    }
+    t->e_lo = s_elo;
+    t->n_l1 = s_nl1;
+  }
+  __syncthreads();
+  if (!s_ok) {
+    if (threadIdx.x == 0) t->ok = 0;
+    __syncthreads();
+    return;
+  }
+  const int nl1 = s_nl1, elo = s_elo;
+  // sizes of the cell tables, per coarse entry (scan_tmp: kL1Max ints)
+  for (int e = threadIdx.x; e < nl1; e += blockDim.x) {
+    int size = 0;
+    if (MB > 0) {
+      const uint64_t lo_u = (uint64_t)(elo + e) << MB;
+      const uint64_t hi_u = lo_u + ((1ULL << MB) - 1);
+      const int c = count_le(t->thr, nt, hi_u) - count_le(t->thr, nt, lo_u);
+      if (c > 0) {
+        int mm = 2;
+        while ((1 << mm) < 4 * c && mm < 10) ++mm;
+        size = 1 << mm;
+      }
+    } else {
+      size = (int)((t->thr[nt] - t->thr[1]) >> t->ishift) + 1;
+    }
+    scan_tmp[e] = size;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {  // exclusive scan (n_l1 <= 4096, once per subproblem)
+    int run = 0;
+    for (int e = 0; e < nl1; ++e) { const int x = scan_tmp[e]; scan_tmp[e] = run; run += x; }
+    if (run > kL2Max) s_ok = 0;
+  }
+  __syncthreads();
+  if (!s_ok) {
+    if (threadIdx.x == 0) t->ok = 0;
+    __syncthreads();
+    return;
+  }
+  for (int e = threadIdx.x; e < nl1; e += blockDim.x) {
+    const int off = scan_tmp[e];
+    if (MB > 0) {
+      const uint64_t lo_u = (uint64_t)(elo + e) << MB;
+      const uint64_t hi_u = lo_u + ((1ULL << MB) - 1);
+      const int b0 = count_le(t->thr, nt, lo_u);
+      const int c = count_le(t->thr, nt, hi_u) - b0;
+      if (c == 0) {
+        t->l1[e] = (uint16_t)b0;
+      } else {
+        int mm = 2;
+        while ((1 << mm) < 4 * c && mm < 10) ++mm;
+        t->l1[e] = (uint16_t)(0x8000 | (mm << 11) | off);
+      }
+    } else {
+      t->l1[0] = 0x8000;
+    }
+  }
+  __syncthreads();
+  // cells in parallel: each finds its entry by binary search over the offsets
+  __shared__ int s_total;
+  if (threadIdx.x == 0) {
+    int total = 0;
+    if (MB > 0) {
+      const unsigned last = t->l1[nl1 - 1];
+      total = scan_tmp[nl1 - 1] + ((last & 0x8000) ? (1 << ((last >> 11) & 15)) : 0);
+    } else {
+      total = (int)((t->thr[nt] - t->thr[1]) >> t->ishift) + 1;
+    }
+    s_total = total;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < s_total; q += blockDim.x) {
+    if (MB > 0) {
+      int lo = 0, hi = nl1 - 1;  // last entry with offset <= q and a cell table
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (scan_tmp[mid] <= q) lo = mid; else hi = mid - 1;
+      }
+      while (lo > 0 && !(t->l1[lo] & 0x8000)) --lo;  // entries without cells have size 0
+      const unsigned ent = t->l1[lo];
+      const int mm = (ent >> 11) & 15;
+      const int k = q - scan_tmp[lo];
+      const uint64_t lo_u = (uint64_t)(elo + lo) << MB;
+      t->l2[q] = (uint8_t)count_le(t->thr, nt, lo_u + ((uint64_t)k << (MB - mm)));
+    } else {
+      t->l2[q] = (uint8_t)count_le(t->thr, nt, t->thr[1] + ((uint64_t)q << t->ishift));
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) t->ok = 1;
+  __syncthreads();
+}
+
+// Bucket of ord key u from the thresholds and their index (t->ok == 1).
+template <class K>
+__device__ __forceinline__ int table_bucket(typename KT<K>::Ord u, const ThrTable& t, int nb) {
+  constexpr int MB = KT<K>::kMant;
+  const uint64_t uu = (uint64_t)u;
+  if (uu < t.thr[1]) return 0;
+  if (uu >= t.thr[nb - 1]) return nb - 1;
+  int g;
+  if (MB > 0) {
+    const unsigned ent = t.l1[(int)(uu >> MB) - t.e_lo];
+    if (!(ent & 0x8000)) return (int)ent;
+    const int mm = (ent >> 11) & 15, off = ent & 0x7FF;
+    g = t.l2[off + (int)((uu >> (MB - mm)) & ((1u << mm) - 1))];
+  } else {
+    g = t.l2[(int)((uu - t.thr[1]) >> t.ishift)];
+  }
+  while (uu >= t.thr[g + 1]) ++g;
+  return g;
+}
+
 // Reserves the tiles of a new grid subproblem of n keys, and the chunks of
 // kChunkTiles tiles the look-back scan walks, in the next level's tile and
 // chunk spaces; fills the Sub fields.  False (and ctl->overflow) when a
@@ -565,6 +787,20 @@ __device__ __forceinline__ unsigned lanemask_lt() {
   unsigned m;
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
   return m;
+}
+
+// Lanes of the warp holding the same bucket id (0..255) as this lane, from
+// eight ballots (cheaper than a match instruction on this GPU); lanes with
+// valid == false are in no set and get 0.
+__device__ __forceinline__ unsigned same_bucket_lanes(int bk, bool valid) {
+  unsigned peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+  for (int bit = 0; bit < 8; ++bit) {
+    const bool on = (bk >> bit) & 1;
+    const unsigned m = __ballot_sync(0xffffffffu, on);
+    peers &= on ? m : ~m;
+  }
+  return valid ? peers : 0u;
 }
 
 }  // namespace ipls

@@ -52,6 +52,27 @@ struct Model {
   uint64_t split[128];
 };
 
+// Exact bucket thresholds of a linear model and a two-level index over them
+// (grid-level subproblems).  thr[j] (j = 1..nb-1) is the smallest
+// totalOrder key whose bucket under the binary64 model is at least j, so the
+// bucket of a key u is the number of thresholds <= u.  Float keys: l1 is
+// indexed by the key's sign and exponent (one entry per binade between thr[1]
+// and thr[nb-1]); an entry is either a constant bucket or, with bit 15 set,
+// (m << 11 | offset) for 2^m cells of l2 indexed by the top m mantissa bits,
+// each cell holding the bucket at its start.  Integer keys: one entry whose
+// cells are (u - thr[1]) >> ishift.
+constexpr int kL1Max = 4096;
+constexpr int kL2Max = 2048;
+struct ThrTable {
+  uint64_t thr[kMaxK + 1];
+  uint16_t l1[kL1Max];
+  uint8_t l2[kL2Max];
+  int32_t ok;       // 1: use the tables; 0: classify with the model
+  int32_t e_lo;     // coarse index of l1[0]
+  int32_t n_l1;
+  int32_t ishift;   // integer keys: cell shift
+};
+
 // A grid-level subproblem.
 struct Sub {
   int64_t off;     // first key in the whole array
@@ -118,6 +139,22 @@ struct RunStatus {
   int64_t resident_fallback;
   int64_t resident_keys;
   int64_t resident_groups;
+  int64_t slow_tasks;
+};
+
+// A range of the user buffer that needs the in-block recursion (a bucket
+// above the cutoff, or a task whose model is the splitter tree or made no
+// progress): keys [off, off+n) form one subproblem at `level`.
+struct SlowTask {
+  int64_t off;
+  int32_t n;
+  int32_t level;
+};
+
+// Counters of the slow list (zeroed before each tail launch).
+struct SlowCtl {
+  int32_t count;
+  uint32_t ticket;
 };
 
 // Per-level device arrays (all device pointers).
@@ -129,6 +166,7 @@ struct LevelArgs {
   int64_t root_sample;
   uint64_t seed;
   int exact_only;
+  int use_tables;        // build and use the exact threshold index
   int64_t spin_limit;
   uint32_t epoch;        // look-back epoch of this level's scatter
   int level;
@@ -137,6 +175,7 @@ struct LevelArgs {
   int32_t nsub;
   Sub* subs;
   Model* models;
+  ThrTable* tabs;        // [nsub]
   uint64_t* counts;      // [nsub][256]
   int64_t* bases;        // [nsub][257]
   int32_t* tile2sub;     // this level's tiles
@@ -144,6 +183,7 @@ struct LevelArgs {
   int32_t* chunk2sub;    // this level's tile chunks
   int64_t nchunks;
   uint32_t* tile_off;    // [ntiles][256]: tile histogram, then offsets in bucket
+  uint8_t* bids;         // bucket of every key of this level (by key position)
   unsigned long long* status;  // look-back words [nchunks][256]
   LevelCtl* ctl;
   RunStatus* run;
@@ -178,6 +218,9 @@ struct ResidentArgs {
   const int32_t* fit_list;
   int32_t nfit;
   LinModel* tail_models;           // indexed by Group::fit
+  SlowTask* slow;                  // slow list (capacity slow_cap)
+  int32_t slow_cap;
+  SlowCtl* slow_ctl;
   RunStatus* run;
   struct iplsTraceRecDev* trace;   // block-resident passes append here
   int64_t trace_cap;
@@ -203,6 +246,7 @@ cudaError_t launch_tilescan(const LevelArgs& a, cudaStream_t s, int grid);
 cudaError_t launch_scatter(const LevelArgs& a, cudaStream_t s, int sms);
 cudaError_t launch_tail_fit(const ResidentArgs& a, cudaStream_t s);
 cudaError_t launch_resident(const ResidentArgs& a, cudaStream_t s);
+cudaError_t launch_slow(const ResidentArgs& a, cudaStream_t s, int sms);
 cudaError_t launch_init_segments(const int64_t* offsets, int64_t nseg, int rmax, int cutoff,
                                  int resident_ok, LevelCtl* ctl, Sub* subs, int32_t sub_cap,
                                  int32_t* tile2sub, int64_t tile_cap, int32_t* chunk2sub,

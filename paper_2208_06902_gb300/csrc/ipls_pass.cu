@@ -3,9 +3,10 @@
 //   k_fit      one block per subproblem: sample alpha*k-1 keys, sort them,
 //              fit FMCD (Ch.3 listing) or the splitter tree, zero counts.
 //   k_hist     every tile of every subproblem: classify each key with the
-//              model (Ch.3 model equation), per-warp shared histograms; the
-//              tile's histogram goes to memory, the subproblem's totals are
-//              accumulated with one atomic per bucket per block.
+//              model (Ch.3 model equation) and store its bucket id, per-warp
+//              shared histograms; the tile's histogram goes to memory, the
+//              subproblem's totals are accumulated with one atomic per
+//              bucket per block.
 //   k_check    no-progress rule: a linear pass that puts every key into one
 //              bucket is redone with the splitter tree from the same sample.
 //   k_scan     exclusive scan of the bucket counts -> bucket bases; children
@@ -15,8 +16,9 @@
 //              per bucket, over its tiles: chunks of kChunkTiles tiles in
 //              ticket order, each chunk's prefix found by decoupled look-back
 //              over the chunks before it.
-//   k_scatter  every tile: classify again, rank each key stably inside the
-//              tile (warp match + per-warp counters), stage the tile in
+//   k_scatter  every tile: read the bucket ids k_hist stored, rank each key
+//              stably inside the tile (warp ballots + per-warp counters),
+//              stage the tile in
 //              bucket order in shared memory and write the bucket runs out
 //              with coalesced stores at bucket base + tile offset (Ch.2
 //              IPS4o: move every key into the region of its bucket).
@@ -49,6 +51,13 @@ __device__ __forceinline__ void copy_model(Model* dst, const Model* src) {
   for (int i = threadIdx.x; i < (int)(sizeof(Model) / 8); i += blockDim.x) d[i] = s[i];
 }
 
+// Copies a ThrTable between memories with all threads of the block.
+__device__ __forceinline__ void copy_table(ThrTable* dst, const ThrTable* src) {
+  const unsigned long long* s = reinterpret_cast<const unsigned long long*>(src);
+  unsigned long long* d = reinterpret_cast<unsigned long long*>(dst);
+  for (int i = threadIdx.x; i < (int)(sizeof(ThrTable) / 8); i += blockDim.x) d[i] = s[i];
+}
+
 // Gathers and sorts the sample of one subproblem (all threads).
 template <class K>
 __device__ int gather_sorted_sample(const LevelArgs& a, const Sub& sub,
@@ -71,12 +80,20 @@ __global__ void __launch_bounds__(kFitThreads) k_fit(LevelArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ Model sm;
   __shared__ FitShared fs;
+  __shared__ ThrTable tab;
+  __shared__ int scan_tmp[kL1Max];
   Ord* so = reinterpret_cast<Ord*>(smem);
   const int s = blockIdx.x;
   const Sub sub = a.subs[s];
   const int S = gather_sorted_sample<K>(a, sub, so);
   fit_model<BlockG, K>(so, S, a.k, &sm, fs);
   copy_model(&a.models[s], &sm);
+  if (sm.l.kind == kLinear && a.use_tables) {
+    build_thr_table<K>(sm.l, &tab, scan_tmp);
+    copy_table(&a.tabs[s], &tab);
+  } else if (threadIdx.x == 0) {
+    a.tabs[s].ok = 0;
+  }
   for (int b = threadIdx.x; b < kMaxK; b += blockDim.x) a.counts[(size_t)s * kMaxK + b] = 0;
   if (threadIdx.x == 0) {
     a.subs[s].flags = 0;
@@ -91,6 +108,7 @@ __global__ void __launch_bounds__(kPassThreads, 4) k_hist(LevelArgs a, int rehis
   using Bits = typename T::Bits;
   constexpr int kChunk = 8;  // keys per thread in flight
   __shared__ Model sm;
+  __shared__ ThrTable tab;
   __shared__ unsigned int hist[kWarps][kMaxK];
   __shared__ unsigned int acc[kMaxK];
   const int warp = threadIdx.x >> 5;
@@ -99,6 +117,7 @@ __global__ void __launch_bounds__(kPassThreads, 4) k_hist(LevelArgs a, int rehis
   const int64_t nt = a.ntiles;
   const int64_t t0 = nt * blockIdx.x / gridDim.x, t1 = nt * (blockIdx.x + 1) / gridDim.x;
   int cur = -1;
+  bool use_tab = false;
   Classifier<K> cls;
   for (int64_t t = t0; t < t1; ++t) {
     const int s = a.tile2sub[t];
@@ -112,9 +131,13 @@ __global__ void __launch_bounds__(kPassThreads, 4) k_hist(LevelArgs a, int rehis
       }
       __syncthreads();
       copy_model(&sm, &a.models[s]);
+      if (threadIdx.x == 0) tab.ok = 0;
+      __syncthreads();
+      if (a.use_tables && a.tabs[s].ok) copy_table(&tab, &a.tabs[s]);
       cur = s;
       __syncthreads();
       cls.load(sm, a.exact_only);
+      use_tab = a.use_tables && sm.l.kind == kLinear && tab.ok;
     }
     const Sub sub = a.subs[s];
     if (rehist_only && !(sub.flags & kRehist)) continue;
@@ -130,10 +153,27 @@ __global__ void __launch_bounds__(kPassThreads, 4) k_hist(LevelArgs a, int rehis
         const int i = c0 + j * kPassThreads + threadIdx.x;
         v[j] = (i < tn) ? src[i] : Bits(0);
       }
+      uint8_t* ids = a.bids + base;
+      if (use_tab) {
 #pragma unroll
-      for (int j = 0; j < kChunk; ++j) {
-        const int i = c0 + j * kPassThreads + threadIdx.x;
-        if (i < tn) atomicAdd(&hist[warp][cls.bucket(v[j])], 1u);
+        for (int j = 0; j < kChunk; ++j) {
+          const int i = c0 + j * kPassThreads + threadIdx.x;
+          if (i < tn) {
+            const int bk = table_bucket<K>(T::ord(v[j]), tab, sm.l.nb);
+            ids[i] = (uint8_t)bk;
+            atomicAdd(&hist[warp][bk], 1u);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < kChunk; ++j) {
+          const int i = c0 + j * kPassThreads + threadIdx.x;
+          if (i < tn) {
+            const int bk = cls.bucket(v[j]);
+            ids[i] = (uint8_t)bk;
+            atomicAdd(&hist[warp][bk], 1u);
+          }
+        }
       }
     }
     __syncthreads();
@@ -179,6 +219,7 @@ __global__ void __launch_bounds__(kFitThreads) k_check(LevelArgs a) {
   copy_model(&a.models[s], &sm);
   for (int b = threadIdx.x; b < kMaxK; b += blockDim.x) a.counts[(size_t)s * kMaxK + b] = 0;
   if (threadIdx.x == 0) {
+    a.tabs[s].ok = 0;
     a.subs[s].flags |= kRehist;
     atomicAdd(&a.ctl->nrehist, 1);
   }
@@ -399,7 +440,6 @@ struct ScatterSmem {
   int tile_start[kMaxK];
   int tile_tot[kMaxK];
   long long gbase[kMaxK];
-  Model model;
 };
 
 template <class K>
@@ -409,7 +449,6 @@ __global__ void __launch_bounds__(kPassThreads, 3) k_scatter(LevelArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ScatterSmem<K>& sh = *reinterpret_cast<ScatterSmem<K>*>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  Classifier<K> cls;
   Bits* dst_base[2] = {reinterpret_cast<Bits*>(a.buf[0]), reinterpret_cast<Bits*>(a.buf[1])};
   const int64_t nt = a.ntiles;
   const int64_t t0 = nt * blockIdx.x / gridDim.x, t1 = nt * (blockIdx.x + 1) / gridDim.x;
@@ -419,31 +458,27 @@ __global__ void __launch_bounds__(kPassThreads, 3) k_scatter(LevelArgs a) {
     const Sub sub = a.subs[s];
     if (sub.flags & kSkipScatter) continue;
     __syncthreads();
-    if (s != cur) {
-      copy_model(&sh.model, &a.models[s]);
-      cur = s;
-      __syncthreads();
-    }
-    cls.load(sh.model, a.exact_only);
+    (void)cur;
     for (int i = threadIdx.x; i < kWarps * kMaxK; i += blockDim.x) (&sh.wcnt[0][0])[i] = 0;
     const int64_t ti = t - sub.tile0;
     const int64_t kbase = sub.off + ti * kTile;
     const int64_t rem = sub.n - ti * kTile;
     const int tn = rem < kTile ? (int)rem : kTile;
     const Bits* src = reinterpret_cast<const Bits*>(a.buf[sub.buf]) + kbase;
+    const uint8_t* ids = a.bids + kbase;
     Bits v[kKPT];
-    unsigned int br[kKPT];   // bucket << 16 | rank within warp
+    unsigned int br[kKPT];   // bucket id, then bucket << 16 | rank within warp
 #pragma unroll
     for (int j = 0; j < kKPT; ++j) {
       const int i = warp * kKPW + j * 32 + lane;
       v[j] = (i < tn) ? src[i] : Bits(0);
+      br[j] = (i < tn) ? (unsigned)ids[i] : (unsigned)kMaxK;
     }
     __syncthreads();  // wcnt zeroed
 #pragma unroll
     for (int j = 0; j < kKPT; ++j) {
-      const int i = warp * kKPW + j * 32 + lane;
-      const int bk = (i < tn) ? cls.bucket(v[j]) : kMaxK;
-      const unsigned peers = __match_any_sync(0xffffffffu, bk);
+      const int bk = (int)br[j];
+      const unsigned peers = same_bucket_lanes(bk, bk < kMaxK);
       const int lt = __popc(peers & lanemask_lt());
       const int leader = __ffs(peers) - 1;
       const int basec = (bk < kMaxK) ? sh.wcnt[warp][bk] : 0;

@@ -5,18 +5,21 @@
 //   k_tail_fit   one warp per subproblem: sample alpha*k-1 keys, sort them,
 //                fit FMCD -- many fits in flight per SM hide the latency of
 //                the sorting network and of the binary64 steps.
-//   k_resident   one block per task.  A fitted subproblem is read from HBM
+//   k_tail       one block per task.  A fitted subproblem is read from HBM
 //                once, classified with its model, ranked stably per bucket
 //                and placed into shared memory in bucket order; each bucket
-//                of at most `cutoff` keys is then base-cased by rank
-//                counting (the position of a key inside its bucket is the
-//                number of smaller keys, ties broken by position), and the
-//                sorted subproblem is written to the user buffer once.  A
-//                task of small children (consecutive buckets or segments of
-//                at most `cutoff` keys) goes straight to the base case.
-//                Rare cases -- a bucket above the cutoff, the splitter tree,
-//                a pass without progress -- continue the recursion inside
-//                the block (sample, sort, fit, classify, stable scatter).
+//                of at most `cutoff` keys is then base-cased by rank counting
+//                (the position of a key inside its bucket is the number of
+//                smaller keys, ties broken by position), and the subproblem
+//                is written to the user buffer once.  A task of small children
+//                (consecutive buckets or segments of at most `cutoff` keys)
+//                goes straight to the base case.  Buckets above the cutoff,
+//                tasks whose model is the splitter tree and passes without
+//                progress are written out in place and queued on the slow
+//                list.
+//   k_slow       persistent blocks drain the slow list: each range recurses
+//                inside one block (sample, sort, fit, classify, stable
+//                scatter, base case) and is written back in place.
 //
 // The paper's base case is SkaSort for n <= 2^12 (Ch.4); any exact sort
 // gives the same, unique result.
@@ -57,23 +60,20 @@ __global__ void __launch_bounds__(kFitWarps * 32) k_tail_fit(ResidentArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// k_resident
+// In-block recursion (the slow path)
 // ---------------------------------------------------------------------------
 template <class K>
 struct ResSmem {
   typename KT<K>::Ord keys[kResidentMax];
-  unsigned char seg[kResidentMax];   // segment (bucket or child) of each position
   union {
     struct {
       typename KT<K>::Ord samp[kResidentSample];
       unsigned short wcnt[kRW][kMaxK];
       unsigned long long tasks[kResidentTasks];  // small list from 0 up, stack from the top
     } s;
-    unsigned short dest[kResidentMax];           // final position inside the task
   } u;
   int bstart[kMaxK + 1];
   int tot[kMaxK];
-  int segb[kMaxK + 1];               // segment bounds for the base case
   Model model;
   FitShared fs;
   int nsmall, nstack, redo, err, slow_all;
@@ -224,7 +224,7 @@ __device__ void resident_pass(ResSmem<K>& sh, const ResidentArgs& a, int64_t gof
         const bool ok = i < c;
         v[j] = ok ? sh.keys[s0 + i] : (Ord)0;
         const int bk = ok ? cls.bucket(T::unord(v[j])) : kMaxK;
-        const unsigned peers = __match_any_sync(0xffffffffu, bk);
+        const unsigned peers = same_bucket_lanes(bk, bk < kMaxK);
         const int lt = __popc(peers & lanemask_lt());
         const int leader = __ffs(peers) - 1;
         const int basec = (bk < kMaxK) ? sh.u.s.wcnt[warp][bk] : 0;
@@ -295,29 +295,80 @@ __device__ void run_stack(ResSmem<K>& sh, const ResidentArgs& a, int64_t goff) {
 }
 
 template <class K>
-__global__ void __launch_bounds__(kResidentThreads, 2) k_resident(ResidentArgs a) {
+__global__ void __launch_bounds__(kResidentThreads, 2) k_slow(ResidentArgs a) {
+  using T = KT<K>;
+  using Bits = typename T::Bits;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ResSmem<K>& sh = *reinterpret_cast<ResSmem<K>*>(smem_raw);
+  __shared__ int s_i;
+  Bits* keys = reinterpret_cast<Bits*>(a.buf[0]);
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_i = (int)atomicAdd(&a.slow_ctl->ticket, 1u);
+    __syncthreads();
+    const int i = s_i;
+    if (i >= a.slow_ctl->count || i >= a.slow_cap) break;
+    const SlowTask st = a.slow[i];
+    Bits* src = keys + st.off;
+    for (int p = threadIdx.x; p < st.n; p += blockDim.x) sh.keys[p] = T::ord(src[p]);
+    if (threadIdx.x == 0) {
+      sh.nsmall = 0;
+      sh.err = 0;
+      sh.nstack = 1;
+      sh.u.s.tasks[kResidentTasks - 1] = enc_task(0, st.n, st.level);
+    }
+    __syncthreads();
+    run_stack<K>(sh, a, st.off);
+    for (int p = threadIdx.x; p < st.n; p += blockDim.x) src[p] = T::unord(sh.keys[p]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_tail
+// ---------------------------------------------------------------------------
+template <class K>
+struct TailSmem {
+  typename KT<K>::Ord keys[kResidentMax];
+  unsigned char seg[kResidentMax];   // segment (bucket or child) of each position
+  unsigned short wcnt[kRW][kMaxK];
+  int bstart[kMaxK + 1];
+  int segb[kMaxK + 1];
+  int tot[kMaxK];
+  LinModel lin;
+  int slow_all;
+  long long rec;
+};
+
+__device__ __forceinline__ void push_slow(const ResidentArgs& a, int64_t off, int n, int level) {
+  const int i = atomicAdd(&a.slow_ctl->count, 1);
+  if (i < a.slow_cap) a.slow[i] = SlowTask{off, n, level};
+  else atomicExch(&a.run->error, -6);
+}
+
+template <class K>
+__global__ void __launch_bounds__(kResidentThreads, 2) k_tail(ResidentArgs a) {
   using T = KT<K>;
   using Bits = typename T::Bits;
   using Ord = typename T::Ord;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  ResSmem<K>& sh = *reinterpret_cast<ResSmem<K>*>(smem_raw);
+  TailSmem<K>& sh = *reinterpret_cast<TailSmem<K>*>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const Group g = a.groups[blockIdx.x];
   const int n = g.n;
   const Bits* src = reinterpret_cast<const Bits*>(a.buf[g.buf]) + g.off;
-  if (threadIdx.x == 0) { sh.nsmall = 0; sh.nstack = 0; sh.err = 0; sh.slow_all = 0; }
-  bool fitted = false;
+  Bits* dst = reinterpret_cast<Bits*>(a.buf[0]) + g.off;
+  int nseg;
   if (g.fit >= 0) {
-    // ---- fast pass with the model fitted by k_tail_fit -------------------
     if (threadIdx.x < (int)(sizeof(LinModel) / 8))
-      reinterpret_cast<unsigned long long*>(&sh.model.l)[threadIdx.x] =
+      reinterpret_cast<unsigned long long*>(&sh.lin)[threadIdx.x] =
           reinterpret_cast<const unsigned long long*>(&a.tail_models[g.fit])[threadIdx.x];
-    for (int i = threadIdx.x; i < kRW * kMaxK; i += blockDim.x) (&sh.u.s.wcnt[0][0])[i] = 0;
+    for (int i = threadIdx.x; i < kRW * kMaxK; i += blockDim.x) (&sh.wcnt[0][0])[i] = 0;
+    if (threadIdx.x == 0) sh.slow_all = 0;
     __syncthreads();
-    fitted = sh.model.l.kind == kLinear;
-    if (fitted) {
+    bool slow = sh.lin.kind != kLinear;
+    if (!slow) {
       Classifier<K> cls;
-      cls.load(sh.model.l, a.exact_only);
+      cls.load(sh.lin, a.exact_only);
       const int chunk = ((n + kRW * 32 - 1) / (kRW * 32)) * 32;
       const int steps = chunk / 32;
       Bits v[kRKPT];
@@ -332,78 +383,114 @@ __global__ void __launch_bounds__(kResidentThreads, 2) k_resident(ResidentArgs a
         if (j < steps) {
           const int i = warp * chunk + j * 32 + lane;
           const int bk = (i < n) ? cls.bucket(v[j]) : kMaxK;
-          const unsigned peers = __match_any_sync(0xffffffffu, bk);
+          const unsigned peers = same_bucket_lanes(bk, bk < kMaxK);
           const int lt = __popc(peers & lanemask_lt());
           const int leader = __ffs(peers) - 1;
-          const int basec = (bk < kMaxK) ? sh.u.s.wcnt[warp][bk] : 0;
+          const int basec = (bk < kMaxK) ? sh.wcnt[warp][bk] : 0;
           br[j] = ((unsigned)bk << 16) | (unsigned)(basec + lt);
           __syncwarp();
-          if (lane == leader && bk < kMaxK) sh.u.s.wcnt[warp][bk] = (unsigned short)(basec + __popc(peers));
+          if (lane == leader && bk < kMaxK) sh.wcnt[warp][bk] = (unsigned short)(basec + __popc(peers));
           __syncwarp();
         }
       }
       __syncthreads();
-      warp_counts_to_offsets(sh);
-      if (threadIdx.x < kMaxK && sh.tot[threadIdx.x] == n) sh.slow_all = 1;  // no progress
+      if (threadIdx.x < kMaxK) {
+        const int b = threadIdx.x;
+        int run = 0;
+#pragma unroll
+        for (int w = 0; w < kRW; ++w) {
+          const int x = sh.wcnt[w][b];
+          sh.wcnt[w][b] = (unsigned short)run;
+          run += x;
+        }
+        sh.tot[b] = run;
+        if (run == n) sh.slow_all = 1;  // no progress: the splitter tree decides
+      }
       __syncthreads();
-      if (!sh.slow_all) {
-        scan_totals(sh);
+      slow = sh.slow_all != 0;
+      if (!slow) {
+        if (warp == 0) {
+          int loc[8];
+          int sum = 0;
+#pragma unroll
+          for (int q = 0; q < 8; ++q) { loc[q] = sh.tot[lane * 8 + q]; sum += loc[q]; }
+          int incl = sum;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const int x = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += x;
+          }
+          int run = incl - sum;
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            sh.bstart[lane * 8 + q] = run;
+            sh.segb[lane * 8 + q] = run;
+            run += loc[q];
+          }
+          if (lane == 31) { sh.bstart[kMaxK] = run; sh.segb[kMaxK] = run; }
+        }
+        __syncthreads();
 #pragma unroll
         for (int j = 0; j < kRKPT; ++j) {
           if (j < steps) {
             const int bk = (int)(br[j] >> 16);
             if (bk < kMaxK) {
-              const int p = sh.bstart[bk] + sh.u.s.wcnt[warp][bk] + (int)(br[j] & 0xFFFF);
+              const int p = sh.bstart[bk] + sh.wcnt[warp][bk] + (int)(br[j] & 0xFFFF);
               sh.keys[p] = T::ord(v[j]);
               sh.seg[p] = (unsigned char)bk;
             }
           }
         }
-        for (int q = threadIdx.x; q <= kMaxK; q += blockDim.x) sh.segb[q] = sh.bstart[q];
+        // trace record of this pass (the model was fitted by k_tail_fit)
+        if (a.trace_cap > 0) {
+          if (threadIdx.x == 0) {
+            sh.rec = (long long)atomicAdd((unsigned long long*)&a.run->trace_count, 1ULL);
+            if (sh.rec < a.trace_cap) {
+              iplsTraceRecDev& r = a.trace[sh.rec];
+              r.off = g.off; r.n = n; r.level = g.level; r.kind = sh.lin.kind;
+              r.capped = sh.lin.capped; r.nbuckets = sh.lin.nb; r.S = sh.lin.S; r.D = sh.lin.D;
+              r.A = sh.lin.A; r.Bc = sh.lin.Bc; r.ud = sh.lin.ud; r.xlo_bits = sh.lin.xlo_bits;
+              r.nsplit = 0; r.where = 1;
+            }
+          }
+          __syncthreads();
+          if (sh.rec < a.trace_cap && threadIdx.x < kMaxK)
+            a.trace[sh.rec].counts[threadIdx.x] = (threadIdx.x < sh.lin.nb) ? sh.tot[threadIdx.x] : 0;
+        }
+        // buckets above the cutoff continue in the slow kernel
+        if (threadIdx.x < sh.lin.nb && sh.tot[threadIdx.x] > a.cutoff)
+          push_slow(a, g.off + sh.bstart[threadIdx.x], sh.tot[threadIdx.x], g.level + 1);
         __syncthreads();
-        if (threadIdx.x == 0) sh.model.nsplit = 0;
-        trace_pass(sh, a, g.off, n, g.level, sh.model);
-        if (threadIdx.x == 0) atomicAdd((unsigned long long*)&a.run->resident_passes, 1ULL);
-        // buckets above the cutoff continue the recursion in the block
-        if (threadIdx.x < sh.model.l.nb && sh.tot[threadIdx.x] > a.cutoff)
-          push_child(sh, sh.bstart[threadIdx.x], sh.tot[threadIdx.x], g.level + 1, a.cutoff);
-        __syncthreads();
-      } else {
-        fitted = false;
       }
     }
-  }
-  if (!fitted) {
+    if (slow) {
+      // the whole task recurses in the slow kernel (the in-block fit draws the
+      // same sample and makes the same model), from the user buffer
+      if (g.buf != 0)
+        for (int p = threadIdx.x; p < n; p += blockDim.x) dst[p] = src[p];
+      if (threadIdx.x == 0) push_slow(a, g.off, n, g.level);
+      if (threadIdx.x == 0) atomicAdd((unsigned long long*)&a.run->resident_groups, 1ULL);
+      return;
+    }
+    nseg = sh.lin.nb;
+  } else {
     for (int i = threadIdx.x; i < n; i += blockDim.x) sh.keys[i] = T::ord(src[i]);
-    if (g.fit >= 0) {
-      // the splitter tree or the no-progress rule: the whole task recurses in
-      // the block (the in-block fit reproduces the same sample and model)
-      for (int i = threadIdx.x; i < n; i += blockDim.x) sh.seg[i] = 0;
-      if (threadIdx.x == 0) {
-        sh.segb[0] = 0;
-        sh.segb[1] = n;
-        sh.nstack = 1;
-        sh.u.s.tasks[kResidentTasks - 1] = enc_task(0, n, g.level);
-      }
-    } else {
-      // consecutive small children: segment ids and bounds
-      const int64_t b0 = g.bounds[0];
-      for (int q = threadIdx.x; q <= g.nchild; q += blockDim.x) sh.segb[q] = (int)(g.bounds[q] - b0);
-      __syncthreads();
-      for (int q = warp; q < g.nchild; q += kRW)
-        for (int i = sh.segb[q] + lane; i < sh.segb[q + 1]; i += 32) sh.seg[i] = (unsigned char)q;
-    }
+    const int64_t b0 = g.bounds[0];
+    for (int q = threadIdx.x; q <= g.nchild; q += blockDim.x) sh.segb[q] = (int)(g.bounds[q] - b0);
     __syncthreads();
+    for (int q = warp; q < g.nchild; q += kRW)
+      for (int i = sh.segb[q] + lane; i < sh.segb[q + 1]; i += 32) sh.seg[i] = (unsigned char)q;
+    nseg = g.nchild;
   }
-  run_stack<K>(sh, a, g.off);
-  // ---- base case by rank counting for every segment of <= cutoff keys -----
+  __syncthreads();
+  // ---- base case: rank counting inside every segment of <= cutoff keys ----
   const int cutoff = a.cutoff;
   for (int p = threadIdx.x; p < n; p += blockDim.x) {
     const int q = sh.seg[p];
     const int s = sh.segb[q], e = sh.segb[q + 1];
+    const Ord kp = sh.keys[p];
     int d = p;
     if (e - s <= cutoff) {
-      const Ord kp = sh.keys[p];
       int cnt = 0;
       for (int r = s; r < e; ++r) {
         const Ord kr = sh.keys[r];
@@ -411,11 +498,8 @@ __global__ void __launch_bounds__(kResidentThreads, 2) k_resident(ResidentArgs a
       }
       d = s + cnt;
     }
-    sh.u.dest[p] = (unsigned short)d;
+    dst[d] = T::unord(kp);
   }
-  __syncthreads();
-  Bits* dst = reinterpret_cast<Bits*>(a.buf[0]) + g.off;
-  for (int p = threadIdx.x; p < n; p += blockDim.x) dst[sh.u.dest[p]] = T::unord(sh.keys[p]);
   if (threadIdx.x == 0) {
     atomicAdd((unsigned long long*)&a.run->resident_keys, (unsigned long long)n);
     atomicAdd((unsigned long long*)&a.run->resident_groups, 1ULL);
@@ -456,9 +540,24 @@ cudaError_t launch_resident(const ResidentArgs& a, cudaStream_t s) {
   if (a.ngroups <= 0) return cudaSuccess;
   return by_dtype_r(a.dtype, [&](auto* tag) {
     using K = std::remove_pointer_t<decltype(tag)>;
+    const size_t smem = sizeof(TailSmem<K>);
+    cudaFuncSetAttribute(k_tail<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_tail<K><<<a.ngroups, kResidentThreads, smem, s>>>(a);
+    return cudaGetLastError();
+  });
+}
+
+cudaError_t launch_slow(const ResidentArgs& a, cudaStream_t s, int sms) {
+  return by_dtype_r(a.dtype, [&](auto* tag) {
+    using K = std::remove_pointer_t<decltype(tag)>;
     const size_t smem = sizeof(ResSmem<K>);
-    cudaFuncSetAttribute(k_resident<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_resident<K><<<a.ngroups, kResidentThreads, smem, s>>>(a);
+    cudaFuncSetAttribute(k_slow<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_slow<K>, kResidentThreads, smem) != cudaSuccess || per < 1) {
+      cudaGetLastError();
+      per = 1;
+    }
+    k_slow<K><<<per * sms, kResidentThreads, smem, s>>>(a);
     return cudaGetLastError();
   });
 }

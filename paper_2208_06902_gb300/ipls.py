@@ -25,7 +25,9 @@ class iplsConfig(ctypes.Structure):
                 ("sync", ctypes.c_int32), ("exact_only", ctypes.c_int32),
                 ("spin_limit", ctypes.c_int64), ("trace_cap", ctypes.c_int64),
                 ("budget_bytes", ctypes.c_int64), ("profile", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 7)]
+                ("flags", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+
+FLAG_THRESHOLD_INDEX = 1
 
 
 class iplsKernelStat(ctypes.Structure):
@@ -208,7 +210,7 @@ class Context:
 
     def __init__(self, *, k: int = 256, cutoff: int = 32, root_sample: int = 0, seed: int = 0,
                  exact_only: bool = False, trace_cap: int = 0, spin_limit: int | None = None,
-                 stream=None, budget_bytes: int = 0, profile: bool = False):
+                 stream=None, budget_bytes: int = 0, profile: bool = False, flags: int = 0):
         import torch
         cfg = iplsDefaultConfig()
         cfg.k, cfg.cutoff, cfg.root_sample, cfg.seed = k, cutoff, root_sample, seed
@@ -216,6 +218,7 @@ class Context:
         cfg.trace_cap = trace_cap
         cfg.budget_bytes = budget_bytes
         cfg.profile = 1 if profile else 0
+        cfg.flags = flags
         if spin_limit is not None:
             cfg.spin_limit = spin_limit
         s = stream if stream is not None else torch.cuda.current_stream()
