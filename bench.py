@@ -2,7 +2,7 @@
 """Throughput of the GB300 learned sort (IPLS learned partitioning pass).
 
 Workload (one step): sort one array of 2^28 float64 keys with the whole IPLS
-recursion (k = 256, alpha*k-1 samples, cutoff 32).  The K timed steps cycle
+recursion (k = 256, alpha*k-1 samples, base-case cutoff 256).  The K timed steps cycle
 through eight seeded synthetic distributions (Normal(0,1), LogNormal(0,0.5),
 Exponential(2), 5-Gaussian mixture, Zipf(0.75), root-dups, two-dups,
 eight-dups) that stand in for the paper's synthetic benchmark datasets.
@@ -45,15 +45,23 @@ UNIT = "Gkeys/s"
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=8)
+    p.add_argument("--steps", type=int, default=16)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--log2n", type=int, default=28)
-    p.add_argument("--cutoff", type=int, default=32)
+    p.add_argument("--cutoff", type=int, default=256)
     p.add_argument("--e2e-steps", type=int, default=4)
-    p.add_argument("--cpu-sample-log2", type=int, default=23)
+    p.add_argument("--cpu-sample-log2", type=int, default=24)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-torch-sort", action="store_true")
+    p.add_argument("--dists", default=",".join(DISTS),
+                   help="comma-separated subset of the distributions (profiling runs)")
+    p.add_argument("--profile-stats", metavar="JSON",
+                   help="profiling run: sort W+K arrays, write the per-kernel launches and "
+                        "algorithmic bytes of ALL of them to JSON, print no bench line")
+    p.add_argument("--ingest-ncu", nargs=2, metavar=("CSV", "STATS_JSON"),
+                   help="write profiles/ncu_traffic.json from an ncu --csv launch list with "
+                        "dram__bytes_{read,write}.sum of a --profile-stats run and its JSON")
     return p.parse_args()
 
 
@@ -83,9 +91,11 @@ def source_digest() -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel: str, launch_bytes_scale: float):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, or
-    None when the summary is missing or the kernel sources changed since."""
+def ncu_traffic(kernel: str, algorithmic_bytes_per_launch: float):
+    """DRAM bytes per launch of `kernel`: the ratio of measured DRAM bytes to
+    algorithmic bytes from the committed ncu capture, times this run's
+    algorithmic bytes per launch.  None when the capture is missing or the
+    kernel sources changed since it was taken."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as f:
@@ -97,11 +107,44 @@ def ncu_traffic(kernel: str, launch_bytes_scale: float):
     k = d.get("kernels", {}).get(kernel)
     if not k:
         return None
-    return float(k["dram_bytes_per_key"]) * launch_bytes_scale
+    return round(float(k["dram_per_algorithmic_byte"]) * algorithmic_bytes_per_launch)
+
+
+def ingest_ncu(csv_path: str, stats_path: str) -> int:
+    """Per-kernel ratio of measured DRAM bytes to algorithmic bytes, from an
+    ncu launch list (dram__bytes_read.sum, dram__bytes_write.sum per launch)
+    of a --profile-stats run and the algorithmic bytes that run reported."""
+    import csv
+    with open(stats_path) as f:
+        stats = json.load(f)
+    with open(csv_path) as f:
+        rows = list(csv.DictReader([ln for ln in f if ln.startswith('"')]))
+    scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}
+    dram = {}
+    for r in rows:
+        if r.get("Metric Name") not in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+            continue
+        name = r["Kernel Name"].split("(")[0].split("<")[0].replace("void ", "").split("::")[-1]
+        v = float(r["Metric Value"].replace(",", "")) * scale.get(r["Metric Unit"], 1)
+        dram[name] = dram.get(name, 0.0) + v
+    kernels = {}
+    for name, st in stats["kernels"].items():
+        # k_hist_redo launches the k_hist kernel; its bytes are counted with k_hist
+        if name == "k_hist_redo" or not st["bytes"] or name not in dram:
+            continue
+        kernels[name] = {"dram_bytes": dram[name], "algorithmic_bytes": st["bytes"],
+                         "dram_per_algorithmic_byte": round(dram[name] / st["bytes"], 4)}
+    out = {"source_digest": source_digest(), "case": stats["case"], "kernels": kernels}
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    with open(path, "w") as f:
+        json.dump(out, f, indent=1)
+        f.write("\n")
+    print(json.dumps(out))
+    return 0
 
 
 class ClockSampler:
-    """nvidia-smi clocks/throttle reasons sampled every 200 ms (one GPU)."""
+    """nvidia-smi clocks/throttle reasons sampled every 50 ms (one GPU)."""
 
     FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -114,11 +157,16 @@ class ClockSampler:
 
     def start(self):
         cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-               "-lms", "200"]
+               "-lms", "50"]
         try:
             self.proc = subprocess.Popen(cmd, stdout=self.file, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        # the timed region starts only once samples are flowing
+        t0 = time.time()
+        while time.time() - t0 < 5.0 and os.path.getsize(self.file.name) == 0:
+            time.sleep(0.02)
 
     def stop(self):
         if self.proc is not None:
@@ -151,23 +199,23 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-def make_inputs(n: int):
+def make_inputs(n: int, dists):
     import datagen
-    return {d: datagen.config2(d, n) for d in DISTS}
+    return {d: datagen.config2(d, n) for d in dists}
 
 
-def cpu_baseline(inputs, sample_log2: int):
+def cpu_baseline(inputs, sample_log2: int, cutoff: int):
     import oracle
     m = 1 << sample_log2
     keys = 0
     t0 = time.perf_counter()
-    for d in DISTS:
+    for d in inputs:
         x = inputs[d][:m]
-        oracle.sort(x, cutoff=32)
+        oracle.sort(x, cutoff=cutoff)
         keys += x.size
     dt = time.perf_counter() - t0
     return {"value": keys / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"first 2^{sample_log2} keys of each of the 8 arrays "
+            "sample": f"first 2^{sample_log2} keys of each of the {len(inputs)} arrays "
                       f"({keys} keys, serial C++ oracle, {dt:.1f} s)"}
 
 
@@ -223,14 +271,16 @@ def run_gb300(args):
     ipls.load()
     dev = torch.device("cuda", torch.cuda.current_device())
     n = 1 << args.log2n
-    inputs = make_inputs(n)
-    pristine = {d: torch.from_numpy(inputs[d].view(np.uint8)).to(dev) for d in DISTS}
+    dists = [d for d in args.dists.split(",") if d]
+    assert dists and all(d in DISTS for d in dists), f"unknown distribution in {args.dists}"
+    inputs = make_inputs(n, dists)
+    pristine = {d: torch.from_numpy(inputs[d].view(np.uint8)).to(dev) for d in dists}
     work = torch.empty(n * 8, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
     ctx = ipls.Context(cutoff=args.cutoff, profile=True, stream=stream)
 
     def step(i, timed):
-        d = DISTS[i % len(DISTS)]
+        d = dists[i % len(dists)]
         work.copy_(pristine[d])  # restores the input; 4 GB of traffic flushes L2
         if timed:
             a = torch.cuda.Event(enable_timing=True)
@@ -241,6 +291,21 @@ def run_gb300(args):
             return d, a, b
         ctx.sort_ptr(work.data_ptr(), n, ipls.F64)
         return d, None, None
+
+    if args.profile_stats:
+        # profiling run under ncu: every sort counts, nothing else runs
+        ctx.kernel_stats(reset=True)
+        for i in range(args.warmup + args.steps):
+            step(i, False)
+        ks = ctx.kernel_stats(reset=True)
+        with open(args.profile_stats, "w") as f:
+            json.dump({"case": f"2^{args.log2n} f64, {args.warmup + args.steps} sorts cycling "
+                               f"{','.join(dists)}, cutoff {args.cutoff}",
+                       "kernels": {k["name"]: {"launches": k["launches"], "bytes": k["bytes"],
+                                               "ms": k["total_ms"]} for k in ks if k["launches"]}},
+                      f, indent=1)
+        ctx.close()
+        return 0
 
     for i in range(args.warmup):
         step(i, False)
@@ -283,8 +348,7 @@ def run_gb300(args):
     peak, peak_kind = measured_peaks()
     achieved = dom["bytes"] / (dom["total_ms"] * 1e-3) / 1e9 if dom["total_ms"] > 0 else 0.0
     per_launch_bytes = dom["bytes"] / max(dom["launches"], 1)
-    traffic = ncu_traffic(dom["name"], per_launch_bytes / 8 / (2 if dom["name"] in (
-        "k_scatter", "k_resident") else 1))
+    traffic = ncu_traffic(dom["name"], per_launch_bytes)
     kernels = {k["name"]: {"launches": k["launches"], "ms": round(k["total_ms"], 3),
                            "GB/s": round(k["bytes"] / (k["total_ms"] * 1e-3) / 1e9, 1)
                            if k["total_ms"] > 0 and k["bytes"] else None}
@@ -297,7 +361,7 @@ def run_gb300(args):
         hv = host.numpy()
         e_ms = 0.0
         for i in range(args.e2e_steps + 1):
-            hv[:] = inputs[DISTS[i % len(DISTS)]].view(np.uint8)
+            hv[:] = inputs[dists[i % len(dists)]].view(np.uint8)
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
@@ -314,7 +378,7 @@ def run_gb300(args):
 
     torch_sort = None
     if not args.no_torch_sort:
-        x = pristine["normal"].view(torch.float64)
+        x = pristine[dists[0]].view(torch.float64)
         torch.sort(x)
         torch.cuda.synchronize()
         ts = []
@@ -330,7 +394,7 @@ def run_gb300(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(inputs, args.cpu_sample_log2)
+        cpu = cpu_baseline(inputs, args.cpu_sample_log2, args.cutoff)
 
     st = ctx.stats()
     if rank == 0:
@@ -340,10 +404,11 @@ def run_gb300(args):
             "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"IPLS sort of 2^{args.log2n} f64 keys, one step per array, "
-                                   "8 seeded distributions",
-                       "distributions": DISTS, "k": 256, "cutoff": args.cutoff,
+                                   f"{len(dists)} seeded distributions",
+                       "distributions": dists, "k": 256, "cutoff": args.cutoff,
                        "sample": "alpha*k-1 keys, alpha = 0.2*floor(log2 n)",
-                       "l2": "flushed: a 2 GiB input-restore copy runs between timed steps",
+                       "l2": f"flushed: a {n * 8 >> 20} MiB input-restore copy runs between "
+                             "timed steps (inputs larger than L2 from 2^25 keys)",
                        "parallelism": f"replicas x{world}"},
             "per_dist_gkeys_s": per_dist,
             "roofline": {"bound": "hbm", "kernel": dom["name"], "achieved": round(achieved, 1),
@@ -367,6 +432,8 @@ def run_gb300(args):
 
 def main():
     args = parse()
+    if args.ingest_ncu:
+        return ingest_ncu(*args.ingest_ncu)
     if args.impl == "reference":
         return run_reference(args)
     return run_gb300(args)
