@@ -191,6 +191,32 @@ iplsStatus iplsGetKernelStats(iplsCtx ctx, iplsKernelStat* out, int32_t cap, int
  * (requires cfg.trace_cap > 0) and sets *count to the records kept. */
 iplsStatus iplsGetTrace(iplsCtx ctx, iplsTraceRec* out, int64_t cap, int64_t* count);
 
+/* Sorts keys[0..n) in place (device pointer) WITHOUT allocating any memory:
+ * no cudaMalloc/cudaFree, no allocator callback, no context.  The paper has
+ * no counterpart; it exists for callers that cannot allocate when they sort
+ * (a framework pool holding the device's memory, a latency-critical loop in
+ * which cudaMalloc/cudaFree could synchronise the device, a pipeline that
+ * must not fail for lack of memory half-way).
+ *   - n <= 8192 (resident_rmax: 8192 for cfg->cutoff >= 7, 1024*(cutoff+1)
+ *     below); a larger n returns IPLS_ERR_ARG with a message naming the
+ *     limit.  One block runs the whole IPLS recursion (Ch.2 IPS4o recursion,
+ *     Ch.3 FMCD model, Ch.4 parameters) in shared memory; the result equals
+ *     iplsSort's on the same keys.
+ *   - cfg NULL = iplsDefaultConfig; k, cutoff, root_sample (<= 1024), seed
+ *     and exact_only are used.  stream = cudaStream_t (NULL = legacy
+ *     default stream).  The call waits for its stream and returns the
+ *     device status.
+ *   - Its only device scratch is a 256-byte status block in a file-scope
+ *     __device__ array of the library, cleared on the stream at the start
+ *     of every call.  The first call on each device looks up that array's
+ *     address (cudaGetSymbolAddress, with the device current); make it
+ *     before capturing the stream into a graph.
+ *   - The status block is shared by every call on a device: calls that
+ *     overlap in time (other threads or streams) race on it and must be
+ *     serialised by the caller. */
+iplsStatus iplsSortSmallNoAlloc(void* keys, int64_t n, iplsDtype dtype, const iplsConfig* cfg,
+                                void* stream);
+
 /* Message of the last failure on this thread ("" if none). */
 const char* iplsLastError(void);
 

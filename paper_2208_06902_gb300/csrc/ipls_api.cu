@@ -449,6 +449,10 @@ iplsStatus validate_cfg(const iplsConfig& c) {
 
 }  // namespace
 
+namespace ipls {
+void set_last_error(const char* msg) { g_last_error = msg; }
+}  // namespace ipls
+
 // ---------------------------------------------------------------------------
 // Segment lists for iplsSortSegmented: windows of 64 consecutive segments,
 // each packed greedily by one thread (same rule as k_scan's bucket packing).

@@ -247,6 +247,11 @@ cudaError_t launch_scatter(const LevelArgs& a, cudaStream_t s, int sms);
 cudaError_t launch_tail_fit(const ResidentArgs& a, cudaStream_t s);
 cudaError_t launch_resident(const ResidentArgs& a, cudaStream_t s);
 cudaError_t launch_slow(const ResidentArgs& a, cudaStream_t s, int sms);
+// One block sorts keys[t.off, t.off + t.n) (t.n <= resident_rmax(a.cutoff));
+// it reads and writes only the keys and *a.run.
+cudaError_t launch_slow_one(const ResidentArgs& a, const SlowTask& t, cudaStream_t s);
+// Sets the message iplsLastError() returns on this thread.
+void set_last_error(const char* msg);
 cudaError_t launch_init_segments(const int64_t* offsets, int64_t nseg, int rmax, int cutoff,
                                  int resident_ok, LevelCtl* ctl, Sub* subs, int32_t sub_cap,
                                  int32_t* tile2sub, int64_t tile_cap, int32_t* chunk2sub,

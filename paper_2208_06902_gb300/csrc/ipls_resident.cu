@@ -571,6 +571,43 @@ cudaError_t launch_fill(const Fill* fills, int32_t nfill, int dtype, void* keys,
   return cudaGetLastError();
 }
 
+// One range sorted by one block with the in-block recursion of k_slow, the
+// range passed by value instead of through the slow list: the only device
+// memory it touches besides the keys is a.run.
+template <class K>
+__global__ void __launch_bounds__(kResidentThreads, 1) k_slow_one(ResidentArgs a, SlowTask st) {
+  using T = KT<K>;
+  using Bits = typename T::Bits;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ResSmem<K>& sh = *reinterpret_cast<ResSmem<K>*>(smem_raw);
+  Bits* src = reinterpret_cast<Bits*>(a.buf[0]) + st.off;
+  for (int p = threadIdx.x; p < st.n; p += blockDim.x) sh.keys[p] = T::ord(src[p]);
+  if (threadIdx.x == 0) {
+    sh.nsmall = 0;
+    sh.err = 0;
+    sh.nstack = st.n > a.cutoff ? 1 : 0;
+    sh.u.s.tasks[kResidentTasks - 1] = enc_task(0, st.n, st.level);
+    if (st.n <= a.cutoff && st.n > 1) {
+      sh.nsmall = 1;
+      sh.u.s.tasks[0] = enc_task(0, st.n, st.level);
+    }
+  }
+  __syncthreads();
+  run_stack<K>(sh, a, st.off);
+  for (int p = threadIdx.x; p < st.n; p += blockDim.x) src[p] = T::unord(sh.keys[p]);
+}
+
+cudaError_t launch_slow_one(const ResidentArgs& a, const SlowTask& t, cudaStream_t s) {
+  return by_dtype_r(a.dtype, [&](auto* tag) {
+    using K = std::remove_pointer_t<decltype(tag)>;
+    const size_t smem = sizeof(ResSmem<K>);
+    cudaError_t e = cudaFuncSetAttribute(k_slow_one<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_slow_one<K><<<1, kResidentThreads, smem, s>>>(a, t);
+    return cudaGetLastError();
+  });
+}
+
 // Largest task a block can hold for this cutoff: every pending range of more
 // than `cutoff` keys must fit in half of the task array.
 int resident_rmax(int cutoff) {

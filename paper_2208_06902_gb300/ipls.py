@@ -83,6 +83,7 @@ def load(build_if_missing: bool = True):
     L.iplsSort.argtypes = [P, P, c.c_int64, c.c_int]
     L.iplsSortSegmented.argtypes = [P, P, P, c.c_int64, c.c_int]
     L.iplsSortHost.argtypes = [P, P, c.c_int64, c.c_int]
+    L.iplsSortSmallNoAlloc.argtypes = [P, c.c_int64, c.c_int, c.POINTER(iplsConfig), P]
     L.iplsGetKernelStats.argtypes = [P, c.POINTER(iplsKernelStat), c.c_int32,
                                      c.POINTER(c.c_int32), c.c_int32]
     L.iplsSubmit.argtypes = [P, P, c.c_int64, c.c_int, c.POINTER(c.c_uint64)]
@@ -139,6 +140,15 @@ def iplsScratchBytes(ctx: int | None, n: int, dtype: int) -> int:
 def iplsSort(ctx: int | None, keys_ptr: int, n: int, dtype: int) -> int:
     return _check(load().iplsSort(ctypes.c_void_p(ctx), ctypes.c_void_p(keys_ptr), n, dtype),
                   "iplsSort")
+
+
+def iplsSortSmallNoAlloc(keys_ptr: int, n: int, dtype: int, cfg: iplsConfig | None = None,
+                         stream: int = 0) -> int:
+    """Sorts at most 8192 device keys in place without allocating memory
+    (one block, the library's static status block as its only scratch)."""
+    return _check(load().iplsSortSmallNoAlloc(ctypes.c_void_p(keys_ptr), n, dtype,
+                                              ctypes.byref(cfg) if cfg is not None else None,
+                                              ctypes.c_void_p(stream)), "iplsSortSmallNoAlloc")
 
 
 def iplsSortSegmented(ctx: int | None, keys_ptr: int, offsets_ptr: int, nseg: int,
