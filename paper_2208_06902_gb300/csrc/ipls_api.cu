@@ -10,7 +10,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/ipls.h"
+#include "ipls.h"
 #include "ipls_device.cuh"
 
 namespace {
@@ -53,7 +53,7 @@ struct Slot {
   int64_t* bases = nullptr;      int64_t base_cap = 0;
   Group* groups = nullptr;       int64_t group_cap = 0;
   int32_t* fit_list = nullptr;   int64_t fit_cap = 0;
-  LinModel* tails = nullptr;     int64_t tail_cap = 0;
+  TailModel* tails = nullptr;    int64_t tail_cap = 0;
   Fill* fills = nullptr;         int64_t fill_cap = 0;
 };
 
@@ -603,7 +603,7 @@ iplsStatus iplsDestroy(iplsCtx c) {
     dev_free(c, s.bases, s.base_cap * sizeof(int64_t));
     dev_free(c, s.groups, s.group_cap * sizeof(Group));
     dev_free(c, s.fit_list, s.fit_cap * sizeof(int32_t));
-    dev_free(c, s.tails, s.tail_cap * sizeof(LinModel));
+    dev_free(c, s.tails, s.tail_cap * sizeof(TailModel));
     dev_free(c, s.fills, s.fill_cap * sizeof(Fill));
   }
   dev_free(c, c->ctl, sizeof(LevelCtl));
@@ -634,7 +634,7 @@ iplsStatus iplsScratchBytes(iplsCtx c, int64_t n, iplsDtype dtype, size_t* bytes
   b += (size_t)tiles * kMaxK * 8;                                  // look-back words
   b += 2 * (size_t)subs * (sizeof(Sub) + sizeof(Model) + kMaxK * 8 + 257 * 8);
   b += 2 * (size_t)tiles * 4;
-  b += 2 * (size_t)(2 * n / rmax + 257 * subs + 16) * sizeof(Group);
+  b += 2 * (size_t)(2 * n / rmax + 257 * subs + 16) * (sizeof(Group) + 4 + sizeof(TailModel));
   b += 2 * (size_t)(n / kFillChunk + 129 * subs + 16) * sizeof(Fill);
   *bytes = b + b / 4 + 4096;
   return IPLS_OK;

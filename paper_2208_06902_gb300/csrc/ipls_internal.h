@@ -52,6 +52,18 @@ struct Model {
   uint64_t split[128];
 };
 
+// Model of a block-resident tail task as k_tail_fit leaves it: the linear
+// part, or (kind kSplitter) up to kTailSplit unique splitters built from the
+// same sorted sample; a splitter tree with more splitters is marked by
+// nsplit > kTailSplit and the task takes the slow path.
+constexpr int kTailSplit = 8;
+struct TailModel {
+  LinModel l;
+  int32_t nsplit;
+  int32_t pad;
+  uint64_t split[kTailSplit];
+};
+
 // Exact bucket thresholds of a linear model and a two-level index over them
 // (grid-level subproblems).  thr[j] (j = 1..nb-1) is the smallest
 // totalOrder key whose bucket under the binary64 model is at least j, so the
@@ -217,7 +229,7 @@ struct ResidentArgs {
   int32_t ngroups;
   const int32_t* fit_list;
   int32_t nfit;
-  LinModel* tail_models;           // indexed by Group::fit
+  TailModel* tail_models;          // indexed by Group::fit
   SlowTask* slow;                  // slow list (capacity slow_cap)
   int32_t slow_cap;
   SlowCtl* slow_ctl;

@@ -22,7 +22,7 @@
 #include <cstring>
 #include <mutex>
 
-#include "../../include/ipls.h"
+#include "ipls.h"
 #include "ipls_internal.h"
 
 namespace {

@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(kFitWarps * 32) k_tail_fit(ResidentArgs a) {
   using Ord = typename T::Ord;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ FitShared fs[kFitWarps];
-  __shared__ LinModel lm[kFitWarps];
+  __shared__ TailModel tm[kFitWarps];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int task = blockIdx.x * kFitWarps + warp;
   if (task >= a.nfit) return;
@@ -53,10 +53,38 @@ __global__ void __launch_bounds__(kFitWarps * 32) k_tail_fit(ResidentArgs a) {
   for (int j = lane; j < S; j += 32) so[j] = T::ord(src[sample_offset(stream, j, g.n)]);
   __syncwarp();
   group_sort<WarpG, Ord>(so, S);
-  fit_linear<WarpG, K>(so, S, a.k, &lm[warp], fs[warp]);
-  const unsigned long long* s = reinterpret_cast<const unsigned long long*>(&lm[warp]);
+  TailModel& m = tm[warp];
+  fit_linear<WarpG, K>(so, S, a.k, &m.l, fs[warp]);
+  if (lane == 0) m.nsplit = 0;
+  __syncwarp();
+  if (m.l.kind == kSplitter) {
+    // splitter tree from the same sorted sample: (k-1)/2 equidistant sample
+    // keys, duplicates dropped (Ch.3 "Decision Trees"; equality buckets)
+    const int want = (a.k - 1) / 2;
+    int cnt = 0;
+    for (int base = 0; base < want; base += 32) {
+      const int i = base + lane;
+      bool keep = false;
+      uint64_t u = 0;
+      if (i < want) {
+        u = (uint64_t)so[(int64_t)(i + 1) * S / (want + 1)];
+        keep = (i == 0) || (u != (uint64_t)so[(int64_t)i * S / (want + 1)]);
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, keep);
+      const int pos = cnt + __popc(bal & lanemask_lt());
+      if (keep && pos < kTailSplit) m.split[pos] = u;
+      cnt += __popc(bal);
+    }
+    if (lane == 0) {
+      m.nsplit = cnt;
+      m.l.nb = 2 * cnt + 1;
+      m.l.fast = 0;
+    }
+    __syncwarp();
+  }
+  const unsigned long long* s = reinterpret_cast<const unsigned long long*>(&m);
   unsigned long long* d = reinterpret_cast<unsigned long long*>(&a.tail_models[g.fit]);
-  if (lane < (int)(sizeof(LinModel) / 8)) d[lane] = s[lane];
+  if (lane < (int)(sizeof(TailModel) / 8)) d[lane] = s[lane];
 }
 
 // ---------------------------------------------------------------------------
@@ -74,6 +102,7 @@ struct ResSmem {
   } u;
   int bstart[kMaxK + 1];
   int tot[kMaxK];
+  int hom[kMaxK];
   Model model;
   FitShared fs;
   int nsmall, nstack, redo, err, slow_all;
@@ -106,6 +135,42 @@ __device__ void trace_pass(ResSmem<K>& sh, const ResidentArgs& a, int64_t off, i
   if (sh.rec < a.trace_cap && threadIdx.x < kMaxK)
     a.trace[sh.rec].counts[threadIdx.x] = (threadIdx.x < m.l.nb) ? sh.tot[threadIdx.x] : 0;
   __syncthreads();
+}
+
+// For every bucket b with more than `cutoff` keys (stored contiguously from
+// keys[start[b]]), hom[b] = 1 when all of them are the same key.  Such a
+// bucket is done: its own pass would draw a homogeneous sample, take the
+// splitter tree with that one key as its only splitter and put every key
+// into the equality bucket, moving nothing (the rule for duplicates).
+template <class Ord>
+__device__ void mark_homogeneous(const Ord* keys, const int* start, const int* tot, int nb,
+                                 int cutoff, int* hom) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) hom[b] = tot[b] > cutoff ? 1 : 0;
+  __syncthreads();
+  for (int b = warp; b < nb; b += blockDim.x >> 5) {
+    if (!hom[b]) continue;
+    const Ord first = keys[start[b]];
+    bool diff = false;
+    for (int i = start[b] + lane; i < start[b] + tot[b]; i += 32) diff |= keys[i] != first;
+    if (__any_sync(0xffffffffu, diff) && lane == 0) hom[b] = 0;
+  }
+  __syncthreads();
+}
+
+// The pass record of such a homogeneous subproblem (one thread): splitter
+// tree with one splitter, every key in its equality bucket.
+__device__ void record_homogeneous(const ResidentArgs& a, int64_t off, int n, int level) {
+  atomicAdd((unsigned long long*)&a.run->resident_passes, 1ULL);
+  atomicAdd((unsigned long long*)&a.run->resident_fallback, 1ULL);
+  if (a.trace_cap <= 0) return;
+  const long long rec = (long long)atomicAdd((unsigned long long*)&a.run->trace_count, 1ULL);
+  if (rec >= a.trace_cap) return;
+  iplsTraceRecDev& r = a.trace[rec];
+  r.off = off; r.n = n; r.level = level; r.kind = kSplitter; r.capped = 0; r.nbuckets = 3;
+  r.S = sample_size(n, level, a.k, a.root_sample); r.D = 0; r.A = 0.0; r.Bc = 0.0; r.ud = 0.0;
+  r.xlo_bits = 0; r.nsplit = 1; r.where = 1;
+  for (int b = 0; b < kMaxK; ++b) r.counts[b] = (b == 1) ? n : 0;
 }
 
 // Exclusive scan of sh.tot into sh.bstart (one warp, 8 values per lane).
@@ -258,11 +323,16 @@ __device__ void resident_pass(ResSmem<K>& sh, const ResidentArgs& a, int64_t gof
     atomicAdd((unsigned long long*)&a.run->resident_passes, 1ULL);
     if (m.l.kind == kSplitter) atomicAdd((unsigned long long*)&a.run->resident_fallback, 1ULL);
   }
-  // children (equality buckets of the splitter tree are homogeneous: done)
+  // children (equality buckets of the splitter tree are homogeneous: done;
+  // so is any other child whose keys are all equal, after its record)
+  mark_homogeneous(sh.keys + s0, sh.bstart, sh.tot, m.l.nb, a.cutoff, sh.hom);
   if (threadIdx.x < m.l.nb) {
     const int b = threadIdx.x;
     const bool eq = (m.l.kind == kSplitter) && (b & 1);
-    if (!eq) push_child(sh, s0 + sh.bstart[b], sh.tot[b], level + 1, a.cutoff);
+    if (!eq) {
+      if (sh.hom[b]) record_homogeneous(a, goff + s0 + sh.bstart[b], sh.tot[b], level + 1);
+      else push_child(sh, s0 + sh.bstart[b], sh.tot[b], level + 1, a.cutoff);
+    }
   }
   __syncthreads();
 }
@@ -334,7 +404,8 @@ struct TailSmem {
   int bstart[kMaxK + 1];
   int segb[kMaxK + 1];
   int tot[kMaxK];
-  LinModel lin;
+  int hom[kMaxK];
+  TailModel tm;
   int slow_all;
   long long rec;
 };
@@ -358,17 +429,21 @@ __global__ void __launch_bounds__(kResidentThreads, 2) k_tail(ResidentArgs a) {
   const Bits* src = reinterpret_cast<const Bits*>(a.buf[g.buf]) + g.off;
   Bits* dst = reinterpret_cast<Bits*>(a.buf[0]) + g.off;
   int nseg;
+  bool split_tree = false;  // children at odd ids are equality buckets
   if (g.fit >= 0) {
-    if (threadIdx.x < (int)(sizeof(LinModel) / 8))
-      reinterpret_cast<unsigned long long*>(&sh.lin)[threadIdx.x] =
+    if (threadIdx.x < (int)(sizeof(TailModel) / 8))
+      reinterpret_cast<unsigned long long*>(&sh.tm)[threadIdx.x] =
           reinterpret_cast<const unsigned long long*>(&a.tail_models[g.fit])[threadIdx.x];
     for (int i = threadIdx.x; i < kRW * kMaxK; i += blockDim.x) (&sh.wcnt[0][0])[i] = 0;
     if (threadIdx.x == 0) sh.slow_all = 0;
     __syncthreads();
-    bool slow = sh.lin.kind != kLinear;
+    split_tree = sh.tm.l.kind == kSplitter;
+    const int nsplit = sh.tm.nsplit;
+    // a splitter tree too large for the tail record recurses in k_slow
+    bool slow = split_tree && nsplit > kTailSplit;
     if (!slow) {
       Classifier<K> cls;
-      cls.load(sh.lin, a.exact_only);
+      cls.load(sh.tm.l, a.exact_only);
       const int chunk = ((n + kRW * 32 - 1) / (kRW * 32)) * 32;
       const int steps = chunk / 32;
       Bits v[kRKPT];
@@ -382,7 +457,9 @@ __global__ void __launch_bounds__(kResidentThreads, 2) k_tail(ResidentArgs a) {
       for (int j = 0; j < kRKPT; ++j) {
         if (j < steps) {
           const int i = warp * chunk + j * 32 + lane;
-          const int bk = (i < n) ? cls.bucket(v[j]) : kMaxK;
+          const int bk = (i < n) ? (split_tree ? splitter_bucket((uint64_t)T::ord(v[j]), sh.tm.split, nsplit)
+                                               : cls.bucket(v[j]))
+                                 : kMaxK;
           const unsigned peers = same_bucket_lanes(bk, bk < kMaxK);
           const int lt = __popc(peers & lanemask_lt());
           const int leader = __ffs(peers) - 1;
@@ -404,7 +481,9 @@ __global__ void __launch_bounds__(kResidentThreads, 2) k_tail(ResidentArgs a) {
           run += x;
         }
         sh.tot[b] = run;
-        if (run == n) sh.slow_all = 1;  // no progress: the splitter tree decides
+        // no progress of the linear model: the splitter tree decides (the
+        // splitter tree itself always progresses or leaves one equality run)
+        if (run == n && !split_tree) sh.slow_all = 1;
       }
       __syncthreads();
       slow = sh.slow_all != 0;
@@ -447,19 +526,25 @@ __global__ void __launch_bounds__(kResidentThreads, 2) k_tail(ResidentArgs a) {
             sh.rec = (long long)atomicAdd((unsigned long long*)&a.run->trace_count, 1ULL);
             if (sh.rec < a.trace_cap) {
               iplsTraceRecDev& r = a.trace[sh.rec];
-              r.off = g.off; r.n = n; r.level = g.level; r.kind = sh.lin.kind;
-              r.capped = sh.lin.capped; r.nbuckets = sh.lin.nb; r.S = sh.lin.S; r.D = sh.lin.D;
-              r.A = sh.lin.A; r.Bc = sh.lin.Bc; r.ud = sh.lin.ud; r.xlo_bits = sh.lin.xlo_bits;
-              r.nsplit = 0; r.where = 1;
+              r.off = g.off; r.n = n; r.level = g.level; r.kind = sh.tm.l.kind;
+              r.capped = sh.tm.l.capped; r.nbuckets = sh.tm.l.nb; r.S = sh.tm.l.S; r.D = sh.tm.l.D;
+              r.A = sh.tm.l.A; r.Bc = sh.tm.l.Bc; r.ud = sh.tm.l.ud; r.xlo_bits = sh.tm.l.xlo_bits;
+              r.nsplit = split_tree ? nsplit : 0; r.where = 1;
             }
           }
           __syncthreads();
           if (sh.rec < a.trace_cap && threadIdx.x < kMaxK)
-            a.trace[sh.rec].counts[threadIdx.x] = (threadIdx.x < sh.lin.nb) ? sh.tot[threadIdx.x] : 0;
+            a.trace[sh.rec].counts[threadIdx.x] = (threadIdx.x < sh.tm.l.nb) ? sh.tot[threadIdx.x] : 0;
         }
-        // buckets above the cutoff continue in the slow kernel
-        if (threadIdx.x < sh.lin.nb && sh.tot[threadIdx.x] > a.cutoff)
-          push_slow(a, g.off + sh.bstart[threadIdx.x], sh.tot[threadIdx.x], g.level + 1);
+        // buckets above the cutoff continue in the slow kernel; an equality
+        // bucket is done, and so is a bucket of equal keys after its record
+        __syncthreads();
+        mark_homogeneous(sh.keys, sh.bstart, sh.tot, sh.tm.l.nb, a.cutoff, sh.hom);
+        if (threadIdx.x < sh.tm.l.nb && sh.tot[threadIdx.x] > a.cutoff && !(split_tree && (threadIdx.x & 1))) {
+          const int b = threadIdx.x;
+          if (sh.hom[b]) record_homogeneous(a, g.off + sh.bstart[b], sh.tot[b], g.level + 1);
+          else push_slow(a, g.off + sh.bstart[b], sh.tot[b], g.level + 1);
+        }
         __syncthreads();
       }
     }
@@ -472,7 +557,7 @@ __global__ void __launch_bounds__(kResidentThreads, 2) k_tail(ResidentArgs a) {
       if (threadIdx.x == 0) atomicAdd((unsigned long long*)&a.run->resident_groups, 1ULL);
       return;
     }
-    nseg = sh.lin.nb;
+    nseg = sh.tm.l.nb;
   } else {
     for (int i = threadIdx.x; i < n; i += blockDim.x) sh.keys[i] = T::ord(src[i]);
     const int64_t b0 = g.bounds[0];
@@ -490,7 +575,7 @@ __global__ void __launch_bounds__(kResidentThreads, 2) k_tail(ResidentArgs a) {
     const int s = sh.segb[q], e = sh.segb[q + 1];
     const Ord kp = sh.keys[p];
     int d = p;
-    if (e - s <= cutoff) {
+    if (e - s <= cutoff && !(split_tree && (q & 1))) {
       int cnt = 0;
       for (int r = s; r < e; ++r) {
         const Ord kr = sh.keys[r];
