@@ -436,6 +436,13 @@ iplsStatus check_common(int64_t n, int dtype) {
   return IPLS_OK;
 }
 
+// Device keys must be aligned to the key width.
+iplsStatus check_keys_ptr(const void* keys, int dtype) {
+  if (reinterpret_cast<uintptr_t>(keys) % (uintptr_t)key_bytes(dtype) != 0)
+    return fail(IPLS_ERR_ARG, "keys must be aligned to the key width");
+  return IPLS_OK;
+}
+
 iplsStatus validate_cfg(const iplsConfig& c) {
   if (c.k < 3 || c.k > 256) return fail(IPLS_ERR_ARG, "k must be in [3, 256]");
   if (c.cutoff < 1 || c.cutoff > kResidentMax) return fail(IPLS_ERR_ARG, "cutoff must be in [1, 8192]");
@@ -660,6 +667,7 @@ static iplsCtx default_ctx(iplsStatus* st) {
 iplsStatus iplsSort(iplsCtx c, void* keys, int64_t n, iplsDtype dtype) {
   IPLS_TRY(check_common(n, dtype));
   if (n > 1 && !keys) return fail(IPLS_ERR_ARG, "keys is NULL");
+  IPLS_TRY(check_keys_ptr(keys, dtype));
   iplsStatus st = IPLS_OK;
   if (!c) { c = default_ctx(&st); if (!c) return st; }
   c->stats.calls += 1;
@@ -674,6 +682,8 @@ iplsStatus iplsSortSegmented(iplsCtx c, void* keys, const int64_t* offsets, int6
   if (nseg < 0) return fail(IPLS_ERR_ARG, "nseg < 0");
   if (nseg == 0) return IPLS_OK;
   if (!offsets || !keys) return fail(IPLS_ERR_ARG, "keys or offsets is NULL");
+  IPLS_TRY(check_keys_ptr(keys, dtype));
+  if (reinterpret_cast<uintptr_t>(offsets) % 8 != 0) return fail(IPLS_ERR_ARG, "offsets must be 8-byte aligned");
   iplsStatus st = IPLS_OK;
   if (!c) { c = default_ctx(&st); if (!c) return st; }
   // validate the offsets on the host (non-decreasing, within 2^40)
@@ -729,6 +739,7 @@ iplsStatus iplsGetKernelStats(iplsCtx c, iplsKernelStat* out, int32_t cap, int32
 iplsStatus iplsSubmit(iplsCtx c, void* keys, int64_t n, iplsDtype dtype, uint64_t* ticket) {
   if (!c || !ticket) return fail(IPLS_ERR_ARG, "ctx or ticket is NULL");
   IPLS_TRY(check_common(n, dtype));
+  IPLS_TRY(check_keys_ptr(keys, dtype));
   if (c->cfg.budget_bytes > 0 && 2 * n * (int64_t)key_bytes(dtype) > c->cfg.budget_bytes)
     return fail(IPLS_ERR_BUDGET, "request exceeds the memory budget");
   const uint64_t t = c->next_ticket++;

@@ -16,12 +16,12 @@
 //              per bucket, over its tiles: chunks of kChunkTiles tiles in
 //              ticket order, each chunk's prefix found by decoupled look-back
 //              over the chunks before it.
-//   k_scatter  every tile: read the bucket ids k_hist stored, rank each key
-//              stably inside the tile (warp ballots + per-warp counters),
-//              stage the tile in
-//              bucket order in shared memory and write the bucket runs out
-//              with coalesced stores at bucket base + tile offset (Ch.2
-//              IPS4o: move every key into the region of its bucket).
+//   k_scatter  every tile: read the keys and the bucket ids k_hist stored,
+//              rank each key stably inside the tile (warp ballots +
+//              per-warp counters), stage the tile in bucket order in shared
+//              memory and write the bucket runs out with coalesced stores at
+//              bucket base + tile offset (Ch.2 IPS4o: move every key into the
+//              region of its bucket).
 #include <cuda/atomic>
 
 #include "ipls_device.cuh"
@@ -32,6 +32,11 @@ constexpr int kTile = kTileKeys;
 constexpr int kWarps = kPassThreads / 32;
 constexpr int kKPT = kTile / kPassThreads;   // keys per thread
 constexpr int kKPW = kTile / kWarps;         // keys per warp
+// k_scatter: 512 threads per tile, 8 keys each
+constexpr int kScatterThreads = 512;
+constexpr int kSWarps = kScatterThreads / 32;
+constexpr int kSKPT = kTile / kScatterThreads;
+constexpr int kSKPW = kTile / kSWarps;
 
 int tile_keys(int) { return kTile; }
 int key_bytes(int dtype) { return (dtype == 0 || dtype == 2) ? 8 : 4; }
@@ -432,18 +437,22 @@ __global__ void __launch_bounds__(256) k_tilescan(LevelArgs a) {
   }
 }
 
+// The tile staged in bucket order, and the block's ranking state.
 template <class K>
 struct ScatterSmem {
   typename KT<K>::Bits stage[kTile];
   unsigned char sbid[kTile];
-  unsigned short wcnt[kWarps][kMaxK];
+  unsigned short wcnt[kSWarps][kMaxK];
+  unsigned int peer[kSWarps][kMaxK];   // lanes of the current step per bucket (kept zero between steps)
   int tile_start[kMaxK];
   int tile_tot[kMaxK];
   long long gbase[kMaxK];
 };
 
+// Stable scatter of every tile of the level: each block owns a contiguous
+// range of tiles; 512 threads, 8 keys each, read straight into registers.
 template <class K>
-__global__ void __launch_bounds__(kPassThreads, 3) k_scatter(LevelArgs a) {
+__global__ void __launch_bounds__(kScatterThreads, 2) k_scatter(LevelArgs a) {
   using T = KT<K>;
   using Bits = typename T::Bits;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -452,52 +461,62 @@ __global__ void __launch_bounds__(kPassThreads, 3) k_scatter(LevelArgs a) {
   Bits* dst_base[2] = {reinterpret_cast<Bits*>(a.buf[0]), reinterpret_cast<Bits*>(a.buf[1])};
   const int64_t nt = a.ntiles;
   const int64_t t0 = nt * blockIdx.x / gridDim.x, t1 = nt * (blockIdx.x + 1) / gridDim.x;
-  int cur = -1;
+  for (int i = threadIdx.x; i < kSWarps * kMaxK; i += blockDim.x) (&sh.peer[0][0])[i] = 0u;
   for (int64_t t = t0; t < t1; ++t) {
     const int s = a.tile2sub[t];
     const Sub sub = a.subs[s];
     if (sub.flags & kSkipScatter) continue;
     __syncthreads();
-    (void)cur;
-    for (int i = threadIdx.x; i < kWarps * kMaxK; i += blockDim.x) (&sh.wcnt[0][0])[i] = 0;
+    for (int i = threadIdx.x; i < kSWarps * kMaxK; i += blockDim.x) (&sh.wcnt[0][0])[i] = 0;
     const int64_t ti = t - sub.tile0;
     const int64_t kbase = sub.off + ti * kTile;
     const int64_t rem = sub.n - ti * kTile;
     const int tn = rem < kTile ? (int)rem : kTile;
     const Bits* src = reinterpret_cast<const Bits*>(a.buf[sub.buf]) + kbase;
     const uint8_t* ids = a.bids + kbase;
-    Bits v[kKPT];
-    unsigned int br[kKPT];   // bucket id, then bucket << 16 | rank within warp
+    Bits v[kSKPT];
+    unsigned int br[kSKPT];   // bucket id, then bucket << 16 | rank within warp
 #pragma unroll
-    for (int j = 0; j < kKPT; ++j) {
-      const int i = warp * kKPW + j * 32 + lane;
+    for (int j = 0; j < kSKPT; ++j) {
+      const int i = warp * kSKPW + j * 32 + lane;
       v[j] = (i < tn) ? src[i] : Bits(0);
       br[j] = (i < tn) ? (unsigned)ids[i] : (unsigned)kMaxK;
     }
     __syncthreads();  // wcnt zeroed
 #pragma unroll
-    for (int j = 0; j < kKPT; ++j) {
+    for (int j = 0; j < kSKPT; ++j) {
       const int bk = (int)br[j];
-      const unsigned peers = same_bucket_lanes(bk, bk < kMaxK);
+      const bool valid = bk < kMaxK;
+      const int bq = valid ? bk : 0;
+      // the lanes of this step with the same bucket: one shared OR each
+      if (valid) atomicOr(&sh.peer[warp][bq], 1u << lane);
+      __syncwarp();
+      const unsigned peers = valid ? sh.peer[warp][bq] : 0u;
       const int lt = __popc(peers & lanemask_lt());
-      const int leader = __ffs(peers) - 1;
-      const int basec = (bk < kMaxK) ? sh.wcnt[warp][bk] : 0;
+      const int basec = sh.wcnt[warp][bq];
       br[j] = ((unsigned)bk << 16) | (unsigned)(basec + lt);
       __syncwarp();
-      if (lane == leader && bk < kMaxK) sh.wcnt[warp][bk] = (unsigned short)(basec + __popc(peers));
+      if (valid && lt == 0) {  // the first lane of the bucket
+        sh.wcnt[warp][bq] = (unsigned short)(basec + __popc(peers));
+        sh.peer[warp][bq] = 0u;
+      }
       __syncwarp();
     }
     __syncthreads();
-    {
-      const int b = threadIdx.x;  // 256 threads = 256 buckets
+    if (threadIdx.x < kMaxK) {
+      const int b = threadIdx.x;
       int run = 0;
 #pragma unroll
-      for (int w = 0; w < kWarps; ++w) {
+      for (int w = 0; w < kSWarps; ++w) {
         const int x = sh.wcnt[w][b];
         sh.wcnt[w][b] = (unsigned short)run;
         run += x;
       }
       sh.tile_tot[b] = run;
+    } else {
+      // meanwhile: this tile's base of every bucket in the destination
+      const int b = threadIdx.x - kMaxK;
+      sh.gbase[b] = sub.off + a.bases[(size_t)s * 257 + b] + (long long)a.tile_off[(size_t)t * kMaxK + b];
     }
     __syncthreads();
     if (warp == 0) {
@@ -514,16 +533,15 @@ __global__ void __launch_bounds__(kPassThreads, 3) k_scatter(LevelArgs a) {
       }
       int run = incl - sum;
 #pragma unroll
-      for (int q = 0; q < 8; ++q) { sh.tile_start[lane * 8 + q] = run; run += loc[q]; }
+      for (int q = 0; q < 8; ++q) {
+        sh.tile_start[lane * 8 + q] = run;
+        sh.gbase[lane * 8 + q] -= run;
+        run += loc[q];
+      }
     }
     __syncthreads();
-    {
-      const int b = threadIdx.x;
-      sh.gbase[b] = sub.off + a.bases[(size_t)s * 257 + b] +
-                    (long long)a.tile_off[(size_t)t * kMaxK + b] - sh.tile_start[b];
-    }
 #pragma unroll
-    for (int j = 0; j < kKPT; ++j) {
+    for (int j = 0; j < kSKPT; ++j) {
       const int bk = (int)(br[j] >> 16);
       if (bk < kMaxK) {
         const int lp = sh.tile_start[bk] + sh.wcnt[warp][bk] + (int)(br[j] & 0xFFFF);
@@ -532,11 +550,11 @@ __global__ void __launch_bounds__(kPassThreads, 3) k_scatter(LevelArgs a) {
       }
     }
     __syncthreads();
-    Bits* dst = dst_base[1 - sub.buf];
-    const int64_t lo = sub.off, hi = sub.off + sub.n;
+    Bits* dst = dst_base[1 - sub.buf] + sub.off;
+    const uint64_t span = (uint64_t)sub.n;
     for (int i = threadIdx.x; i < tn; i += blockDim.x) {
-      const int64_t p = sh.gbase[sh.sbid[i]] + i;
-      if (p >= lo && p < hi) dst[p] = sh.stage[i];
+      const uint64_t p = (uint64_t)(sh.gbase[sh.sbid[i]] - sub.off + i);
+      if (p < span) dst[p] = sh.stage[i];
     }
   }
 }
@@ -627,9 +645,9 @@ cudaError_t launch_scatter(const LevelArgs& a, cudaStream_t s, int grid) {
     using K = std::remove_pointer_t<decltype(tag)>;
     const size_t smem = sizeof(ScatterSmem<K>);
     cudaFuncSetAttribute(k_scatter<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int g = resident_blocks((const void*)k_scatter<K>, kPassThreads, smem, grid);
+    int g = resident_blocks((const void*)k_scatter<K>, kScatterThreads, smem, grid);
     if (g > a.ntiles) g = (int)a.ntiles;
-    k_scatter<K><<<g, kPassThreads, smem, s>>>(a);
+    k_scatter<K><<<g, kScatterThreads, smem, s>>>(a);
     return cudaGetLastError();
   });
 }

@@ -401,6 +401,7 @@ struct TailSmem {
   typename KT<K>::Ord keys[kResidentMax];
   unsigned char seg[kResidentMax];   // segment (bucket or child) of each position
   unsigned short wcnt[kRW][kMaxK];
+  unsigned int peer[kRW][kMaxK];     // lanes of the current step per bucket (kept zero between steps)
   int bstart[kMaxK + 1];
   int segb[kMaxK + 1];
   int tot[kMaxK];
@@ -434,7 +435,10 @@ __global__ void __launch_bounds__(kResidentThreads, 2) k_tail(ResidentArgs a) {
     if (threadIdx.x < (int)(sizeof(TailModel) / 8))
       reinterpret_cast<unsigned long long*>(&sh.tm)[threadIdx.x] =
           reinterpret_cast<const unsigned long long*>(&a.tail_models[g.fit])[threadIdx.x];
-    for (int i = threadIdx.x; i < kRW * kMaxK; i += blockDim.x) (&sh.wcnt[0][0])[i] = 0;
+    for (int i = threadIdx.x; i < kRW * kMaxK; i += blockDim.x) {
+      (&sh.wcnt[0][0])[i] = 0;
+      (&sh.peer[0][0])[i] = 0u;
+    }
     if (threadIdx.x == 0) sh.slow_all = 0;
     __syncthreads();
     split_tree = sh.tm.l.kind == kSplitter;
@@ -460,13 +464,20 @@ __global__ void __launch_bounds__(kResidentThreads, 2) k_tail(ResidentArgs a) {
           const int bk = (i < n) ? (split_tree ? splitter_bucket((uint64_t)T::ord(v[j]), sh.tm.split, nsplit)
                                                : cls.bucket(v[j]))
                                  : kMaxK;
-          const unsigned peers = same_bucket_lanes(bk, bk < kMaxK);
+          // the lanes of this step with the same bucket: one shared OR each
+          const bool valid = bk < kMaxK;
+          const int bq = valid ? bk : 0;
+          if (valid) atomicOr(&sh.peer[warp][bq], 1u << lane);
+          __syncwarp();
+          const unsigned peers = valid ? sh.peer[warp][bq] : 0u;
           const int lt = __popc(peers & lanemask_lt());
-          const int leader = __ffs(peers) - 1;
-          const int basec = (bk < kMaxK) ? sh.wcnt[warp][bk] : 0;
+          const int basec = sh.wcnt[warp][bq];
           br[j] = ((unsigned)bk << 16) | (unsigned)(basec + lt);
           __syncwarp();
-          if (lane == leader && bk < kMaxK) sh.wcnt[warp][bk] = (unsigned short)(basec + __popc(peers));
+          if (valid && lt == 0) {  // the first lane of the bucket
+            sh.wcnt[warp][bq] = (unsigned short)(basec + __popc(peers));
+            sh.peer[warp][bq] = 0u;
+          }
           __syncwarp();
         }
       }

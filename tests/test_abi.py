@@ -38,6 +38,8 @@ def test_host_side_validation_without_gpu():
     assert lib.iplsSort(None, None, 2**32, 0) == -1
     assert lib.iplsSort(None, None, 10, 0) == -1      # NULL keys
     assert "NULL" in p.iplsLastError()
+    assert lib.iplsSort(None, ctypes.c_void_p(0x1004), 10, 0) == -1   # f64 keys not 8-aligned
+    assert "aligned" in p.iplsLastError()
     assert lib.iplsSortSegmented(None, None, None, -1, 0) == -1
     assert lib.iplsSortSegmented(None, None, None, 0, 0) == 0   # nothing to do
     cfg = p.iplsDefaultConfig()
