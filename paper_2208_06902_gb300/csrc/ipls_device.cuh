@@ -538,6 +538,24 @@ struct Classifier {
     }
     return classify_exact<K>(b, A, Bc, xlo, nb);
   }
+  // The fixed-point / FP32 estimate when it decides, -1 when the key needs
+  // the binary64 model (the caller may batch those), the full answer for
+  // the splitter tree or when the estimate is off.
+  __device__ __forceinline__ int bucket_or_defer(Bits b) const {
+    if (kind == kSplitter) return splitter_bucket((uint64_t)KT<K>::ord(b), split, nsplit);
+    if (fast) return fast_bucket(b);
+    return classify_exact<K>(b, A, Bc, xlo, nb);
+  }
+  __device__ __forceinline__ int exact(Bits b) const { return classify_exact<K>(b, A, Bc, xlo, nb); }
+};
+
+// Tile positions of the keys of one warp whose bucket needs the binary64
+// model, queued so that the FP64 instructions run with all 32 lanes busy
+// (on this GPU an FP64 warp instruction costs the same with one active lane
+// as with 32).
+template <int kCap>
+struct ExactQueue {
+  unsigned short idx[kCap];
 };
 
 // ---------------------------------------------------------------------------

@@ -116,7 +116,8 @@ __global__ void __launch_bounds__(kPassThreads, 4) k_hist(LevelArgs a, int rehis
   __shared__ ThrTable tab;
   __shared__ unsigned int hist[kWarps][kMaxK];
   __shared__ unsigned int acc[kMaxK];
-  const int warp = threadIdx.x >> 5;
+  __shared__ ExactQueue<kChunk * 32> xq[kWarps];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int i = threadIdx.x; i < kWarps * kMaxK; i += blockDim.x) (&hist[0][0])[i] = 0;
   for (int i = threadIdx.x; i < kMaxK; i += blockDim.x) acc[i] = 0;
   const int64_t nt = a.ntiles;
@@ -170,14 +171,37 @@ __global__ void __launch_bounds__(kPassThreads, 4) k_hist(LevelArgs a, int rehis
           }
         }
       } else {
+        unsigned dmask = 0;  // steps whose key needs the binary64 model
 #pragma unroll
         for (int j = 0; j < kChunk; ++j) {
           const int i = c0 + j * kPassThreads + threadIdx.x;
           if (i < tn) {
-            const int bk = cls.bucket(v[j]);
-            ids[i] = (uint8_t)bk;
-            atomicAdd(&hist[warp][bk], 1u);
+            const int bk = cls.bucket_or_defer(v[j]);
+            if (bk >= 0) {
+              ids[i] = (uint8_t)bk;
+              atomicAdd(&hist[warp][bk], 1u);
+            } else {
+              dmask |= 1u << j;
+            }
           }
+        }
+        if (__any_sync(0xffffffffu, dmask != 0)) {
+          // queue them and evaluate 32 at a time
+          int nq = 0;
+          for (int j = 0; j < kChunk; ++j) {
+            const bool d = (dmask >> j) & 1u;
+            const unsigned dm = __ballot_sync(0xffffffffu, d);
+            if (d) xq[warp].idx[nq + __popc(dm & lanemask_lt())] = (unsigned short)(c0 + j * kPassThreads + threadIdx.x);
+            nq += __popc(dm);
+          }
+          __syncwarp();
+          for (int q = lane; q < nq; q += 32) {
+            const int i = xq[warp].idx[q];
+            const int e = cls.exact(src[i]);
+            ids[i] = (uint8_t)e;
+            atomicAdd(&hist[warp][e], 1u);
+          }
+          __syncwarp();
         }
       }
     }

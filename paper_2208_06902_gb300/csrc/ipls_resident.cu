@@ -457,13 +457,49 @@ __global__ void __launch_bounds__(kResidentThreads, 2) k_tail(ResidentArgs a) {
         const int i = warp * chunk + j * 32 + lane;
         v[j] = (j < steps && i < n) ? src[i] : Bits(0);
       }
+      // classify; keys that need the binary64 model are deferred
+      unsigned dmask = 0;
 #pragma unroll
       for (int j = 0; j < kRKPT; ++j) {
         if (j < steps) {
           const int i = warp * chunk + j * 32 + lane;
-          const int bk = (i < n) ? (split_tree ? splitter_bucket((uint64_t)T::ord(v[j]), sh.tm.split, nsplit)
-                                               : cls.bucket(v[j]))
-                                 : kMaxK;
+          int bk = kMaxK;
+          if (i < n) {
+            bk = split_tree ? splitter_bucket((uint64_t)T::ord(v[j]), sh.tm.split, nsplit)
+                            : cls.bucket_or_defer(v[j]);
+            if (bk < 0) dmask |= 1u << j;
+          }
+          br[j] = (unsigned)bk;
+        }
+      }
+      if (__any_sync(0xffffffffu, dmask != 0)) {
+        // queue them (in the key area, free until the tile is placed) and
+        // evaluate 32 at a time
+        static_assert(kRW * kRKPT * 32 * 3 <= (int)sizeof(sh.keys), "deferred queue must fit in the key area");
+        unsigned short* xq = reinterpret_cast<unsigned short*>(sh.keys) + warp * kRKPT * 32;
+        unsigned char* xr = reinterpret_cast<unsigned char*>(sh.keys) + kRW * kRKPT * 32 * 2 + warp * kRKPT * 32;
+        int nq = 0;
+        for (int j = 0; j < steps; ++j) {
+          const bool d = (dmask >> j) & 1u;
+          const unsigned dm = __ballot_sync(0xffffffffu, d);
+          if (d) xq[nq + __popc(dm & lanemask_lt())] = (unsigned short)(j * 32 + lane);
+          nq += __popc(dm);
+        }
+        __syncwarp();
+        for (int q = lane; q < nq; q += 32) {
+          const int code = xq[q];
+          xr[code] = (unsigned char)cls.exact(src[warp * chunk + code]);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < kRKPT; ++j)
+          if (j < steps && ((dmask >> j) & 1u)) br[j] = xr[j * 32 + lane];
+        __syncwarp();
+      }
+#pragma unroll
+      for (int j = 0; j < kRKPT; ++j) {
+        if (j < steps) {
+          const int bk = (int)br[j];
           // the lanes of this step with the same bucket: one shared OR each
           const bool valid = bk < kMaxK;
           const int bq = valid ? bk : 0;
@@ -526,7 +562,8 @@ __global__ void __launch_bounds__(kResidentThreads, 2) k_tail(ResidentArgs a) {
             const int bk = (int)(br[j] >> 16);
             if (bk < kMaxK) {
               const int p = sh.bstart[bk] + sh.wcnt[warp][bk] + (int)(br[j] & 0xFFFF);
-              sh.keys[p] = T::ord(v[j]);
+              // read again (from cache) rather than held in registers
+              sh.keys[p] = T::ord(src[warp * chunk + j * 32 + lane]);
               sh.seg[p] = (unsigned char)bk;
             }
           }
