@@ -283,6 +283,7 @@ iplsStatus sort_impl(iplsCtx c, void* keys, int64_t n, int dtype, const int64_t*
   ra.run = c->run; ra.trace = cfg.trace_cap > 0 ? c->trace_res : nullptr; ra.trace_cap = cfg.trace_cap;
 
   int64_t nsub = 0, ntiles = 0, nchunks = 0;
+  int64_t max_sub_n = n;  // bound on the size of this level's grid subproblems
   const int64_t sub_bound = n / (rmax + 1) + 2;
   const int64_t tile_bound = n / tile + sub_bound + 2;
   const int64_t chunk_bound = tile_bound / kChunkTiles + sub_bound + 2;
@@ -311,6 +312,7 @@ iplsStatus sort_impl(iplsCtx c, void* keys, int64_t n, int dtype, const int64_t*
     nsub = c->h_ctl->nsub_next;
     ntiles = c->h_ctl->tiles_next;
     nchunks = c->h_ctl->chunks_next;
+    max_sub_n = c->h_ctl->max_sub_n;
   } else if (n <= rmax && resident_root_ok) {
     // the whole array is one block-resident task (base case only when n is
     // at most the cutoff, otherwise a fitted pass first)
@@ -392,8 +394,7 @@ iplsStatus sort_impl(iplsCtx c, void* keys, int64_t n, int dtype, const int64_t*
     a.trace = cfg.trace_cap > 0 ? c->trace_grid : nullptr;
     a.trace_cap = cfg.trace_cap;
     a.trace_base = c->trace_grid_count;
-    int max_sample = sample_size_host(n, 1, cfg.k, 0);
-    if (level == 0 && cfg.root_sample > max_sample) max_sample = (int)cfg.root_sample;
+    const int max_sample = sample_size_host(std::max<int64_t>(max_sub_n, 2), level, cfg.k, cfg.root_sample);
     IPLS_CUDA(timed(c, kkFit, [&] { return launch_fit(a, c->stream, max_sample); }));
     IPLS_CUDA(timed(c, kkHist, [&] { return launch_hist(a, c->stream, 0, occupancy_grid(c, 0, dtype)); }));
     IPLS_CUDA(timed(c, kkCheck, [&] { return launch_check(a, c->stream, max_sample); }));
@@ -420,6 +421,7 @@ iplsStatus sort_impl(iplsCtx c, void* keys, int64_t n, int dtype, const int64_t*
     nsub = lc.nsub_next;
     ntiles = lc.tiles_next;
     nchunks = lc.chunks_next;
+    max_sub_n = lc.max_sub_n;
     ++level;
   }
   IPLS_TRY(check_run(c));

@@ -792,6 +792,7 @@ __device__ __forceinline__ bool reserve_tiles(LevelCtl* ctl, int32_t idx, Sub& s
     ctl->overflow = 1;
     return false;
   }
+  atomicMax((unsigned long long*)&ctl->max_sub_n, (unsigned long long)sub.n);
   sub.tile0 = t0;
   sub.ntiles = nt;
   sub.chunk0 = (int32_t)c0;

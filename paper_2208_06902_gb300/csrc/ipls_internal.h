@@ -139,7 +139,8 @@ struct LevelCtl {
   int64_t max_bucket;    // max over passes of largest bucket / n, scaled by 2^20
   int64_t keys_moved;    // keys scattered by this level's grid passes
   int64_t keys_level;    // keys in this level's grid subproblems
-  int64_t pad[2];
+  int64_t max_sub_n;     // largest grid subproblem created for the next level
+  int64_t pad;
 };
 
 // Run-wide device status (persists across levels of one call).

@@ -1,7 +1,8 @@
 // Grid-wide learned partition pass over all subproblems of one level.
 //
-//   k_fit      one block per subproblem: sample alpha*k-1 keys, sort them,
-//              fit FMCD (Ch.3 listing) or the splitter tree, zero counts.
+//   k_fit      sample alpha*k-1 keys, sort them, fit FMCD (Ch.3 listing) or
+//              the splitter tree, zero counts: one warp per subproblem
+//              (k_fit_warp) when the sample fits, else one block.
 //   k_hist     every tile of every subproblem: classify each key with the
 //              model (Ch.3 model equation) and store its bucket id, per-warp
 //              shared histograms; the tile's histogram goes to memory, the
@@ -78,6 +79,53 @@ __device__ int gather_sorted_sample(const LevelArgs& a, const Sub& sub,
   return S;
 }
 
+// Subproblems whose sample fits a warp's share of shared memory are fitted
+// by one warp each (k_fit_warp), many at a time; the others (the root and
+// very large subproblems, or all when the threshold index is built) by one
+// block each (k_fit).
+// A level with fewer subproblems than kWarpFitMin keeps one block per fit
+// (eight fits per block would leave most SMs idle).
+constexpr int kFitWarpsG = 8;
+constexpr int kWarpFitMin = 1024;
+__host__ __device__ __forceinline__ bool warp_fits(const LevelArgs& a) {
+  return !a.use_tables && a.nsub >= kWarpFitMin;
+}
+__device__ __forceinline__ bool fit_by_warp(const LevelArgs& a, const Sub& sub) {
+  return warp_fits(a) && sample_size(sub.n, sub.level, a.k, a.root_sample) <= kResidentSample;
+}
+
+template <class K>
+__global__ void __launch_bounds__(kFitWarpsG * 32) k_fit_warp(LevelArgs a) {
+  using T = KT<K>;
+  using Ord = typename T::Ord;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ FitShared fs[kFitWarpsG];
+  __shared__ Model mod[kFitWarpsG];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int s = blockIdx.x * kFitWarpsG + warp;
+  if (s >= a.nsub) return;
+  const Sub sub = a.subs[s];
+  if (!fit_by_warp(a, sub)) return;
+  const int S = (int)sample_size(sub.n, sub.level, a.k, a.root_sample);
+  Ord* so = reinterpret_cast<Ord*>(smem_raw) + warp * kResidentSample;
+  const uint64_t st = stream_key(a.seed, sub.off, sub.n, sub.level);
+  const typename T::Bits* src = buf_ptr<K>(a, sub.buf) + sub.off;
+  for (int j = lane; j < S; j += 32) so[j] = T::ord(src[sample_offset(st, j, sub.n)]);
+  __syncwarp();
+  group_sort<WarpG, Ord>(so, S);
+  Model& m = mod[warp];
+  fit_model<WarpG, K>(so, S, a.k, &m, fs[warp]);
+  const unsigned long long* ms = reinterpret_cast<const unsigned long long*>(&m);
+  unsigned long long* md = reinterpret_cast<unsigned long long*>(&a.models[s]);
+  for (int i = lane; i < (int)(sizeof(Model) / 8); i += 32) md[i] = ms[i];
+  for (int b = lane; b < kMaxK; b += 32) a.counts[(size_t)s * kMaxK + b] = 0;
+  if (lane == 0) {
+    a.tabs[s].ok = 0;
+    a.subs[s].flags = 0;
+    atomicAdd((unsigned long long*)&a.ctl->keys_level, (unsigned long long)sub.n);
+  }
+}
+
 // ---------------------------------------------------------------------------
 template <class K>
 __global__ void __launch_bounds__(kFitThreads) k_fit(LevelArgs a) {
@@ -90,6 +138,7 @@ __global__ void __launch_bounds__(kFitThreads) k_fit(LevelArgs a) {
   Ord* so = reinterpret_cast<Ord*>(smem);
   const int s = blockIdx.x;
   const Sub sub = a.subs[s];
+  if (fit_by_warp(a, sub)) return;  // k_fit_warp fits this one
   const int S = gather_sorted_sample<K>(a, sub, so);
   fit_model<BlockG, K>(so, S, a.k, &sm, fs);
   copy_model(&a.models[s], &sm);
@@ -608,7 +657,16 @@ cudaError_t launch_fit(const LevelArgs& a, cudaStream_t s, int max_sample) {
   if (a.nsub <= 0) return cudaSuccess;
   return by_dtype(a.dtype, [&](auto* tag) {
     using K = std::remove_pointer_t<decltype(tag)>;
-    const size_t smem = (size_t)max_sample * sizeof(typename KT<K>::Ord);
+    using Ord = typename KT<K>::Ord;
+    if (warp_fits(a)) {
+      const size_t wsmem = (size_t)kFitWarpsG * kResidentSample * sizeof(Ord);
+      cudaFuncSetAttribute(k_fit_warp<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem);
+      k_fit_warp<K><<<(a.nsub + kFitWarpsG - 1) / kFitWarpsG, kFitWarpsG * 32, wsmem, s>>>(a);
+      const cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+      if (max_sample <= kResidentSample) return cudaSuccess;  // every subproblem went to a warp
+    }
+    const size_t smem = (size_t)max_sample * sizeof(Ord);
     cudaFuncSetAttribute(k_fit<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_fit<K><<<a.nsub, kFitThreads, smem, s>>>(a);
     return cudaGetLastError();
