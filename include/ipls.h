@@ -122,6 +122,8 @@ typedef struct iplsStats {
   int64_t scratch_bytes;      /* device scratch held by the context */
   int64_t trace_records;      /* passes recorded (may exceed trace_cap) */
   double max_bucket_frac;     /* largest bucket / subproblem size, grid passes */
+  int64_t slow_tasks;         /* ranges recursed inside one block (slow list), last call */
+  int64_t slow_passes;        /* partition passes run by that in-block recursion, last call */
 } iplsStats;
 
 typedef struct iplsContext* iplsCtx;

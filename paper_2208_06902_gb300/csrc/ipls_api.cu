@@ -100,6 +100,7 @@ struct iplsContext {
   // slow list of the block-resident tail
   SlowTask* slow = nullptr; int64_t slow_cap = 0;
   SlowCtl* slow_ctl = nullptr;
+  uint64_t* split_pool = nullptr;     int64_t split_pool_cap = 0;  // words
 };
 
 namespace {
@@ -219,8 +220,10 @@ iplsStatus launch_tail(iplsCtx c, ResidentArgs& ra, Slot& s, int32_t ngroups, in
   ra.slow_cap = (int32_t)std::min<int64_t>(c->slow_cap, INT32_MAX);
   ra.slow_ctl = c->slow_ctl;
   if (ngroups <= 0) return IPLS_OK;
-  if (nfit > 0) IPLS_CUDA(timed(c, kkTailFit, [&] { return launch_tail_fit(ra, c->stream); }));
+  if (nfit > 0) IPLS_TRY(ensure(c, c->split_pool, c->split_pool_cap, (int64_t)kSplitPoolCap * 128));
+  ra.split_pool = c->split_pool;
   IPLS_CUDA(cudaMemsetAsync(c->slow_ctl, 0, sizeof(SlowCtl), c->stream));
+  if (nfit > 0) IPLS_CUDA(timed(c, kkTailFit, [&] { return launch_tail_fit(ra, c->stream); }));
   IPLS_CUDA(timed(c, kkResident, [&] { return launch_resident(ra, c->stream); }));
   IPLS_CUDA(timed(c, kkSlow, [&] { return launch_slow(ra, c->stream, c->num_sms); }));
   return IPLS_OK;
@@ -234,6 +237,8 @@ iplsStatus check_run(iplsCtx c) {
   if (c->h_run->error != 0)
     return fail((iplsStatus)c->h_run->error, "device reported status " + std::to_string(c->h_run->error));
   c->stats.resident_groups = c->h_run->resident_groups;
+  c->stats.slow_tasks = c->h_run->slow_tasks;
+  c->stats.slow_passes = c->h_run->slow_passes;
   c->stats.fallback_passes += c->h_run->resident_fallback;
   c->stats.trace_records = c->trace_grid_count + c->h_run->trace_count;
   return IPLS_OK;
@@ -627,6 +632,7 @@ iplsStatus iplsDestroy(iplsCtx c) {
   dev_free(c, c->host_stage, (size_t)c->host_stage_cap);
   dev_free(c, c->slow, (size_t)c->slow_cap * sizeof(SlowTask));
   dev_free(c, c->slow_ctl, sizeof(SlowCtl));
+  dev_free(c, c->split_pool, (size_t)c->split_pool_cap * 8);
   delete c;
   return IPLS_OK;
 }
@@ -640,6 +646,7 @@ iplsStatus iplsScratchBytes(iplsCtx c, int64_t n, iplsDtype dtype, size_t* bytes
   const int64_t tiles = n / tile_keys(dtype) + subs + 2;
   size_t b = (size_t)n * key_bytes(dtype);                         // ping-pong keys
   b += (size_t)n;                                                  // bucket ids
+  b += (size_t)kSplitPoolCap * 128 * 8;                            // splitter pool
   b += (size_t)tiles * kMaxK * 8;                                  // look-back words
   b += 2 * (size_t)subs * (sizeof(Sub) + sizeof(Model) + kMaxK * 8 + 257 * 8);
   b += 2 * (size_t)tiles * 4;

@@ -185,6 +185,13 @@ struct BlockG {
   __device__ static __forceinline__ void sync() { __syncthreads(); }
   __device__ static __forceinline__ bool any(bool p) { return __syncthreads_or(p) != 0; }
 };
+// Bits of the lanes below this one.
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
 struct WarpG {
   __device__ static __forceinline__ int tid() { return threadIdx.x & 31; }
   __device__ static __forceinline__ int size() { return 32; }
@@ -232,6 +239,90 @@ __device__ void group_sort(T* a, int n) {
 
 template <class T>
 __device__ __forceinline__ void block_sort(T* a, int n) { group_sort<BlockG, T>(a, n); }
+
+// LSD radix sort of a[0..n) (n <= 32*kSteps) by one warp, on 8-bit digits of
+// (key - min): a sample drawn from one subproblem spans a narrow range, so
+// few passes are needed (none when all keys are equal).  tmp holds n more
+// keys; cnt and peer are 256 words each, peer zero on entry and on exit.
+// Each pass is a stable counting sort; the in-warp rank of a key among the
+// keys of its step with the same digit comes from a shared OR of lane bits.
+template <int kSteps, class Ord>
+__device__ void warp_radix_sort(Ord* a, Ord* tmp, unsigned* cnt, unsigned* peer, int n) {
+  const int lane = threadIdx.x & 31;
+  Ord lo = ~(Ord)0, hi = 0;
+  for (int i = lane; i < n; i += 32) {
+    const Ord v = a[i];
+    lo = v < lo ? v : lo;
+    hi = v > hi ? v : hi;
+  }
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    const Ord l2 = __shfl_xor_sync(0xffffffffu, lo, o), h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+    lo = l2 < lo ? l2 : lo;
+    hi = h2 > hi ? h2 : hi;
+  }
+  const Ord range = hi - lo;
+  const int bits = range == 0 ? 0 : (int)(sizeof(Ord) * 8) - (sizeof(Ord) == 8 ? __clzll((long long)range) : __clz((int)range));
+  const int passes = (bits + 7) / 8;
+  Ord* src = a;
+  Ord* dst = tmp;
+  for (int p = 0; p < passes; ++p) {
+    const int shift = 8 * p;
+    for (int i = lane; i < 256; i += 32) cnt[i] = 0;
+    __syncwarp();
+    unsigned rk[kSteps];  // digit << 16 | rank among the equal digits before it
+#pragma unroll
+    for (int t = 0; t < kSteps; ++t) {
+      if (t * 32 < n) {
+        const int i = t * 32 + lane;
+        const bool valid = i < n;
+        const int d = valid ? (int)(((src[i] - lo) >> shift) & 255) : 0;
+        if (valid) atomicOr(&peer[d], 1u << lane);
+        __syncwarp();
+        const unsigned pm = valid ? peer[d] : 0u;
+        const int lt = __popc(pm & lanemask_lt());
+        const unsigned base = cnt[d];
+        rk[t] = ((unsigned)d << 16) | (base + (unsigned)lt);
+        __syncwarp();
+        if (valid && lt == 0) {
+          cnt[d] = base + (unsigned)__popc(pm);
+          peer[d] = 0u;
+        }
+        __syncwarp();
+      }
+    }
+    {  // exclusive scan of the 256 digit counts, 8 per lane
+      unsigned loc[8], sum = 0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) { loc[q] = cnt[lane * 8 + q]; sum += loc[q]; }
+      unsigned incl = sum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned x = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += x;
+      }
+      unsigned run = incl - sum;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) { cnt[lane * 8 + q] = run; run += loc[q]; }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int t = 0; t < kSteps; ++t) {
+      if (t * 32 < n) {
+        const int i = t * 32 + lane;
+        if (i < n) dst[cnt[rk[t] >> 16] + (rk[t] & 0xFFFFu)] = src[i];
+      }
+    }
+    __syncwarp();
+    Ord* sw = src;
+    src = dst;
+    dst = sw;
+  }
+  if (src != a) {
+    for (int i = lane; i < n; i += 32) a[i] = src[i];
+    __syncwarp();
+  }
+}
 
 // Warp-wide bitonic sort of up to 32 values (one per lane; absent lanes hold
 // the maximum value).  Returns this lane's value of the sorted sequence.
@@ -802,11 +893,6 @@ __device__ __forceinline__ bool reserve_tiles(LevelCtl* ctl, int32_t idx, Sub& s
   return true;
 }
 
-__device__ __forceinline__ unsigned lanemask_lt() {
-  unsigned m;
-  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-  return m;
-}
 
 // Lanes of the warp holding the same bucket id (0..255) as this lane, from
 // eight ballots (cheaper than a match instruction on this GPU); lanes with

@@ -53,14 +53,14 @@ struct Model {
 };
 
 // Model of a block-resident tail task as k_tail_fit leaves it: the linear
-// part, or (kind kSplitter) up to kTailSplit unique splitters built from the
-// same sorted sample; a splitter tree with more splitters is marked by
-// nsplit > kTailSplit and the task takes the slow path.
+// part, or (kind kSplitter) the unique splitters built from the same sorted
+// sample -- up to kTailSplit inline, more in slot `pool` of the splitter
+// pool (pool < 0: none was free, the task takes the slow path).
 constexpr int kTailSplit = 8;
 struct TailModel {
   LinModel l;
   int32_t nsplit;
-  int32_t pad;
+  int32_t pool;
   uint64_t split[kTailSplit];
 };
 
@@ -153,6 +153,7 @@ struct RunStatus {
   int64_t resident_keys;
   int64_t resident_groups;
   int64_t slow_tasks;
+  int64_t slow_passes;
 };
 
 // A range of the user buffer that needs the in-block recursion (a bucket
@@ -168,7 +169,14 @@ struct SlowTask {
 struct SlowCtl {
   int32_t count;
   uint32_t ticket;
+  int32_t pool_used;   // splitter-pool slots taken by this tail launch
+  int32_t pad;
 };
+
+// Splitters of a tail task whose tree has more than kTailSplit of them (one
+// pool slot per such task; a task that finds the pool full takes the slow
+// path).
+constexpr int kSplitPoolCap = 16384;
 
 // Per-level device arrays (all device pointers).
 struct LevelArgs {
@@ -234,6 +242,7 @@ struct ResidentArgs {
   SlowTask* slow;                  // slow list (capacity slow_cap)
   int32_t slow_cap;
   SlowCtl* slow_ctl;
+  uint64_t* split_pool;            // [kSplitPoolCap][128] splitters
   RunStatus* run;
   struct iplsTraceRecDev* trace;   // block-resident passes append here
   int64_t trace_cap;

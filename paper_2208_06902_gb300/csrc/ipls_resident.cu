@@ -2,9 +2,10 @@
 // independent buckets; Ch.4 IPLS), for subproblems of at most kResidentMax
 // keys.
 //
-//   k_tail_fit   one warp per subproblem: sample alpha*k-1 keys, sort them,
+//   k_tail_fit   one warp per subproblem: sample alpha*k-1 keys, sort them
+//                (warp radix sort on the few digits the sample's range needs),
 //                fit FMCD -- many fits in flight per SM hide the latency of
-//                the sorting network and of the binary64 steps.
+//                the sort and of the binary64 steps.
 //   k_tail       one block per task.  A fitted subproblem is read from HBM
 //                once, classified with its model, ranked stably per bucket
 //                and placed into shared memory in bucket order; each bucket
@@ -30,6 +31,12 @@ namespace ipls {
 constexpr int kRW = kResidentThreads / 32;  // warps
 constexpr int kRKPT = kResidentMax / kResidentThreads;
 constexpr int kFitWarps = 8;
+// k_tail_fit: sample sort by warp radix sort up to this many keys (every
+// tail task: n <= 8192 gives at most 664), bitonic network above
+constexpr int kRadixSteps = 22;
+constexpr int kRadixMax = 32 * kRadixSteps;
+constexpr int kFitSlot = 2 * kRadixMax;  // sample + radix buffer per warp
+static_assert(kFitSlot >= kResidentSample, "a warp's slot must also hold the largest sample");
 
 // ---------------------------------------------------------------------------
 // k_tail_fit
@@ -41,10 +48,12 @@ __global__ void __launch_bounds__(kFitWarps * 32) k_tail_fit(ResidentArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ FitShared fs[kFitWarps];
   __shared__ TailModel tm[kFitWarps];
+  __shared__ unsigned rcnt[kFitWarps][256], rpeer[kFitWarps][256];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = lane; i < 256; i += 32) rpeer[warp][i] = 0u;
   const int task = blockIdx.x * kFitWarps + warp;
   if (task >= a.nfit) return;
-  Ord* so = reinterpret_cast<Ord*>(smem_raw) + warp * kResidentSample;
+  Ord* so = reinterpret_cast<Ord*>(smem_raw) + warp * kFitSlot;
   const Group g = a.groups[a.fit_list[task]];
   int S = (int)sample_size(g.n, g.level, a.k, a.root_sample);
   if (S > kResidentSample) S = kResidentSample;  // never planned by the host
@@ -52,31 +61,52 @@ __global__ void __launch_bounds__(kFitWarps * 32) k_tail_fit(ResidentArgs a) {
   const typename T::Bits* src = reinterpret_cast<const typename T::Bits*>(a.buf[g.buf]) + g.off;
   for (int j = lane; j < S; j += 32) so[j] = T::ord(src[sample_offset(stream, j, g.n)]);
   __syncwarp();
-  group_sort<WarpG, Ord>(so, S);
+  if (S <= kRadixMax) warp_radix_sort<kRadixSteps>(so, so + kRadixMax, rcnt[warp], rpeer[warp], S);
+  else group_sort<WarpG, Ord>(so, S);
   TailModel& m = tm[warp];
   fit_linear<WarpG, K>(so, S, a.k, &m.l, fs[warp]);
-  if (lane == 0) m.nsplit = 0;
+  if (lane == 0) {
+    m.nsplit = 0;
+    m.pool = -1;
+  }
   __syncwarp();
   if (m.l.kind == kSplitter) {
     // splitter tree from the same sorted sample: (k-1)/2 equidistant sample
-    // keys, duplicates dropped (Ch.3 "Decision Trees"; equality buckets)
+    // keys, duplicates dropped (Ch.3 "Decision Trees"; equality buckets).
+    // First count them, then store them inline or in a pool slot.
     const int want = (a.k - 1) / 2;
     int cnt = 0;
     for (int base = 0; base < want; base += 32) {
       const int i = base + lane;
-      bool keep = false;
-      uint64_t u = 0;
-      if (i < want) {
-        u = (uint64_t)so[(int64_t)(i + 1) * S / (want + 1)];
-        keep = (i == 0) || (u != (uint64_t)so[(int64_t)i * S / (want + 1)]);
+      const bool keep = i < want && (i == 0 || so[(int64_t)(i + 1) * S / (want + 1)] !=
+                                                   so[(int64_t)i * S / (want + 1)]);
+      cnt += __popc(__ballot_sync(0xffffffffu, keep));
+    }
+    int slot = -1;
+    if (cnt > kTailSplit && lane == 0) {
+      slot = atomicAdd(&a.slow_ctl->pool_used, 1);
+      if (slot >= kSplitPoolCap) slot = -1;
+    }
+    slot = __shfl_sync(0xffffffffu, slot, 0);
+    uint64_t* out = cnt <= kTailSplit ? m.split : (slot >= 0 ? a.split_pool + (size_t)slot * 128 : nullptr);
+    if (out) {
+      int pos0 = 0;
+      for (int base = 0; base < want; base += 32) {
+        const int i = base + lane;
+        bool keep = false;
+        uint64_t u = 0;
+        if (i < want) {
+          u = (uint64_t)so[(int64_t)(i + 1) * S / (want + 1)];
+          keep = (i == 0) || (u != (uint64_t)so[(int64_t)i * S / (want + 1)]);
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        if (keep) out[pos0 + __popc(bal & lanemask_lt())] = u;
+        pos0 += __popc(bal);
       }
-      const unsigned bal = __ballot_sync(0xffffffffu, keep);
-      const int pos = cnt + __popc(bal & lanemask_lt());
-      if (keep && pos < kTailSplit) m.split[pos] = u;
-      cnt += __popc(bal);
     }
     if (lane == 0) {
       m.nsplit = cnt;
+      m.pool = slot;
       m.l.nb = 2 * cnt + 1;
       m.l.fast = 0;
     }
@@ -214,7 +244,8 @@ __device__ __forceinline__ void warp_counts_to_offsets(ResSmem<K>& sh) {
 }
 
 // Base-cases every pending small range of the slow path (warp bitonic up to
-// 32 keys, block network above).
+// 32 keys in registers, above that one warp's bitonic network in shared
+// memory per range).
 template <class K>
 __device__ void flush_small(ResSmem<K>& sh) {
   using Ord = typename KT<K>::Ord;
@@ -229,10 +260,10 @@ __device__ void flush_small(ResSmem<K>& sh) {
     v = warp_sort32(v);
     if (lane < len) sh.keys[st + lane] = v;
   }
-  __syncthreads();
-  for (int q = 0; q < ns; ++q) {
+  // larger ranges (up to the cutoff): one warp each, many at a time
+  for (int q = warp; q < ns; q += kRW) {
     const unsigned long long e = sh.u.s.tasks[q];
-    if (task_len(e) > 32) block_sort(sh.keys + task_start(e), task_len(e));
+    if (task_len(e) > 32) group_sort<WarpG>(sh.keys + task_start(e), task_len(e));
   }
   __syncthreads();
   if (threadIdx.x == 0) sh.nsmall = 0;
@@ -321,6 +352,7 @@ __device__ void resident_pass(ResSmem<K>& sh, const ResidentArgs& a, int64_t gof
   trace_pass(sh, a, goff + s0, c, level, m);
   if (threadIdx.x == 0) {
     atomicAdd((unsigned long long*)&a.run->resident_passes, 1ULL);
+    atomicAdd((unsigned long long*)&a.run->slow_passes, 1ULL);
     if (m.l.kind == kSplitter) atomicAdd((unsigned long long*)&a.run->resident_fallback, 1ULL);
   }
   // children (equality buckets of the splitter tree are homogeneous: done;
@@ -379,6 +411,7 @@ __global__ void __launch_bounds__(kResidentThreads, 2) k_slow(ResidentArgs a) {
     const int i = s_i;
     if (i >= a.slow_ctl->count || i >= a.slow_cap) break;
     const SlowTask st = a.slow[i];
+    if (threadIdx.x == 0) atomicAdd((unsigned long long*)&a.run->slow_tasks, 1ULL);
     Bits* src = keys + st.off;
     for (int p = threadIdx.x; p < st.n; p += blockDim.x) sh.keys[p] = T::ord(src[p]);
     if (threadIdx.x == 0) {
@@ -407,6 +440,7 @@ struct TailSmem {
   int tot[kMaxK];
   int hom[kMaxK];
   TailModel tm;
+  uint64_t split[128];   // a tree too large for the record, from the pool
   int slow_all;
   long long rec;
 };
@@ -443,8 +477,16 @@ __global__ void __launch_bounds__(kResidentThreads, 2) k_tail(ResidentArgs a) {
     __syncthreads();
     split_tree = sh.tm.l.kind == kSplitter;
     const int nsplit = sh.tm.nsplit;
-    // a splitter tree too large for the tail record recurses in k_slow
-    bool slow = split_tree && nsplit > kTailSplit;
+    // a large splitter tree comes from its pool slot; without one the task
+    // recurses in k_slow
+    bool slow = split_tree && nsplit > kTailSplit && sh.tm.pool < 0;
+    const uint64_t* splits = sh.tm.split;
+    if (split_tree && nsplit > kTailSplit && !slow) {
+      for (int i = threadIdx.x; i < nsplit; i += blockDim.x)
+        sh.split[i] = a.split_pool[(size_t)sh.tm.pool * 128 + i];
+      __syncthreads();
+      splits = sh.split;
+    }
     if (!slow) {
       Classifier<K> cls;
       cls.load(sh.tm.l, a.exact_only);
@@ -465,7 +507,7 @@ __global__ void __launch_bounds__(kResidentThreads, 2) k_tail(ResidentArgs a) {
           const int i = warp * chunk + j * 32 + lane;
           int bk = kMaxK;
           if (i < n) {
-            bk = split_tree ? splitter_bucket((uint64_t)T::ord(v[j]), sh.tm.split, nsplit)
+            bk = split_tree ? splitter_bucket((uint64_t)T::ord(v[j]), splits, nsplit)
                             : cls.bucket_or_defer(v[j]);
             if (bk < 0) dmask |= 1u << j;
           }
@@ -661,7 +703,7 @@ cudaError_t launch_tail_fit(const ResidentArgs& a, cudaStream_t s) {
   if (a.nfit <= 0) return cudaSuccess;
   return by_dtype_r(a.dtype, [&](auto* tag) {
     using K = std::remove_pointer_t<decltype(tag)>;
-    const size_t smem = (size_t)kFitWarps * kResidentSample * sizeof(typename KT<K>::Ord);
+    const size_t smem = (size_t)kFitWarps * kFitSlot * sizeof(typename KT<K>::Ord);
     cudaFuncSetAttribute(k_tail_fit<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int blocks = (a.nfit + kFitWarps - 1) / kFitWarps;
     k_tail_fit<K><<<blocks, kFitWarps * 32, smem, s>>>(a);
