@@ -59,6 +59,11 @@ def parse():
     p.add_argument("--profile-stats", metavar="JSON",
                    help="profiling run: sort W+K arrays, write the per-kernel launches and "
                         "algorithmic bytes of ALL of them to JSON, print no bench line")
+    p.add_argument("--workload", default="single", choices=["single", "segmented"],
+                   help="single: the 2^28 arrays (headline); segmented: a batch of "
+                        "200,000 uneven segments in one call vs one call per segment")
+    p.add_argument("--segments", type=int, default=200_000)
+    p.add_argument("--tuned", metavar="JSON", help="autotuner table; picks k and cutoff")
     p.add_argument("--ingest-ncu", nargs=2, metavar=("CSV", "STATS_JSON"),
                    help="write profiles/ncu_traffic.json from an ncu --csv launch list with "
                         "dram__bytes_{read,write}.sum of a --profile-stats run and its JSON")
@@ -430,12 +435,91 @@ def run_gb300(args):
     return 0
 
 
+def run_segmented(args):
+    """Batched segmented sort: segment sizes LogNormal(median 2048, sigma 1.5)
+    clamped to [16, 4,194,304], rescaled so they sum to about 2^log2n keys,
+    each segment from one of nine distributions; one iplsSortSegmented call
+    against one iplsSort call per segment on the same keys. Both outputs are
+    compared bit for bit."""
+    import numpy as np
+    import torch
+
+    import datagen
+    torch.cuda.set_device(0)
+    import paper_2208_06902_gb300 as ipls
+    ipls.load()
+    dev = torch.device("cuda", 0)
+    sizes = datagen.segment_sizes(args.segments)
+    scale = (1 << args.log2n) / float(sizes.sum())
+    sizes = np.maximum(np.rint(sizes * scale), 16).astype(np.int64)
+    keys, offsets, _ = datagen.segmented(sizes)
+    n = int(offsets[-1])
+    k, cutoff = 256, args.cutoff
+    if args.tuned:
+        from paper_2208_06902_gb300 import autotune
+        cfg = autotune.tuned_config(int(np.median(sizes)), ipls.F64, autotune.load(args.tuned))
+        k, cutoff = cfg["k"], cfg["cutoff"]
+    src = torch.from_numpy(keys.view(np.uint8)).to(dev)
+    off = torch.from_numpy(offsets).to(dev)
+    work = torch.empty_like(src)
+    stream = torch.cuda.current_stream()
+    ctx = ipls.Context(k=k, cutoff=cutoff, stream=stream)
+
+    def batch():
+        work.copy_(src)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ipls.iplsSortSegmented(ctx.ctx, work.data_ptr(), off.data_ptr(), sizes.size, ipls.F64)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b)
+
+    for _ in range(args.warmup):
+        batch()
+    t_batch = [batch() for _ in range(args.steps)]
+    got = work.clone()
+    # one plain call per segment (the same context, kernels and parameters)
+    work.copy_(src)
+    torch.cuda.synchronize()
+    base = work.data_ptr()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for i in range(sizes.size):
+        ctx.sort_ptr(base + int(offsets[i]) * 8, int(sizes[i]), ipls.F64)
+    b.record(stream)
+    torch.cuda.synchronize()
+    t_each = a.elapsed_time(b)
+    same = bool(torch.equal(got, work))
+    ms = statistics.median(t_batch)
+    line = {"metric": "Gkeys/s, segmented batch sort (one call, all segments)",
+            "value": round(n / (ms * 1e-3) / 1e9, 4), "unit": "Gkeys/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"{sizes.size} segments, {n} f64 keys in total",
+                       "sizes": "LogNormal(median 2048, sigma 1.5) clamped to [16, 4194304], "
+                                f"rescaled to sum ~2^{args.log2n}",
+                       "median_segment": int(np.median(sizes)), "max_segment": int(sizes.max()),
+                       "k": k, "cutoff": cutoff, "tuned": bool(args.tuned)},
+            "per_segment_calls": {"value": round(n / (t_each * 1e-3) / 1e9, 4), "unit": "Gkeys/s",
+                                  "ms": round(t_each, 1), "calls": int(sizes.size)},
+            "speedup_vs_per_segment": round(t_each / ms, 2),
+            "outputs_identical": same}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0 if same else 1
+
+
 def main():
     args = parse()
     if args.ingest_ncu:
         return ingest_ncu(*args.ingest_ncu)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "segmented":
+        return run_segmented(args)
     return run_gb300(args)
 
 

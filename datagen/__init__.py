@@ -67,6 +67,8 @@ def _load():
         c = ctypes
         L.datagen_fill.argtypes = [c.c_int, c.c_int, c.c_int64, c.c_uint64, c.c_double,
                                    c.c_int64, c.c_int64, c.c_int64, c.c_void_p, c.c_int]
+        L.datagen_fill_segments.argtypes = [c.c_void_p, c.c_int64, c.c_void_p, c.c_uint64, c.c_int,
+                                            c.c_void_p, c.c_int]
         _lib = L
     return _lib
 
@@ -131,7 +133,11 @@ def segmented(sizes: np.ndarray, seed: int = 4, dtype=np.float64):
     keys = np.empty(int(offsets[-1]), np.dtype(dtype))
     pick = generate("raw64", sizes.size, np.uint64, seed ^ 0xabcdef)
     dist_ix = (pick % np.uint64(len(NINE))).astype(np.int64)
-    for s in range(sizes.size):
-        a, b = int(offsets[s]), int(offsets[s + 1])
-        generate(NINE[dist_ix[s]], b - a, dtype, seed * 1_000_003 + s, out=keys[a:b])
+    codes = np.array([DISTS[NINE[i]] for i in dist_ix], np.int32)
+    rc = _load().datagen_fill_segments(offsets.ctypes.data_as(ctypes.c_void_p), sizes.size,
+                                       codes.ctypes.data_as(ctypes.c_void_p), seed & (2**64 - 1),
+                                       _T[np.dtype(dtype)], keys.ctypes.data_as(ctypes.c_void_p),
+                                       _threads())
+    if rc != 0:
+        raise ValueError("datagen: bad segment arguments")
     return keys, offsets, dist_ix

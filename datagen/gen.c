@@ -182,3 +182,72 @@ int datagen_fill(int dist, int dtype, int64_t n, uint64_t seed, double zipf_s,
   free(cdf);
   return 0;
 }
+
+/* Job of one whole stream (a segment): the same keys datagen_fill gives for
+ * [0, n) with this seed. */
+static void init_job(Job* j, int dist, int dtype, int64_t n, uint64_t seed, const double* cdf,
+                     int64_t zipf_n, void* out) {
+  memset(j, 0, sizeof(*j));
+  j->dist = dist; j->dtype = dtype; j->n = n; j->seed = seed;
+  j->zipf_s = 0.75; j->zipf_n = zipf_n; j->zipf_cdf = cdf; j->out = out;
+  j->lo = 0; j->hi = n;
+  if (dist == G_MIXGAUSS) {
+    uint64_t ps = mix64(seed + 0x6a09e667f3bcc909ULL);
+    for (int c = 0; c < 5; ++c) {
+      j->mu[c] = -100.0 + 200.0 * unit01(draw(ps, 2 * c));
+      j->sd[c] = 1.0 + 9.0 * unit01(draw(ps, 2 * c + 1));
+    }
+  }
+}
+
+typedef struct {
+  const int64_t* offsets;
+  const int32_t* dist;
+  int64_t s0, s1;
+  uint64_t seed;
+  int dtype;
+  const double* cdf;
+  void* out;
+} SegJob;
+
+static void* run_segments(void* arg) {
+  const SegJob* sj = (const SegJob*)arg;
+  const int64_t w = (sj->dtype == T_F64 || sj->dtype == T_U64) ? 8 : 4;
+  for (int64_t s = sj->s0; s < sj->s1; ++s) {
+    const int64_t a = sj->offsets[s], n = sj->offsets[s + 1] - a;
+    if (n <= 0) continue;
+    Job j;
+    init_job(&j, sj->dist[s], sj->dtype, n, sj->seed * 1000003ULL + (uint64_t)s, sj->cdf, 1000000,
+             (char*)sj->out + a * w);
+    run(&j);
+  }
+  return 0;
+}
+
+/* Segment s of a batch: keys [offsets[s], offsets[s+1]) from distribution
+ * dist[s] with stream seed seed*1000003+s (Zipf with s=0.75 over 1..1e6), i.e.
+ * what datagen_fill gives for the whole segment.  Segments are shared out
+ * over threads; the keys do not depend on the thread count. */
+int datagen_fill_segments(const int64_t* offsets, int64_t nseg, const int32_t* dist, uint64_t seed,
+                          int dtype, void* out, int threads) {
+  if (nseg < 0) return -1;
+  for (int64_t s = 0; s < nseg; ++s)
+    if (dist[s] < 0 || dist[s] > G_RAW64 || offsets[s + 1] < offsets[s]) return -1;
+  double* cdf = zipf_table(0.75, 1000000);
+  if (!cdf) return -1;
+  if (threads < 1) threads = 1;
+  if (threads > 256) threads = 256;
+  pthread_t tid[256];
+  SegJob jobs[256];
+  for (int t = 0; t < threads; ++t) {
+    jobs[t].offsets = offsets; jobs[t].dist = dist; jobs[t].seed = seed; jobs[t].dtype = dtype;
+    jobs[t].cdf = cdf; jobs[t].out = out;
+    jobs[t].s0 = nseg * t / threads;
+    jobs[t].s1 = nseg * (t + 1) / threads;
+  }
+  for (int t = 0; t < threads; ++t)
+    if (threads == 1 || pthread_create(&tid[t], 0, run_segments, &jobs[t]) != 0) { run_segments(&jobs[t]); tid[t] = 0; }
+  for (int t = 0; t < threads; ++t) if (tid[t]) pthread_join(tid[t], 0);
+  free(cdf);
+  return 0;
+}
