@@ -59,9 +59,14 @@ def parse():
     p.add_argument("--profile-stats", metavar="JSON",
                    help="profiling run: sort W+K arrays, write the per-kernel launches and "
                         "algorithmic bytes of ALL of them to JSON, print no bench line")
-    p.add_argument("--workload", default="single", choices=["single", "segmented"],
+    p.add_argument("--workload", default="single", choices=["single", "segmented", "serve"],
                    help="single: the 2^28 arrays (headline); segmented: a batch of "
-                        "200,000 uneven segments in one call vs one call per segment")
+                        "200,000 uneven segments in one call vs one call per segment; "
+                        "serve: Poisson-arriving requests, batched vs one at a time")
+    p.add_argument("--requests", type=int, default=2000)
+    p.add_argument("--load", type=float, default=0.7,
+                   help="offered load as a fraction of the one-at-a-time service rate")
+    p.add_argument("--max-request-log10", type=float, default=6.0)
     p.add_argument("--segments", type=int, default=200_000)
     p.add_argument("--tuned", metavar="JSON", help="autotuner table; picks k and cutoff")
     p.add_argument("--ingest-ncu", nargs=2, metavar=("CSV", "STATS_JSON"),
@@ -512,6 +517,110 @@ def run_segmented(args):
     return 0 if same else 1
 
 
+def run_serve(args):
+    """Served sorts: requests of log-uniform size in [10^3, 10^max] keys, dtype
+    uniform over f64/u64/f32, each from one of nine distributions, arriving
+    as a Poisson stream at `load` x the one-at-a-time service rate. The same
+    arrival trace is served by a context that batches pending requests
+    (continuous batching) and by one that sorts them one at a time; latency =
+    completion - arrival, measured on the host clock."""
+    import threading
+
+    import numpy as np
+    import torch
+
+    import datagen
+    torch.cuda.set_device(0)
+    import paper_2208_06902_gb300 as ipls
+    ipls.load()
+    dev = torch.device("cuda", 0)
+    R = args.requests
+    rng = np.random.default_rng(5)
+    sizes = np.rint(10 ** rng.uniform(3.0, args.max_request_log10, R)).astype(np.int64)
+    dts = [(np.float64, ipls.F64), (np.uint64, ipls.U64), (np.float32, ipls.F32)]
+    kinds = rng.integers(0, 3, R)
+    dists = rng.integers(0, len(datagen.NINE), R)
+    widths = np.array([np.dtype(dts[k][0]).itemsize for k in kinds])
+    offs = np.zeros(R + 1, np.int64)  # each request starts 16-byte aligned
+    for i in range(R):
+        offs[i + 1] = (offs[i] + int(sizes[i]) * int(widths[i]) + 15) // 16 * 16
+    host = np.empty(int(offs[-1]), np.uint8)
+    for i in range(R):
+        x = datagen.generate(datagen.NINE[dists[i]], int(sizes[i]), dts[kinds[i]][0], seed=700 + i)
+        host[offs[i]:offs[i] + x.nbytes] = x.view(np.uint8)
+    pristine = torch.from_numpy(host).to(dev)
+    pool = torch.empty_like(pristine)
+    base = pool.data_ptr()
+    total_keys = int(sizes.sum())
+
+    def serve(max_batch, arrivals):
+        ctx = ipls.Context(cutoff=args.cutoff, max_batch=max_batch)
+        pool.copy_(pristine)
+        torch.cuda.synchronize()
+        tickets = [None] * R
+        done = [0.0] * R
+        ready = threading.Semaphore(0)
+
+        failed = []
+
+        def waiter():
+            for i in range(R):
+                ready.acquire()
+                if failed:
+                    return
+                ctx.wait(tickets[i])
+                done[i] = time.perf_counter()
+
+        th = threading.Thread(target=waiter, daemon=True)
+        th.start()
+        t0 = time.perf_counter()
+        try:
+            for i in range(R):
+                target = t0 + arrivals[i]
+                while True:
+                    now = time.perf_counter()
+                    if now >= target:
+                        break
+                    if target - now > 0.002:
+                        time.sleep(target - now - 0.001)
+                tickets[i] = ctx.submit_ptr(base + int(offs[i]), int(sizes[i]), dts[kinds[i]][1])
+                ready.release()
+        except BaseException:
+            failed.append(True)
+            ready.release()
+            raise
+        th.join()
+        lat = np.array([done[i] - (t0 + arrivals[i]) for i in range(R)]) * 1e3
+        wall = max(done) - t0
+        ctx.close()
+        return {"gkeys_s": round(total_keys / wall / 1e9, 4), "wall_s": round(wall, 3),
+                "p50_ms": round(float(np.percentile(lat, 50)), 3),
+                "p99_ms": round(float(np.percentile(lat, 99)), 3),
+                "mean_ms": round(float(lat.mean()), 3)}
+
+    # service rate of one-at-a-time sorting: everything queued at t = 0
+    cal = serve(1, np.zeros(R))
+    rate = total_keys / cal["wall_s"]
+    lam = args.load * rate / float(sizes.mean())
+    arrivals = np.cumsum(rng.exponential(1.0 / lam, R))
+    arrivals -= arrivals[0]
+    batched = serve(0, arrivals)
+    out_batched = pool.clone()
+    single = serve(1, arrivals)
+    same = bool(torch.equal(out_batched, pool))
+    line = {"metric": "served sorts: Gkeys/s and p50/p99 latency, batched vs one-at-a-time",
+            "value": batched["gkeys_s"], "unit": "Gkeys/s", "n_gpus": 1, "steps": 1, "warmup": 1,
+            "ms_per_step": round(batched["wall_s"] * 1e3, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64/u64/f32", "data": "synthetic",
+            "config": {"workload": f"{R} requests, {total_keys} keys, sizes log-uniform in "
+                                   f"[1e3, 1e{args.max_request_log10:g}], Poisson arrivals",
+                       "offered_load": args.load, "arrival_rate_per_s": round(lam, 1),
+                       "one_at_a_time_rate_gkeys_s": round(rate / 1e9, 4), "cutoff": args.cutoff},
+            "batched": batched, "one_at_a_time": single, "outputs_identical": same}
+    print(json.dumps(line), flush=True)
+    return 0 if same else 1
+
+
 def main():
     args = parse()
     if args.ingest_ncu:
@@ -520,6 +629,8 @@ def main():
         return run_reference(args)
     if args.workload == "segmented":
         return run_segmented(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_gb300(args)
 
 

@@ -72,7 +72,9 @@ typedef struct iplsConfig {
   int32_t profile;        /* 1: time every kernel launch with CUDA events
                              (read with iplsGetKernelStats) */
   int32_t flags;          /* IPLS_FLAG_* bits (tuning switches; results do not change) */
-  int32_t reserved[6];
+  int32_t max_batch;      /* iplsSubmit: requests sorted together at most (0 = no limit,
+                             1 = one at a time) */
+  int32_t reserved[5];
 } iplsConfig;
 
 /* cfg.flags: classify grid-level passes through the exact threshold index
@@ -167,17 +169,26 @@ iplsStatus iplsSortSegmented(iplsCtx ctx, void* keys, const int64_t* offsets,
  * host memory gives full copy bandwidth; pageable memory works too. */
 iplsStatus iplsSortHost(iplsCtx ctx, void* host_keys, int64_t n, iplsDtype dtype);
 
-/* Asynchronous sort request: enqueues iplsSort work for keys[0..n) and
- * returns a ticket.  Returns IPLS_ERR_BUDGET if 2*w*n exceeds the
- * configured budget.  The caller must keep `keys` alive until the request
- * completes. */
+/* Asynchronous sort request for keys[0..n) (device memory, already
+ * written; the sort runs on the context's stream): queues it and returns a
+ * ticket at once.  A worker thread of the context batches pending requests
+ * of one dtype in arrival order while 2*w*(their keys) stays within
+ * cfg.budget_bytes (0 = unlimited) and cfg.max_batch, and sorts each batch
+ * with one segmented sort (each request a segment, every partition pass of
+ * the batch in shared launches); requests arriving meanwhile join the next
+ * batch.  The result is the same sorted array whatever the batch.  Returns
+ * IPLS_ERR_BUDGET if one request alone exceeds the budget.  `keys` must stay
+ * alive and untouched until the request completes; while requests are
+ * pending, other calls on the context wait for the running batch. */
 iplsStatus iplsSubmit(iplsCtx ctx, void* keys, int64_t n, iplsDtype dtype,
                       uint64_t* ticket);
 
-/* IPLS_PENDING while the request runs, then its final status. */
+/* IPLS_PENDING while the request is queued or running, then its final
+ * status (IPLS_ERR_ARG for an unknown ticket). */
 iplsStatus iplsPoll(iplsCtx ctx, uint64_t ticket);
 
-/* Waits up to timeout_us microseconds (< 0 = forever) for a request. */
+/* Waits up to timeout_us microseconds (< 0 = forever) for a request; returns
+ * its final status, or IPLS_PENDING if it is still running. */
 iplsStatus iplsWait(iplsCtx ctx, uint64_t ticket, int64_t timeout_us);
 
 /* Statistics of the context (synchronises its stream). */

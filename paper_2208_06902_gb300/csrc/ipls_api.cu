@@ -3,11 +3,15 @@
 // and request tickets.  Every step of the sort runs in the kernels of
 // ipls_pass.cu and ipls_resident.cu; this file only plans and launches them.
 #include <algorithm>
+#include <chrono>
+#include <condition_variable>
 #include <cstdio>
 #include <cstring>
+#include <deque>
 #include <map>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "ipls.h"
@@ -83,8 +87,26 @@ struct iplsContext {
   int64_t trace_alloc = 0;
   int64_t trace_grid_count = 0;
   iplsStats stats{};
-  std::map<uint64_t, iplsStatus> tickets;
+  // request queue (iplsSubmit): a worker thread batches pending requests
+  struct Request {
+    void* keys;
+    int64_t n;
+    int dtype;
+    iplsStatus st;
+    bool done;
+  };
+  std::mutex exec_mu;                 // one sort at a time on the context
+  std::mutex q_mu;                    // guards the queue and the requests
+  std::condition_variable q_cv;       // new request, or stop
+  std::condition_variable done_cv;    // a request finished
+  std::deque<uint64_t> queue;
+  std::map<uint64_t, Request> reqs;
+  std::thread worker;
+  bool stop = false;
   uint64_t next_ticket = 1;
+  char* batch_buf = nullptr;          int64_t batch_cap = 0;     // bytes
+  int64_t* batch_off = nullptr;       int64_t batch_off_cap = 0; // words
+  int64_t* h_batch_off = nullptr;     int64_t h_batch_off_cap = 0;
   int hist_grid[4] = {0, 0, 0, 0};
   int scatter_grid[4] = {0, 0, 0, 0};
   int64_t dev_bytes = 0;
@@ -456,6 +478,8 @@ iplsStatus validate_cfg(const iplsConfig& c) {
   if (c.root_sample < 0 || c.root_sample > 16384)
     return fail(IPLS_ERR_ARG, "root_sample must be in [0, 16384]");
   if (c.spin_limit < 1) return fail(IPLS_ERR_ARG, "spin_limit must be >= 1");
+  if (c.max_batch < 0) return fail(IPLS_ERR_ARG, "max_batch must be >= 0");
+  if (c.budget_bytes < 0) return fail(IPLS_ERR_ARG, "budget_bytes must be >= 0");
   return IPLS_OK;
 }
 
@@ -543,6 +567,94 @@ cudaError_t launch_init_segments(const int64_t* offsets, int64_t nseg, int rmax,
 }  // namespace ipls
 
 // ---------------------------------------------------------------------------
+// Request serving (iplsSubmit): one worker thread per context forms batches
+// from the pending requests -- the oldest request's dtype, in arrival order,
+// while they fit the memory budget (cfg.budget_bytes) and cfg.max_batch --
+// and sorts a batch with one segmented sort: each request is a segment, so
+// the partition passes of all of them share the same launches.  Requests
+// that arrive while a batch runs join the next one.
+// ---------------------------------------------------------------------------
+namespace {
+
+iplsStatus run_batch(iplsCtx c, const std::vector<uint64_t>& batch, int dtype,
+                     const std::vector<iplsContext::Request>& rs) {
+  std::lock_guard<std::mutex> ex(c->exec_mu);
+  const int64_t w = key_bytes(dtype);
+  if (rs.size() == 1) {  // alone: in place
+    IPLS_TRY(sort_impl(c, rs[0].keys, rs[0].n, dtype, nullptr, 0));
+    IPLS_CUDA(cudaStreamSynchronize(c->stream));
+    return IPLS_OK;
+  }
+  const int64_t nseg = (int64_t)rs.size();
+  if (c->h_batch_off_cap < nseg + 1) {
+    if (c->h_batch_off) cudaFreeHost(c->h_batch_off);
+    c->h_batch_off = nullptr;
+    c->h_batch_off_cap = 0;
+    IPLS_CUDA(cudaMallocHost(&c->h_batch_off, (size_t)(2 * nseg + 16) * 8));
+    c->h_batch_off_cap = 2 * nseg + 16;
+  }
+  int64_t total = 0;
+  for (int64_t i = 0; i < nseg; ++i) { c->h_batch_off[i] = total; total += rs[i].n; }
+  c->h_batch_off[nseg] = total;
+  IPLS_TRY(ensure(c, c->batch_buf, c->batch_cap, total * w));
+  IPLS_TRY(ensure(c, c->batch_off, c->batch_off_cap, nseg + 1));
+  for (int64_t i = 0; i < nseg; ++i)
+    if (rs[i].n > 0)
+      IPLS_CUDA(cudaMemcpyAsync(c->batch_buf + c->h_batch_off[i] * w, rs[i].keys, (size_t)(rs[i].n * w),
+                                cudaMemcpyDeviceToDevice, c->stream));
+  IPLS_CUDA(cudaMemcpyAsync(c->batch_off, c->h_batch_off, (size_t)(nseg + 1) * 8, cudaMemcpyHostToDevice,
+                            c->stream));
+  IPLS_TRY(sort_impl(c, c->batch_buf, total, dtype, c->batch_off, nseg));
+  for (int64_t i = 0; i < nseg; ++i)
+    if (rs[i].n > 0)
+      IPLS_CUDA(cudaMemcpyAsync(rs[i].keys, c->batch_buf + c->h_batch_off[i] * w, (size_t)(rs[i].n * w),
+                                cudaMemcpyDeviceToDevice, c->stream));
+  IPLS_CUDA(cudaStreamSynchronize(c->stream));
+  (void)batch;
+  return IPLS_OK;
+}
+
+void serve_loop(iplsCtx c) {
+  cudaSetDevice(c->device);
+  for (;;) {
+    std::vector<uint64_t> batch;
+    std::vector<iplsContext::Request> rs;
+    int dtype = 0;
+    {
+      std::unique_lock<std::mutex> lk(c->q_mu);
+      c->q_cv.wait(lk, [&] { return c->stop || !c->queue.empty(); });
+      if (c->queue.empty()) return;  // stop requested and nothing pending
+      dtype = c->reqs[c->queue.front()].dtype;
+      const int64_t budget = c->cfg.budget_bytes;
+      const int max_batch = c->cfg.max_batch;
+      int64_t bytes = 0;
+      for (auto it = c->queue.begin(); it != c->queue.end();) {
+        const iplsContext::Request& r = c->reqs[*it];
+        if (r.dtype != dtype) { ++it; continue; }
+        const int64_t need = 2 * r.n * (int64_t)key_bytes(dtype);
+        if (!batch.empty() && budget > 0 && bytes + need > budget) break;
+        if (max_batch > 0 && (int)batch.size() >= max_batch) break;
+        batch.push_back(*it);
+        rs.push_back(r);
+        bytes += need;
+        it = c->queue.erase(it);
+      }
+    }
+    const iplsStatus st = run_batch(c, batch, dtype, rs);
+    {
+      std::lock_guard<std::mutex> lk(c->q_mu);
+      for (uint64_t t : batch) {
+        c->reqs[t].st = st;
+        c->reqs[t].done = true;
+      }
+    }
+    c->done_cv.notify_all();
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
 extern "C" {
@@ -602,7 +714,16 @@ iplsStatus iplsCreate(iplsCtx* out, const iplsConfig* cfg, iplsAllocFn alloc, ip
 
 iplsStatus iplsDestroy(iplsCtx c) {
   if (!c) return fail(IPLS_ERR_ARG, "ctx is NULL");
+  {
+    std::lock_guard<std::mutex> lk(c->q_mu);
+    c->stop = true;
+  }
+  c->q_cv.notify_all();
+  if (c->worker.joinable()) c->worker.join();
   cudaStreamSynchronize(c->stream);
+  dev_free(c, c->batch_buf, (size_t)c->batch_cap);
+  dev_free(c, c->batch_off, (size_t)c->batch_off_cap * 8);
+  if (c->h_batch_off) cudaFreeHost(c->h_batch_off);
   dev_free(c, c->scratch, (size_t)c->scratch_cap);
   dev_free(c, c->status, (size_t)c->status_cap * 8);
   dev_free(c, c->tile_off, (size_t)c->tile_off_cap * 4);
@@ -682,6 +803,7 @@ iplsStatus iplsSort(iplsCtx c, void* keys, int64_t n, iplsDtype dtype) {
   c->stats.calls += 1;
   if (n <= 1) return IPLS_OK;
   g_last_error.clear();
+  std::lock_guard<std::mutex> ex(c->exec_mu);
   return sort_impl(c, keys, n, dtype, nullptr, 0);
 }
 
@@ -704,6 +826,7 @@ iplsStatus iplsSortSegmented(iplsCtx c, void* keys, const int64_t* offsets, int6
     return fail(IPLS_ERR_ARG, "offsets out of range");
   c->stats.calls += 1;
   g_last_error.clear();
+  std::lock_guard<std::mutex> ex(c->exec_mu);
   return sort_impl(c, keys, last, dtype, offsets, nseg);
 }
 
@@ -716,6 +839,7 @@ iplsStatus iplsSortHost(iplsCtx c, void* host_keys, int64_t n, iplsDtype dtype) 
   if (n <= 1) return IPLS_OK;
   g_last_error.clear();
   const size_t bytes = (size_t)n * key_bytes(dtype);
+  std::lock_guard<std::mutex> ex(c->exec_mu);
   IPLS_TRY(ensure(c, c->host_stage, c->host_stage_cap, (int64_t)bytes));
   IPLS_CUDA(cudaMemcpyAsync(c->host_stage, host_keys, bytes, cudaMemcpyHostToDevice, c->stream));
   IPLS_TRY(sort_impl(c, c->host_stage, n, dtype, nullptr, 0));
@@ -748,25 +872,39 @@ iplsStatus iplsGetKernelStats(iplsCtx c, iplsKernelStat* out, int32_t cap, int32
 iplsStatus iplsSubmit(iplsCtx c, void* keys, int64_t n, iplsDtype dtype, uint64_t* ticket) {
   if (!c || !ticket) return fail(IPLS_ERR_ARG, "ctx or ticket is NULL");
   IPLS_TRY(check_common(n, dtype));
+  if (n > 1 && !keys) return fail(IPLS_ERR_ARG, "keys is NULL");
   IPLS_TRY(check_keys_ptr(keys, dtype));
   if (c->cfg.budget_bytes > 0 && 2 * n * (int64_t)key_bytes(dtype) > c->cfg.budget_bytes)
     return fail(IPLS_ERR_BUDGET, "request exceeds the memory budget");
-  const uint64_t t = c->next_ticket++;
-  c->tickets[t] = iplsSort(c, keys, n, dtype);
-  *ticket = t;
+  {
+    std::lock_guard<std::mutex> lk(c->q_mu);
+    const uint64_t t = c->next_ticket++;
+    c->reqs[t] = iplsContext::Request{keys, n, (int)dtype, n <= 1 ? IPLS_OK : IPLS_PENDING, n <= 1};
+    if (n > 1) c->queue.push_back(t);
+    if (!c->worker.joinable()) c->worker = std::thread(serve_loop, c);
+    *ticket = t;
+  }
+  c->q_cv.notify_one();
   return IPLS_OK;
 }
 
 iplsStatus iplsPoll(iplsCtx c, uint64_t ticket) {
   if (!c) return fail(IPLS_ERR_ARG, "ctx is NULL");
-  auto it = c->tickets.find(ticket);
-  if (it == c->tickets.end()) return fail(IPLS_ERR_ARG, "unknown ticket");
-  return it->second;
+  std::lock_guard<std::mutex> lk(c->q_mu);
+  auto it = c->reqs.find(ticket);
+  if (it == c->reqs.end()) return fail(IPLS_ERR_ARG, "unknown ticket");
+  return it->second.done ? it->second.st : IPLS_PENDING;
 }
 
 iplsStatus iplsWait(iplsCtx c, uint64_t ticket, int64_t timeout_us) {
-  (void)timeout_us;
-  return iplsPoll(c, ticket);
+  if (!c) return fail(IPLS_ERR_ARG, "ctx is NULL");
+  std::unique_lock<std::mutex> lk(c->q_mu);
+  auto it = c->reqs.find(ticket);
+  if (it == c->reqs.end()) return fail(IPLS_ERR_ARG, "unknown ticket");
+  auto done = [&] { return it->second.done; };
+  if (timeout_us < 0) c->done_cv.wait(lk, done);
+  else c->done_cv.wait_for(lk, std::chrono::microseconds(timeout_us), done);
+  return it->second.done ? it->second.st : IPLS_PENDING;
 }
 
 iplsStatus iplsGetStats(iplsCtx c, iplsStats* out) {

@@ -25,7 +25,8 @@ class iplsConfig(ctypes.Structure):
                 ("sync", ctypes.c_int32), ("exact_only", ctypes.c_int32),
                 ("spin_limit", ctypes.c_int64), ("trace_cap", ctypes.c_int64),
                 ("budget_bytes", ctypes.c_int64), ("profile", ctypes.c_int32),
-                ("flags", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("flags", ctypes.c_int32), ("max_batch", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 FLAG_THRESHOLD_INDEX = 1
 
@@ -221,7 +222,8 @@ class Context:
 
     def __init__(self, *, k: int = 256, cutoff: int = 32, root_sample: int = 0, seed: int = 0,
                  exact_only: bool = False, trace_cap: int = 0, spin_limit: int | None = None,
-                 stream=None, budget_bytes: int = 0, profile: bool = False, flags: int = 0):
+                 stream=None, budget_bytes: int = 0, profile: bool = False, flags: int = 0,
+                 max_batch: int = 0):
         import torch
         cfg = iplsDefaultConfig()
         cfg.k, cfg.cutoff, cfg.root_sample, cfg.seed = k, cutoff, root_sample, seed
@@ -230,12 +232,24 @@ class Context:
         cfg.budget_bytes = budget_bytes
         cfg.profile = 1 if profile else 0
         cfg.flags = flags
+        cfg.max_batch = max_batch
         if spin_limit is not None:
             cfg.spin_limit = spin_limit
         s = stream if stream is not None else torch.cuda.current_stream()
         self.stream = s
         self.ctx = iplsCreate(cfg, s.cuda_stream)
         self.trace_cap = trace_cap
+
+    def submit_ptr(self, ptr: int, n: int, dtype: int) -> int:
+        """Queues an asynchronous sort of n device keys; returns its ticket."""
+        return iplsSubmit(self.ctx, ptr, n, dtype)
+
+    def poll(self, ticket: int) -> int:
+        """PENDING (1) while the request runs, then 0 (errors raise)."""
+        return iplsPoll(self.ctx, ticket)
+
+    def wait(self, ticket: int, timeout_us: int = -1) -> int:
+        return iplsWait(self.ctx, ticket, timeout_us)
 
     def sort_(self, keys) -> None:
         """Sorts a contiguous CUDA tensor in place."""
