@@ -82,6 +82,20 @@ def dist_env():
     return rank, world, local
 
 
+def replica_throughput(local_ms: float, keys_per_rank: int, world: int, device) -> tuple:
+    """Whole-job throughput of N independent replicas: every rank sorted
+    keys_per_rank keys in local_ms; the job took the slowest rank's time
+    (max over ranks).  Returns (Gkeys/s over all ranks, max ms)."""
+    ms = local_ms
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([local_ms], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return world * keys_per_rank / (ms * 1e-3) / 1e9, ms
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -343,11 +357,7 @@ def run_gb300(args):
     times = [(d, a.elapsed_time(b)) for d, a, b in events]
     total_ms = sum(t for _, t in times)
     kstats = ctx.kernel_stats(reset=True)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * n * args.steps / (total_ms * 1e-3) / 1e9
+    value, total_ms = replica_throughput(total_ms, n * args.steps, world, dev)
     per_dist = {}
     for d, t in times:
         per_dist.setdefault(d, []).append(t)
