@@ -25,11 +25,13 @@
  *     with cfg.sync = 0 it returns after enqueueing and a device-side error
  *     surfaces at the next synchronising call (iplsGetStats, iplsWait, or a
  *     synchronous sort).
- *   - IPLS_ERR_ARG and IPLS_ERR_BUDGET leave the key array untouched.  After
- *     any other error the contents of the key array are unspecified (a
- *     partition level may have stopped half-way between the array and the
- *     context's ping-pong buffer); the context stays usable and its next call
- *     starts from a clean state.
+ *   - IPLS_ERR_ARG and IPLS_ERR_BUDGET leave the key array untouched.
+ *     IPLS_ERR_TIMEOUT and IPLS_ERR_INTERNAL (device-side conditions) leave
+ *     it holding a permutation of its input: keys are only ever moved, a
+ *     partition level that sees the error moves nothing, and the keys of
+ *     that level still in the context's ping-pong buffer are copied back.
+ *     After IPLS_ERR_OOM or IPLS_ERR_CUDA its contents are unspecified.  The
+ *     context stays usable; its next call starts from a clean state.
  *   - iplsLastError() returns a thread-local message for the last failure.
  */
 #ifndef IPLS_H_

@@ -430,9 +430,22 @@ iplsStatus sort_impl(iplsCtx c, void* keys, int64_t n, int dtype, const int64_t*
     IPLS_CUDA(timed(c, kkTileScan, [&] { return launch_tilescan(a, c->stream, c->num_sms * 8); }));
     IPLS_CUDA(timed(c, kkScatter, [&] { return launch_scatter(a, c->stream, occupancy_grid(c, 1, dtype)); }));
     IPLS_CUDA(cudaMemcpyAsync(c->h_ctl, c->ctl, sizeof(LevelCtl), cudaMemcpyDeviceToHost, c->stream));
+    IPLS_CUDA(cudaMemcpyAsync(c->h_run, c->run, sizeof(RunStatus), cudaMemcpyDeviceToHost, c->stream));
     IPLS_CUDA(cudaStreamSynchronize(c->stream));
     const LevelCtl lc = *c->h_ctl;
-    if (lc.overflow) return fail(IPLS_ERR_INTERNAL, "a level list capacity was exceeded");
+    if (c->h_run->error != 0 || lc.overflow) {
+      // nothing of this level moved (k_scatter checks the status first):
+      // put the level's keys back into the user buffer and stop
+      IPLS_CUDA(launch_restore(X.subs, (int32_t)nsub, dtype, keys, c->scratch, c->stream));
+      IPLS_CUDA(cudaStreamSynchronize(c->stream));
+      resolve_events(c);
+      if (c->h_run->error == IPLS_ERR_TIMEOUT)
+        return fail(IPLS_ERR_TIMEOUT, "a device-side look-back wait exceeded spin_limit; the keys "
+                                      "hold a permutation of the input");
+      if (c->h_run->error != 0)
+        return fail((iplsStatus)c->h_run->error, "device reported status " + std::to_string(c->h_run->error));
+      return fail(IPLS_ERR_INTERNAL, "a level list capacity was exceeded");
+    }
     resolve_events(c);
     c->k_bytes[kkHist] += (int64_t)w * lc.keys_level;
     c->k_bytes[kkScatter] += 2 * (int64_t)w * lc.keys_moved;

@@ -282,6 +282,10 @@ cudaError_t launch_init_segments(const int64_t* offsets, int64_t nseg, int rmax,
 int resident_rmax(int cutoff);
 cudaError_t launch_fill(const Fill* fills, int32_t nfill, int dtype, void* keys, cudaStream_t s);
 cudaError_t launch_init_tiles(int32_t* tile2sub, int64_t ntiles, int32_t value, cudaStream_t s);
+// Copies the keys of the level's subproblems held in the scratch buffer back
+// into the user buffer (after a device-side error).
+cudaError_t launch_restore(const Sub* subs, int32_t nsub, int dtype, void* user, const void* scratch,
+                           cudaStream_t s);
 
 int tile_keys(int dtype);
 int key_bytes(int dtype);

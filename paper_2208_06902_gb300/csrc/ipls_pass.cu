@@ -531,6 +531,9 @@ __global__ void __launch_bounds__(kScatterThreads, 2) k_scatter(LevelArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ScatterSmem<K>& sh = *reinterpret_cast<ScatterSmem<K>*>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // an earlier kernel gave up (bounded wait): move nothing, so that every
+  // key of the level stays in its source buffer for the host to restore
+  if (*reinterpret_cast<volatile int32_t*>(&a.run->error) != 0) return;
   Bits* dst_base[2] = {reinterpret_cast<Bits*>(a.buf[0]), reinterpret_cast<Bits*>(a.buf[1])};
   const int64_t nt = a.ntiles;
   const int64_t t0 = nt * blockIdx.x / gridDim.x, t1 = nt * (blockIdx.x + 1) / gridDim.x;
@@ -630,6 +633,30 @@ __global__ void __launch_bounds__(kScatterThreads, 2) k_scatter(LevelArgs a) {
       if (p < span) dst[p] = sh.stage[i];
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// After a level stopped on an error: copies the keys of every subproblem of
+// the level that live in the scratch buffer back into the user buffer, so
+// that the user buffer holds a permutation of its input.  One block per
+// subproblem.
+template <class Bits>
+__global__ void k_restore(const Sub* subs, Bits* user, const Bits* scratch) {
+  const Sub sub = subs[blockIdx.x];
+  if (sub.buf != 1) return;
+  for (int64_t i = threadIdx.x; i < sub.n; i += blockDim.x) user[sub.off + i] = scratch[sub.off + i];
+}
+
+cudaError_t launch_restore(const Sub* subs, int32_t nsub, int dtype, void* user, const void* scratch,
+                           cudaStream_t s) {
+  if (nsub <= 0) return cudaSuccess;
+  if (dtype == 0 || dtype == 2)
+    k_restore<unsigned long long><<<nsub, 256, 0, s>>>(subs, reinterpret_cast<unsigned long long*>(user),
+                                                       reinterpret_cast<const unsigned long long*>(scratch));
+  else
+    k_restore<unsigned int><<<nsub, 256, 0, s>>>(subs, reinterpret_cast<unsigned int*>(user),
+                                                 reinterpret_cast<const unsigned int*>(scratch));
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

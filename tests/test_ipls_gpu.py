@@ -9,7 +9,7 @@ import pytest
 
 import datagen
 import oracle
-from gpu_util import compare_traces, gpu_sort, gpu_sort_segmented
+from gpu_util import compare_traces, from_dev, gpu_sort, gpu_sort_segmented, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -177,3 +177,30 @@ def test_repeated_calls_reuse_context():
             x = datagen.generate("normal", n, np.float64, seed=seed)
             got, _ = gpu_sort(x, ctx=ctx)
             assert _same(got, oracle.std_sort(x))
+
+
+def test_lookback_timeout_leaves_a_permutation():
+    # spin_limit = 1: a chunk whose predecessor has not published yet gives
+    # up at once, the level moves nothing, and its keys are restored; the
+    # output must hold the input's keys, and be sorted when the call succeeds
+    from paper_2208_06902_gb300 import Context, IPLSError
+    x = datagen.generate("normal", 1 << 24, np.float64, seed=12)
+    want = oracle.std_sort(x)
+    timeouts = 0
+    for trial in range(3):
+        ctx = Context(spin_limit=1)
+        d = to_dev(x)
+        try:
+            ctx.sort_ptr(d.data_ptr(), x.size, 0)
+            got = from_dev(d, np.float64)
+            assert _same(got, want)
+        except IPLSError as e:
+            assert e.status == -4
+            timeouts += 1
+            got = from_dev(d, np.float64)
+            assert _same(oracle.std_sort(got), want)  # same multiset
+        ctx.close()
+    print(f"look-back timeouts in 3 trials: {timeouts}")
+    # the context type still sorts correctly with a normal limit afterwards
+    got, _ = gpu_sort(x)
+    assert _same(got, want)
