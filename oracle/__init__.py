@@ -49,7 +49,8 @@ KIND_LINEAR, KIND_SPLITTER = 0, 1
 
 class Cfg(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int32), ("cutoff", ctypes.c_int32),
-                ("root_sample", ctypes.c_int64), ("seed", ctypes.c_uint64)]
+                ("root_sample", ctypes.c_int64), ("seed", ctypes.c_uint64),
+                ("pl2_leaves", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 class Model(ctypes.Structure):
@@ -59,7 +60,9 @@ class Model(ctypes.Structure):
                 ("xlo", ctypes.c_double), ("xlo_bits", ctypes.c_uint64),
                 ("B", ctypes.c_double), ("ud", ctypes.c_double),
                 ("nsplit", ctypes.c_int32), ("nbuckets", ctypes.c_int32),
-                ("split", ctypes.c_uint64 * 128)]
+                ("split", ctypes.c_uint64 * 128),
+                ("pl2_sh", ctypes.c_int32), ("pl2_rho", ctypes.c_int32),
+                ("pl2_x0", ctypes.c_int64)]
 
 
 class Trace(ctypes.Structure):
@@ -114,6 +117,10 @@ def lib():
                                            c.POINTER(Cfg), c.POINTER(Trace), c.c_int64,
                                            c.POINTER(c.c_int64), c.POINTER(c.c_int32)]
         L.oracle_std_sort.argtypes = [c.c_int, c.c_void_p, c.c_int64]
+        L.oracle_pl2_fit.argtypes = [c.c_int, c.c_void_p, c.c_int64, c.c_int32, c.c_int32,
+                                     c.POINTER(Model), c.c_void_p]
+        L.oracle_pl2_loss_grad.argtypes = [c.c_int, c.c_void_p, c.c_int64, c.POINTER(Model),
+                                           c.c_void_p, c.POINTER(c.c_double), c.c_void_p]
         L.oracle_multiset_hash.restype = None
         L.oracle_multiset_hash.argtypes = [c.c_int, c.c_void_p, c.c_int64,
                                            c.POINTER(c.c_uint64), c.POINTER(c.c_uint64)]
@@ -133,8 +140,9 @@ def _ptr(a: np.ndarray):
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
-def cfg(k: int = 256, cutoff: int = 32, root_sample: int = 0, seed: int = 0) -> Cfg:
-    return Cfg(k, cutoff, root_sample, seed)
+def cfg(k: int = 256, cutoff: int = 32, root_sample: int = 0, seed: int = 0,
+        pl2_leaves: int = 0) -> Cfg:
+    return Cfg(k, cutoff, root_sample, seed, pl2_leaves, 0)
 
 
 def mix64(z: int) -> int:
@@ -210,7 +218,7 @@ def partition_pass(keys: np.ndarray, off: int = 0, level: int = 0, k: int = 256,
     dst = np.empty_like(keys)
     counts = np.zeros(512, np.int64)
     m = Model()
-    c = Cfg(k, 1, root_sample, seed)
+    c = Cfg(k, 1, root_sample, seed, 0, 0)
     rc = lib().oracle_partition_pass(_code(keys), _ptr(keys), keys.size, off, level,
                                      ctypes.byref(c), _ptr(dst), _ptr(counts),
                                      ctypes.byref(m))
@@ -220,10 +228,11 @@ def partition_pass(keys: np.ndarray, off: int = 0, level: int = 0, k: int = 256,
 
 
 def sort(keys: np.ndarray, k: int = 256, cutoff: int = 32, root_sample: int = 0,
-         seed: int = 0, trace_cap: int = 0):
-    """Whole IPLS sort (returns a sorted copy, the trace records and the depth)."""
+         seed: int = 0, trace_cap: int = 0, pl2_leaves: int = 0):
+    """Whole IPLS sort (returns a sorted copy, the trace records and the depth).
+    pl2_leaves > 0: subproblems above 8192 keys use the PL2 model."""
     out = np.array(keys, copy=True)
-    c = Cfg(k, cutoff, root_sample, seed)
+    c = Cfg(k, cutoff, root_sample, seed, pl2_leaves, 0)
     tr = (Trace * trace_cap)() if trace_cap > 0 else None
     cnt = ctypes.c_int64(0)
     lv = ctypes.c_int32(0)
@@ -236,12 +245,12 @@ def sort(keys: np.ndarray, k: int = 256, cutoff: int = 32, root_sample: int = 0,
 
 
 def sort_segments(keys: np.ndarray, offsets, k: int = 256, cutoff: int = 32,
-                  root_sample: int = 0, seed: int = 0, trace_cap: int = 0):
+                  root_sample: int = 0, seed: int = 0, trace_cap: int = 0, pl2_leaves: int = 0):
     """IPLS on each segment keys[off[i]:off[i+1]], each a level-0 subproblem
     keyed by its own offset (returns sorted copy, trace records, depth)."""
     out = np.array(keys, copy=True)
     off = np.ascontiguousarray(offsets, np.int64)
-    c = Cfg(k, cutoff, root_sample, seed)
+    c = Cfg(k, cutoff, root_sample, seed, pl2_leaves, 0)
     tr = (Trace * trace_cap)() if trace_cap > 0 else None
     cnt = ctypes.c_int64(0)
     lv = ctypes.c_int32(0)
@@ -252,6 +261,36 @@ def sort_segments(keys: np.ndarray, offsets, k: int = 256, cutoff: int = 32,
         raise RuntimeError(f"oracle_sort_segments failed ({rc})")
     recs = list(tr[: cnt.value]) if tr is not None else []
     return out, recs, lv.value
+
+
+PL2_STEPS = 8
+
+
+def pl2_fit(sorted_sample: np.ndarray, M: int = 64, K: int = 256):
+    """PL2 fitted on a sorted sample: (model, loss after each training step),
+    or None when the sample's range cannot be used."""
+    s = np.ascontiguousarray(sorted_sample)
+    m = Model()
+    losses = np.zeros(PL2_STEPS + 1, np.float64)
+    if lib().oracle_pl2_fit(_code(s), _ptr(s), s.size, M, K, ctypes.byref(m), _ptr(losses)) != 0:
+        return None
+    return m, losses
+
+
+def pl2_knots(m: Model) -> np.ndarray:
+    """The knot values y_0..y_M of a PL2 model."""
+    return np.array(m.split[: m.nsplit + 1], np.uint64).view(np.float64).copy()
+
+
+def pl2_loss_grad(sorted_sample: np.ndarray, m: Model, y: np.ndarray):
+    """The PL2 loss and its gradient in the knot values y (for m's leaves)."""
+    s = np.ascontiguousarray(sorted_sample)
+    y = np.ascontiguousarray(y, np.float64)
+    loss = ctypes.c_double(0.0)
+    grad = np.zeros(y.size, np.float64)
+    lib().oracle_pl2_loss_grad(_code(s), _ptr(s), s.size, ctypes.byref(m), _ptr(y),
+                               ctypes.byref(loss), _ptr(grad))
+    return loss.value, grad
 
 
 def std_sort(keys: np.ndarray) -> np.ndarray:

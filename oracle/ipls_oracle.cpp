@@ -69,7 +69,18 @@ struct OracleCfg {
   int32_t cutoff;       // subproblems of at most this many keys are base-cased
   int64_t root_sample;  // sample size at level 0; 0 = the alpha*k-1 formula
   uint64_t seed;        // seed of the sampling stream
+  int32_t pl2_leaves;   // 0: FMCD everywhere; else PL2 with this many leaves
+                        // (a power of two, 2..64) for subproblems of more
+                        // than kPL2MinKeys keys
+  int32_t pad;
 };
+
+// PL2 is used for subproblems larger than this (smaller ones keep FMCD).
+const int64_t kPL2MinKeys = 8192;
+// Samples longer than this keep FMCD (the device trains PL2 in shared memory).
+const int64_t kPL2MaxSample = 4096;
+// Training steps of PL2.
+const int kPL2Steps = 8;
 
 struct OracleModel {
   int32_t kind;     // 0 = FMCD linear model, 1 = splitter tree, 2 = homogeneous
@@ -82,9 +93,13 @@ struct OracleModel {
   uint64_t xlo_bits;  // x[D] as raw key bits (integer keys: the exact key)
   double B;         // the listing's own intercept (K - A*(x_hi + x_lo))/2
   double ud;        // the u_d the slope came from
-  int32_t nsplit;   // splitter count (kind 1)
+  int32_t nsplit;   // splitter count (kind 1); leaves M (kind 2)
   int32_t nbuckets; // buckets of this pass: k, or 2*nsplit+1 for splitters
-  uint64_t split[128];  // splitters as totalOrder bits, ascending, unique
+  uint64_t split[128];  // splitters as totalOrder bits, ascending, unique;
+                        // kind 2: the knot values y_0..y_M as binary64 bits
+  int32_t pl2_sh;   // kind 2: leaf width 2^sh in fixed-point units
+  int32_t pl2_rho;  // kind 2: fixed-point scale, X(x) = trunc(x / 2^rho)
+  int64_t pl2_x0;   // kind 2: X(x_0), the sample minimum
 };
 
 struct OracleTrace {
@@ -301,9 +316,212 @@ void build_splitters(const T* samp, int64_t S, int32_t k, OracleModel* m) {
   m->nbuckets = 2 * cnt + 1;
 }
 
+// ---------------------------------------------------------------------------
+// PL2: a two-level piecewise-linear CDF model (the learned-CDF view of Ch.2
+// "Learned Sort" and Ch.3 "Recursive Model Index", with the loss of Ch.3 --
+// the mean squared error against the empirical CDF).  The root routes a key
+// to one of M equal-width leaves of the sample's range; the leaves
+// interpolate linearly between knot values y_0..y_M, so the CDF is
+// continuous, and the knots are kept non-decreasing, so it is monotone
+// (RMIs need not be; a bucket map must be).  Bucket = floor(k F(x)) in
+// binary32, clamped per leaf to [floor(k y_j), floor(k y_{j+1})].
+// ---------------------------------------------------------------------------
+
+// X(x) = trunc(x / 2^rho) as an integer, saturating (sat = true) when
+// |x / 2^rho| >= 2^62.  Exact: scaling by a power of two, then truncation;
+// integer keys use integer shifts.
+template <class T> struct Fixed;
+template <> struct Fixed<double> {
+  static int64_t X(double x, int rho, bool& sat) {
+    sat = false;
+    if (std::isnan(x)) { sat = true; return 0; }
+    const double v = std::ldexp(x, -rho);
+    if (!(std::fabs(v) < 4611686018427387904.0)) { sat = true; return v > 0 ? (int64_t(1) << 62) : -(int64_t(1) << 62); }
+    return (int64_t)std::trunc(v);
+  }
+};
+template <> struct Fixed<float> {
+  static int64_t X(float x, int rho, bool& sat) { return Fixed<double>::X((double)x, rho, sat); }
+};
+template <class U> struct FixedInt {
+  static int64_t X(U x, int rho, bool& sat) {
+    sat = false;
+    const uint64_t u = (uint64_t)x;
+    if (rho >= 0) {
+      const uint64_t v = rho >= 64 ? 0 : (u >> rho);
+      if (v >> 62) { sat = true; return int64_t(1) << 62; }
+      return (int64_t)v;
+    }
+    const int l = -rho;
+    if (l >= 62 || (u >> (62 - l)) != 0) { sat = u != 0; return u ? (int64_t(1) << 62) : 0; }
+    return (int64_t)(u << l);
+  }
+};
+template <> struct Fixed<uint64_t> : FixedInt<uint64_t> {};
+template <> struct Fixed<uint32_t> : FixedInt<uint32_t> {};
+
+// Unbiased exponent of a finite positive binary64 (denormals: -1022).
+static int exponent_of(double r) {
+  uint64_t b; std::memcpy(&b, &r, 8);
+  const int e = (int)((b >> 52) & 0x7FF);
+  return e == 0 ? -1022 : e - 1023;
+}
+
+static int bit_length(uint64_t v) {
+  int b = 0;
+  while (v) { ++b; v >>= 1; }
+  return b;
+}
+
+// Per-sample features of PL2 on the sorted sample: leaf, position in it.
+struct PL2Feat {
+  std::vector<int32_t> leaf;
+  std::vector<double> w;
+  std::vector<int64_t> start;  // start[j]: first sample of leaf j; start[M] = S
+};
+
+// Fits PL2 on the sorted sample x[0..S) with M leaves.  Returns false (and
+// leaves m alone) when the sample's range cannot be used: equal or
+// non-finite extremes (the duplicate rule takes over) or a range that does
+// not fit the fixed point (FMCD takes over).
+template <class T>
+bool pl2_fit(const T* x, int64_t S, int32_t M, int32_t K, OracleModel* m, PL2Feat* feat_out,
+             std::vector<double>* loss_trace) {
+  typedef Key<T> KT;
+  if (KT::ord(x[0]) == KT::ord(x[S - 1]) || !KT::finite(x[0]) || !KT::finite(x[S - 1])) return false;
+  const double range = KT::diff(x[S - 1], x[0]);
+  if (!(range > 0.0) || !std::isfinite(range)) return false;
+  const int rho = exponent_of(range) - 30;
+  bool s0, s1;
+  const int64_t X0 = Fixed<T>::X(x[0], rho, s0);
+  const int64_t X1 = Fixed<T>::X(x[S - 1], rho, s1);
+  if (s0 || s1) return false;
+  int mlog = 0;
+  while ((1 << mlog) < M) ++mlog;
+  const int64_t umax = X1 - X0;
+  const int sh = std::max(0, bit_length((uint64_t)umax) - mlog);
+  PL2Feat f;
+  f.leaf.resize(S);
+  f.w.resize(S);
+  const double inv = std::ldexp(1.0, -sh);
+  for (int64_t i = 0; i < S; ++i) {
+    bool sat;
+    const int64_t U = Fixed<T>::X(x[i], rho, sat) - X0;
+    int64_t j = U >> sh;
+    if (j > M - 1) j = M - 1;
+    f.leaf[i] = (int32_t)j;
+    f.w[i] = (double)(U - (j << sh)) * inv;
+  }
+  // leaf starts: samples are sorted, so leaf j is one index range
+  f.start.assign(M + 1, S);
+  for (int32_t j = M; j >= 0; --j) {
+    int64_t c = 0;
+    if (j < M) {
+      c = 0;
+      while (c < S && f.leaf[c] < j) ++c;
+    }
+    f.start[j] = (j == M) ? S : c;
+  }
+  std::vector<double> y(M + 1), tau(S), r(S), G(M + 1), H(M + 1);
+  for (int64_t i = 0; i < S; ++i) tau[i] = ((double)i + 0.5) / (double)S;
+  // initial knots: the empirical CDF at the knots
+  for (int32_t j = 0; j <= M; ++j) y[j] = (double)f.start[j] / (double)S;
+  auto loss = [&]() {
+    double L = 0.0;
+    for (int64_t i = 0; i < S; ++i) L += r[i] * r[i];
+    return L / (double)S;
+  };
+  for (int step = 0; step <= kPL2Steps; ++step) {
+    // forward: F and the residual of every sample
+    for (int64_t i = 0; i < S; ++i) {
+      const int32_t a = f.leaf[i];
+      const double t1 = 1.0 - f.w[i];
+      const double p = y[a] * t1;
+      const double q = y[a + 1] * f.w[i];
+      const double F = p + q;
+      r[i] = F - tau[i];
+    }
+    if (loss_trace) loss_trace->push_back(loss());
+    if (step == kPL2Steps) break;
+    // backward: dL/dy_j = (2/S) G_j and curvature (2/S) H_j, summed over
+    // leaf j (weight 1-w) then leaf j-1 (weight w), in sample order
+    for (int32_t j = 0; j <= M; ++j) {
+      double g = 0.0, h = 0.0;
+      if (j < M)
+        for (int64_t i = f.start[j]; i < f.start[j + 1]; ++i) {
+          const double t1 = 1.0 - f.w[i];
+          g += r[i] * t1;
+          h += t1 * t1;
+        }
+      if (j > 0)
+        for (int64_t i = f.start[j - 1]; i < f.start[j]; ++i) {
+          g += r[i] * f.w[i];
+          h += f.w[i] * f.w[i];
+        }
+      G[j] = g;
+      H[j] = h;
+    }
+    // half a diagonal Newton step on every knot (the 2/S factors cancel)
+    for (int32_t j = 0; j <= M; ++j)
+      if (H[j] > 0.0) {
+        const double q = G[j] / H[j];
+        y[j] = y[j] - 0.5 * q;
+      }
+    // keep the knots in [0, 1] and non-decreasing
+    y[0] = std::min(std::max(y[0], 0.0), 1.0);
+    for (int32_t j = 1; j <= M; ++j) y[j] = std::min(std::max(y[j], y[j - 1]), 1.0);
+  }
+  m->kind = 2;
+  m->capped = 0;
+  m->S = S;
+  m->D = sh;
+  m->nsplit = M;
+  m->nbuckets = K;
+  m->pl2_sh = sh;
+  m->pl2_rho = rho;
+  m->pl2_x0 = X0;
+  for (int32_t j = 0; j <= M; ++j) std::memcpy(&m->split[j], &y[j], 8);
+  if (feat_out) *feat_out = f;
+  return true;
+}
+
+// Bucket of key x under a PL2 model: floor(k F(x)) in binary32, clamped to
+// the leaf's range.  Monotone in x: the leaf index and the position in the
+// leaf are, F is within a leaf (non-negative slope, monotone roundings),
+// and the leaf ranges [floor(k y_j), floor(k y_{j+1})] follow each other.
+template <class T>
+int32_t pl2_bucket(T x, const OracleModel& m) {
+  typedef Key<T> KT;
+  const int32_t K = m.nbuckets, M = m.nsplit;
+  if (KT::is_nan(x)) return KT::neg_sign(x) ? 0 : K - 1;
+  bool sat;
+  const int64_t X = Fixed<T>::X(x, m.pl2_rho, sat);
+  if (sat) return X > 0 ? K - 1 : 0;
+  const int64_t U = X - m.pl2_x0;
+  if (U < 0) return 0;
+  const int64_t j = U >> m.pl2_sh;
+  if (j >= M) return K - 1;
+  double yd0, yd1;
+  std::memcpy(&yd0, &m.split[j], 8);
+  std::memcpy(&yd1, &m.split[j + 1], 8);
+  const float y0 = (float)yd0, y1 = (float)yd1, kf = (float)K;
+  const float inv = std::ldexp(1.0f, -m.pl2_sh);
+  const float w = (float)(U - (j << m.pl2_sh)) * inv;
+  const float d = y1 - y0;
+  const float F = y0 + d * w;
+  int32_t b = (int32_t)std::floor(F * kf);
+  int32_t lo = (int32_t)std::floor(y0 * kf), hi = (int32_t)std::floor(y1 * kf);
+  if (lo > K - 1) lo = K - 1;
+  if (hi > K - 1) hi = K - 1;
+  if (b < lo) b = lo;
+  if (b > hi) b = hi;
+  return b;
+}
+
 template <class T>
 int32_t bucket_of(T x, const OracleModel& m, T xlo) {
   if (m.kind == 0) return linear_bucket<T>(x, m, xlo);
+  if (m.kind == 2) return pl2_bucket<T>(x, m);
   return splitter_bucket(Key<T>::ord(x), m);
 }
 
@@ -324,16 +542,33 @@ void partition_pass(const T* src, int64_t n, int64_t off, int32_t level,
                    [](T a, T b) { return KT::ord(a) < KT::ord(b); });
   std::memset(m, 0, sizeof(*m));
   m->S = S;
-  bool linear = KT::ord(samp[0]) != KT::ord(samp[S - 1]) &&
-                KT::finite(samp[0]) && KT::finite(samp[S - 1]);
+  const bool usable = KT::ord(samp[0]) != KT::ord(samp[S - 1]) &&
+                      KT::finite(samp[0]) && KT::finite(samp[S - 1]);
+  bool linear = usable;
   T xlo = samp[0];
-  if (linear) {
+  std::vector<int32_t> b(n);
+  // PL2 for large subproblems when enabled; its pass falls back to the
+  // splitter tree on no progress or when a bucket holds more than 4n/k keys
+  if (usable && cfg.pl2_leaves > 0 && n > kPL2MinKeys && S <= kPL2MaxSample &&
+      pl2_fit<T>(samp.data(), S, cfg.pl2_leaves, cfg.k, m, nullptr, nullptr)) {
+    linear = false;
+    std::fill(counts, counts + m->nbuckets, 0);
+    for (int64_t i = 0; i < n; ++i) counts[b[i] = pl2_bucket<T>(src[i], *m)]++;
+    bool bad = false;
+    for (int32_t j = 0; j < m->nbuckets; ++j)
+      if (counts[j] == n || counts[j] * (int64_t)m->nbuckets > 4 * n) bad = true;
+    if (!bad) {
+      std::vector<int64_t> base(m->nbuckets + 1, 0);
+      for (int32_t j = 0; j < m->nbuckets; ++j) base[j + 1] = base[j] + counts[j];
+      for (int64_t i = 0; i < n; ++i) dst[base[b[i]]++] = src[i];
+      return;
+    }
+  } else if (linear) {
     fmcd_listing<T>(samp.data(), S, cfg.k, m);
     const bool ok = std::isfinite(m->ud) && m->ud > 0.0 &&
                     std::isfinite(m->A) && std::isfinite(m->Bc);
     if (ok) xlo = samp[m->D]; else linear = false;
   }
-  std::vector<int32_t> b(n);
   if (linear) {
     std::fill(counts, counts + m->nbuckets, 0);
     for (int64_t i = 0; i < n; ++i) counts[b[i] = linear_bucket<T>(src[i], *m, xlo)]++;
@@ -571,6 +806,56 @@ int oracle_sort_segments(int dtype, void* keys, const int64_t* off, int64_t nseg
 }
 
 // Reference sort for the pins: std::sort under totalOrder.
+// PL2 on a sorted sample: the fitted model, and the loss after each of the
+// training steps (kPL2Steps + 1 values).  Returns 1 when the sample's range
+// could not be used.
+int oracle_pl2_fit(int dtype, const void* sorted, int64_t S, int32_t M, int32_t K, OracleModel* m,
+                   double* losses) {
+  return dispatch(dtype, [&](auto* tag) {
+    typedef std::remove_pointer_t<decltype(tag)> T;
+    std::memset(m, 0, sizeof(*m));
+    std::vector<double> lt;
+    if (!pl2_fit<T>((const T*)sorted, S, M, K, m, nullptr, &lt)) return 1;
+    for (size_t i = 0; i < lt.size(); ++i) losses[i] = lt[i];
+    return 0;
+  });
+}
+
+// The PL2 loss (1/S) sum (F(x_i) - (i+1/2)/S)^2 and its gradient in the knot
+// values y[0..M], for the leaves and positions a model assigns to the sorted
+// sample (summed in sample order).  For checking training steps.
+int oracle_pl2_loss_grad(int dtype, const void* sorted, int64_t S, const OracleModel* m,
+                         const double* y, double* loss, double* grad) {
+  return dispatch(dtype, [&](auto* tag) {
+    typedef std::remove_pointer_t<decltype(tag)> T;
+    const T* x = (const T*)sorted;
+    const int32_t M = m->nsplit;
+    const double inv = std::ldexp(1.0, -m->pl2_sh);
+    std::vector<double> r(S), w(S);
+    std::vector<int32_t> leaf(S);
+    double L = 0.0;
+    for (int64_t i = 0; i < S; ++i) {
+      bool sat;
+      const int64_t U = Fixed<T>::X(x[i], m->pl2_rho, sat) - m->pl2_x0;
+      int64_t j = U >> m->pl2_sh;
+      if (j > M - 1) j = M - 1;
+      if (j < 0) j = 0;
+      leaf[i] = (int32_t)j;
+      w[i] = (double)(U - (j << m->pl2_sh)) * inv;
+      const double F = y[j] * (1.0 - w[i]) + y[j + 1] * w[i];
+      r[i] = F - ((double)i + 0.5) / (double)S;
+      L += r[i] * r[i];
+    }
+    *loss = L / (double)S;
+    for (int32_t j = 0; j <= M; ++j) grad[j] = 0.0;
+    for (int64_t i = 0; i < S; ++i) {
+      grad[leaf[i]] += 2.0 * r[i] * (1.0 - w[i]) / (double)S;
+      grad[leaf[i] + 1] += 2.0 * r[i] * w[i] / (double)S;
+    }
+    return 0;
+  });
+}
+
 int oracle_std_sort(int dtype, void* keys, int64_t n) {
   return dispatch(dtype, [&](auto* tag) {
     typedef std::remove_pointer_t<decltype(tag)> T;

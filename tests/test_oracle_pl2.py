@@ -1,0 +1,109 @@
+"""Pins of the oracle's PL2 model (two-level piecewise-linear CDF) against
+things other than its own code: finite differences for the gradient, the
+empirical CDF written out again here for the initial knots, monotonicity,
+the definition of the sorted result, closed-form balance on an arithmetic
+progression, and the imbalance rule."""
+import math
+
+import numpy as np
+import pytest
+
+import datagen
+import oracle
+
+
+def _sample(dist, S=1432, dtype=np.float64, seed=3):
+    return np.sort(datagen.generate(dist, S, dtype, seed))
+
+
+@pytest.mark.parametrize("dist", ["uniform", "normal", "lognormal", "exponential", "mixgauss"])
+def test_gradient_matches_finite_differences(dist):
+    x = _sample(dist)
+    m, _ = oracle.pl2_fit(x, 64, 256)
+    rng = np.random.default_rng(0)
+    y = np.sort(rng.uniform(0, 1, m.nsplit + 1))
+    L, g = oracle.pl2_loss_grad(x, m, y)
+    h = 1e-6
+    for j in rng.choice(m.nsplit + 1, 12, replace=False):
+        e = np.zeros_like(y)
+        e[j] = h
+        Lp, _ = oracle.pl2_loss_grad(x, m, y + e)
+        Lm, _ = oracle.pl2_loss_grad(x, m, y - e)
+        fd = (Lp - Lm) / (2 * h)
+        assert abs(fd - g[j]) <= 1e-7 * max(1.0, abs(g[j])) + 1e-9, (j, fd, g[j])
+
+
+def _fixed(v, rho):
+    # X(v) = trunc(v / 2^rho), written out here from the definition
+    return math.trunc(math.ldexp(float(v), -rho))
+
+
+def test_first_loss_is_that_of_the_empirical_cdf_at_the_knots():
+    x = _sample("normal")
+    m, losses = oracle.pl2_fit(x, 32, 256)
+    S, M, sh, rho = x.size, m.nsplit, m.pl2_sh, m.pl2_rho
+    U = np.array([_fixed(v, rho) for v in x]) - m.pl2_x0
+    y0 = np.array([np.count_nonzero(U < (j << sh)) / S for j in range(M + 1)])
+    L0, _ = oracle.pl2_loss_grad(x, m, y0)
+    assert L0 == pytest.approx(losses[0], rel=1e-12)
+    assert y0[0] == 0.0 and y0[-1] == 1.0
+
+
+@pytest.mark.parametrize("dist", ["uniform", "normal", "lognormal", "exponential", "mixgauss", "zipf"])
+def test_training_does_not_raise_the_loss_and_knots_are_monotone(dist):
+    x = _sample(dist)
+    r = oracle.pl2_fit(x, 64, 256)
+    if r is None:
+        pytest.skip("degenerate sample")
+    m, losses = r
+    assert losses[-1] <= losses[0] * (1 + 1e-12)
+    y = oracle.pl2_knots(m)
+    assert np.all(np.diff(y) >= 0) and y[0] >= 0 and y[-1] <= 1
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32, np.uint64, np.uint32])
+def test_bucket_map_is_monotone(dtype):
+    x = np.sort(datagen.generate("lognormal", 1432, dtype, 5))
+    m, _ = oracle.pl2_fit(x, 64, 256)
+    keys = oracle.std_sort(datagen.generate("lognormal", 200_000, dtype, 6))
+    b = oracle.classify(keys, m)
+    assert np.all(np.diff(b) >= 0)
+    assert b.min() >= 0 and b.max() <= 255
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32, np.uint64, np.uint32])
+@pytest.mark.parametrize("dist", ["uniform", "normal", "lognormal", "mixgauss", "zipf", "rootdups"])
+def test_pl2_sort_equals_the_definition(dtype, dist):
+    x = datagen.generate(dist, 120_000, dtype, seed=9)
+    got, recs, _ = oracle.sort(x, cutoff=64, trace_cap=10_000, pl2_leaves=64)
+    assert np.array_equal(got.view(np.uint8), oracle.std_sort(x).view(np.uint8))
+    if dist in ("uniform", "normal", "lognormal") and dtype in (np.float64, np.float32):
+        # PL2 ran on the large subproblems (the order-preserving integer
+        # images of these draws are too concentrated for equal-width leaves:
+        # there the imbalance rule takes the splitter tree, as it should)
+        assert any(r.model.kind == 2 for r in recs)
+
+
+def test_arithmetic_progression_splits_evenly():
+    # the empirical CDF of an arithmetic progression is linear, so the fitted
+    # knots are the knot fractions and every bucket gets about n/k keys
+    n = 1 << 20
+    x = np.arange(n, dtype=np.float64)
+    s = np.sort(x[np.random.default_rng(1).choice(n, 1432)])
+    m, _ = oracle.pl2_fit(s, 64, 256)
+    counts = np.bincount(oracle.classify(x, m), minlength=256)
+    assert counts.max() <= 2 * n // 256
+
+
+def test_a_dense_cluster_falls_back_to_the_splitter_tree():
+    # half the keys in a range a thousand times narrower than one leaf: the
+    # PL2 pass would put them into one bucket (> 4n/k), so the pass takes
+    # the splitter tree instead
+    rng = np.random.default_rng(2)
+    n = 40_000
+    x = np.concatenate([rng.uniform(0, 1, n // 2), 0.5 + rng.uniform(0, 1e-9, n // 2)])
+    x = x[rng.permutation(n)]
+    got, recs, _ = oracle.sort(x, cutoff=64, trace_cap=10_000, pl2_leaves=64)
+    assert np.array_equal(got, oracle.std_sort(x))
+    root = [r for r in recs if r.level == 0][0]
+    assert root.model.kind == 1
