@@ -69,6 +69,8 @@ def parse():
     p.add_argument("--max-request-log10", type=float, default=6.0)
     p.add_argument("--segments", type=int, default=200_000)
     p.add_argument("--tuned", metavar="JSON", help="autotuner table; picks k and cutoff")
+    p.add_argument("--pl2", type=int, default=0,
+                   help="PL2 leaves for subproblems above 8192 keys (0: FMCD, the paper's IPLS)")
     p.add_argument("--ingest-ncu", nargs=2, metavar=("CSV", "STATS_JSON"),
                    help="write profiles/ncu_traffic.json from an ncu --csv launch list with "
                         "dram__bytes_{read,write}.sum of a --profile-stats run and its JSON")
@@ -301,7 +303,7 @@ def run_gb300(args):
     pristine = {d: torch.from_numpy(inputs[d].view(np.uint8)).to(dev) for d in dists}
     work = torch.empty(n * 8, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
-    ctx = ipls.Context(cutoff=args.cutoff, profile=True, stream=stream)
+    ctx = ipls.Context(cutoff=args.cutoff, profile=True, stream=stream, pl2_leaves=args.pl2)
 
     def step(i, timed):
         d = dists[i % len(dists)]
@@ -426,6 +428,7 @@ def run_gb300(args):
             "config": {"workload": f"IPLS sort of 2^{args.log2n} f64 keys, one step per array, "
                                    f"{len(dists)} seeded distributions",
                        "distributions": dists, "k": 256, "cutoff": args.cutoff,
+                       "model": f"PL2, {args.pl2} leaves, above 8192 keys" if args.pl2 else "FMCD",
                        "sample": "alpha*k-1 keys, alpha = 0.2*floor(log2 n)",
                        "l2": f"flushed: a {n * 8 >> 20} MiB input-restore copy runs between "
                              "timed steps (inputs larger than L2 from 2^25 keys)",

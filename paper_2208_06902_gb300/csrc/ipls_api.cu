@@ -422,6 +422,8 @@ iplsStatus sort_impl(iplsCtx c, void* keys, int64_t n, int dtype, const int64_t*
     a.trace_cap = cfg.trace_cap;
     a.trace_base = c->trace_grid_count;
     const int max_sample = sample_size_host(std::max<int64_t>(max_sub_n, 2), level, cfg.k, cfg.root_sample);
+    a.max_sample = max_sample;
+    a.pl2_leaves = cfg.pl2_leaves;
     IPLS_CUDA(timed(c, kkFit, [&] { return launch_fit(a, c->stream, max_sample); }));
     IPLS_CUDA(timed(c, kkHist, [&] { return launch_hist(a, c->stream, 0, occupancy_grid(c, 0, dtype)); }));
     IPLS_CUDA(timed(c, kkCheck, [&] { return launch_check(a, c->stream, max_sample); }));
@@ -492,6 +494,8 @@ iplsStatus validate_cfg(const iplsConfig& c) {
     return fail(IPLS_ERR_ARG, "root_sample must be in [0, 16384]");
   if (c.spin_limit < 1) return fail(IPLS_ERR_ARG, "spin_limit must be >= 1");
   if (c.max_batch < 0) return fail(IPLS_ERR_ARG, "max_batch must be >= 0");
+  if (c.pl2_leaves != 0 && (c.pl2_leaves < 2 || c.pl2_leaves > kPL2MaxLeaves || (c.pl2_leaves & (c.pl2_leaves - 1))))
+    return fail(IPLS_ERR_ARG, "pl2_leaves must be 0 or a power of two in [2, 64]");
   if (c.budget_bytes < 0) return fail(IPLS_ERR_ARG, "budget_bytes must be >= 0");
   return IPLS_OK;
 }

@@ -650,6 +650,177 @@ struct ExactQueue {
 };
 
 // ---------------------------------------------------------------------------
+// PL2: two-level piecewise-linear CDF (learned CDF of Ch.2 "Learned Sort" /
+// Ch.3 "Recursive Model Index", mean squared error against the empirical
+// CDF as in Ch.3).  The root maps a key to fixed point X = trunc(x/2^rho)
+// and to leaf j = (X - X0) >> sh of M equal-width leaves over the sample's
+// range; leaf j interpolates between knot values y_j and y_{j+1}.
+// Training: knots start at the empirical CDF, then kPL2Steps steps of half
+// a diagonal Newton step per knot, each followed by clamping the knots into
+// [0, 1] non-decreasing.  Every sum runs over sample indices in order (the
+// samples of a leaf are contiguous), with one rounding per operation, so
+// the model is the same bit for bit wherever it is computed.
+// ---------------------------------------------------------------------------
+struct PL2Scratch {
+  int32_t* leaf;    // [S]
+  double* w;        // [S]
+  double* r;        // [S]
+};
+
+__device__ __forceinline__ int exponent_of(double r) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(r);
+  const int e = (int)((b >> 52) & 0x7FF);
+  return e == 0 ? -1022 : e - 1023;
+}
+
+// Block-wide (all threads).  so[0..S) is the sorted sample (order bits).
+// Returns false (m untouched) when the sample's range cannot carry PL2.
+template <class K>
+__device__ bool fit_pl2(const typename KT<K>::Ord* so, int S, int M, int K_, Model* m,
+                        PL2Scratch sc, double* y, int64_t* start, int* s_flag, long long* s_x0,
+                        int* s_rho, int* s_sh) {
+  using T = KT<K>;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid == 0) {
+    *s_flag = 0;
+    const typename T::Bits b0 = T::unord(so[0]), b1 = T::unord(so[S - 1]);
+    if (so[0] != so[S - 1] && !T::special(b0) && !T::special(b1)) {
+      const double range = T::diff(b1, b0);
+      if (range > 0.0 && isfinite(range)) {
+        const int rho = exponent_of(range) - 30;
+        bool s0, s1;
+        const long long X0 = fixed_point<K>(b0, rho, s0), X1 = fixed_point<K>(b1, rho, s1);
+        if (!s0 && !s1) {
+          int mlog = 0;
+          while ((1 << mlog) < M) ++mlog;
+          const unsigned long long umax = (unsigned long long)(X1 - X0);
+          const int bl = umax == 0 ? 0 : 64 - __clzll((long long)umax);
+          *s_sh = bl - mlog > 0 ? bl - mlog : 0;
+          *s_rho = rho;
+          *s_x0 = X0;
+          *s_flag = 1;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (!*s_flag) return false;
+  const int rho = *s_rho, sh = *s_sh;
+  const long long X0 = *s_x0;
+  const double inv = __longlong_as_double((long long)(1023 - sh) << 52);  // 2^-sh
+  for (int i = tid; i < S; i += nt) {
+    bool sat;
+    const long long U = fixed_point<K>(T::unord(so[i]), rho, sat) - X0;
+    long long j = U >> sh;
+    if (j > M - 1) j = M - 1;
+    sc.leaf[i] = (int32_t)j;
+    sc.w[i] = __dmul_rn((double)(U - (j << sh)), inv);
+  }
+  __syncthreads();
+  // leaf starts: the first sample of every leaf (leaves are non-decreasing)
+  for (int j = tid; j <= M; j += nt) {
+    int lo = 0, hi = S;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (sc.leaf[mid] < j) lo = mid + 1; else hi = mid;
+    }
+    start[j] = (j == M) ? S : lo;
+    y[j] = __ddiv_rn((double)((j == M) ? S : lo), (double)S);
+  }
+  __syncthreads();
+  for (int step = 0; step < kPL2Steps; ++step) {
+    for (int i = tid; i < S; i += nt) {  // forward: residual of every sample
+      const int a = sc.leaf[i];
+      const double t1 = __dsub_rn(1.0, sc.w[i]);
+      const double F = __dadd_rn(__dmul_rn(y[a], t1), __dmul_rn(y[a + 1], sc.w[i]));
+      const double tau = __ddiv_rn(__dadd_rn((double)i, 0.5), (double)S);
+      sc.r[i] = __dsub_rn(F, tau);
+    }
+    __syncthreads();
+    double q = 0.0;
+    bool upd = false;
+    if (tid <= M) {  // backward: gradient and curvature of knot tid
+      const int j = tid;
+      double g = 0.0, h = 0.0;
+      if (j < M)
+        for (int64_t i = start[j]; i < start[j + 1]; ++i) {
+          const double t1 = __dsub_rn(1.0, sc.w[i]);
+          g = __dadd_rn(g, __dmul_rn(sc.r[i], t1));
+          h = __dadd_rn(h, __dmul_rn(t1, t1));
+        }
+      if (j > 0)
+        for (int64_t i = start[j - 1]; i < start[j]; ++i) {
+          g = __dadd_rn(g, __dmul_rn(sc.r[i], sc.w[i]));
+          h = __dadd_rn(h, __dmul_rn(sc.w[i], sc.w[i]));
+        }
+      if (h > 0.0) {
+        q = __ddiv_rn(g, h);
+        upd = true;
+      }
+    }
+    __syncthreads();
+    if (upd) y[tid] = __dsub_rn(y[tid], __dmul_rn(0.5, q));
+    __syncthreads();
+    if (tid == 0) {  // knots in [0, 1], non-decreasing
+      y[0] = fmin(fmax(y[0], 0.0), 1.0);
+      for (int j = 1; j <= M; ++j) y[j] = fmin(fmax(y[j], y[j - 1]), 1.0);
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    m->l.kind = kPL2;
+    m->l.nb = K_;
+    m->l.capped = 0;
+    m->l.fast = 0;
+    m->l.S = S;
+    m->l.D = sh;
+    m->l.rho = rho;
+    m->l.qlo = X0;
+    m->nsplit = M;
+  }
+  for (int j = tid; j <= M; j += nt) m->split[j] = (uint64_t)__double_as_longlong(y[j]);
+  __syncthreads();
+  return true;
+}
+
+// Per-model tables for classifying with a PL2 model: binary32 knots and the
+// first bucket of every leaf.
+__device__ __forceinline__ void pl2_tables(const Model& m, float* yf, int* lo, int nthreads_tid,
+                                           int nthreads) {
+  const int M = m.nsplit, K = m.l.nb;
+  const float kf = (float)K;
+  for (int j = nthreads_tid; j <= M; j += nthreads) {
+    yf[j] = __double2float_rn(__longlong_as_double((long long)m.split[j]));
+    int b = (int)floorf(__fmul_rn(yf[j], kf));
+    lo[j] = b > K - 1 ? K - 1 : b;
+  }
+}
+
+// Bucket under a PL2 model: floor(k F(x)) in binary32, clamped to the
+// leaf's range [lo_j, lo_{j+1}], so monotone in x.
+template <class K>
+__device__ __forceinline__ int pl2_bucket(typename KT<K>::Bits b, const Model& m, const float* yf,
+                                          const int* lo) {
+  using T = KT<K>;
+  const int K_ = m.l.nb, M = m.nsplit, sh = (int)m.l.D;
+  if (T::is_nan(b)) return T::negative(b) ? 0 : K_ - 1;
+  bool sat;
+  const long long X = fixed_point<K>(b, m.l.rho, sat);
+  if (sat) return X > 0 ? K_ - 1 : 0;
+  const long long U = X - m.l.qlo;
+  if (U < 0) return 0;
+  const long long j = U >> sh;
+  if (j >= M) return K_ - 1;
+  const float inv = __int_as_float((127 - sh) << 23);  // 2^-sh
+  const float w = __fmul_rn(__ll2float_rn(U - (j << sh)), inv);
+  const float F = __fadd_rn(yf[j], __fmul_rn(__fsub_rn(yf[j + 1], yf[j]), w));
+  int bk = (int)floorf(__fmul_rn(F, (float)K_));
+  if (bk < lo[j]) bk = lo[j];
+  if (bk > lo[j + 1]) bk = lo[j + 1];
+  return bk;
+}
+
+// ---------------------------------------------------------------------------
 // Exact thresholds of the linear model and the two-level index (ThrTable).
 // ---------------------------------------------------------------------------
 template <class K>

@@ -17,7 +17,16 @@ constexpr int kResidentTasks = 2048;    // pending ranges inside a resident bloc
 constexpr int kFitThreads = 1024;
 constexpr int kFillChunk = 65536;
 
-enum ModelKind : int32_t { kLinear = 0, kSplitter = 1 };
+enum ModelKind : int32_t { kLinear = 0, kSplitter = 1, kPL2 = 2 };
+
+// PL2 (piecewise-linear CDF): used, when enabled, for subproblems larger
+// than kPL2MinKeys whose sample has at most kPL2MaxSample keys; trained for
+// kPL2Steps steps.  Model layout: l.kind = kPL2, l.nb = k, l.S, l.D = l.rho
+// ... see fit_pl2; nsplit = leaves M, split[0..M] = knot values (binary64).
+constexpr int64_t kPL2MinKeys = 8192;
+constexpr int kPL2MaxSample = 4096;
+constexpr int kPL2Steps = 8;
+constexpr int kPL2MaxLeaves = 64;
 
 // Linear partition model of one subproblem: b(x) = clamp(floor(fma(A,
 // x (-) x_lo, Bc)), 0, nb-1) (Ch.3 model equation, centred form).
@@ -188,6 +197,8 @@ struct LevelArgs {
   uint64_t seed;
   int exact_only;
   int use_tables;        // build and use the exact threshold index
+  int pl2_leaves;        // 0, or PL2 leaves for subproblems above kPL2MinKeys
+  int max_sample;        // largest sample of the level (k_fit's shared-memory layout)
   int64_t spin_limit;
   uint32_t epoch;        // look-back epoch of this level's scatter
   int level;

@@ -31,8 +31,6 @@ namespace ipls {
 
 constexpr int kTile = kTileKeys;
 constexpr int kWarps = kPassThreads / 32;
-constexpr int kKPT = kTile / kPassThreads;   // keys per thread
-constexpr int kKPW = kTile / kWarps;         // keys per warp
 // k_scatter: 512 threads per tile, 8 keys each
 constexpr int kScatterThreads = 512;
 constexpr int kSWarps = kScatterThreads / 32;
@@ -90,8 +88,15 @@ constexpr int kWarpFitMin = 1024;
 __host__ __device__ __forceinline__ bool warp_fits(const LevelArgs& a) {
   return !a.use_tables && a.nsub >= kWarpFitMin;
 }
+// Subproblems that take PL2 (when enabled) are fitted by a block.
+__device__ __forceinline__ bool takes_pl2(const LevelArgs& a, const Sub& sub, int S) {
+  // (a level whose largest sample exceeds kPL2MaxSample is a level-0 launch
+  // in which every sample does; it reserves no PL2 scratch)
+  return a.pl2_leaves > 0 && sub.n > kPL2MinKeys && S <= kPL2MaxSample && a.max_sample <= kPL2MaxSample;
+}
 __device__ __forceinline__ bool fit_by_warp(const LevelArgs& a, const Sub& sub) {
-  return warp_fits(a) && sample_size(sub.n, sub.level, a.k, a.root_sample) <= kResidentSample;
+  const int S = (int)sample_size(sub.n, sub.level, a.k, a.root_sample);
+  return warp_fits(a) && S <= kResidentSample && !takes_pl2(a, sub, S);
 }
 
 template <class K>
@@ -140,7 +145,20 @@ __global__ void __launch_bounds__(kFitThreads) k_fit(LevelArgs a) {
   const Sub sub = a.subs[s];
   if (fit_by_warp(a, sub)) return;  // k_fit_warp fits this one
   const int S = gather_sorted_sample<K>(a, sub, so);
-  fit_model<BlockG, K>(so, S, a.k, &sm, fs);
+  bool pl2 = false;
+  if (takes_pl2(a, sub, S)) {
+    // scratch after the sample: leaf, w and r per sample
+    unsigned char* base = smem + (((size_t)a.max_sample * sizeof(Ord) + 15) & ~(size_t)15);
+    PL2Scratch sc{reinterpret_cast<int32_t*>(base + (size_t)kPL2MaxSample * 16),
+                  reinterpret_cast<double*>(base), reinterpret_cast<double*>(base + (size_t)kPL2MaxSample * 8)};
+    __shared__ double py[kPL2MaxLeaves + 1];
+    __shared__ int64_t pstart[kPL2MaxLeaves + 1];
+    __shared__ int pflag, prho, psh;
+    __shared__ long long px0;
+    if (threadIdx.x == 0) sm.nsplit = 0;
+    pl2 = fit_pl2<K>(so, S, a.pl2_leaves, a.k, &sm, sc, py, pstart, &pflag, &px0, &prho, &psh);
+  }
+  if (!pl2) fit_model<BlockG, K>(so, S, a.k, &sm, fs);
   copy_model(&a.models[s], &sm);
   if (sm.l.kind == kLinear && a.use_tables) {
     build_thr_table<K>(sm.l, &tab, scan_tmp);
@@ -166,6 +184,8 @@ __global__ void __launch_bounds__(kPassThreads, 4) k_hist(LevelArgs a, int rehis
   __shared__ unsigned int hist[kWarps][kMaxK];
   __shared__ unsigned int acc[kMaxK];
   __shared__ ExactQueue<kChunk * 32> xq[kWarps];
+  __shared__ float pl_yf[kPL2MaxLeaves + 1];
+  __shared__ int pl_lo[kPL2MaxLeaves + 1];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int i = threadIdx.x; i < kWarps * kMaxK; i += blockDim.x) (&hist[0][0])[i] = 0;
   for (int i = threadIdx.x; i < kMaxK; i += blockDim.x) acc[i] = 0;
@@ -193,6 +213,10 @@ __global__ void __launch_bounds__(kPassThreads, 4) k_hist(LevelArgs a, int rehis
       __syncthreads();
       cls.load(sm, a.exact_only);
       use_tab = a.use_tables && sm.l.kind == kLinear && tab.ok;
+      if (sm.l.kind == kPL2) {
+        pl2_tables(sm, pl_yf, pl_lo, threadIdx.x, blockDim.x);
+        __syncthreads();
+      }
     }
     const Sub sub = a.subs[s];
     if (rehist_only && !(sub.flags & kRehist)) continue;
@@ -225,7 +249,7 @@ __global__ void __launch_bounds__(kPassThreads, 4) k_hist(LevelArgs a, int rehis
         for (int j = 0; j < kChunk; ++j) {
           const int i = c0 + j * kPassThreads + threadIdx.x;
           if (i < tn) {
-            const int bk = cls.bucket_or_defer(v[j]);
+            const int bk = sm.l.kind == kPL2 ? pl2_bucket<K>(v[j], sm, pl_yf, pl_lo) : cls.bucket_or_defer(v[j]);
             if (bk >= 0) {
               ids[i] = (uint8_t)bk;
               atomicAdd(&hist[warp][bk], 1u);
@@ -287,6 +311,12 @@ __global__ void __launch_bounds__(kFitThreads) k_check(LevelArgs a) {
   if (gm.l.kind == kLinear) {
     for (int b = threadIdx.x; b < gm.l.nb; b += blockDim.x)
       if ((int64_t)a.counts[(size_t)s * kMaxK + b] == sub.n) s_redo = 1;
+  } else if (gm.l.kind == kPL2) {
+    // no progress, or one bucket above 4n/k: the splitter tree instead
+    for (int b = threadIdx.x; b < gm.l.nb; b += blockDim.x) {
+      const int64_t c = (int64_t)a.counts[(size_t)s * kMaxK + b];
+      if (c == sub.n || c * gm.l.nb > 4 * sub.n) s_redo = 1;
+    }
   }
   __syncthreads();
   if (!s_redo) return;
@@ -691,9 +721,11 @@ cudaError_t launch_fit(const LevelArgs& a, cudaStream_t s, int max_sample) {
       k_fit_warp<K><<<(a.nsub + kFitWarpsG - 1) / kFitWarpsG, kFitWarpsG * 32, wsmem, s>>>(a);
       const cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) return e;
-      if (max_sample <= kResidentSample) return cudaSuccess;  // every subproblem went to a warp
+      if (max_sample <= kResidentSample && a.pl2_leaves == 0) return cudaSuccess;  // all went to warps
     }
-    const size_t smem = (size_t)max_sample * sizeof(Ord);
+    size_t smem = (size_t)max_sample * sizeof(Ord);
+    if (a.pl2_leaves > 0 && max_sample <= kPL2MaxSample)
+      smem = ((smem + 15) & ~(size_t)15) + (size_t)kPL2MaxSample * 20;
     cudaFuncSetAttribute(k_fit<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_fit<K><<<a.nsub, kFitThreads, smem, s>>>(a);
     return cudaGetLastError();

@@ -26,7 +26,7 @@ class iplsConfig(ctypes.Structure):
                 ("spin_limit", ctypes.c_int64), ("trace_cap", ctypes.c_int64),
                 ("budget_bytes", ctypes.c_int64), ("profile", ctypes.c_int32),
                 ("flags", ctypes.c_int32), ("max_batch", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("pl2_leaves", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 FLAG_THRESHOLD_INDEX = 1
 
@@ -223,7 +223,7 @@ class Context:
     def __init__(self, *, k: int = 256, cutoff: int = 32, root_sample: int = 0, seed: int = 0,
                  exact_only: bool = False, trace_cap: int = 0, spin_limit: int | None = None,
                  stream=None, budget_bytes: int = 0, profile: bool = False, flags: int = 0,
-                 max_batch: int = 0):
+                 max_batch: int = 0, pl2_leaves: int = 0):
         import torch
         cfg = iplsDefaultConfig()
         cfg.k, cfg.cutoff, cfg.root_sample, cfg.seed = k, cutoff, root_sample, seed
@@ -233,6 +233,7 @@ class Context:
         cfg.profile = 1 if profile else 0
         cfg.flags = flags
         cfg.max_batch = max_batch
+        cfg.pl2_leaves = pl2_leaves
         if spin_limit is not None:
             cfg.spin_limit = spin_limit
         s = stream if stream is not None else torch.cuda.current_stream()
