@@ -278,8 +278,8 @@ def pl2_fit(sorted_sample: np.ndarray, M: int = 64, K: int = 256):
 
 
 def pl2_knots(m: Model) -> np.ndarray:
-    """The knot values y_0..y_M of a PL2 model."""
-    return np.array(m.split[: m.nsplit + 1], np.uint64).view(np.float64).copy()
+    """The knot values y_0..y_M of a PL2 model (binary32)."""
+    return np.array(m.split[: m.nsplit + 1], np.uint64).astype(np.uint32).view(np.float32).copy()
 
 
 def pl2_loss_grad(sorted_sample: np.ndarray, m: Model, y: np.ndarray):

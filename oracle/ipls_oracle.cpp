@@ -96,7 +96,7 @@ struct OracleModel {
   int32_t nsplit;   // splitter count (kind 1); leaves M (kind 2)
   int32_t nbuckets; // buckets of this pass: k, or 2*nsplit+1 for splitters
   uint64_t split[128];  // splitters as totalOrder bits, ascending, unique;
-                        // kind 2: the knot values y_0..y_M as binary64 bits
+                        // kind 2: the knot values y_0..y_M as binary32 bits
   int32_t pl2_sh;   // kind 2: leaf width 2^sh in fixed-point units
   int32_t pl2_rho;  // kind 2: fixed-point scale, X(x) = trunc(x / 2^rho)
   int64_t pl2_x0;   // kind 2: X(x_0), the sample minimum
@@ -323,8 +323,9 @@ void build_splitters(const T* samp, int64_t S, int32_t k, OracleModel* m) {
 // to one of M equal-width leaves of the sample's range; the leaves
 // interpolate linearly between knot values y_0..y_M, so the CDF is
 // continuous, and the knots are kept non-decreasing, so it is monotone
-// (RMIs need not be; a bucket map must be).  Bucket = floor(k F(x)) in
-// binary32, clamped per leaf to [floor(k y_j), floor(k y_{j+1})].
+// (RMIs need not be; a bucket map must be).  Trained and evaluated in
+// binary32.  Bucket = floor(k F(x)), clamped per leaf to
+// [floor(k y_j), floor(k y_{j+1})].
 // ---------------------------------------------------------------------------
 
 // X(x) = trunc(x / 2^rho) as an integer, saturating (sat = true) when
@@ -376,14 +377,15 @@ static int bit_length(uint64_t v) {
 // Per-sample features of PL2 on the sorted sample: leaf, position in it.
 struct PL2Feat {
   std::vector<int32_t> leaf;
-  std::vector<double> w;
+  std::vector<float> w;
   std::vector<int64_t> start;  // start[j]: first sample of leaf j; start[M] = S
 };
 
-// Fits PL2 on the sorted sample x[0..S) with M leaves.  Returns false (and
-// leaves m alone) when the sample's range cannot be used: equal or
-// non-finite extremes (the duplicate rule takes over) or a range that does
-// not fit the fixed point (FMCD takes over).
+// Fits PL2 on the sorted sample x[0..S) with M leaves, in binary32 (one
+// rounding per operation, sums in sample order).  Returns false (and leaves
+// m alone) when the sample's range cannot be used: equal or non-finite
+// extremes (the duplicate rule takes over) or a range that does not fit the
+// fixed point (FMCD takes over).
 template <class T>
 bool pl2_fit(const T* x, int64_t S, int32_t M, int32_t K, OracleModel* m, PL2Feat* feat_out,
              std::vector<double>* loss_trace) {
@@ -403,42 +405,39 @@ bool pl2_fit(const T* x, int64_t S, int32_t M, int32_t K, OracleModel* m, PL2Fea
   PL2Feat f;
   f.leaf.resize(S);
   f.w.resize(S);
-  const double inv = std::ldexp(1.0, -sh);
+  const float inv = std::ldexp(1.0f, -sh);
   for (int64_t i = 0; i < S; ++i) {
     bool sat;
     const int64_t U = Fixed<T>::X(x[i], rho, sat) - X0;
     int64_t j = U >> sh;
     if (j > M - 1) j = M - 1;
     f.leaf[i] = (int32_t)j;
-    f.w[i] = (double)(U - (j << sh)) * inv;
+    f.w[i] = (float)(U - (j << sh)) * inv;   // the position the classifier uses
   }
   // leaf starts: samples are sorted, so leaf j is one index range
   f.start.assign(M + 1, S);
-  for (int32_t j = M; j >= 0; --j) {
+  for (int32_t j = 0; j < M; ++j) {
     int64_t c = 0;
-    if (j < M) {
-      c = 0;
-      while (c < S && f.leaf[c] < j) ++c;
-    }
-    f.start[j] = (j == M) ? S : c;
+    while (c < S && f.leaf[c] < j) ++c;
+    f.start[j] = c;
   }
-  std::vector<double> y(M + 1), tau(S), r(S), G(M + 1), H(M + 1);
-  for (int64_t i = 0; i < S; ++i) tau[i] = ((double)i + 0.5) / (double)S;
+  std::vector<float> y(M + 1), tau(S), r(S), G(M + 1), H(M + 1);
+  for (int64_t i = 0; i < S; ++i) tau[i] = ((float)i + 0.5f) / (float)S;
   // initial knots: the empirical CDF at the knots
-  for (int32_t j = 0; j <= M; ++j) y[j] = (double)f.start[j] / (double)S;
+  for (int32_t j = 0; j <= M; ++j) y[j] = (float)f.start[j] / (float)S;
   auto loss = [&]() {
     double L = 0.0;
-    for (int64_t i = 0; i < S; ++i) L += r[i] * r[i];
+    for (int64_t i = 0; i < S; ++i) L += (double)r[i] * (double)r[i];
     return L / (double)S;
   };
   for (int step = 0; step <= kPL2Steps; ++step) {
     // forward: F and the residual of every sample
     for (int64_t i = 0; i < S; ++i) {
       const int32_t a = f.leaf[i];
-      const double t1 = 1.0 - f.w[i];
-      const double p = y[a] * t1;
-      const double q = y[a + 1] * f.w[i];
-      const double F = p + q;
+      const float t1 = 1.0f - f.w[i];
+      const float p = y[a] * t1;
+      const float q = y[a + 1] * f.w[i];
+      const float F = p + q;
       r[i] = F - tau[i];
     }
     if (loss_trace) loss_trace->push_back(loss());
@@ -446,30 +445,30 @@ bool pl2_fit(const T* x, int64_t S, int32_t M, int32_t K, OracleModel* m, PL2Fea
     // backward: dL/dy_j = (2/S) G_j and curvature (2/S) H_j, summed over
     // leaf j (weight 1-w) then leaf j-1 (weight w), in sample order
     for (int32_t j = 0; j <= M; ++j) {
-      double g = 0.0, h = 0.0;
+      float g = 0.0f, h = 0.0f;
       if (j < M)
         for (int64_t i = f.start[j]; i < f.start[j + 1]; ++i) {
-          const double t1 = 1.0 - f.w[i];
-          g += r[i] * t1;
-          h += t1 * t1;
+          const float t1 = 1.0f - f.w[i];
+          g = g + r[i] * t1;
+          h = h + t1 * t1;
         }
       if (j > 0)
         for (int64_t i = f.start[j - 1]; i < f.start[j]; ++i) {
-          g += r[i] * f.w[i];
-          h += f.w[i] * f.w[i];
+          g = g + r[i] * f.w[i];
+          h = h + f.w[i] * f.w[i];
         }
       G[j] = g;
       H[j] = h;
     }
     // half a diagonal Newton step on every knot (the 2/S factors cancel)
     for (int32_t j = 0; j <= M; ++j)
-      if (H[j] > 0.0) {
-        const double q = G[j] / H[j];
-        y[j] = y[j] - 0.5 * q;
+      if (H[j] > 0.0f) {
+        const float q = G[j] / H[j];
+        y[j] = y[j] - 0.5f * q;
       }
     // keep the knots in [0, 1] and non-decreasing
-    y[0] = std::min(std::max(y[0], 0.0), 1.0);
-    for (int32_t j = 1; j <= M; ++j) y[j] = std::min(std::max(y[j], y[j - 1]), 1.0);
+    y[0] = std::min(std::max(y[0], 0.0f), 1.0f);
+    for (int32_t j = 1; j <= M; ++j) y[j] = std::min(std::max(y[j], y[j - 1]), 1.0f);
   }
   m->kind = 2;
   m->capped = 0;
@@ -480,7 +479,11 @@ bool pl2_fit(const T* x, int64_t S, int32_t M, int32_t K, OracleModel* m, PL2Fea
   m->pl2_sh = sh;
   m->pl2_rho = rho;
   m->pl2_x0 = X0;
-  for (int32_t j = 0; j <= M; ++j) std::memcpy(&m->split[j], &y[j], 8);
+  for (int32_t j = 0; j <= M; ++j) {
+    uint32_t b32;
+    std::memcpy(&b32, &y[j], 4);
+    m->split[j] = b32;   // binary32 knot bits
+  }
   if (feat_out) *feat_out = f;
   return true;
 }
@@ -501,10 +504,11 @@ int32_t pl2_bucket(T x, const OracleModel& m) {
   if (U < 0) return 0;
   const int64_t j = U >> m.pl2_sh;
   if (j >= M) return K - 1;
-  double yd0, yd1;
-  std::memcpy(&yd0, &m.split[j], 8);
-  std::memcpy(&yd1, &m.split[j + 1], 8);
-  const float y0 = (float)yd0, y1 = (float)yd1, kf = (float)K;
+  float y0, y1;
+  const uint32_t b0 = (uint32_t)m.split[j], b1 = (uint32_t)m.split[j + 1];
+  std::memcpy(&y0, &b0, 4);
+  std::memcpy(&y1, &b1, 4);
+  const float kf = (float)K;
   const float inv = std::ldexp(1.0f, -m.pl2_sh);
   const float w = (float)(U - (j << m.pl2_sh)) * inv;
   const float d = y1 - y0;

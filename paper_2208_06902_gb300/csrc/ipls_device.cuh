@@ -657,14 +657,15 @@ struct ExactQueue {
 // range; leaf j interpolates between knot values y_j and y_{j+1}.
 // Training: knots start at the empirical CDF, then kPL2Steps steps of half
 // a diagonal Newton step per knot, each followed by clamping the knots into
-// [0, 1] non-decreasing.  Every sum runs over sample indices in order (the
-// samples of a leaf are contiguous), with one rounding per operation, so
-// the model is the same bit for bit wherever it is computed.
+// [0, 1] non-decreasing.  Binary32 throughout; every sum runs over sample
+// indices in order (the samples of a leaf are contiguous), with one rounding
+// per operation, so the model is the same bit for bit wherever it is
+// computed.
 // ---------------------------------------------------------------------------
 struct PL2Scratch {
   int32_t* leaf;    // [S]
-  double* w;        // [S]
-  double* r;        // [S]
+  float* w;         // [S]
+  float* r;         // [S]
 };
 
 __device__ __forceinline__ int exponent_of(double r) {
@@ -675,9 +676,10 @@ __device__ __forceinline__ int exponent_of(double r) {
 
 // Block-wide (all threads).  so[0..S) is the sorted sample (order bits).
 // Returns false (m untouched) when the sample's range cannot carry PL2.
+// Training is binary32, one rounding per operation.
 template <class K>
 __device__ bool fit_pl2(const typename KT<K>::Ord* so, int S, int M, int K_, Model* m,
-                        PL2Scratch sc, double* y, int64_t* start, int* s_flag, long long* s_x0,
+                        PL2Scratch sc, float* y, int* start, int* s_flag, long long* s_x0,
                         int* s_rho, int* s_sh) {
   using T = KT<K>;
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -707,14 +709,14 @@ __device__ bool fit_pl2(const typename KT<K>::Ord* so, int S, int M, int K_, Mod
   if (!*s_flag) return false;
   const int rho = *s_rho, sh = *s_sh;
   const long long X0 = *s_x0;
-  const double inv = __longlong_as_double((long long)(1023 - sh) << 52);  // 2^-sh
+  const float inv = __int_as_float((127 - sh) << 23);  // 2^-sh
   for (int i = tid; i < S; i += nt) {
     bool sat;
     const long long U = fixed_point<K>(T::unord(so[i]), rho, sat) - X0;
     long long j = U >> sh;
     if (j > M - 1) j = M - 1;
     sc.leaf[i] = (int32_t)j;
-    sc.w[i] = __dmul_rn((double)(U - (j << sh)), inv);
+    sc.w[i] = __fmul_rn(__ll2float_rn(U - (j << sh)), inv);
   }
   __syncthreads();
   // leaf starts: the first sample of every leaf (leaves are non-decreasing)
@@ -725,45 +727,45 @@ __device__ bool fit_pl2(const typename KT<K>::Ord* so, int S, int M, int K_, Mod
       if (sc.leaf[mid] < j) lo = mid + 1; else hi = mid;
     }
     start[j] = (j == M) ? S : lo;
-    y[j] = __ddiv_rn((double)((j == M) ? S : lo), (double)S);
+    y[j] = __fdiv_rn((float)((j == M) ? S : lo), (float)S);
   }
   __syncthreads();
   for (int step = 0; step < kPL2Steps; ++step) {
     for (int i = tid; i < S; i += nt) {  // forward: residual of every sample
       const int a = sc.leaf[i];
-      const double t1 = __dsub_rn(1.0, sc.w[i]);
-      const double F = __dadd_rn(__dmul_rn(y[a], t1), __dmul_rn(y[a + 1], sc.w[i]));
-      const double tau = __ddiv_rn(__dadd_rn((double)i, 0.5), (double)S);
-      sc.r[i] = __dsub_rn(F, tau);
+      const float t1 = __fsub_rn(1.0f, sc.w[i]);
+      const float F = __fadd_rn(__fmul_rn(y[a], t1), __fmul_rn(y[a + 1], sc.w[i]));
+      const float tau = __fdiv_rn(__fadd_rn((float)i, 0.5f), (float)S);
+      sc.r[i] = __fsub_rn(F, tau);
     }
     __syncthreads();
-    double q = 0.0;
+    float q = 0.0f;
     bool upd = false;
     if (tid <= M) {  // backward: gradient and curvature of knot tid
       const int j = tid;
-      double g = 0.0, h = 0.0;
+      float g = 0.0f, h = 0.0f;
       if (j < M)
-        for (int64_t i = start[j]; i < start[j + 1]; ++i) {
-          const double t1 = __dsub_rn(1.0, sc.w[i]);
-          g = __dadd_rn(g, __dmul_rn(sc.r[i], t1));
-          h = __dadd_rn(h, __dmul_rn(t1, t1));
+        for (int i = start[j]; i < start[j + 1]; ++i) {
+          const float t1 = __fsub_rn(1.0f, sc.w[i]);
+          g = __fadd_rn(g, __fmul_rn(sc.r[i], t1));
+          h = __fadd_rn(h, __fmul_rn(t1, t1));
         }
       if (j > 0)
-        for (int64_t i = start[j - 1]; i < start[j]; ++i) {
-          g = __dadd_rn(g, __dmul_rn(sc.r[i], sc.w[i]));
-          h = __dadd_rn(h, __dmul_rn(sc.w[i], sc.w[i]));
+        for (int i = start[j - 1]; i < start[j]; ++i) {
+          g = __fadd_rn(g, __fmul_rn(sc.r[i], sc.w[i]));
+          h = __fadd_rn(h, __fmul_rn(sc.w[i], sc.w[i]));
         }
-      if (h > 0.0) {
-        q = __ddiv_rn(g, h);
+      if (h > 0.0f) {
+        q = __fdiv_rn(g, h);
         upd = true;
       }
     }
     __syncthreads();
-    if (upd) y[tid] = __dsub_rn(y[tid], __dmul_rn(0.5, q));
+    if (upd) y[tid] = __fsub_rn(y[tid], __fmul_rn(0.5f, q));
     __syncthreads();
     if (tid == 0) {  // knots in [0, 1], non-decreasing
-      y[0] = fmin(fmax(y[0], 0.0), 1.0);
-      for (int j = 1; j <= M; ++j) y[j] = fmin(fmax(y[j], y[j - 1]), 1.0);
+      y[0] = fminf(fmaxf(y[0], 0.0f), 1.0f);
+      for (int j = 1; j <= M; ++j) y[j] = fminf(fmaxf(y[j], y[j - 1]), 1.0f);
     }
     __syncthreads();
   }
@@ -778,19 +780,19 @@ __device__ bool fit_pl2(const typename KT<K>::Ord* so, int S, int M, int K_, Mod
     m->l.qlo = X0;
     m->nsplit = M;
   }
-  for (int j = tid; j <= M; j += nt) m->split[j] = (uint64_t)__double_as_longlong(y[j]);
+  for (int j = tid; j <= M; j += nt) m->split[j] = (uint64_t)__float_as_uint(y[j]);
   __syncthreads();
   return true;
 }
 
-// Per-model tables for classifying with a PL2 model: binary32 knots and the
-// first bucket of every leaf.
+// Per-model tables for classifying with a PL2 model: the binary32 knots and
+// the first bucket of every leaf.
 __device__ __forceinline__ void pl2_tables(const Model& m, float* yf, int* lo, int nthreads_tid,
                                            int nthreads) {
   const int M = m.nsplit, K = m.l.nb;
   const float kf = (float)K;
   for (int j = nthreads_tid; j <= M; j += nthreads) {
-    yf[j] = __double2float_rn(__longlong_as_double((long long)m.split[j]));
+    yf[j] = __uint_as_float((unsigned)m.split[j]);
     int b = (int)floorf(__fmul_rn(yf[j], kf));
     lo[j] = b > K - 1 ? K - 1 : b;
   }

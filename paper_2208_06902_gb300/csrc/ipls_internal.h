@@ -22,7 +22,7 @@ enum ModelKind : int32_t { kLinear = 0, kSplitter = 1, kPL2 = 2 };
 // PL2 (piecewise-linear CDF): used, when enabled, for subproblems larger
 // than kPL2MinKeys whose sample has at most kPL2MaxSample keys; trained for
 // kPL2Steps steps.  Model layout: l.kind = kPL2, l.nb = k, l.S, l.D = l.rho
-// ... see fit_pl2; nsplit = leaves M, split[0..M] = knot values (binary64).
+// ... see fit_pl2; nsplit = leaves M, split[0..M] = knot values (binary32 bits).
 constexpr int64_t kPL2MinKeys = 8192;
 constexpr int kPL2MaxSample = 4096;
 constexpr int kPL2Steps = 8;

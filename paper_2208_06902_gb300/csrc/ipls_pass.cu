@@ -149,10 +149,10 @@ __global__ void __launch_bounds__(kFitThreads) k_fit(LevelArgs a) {
   if (takes_pl2(a, sub, S)) {
     // scratch after the sample: leaf, w and r per sample
     unsigned char* base = smem + (((size_t)a.max_sample * sizeof(Ord) + 15) & ~(size_t)15);
-    PL2Scratch sc{reinterpret_cast<int32_t*>(base + (size_t)kPL2MaxSample * 16),
-                  reinterpret_cast<double*>(base), reinterpret_cast<double*>(base + (size_t)kPL2MaxSample * 8)};
-    __shared__ double py[kPL2MaxLeaves + 1];
-    __shared__ int64_t pstart[kPL2MaxLeaves + 1];
+    PL2Scratch sc{reinterpret_cast<int32_t*>(base + (size_t)kPL2MaxSample * 8),
+                  reinterpret_cast<float*>(base), reinterpret_cast<float*>(base + (size_t)kPL2MaxSample * 4)};
+    __shared__ float py[kPL2MaxLeaves + 1];
+    __shared__ int pstart[kPL2MaxLeaves + 1];
     __shared__ int pflag, prho, psh;
     __shared__ long long px0;
     if (threadIdx.x == 0) sm.nsplit = 0;
@@ -725,7 +725,7 @@ cudaError_t launch_fit(const LevelArgs& a, cudaStream_t s, int max_sample) {
     }
     size_t smem = (size_t)max_sample * sizeof(Ord);
     if (a.pl2_leaves > 0 && max_sample <= kPL2MaxSample)
-      smem = ((smem + 15) & ~(size_t)15) + (size_t)kPL2MaxSample * 20;
+      smem = ((smem + 15) & ~(size_t)15) + (size_t)kPL2MaxSample * 12;
     cudaFuncSetAttribute(k_fit<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_fit<K><<<a.nsub, kFitThreads, smem, s>>>(a);
     return cudaGetLastError();

@@ -45,7 +45,7 @@ def test_first_loss_is_that_of_the_empirical_cdf_at_the_knots():
     U = np.array([_fixed(v, rho) for v in x]) - m.pl2_x0
     y0 = np.array([np.count_nonzero(U < (j << sh)) / S for j in range(M + 1)])
     L0, _ = oracle.pl2_loss_grad(x, m, y0)
-    assert L0 == pytest.approx(losses[0], rel=1e-12)
+    assert L0 == pytest.approx(losses[0], rel=1e-4)   # training runs in binary32
     assert y0[0] == 0.0 and y0[-1] == 1.0
 
 
@@ -56,7 +56,7 @@ def test_training_does_not_raise_the_loss_and_knots_are_monotone(dist):
     if r is None:
         pytest.skip("degenerate sample")
     m, losses = r
-    assert losses[-1] <= losses[0] * (1 + 1e-12)
+    assert losses[-1] <= losses[0] * (1 + 1e-6)
     y = oracle.pl2_knots(m)
     assert np.all(np.diff(y) >= 0) and y[0] >= 0 and y[-1] <= 1
 
@@ -107,3 +107,18 @@ def test_a_dense_cluster_falls_back_to_the_splitter_tree():
     assert np.array_equal(got, oracle.std_sort(x))
     root = [r for r in recs if r.level == 0][0]
     assert root.model.kind == 1
+
+
+@pytest.mark.parametrize("dist", ["lognormal", "exponential"])
+def test_pl2_balances_a_skewed_root_better_than_fmcd(dist):
+    # what the learned CDF gains: on skewed keys the linear FMCD model leaves
+    # some root buckets far above n/k; the trained PL2 stays close to n/k
+    x = datagen.generate(dist, 1 << 20, np.float64, seed=7)
+    _, rf, _ = oracle.sort(x, cutoff=256, trace_cap=50_000)
+    _, rp, _ = oracle.sort(x, cutoff=256, trace_cap=50_000, pl2_leaves=64)
+    root_f = [r for r in rf if r.level == 0][0]
+    root_p = [r for r in rp if r.level == 0][0]
+    assert root_p.model.kind == 2 and root_f.model.kind == 0
+    max_f = max(root_f.counts[: root_f.model.nbuckets])
+    max_p = max(root_p.counts[: root_p.model.nbuckets])
+    assert max_p * 2 < max_f, (max_p, max_f)
