@@ -373,8 +373,19 @@ struct FitShared {
 // dq reaches t_hi certainly passes and one below t_lo certainly fails (the
 // margins cover both the truncations and the roundings).  Only windows in
 // between are decided with u_d and the gap computed in binary64.
+// q, when given, holds the sample's fixed-point images (q[i] = X(so[i]) at
+// fs.rho), computed once per fit instead of once per window and probe.
+template <class K>
+__device__ __forceinline__ long long fixed_of(const typename KT<K>::Ord* so, const long long* q, int i,
+                                              int rho) {
+  if (q) return q[i];
+  bool sat;
+  return fixed_point<K>(KT<K>::unord(so[i]), rho, sat);
+}
+
 template <class G, class K>
-__device__ bool fmcd_probe(const typename KT<K>::Ord* so, int N, int D, int K_, FitShared& fs) {
+__device__ bool fmcd_probe(const typename KT<K>::Ord* so, const long long* q, int N, int D, int K_,
+                           FitShared& fs) {
   using T = KT<K>;
   int fail = 0, amb = 0;
   const int W = N - D;  // windows i = 0 .. N-1-D
@@ -382,17 +393,14 @@ __device__ bool fmcd_probe(const typename KT<K>::Ord* so, int N, int D, int K_, 
   const int rho = fs.rho;
   long long t_lo = -1, t_hi = 0;
   if (filter) {
-    bool s1, s2;
-    const long long Sq = fixed_point<K>(T::unord(so[N - 1 - D]), rho, s1) -
-                         fixed_point<K>(T::unord(so[D]), rho, s2);
+    const long long Sq = fixed_of<K>(so, q, N - 1 - D, rho) - fixed_of<K>(so, q, D, rho);
     const long long km2 = K_ - 2;
     const long long marg = (Sq >> 48) + 8;
     t_hi = (Sq + 2 + marg) / km2 + 3;
     const long long lo_num = Sq - 2 - marg;
     t_lo = lo_num > 0 ? lo_num / km2 - 3 : -1;
     for (int i = G::tid(); i < W; i += G::size()) {
-      const long long dq = fixed_point<K>(T::unord(so[i + D]), rho, s1) -
-                           fixed_point<K>(T::unord(so[i]), rho, s2);
+      const long long dq = fixed_of<K>(so, q, i + D, rho) - fixed_of<K>(so, q, i, rho);
       if (dq < t_lo) fail = 1;
       else if (dq < t_hi) amb = 1;
     }
@@ -408,9 +416,7 @@ __device__ bool fmcd_probe(const typename KT<K>::Ord* so, int N, int D, int K_, 
   if (amb) {
     for (int i = G::tid(); i < W; i += G::size()) {
       if (filter) {
-        bool s1, s2;
-        const long long dq = fixed_point<K>(T::unord(so[i + D]), rho, s2) -
-                             fixed_point<K>(T::unord(so[i]), rho, s1);
+        const long long dq = fixed_of<K>(so, q, i + D, rho) - fixed_of<K>(so, q, i, rho);
         if (dq < t_lo || dq >= t_hi) continue;
       }
       if (!(T::diff(T::unord(so[i + D]), T::unord(so[i])) >= ud)) { fail = 1; break; }
@@ -424,7 +430,8 @@ __device__ bool fmcd_probe(const typename KT<K>::Ord* so, int N, int D, int K_, 
 // sample's extremes are equal or not finite or FMCD degenerates (u_d <= 0
 // or not finite, A or Bc not finite); the FMCD fields are kept either way.
 template <class G, class K>
-__device__ void fit_linear(const typename KT<K>::Ord* so, int N, int K_, LinModel* m, FitShared& fs) {
+__device__ void fit_linear(const typename KT<K>::Ord* so, int N, int K_, LinModel* m, FitShared& fs,
+                           long long* q = nullptr) {
   using T = KT<K>;
   using Bits = typename T::Bits;
   if (G::tid() == 0) {
@@ -454,18 +461,26 @@ __device__ void fit_linear(const typename KT<K>::Ord* so, int N, int K_, LinMode
     }
   }
   G::sync();
+  if (fs.linear && q && fs.filter) {  // fixed-point images, once
+    for (int i = G::tid(); i < N; i += G::size()) {
+      bool sat;
+      q[i] = fixed_point<K>(T::unord(so[i]), fs.rho, sat);
+    }
+    G::sync();
+  }
+  if (!fs.filter) q = nullptr;
   if (fs.linear) {
     const int Dcap = N / 3 + 1;  // smallest D with 3D > N
     int D;
     int capped = 0;
-    if (!fmcd_probe<G, K>(so, N, Dcap - 1, K_, fs)) {
+    if (!fmcd_probe<G, K>(so, q, N, Dcap - 1, K_, fs)) {
       capped = 1;
       D = Dcap;
     } else {
       int lo = 1, hi = Dcap - 1;
       while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        if (fmcd_probe<G, K>(so, N, mid, K_, fs)) hi = mid; else lo = mid + 1;
+        if (fmcd_probe<G, K>(so, q, N, mid, K_, fs)) hi = mid; else lo = mid + 1;
       }
       D = lo;
     }

@@ -35,8 +35,14 @@ constexpr int kFitWarps = 8;
 // tail task: n <= 8192 gives at most 664), bitonic network above
 constexpr int kRadixSteps = 22;
 constexpr int kRadixMax = 32 * kRadixSteps;
-constexpr int kFitSlot = 2 * kRadixMax;  // sample + radix buffer per warp
-static_assert(kFitSlot >= kResidentSample, "a warp's slot must also hold the largest sample");
+// Per warp: the sample (kRadixMax keys), then kRadixMax 8-byte words that
+// hold first the radix sort's second buffer and then the sample's
+// fixed-point images.  A bitonic-sorted sample (up to kResidentSample keys)
+// uses the whole slot.
+template <class Ord>
+__host__ __device__ constexpr size_t fit_slot_bytes() { return (size_t)kRadixMax * sizeof(Ord) + (size_t)kRadixMax * 8; }
+static_assert(fit_slot_bytes<unsigned int>() >= kResidentSample * 4, "slot must hold the largest sample");
+static_assert(fit_slot_bytes<unsigned long long>() >= kResidentSample * 8, "slot must hold the largest sample");
 
 // ---------------------------------------------------------------------------
 // k_tail_fit
@@ -53,7 +59,10 @@ __global__ void __launch_bounds__(kFitWarps * 32) k_tail_fit(ResidentArgs a) {
   for (int i = lane; i < 256; i += 32) rpeer[warp][i] = 0u;
   const int task = blockIdx.x * kFitWarps + warp;
   if (task >= a.nfit) return;
-  Ord* so = reinterpret_cast<Ord*>(smem_raw) + warp * kFitSlot;
+  unsigned char* slot = smem_raw + (size_t)warp * fit_slot_bytes<Ord>();
+  Ord* so = reinterpret_cast<Ord*>(slot);
+  Ord* rtmp = reinterpret_cast<Ord*>(slot + (size_t)kRadixMax * sizeof(Ord));
+  long long* qimg = reinterpret_cast<long long*>(slot + (size_t)kRadixMax * sizeof(Ord));
   const Group g = a.groups[a.fit_list[task]];
   int S = (int)sample_size(g.n, g.level, a.k, a.root_sample);
   if (S > kResidentSample) S = kResidentSample;  // never planned by the host
@@ -61,10 +70,11 @@ __global__ void __launch_bounds__(kFitWarps * 32) k_tail_fit(ResidentArgs a) {
   const typename T::Bits* src = reinterpret_cast<const typename T::Bits*>(a.buf[g.buf]) + g.off;
   for (int j = lane; j < S; j += 32) so[j] = T::ord(src[sample_offset(stream, j, g.n)]);
   __syncwarp();
-  if (S <= kRadixMax) warp_radix_sort<kRadixSteps>(so, so + kRadixMax, rcnt[warp], rpeer[warp], S);
+  if (S <= kRadixMax) warp_radix_sort<kRadixSteps>(so, rtmp, rcnt[warp], rpeer[warp], S);
   else group_sort<WarpG, Ord>(so, S);
   TailModel& m = tm[warp];
-  fit_linear<WarpG, K>(so, S, a.k, &m.l, fs[warp]);
+  // after the radix sort its second buffer holds the fixed-point images
+  fit_linear<WarpG, K>(so, S, a.k, &m.l, fs[warp], S <= kRadixMax ? qimg : nullptr);
   if (lane == 0) {
     m.nsplit = 0;
     m.pool = -1;
@@ -703,7 +713,7 @@ cudaError_t launch_tail_fit(const ResidentArgs& a, cudaStream_t s) {
   if (a.nfit <= 0) return cudaSuccess;
   return by_dtype_r(a.dtype, [&](auto* tag) {
     using K = std::remove_pointer_t<decltype(tag)>;
-    const size_t smem = (size_t)kFitWarps * kFitSlot * sizeof(typename KT<K>::Ord);
+    const size_t smem = (size_t)kFitWarps * fit_slot_bytes<typename KT<K>::Ord>();
     cudaFuncSetAttribute(k_tail_fit<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int blocks = (a.nfit + kFitWarps - 1) / kFitWarps;
     k_tail_fit<K><<<blocks, kFitWarps * 32, smem, s>>>(a);
