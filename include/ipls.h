@@ -136,6 +136,8 @@ typedef struct iplsStats {
   double max_bucket_frac;     /* largest bucket / subproblem size, grid passes */
   int64_t slow_tasks;         /* ranges recursed inside one block (slow list), last call */
   int64_t slow_passes;        /* partition passes run by that in-block recursion, last call */
+  int64_t sweep_tasks;        /* children above the cutoff taken by a second block-resident
+                                 sweep (fit + pass + base case) instead, last call */
 } iplsStats;
 
 typedef struct iplsContext* iplsCtx;

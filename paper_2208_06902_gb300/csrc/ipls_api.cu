@@ -122,6 +122,7 @@ struct iplsContext {
   // slow list of the block-resident tail
   SlowTask* slow = nullptr; int64_t slow_cap = 0;
   SlowCtl* slow_ctl = nullptr;
+  SlowCtl* h_slow = nullptr;          // pinned copy of *slow_ctl
   uint64_t* split_pool = nullptr;     int64_t split_pool_cap = 0;  // words
 };
 
@@ -171,11 +172,11 @@ iplsStatus ensure(iplsCtx c, T*& p, int64_t& cap, int64_t need) {
 bool valid_dtype(int d) { return d >= 0 && d <= 3; }
 
 enum KernelKind { kkFit, kkHist, kkCheck, kkRehist, kkScan, kkScatter, kkResident, kkFill,
-                  kkInitSeg, kkInitTiles, kkTailFit, kkTileScan, kkSlow, kkCount };
+                  kkInitSeg, kkInitTiles, kkTailFit, kkTileScan, kkSlow, kkSlowGroups, kkCount };
 const char* const kKernelNames[kkCount] = {"k_fit", "k_hist", "k_check", "k_hist_redo", "k_scan",
                                            "k_scatter", "k_tail", "k_fill",
                                            "k_init_segments", "k_init_tiles", "k_tail_fit",
-                                           "k_tilescan", "k_slow"};
+                                           "k_tilescan", "k_slow", "k_slow_groups"};
 
 cudaEvent_t take_event(iplsCtx c) {
   if (!c->spare_events.empty()) {
@@ -231,22 +232,64 @@ iplsStatus ensure_groups(iplsCtx c, Slot& s, int64_t need) {
   return IPLS_OK;
 }
 
-// Fits and runs the block-resident tasks listed in slot s.
+// Splitter-pool slots for a tail sweep of nfit fitted tasks.
+int64_t pool_slots(int64_t nfit) {
+  return std::min<int64_t>(std::max<int64_t>(nfit, kSplitPoolMin), kSplitPoolMax);
+}
+
+// One sweep of k_tail_fit + k_tail over the groups in ra.
+iplsStatus tail_sweep(iplsCtx c, ResidentArgs& ra) {
+  if (ra.nfit > 0) {
+    IPLS_TRY(ensure(c, c->split_pool, c->split_pool_cap, pool_slots(ra.nfit) * 128));
+    ra.split_pool = c->split_pool;
+    ra.split_pool_slots = (int32_t)std::min<int64_t>(c->split_pool_cap / 128, kSplitPoolMax);
+    IPLS_CUDA(timed(c, kkTailFit, [&] { return launch_tail_fit(ra, c->stream); }));
+  }
+  IPLS_CUDA(timed(c, kkResident, [&] { return launch_resident(ra, c->stream); }));
+  return IPLS_OK;
+}
+
+// Fits and runs the block-resident tasks listed in slot s: one sweep over
+// them, a second one over the children above the cutoff when the first
+// queued many (in place in the user buffer; the slot's group list is free
+// again once the first sweep ran), and k_slow for the rest.
 iplsStatus launch_tail(iplsCtx c, ResidentArgs& ra, Slot& s, int32_t ngroups, int32_t nfit) {
   ra.groups = s.groups;
   ra.ngroups = ngroups;
   ra.fit_list = s.fit_list;
   ra.nfit = nfit;
   ra.tail_models = s.tails;
+  // disjoint ranges of more than `cutoff` keys each: both lists together
+  // hold at most n / (cutoff + 1), and each half of the buffer holds that
+  const int64_t half = c->slow_cap / 2;
   ra.slow = c->slow;
-  ra.slow_cap = (int32_t)std::min<int64_t>(c->slow_cap, INT32_MAX);
+  ra.slow_cap = (int32_t)std::min<int64_t>(half, INT32_MAX);
+  ra.whole = c->slow + half;
+  ra.whole_cap = (int32_t)std::min<int64_t>(c->slow_cap - half, INT32_MAX);
   ra.slow_ctl = c->slow_ctl;
-  if (ngroups <= 0) return IPLS_OK;
-  if (nfit > 0) IPLS_TRY(ensure(c, c->split_pool, c->split_pool_cap, (int64_t)kSplitPoolCap * 128));
   ra.split_pool = c->split_pool;
+  ra.split_pool_slots = (int32_t)std::min<int64_t>(c->split_pool_cap / 128, kSplitPoolMax);
+  if (ngroups <= 0) return IPLS_OK;
   IPLS_CUDA(cudaMemsetAsync(c->slow_ctl, 0, sizeof(SlowCtl), c->stream));
-  if (nfit > 0) IPLS_CUDA(timed(c, kkTailFit, [&] { return launch_tail_fit(ra, c->stream); }));
-  IPLS_CUDA(timed(c, kkResident, [&] { return launch_resident(ra, c->stream); }));
+  IPLS_TRY(tail_sweep(c, ra));
+  if (ngroups >= kTailSweepMin) {
+    IPLS_CUDA(cudaMemcpyAsync(c->h_slow, c->slow_ctl, sizeof(SlowCtl), cudaMemcpyDeviceToHost, c->stream));
+    IPLS_CUDA(cudaStreamSynchronize(c->stream));
+    const int32_t nc = c->h_slow->count;
+    if (nc >= kTailSweepMin && nc <= ra.slow_cap) {
+      IPLS_TRY(ensure_groups(c, s, nc));
+      IPLS_CUDA(timed(c, kkSlowGroups, [&] { return launch_slow_groups(c->slow, nc, s.groups, s.fit_list, c->stream); }));
+      // the child list starts again (count, ticket, pool_used); whole tasks stay
+      IPLS_CUDA(cudaMemsetAsync(c->slow_ctl, 0, 3 * sizeof(int32_t), c->stream));
+      ra.groups = s.groups;
+      ra.ngroups = nc;
+      ra.fit_list = s.fit_list;
+      ra.nfit = nc;
+      ra.tail_models = s.tails;
+      IPLS_TRY(tail_sweep(c, ra));
+      c->stats.sweep_tasks += nc;
+    }
+  }
   IPLS_CUDA(timed(c, kkSlow, [&] { return launch_slow(ra, c->stream, c->num_sms); }));
   return IPLS_OK;
 }
@@ -282,6 +325,7 @@ iplsStatus sort_impl(iplsCtx c, void* keys, int64_t n, int dtype, const int64_t*
   c->stats.keys_partitioned = 0;
   c->stats.resident_groups = 0;
   c->stats.fallback_passes = 0;
+  c->stats.sweep_tasks = 0;
   c->stats.algorithmic_bytes = 0;
   c->stats.max_bucket_frac = 0.0;
   c->trace_grid_count = 0;
@@ -709,10 +753,12 @@ iplsStatus iplsCreate(iplsCtx* out, const iplsConfig* cfg, iplsAllocFn alloc, ip
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
   if (e == cudaSuccess) e = cudaMallocHost(&c->h_ctl, sizeof(LevelCtl));
   if (e == cudaSuccess) e = cudaMallocHost(&c->h_run, sizeof(RunStatus));
+  if (e == cudaSuccess) e = cudaMallocHost(&c->h_slow, sizeof(SlowCtl));
   if (e != cudaSuccess) {
     cudaGetLastError();
     if (c->h_ctl) cudaFreeHost(c->h_ctl);
     if (c->h_run) cudaFreeHost(c->h_run);
+    if (c->h_slow) cudaFreeHost(c->h_slow);
     delete c;
     return cuda_fail(e, "iplsCreate");
   }
@@ -765,6 +811,7 @@ iplsStatus iplsDestroy(iplsCtx c) {
   dev_free(c, c->trace_res, (size_t)c->trace_alloc * sizeof(iplsTraceRecDev));
   if (c->h_ctl) cudaFreeHost(c->h_ctl);
   if (c->h_run) cudaFreeHost(c->h_run);
+  if (c->h_slow) cudaFreeHost(c->h_slow);
   for (auto& p : c->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
   for (cudaEvent_t e : c->spare_events) cudaEventDestroy(e);
   dev_free(c, c->host_stage, (size_t)c->host_stage_cap);
@@ -784,7 +831,7 @@ iplsStatus iplsScratchBytes(iplsCtx c, int64_t n, iplsDtype dtype, size_t* bytes
   const int64_t tiles = n / tile_keys(dtype) + subs + 2;
   size_t b = (size_t)n * key_bytes(dtype);                         // ping-pong keys
   b += (size_t)n;                                                  // bucket ids
-  b += (size_t)kSplitPoolCap * 128 * 8;                            // splitter pool
+  b += (size_t)pool_slots(n / (cutoff + 1)) * 128 * 8;             // splitter pool
   b += (size_t)tiles * kMaxK * 8;                                  // look-back words
   b += 2 * (size_t)subs * (sizeof(Sub) + sizeof(Model) + kMaxK * 8 + 257 * 8);
   b += 2 * (size_t)tiles * 4;

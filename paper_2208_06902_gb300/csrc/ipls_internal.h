@@ -174,18 +174,25 @@ struct SlowTask {
   int32_t level;
 };
 
-// Counters of the slow list (zeroed before each tail launch).
+// Counters of the slow lists (zeroed before each tail launch).  `count`
+// children above the cutoff wait in the child list, `wcount` whole tasks
+// (no progress, or no pool slot for their splitters) in the whole list.
 struct SlowCtl {
   int32_t count;
   uint32_t ticket;
-  int32_t pool_used;   // splitter-pool slots taken by this tail launch
-  int32_t pad;
+  int32_t pool_used;   // splitter-pool slots taken by this tail sweep
+  int32_t wcount;
 };
 
 // Splitters of a tail task whose tree has more than kTailSplit of them (one
 // pool slot per such task; a task that finds the pool full takes the slow
-// path).
-constexpr int kSplitPoolCap = 16384;
+// path).  The pool has a slot for every fitted task of a round, at least
+// kSplitPoolMin and at most kSplitPoolMax of them.
+constexpr int kSplitPoolMin = 16384;
+constexpr int kSplitPoolMax = 1 << 18;
+// A second tail sweep takes the children above the cutoff when the first
+// round queued at least this many (fewer go straight to k_slow).
+constexpr int kTailSweepMin = 1024;
 
 // Per-level device arrays (all device pointers).
 struct LevelArgs {
@@ -250,10 +257,13 @@ struct ResidentArgs {
   const int32_t* fit_list;
   int32_t nfit;
   TailModel* tail_models;          // indexed by Group::fit
-  SlowTask* slow;                  // slow list (capacity slow_cap)
+  SlowTask* slow;                  // child list (capacity slow_cap)
   int32_t slow_cap;
+  int32_t whole_cap;
+  SlowTask* whole;                 // whole-task list (capacity whole_cap)
   SlowCtl* slow_ctl;
-  uint64_t* split_pool;            // [kSplitPoolCap][128] splitters
+  uint64_t* split_pool;            // [split_pool_slots][128] splitters
+  int32_t split_pool_slots;
   RunStatus* run;
   struct iplsTraceRecDev* trace;   // block-resident passes append here
   int64_t trace_cap;
@@ -280,6 +290,9 @@ cudaError_t launch_scatter(const LevelArgs& a, cudaStream_t s, int sms);
 cudaError_t launch_tail_fit(const ResidentArgs& a, cudaStream_t s);
 cudaError_t launch_resident(const ResidentArgs& a, cudaStream_t s);
 cudaError_t launch_slow(const ResidentArgs& a, cudaStream_t s, int sms);
+// groups[i] = the fitted tail task of list[i], fit_list[i] = i (i < n).
+cudaError_t launch_slow_groups(const SlowTask* list, int32_t n, Group* groups, int32_t* fit_list,
+                               cudaStream_t s);
 // One block sorts keys[t.off, t.off + t.n) (t.n <= resident_rmax(a.cutoff));
 // it reads and writes only the keys and *a.run.
 cudaError_t launch_slow_one(const ResidentArgs& a, const SlowTask& t, cudaStream_t s);

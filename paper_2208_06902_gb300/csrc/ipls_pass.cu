@@ -395,6 +395,8 @@ __global__ void __launch_bounds__(256) k_scan(LevelArgs a) {
     r.counts[b] = c;
   }
   __syncthreads();
+  // every splitter-tree pass counts, a homogeneous one too
+  if (b == 0 && splitter) atomicAdd((unsigned long long*)&a.ctl->fallback, 1ULL);
   if (s_skip) {
     // homogeneous subproblem: every key equals one splitter; nothing moves
     if (b == 0) {
@@ -454,7 +456,6 @@ __global__ void __launch_bounds__(256) k_scan(LevelArgs a) {
         blast = q;
       }
     }
-    if (splitter) atomicAdd((unsigned long long*)&a.ctl->fallback, 1ULL);
     atomicAdd((unsigned long long*)&a.ctl->keys_moved, (unsigned long long)sub.n);
     int64_t mx = 0;
     for (int q = 0; q < nb; ++q) mx = cnt[q] > mx ? cnt[q] : mx;

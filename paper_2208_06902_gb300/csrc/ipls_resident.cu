@@ -14,11 +14,14 @@
 //                smaller keys, ties broken by position), and the subproblem
 //                is written to the user buffer once.  A task of small children
 //                (consecutive buckets or segments of at most `cutoff` keys)
-//                goes straight to the base case.  Buckets above the cutoff,
-//                tasks whose model is the splitter tree and passes without
-//                progress are written out in place and queued on the slow
-//                list.
-//   k_slow       persistent blocks drain the slow list: each range recurses
+//                goes straight to the base case.  Buckets above the cutoff
+//                are written out in place and queued on the child list;
+//                tasks without progress, or whose splitter tree found no
+//                pool slot, on the whole-task list.
+//   (2nd sweep)  when many children were queued, k_tail_fit and k_tail run
+//                once more over them, in place in the user buffer; what
+//                they queue in turn is left to k_slow.
+//   k_slow       persistent blocks drain both lists: each range recurses
 //                inside one block (sample, sort, fit, classify, stable
 //                scatter, base case) and is written back in place.
 //
@@ -95,7 +98,7 @@ __global__ void __launch_bounds__(kFitWarps * 32) k_tail_fit(ResidentArgs a) {
     int slot = -1;
     if (cnt > kTailSplit && lane == 0) {
       slot = atomicAdd(&a.slow_ctl->pool_used, 1);
-      if (slot >= kSplitPoolCap) slot = -1;
+      if (slot >= a.split_pool_slots) slot = -1;
     }
     slot = __shfl_sync(0xffffffffu, slot, 0);
     uint64_t* out = cnt <= kTailSplit ? m.split : (slot >= 0 ? a.split_pool + (size_t)slot * 128 : nullptr);
@@ -418,9 +421,12 @@ __global__ void __launch_bounds__(kResidentThreads, 2) k_slow(ResidentArgs a) {
     __syncthreads();
     if (threadIdx.x == 0) s_i = (int)atomicAdd(&a.slow_ctl->ticket, 1u);
     __syncthreads();
+    // the whole tasks first, then the children
     const int i = s_i;
-    if (i >= a.slow_ctl->count || i >= a.slow_cap) break;
-    const SlowTask st = a.slow[i];
+    const int nw = min(a.slow_ctl->wcount, a.whole_cap);
+    const int nc = min(a.slow_ctl->count, a.slow_cap);
+    if (i >= nw + nc) break;
+    const SlowTask st = i < nw ? a.whole[i] : a.slow[i - nw];
     if (threadIdx.x == 0) atomicAdd((unsigned long long*)&a.run->slow_tasks, 1ULL);
     Bits* src = keys + st.off;
     for (int p = threadIdx.x; p < st.n; p += blockDim.x) sh.keys[p] = T::ord(src[p]);
@@ -455,9 +461,17 @@ struct TailSmem {
   long long rec;
 };
 
+// A child above the cutoff (it may take another tail round).
 __device__ __forceinline__ void push_slow(const ResidentArgs& a, int64_t off, int n, int level) {
   const int i = atomicAdd(&a.slow_ctl->count, 1);
   if (i < a.slow_cap) a.slow[i] = SlowTask{off, n, level};
+  else atomicExch(&a.run->error, -6);
+}
+
+// A whole task that recurses inside one block (k_slow).
+__device__ __forceinline__ void push_whole(const ResidentArgs& a, int64_t off, int n, int level) {
+  const int i = atomicAdd(&a.slow_ctl->wcount, 1);
+  if (i < a.whole_cap) a.whole[i] = SlowTask{off, n, level};
   else atomicExch(&a.run->error, -6);
 }
 
@@ -620,6 +634,10 @@ __global__ void __launch_bounds__(kResidentThreads, 2) k_tail(ResidentArgs a) {
             }
           }
         }
+        if (threadIdx.x == 0) {
+          atomicAdd((unsigned long long*)&a.run->resident_passes, 1ULL);
+          if (split_tree) atomicAdd((unsigned long long*)&a.run->resident_fallback, 1ULL);
+        }
         // trace record of this pass (the model was fitted by k_tail_fit)
         if (a.trace_cap > 0) {
           if (threadIdx.x == 0) {
@@ -636,7 +654,7 @@ __global__ void __launch_bounds__(kResidentThreads, 2) k_tail(ResidentArgs a) {
           if (sh.rec < a.trace_cap && threadIdx.x < kMaxK)
             a.trace[sh.rec].counts[threadIdx.x] = (threadIdx.x < sh.tm.l.nb) ? sh.tot[threadIdx.x] : 0;
         }
-        // buckets above the cutoff continue in the slow kernel; an equality
+        // buckets above the cutoff are queued as children; an equality
         // bucket is done, and so is a bucket of equal keys after its record
         __syncthreads();
         mark_homogeneous(sh.keys, sh.bstart, sh.tot, sh.tm.l.nb, a.cutoff, sh.hom);
@@ -653,7 +671,7 @@ __global__ void __launch_bounds__(kResidentThreads, 2) k_tail(ResidentArgs a) {
       // same sample and makes the same model), from the user buffer
       if (g.buf != 0)
         for (int p = threadIdx.x; p < n; p += blockDim.x) dst[p] = src[p];
-      if (threadIdx.x == 0) push_slow(a, g.off, n, g.level);
+      if (threadIdx.x == 0) push_whole(a, g.off, n, g.level);
       if (threadIdx.x == 0) atomicAdd((unsigned long long*)&a.run->resident_groups, 1ULL);
       return;
     }
@@ -745,6 +763,21 @@ cudaError_t launch_slow(const ResidentArgs& a, cudaStream_t s, int sms) {
     k_slow<K><<<per * sms, kResidentThreads, smem, s>>>(a);
     return cudaGetLastError();
   });
+}
+
+__global__ void k_slow_groups(const SlowTask* list, int32_t n, Group* groups, int32_t* fit_list) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const SlowTask t = list[i];
+  groups[i] = Group{t.off, nullptr, t.n, t.level, 0, 1, i, 0};
+  fit_list[i] = i;
+}
+
+cudaError_t launch_slow_groups(const SlowTask* list, int32_t n, Group* groups, int32_t* fit_list,
+                               cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_slow_groups<<<(n + 255) / 256, 256, 0, s>>>(list, n, groups, fit_list);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_fill(const Fill* fills, int32_t nfill, int dtype, void* keys, cudaStream_t s) {

@@ -51,7 +51,8 @@ class iplsStats(ctypes.Structure):
                 ("resident_groups", ctypes.c_int64), ("fallback_passes", ctypes.c_int64),
                 ("algorithmic_bytes", ctypes.c_int64), ("scratch_bytes", ctypes.c_int64),
                 ("trace_records", ctypes.c_int64), ("max_bucket_frac", ctypes.c_double),
-                ("slow_tasks", ctypes.c_int64), ("slow_passes", ctypes.c_int64)]
+                ("slow_tasks", ctypes.c_int64), ("slow_passes", ctypes.c_int64),
+                ("sweep_tasks", ctypes.c_int64)]
 
 
 _lib = None

@@ -49,6 +49,8 @@ def test_distributions_bit_exact_with_trace(dtype, dist):
     got, ctx = gpu_sort(x, trace_cap=100_000)
     assert _same(got, want), dist
     compare_traces(ctx.trace(), recs)
+    # every splitter-tree pass is counted once, wherever it ran
+    assert ctx.stats().fallback_passes == sum(1 for r in recs if r.model.kind == 1)
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
@@ -150,6 +152,23 @@ def test_other_parameters(cutoff, k):
     got, ctx = gpu_sort(x, k=k, cutoff=cutoff, trace_cap=200_000)
     assert _same(got, want)
     compare_traces(ctx.trace(), recs)
+
+
+@pytest.mark.parametrize("dist,dtype", [("uniform", np.float64), ("twodups", np.uint32),
+                                        ("zipf", np.float32)])
+def test_second_tail_sweep_matches_the_oracle(dist, dtype):
+    # k = 64 and cutoff 16 on 2^22 keys: 4096 block-resident tasks of about
+    # 1024 keys, whose buckets of about 16 keys are often above the cutoff
+    # (some 50k children) -- those children take the second sweep, and what
+    # they leave above the cutoff takes k_slow
+    x = datagen.generate(dist, 1 << 22, dtype, seed=8)
+    want, recs, _ = oracle.sort(x, k=64, cutoff=16, trace_cap=200_000)
+    got, ctx = gpu_sort(x, k=64, cutoff=16, trace_cap=200_000)
+    assert _same(got, want)
+    compare_traces(ctx.trace(), recs)
+    st = ctx.stats()
+    assert st.sweep_tasks >= 1024
+    assert st.fallback_passes == sum(1 for r in recs if r.model.kind == 1)
 
 
 def test_segmented_equals_each_segment_alone():
