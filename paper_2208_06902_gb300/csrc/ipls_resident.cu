@@ -457,9 +457,13 @@ struct TailSmem {
   int hom[kMaxK];
   TailModel tm;
   uint64_t split[128];   // a tree too large for the record, from the pool
+  typename KT<K>::Ord seglo[kMaxK];  // smallest key of each base-cased segment
+  unsigned char segpk[kMaxK];        // 1: the segment is ranked on packed words
   int slow_all;
   long long rec;
 };
+// two blocks per SM (each with its 1 KB of reserved shared memory)
+static_assert(2 * (sizeof(TailSmem<double>) + 1024) <= 233472, "k_tail must keep two blocks per SM");
 
 // A child above the cutoff (it may take another tail round).
 __device__ __forceinline__ void push_slow(const ResidentArgs& a, int64_t off, int n, int level) {
@@ -687,13 +691,50 @@ __global__ void __launch_bounds__(kResidentThreads, 2) k_tail(ResidentArgs a) {
   }
   __syncthreads();
   // ---- base case: rank counting inside every segment of <= cutoff keys ----
+  // The position of a key in its segment is the number of keys before it in
+  // (key, position) order.  When the segment's keys span fewer than
+  // 2^(bits - kPosBits) values, each becomes one word (key - min) << kPosBits
+  // | position, and one unsigned compare per pair decides that order.
+  constexpr int kPosBits = 13;
+  static_assert(kResidentMax <= (1 << kPosBits), "positions must fit the packed word");
+  constexpr Ord kSpan = (Ord)1 << (sizeof(Ord) * 8 - kPosBits);
   const int cutoff = a.cutoff;
+  for (int q = threadIdx.x; q < nseg; q += blockDim.x) {
+    const int s = sh.segb[q], e = sh.segb[q + 1];
+    Ord mn = 0;
+    bool pk = false;
+    if (e - s >= 2 && e - s <= cutoff && !(split_tree && (q & 1))) {
+      mn = sh.keys[s];
+      Ord mx = mn;
+      for (int r = s + 1; r < e; ++r) {
+        const Ord k = sh.keys[r];
+        mn = k < mn ? k : mn;
+        mx = k > mx ? k : mx;
+      }
+      pk = (Ord)(mx - mn) < kSpan;
+    }
+    sh.seglo[q] = mn;
+    sh.segpk[q] = pk ? 1 : 0;
+  }
+  __syncthreads();
+  for (int p = threadIdx.x; p < n; p += blockDim.x) {
+    const int q = sh.seg[p];
+    if (sh.segpk[q]) sh.keys[p] = (Ord)((Ord)(sh.keys[p] - sh.seglo[q]) << kPosBits) | (Ord)p;
+  }
+  __syncthreads();
   for (int p = threadIdx.x; p < n; p += blockDim.x) {
     const int q = sh.seg[p];
     const int s = sh.segb[q], e = sh.segb[q + 1];
     const Ord kp = sh.keys[p];
     int d = p;
-    if (e - s <= cutoff && !(split_tree && (q & 1))) {
+    Ord out = kp;
+    if (sh.segpk[q]) {
+      int cnt = 0;
+#pragma unroll 4
+      for (int r = s; r < e; ++r) cnt += sh.keys[r] < kp ? 1 : 0;
+      d = s + cnt;
+      out = (Ord)(sh.seglo[q] + (kp >> kPosBits));
+    } else if (e - s <= cutoff && !(split_tree && (q & 1))) {
       int cnt = 0;
       for (int r = s; r < e; ++r) {
         const Ord kr = sh.keys[r];
@@ -701,7 +742,7 @@ __global__ void __launch_bounds__(kResidentThreads, 2) k_tail(ResidentArgs a) {
       }
       d = s + cnt;
     }
-    dst[d] = T::unord(kp);
+    dst[d] = T::unord(out);
   }
   if (threadIdx.x == 0) {
     atomicAdd((unsigned long long*)&a.run->resident_keys, (unsigned long long)n);
