@@ -249,25 +249,31 @@ __device__ __forceinline__ void block_sort(T* a, int n) { group_sort<BlockG, T>(
 template <int kSteps, class Ord>
 __device__ void warp_radix_sort(Ord* a, Ord* tmp, unsigned* cnt, unsigned* peer, int n) {
   const int lane = threadIdx.x & 31;
-  Ord lo = ~(Ord)0, hi = 0;
+  Ord lo = ~(Ord)0;
   for (int i = lane; i < n; i += 32) {
     const Ord v = a[i];
     lo = v < lo ? v : lo;
-    hi = v > hi ? v : hi;
   }
 #pragma unroll
   for (int o = 16; o >= 1; o >>= 1) {
-    const Ord l2 = __shfl_xor_sync(0xffffffffu, lo, o), h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+    const Ord l2 = __shfl_xor_sync(0xffffffffu, lo, o);
     lo = l2 < lo ? l2 : lo;
-    hi = h2 > hi ? h2 : hi;
   }
-  const Ord range = hi - lo;
-  const int bits = range == 0 ? 0 : (int)(sizeof(Ord) * 8) - (sizeof(Ord) == 8 ? __clzll((long long)range) : __clz((int)range));
+  // bits set in some key minus lo (the smallest key has none): a digit that
+  // is zero for every key leaves the order as it is, so its pass is skipped
+  // (keys with trailing zero bits, such as integer-valued doubles, skip the
+  // low digits)
+  Ord vary = 0;
+  for (int i = lane; i < n; i += 32) vary |= a[i] - lo;
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) vary |= __shfl_xor_sync(0xffffffffu, vary, o);
+  const int bits = vary == 0 ? 0 : (int)(sizeof(Ord) * 8) - (sizeof(Ord) == 8 ? __clzll((long long)vary) : __clz((int)vary));
   const int passes = (bits + 7) / 8;
   Ord* src = a;
   Ord* dst = tmp;
   for (int p = 0; p < passes; ++p) {
     const int shift = 8 * p;
+    if (((vary >> shift) & 255) == 0) continue;
     for (int i = lane; i < 256; i += 32) cnt[i] = 0;
     __syncwarp();
     unsigned rk[kSteps];  // digit << 16 | rank among the equal digits before it
@@ -558,14 +564,14 @@ __device__ void fit_model(const typename KT<K>::Ord* so, int N, int K_, Model* m
 
 // Splitter tree with equality buckets: p = #{s_i <= u}; bucket 2p-1 if
 // s_p == u, else bucket 2p.
+// p is found by steps of decreasing powers of two (split[0..p) <= u holds
+// after every step), the same number of probes on every lane.
 __device__ __forceinline__ int splitter_bucket(uint64_t u, const uint64_t* split, int nsplit) {
-  int lo = 0, hi = nsplit;
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    if (split[mid] <= u) lo = mid + 1; else hi = mid;
-  }
-  if (lo > 0 && split[lo - 1] == u) return 2 * lo - 1;
-  return 2 * lo;
+  int p = 0;
+  for (int step = nsplit > 0 ? 1 << (31 - __clz(nsplit)) : 0; step > 0; step >>= 1)
+    if (p + step <= nsplit && split[p + step - 1] <= u) p += step;
+  if (p > 0 && split[p - 1] == u) return 2 * p - 1;
+  return 2 * p;
 }
 
 // The model equation in binary64 (reading: one fma, floor, clamp, cast).
