@@ -243,7 +243,7 @@ iplsStatus tail_sweep(iplsCtx c, ResidentArgs& ra) {
     IPLS_TRY(ensure(c, c->split_pool, c->split_pool_cap, pool_slots(ra.nfit) * 128));
     ra.split_pool = c->split_pool;
     ra.split_pool_slots = (int32_t)std::min<int64_t>(c->split_pool_cap / 128, kSplitPoolMax);
-    IPLS_CUDA(timed(c, kkTailFit, [&] { return launch_tail_fit(ra, c->stream); }));
+    IPLS_CUDA(timed(c, kkTailFit, [&] { return launch_tail_fit(ra, c->stream, c->num_sms); }));
   }
   IPLS_CUDA(timed(c, kkResident, [&] { return launch_resident(ra, c->stream); }));
   return IPLS_OK;
@@ -279,8 +279,9 @@ iplsStatus launch_tail(iplsCtx c, ResidentArgs& ra, Slot& s, int32_t ngroups, in
     if (nc >= kTailSweepMin && nc <= ra.slow_cap) {
       IPLS_TRY(ensure_groups(c, s, nc));
       IPLS_CUDA(timed(c, kkSlowGroups, [&] { return launch_slow_groups(c->slow, nc, s.groups, s.fit_list, c->stream); }));
-      // the child list starts again (count, ticket, pool_used); whole tasks stay
-      IPLS_CUDA(cudaMemsetAsync(c->slow_ctl, 0, 3 * sizeof(int32_t), c->stream));
+      // the child list starts again (count, ticket, pool_used, fit_ticket);
+      // whole tasks stay
+      IPLS_CUDA(cudaMemsetAsync(c->slow_ctl, 0, 4 * sizeof(int32_t), c->stream));
       ra.groups = s.groups;
       ra.ngroups = nc;
       ra.fit_list = s.fit_list;

@@ -181,7 +181,9 @@ struct SlowCtl {
   int32_t count;
   uint32_t ticket;
   int32_t pool_used;   // splitter-pool slots taken by this tail sweep
+  int32_t fit_ticket;  // next task of k_tail_fit's persistent warps
   int32_t wcount;
+  int32_t pad;
 };
 
 // Splitters of a tail task whose tree has more than kTailSplit of them (one
@@ -287,7 +289,7 @@ cudaError_t launch_check(const LevelArgs& a, cudaStream_t s, int max_sample);
 cudaError_t launch_scan(const LevelArgs& a, cudaStream_t s);
 cudaError_t launch_tilescan(const LevelArgs& a, cudaStream_t s, int grid);
 cudaError_t launch_scatter(const LevelArgs& a, cudaStream_t s, int sms);
-cudaError_t launch_tail_fit(const ResidentArgs& a, cudaStream_t s);
+cudaError_t launch_tail_fit(const ResidentArgs& a, cudaStream_t s, int sms);
 cudaError_t launch_resident(const ResidentArgs& a, cudaStream_t s);
 cudaError_t launch_slow(const ResidentArgs& a, cudaStream_t s, int sms);
 // groups[i] = the fitted tail task of list[i], fit_list[i] = i (i < n).

@@ -60,74 +60,80 @@ __global__ void __launch_bounds__(kFitWarps * 32) k_tail_fit(ResidentArgs a) {
   __shared__ unsigned rcnt[kFitWarps][256], rpeer[kFitWarps][256];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int i = lane; i < 256; i += 32) rpeer[warp][i] = 0u;
-  const int task = blockIdx.x * kFitWarps + warp;
-  if (task >= a.nfit) return;
   unsigned char* slot = smem_raw + (size_t)warp * fit_slot_bytes<Ord>();
   Ord* so = reinterpret_cast<Ord*>(slot);
   Ord* rtmp = reinterpret_cast<Ord*>(slot + (size_t)kRadixMax * sizeof(Ord));
   long long* qimg = reinterpret_cast<long long*>(slot + (size_t)kRadixMax * sizeof(Ord));
-  const Group g = a.groups[a.fit_list[task]];
-  int S = (int)sample_size(g.n, g.level, a.k, a.root_sample);
-  if (S > kResidentSample) S = kResidentSample;  // never planned by the host
-  const uint64_t stream = stream_key(a.seed, g.off, g.n, g.level);
-  const typename T::Bits* src = reinterpret_cast<const typename T::Bits*>(a.buf[g.buf]) + g.off;
-  for (int j = lane; j < S; j += 32) so[j] = T::ord(src[sample_offset(stream, j, g.n)]);
-  __syncwarp();
-  if (S <= kRadixMax) warp_radix_sort<kRadixSteps>(so, rtmp, rcnt[warp], rpeer[warp], S);
-  else group_sort<WarpG, Ord>(so, S);
-  TailModel& m = tm[warp];
-  // after the radix sort its second buffer holds the fixed-point images
-  fit_linear<WarpG, K>(so, S, a.k, &m.l, fs[warp], S <= kRadixMax ? qimg : nullptr);
-  if (lane == 0) {
-    m.nsplit = 0;
-    m.pool = -1;
-  }
-  __syncwarp();
-  if (m.l.kind == kSplitter) {
-    // splitter tree from the same sorted sample: (k-1)/2 equidistant sample
-    // keys, duplicates dropped (Ch.3 "Decision Trees"; equality buckets).
-    // First count them, then store them inline or in a pool slot.
-    const int want = (a.k - 1) / 2;
-    int cnt = 0;
-    for (int base = 0; base < want; base += 32) {
-      const int i = base + lane;
-      const bool keep = i < want && (i == 0 || so[(int64_t)(i + 1) * S / (want + 1)] !=
-                                                   so[(int64_t)i * S / (want + 1)]);
-      cnt += __popc(__ballot_sync(0xffffffffu, keep));
-    }
-    int slot = -1;
-    if (cnt > kTailSplit && lane == 0) {
-      slot = atomicAdd(&a.slow_ctl->pool_used, 1);
-      if (slot >= a.split_pool_slots) slot = -1;
-    }
-    slot = __shfl_sync(0xffffffffu, slot, 0);
-    uint64_t* out = cnt <= kTailSplit ? m.split : (slot >= 0 ? a.split_pool + (size_t)slot * 128 : nullptr);
-    if (out) {
-      int pos0 = 0;
-      for (int base = 0; base < want; base += 32) {
-        const int i = base + lane;
-        bool keep = false;
-        uint64_t u = 0;
-        if (i < want) {
-          u = (uint64_t)so[(int64_t)(i + 1) * S / (want + 1)];
-          keep = (i == 0) || (u != (uint64_t)so[(int64_t)i * S / (want + 1)]);
-        }
-        const unsigned bal = __ballot_sync(0xffffffffu, keep);
-        if (keep) out[pos0 + __popc(bal & lanemask_lt())] = u;
-        pos0 += __popc(bal);
-      }
-    }
+  // persistent warps: each takes the next task until none is left
+  for (;;) {
+    int task = 0;
+    if (lane == 0) task = atomicAdd(&a.slow_ctl->fit_ticket, 1);
+    task = __shfl_sync(0xffffffffu, task, 0);
+    if (task >= a.nfit) break;
+    const Group g = a.groups[a.fit_list[task]];
+    int S = (int)sample_size(g.n, g.level, a.k, a.root_sample);
+    if (S > kResidentSample) S = kResidentSample;  // never planned by the host
+    const uint64_t stream = stream_key(a.seed, g.off, g.n, g.level);
+    const typename T::Bits* src = reinterpret_cast<const typename T::Bits*>(a.buf[g.buf]) + g.off;
+    for (int j = lane; j < S; j += 32) so[j] = T::ord(src[sample_offset(stream, j, g.n)]);
+    __syncwarp();
+    if (S <= kRadixMax) warp_radix_sort<kRadixSteps>(so, rtmp, rcnt[warp], rpeer[warp], S);
+    else group_sort<WarpG, Ord>(so, S);
+    TailModel& m = tm[warp];
+    // after the radix sort its second buffer holds the fixed-point images
+    fit_linear<WarpG, K>(so, S, a.k, &m.l, fs[warp], S <= kRadixMax ? qimg : nullptr);
     if (lane == 0) {
-      m.nsplit = cnt;
-      m.pool = slot;
-      m.l.nb = 2 * cnt + 1;
-      m.l.fast = 0;
+      m.nsplit = 0;
+      m.pool = -1;
     }
     __syncwarp();
+    if (m.l.kind == kSplitter) {
+      // splitter tree from the same sorted sample: (k-1)/2 equidistant sample
+      // keys, duplicates dropped (Ch.3 "Decision Trees"; equality buckets).
+      // First count them, then store them inline or in a pool slot.
+      const int want = (a.k - 1) / 2;
+      int cnt = 0;
+      for (int base = 0; base < want; base += 32) {
+        const int i = base + lane;
+        const bool keep = i < want && (i == 0 || so[(int64_t)(i + 1) * S / (want + 1)] !=
+                                                     so[(int64_t)i * S / (want + 1)]);
+        cnt += __popc(__ballot_sync(0xffffffffu, keep));
+      }
+      int slot = -1;
+      if (cnt > kTailSplit && lane == 0) {
+        slot = atomicAdd(&a.slow_ctl->pool_used, 1);
+        if (slot >= a.split_pool_slots) slot = -1;
+      }
+      slot = __shfl_sync(0xffffffffu, slot, 0);
+      uint64_t* out = cnt <= kTailSplit ? m.split : (slot >= 0 ? a.split_pool + (size_t)slot * 128 : nullptr);
+      if (out) {
+        int pos0 = 0;
+        for (int base = 0; base < want; base += 32) {
+          const int i = base + lane;
+          bool keep = false;
+          uint64_t u = 0;
+          if (i < want) {
+            u = (uint64_t)so[(int64_t)(i + 1) * S / (want + 1)];
+            keep = (i == 0) || (u != (uint64_t)so[(int64_t)i * S / (want + 1)]);
+          }
+          const unsigned bal = __ballot_sync(0xffffffffu, keep);
+          if (keep) out[pos0 + __popc(bal & lanemask_lt())] = u;
+          pos0 += __popc(bal);
+        }
+      }
+      if (lane == 0) {
+        m.nsplit = cnt;
+        m.pool = slot;
+        m.l.nb = 2 * cnt + 1;
+        m.l.fast = 0;
+      }
+      __syncwarp();
+    }
+    const unsigned long long* s = reinterpret_cast<const unsigned long long*>(&m);
+    unsigned long long* d = reinterpret_cast<unsigned long long*>(&a.tail_models[g.fit]);
+    if (lane < (int)(sizeof(TailModel) / 8)) d[lane] = s[lane];
+    __syncwarp();
   }
-  const unsigned long long* s = reinterpret_cast<const unsigned long long*>(&m);
-  unsigned long long* d = reinterpret_cast<unsigned long long*>(&a.tail_models[g.fit]);
-  if (lane < (int)(sizeof(TailModel) / 8)) d[lane] = s[lane];
 }
 
 // ---------------------------------------------------------------------------
@@ -768,13 +774,19 @@ static cudaError_t by_dtype_r(int dtype, F f) {
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_tail_fit(const ResidentArgs& a, cudaStream_t s) {
+cudaError_t launch_tail_fit(const ResidentArgs& a, cudaStream_t s, int sms) {
   if (a.nfit <= 0) return cudaSuccess;
   return by_dtype_r(a.dtype, [&](auto* tag) {
     using K = std::remove_pointer_t<decltype(tag)>;
     const size_t smem = (size_t)kFitWarps * fit_slot_bytes<typename KT<K>::Ord>();
     cudaFuncSetAttribute(k_tail_fit<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const int blocks = (a.nfit + kFitWarps - 1) / kFitWarps;
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_tail_fit<K>, kFitWarps * 32, smem) != cudaSuccess || per < 1) {
+      cudaGetLastError();
+      per = 1;
+    }
+    const int64_t need = (a.nfit + kFitWarps - 1) / kFitWarps;
+    const int blocks = (int)std::min<int64_t>(need, (int64_t)per * sms);
     k_tail_fit<K><<<blocks, kFitWarps * 32, smem, s>>>(a);
     return cudaGetLastError();
   });
