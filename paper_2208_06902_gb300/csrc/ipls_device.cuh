@@ -564,14 +564,14 @@ __device__ void fit_model(const typename KT<K>::Ord* so, int N, int K_, Model* m
 
 // Splitter tree with equality buckets: p = #{s_i <= u}; bucket 2p-1 if
 // s_p == u, else bucket 2p.
-// p is found by steps of decreasing powers of two (split[0..p) <= u holds
-// after every step), the same number of probes on every lane.
 __device__ __forceinline__ int splitter_bucket(uint64_t u, const uint64_t* split, int nsplit) {
-  int p = 0;
-  for (int step = nsplit > 0 ? 1 << (31 - __clz(nsplit)) : 0; step > 0; step >>= 1)
-    if (p + step <= nsplit && split[p + step - 1] <= u) p += step;
-  if (p > 0 && split[p - 1] == u) return 2 * p - 1;
-  return 2 * p;
+  int lo = 0, hi = nsplit;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (split[mid] <= u) lo = mid + 1; else hi = mid;
+  }
+  if (lo > 0 && split[lo - 1] == u) return 2 * lo - 1;
+  return 2 * lo;
 }
 
 // The model equation in binary64 (reading: one fma, floor, clamp, cast).
