@@ -466,6 +466,7 @@ struct TailSmem {
   typename KT<K>::Ord seglo[kMaxK];  // smallest key of each base-cased segment
   unsigned char segpk[kMaxK];        // 1: the segment is ranked on packed words
   int slow_all;
+  int any_big;   // some bucket above the cutoff would be queued
   long long rec;
 };
 // two blocks per SM (each with its 1 KB of reserved shared memory)
@@ -507,7 +508,10 @@ __global__ void __launch_bounds__(kResidentThreads, 2) k_tail(ResidentArgs a) {
       (&sh.wcnt[0][0])[i] = 0;
       (&sh.peer[0][0])[i] = 0u;
     }
-    if (threadIdx.x == 0) sh.slow_all = 0;
+    if (threadIdx.x == 0) {
+      sh.slow_all = 0;
+      sh.any_big = 0;
+    }
     __syncthreads();
     split_tree = sh.tm.l.kind == kSplitter;
     const int nsplit = sh.tm.nsplit;
@@ -607,6 +611,7 @@ __global__ void __launch_bounds__(kResidentThreads, 2) k_tail(ResidentArgs a) {
         // no progress of the linear model: the splitter tree decides (the
         // splitter tree itself always progresses or leaves one equality run)
         if (run == n && !split_tree) sh.slow_all = 1;
+        if (run > a.cutoff && b < sh.tm.l.nb && !(split_tree && (b & 1))) sh.any_big = 1;
       }
       __syncthreads();
       slow = sh.slow_all != 0;
@@ -666,14 +671,17 @@ __global__ void __launch_bounds__(kResidentThreads, 2) k_tail(ResidentArgs a) {
         }
         // buckets above the cutoff are queued as children; an equality
         // bucket is done, and so is a bucket of equal keys after its record
-        __syncthreads();
-        mark_homogeneous(sh.keys, sh.bstart, sh.tot, sh.tm.l.nb, a.cutoff, sh.hom);
-        if (threadIdx.x < sh.tm.l.nb && sh.tot[threadIdx.x] > a.cutoff && !(split_tree && (threadIdx.x & 1))) {
-          const int b = threadIdx.x;
-          if (sh.hom[b]) record_homogeneous(a, g.off + sh.bstart[b], sh.tot[b], g.level + 1);
-          else push_slow(a, g.off + sh.bstart[b], sh.tot[b], g.level + 1);
+        // (most tasks have no bucket above the cutoff and skip this)
+        if (sh.any_big) {
+          __syncthreads();
+          mark_homogeneous(sh.keys, sh.bstart, sh.tot, sh.tm.l.nb, a.cutoff, sh.hom);
+          if (threadIdx.x < sh.tm.l.nb && sh.tot[threadIdx.x] > a.cutoff && !(split_tree && (threadIdx.x & 1))) {
+            const int b = threadIdx.x;
+            if (sh.hom[b]) record_homogeneous(a, g.off + sh.bstart[b], sh.tot[b], g.level + 1);
+            else push_slow(a, g.off + sh.bstart[b], sh.tot[b], g.level + 1);
+          }
+          __syncthreads();
         }
-        __syncthreads();
       }
     }
     if (slow) {
