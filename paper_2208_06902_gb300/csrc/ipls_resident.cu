@@ -187,21 +187,23 @@ __device__ void trace_pass(ResSmem<K>& sh, const ResidentArgs& a, int64_t off, i
 }
 
 // For every bucket b with more than `cutoff` keys (stored contiguously from
-// keys[start[b]]), hom[b] = 1 when all of them are the same key.  Such a
+// keys[start[b]]), hom[b] = 1 when all of them are the same key (compared
+// after a right shift by `shift`, which drops the position bits of packed
+// words).  Such a
 // bucket is done: its own pass would draw a homogeneous sample, take the
 // splitter tree with that one key as its only splitter and put every key
 // into the equality bucket, moving nothing (the rule for duplicates).
 template <class Ord>
 __device__ void mark_homogeneous(const Ord* keys, const int* start, const int* tot, int nb,
-                                 int cutoff, int* hom) {
+                                 int cutoff, int* hom, int shift = 0) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int b = threadIdx.x; b < nb; b += blockDim.x) hom[b] = tot[b] > cutoff ? 1 : 0;
   __syncthreads();
   for (int b = warp; b < nb; b += blockDim.x >> 5) {
     if (!hom[b]) continue;
-    const Ord first = keys[start[b]];
+    const Ord first = keys[start[b]] >> shift;
     bool diff = false;
-    for (int i = start[b] + lane; i < start[b] + tot[b]; i += 32) diff |= keys[i] != first;
+    for (int i = start[b] + lane; i < start[b] + tot[b]; i += 32) diff |= (keys[i] >> shift) != first;
     if (__any_sync(0xffffffffu, diff) && lane == 0) hom[b] = 0;
   }
   __syncthreads();
@@ -465,6 +467,9 @@ struct TailSmem {
   uint64_t split[128];   // a tree too large for the record, from the pool
   typename KT<K>::Ord seglo[kMaxK];  // smallest key of each base-cased segment
   unsigned char segpk[kMaxK];        // 1: the segment is ranked on packed words
+  typename KT<K>::Ord wlo[kRW], whi[kRW];  // per-warp key range of a fitted task
+  typename KT<K>::Ord tlo;           // smallest key of a fitted task
+  int tpk;                           // 1: the fitted task's keys are placed packed
   int slow_all;
   int any_big;   // some bucket above the cutoff would be queued
   long long rec;
@@ -486,11 +491,18 @@ __device__ __forceinline__ void push_whole(const ResidentArgs& a, int64_t off, i
   else atomicExch(&a.run->error, -6);
 }
 
+// Base case on packed words: a key whose group of keys spans fewer than
+// 2^(bits - kPosBits) values is held as (key - min) << kPosBits | position,
+// and one unsigned compare of two words gives their (key, position) order.
+constexpr int kPosBits = 13;
+static_assert(kResidentMax <= (1 << kPosBits), "positions must fit the packed word");
+
 template <class K>
 __global__ void __launch_bounds__(kResidentThreads, 2) k_tail(ResidentArgs a) {
   using T = KT<K>;
   using Bits = typename T::Bits;
   using Ord = typename T::Ord;
+  constexpr Ord kSpan = (Ord)1 << (sizeof(Ord) * 8 - kPosBits);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TailSmem<K>& sh = *reinterpret_cast<TailSmem<K>*>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -537,20 +549,35 @@ __global__ void __launch_bounds__(kResidentThreads, 2) k_tail(ResidentArgs a) {
         const int i = warp * chunk + j * 32 + lane;
         v[j] = (j < steps && i < n) ? src[i] : Bits(0);
       }
-      // classify; keys that need the binary64 model are deferred
+      // classify; keys that need the binary64 model are deferred; the
+      // task's key range on the side
       unsigned dmask = 0;
+      Ord klo = ~(Ord)0, khi = 0;
 #pragma unroll
       for (int j = 0; j < kRKPT; ++j) {
         if (j < steps) {
           const int i = warp * chunk + j * 32 + lane;
           int bk = kMaxK;
           if (i < n) {
-            bk = split_tree ? splitter_bucket((uint64_t)T::ord(v[j]), splits, nsplit)
+            const Ord o = T::ord(v[j]);
+            klo = o < klo ? o : klo;
+            khi = o > khi ? o : khi;
+            bk = split_tree ? splitter_bucket((uint64_t)o, splits, nsplit)
                             : cls.bucket_or_defer(v[j]);
             if (bk < 0) dmask |= 1u << j;
           }
           br[j] = (unsigned)bk;
         }
+      }
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) {
+        const Ord l2 = __shfl_xor_sync(0xffffffffu, klo, o), h2 = __shfl_xor_sync(0xffffffffu, khi, o);
+        klo = l2 < klo ? l2 : klo;
+        khi = h2 > khi ? h2 : khi;
+      }
+      if (lane == 0) {
+        sh.wlo[warp] = klo;
+        sh.whi[warp] = khi;
       }
       if (__any_sync(0xffffffffu, dmask != 0)) {
         // queue them (in the key area, free until the tile is placed) and
@@ -612,6 +639,15 @@ __global__ void __launch_bounds__(kResidentThreads, 2) k_tail(ResidentArgs a) {
         // splitter tree itself always progresses or leaves one equality run)
         if (run == n && !split_tree) sh.slow_all = 1;
         if (run > a.cutoff && b < sh.tm.l.nb && !(split_tree && (b & 1))) sh.any_big = 1;
+      } else if (threadIdx.x == kMaxK) {
+        Ord lo = ~(Ord)0, hi = 0;
+#pragma unroll
+        for (int w = 0; w < kRW; ++w) {
+          lo = sh.wlo[w] < lo ? sh.wlo[w] : lo;
+          hi = sh.whi[w] > hi ? sh.whi[w] : hi;
+        }
+        sh.tlo = lo;
+        sh.tpk = (Ord)(hi - lo) < kSpan ? 1 : 0;
       }
       __syncthreads();
       slow = sh.slow_all != 0;
@@ -637,6 +673,8 @@ __global__ void __launch_bounds__(kResidentThreads, 2) k_tail(ResidentArgs a) {
           if (lane == 31) { sh.bstart[kMaxK] = run; sh.segb[kMaxK] = run; }
         }
         __syncthreads();
+        const bool tpk = sh.tpk != 0;
+        const Ord tlo = sh.tlo;
 #pragma unroll
         for (int j = 0; j < kRKPT; ++j) {
           if (j < steps) {
@@ -644,7 +682,8 @@ __global__ void __launch_bounds__(kResidentThreads, 2) k_tail(ResidentArgs a) {
             if (bk < kMaxK) {
               const int p = sh.bstart[bk] + sh.wcnt[warp][bk] + (int)(br[j] & 0xFFFF);
               // read again (from cache) rather than held in registers
-              sh.keys[p] = T::ord(src[warp * chunk + j * 32 + lane]);
+              const Ord o = T::ord(src[warp * chunk + j * 32 + lane]);
+              sh.keys[p] = tpk ? (Ord)((Ord)(o - tlo) << kPosBits) | (Ord)p : o;
               sh.seg[p] = (unsigned char)bk;
             }
           }
@@ -674,7 +713,8 @@ __global__ void __launch_bounds__(kResidentThreads, 2) k_tail(ResidentArgs a) {
         // (most tasks have no bucket above the cutoff and skip this)
         if (sh.any_big) {
           __syncthreads();
-          mark_homogeneous(sh.keys, sh.bstart, sh.tot, sh.tm.l.nb, a.cutoff, sh.hom);
+          mark_homogeneous(sh.keys, sh.bstart, sh.tot, sh.tm.l.nb, a.cutoff, sh.hom,
+                           sh.tpk ? kPosBits : 0);
           if (threadIdx.x < sh.tm.l.nb && sh.tot[threadIdx.x] > a.cutoff && !(split_tree && (threadIdx.x & 1))) {
             const int b = threadIdx.x;
             if (sh.hom[b]) record_homogeneous(a, g.off + sh.bstart[b], sh.tot[b], g.level + 1);
@@ -706,49 +746,52 @@ __global__ void __launch_bounds__(kResidentThreads, 2) k_tail(ResidentArgs a) {
   __syncthreads();
   // ---- base case: rank counting inside every segment of <= cutoff keys ----
   // The position of a key in its segment is the number of keys before it in
-  // (key, position) order.  When the segment's keys span fewer than
-  // 2^(bits - kPosBits) values, each becomes one word (key - min) << kPosBits
-  // | position, and one unsigned compare per pair decides that order.
-  constexpr int kPosBits = 13;
-  static_assert(kResidentMax <= (1 << kPosBits), "positions must fit the packed word");
-  constexpr Ord kSpan = (Ord)1 << (sizeof(Ord) * 8 - kPosBits);
+  // (key, position) order, counted on packed words where they fit: a fitted
+  // task was placed packed when its whole key range fits; a group of small
+  // children is packed here, segment by segment.
   const int cutoff = a.cutoff;
-  for (int q = threadIdx.x; q < nseg; q += blockDim.x) {
-    const int s = sh.segb[q], e = sh.segb[q + 1];
-    Ord mn = 0;
-    bool pk = false;
-    if (e - s >= 2 && e - s <= cutoff && !(split_tree && (q & 1))) {
-      mn = sh.keys[s];
-      Ord mx = mn;
-      for (int r = s + 1; r < e; ++r) {
-        const Ord k = sh.keys[r];
-        mn = k < mn ? k : mn;
-        mx = k > mx ? k : mx;
+  const bool task_pk = g.fit >= 0 && sh.tpk != 0;
+  if (g.fit < 0) {
+    for (int q = threadIdx.x; q < nseg; q += blockDim.x) {
+      const int s = sh.segb[q], e = sh.segb[q + 1];
+      Ord mn = 0;
+      bool pk = false;
+      if (e - s >= 2 && e - s <= cutoff) {
+        mn = sh.keys[s];
+        Ord mx = mn;
+        for (int r = s + 1; r < e; ++r) {
+          const Ord k = sh.keys[r];
+          mn = k < mn ? k : mn;
+          mx = k > mx ? k : mx;
+        }
+        pk = (Ord)(mx - mn) < kSpan;
       }
-      pk = (Ord)(mx - mn) < kSpan;
+      sh.seglo[q] = mn;
+      sh.segpk[q] = pk ? 1 : 0;
     }
-    sh.seglo[q] = mn;
-    sh.segpk[q] = pk ? 1 : 0;
+    __syncthreads();
+    for (int p = threadIdx.x; p < n; p += blockDim.x) {
+      const int q = sh.seg[p];
+      if (sh.segpk[q]) sh.keys[p] = (Ord)((Ord)(sh.keys[p] - sh.seglo[q]) << kPosBits) | (Ord)p;
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  for (int p = threadIdx.x; p < n; p += blockDim.x) {
-    const int q = sh.seg[p];
-    if (sh.segpk[q]) sh.keys[p] = (Ord)((Ord)(sh.keys[p] - sh.seglo[q]) << kPosBits) | (Ord)p;
-  }
-  __syncthreads();
   for (int p = threadIdx.x; p < n; p += blockDim.x) {
     const int q = sh.seg[p];
     const int s = sh.segb[q], e = sh.segb[q + 1];
     const Ord kp = sh.keys[p];
+    const bool based = e - s <= cutoff && !(split_tree && (q & 1));
     int d = p;
     Ord out = kp;
-    if (sh.segpk[q]) {
-      int cnt = 0;
+    if (task_pk || (g.fit < 0 && sh.segpk[q])) {
+      if (based) {
+        int cnt = 0;
 #pragma unroll 4
-      for (int r = s; r < e; ++r) cnt += sh.keys[r] < kp ? 1 : 0;
-      d = s + cnt;
-      out = (Ord)(sh.seglo[q] + (kp >> kPosBits));
-    } else if (e - s <= cutoff && !(split_tree && (q & 1))) {
+        for (int r = s; r < e; ++r) cnt += sh.keys[r] < kp ? 1 : 0;
+        d = s + cnt;
+      }
+      out = (Ord)((task_pk ? sh.tlo : sh.seglo[q]) + (kp >> kPosBits));
+    } else if (based) {
       int cnt = 0;
       for (int r = s; r < e; ++r) {
         const Ord kr = sh.keys[r];
