@@ -513,33 +513,37 @@ __global__ void __launch_bounds__(kResidentThreads, 2) k_tail(ResidentArgs a) {
   int nseg;
   bool split_tree = false;  // children at odd ids are equality buckets
   if (g.fit >= 0) {
+    // the model: a copy in shared memory for the phases after the first
+    // barrier; until then every thread reads it from global memory, and each
+    // warp zeroes its own rank counters, so no barrier is needed to start
+    const TailModel& gm = a.tail_models[g.fit];
     if (threadIdx.x < (int)(sizeof(TailModel) / 8))
       reinterpret_cast<unsigned long long*>(&sh.tm)[threadIdx.x] =
-          reinterpret_cast<const unsigned long long*>(&a.tail_models[g.fit])[threadIdx.x];
-    for (int i = threadIdx.x; i < kRW * kMaxK; i += blockDim.x) {
-      (&sh.wcnt[0][0])[i] = 0;
-      (&sh.peer[0][0])[i] = 0u;
+          reinterpret_cast<const unsigned long long*>(&gm)[threadIdx.x];
+    for (int i = lane; i < kMaxK; i += 32) {
+      sh.wcnt[warp][i] = 0;
+      sh.peer[warp][i] = 0u;
     }
     if (threadIdx.x == 0) {
       sh.slow_all = 0;
       sh.any_big = 0;
     }
-    __syncthreads();
-    split_tree = sh.tm.l.kind == kSplitter;
-    const int nsplit = sh.tm.nsplit;
+    __syncwarp();
+    split_tree = gm.l.kind == kSplitter;
+    const int nsplit = gm.nsplit;
     // a large splitter tree comes from its pool slot; without one the task
     // recurses in k_slow
-    bool slow = split_tree && nsplit > kTailSplit && sh.tm.pool < 0;
-    const uint64_t* splits = sh.tm.split;
+    bool slow = split_tree && nsplit > kTailSplit && gm.pool < 0;
+    const uint64_t* splits = gm.split;
     if (split_tree && nsplit > kTailSplit && !slow) {
       for (int i = threadIdx.x; i < nsplit; i += blockDim.x)
-        sh.split[i] = a.split_pool[(size_t)sh.tm.pool * 128 + i];
+        sh.split[i] = a.split_pool[(size_t)gm.pool * 128 + i];
       __syncthreads();
       splits = sh.split;
     }
     if (!slow) {
       Classifier<K> cls;
-      cls.load(sh.tm.l, a.exact_only);
+      cls.load(gm.l, a.exact_only);
       const int chunk = ((n + kRW * 32 - 1) / (kRW * 32)) * 32;
       const int steps = chunk / 32;
       Bits v[kRKPT];
