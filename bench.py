@@ -240,9 +240,22 @@ def cpu_baseline(inputs, sample_log2: int, cutoff: int):
         oracle.sort(x, cutoff=cutoff)
         keys += x.size
     dt = time.perf_counter() - t0
+    # beside it, on a quarter of that sample: std::sort under the totalOrder
+    # comparator on one core (the textbook routine the result must equal)
+    ms = max(1, m >> 2)
+    t1 = time.perf_counter()
+    skeys = 0
+    for d in inputs:
+        x = inputs[d][:ms]
+        oracle.std_sort(x)
+        skeys += x.size
+    st = time.perf_counter() - t1
     return {"value": keys / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"first 2^{sample_log2} keys of each of the {len(inputs)} arrays "
-                      f"({keys} keys, serial C++ oracle, {dt:.1f} s)"}
+                      f"({keys} keys, serial C++ oracle, {dt:.1f} s)",
+            "std_sort": {"value": skeys / st / 1e9, "unit": UNIT, "cores": 1,
+                         "sample": f"first 2^{max(0, sample_log2 - 2)} keys of each array, "
+                                   f"std::sort with the totalOrder comparator, {st:.1f} s"}}
 
 
 def run_reference(args):
