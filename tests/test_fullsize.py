@@ -1,0 +1,75 @@
+"""Sorts at the workloads' full sizes, in the launch configuration the bench
+times (k = 256, cutoff 256): 2^28 f64 keys of each of the eight
+distributions, 2^30 u64 keys, 2^30 u32 Zipf(1.0) keys over 1..2^24 and 2^29
+f32 normal keys.  The oracle cannot sort arrays this large within a test, so
+the checks are properties that hold at any size, evaluated on the device on
+keys mapped to signed integers whose order is IEEE totalOrder:
+
+- the output is non-decreasing;
+- the output is the input permuted: it equals, bit for bit, a library sort of
+  the same mapped input (the sorted order of a multiset is unique);
+- at sampled positions r, the output key y has fewer than r + 1 input keys
+  below it and more than r at or below it (its rank, counted from the input
+  alone)."""
+import numpy as np
+import pytest
+
+import datagen
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2208_06902_gb300 as p
+    p.load()
+
+
+def _total_order_key(t, code):
+    """int64 (or int32 widened) keys whose signed order is totalOrder."""
+    if code == 0:    # f64
+        b = t.view(torch.int64)
+        return b ^ ((b >> 63) & 0x7FFFFFFFFFFFFFFF)
+    if code == 1:    # f32
+        b = t.view(torch.int32).to(torch.int64)
+        return b ^ ((b >> 31) & 0x7FFFFFFF)
+    if code == 2:    # u64: flip the top bit
+        return t.view(torch.int64) ^ torch.iinfo(torch.int64).min
+    return t.view(torch.int32).to(torch.int64) & 0xFFFFFFFF   # u32
+
+
+def _check(x_host, code):
+    from paper_2208_06902_gb300 import Context
+    dev = torch.from_numpy(x_host.view(np.uint8)).cuda()
+    ref = _total_order_key(dev.view({0: torch.float64, 1: torch.float32,
+                                     2: torch.int64, 3: torch.int32}[code]), code)
+    ctx = Context(k=256, cutoff=256)
+    ctx.sort_ptr(dev.data_ptr(), x_host.size, code)
+    torch.cuda.synchronize()
+    out = _total_order_key(dev.view({0: torch.float64, 1: torch.float32,
+                                     2: torch.int64, 3: torch.int32}[code]), code)
+    assert bool((out[1:] >= out[:-1]).all()), "output not non-decreasing"
+    g = torch.Generator().manual_seed(x_host.size)
+    n = x_host.size
+    for r in torch.randint(0, n, (6,), generator=g).tolist() + [0, n - 1]:
+        y = out[r]
+        below = int((ref < y).sum())
+        at_or_below = int((ref <= y).sum())
+        assert below <= r < at_or_below, (r, below, at_or_below)
+    want = torch.sort(ref).values
+    assert torch.equal(out, want), "output is not the sorted input"
+    ctx.close()
+
+
+@pytest.mark.parametrize("dist", datagen.CONFIG2)
+def test_2p28_f64_distributions(dist):
+    _check(datagen.config2(dist, 1 << 28), 0)
+
+
+@pytest.mark.parametrize("kind,code", [("u64", 2), ("u32", 3), ("f32", 1)])
+def test_integer_and_f32_full_sizes(kind, code):
+    _check(datagen.config3(kind), code)
