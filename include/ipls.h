@@ -134,7 +134,7 @@ typedef struct iplsStats {
   int64_t scratch_bytes;      /* device scratch held by the context */
   int64_t trace_records;      /* passes recorded (may exceed trace_cap) */
   double max_bucket_frac;     /* largest bucket / subproblem size, grid passes */
-  int64_t slow_tasks;         /* ranges recursed inside one block (slow list), last call */
+  int64_t slow_tasks;         /* ranges recursed inside one block (slow lists), last call */
   int64_t slow_passes;        /* partition passes run by that in-block recursion, last call */
   int64_t sweep_tasks;        /* children above the cutoff taken by a second block-resident
                                  sweep (fit + pass + base case) instead, last call */

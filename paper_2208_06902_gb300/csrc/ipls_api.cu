@@ -119,7 +119,7 @@ struct iplsContext {
   int64_t k_bytes[16] = {};
   // host-buffer sorting
   char* host_stage = nullptr; int64_t host_stage_cap = 0;
-  // slow list of the block-resident tail
+  // slow lists of the block-resident tail (children / whole tasks, one half each)
   SlowTask* slow = nullptr; int64_t slow_cap = 0;
   SlowCtl* slow_ctl = nullptr;
   SlowCtl* h_slow = nullptr;          // pinned copy of *slow_ctl

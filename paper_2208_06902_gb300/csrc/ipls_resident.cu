@@ -898,7 +898,7 @@ cudaError_t launch_fill(const Fill* fills, int32_t nfill, int dtype, void* keys,
 }
 
 // One range sorted by one block with the in-block recursion of k_slow, the
-// range passed by value instead of through the slow list: the only device
+// range passed by value instead of through the slow lists: the only device
 // memory it touches besides the keys is a.run.
 template <class K>
 __global__ void __launch_bounds__(kResidentThreads, 1) k_slow_one(ResidentArgs a, SlowTask st) {
