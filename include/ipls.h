@@ -77,7 +77,7 @@ typedef struct iplsConfig {
   int32_t max_batch;      /* iplsSubmit: requests sorted together at most (0 = no limit,
                              1 = one at a time) */
   int32_t pl2_leaves;     /* 0: the FMCD linear model everywhere (the paper's IPLS).
-                             2..64 (a power of two): subproblems of more than 8192 keys
+                             2..1024 (a power of two): subproblems of more than 8192 keys
                              whose sample has at most 4096 keys use the two-level
                              piecewise-linear CDF model PL2 with this many leaves
                              (Ch.2 Learned Sort, Ch.3 RMI: a learned CDF trained on

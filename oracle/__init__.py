@@ -118,7 +118,9 @@ def lib():
                                            c.POINTER(c.c_int64), c.POINTER(c.c_int32)]
         L.oracle_std_sort.argtypes = [c.c_int, c.c_void_p, c.c_int64]
         L.oracle_pl2_fit.argtypes = [c.c_int, c.c_void_p, c.c_int64, c.c_int32, c.c_int32,
-                                     c.POINTER(Model), c.c_void_p]
+                                     c.POINTER(Model), c.c_void_p, c.c_void_p]
+        L.oracle_pl2_classify.argtypes = [c.c_int, c.c_void_p, c.c_int64, c.POINTER(Model),
+                                          c.c_void_p, c.c_void_p]
         L.oracle_pl2_loss_grad.argtypes = [c.c_int, c.c_void_p, c.c_int64, c.POINTER(Model),
                                            c.c_void_p, c.POINTER(c.c_double), c.c_void_p]
         L.oracle_multiset_hash.restype = None
@@ -195,10 +197,18 @@ def linear_model(A: float, Bc: float, k: int, xlo_bits: int = 0) -> Model:
 
 
 def classify(keys: np.ndarray, m: Model) -> np.ndarray:
-    """Bucket of every key: the model equation of Ch.3 (or the splitter tree)."""
+    """Bucket of every key: the model equation of Ch.3 (or the splitter tree,
+    or a PL2 model from pl2_fit, which carries its knots)."""
     keys = np.ascontiguousarray(keys)
     out = np.empty(keys.size, np.int32)
-    lib().oracle_classify(_code(keys), _ptr(keys), keys.size, ctypes.byref(m), _ptr(out))
+    if m.kind == 2:
+        y = np.ascontiguousarray(m.knots, np.float32)
+        rc = lib().oracle_pl2_classify(_code(keys), _ptr(keys), keys.size, ctypes.byref(m),
+                                       _ptr(y), _ptr(out))
+    else:
+        rc = lib().oracle_classify(_code(keys), _ptr(keys), keys.size, ctypes.byref(m), _ptr(out))
+    if rc != 0:
+        raise RuntimeError(f"oracle classify failed ({rc})")
     return out
 
 
@@ -272,14 +282,17 @@ def pl2_fit(sorted_sample: np.ndarray, M: int = 64, K: int = 256):
     s = np.ascontiguousarray(sorted_sample)
     m = Model()
     losses = np.zeros(PL2_STEPS + 1, np.float64)
-    if lib().oracle_pl2_fit(_code(s), _ptr(s), s.size, M, K, ctypes.byref(m), _ptr(losses)) != 0:
+    knots = np.zeros(M + 1, np.float32)
+    if lib().oracle_pl2_fit(_code(s), _ptr(s), s.size, M, K, ctypes.byref(m), _ptr(losses),
+                            _ptr(knots)) != 0:
         return None
+    m.knots = knots
     return m, losses
 
 
 def pl2_knots(m: Model) -> np.ndarray:
-    """The knot values y_0..y_M of a PL2 model (binary32)."""
-    return np.array(m.split[: m.nsplit + 1], np.uint64).astype(np.uint32).view(np.float32).copy()
+    """The knot values y_0..y_M of a PL2 model from pl2_fit (binary32)."""
+    return np.array(m.knots, np.float32)
 
 
 def pl2_loss_grad(sorted_sample: np.ndarray, m: Model, y: np.ndarray):

@@ -95,8 +95,8 @@ struct OracleModel {
   double ud;        // the u_d the slope came from
   int32_t nsplit;   // splitter count (kind 1); leaves M (kind 2)
   int32_t nbuckets; // buckets of this pass: k, or 2*nsplit+1 for splitters
-  uint64_t split[128];  // splitters as totalOrder bits, ascending, unique;
-                        // kind 2: the knot values y_0..y_M as binary32 bits
+  uint64_t split[128];  // splitters as totalOrder bits, ascending, unique
+                        // (kind 2 keeps its knots y_0..y_M beside the model)
   int32_t pl2_sh;   // kind 2: leaf width 2^sh in fixed-point units
   int32_t pl2_rho;  // kind 2: fixed-point scale, X(x) = trunc(x / 2^rho)
   int64_t pl2_x0;   // kind 2: X(x_0), the sample minimum
@@ -387,8 +387,8 @@ struct PL2Feat {
 // extremes (the duplicate rule takes over) or a range that does not fit the
 // fixed point (FMCD takes over).
 template <class T>
-bool pl2_fit(const T* x, int64_t S, int32_t M, int32_t K, OracleModel* m, PL2Feat* feat_out,
-             std::vector<double>* loss_trace) {
+bool pl2_fit(const T* x, int64_t S, int32_t M, int32_t K, OracleModel* m, std::vector<float>* knots,
+             PL2Feat* feat_out, std::vector<double>* loss_trace) {
   typedef Key<T> KT;
   if (KT::ord(x[0]) == KT::ord(x[S - 1]) || !KT::finite(x[0]) || !KT::finite(x[S - 1])) return false;
   const double range = KT::diff(x[S - 1], x[0]);
@@ -421,7 +421,7 @@ bool pl2_fit(const T* x, int64_t S, int32_t M, int32_t K, OracleModel* m, PL2Fea
     while (c < S && f.leaf[c] < j) ++c;
     f.start[j] = c;
   }
-  std::vector<float> y(M + 1), tau(S), r(S), G(M + 1), H(M + 1);
+  std::vector<float> y(M + 1), tau(S), r(S);
   for (int64_t i = 0; i < S; ++i) tau[i] = ((float)i + 0.5f) / (float)S;
   // initial knots: the empirical CDF at the knots
   for (int32_t j = 0; j <= M; ++j) y[j] = (float)f.start[j] / (float)S;
@@ -430,8 +430,7 @@ bool pl2_fit(const T* x, int64_t S, int32_t M, int32_t K, OracleModel* m, PL2Fea
     for (int64_t i = 0; i < S; ++i) L += (double)r[i] * (double)r[i];
     return L / (double)S;
   };
-  for (int step = 0; step <= kPL2Steps; ++step) {
-    // forward: F and the residual of every sample
+  auto forward = [&]() {  // F and the residual of every sample
     for (int64_t i = 0; i < S; ++i) {
       const int32_t a = f.leaf[i];
       const float t1 = 1.0f - f.w[i];
@@ -440,35 +439,41 @@ bool pl2_fit(const T* x, int64_t S, int32_t M, int32_t K, OracleModel* m, PL2Fea
       const float F = p + q;
       r[i] = F - tau[i];
     }
-    if (loss_trace) loss_trace->push_back(loss());
-    if (step == kPL2Steps) break;
-    // backward: dL/dy_j = (2/S) G_j and curvature (2/S) H_j, summed over
-    // leaf j (weight 1-w) then leaf j-1 (weight w), in sample order
-    for (int32_t j = 0; j <= M; ++j) {
-      float g = 0.0f, h = 0.0f;
-      if (j < M)
-        for (int64_t i = f.start[j]; i < f.start[j + 1]; ++i) {
-          const float t1 = 1.0f - f.w[i];
-          g = g + r[i] * t1;
-          h = h + t1 * t1;
-        }
-      if (j > 0)
-        for (int64_t i = f.start[j - 1]; i < f.start[j]; ++i) {
-          g = g + r[i] * f.w[i];
-          h = h + f.w[i] * f.w[i];
-        }
-      G[j] = g;
-      H[j] = h;
+  };
+  for (int step = 0; step <= kPL2Steps; ++step) {
+    if (loss_trace) {
+      forward();
+      loss_trace->push_back(loss());
     }
-    // half a diagonal Newton step on every knot (the 2/S factors cancel)
-    for (int32_t j = 0; j <= M; ++j)
-      if (H[j] > 0.0f) {
-        const float q = G[j] / H[j];
-        y[j] = y[j] - 0.5f * q;
+    if (step == kPL2Steps) break;
+    // red-black coordinate descent: the odd knots, then the even ones.  Knots
+    // of one parity share no sample, so each moves to the exact minimiser of
+    // the loss along its own coordinate, y_j - G_j / H_j (the 1-D quadratic's
+    // Newton step), clamped to [y_{j-1}, y_{j+1}] (0 and 1 at the ends): in
+    // exact arithmetic the loss never rises, and the knots stay in [0, 1],
+    // non-decreasing.  G_j and H_j sum leaf j (weight 1-w) then leaf j-1
+    // (weight w) in sample order.
+    for (int parity = 1; parity >= 0; --parity) {
+      forward();
+      for (int32_t j = parity; j <= M; j += 2) {
+        float g = 0.0f, h = 0.0f;
+        if (j < M)
+          for (int64_t i = f.start[j]; i < f.start[j + 1]; ++i) {
+            const float t1 = 1.0f - f.w[i];
+            g = g + r[i] * t1;
+            h = h + t1 * t1;
+          }
+        if (j > 0)
+          for (int64_t i = f.start[j - 1]; i < f.start[j]; ++i) {
+            g = g + r[i] * f.w[i];
+            h = h + f.w[i] * f.w[i];
+          }
+        if (h > 0.0f) {
+          const float lo = j > 0 ? y[j - 1] : 0.0f, hi = j < M ? y[j + 1] : 1.0f;
+          y[j] = std::min(std::max(y[j] - g / h, lo), hi);
+        }
       }
-    // keep the knots in [0, 1] and non-decreasing
-    y[0] = std::min(std::max(y[0], 0.0f), 1.0f);
-    for (int32_t j = 1; j <= M; ++j) y[j] = std::min(std::max(y[j], y[j - 1]), 1.0f);
+    }
   }
   m->kind = 2;
   m->capped = 0;
@@ -479,11 +484,7 @@ bool pl2_fit(const T* x, int64_t S, int32_t M, int32_t K, OracleModel* m, PL2Fea
   m->pl2_sh = sh;
   m->pl2_rho = rho;
   m->pl2_x0 = X0;
-  for (int32_t j = 0; j <= M; ++j) {
-    uint32_t b32;
-    std::memcpy(&b32, &y[j], 4);
-    m->split[j] = b32;   // binary32 knot bits
-  }
+  *knots = y;
   if (feat_out) *feat_out = f;
   return true;
 }
@@ -493,7 +494,7 @@ bool pl2_fit(const T* x, int64_t S, int32_t M, int32_t K, OracleModel* m, PL2Fea
 // leaf are, F is within a leaf (non-negative slope, monotone roundings),
 // and the leaf ranges [floor(k y_j), floor(k y_{j+1})] follow each other.
 template <class T>
-int32_t pl2_bucket(T x, const OracleModel& m) {
+int32_t pl2_bucket(T x, const OracleModel& m, const float* y) {
   typedef Key<T> KT;
   const int32_t K = m.nbuckets, M = m.nsplit;
   if (KT::is_nan(x)) return KT::neg_sign(x) ? 0 : K - 1;
@@ -504,10 +505,7 @@ int32_t pl2_bucket(T x, const OracleModel& m) {
   if (U < 0) return 0;
   const int64_t j = U >> m.pl2_sh;
   if (j >= M) return K - 1;
-  float y0, y1;
-  const uint32_t b0 = (uint32_t)m.split[j], b1 = (uint32_t)m.split[j + 1];
-  std::memcpy(&y0, &b0, 4);
-  std::memcpy(&y1, &b1, 4);
+  const float y0 = y[j], y1 = y[j + 1];
   const float kf = (float)K;
   const float inv = std::ldexp(1.0f, -m.pl2_sh);
   const float w = (float)(U - (j << m.pl2_sh)) * inv;
@@ -523,9 +521,9 @@ int32_t pl2_bucket(T x, const OracleModel& m) {
 }
 
 template <class T>
-int32_t bucket_of(T x, const OracleModel& m, T xlo) {
+int32_t bucket_of(T x, const OracleModel& m, T xlo, const float* knots = nullptr) {
   if (m.kind == 0) return linear_bucket<T>(x, m, xlo);
-  if (m.kind == 2) return pl2_bucket<T>(x, m);
+  if (m.kind == 2) return pl2_bucket<T>(x, m, knots);
   return splitter_bucket(Key<T>::ord(x), m);
 }
 
@@ -553,11 +551,12 @@ void partition_pass(const T* src, int64_t n, int64_t off, int32_t level,
   std::vector<int32_t> b(n);
   // PL2 for large subproblems when enabled; its pass falls back to the
   // splitter tree on no progress or when a bucket holds more than 4n/k keys
+  std::vector<float> knots;
   if (usable && cfg.pl2_leaves > 0 && n > kPL2MinKeys && S <= kPL2MaxSample &&
-      pl2_fit<T>(samp.data(), S, cfg.pl2_leaves, cfg.k, m, nullptr, nullptr)) {
+      pl2_fit<T>(samp.data(), S, cfg.pl2_leaves, cfg.k, m, &knots, nullptr, nullptr)) {
     linear = false;
     std::fill(counts, counts + m->nbuckets, 0);
-    for (int64_t i = 0; i < n; ++i) counts[b[i] = pl2_bucket<T>(src[i], *m)]++;
+    for (int64_t i = 0; i < n; ++i) counts[b[i] = pl2_bucket<T>(src[i], *m, knots.data())]++;
     bool bad = false;
     for (int32_t j = 0; j < m->nbuckets; ++j)
       if (counts[j] == n || counts[j] * (int64_t)m->nbuckets > 4 * n) bad = true;
@@ -734,9 +733,11 @@ int oracle_fmcd_bruteforce(int dtype, const void* sorted, int64_t N, int32_t K, 
 }
 
 // Bucket of every key under a given model (kind 0 uses A, Bc and the key
-// whose raw bits are xlo_bits; kind 1 uses the splitters).
+// whose raw bits are xlo_bits; kind 1 uses the splitters).  A PL2 model
+// (kind 2) needs its knots: oracle_pl2_classify.
 int oracle_classify(int dtype, const void* keys, int64_t n, const OracleModel* m,
                     int32_t* out) {
+  if (m->kind == 2) return 2;
   return dispatch(dtype, [&](auto* tag) {
     typedef std::remove_pointer_t<decltype(tag)> T;
     T xlo;
@@ -810,17 +811,31 @@ int oracle_sort_segments(int dtype, void* keys, const int64_t* off, int64_t nseg
 }
 
 // Reference sort for the pins: std::sort under totalOrder.
-// PL2 on a sorted sample: the fitted model, and the loss after each of the
-// training steps (kPL2Steps + 1 values).  Returns 1 when the sample's range
-// could not be used.
+// PL2 on a sorted sample: the fitted model, its knots y_0..y_M (M + 1
+// floats into `knots`) and the loss after each of the training steps
+// (kPL2Steps + 1 values).  Returns 1 when the sample's range could not be
+// used.
 int oracle_pl2_fit(int dtype, const void* sorted, int64_t S, int32_t M, int32_t K, OracleModel* m,
-                   double* losses) {
+                   double* losses, float* knots) {
   return dispatch(dtype, [&](auto* tag) {
     typedef std::remove_pointer_t<decltype(tag)> T;
     std::memset(m, 0, sizeof(*m));
     std::vector<double> lt;
-    if (!pl2_fit<T>((const T*)sorted, S, M, K, m, nullptr, &lt)) return 1;
+    std::vector<float> y;
+    if (!pl2_fit<T>((const T*)sorted, S, M, K, m, &y, nullptr, &lt)) return 1;
     for (size_t i = 0; i < lt.size(); ++i) losses[i] = lt[i];
+    for (size_t j = 0; j < y.size(); ++j) knots[j] = y[j];
+    return 0;
+  });
+}
+
+// Buckets of keys[0..n) under a PL2 model with knots y_0..y_M.
+int oracle_pl2_classify(int dtype, const void* keys, int64_t n, const OracleModel* m,
+                        const float* knots, int32_t* out) {
+  return dispatch(dtype, [&](auto* tag) {
+    typedef std::remove_pointer_t<decltype(tag)> T;
+    const T* x = (const T*)keys;
+    for (int64_t i = 0; i < n; ++i) out[i] = pl2_bucket<T>(x[i], *m, knots);
     return 0;
   });
 }

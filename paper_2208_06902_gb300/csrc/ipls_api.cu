@@ -53,6 +53,7 @@ struct Slot {
   int32_t* chunk2sub = nullptr;  int64_t chunk_cap = 0;
   Model* models = nullptr;       int64_t model_cap = 0;
   ThrTable* tabs = nullptr;      int64_t tab_cap = 0;
+  float* knots = nullptr;        int64_t knot_cap = 0;   // PL2 knots, when enabled
   uint64_t* counts = nullptr;    int64_t count_cap = 0;
   int64_t* bases = nullptr;      int64_t base_cap = 0;
   Group* groups = nullptr;       int64_t group_cap = 0;
@@ -427,6 +428,7 @@ iplsStatus sort_impl(iplsCtx c, void* keys, int64_t n, int dtype, const int64_t*
     Slot& Y = c->slot[(level + 1) & 1];
     IPLS_TRY(ensure(c, X.models, X.model_cap, nsub));
     IPLS_TRY(ensure(c, X.tabs, X.tab_cap, nsub));
+    if (cfg.pl2_leaves > 0) IPLS_TRY(ensure(c, X.knots, X.knot_cap, nsub * (int64_t)(cfg.pl2_leaves + 1)));
     IPLS_TRY(ensure(c, X.counts, X.count_cap, nsub * kMaxK));
     IPLS_TRY(ensure(c, X.bases, X.base_cap, nsub * 257));
     IPLS_TRY(ensure_groups(c, X, 2 * n / (cfg.cutoff + 1) + 257 * nsub + 16));
@@ -469,6 +471,7 @@ iplsStatus sort_impl(iplsCtx c, void* keys, int64_t n, int dtype, const int64_t*
     const int max_sample = sample_size_host(std::max<int64_t>(max_sub_n, 2), level, cfg.k, cfg.root_sample);
     a.max_sample = max_sample;
     a.pl2_leaves = cfg.pl2_leaves;
+    a.knots = cfg.pl2_leaves > 0 ? X.knots : nullptr;
     IPLS_CUDA(timed(c, kkFit, [&] { return launch_fit(a, c->stream, max_sample); }));
     IPLS_CUDA(timed(c, kkHist, [&] { return launch_hist(a, c->stream, 0, occupancy_grid(c, 0, dtype)); }));
     IPLS_CUDA(timed(c, kkCheck, [&] { return launch_check(a, c->stream, max_sample); }));
@@ -540,7 +543,7 @@ iplsStatus validate_cfg(const iplsConfig& c) {
   if (c.spin_limit < 1) return fail(IPLS_ERR_ARG, "spin_limit must be >= 1");
   if (c.max_batch < 0) return fail(IPLS_ERR_ARG, "max_batch must be >= 0");
   if (c.pl2_leaves != 0 && (c.pl2_leaves < 2 || c.pl2_leaves > kPL2MaxLeaves || (c.pl2_leaves & (c.pl2_leaves - 1))))
-    return fail(IPLS_ERR_ARG, "pl2_leaves must be 0 or a power of two in [2, 64]");
+    return fail(IPLS_ERR_ARG, "pl2_leaves must be 0 or a power of two in [2, 1024]");
   if (c.budget_bytes < 0) return fail(IPLS_ERR_ARG, "budget_bytes must be >= 0");
   return IPLS_OK;
 }
@@ -798,6 +801,7 @@ iplsStatus iplsDestroy(iplsCtx c) {
     dev_free(c, s.chunk2sub, s.chunk_cap * sizeof(int32_t));
     dev_free(c, s.models, s.model_cap * sizeof(Model));
     dev_free(c, s.tabs, s.tab_cap * sizeof(ThrTable));
+    dev_free(c, s.knots, s.knot_cap * sizeof(float));
     dev_free(c, s.counts, s.count_cap * sizeof(uint64_t));
     dev_free(c, s.bases, s.base_cap * sizeof(int64_t));
     dev_free(c, s.groups, s.group_cap * sizeof(Group));
@@ -835,6 +839,7 @@ iplsStatus iplsScratchBytes(iplsCtx c, int64_t n, iplsDtype dtype, size_t* bytes
   b += (size_t)pool_slots(n / (cutoff + 1)) * 128 * 8;             // splitter pool
   b += (size_t)tiles * kMaxK * 8;                                  // look-back words
   b += 2 * (size_t)subs * (sizeof(Sub) + sizeof(Model) + kMaxK * 8 + 257 * 8);
+  if (c && c->cfg.pl2_leaves > 0) b += 2 * (size_t)subs * (c->cfg.pl2_leaves + 1) * sizeof(float);
   b += 2 * (size_t)tiles * 4;
   b += 2 * (size_t)(2 * n / rmax + 257 * subs + 16) * (sizeof(Group) + 4 + sizeof(TailModel));
   b += 2 * (size_t)(n / kFillChunk + 129 * subs + 16) * sizeof(Fill);

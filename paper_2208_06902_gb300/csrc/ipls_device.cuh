@@ -676,12 +676,15 @@ struct ExactQueue {
 // CDF as in Ch.3).  The root maps a key to fixed point X = trunc(x/2^rho)
 // and to leaf j = (X - X0) >> sh of M equal-width leaves over the sample's
 // range; leaf j interpolates between knot values y_j and y_{j+1}.
-// Training: knots start at the empirical CDF, then kPL2Steps steps of half
-// a diagonal Newton step per knot, each followed by clamping the knots into
-// [0, 1] non-decreasing.  Binary32 throughout; every sum runs over sample
-// indices in order (the samples of a leaf are contiguous), with one rounding
-// per operation, so the model is the same bit for bit wherever it is
-// computed.
+// Training: knots start at the empirical CDF, then kPL2Steps red-black sweeps
+// of coordinate descent: every odd knot, then every even one, moves to the
+// exact minimiser of the loss along its coordinate (y_j - G_j / H_j),
+// clamped to [y_{j-1}, y_{j+1}] (0 and 1 at the ends); knots of one parity
+// share no sample, so a half-sweep is parallel, the loss does not rise (in
+// exact arithmetic) and the knots stay in [0, 1], non-decreasing.  Binary32
+// throughout; every sum runs over sample indices in order (the samples of a
+// leaf are contiguous), with one rounding per operation, so the model is the
+// same bit for bit wherever it is computed.
 // ---------------------------------------------------------------------------
 struct PL2Scratch {
   int32_t* leaf;    // [S]
@@ -696,10 +699,11 @@ __device__ __forceinline__ int exponent_of(double r) {
 }
 
 // Block-wide (all threads).  so[0..S) is the sorted sample (order bits).
-// Returns false (m untouched) when the sample's range cannot carry PL2.
-// Training is binary32, one rounding per operation.
+// Returns false (m untouched) when the sample's range cannot carry PL2; else
+// the knots y_0..y_M go to kout.  Training is binary32, one rounding per
+// operation.
 template <class K>
-__device__ bool fit_pl2(const typename KT<K>::Ord* so, int S, int M, int K_, Model* m,
+__device__ bool fit_pl2(const typename KT<K>::Ord* so, int S, int M, int K_, Model* m, float* kout,
                         PL2Scratch sc, float* y, int* start, int* s_flag, long long* s_x0,
                         int* s_rho, int* s_sh) {
   using T = KT<K>;
@@ -752,43 +756,36 @@ __device__ bool fit_pl2(const typename KT<K>::Ord* so, int S, int M, int K_, Mod
   }
   __syncthreads();
   for (int step = 0; step < kPL2Steps; ++step) {
-    for (int i = tid; i < S; i += nt) {  // forward: residual of every sample
-      const int a = sc.leaf[i];
-      const float t1 = __fsub_rn(1.0f, sc.w[i]);
-      const float F = __fadd_rn(__fmul_rn(y[a], t1), __fmul_rn(y[a + 1], sc.w[i]));
-      const float tau = __fdiv_rn(__fadd_rn((float)i, 0.5f), (float)S);
-      sc.r[i] = __fsub_rn(F, tau);
-    }
-    __syncthreads();
-    float q = 0.0f;
-    bool upd = false;
-    if (tid <= M) {  // backward: gradient and curvature of knot tid
-      const int j = tid;
-      float g = 0.0f, h = 0.0f;
-      if (j < M)
-        for (int i = start[j]; i < start[j + 1]; ++i) {
-          const float t1 = __fsub_rn(1.0f, sc.w[i]);
-          g = __fadd_rn(g, __fmul_rn(sc.r[i], t1));
-          h = __fadd_rn(h, __fmul_rn(t1, t1));
-        }
-      if (j > 0)
-        for (int i = start[j - 1]; i < start[j]; ++i) {
-          g = __fadd_rn(g, __fmul_rn(sc.r[i], sc.w[i]));
-          h = __fadd_rn(h, __fmul_rn(sc.w[i], sc.w[i]));
-        }
-      if (h > 0.0f) {
-        q = __fdiv_rn(g, h);
-        upd = true;
+    for (int parity = 1; parity >= 0; --parity) {
+      for (int i = tid; i < S; i += nt) {  // forward: residual of every sample
+        const int a = sc.leaf[i];
+        const float t1 = __fsub_rn(1.0f, sc.w[i]);
+        const float F = __fadd_rn(__fmul_rn(y[a], t1), __fmul_rn(y[a + 1], sc.w[i]));
+        const float tau = __fdiv_rn(__fadd_rn((float)i, 0.5f), (float)S);
+        sc.r[i] = __fsub_rn(F, tau);
       }
+      __syncthreads();
+      // the knots of this parity (they read only knots of the other one)
+      for (int j = 2 * tid + parity; j <= M; j += 2 * nt) {
+        float g = 0.0f, h = 0.0f;
+        if (j < M)
+          for (int i = start[j]; i < start[j + 1]; ++i) {
+            const float t1 = __fsub_rn(1.0f, sc.w[i]);
+            g = __fadd_rn(g, __fmul_rn(sc.r[i], t1));
+            h = __fadd_rn(h, __fmul_rn(t1, t1));
+          }
+        if (j > 0)
+          for (int i = start[j - 1]; i < start[j]; ++i) {
+            g = __fadd_rn(g, __fmul_rn(sc.r[i], sc.w[i]));
+            h = __fadd_rn(h, __fmul_rn(sc.w[i], sc.w[i]));
+          }
+        if (h > 0.0f) {
+          const float lo = j > 0 ? y[j - 1] : 0.0f, hi = j < M ? y[j + 1] : 1.0f;
+          y[j] = fminf(fmaxf(__fsub_rn(y[j], __fdiv_rn(g, h)), lo), hi);
+        }
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    if (upd) y[tid] = __fsub_rn(y[tid], __fmul_rn(0.5f, q));
-    __syncthreads();
-    if (tid == 0) {  // knots in [0, 1], non-decreasing
-      y[0] = fminf(fmaxf(y[0], 0.0f), 1.0f);
-      for (int j = 1; j <= M; ++j) y[j] = fminf(fmaxf(y[j], y[j - 1]), 1.0f);
-    }
-    __syncthreads();
   }
   if (tid == 0) {
     m->l.kind = kPL2;
@@ -801,19 +798,19 @@ __device__ bool fit_pl2(const typename KT<K>::Ord* so, int S, int M, int K_, Mod
     m->l.qlo = X0;
     m->nsplit = M;
   }
-  for (int j = tid; j <= M; j += nt) m->split[j] = (uint64_t)__float_as_uint(y[j]);
+  for (int j = tid; j <= M; j += nt) kout[j] = y[j];
   __syncthreads();
   return true;
 }
 
-// Per-model tables for classifying with a PL2 model: the binary32 knots and
-// the first bucket of every leaf.
-__device__ __forceinline__ void pl2_tables(const Model& m, float* yf, int* lo, int nthreads_tid,
-                                           int nthreads) {
+// Per-model tables for classifying with a PL2 model: its binary32 knots
+// (from the level's knot buffer) and the first bucket of every leaf.
+__device__ __forceinline__ void pl2_tables(const Model& m, const float* knots, float* yf, int* lo,
+                                           int nthreads_tid, int nthreads) {
   const int M = m.nsplit, K = m.l.nb;
   const float kf = (float)K;
   for (int j = nthreads_tid; j <= M; j += nthreads) {
-    yf[j] = __uint_as_float((unsigned)m.split[j]);
+    yf[j] = knots[j];
     int b = (int)floorf(__fmul_rn(yf[j], kf));
     lo[j] = b > K - 1 ? K - 1 : b;
   }

@@ -21,12 +21,13 @@ enum ModelKind : int32_t { kLinear = 0, kSplitter = 1, kPL2 = 2 };
 
 // PL2 (piecewise-linear CDF): used, when enabled, for subproblems larger
 // than kPL2MinKeys whose sample has at most kPL2MaxSample keys; trained for
-// kPL2Steps steps.  Model layout: l.kind = kPL2, l.nb = k, l.S, l.D = l.rho
-// ... see fit_pl2; nsplit = leaves M, split[0..M] = knot values (binary32 bits).
+// kPL2Steps steps.  Model layout: l.kind = kPL2, l.nb = k, l.S, l.D = leaf
+// shift, l.rho, l.qlo = X(sample minimum); nsplit = leaves M.  The knot values
+// y_0..y_M (binary32) are in the level's knot buffer, M + 1 per subproblem.
 constexpr int64_t kPL2MinKeys = 8192;
 constexpr int kPL2MaxSample = 4096;
 constexpr int kPL2Steps = 8;
-constexpr int kPL2MaxLeaves = 64;
+constexpr int kPL2MaxLeaves = 1024;
 
 // Linear partition model of one subproblem: b(x) = clamp(floor(fma(A,
 // x (-) x_lo, Bc)), 0, nb-1) (Ch.3 model equation, centred form).
@@ -207,6 +208,7 @@ struct LevelArgs {
   int exact_only;
   int use_tables;        // build and use the exact threshold index
   int pl2_leaves;        // 0, or PL2 leaves for subproblems above kPL2MinKeys
+  float* knots;          // [nsub][pl2_leaves + 1] PL2 knot values (when pl2_leaves > 0)
   int max_sample;        // largest sample of the level (k_fit's shared-memory layout)
   int64_t spin_limit;
   uint32_t epoch;        // look-back epoch of this level's scatter

@@ -156,7 +156,8 @@ __global__ void __launch_bounds__(kFitThreads) k_fit(LevelArgs a) {
     __shared__ int pflag, prho, psh;
     __shared__ long long px0;
     if (threadIdx.x == 0) sm.nsplit = 0;
-    pl2 = fit_pl2<K>(so, S, a.pl2_leaves, a.k, &sm, sc, py, pstart, &pflag, &px0, &prho, &psh);
+    pl2 = fit_pl2<K>(so, S, a.pl2_leaves, a.k, &sm, a.knots + (size_t)s * (a.pl2_leaves + 1), sc, py,
+                     pstart, &pflag, &px0, &prho, &psh);
   }
   if (!pl2) fit_model<BlockG, K>(so, S, a.k, &sm, fs);
   copy_model(&a.models[s], &sm);
@@ -214,7 +215,7 @@ __global__ void __launch_bounds__(kPassThreads, 4) k_hist(LevelArgs a, int rehis
       cls.load(sm, a.exact_only);
       use_tab = a.use_tables && sm.l.kind == kLinear && tab.ok;
       if (sm.l.kind == kPL2) {
-        pl2_tables(sm, pl_yf, pl_lo, threadIdx.x, blockDim.x);
+        pl2_tables(sm, a.knots + (size_t)s * (a.pl2_leaves + 1), pl_yf, pl_lo, threadIdx.x, blockDim.x);
         __syncthreads();
       }
     }

@@ -24,20 +24,21 @@ def _same(a, b):
     return a.dtype == b.dtype and np.array_equal(a.view(np.uint8), b.view(np.uint8))
 
 
+@pytest.mark.parametrize("leaves", [64, 1024])
 @pytest.mark.parametrize("dtype", [np.float64, np.float32, np.uint64, np.uint32])
 @pytest.mark.parametrize("dist", ["uniform", "normal", "lognormal", "exponential", "mixgauss",
                                   "zipf", "rootdups", "twodups"])
-def test_pl2_passes_match_the_oracle(dtype, dist):
+def test_pl2_passes_match_the_oracle(dtype, dist, leaves):
     x = datagen.generate(dist, 300_017, dtype, seed=31)
-    want, recs, _ = oracle.sort(x, cutoff=64, trace_cap=100_000, pl2_leaves=64)
-    got, ctx = gpu_sort(x, cutoff=64, trace_cap=100_000, pl2_leaves=64)
+    want, recs, _ = oracle.sort(x, cutoff=64, trace_cap=100_000, pl2_leaves=leaves)
+    got, ctx = gpu_sort(x, cutoff=64, trace_cap=100_000, pl2_leaves=leaves)
     assert _same(got, want)
     compare_traces(ctx.trace(), recs)
     if dist in ("uniform", "normal", "lognormal") and dtype in (np.float64, np.float32):
         assert any(r.kind == 2 for r in ctx.trace())
 
 
-@pytest.mark.parametrize("leaves", [2, 16, 64])
+@pytest.mark.parametrize("leaves", [2, 16, 64, 256, 1024])
 def test_pl2_grid_levels_match_the_oracle(leaves):
     x = datagen.generate("lognormal", 1 << 22, np.float64, seed=32)
     want, recs, _ = oracle.sort(x, cutoff=256, trace_cap=300_000, pl2_leaves=leaves)
