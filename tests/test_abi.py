@@ -55,3 +55,22 @@ def test_product_package_does_not_import_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "ipls_oracle" not in text, f
+
+
+def test_config_validation_without_gpu():
+    # iplsCreate checks the configuration before any CUDA call
+    import paper_2208_06902_gb300 as p
+    lib = p.load()
+    ctx = ctypes.c_void_p()
+    for bad in (1, 3, 96, 2048, -2):
+        cfg = p.iplsDefaultConfig()
+        cfg.pl2_leaves = bad
+        assert lib.iplsCreate(ctypes.byref(ctx), ctypes.byref(cfg), None, None, None, None) == -1
+        assert "pl2_leaves" in p.iplsLastError()
+    for good in (0, 2, 64, 1024):
+        cfg = p.iplsDefaultConfig()
+        cfg.pl2_leaves = good
+        rc = lib.iplsCreate(ctypes.byref(ctx), ctypes.byref(cfg), None, None, None, None)
+        assert rc != -1 or "pl2_leaves" not in p.iplsLastError()
+        if rc == 0:
+            lib.iplsDestroy(ctx)
