@@ -246,7 +246,8 @@ iplsStatus tail_sweep(iplsCtx c, ResidentArgs& ra) {
     ra.split_pool_slots = (int32_t)std::min<int64_t>(c->split_pool_cap / 128, kSplitPoolMax);
     IPLS_CUDA(timed(c, kkTailFit, [&] { return launch_tail_fit(ra, c->stream, c->num_sms); }));
   }
-  IPLS_CUDA(timed(c, kkResident, [&] { return launch_resident(ra, c->stream); }));
+  IPLS_CUDA(timed(c, kkResident, [&] { return launch_resident(ra, c->stream, 0); }));
+  IPLS_CUDA(timed(c, kkResident, [&] { return launch_resident(ra, c->stream, 1); }));
   return IPLS_OK;
 }
 

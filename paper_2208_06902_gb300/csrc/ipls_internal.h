@@ -292,7 +292,8 @@ cudaError_t launch_scan(const LevelArgs& a, cudaStream_t s);
 cudaError_t launch_tilescan(const LevelArgs& a, cudaStream_t s, int grid);
 cudaError_t launch_scatter(const LevelArgs& a, cudaStream_t s, int sms);
 cudaError_t launch_tail_fit(const ResidentArgs& a, cudaStream_t s, int sms);
-cudaError_t launch_resident(const ResidentArgs& a, cudaStream_t s);
+// large = 0: tasks of up to 4096 keys (256-thread blocks); 1: the rest.
+cudaError_t launch_resident(const ResidentArgs& a, cudaStream_t s, int large);
 cudaError_t launch_slow(const ResidentArgs& a, cudaStream_t s, int sms);
 // groups[i] = the fitted tail task of list[i], fit_list[i] = i (i < n).
 cudaError_t launch_slow_groups(const SlowTask* list, int32_t n, Group* groups, int32_t* fit_list,

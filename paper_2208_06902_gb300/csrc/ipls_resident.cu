@@ -453,12 +453,16 @@ __global__ void __launch_bounds__(kResidentThreads, 2) k_slow(ResidentArgs a) {
 // ---------------------------------------------------------------------------
 // k_tail
 // ---------------------------------------------------------------------------
-template <class K>
+// k_tail runs in two sizes: tasks of up to kTailSmall keys in 256-thread
+// blocks (four per SM), larger ones in 512-thread blocks (two per SM).
+constexpr int kTailSmall = 4096;
+
+template <class K, int kCap, int kW>
 struct TailSmem {
-  typename KT<K>::Ord keys[kResidentMax];
-  unsigned char seg[kResidentMax];   // segment (bucket or child) of each position
-  unsigned short wcnt[kRW][kMaxK];
-  unsigned int peer[kRW][kMaxK];     // lanes of the current step per bucket (kept zero between steps)
+  typename KT<K>::Ord keys[kCap];
+  unsigned char seg[kCap];   // segment (bucket or child) of each position
+  unsigned short wcnt[kW][kMaxK];
+  unsigned int peer[kW][kMaxK];     // lanes of the current step per bucket (kept zero between steps)
   int bstart[kMaxK + 1];
   int segb[kMaxK + 1];
   int tot[kMaxK];
@@ -467,15 +471,18 @@ struct TailSmem {
   uint64_t split[128];   // a tree too large for the record, from the pool
   typename KT<K>::Ord seglo[kMaxK];  // smallest key of each base-cased segment
   unsigned char segpk[kMaxK];        // 1: the segment is ranked on packed words
-  typename KT<K>::Ord wlo[kRW], whi[kRW];  // per-warp key range of a fitted task
+  typename KT<K>::Ord wlo[kW], whi[kW];    // per-warp key range of a fitted task
   typename KT<K>::Ord tlo;           // smallest key of a fitted task
   int tpk;                           // 1: the fitted task's keys are placed packed
   int slow_all;
   int any_big;   // some bucket above the cutoff would be queued
   long long rec;
 };
-// two blocks per SM (each with its 1 KB of reserved shared memory)
-static_assert(2 * (sizeof(TailSmem<double>) + 1024) <= 233472, "k_tail must keep two blocks per SM");
+// two (four) blocks per SM, each with its 1 KB of reserved shared memory
+static_assert(2 * (sizeof(TailSmem<double, kResidentMax, kRW>) + 1024) <= 233472,
+              "the large k_tail must keep two blocks per SM");
+static_assert(4 * (sizeof(TailSmem<double, kTailSmall, kRW / 2>) + 1024) <= 233472,
+              "the small k_tail must keep four blocks per SM");
 
 // A child above the cutoff (it may take another tail round).
 __device__ __forceinline__ void push_slow(const ResidentArgs& a, int64_t off, int n, int level) {
@@ -497,16 +504,21 @@ __device__ __forceinline__ void push_whole(const ResidentArgs& a, int64_t off, i
 constexpr int kPosBits = 13;
 static_assert(kResidentMax <= (1 << kPosBits), "positions must fit the packed word");
 
-template <class K>
-__global__ void __launch_bounds__(kResidentThreads, 2) k_tail(ResidentArgs a) {
+// kThreads threads, tasks of at most kCap keys; the small size takes tasks
+// of up to kTailSmall keys, the large one the rest (each skips the other's).
+template <class K, int kThreads, int kCap>
+__global__ void __launch_bounds__(kThreads, kCap == kResidentMax ? 2 : 4) k_tail(ResidentArgs a) {
   using T = KT<K>;
   using Bits = typename T::Bits;
   using Ord = typename T::Ord;
+  constexpr int kW = kThreads / 32;     // warps
+  constexpr int kPT = kCap / kThreads;  // keys per thread
   constexpr Ord kSpan = (Ord)1 << (sizeof(Ord) * 8 - kPosBits);
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  TailSmem<K>& sh = *reinterpret_cast<TailSmem<K>*>(smem_raw);
+  TailSmem<K, kCap, kW>& sh = *reinterpret_cast<TailSmem<K, kCap, kW>*>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const Group g = a.groups[blockIdx.x];
+  if (kCap < kResidentMax ? g.n > kCap : g.n <= kTailSmall) return;
   const int n = g.n;
   const Bits* src = reinterpret_cast<const Bits*>(a.buf[g.buf]) + g.off;
   Bits* dst = reinterpret_cast<Bits*>(a.buf[0]) + g.off;
@@ -544,12 +556,12 @@ __global__ void __launch_bounds__(kResidentThreads, 2) k_tail(ResidentArgs a) {
     if (!slow) {
       Classifier<K> cls;
       cls.load(gm.l, a.exact_only);
-      const int chunk = ((n + kRW * 32 - 1) / (kRW * 32)) * 32;
+      const int chunk = ((n + kW * 32 - 1) / (kW * 32)) * 32;
       const int steps = chunk / 32;
-      Bits v[kRKPT];
-      unsigned int br[kRKPT];
+      Bits v[kPT];
+      unsigned int br[kPT];
 #pragma unroll
-      for (int j = 0; j < kRKPT; ++j) {
+      for (int j = 0; j < kPT; ++j) {
         const int i = warp * chunk + j * 32 + lane;
         v[j] = (j < steps && i < n) ? src[i] : Bits(0);
       }
@@ -558,7 +570,7 @@ __global__ void __launch_bounds__(kResidentThreads, 2) k_tail(ResidentArgs a) {
       unsigned dmask = 0;
       Ord klo = ~(Ord)0, khi = 0;
 #pragma unroll
-      for (int j = 0; j < kRKPT; ++j) {
+      for (int j = 0; j < kPT; ++j) {
         if (j < steps) {
           const int i = warp * chunk + j * 32 + lane;
           int bk = kMaxK;
@@ -586,9 +598,9 @@ __global__ void __launch_bounds__(kResidentThreads, 2) k_tail(ResidentArgs a) {
       if (__any_sync(0xffffffffu, dmask != 0)) {
         // queue them (in the key area, free until the tile is placed) and
         // evaluate 32 at a time
-        static_assert(kRW * kRKPT * 32 * 3 <= (int)sizeof(sh.keys), "deferred queue must fit in the key area");
-        unsigned short* xq = reinterpret_cast<unsigned short*>(sh.keys) + warp * kRKPT * 32;
-        unsigned char* xr = reinterpret_cast<unsigned char*>(sh.keys) + kRW * kRKPT * 32 * 2 + warp * kRKPT * 32;
+        static_assert(kW * kPT * 32 * 3 <= (int)sizeof(sh.keys), "deferred queue must fit in the key area");
+        unsigned short* xq = reinterpret_cast<unsigned short*>(sh.keys) + warp * kPT * 32;
+        unsigned char* xr = reinterpret_cast<unsigned char*>(sh.keys) + kW * kPT * 32 * 2 + warp * kPT * 32;
         int nq = 0;
         for (int j = 0; j < steps; ++j) {
           const bool d = (dmask >> j) & 1u;
@@ -603,12 +615,12 @@ __global__ void __launch_bounds__(kResidentThreads, 2) k_tail(ResidentArgs a) {
         }
         __syncwarp();
 #pragma unroll
-        for (int j = 0; j < kRKPT; ++j)
+        for (int j = 0; j < kPT; ++j)
           if (j < steps && ((dmask >> j) & 1u)) br[j] = xr[j * 32 + lane];
         __syncwarp();
       }
 #pragma unroll
-      for (int j = 0; j < kRKPT; ++j) {
+      for (int j = 0; j < kPT; ++j) {
         if (j < steps) {
           const int bk = (int)br[j];
           // the lanes of this step with the same bucket: one shared OR each
@@ -633,7 +645,7 @@ __global__ void __launch_bounds__(kResidentThreads, 2) k_tail(ResidentArgs a) {
         const int b = threadIdx.x;
         int run = 0;
 #pragma unroll
-        for (int w = 0; w < kRW; ++w) {
+        for (int w = 0; w < kW; ++w) {
           const int x = sh.wcnt[w][b];
           sh.wcnt[w][b] = (unsigned short)run;
           run += x;
@@ -643,10 +655,11 @@ __global__ void __launch_bounds__(kResidentThreads, 2) k_tail(ResidentArgs a) {
         // splitter tree itself always progresses or leaves one equality run)
         if (run == n && !split_tree) sh.slow_all = 1;
         if (run > a.cutoff && b < sh.tm.l.nb && !(split_tree && (b & 1))) sh.any_big = 1;
-      } else if (threadIdx.x == kMaxK) {
+      }
+      if (threadIdx.x == 0) {  // the task's key range (after bucket 0's sum)
         Ord lo = ~(Ord)0, hi = 0;
 #pragma unroll
-        for (int w = 0; w < kRW; ++w) {
+        for (int w = 0; w < kW; ++w) {
           lo = sh.wlo[w] < lo ? sh.wlo[w] : lo;
           hi = sh.whi[w] > hi ? sh.whi[w] : hi;
         }
@@ -680,7 +693,7 @@ __global__ void __launch_bounds__(kResidentThreads, 2) k_tail(ResidentArgs a) {
         const bool tpk = sh.tpk != 0;
         const Ord tlo = sh.tlo;
 #pragma unroll
-        for (int j = 0; j < kRKPT; ++j) {
+        for (int j = 0; j < kPT; ++j) {
           if (j < steps) {
             const int bk = (int)(br[j] >> 16);
             if (bk < kMaxK) {
@@ -743,7 +756,7 @@ __global__ void __launch_bounds__(kResidentThreads, 2) k_tail(ResidentArgs a) {
     const int64_t b0 = g.bounds[0];
     for (int q = threadIdx.x; q <= g.nchild; q += blockDim.x) sh.segb[q] = (int)(g.bounds[q] - b0);
     __syncthreads();
-    for (int q = warp; q < g.nchild; q += kRW)
+    for (int q = warp; q < g.nchild; q += kW)
       for (int i = sh.segb[q] + lane; i < sh.segb[q + 1]; i += 32) sh.seg[i] = (unsigned char)q;
     nseg = g.nchild;
   }
@@ -847,13 +860,23 @@ cudaError_t launch_tail_fit(const ResidentArgs& a, cudaStream_t s, int sms) {
   });
 }
 
-cudaError_t launch_resident(const ResidentArgs& a, cudaStream_t s) {
+cudaError_t launch_resident(const ResidentArgs& a, cudaStream_t s, int large) {
   if (a.ngroups <= 0) return cudaSuccess;
   return by_dtype_r(a.dtype, [&](auto* tag) {
     using K = std::remove_pointer_t<decltype(tag)>;
-    const size_t smem = sizeof(TailSmem<K>);
-    cudaFuncSetAttribute(k_tail<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_tail<K><<<a.ngroups, kResidentThreads, smem, s>>>(a);
+    // tasks of up to kTailSmall keys in the small blocks, the rest in the
+    // large ones (every block of the other size returns at once)
+    if (!large) {
+      const size_t ss = sizeof(TailSmem<K, kTailSmall, kRW / 2>);
+      cudaFuncSetAttribute(k_tail<K, kResidentThreads / 2, kTailSmall>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
+      k_tail<K, kResidentThreads / 2, kTailSmall><<<a.ngroups, kResidentThreads / 2, ss, s>>>(a);
+      return cudaGetLastError();
+    }
+    const size_t sl = sizeof(TailSmem<K, kResidentMax, kRW>);
+    cudaFuncSetAttribute(k_tail<K, kResidentThreads, kResidentMax>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sl);
+    k_tail<K, kResidentThreads, kResidentMax><<<a.ngroups, kResidentThreads, sl, s>>>(a);
     return cudaGetLastError();
   });
 }
