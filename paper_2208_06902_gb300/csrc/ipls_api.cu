@@ -246,8 +246,10 @@ iplsStatus tail_sweep(iplsCtx c, ResidentArgs& ra) {
     ra.split_pool_slots = (int32_t)std::min<int64_t>(c->split_pool_cap / 128, kSplitPoolMax);
     IPLS_CUDA(timed(c, kkTailFit, [&] { return launch_tail_fit(ra, c->stream, c->num_sms); }));
   }
-  IPLS_CUDA(timed(c, kkResident, [&] { return launch_resident(ra, c->stream, 0); }));
-  IPLS_CUDA(timed(c, kkResident, [&] { return launch_resident(ra, c->stream, 1); }));
+  if (ra.ngroups > 0)
+    IPLS_CUDA(timed(c, kkResident, [&] { return launch_resident(ra, c->stream, 0); }));
+  if ((ra.large_from_end ? ra.nlarge : ra.ngroups) > 0)
+    IPLS_CUDA(timed(c, kkResident, [&] { return launch_resident(ra, c->stream, 1); }));
   return IPLS_OK;
 }
 
@@ -255,9 +257,17 @@ iplsStatus tail_sweep(iplsCtx c, ResidentArgs& ra) {
 // them, a second one over the children above the cutoff when the first
 // queued many (in place in the user buffer; the slot's group list is free
 // again once the first sweep ran), and k_slow for the rest.
-iplsStatus launch_tail(iplsCtx c, ResidentArgs& ra, Slot& s, int32_t ngroups, int32_t nfit) {
+// nsmall/nlarge: from a level's list (small tasks from the front, large ones
+// from the back); with nlarge < 0 the nsmall groups are in plain order and
+// both k_tail sizes walk them all.
+iplsStatus launch_tail(iplsCtx c, ResidentArgs& ra, Slot& s, int32_t nsmall, int32_t nlarge, int32_t nfit) {
+  const bool from_end = nlarge >= 0;
+  const int32_t ngroups = from_end ? nsmall + nlarge : nsmall;
   ra.groups = s.groups;
-  ra.ngroups = ngroups;
+  ra.ngroups = nsmall;
+  ra.nlarge = from_end ? nlarge : nsmall;
+  ra.group_cap = (int32_t)std::min<int64_t>(s.group_cap, INT32_MAX);
+  ra.large_from_end = from_end ? 1 : 0;
   ra.fit_list = s.fit_list;
   ra.nfit = nfit;
   ra.tail_models = s.tails;
@@ -286,6 +296,8 @@ iplsStatus launch_tail(iplsCtx c, ResidentArgs& ra, Slot& s, int32_t ngroups, in
       IPLS_CUDA(cudaMemsetAsync(c->slow_ctl, 0, 4 * sizeof(int32_t), c->stream));
       ra.groups = s.groups;
       ra.ngroups = nc;
+      ra.nlarge = nc;            // plain order: both sizes walk the list
+      ra.large_from_end = 0;
       ra.fit_list = s.fit_list;
       ra.nfit = nc;
       ra.tail_models = s.tails;
@@ -382,7 +394,9 @@ iplsStatus sort_impl(iplsCtx c, void* keys, int64_t n, int dtype, const int64_t*
     IPLS_CUDA(cudaStreamSynchronize(c->stream));
     if (c->h_ctl->overflow) return fail(IPLS_ERR_INTERNAL, "segment list capacity exceeded");
     resolve_events(c);
-    IPLS_TRY(launch_tail(c, ra, s1, c->h_ctl->ngroups, c->h_ctl->nfit));
+    if ((int64_t)c->h_ctl->ngroups + c->h_ctl->ngroups_large > s1.group_cap)
+      return fail(IPLS_ERR_INTERNAL, "segment list capacity exceeded");
+    IPLS_TRY(launch_tail(c, ra, s1, c->h_ctl->ngroups, c->h_ctl->ngroups_large, c->h_ctl->nfit));
     nsub = c->h_ctl->nsub_next;
     ntiles = c->h_ctl->tiles_next;
     nchunks = c->h_ctl->chunks_next;
@@ -401,7 +415,7 @@ iplsStatus sort_impl(iplsCtx c, void* keys, int64_t n, int dtype, const int64_t*
       const int32_t zero = 0;
       IPLS_CUDA(cudaMemcpyAsync(s1.fit_list, &zero, sizeof(zero), cudaMemcpyHostToDevice, c->stream));
     }
-    IPLS_TRY(launch_tail(c, ra, s1, 1, fitted));
+    IPLS_TRY(launch_tail(c, ra, s1, 1, -1, fitted));
     IPLS_TRY(check_run(c));
     resolve_events(c);
     c->k_bytes[kkResident] += 2 * (int64_t)w * n;
@@ -484,7 +498,7 @@ iplsStatus sort_impl(iplsCtx c, void* keys, int64_t n, int dtype, const int64_t*
     IPLS_CUDA(cudaMemcpyAsync(c->h_run, c->run, sizeof(RunStatus), cudaMemcpyDeviceToHost, c->stream));
     IPLS_CUDA(cudaStreamSynchronize(c->stream));
     const LevelCtl lc = *c->h_ctl;
-    if (c->h_run->error != 0 || lc.overflow) {
+    if (c->h_run->error != 0 || lc.overflow || (int64_t)lc.ngroups + lc.ngroups_large > X.group_cap) {
       // nothing of this level moved (k_scatter checks the status first):
       // put the level's keys back into the user buffer and stop
       IPLS_CUDA(launch_restore(X.subs, (int32_t)nsub, dtype, keys, c->scratch, c->stream));
@@ -506,7 +520,7 @@ iplsStatus sort_impl(iplsCtx c, void* keys, int64_t n, int dtype, const int64_t*
     moved += lc.keys_moved;
     c->stats.max_bucket_frac = std::max(c->stats.max_bucket_frac, (double)lc.max_bucket / 1048576.0);
     c->trace_grid_count += nsub;
-    IPLS_TRY(launch_tail(c, ra, X, lc.ngroups, lc.nfit));
+    IPLS_TRY(launch_tail(c, ra, X, lc.ngroups, lc.ngroups_large, lc.nfit));
     if (lc.nfill > 0)
       IPLS_CUDA(timed(c, kkFill, [&] { return launch_fill(X.fills, lc.nfill, dtype, keys, c->stream); }));
     nsub = lc.nsub_next;
@@ -582,15 +596,15 @@ __global__ void k_init_segments(const int64_t* off, int64_t nseg, int rmax, int 
     const bool brk = (q == q1) || big || mid;
     const bool fits = (cq > 0) && !brk;
     if (g0 >= 0 && (brk || (fits && tot + cq > rmax))) {
-      const int g = atomicAdd(&ctl->ngroups, 1);
-      if (g >= group_cap) ctl->overflow = 1;
+      const int g = group_slot(ctl, tot, group_cap);
+      if (g < 0) ctl->overflow = 1;
       else groups[g] = Group{off[g0], off + g0, (int32_t)tot, 0, 0, (int32_t)(glast - g0 + 1), -1, 0};
       g0 = -1;
       tot = 0;
     }
     if (mid) {
-      const int g = atomicAdd(&ctl->ngroups, 1);
-      if (g >= group_cap) {
+      const int g = group_slot(ctl, cq, group_cap);
+      if (g < 0) {
         ctl->overflow = 1;
       } else {
         groups[g] = Group{off[q], nullptr, (int32_t)cq, 0, 0, 1, g, 0};

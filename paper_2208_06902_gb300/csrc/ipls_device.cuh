@@ -1063,6 +1063,19 @@ __device__ __forceinline__ int table_bucket(typename KT<K>::Ord u, const ThrTabl
 // kChunkTiles tiles the look-back scan walks, in the next level's tile and
 // chunk spaces; fills the Sub fields.  False (and ctl->overflow) when a
 // capacity is exceeded.
+// Slot of a new block-resident task in the level's group list: tasks of up
+// to kTailSmall keys from the front, larger ones from the back (so each
+// k_tail size launches exactly its own).  -1 when that end is full; the host
+// also checks that the two ends did not meet.
+__device__ __forceinline__ int group_slot(LevelCtl* ctl, int64_t n, int32_t cap) {
+  if (n <= kTailSmall) {
+    const int i = atomicAdd(&ctl->ngroups, 1);
+    return i < cap ? i : -1;
+  }
+  const int j = atomicAdd(&ctl->ngroups_large, 1);
+  return j < cap ? cap - 1 - j : -1;
+}
+
 __device__ __forceinline__ bool reserve_tiles(LevelCtl* ctl, int32_t idx, Sub& sub, int32_t* tile2sub,
                                               int64_t tile_cap, int32_t* chunk2sub,
                                               int64_t chunk_cap) {

@@ -13,6 +13,9 @@ constexpr int kPassThreads = 256; // threads of the grid-pass kernels
 constexpr int kResidentMax = 8192;      // keys of one block-resident group
 constexpr int kResidentThreads = 512;
 constexpr int kResidentSample = 1024;   // sample capacity inside a resident block
+// Block-resident tasks of at most kTailSmall keys run in 256-thread blocks
+// (four per SM), larger ones in 512-thread blocks (two per SM).
+constexpr int kTailSmall = 4096;
 constexpr int kResidentTasks = 2048;    // pending ranges inside a resident block
 constexpr int kFitThreads = 1024;
 constexpr int kFillChunk = 65536;
@@ -140,7 +143,7 @@ struct LevelCtl {
   int32_t nfill;
   int32_t nrehist;
   int32_t nfit;          // tasks needing a tail fit
-  int32_t pad0;
+  int32_t ngroups_large; // tasks of more than kTailSmall keys (listed from the back)
   int64_t tiles_next;
   int64_t chunks_next;
   uint32_t ticket;
@@ -257,7 +260,11 @@ struct ResidentArgs {
   int exact_only;
   void* buf[2];
   const Group* groups;
-  int32_t ngroups;
+  int32_t ngroups;                 // groups[0, ngroups) (the small ones when large_from_end)
+  int32_t nlarge;                  // tasks for the large blocks
+  int32_t group_cap;
+  int32_t large_from_end;          // 1: the large tasks are groups[group_cap-1-i], i < nlarge;
+                                   // 0: both sizes walk groups[0, ngroups) and skip the other's
   const int32_t* fit_list;
   int32_t nfit;
   TailModel* tail_models;          // indexed by Group::fit

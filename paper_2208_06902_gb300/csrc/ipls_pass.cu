@@ -424,8 +424,8 @@ __global__ void __launch_bounds__(256) k_scan(LevelArgs a) {
       }
     } else if (c > a.cutoff) {
       // a block-resident subproblem whose model k_tail_fit fits
-      const int g = atomicAdd(&a.ctl->ngroups, 1);
-      if (g >= a.group_cap) {
+      const int g = group_slot(a.ctl, c, a.group_cap);
+      if (g < 0) {
         a.ctl->overflow = 1;
       } else {
         a.groups[g] = Group{sub.off + bas[b], nullptr, (int32_t)c, sub.level + 1, dst_buf, 1, g, 0};
@@ -444,8 +444,8 @@ __global__ void __launch_bounds__(256) k_scan(LevelArgs a) {
       const bool brk = (q == nb) || (cq > 0 && (eqq || cq > a.cutoff));
       const bool fits = (cq > 0) && !brk;
       if (b0 >= 0 && (brk || (fits && tot + cq > a.rmax))) {
-        const int g = atomicAdd(&a.ctl->ngroups, 1);
-        if (g >= a.group_cap) a.ctl->overflow = 1;
+        const int g = group_slot(a.ctl, tot, a.group_cap);
+        if (g < 0) a.ctl->overflow = 1;
         else a.groups[g] = Group{sub.off + bas[b0], gb + b0, (int32_t)tot, sub.level + 1,
                                  dst_buf, blast - b0 + 1, -1, 0};
         b0 = -1;

@@ -453,10 +453,6 @@ __global__ void __launch_bounds__(kResidentThreads, 2) k_slow(ResidentArgs a) {
 // ---------------------------------------------------------------------------
 // k_tail
 // ---------------------------------------------------------------------------
-// k_tail runs in two sizes: tasks of up to kTailSmall keys in 256-thread
-// blocks (four per SM), larger ones in 512-thread blocks (two per SM).
-constexpr int kTailSmall = 4096;
-
 template <class K, int kCap, int kW>
 struct TailSmem {
   typename KT<K>::Ord keys[kCap];
@@ -517,8 +513,9 @@ __global__ void __launch_bounds__(kThreads, kCap == kResidentMax ? 2 : 4) k_tail
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TailSmem<K, kCap, kW>& sh = *reinterpret_cast<TailSmem<K, kCap, kW>*>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const Group g = a.groups[blockIdx.x];
-  if (kCap < kResidentMax ? g.n > kCap : g.n <= kTailSmall) return;
+  const bool large = kCap == kResidentMax;
+  const Group g = a.groups[large && a.large_from_end ? a.group_cap - 1 - (int)blockIdx.x : (int)blockIdx.x];
+  if (large ? g.n <= kTailSmall : g.n > kCap) return;
   const int n = g.n;
   const Bits* src = reinterpret_cast<const Bits*>(a.buf[g.buf]) + g.off;
   Bits* dst = reinterpret_cast<Bits*>(a.buf[0]) + g.off;
@@ -861,12 +858,12 @@ cudaError_t launch_tail_fit(const ResidentArgs& a, cudaStream_t s, int sms) {
 }
 
 cudaError_t launch_resident(const ResidentArgs& a, cudaStream_t s, int large) {
-  if (a.ngroups <= 0) return cudaSuccess;
   return by_dtype_r(a.dtype, [&](auto* tag) {
     using K = std::remove_pointer_t<decltype(tag)>;
     // tasks of up to kTailSmall keys in the small blocks, the rest in the
     // large ones (every block of the other size returns at once)
     if (!large) {
+      if (a.ngroups <= 0) return cudaSuccess;
       const size_t ss = sizeof(TailSmem<K, kTailSmall, kRW / 2>);
       cudaFuncSetAttribute(k_tail<K, kResidentThreads / 2, kTailSmall>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
@@ -876,7 +873,9 @@ cudaError_t launch_resident(const ResidentArgs& a, cudaStream_t s, int large) {
     const size_t sl = sizeof(TailSmem<K, kResidentMax, kRW>);
     cudaFuncSetAttribute(k_tail<K, kResidentThreads, kResidentMax>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sl);
-    k_tail<K, kResidentThreads, kResidentMax><<<a.ngroups, kResidentThreads, sl, s>>>(a);
+    const int nl = a.large_from_end ? a.nlarge : a.ngroups;
+    if (nl <= 0) return cudaSuccess;
+    k_tail<K, kResidentThreads, kResidentMax><<<nl, kResidentThreads, sl, s>>>(a);
     return cudaGetLastError();
   });
 }
