@@ -3,11 +3,14 @@
 //  * key traits: IEEE totalOrder keys ("ord"), binary64 values, exact
 //    differences, fixed-point images of keys;
 //  * SplitMix64 counter-based sampling (Steele, Lea and Flood 2014);
-//  * a block-wide sorting network for samples and small runs;
+//  * a block-wide sorting network for samples and small runs, and a warp
+//    LSD radix sort for the samples of block-resident tasks;
 //  * the FMCD fit (Ch.3 "Linear Models", its listing) as a binary search over
 //    the conflict-degree parameter D with a certified integer filter;
 //  * classification by the clamped linear model (Ch.3 model equation) or by
-//    the splitter tree with equality buckets (Ch.3 "Decision Trees").
+//    the splitter tree with equality buckets (Ch.3 "Decision Trees");
+//  * the PL2 learned CDF (training and classification);
+//  * the slots of block-resident tasks in a level's group list.
 #pragma once
 
 #include <cfloat>

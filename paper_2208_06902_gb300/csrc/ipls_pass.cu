@@ -1,7 +1,8 @@
 // Grid-wide learned partition pass over all subproblems of one level.
 //
 //   k_fit      sample alpha*k-1 keys, sort them, fit FMCD (Ch.3 listing) or
-//              the splitter tree, zero counts: one warp per subproblem
+//              the splitter tree -- or, when enabled, train the PL2 learned
+//              CDF -- and zero the counts: one warp per subproblem
 //              (k_fit_warp) when the sample fits, else one block.
 //   k_hist     every tile of every subproblem: classify each key with the
 //              model (Ch.3 model equation) and store its bucket id, per-warp
@@ -9,16 +10,18 @@
 //              subproblem's totals are accumulated with one atomic per
 //              bucket per block.
 //   k_check    no-progress rule: a linear pass that puts every key into one
-//              bucket is redone with the splitter tree from the same sample.
+//              bucket (or a PL2 pass with a bucket above 4n/k) is redone with
+//              the splitter tree from the same sample.
 //   k_scan     exclusive scan of the bucket counts -> bucket bases; children
-//              become next-level subproblems, block-resident groups, or
-//              (equality buckets) fills; records the trace.
+//              become next-level subproblems, block-resident groups (tasks of
+//              up to kTailSmall keys from the front of the list, larger ones
+//              from the back), or (equality buckets) fills; records the trace.
 //   k_tilescan exclusive scan of the tile histograms of every subproblem,
 //              per bucket, over its tiles: chunks of kChunkTiles tiles in
 //              ticket order, each chunk's prefix found by decoupled look-back
 //              over the chunks before it.
 //   k_scatter  every tile: read the keys and the bucket ids k_hist stored,
-//              rank each key stably inside the tile (warp ballots +
+//              rank each key stably inside the tile (per-bucket peer masks +
 //              per-warp counters), stage the tile in bucket order in shared
 //              memory and write the bucket runs out with coalesced stores at
 //              bucket base + tile offset (Ch.2 IPS4o: move every key into the

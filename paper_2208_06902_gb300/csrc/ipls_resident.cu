@@ -2,11 +2,13 @@
 // independent buckets; Ch.4 IPLS), for subproblems of at most kResidentMax
 // keys.
 //
-//   k_tail_fit   one warp per subproblem: sample alpha*k-1 keys, sort them
-//                (warp radix sort on the few digits the sample's range needs),
-//                fit FMCD -- many fits in flight per SM hide the latency of
-//                the sort and of the binary64 steps.
-//   k_tail       one block per task.  A fitted subproblem is read from HBM
+//   k_tail_fit   persistent warps, one subproblem at a time: sample
+//                alpha*k-1 keys, sort them (warp radix sort on the digits the
+//                sample's keys set), fit FMCD -- many fits in flight per SM
+//                hide the latency of the sort and of the binary64 steps.
+//   k_tail       one block per task, in two sizes: 256 threads (four blocks
+//                per SM) for tasks of up to kTailSmall keys, 512 threads for
+//                larger ones.  A fitted subproblem is read from HBM
 //                once, classified with its model, ranked stably per bucket
 //                and placed into shared memory in bucket order; each bucket
 //                of at most `cutoff` keys is then base-cased by rank counting
