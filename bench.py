@@ -59,7 +59,7 @@ def parse():
     p.add_argument("--profile-stats", metavar="JSON",
                    help="profiling run: sort W+K arrays, write the per-kernel launches and "
                         "algorithmic bytes of ALL of them to JSON, print no bench line")
-    p.add_argument("--workload", default="single", choices=["single", "segmented", "serve"],
+    p.add_argument("--workload", default="single", choices=["single", "segmented", "serve", "integers"],
                    help="single: the 2^28 arrays (headline); segmented: a batch of "
                         "200,000 uneven segments in one call vs one call per segment; "
                         "serve: Poisson-arriving requests, batched vs one at a time")
@@ -647,6 +647,93 @@ def run_serve(args):
     return 0 if same else 1
 
 
+def _sorted_on_device(t, code) -> bool:
+    """Non-decreasing in totalOrder, checked on the device."""
+    import torch
+    if code == 2:    # u64: flip the top bit, compare as int64
+        k = t.view(torch.int64) ^ torch.iinfo(torch.int64).min
+    elif code == 3:  # u32
+        k = t.view(torch.int32).to(torch.int64) & 0xFFFFFFFF
+    else:            # f32 bits to a signed key in totalOrder
+        b = t.view(torch.int32).to(torch.int64)
+        k = b ^ ((b >> 31) & 0x7FFFFFFF)
+    return bool((k[1:] >= k[:-1]).all())
+
+
+def run_integers(args):
+    """The integer and f32 workloads at full size: 2^30 u64 raw 64-bit draws,
+    2^30 u32 Zipf(1.0) over 1..2^24 and 2^29 f32 Normal(0,1).  Per array:
+    Gkeys/s, grid levels and passes, and each kernel's GB/s (its algorithmic
+    bytes / its time) against the measured copy bandwidth.  The output is
+    checked to be sorted on the device."""
+    import numpy as np
+    import torch
+
+    import datagen
+    torch.cuda.set_device(0)
+    import paper_2208_06902_gb300 as ipls
+    ipls.load()
+    dev = torch.device("cuda", 0)
+    peak, peak_src = measured_peaks()
+    stream = torch.cuda.current_stream()
+    ctx = ipls.Context(k=256, cutoff=args.cutoff, stream=stream, profile=True)
+    arrays = {}
+    total_keys, total_ms, ok = 0, 0.0, True
+    for kind, code in (("u64", ipls.U64), ("u32", ipls.U32), ("f32", ipls.F32)):
+        x = datagen.config3(kind)
+        n = int(x.size)
+        src = torch.from_numpy(x.view(np.uint8)).to(dev)
+        del x
+        work = torch.empty_like(src)
+
+        def step():
+            work.copy_(src)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ctx.sort_ptr(work.data_ptr(), n, code)
+            b.record(stream)
+            torch.cuda.synchronize()
+            return a.elapsed_time(b)
+
+        for _ in range(args.warmup):
+            step()
+        ctx.kernel_stats(reset=True)
+        ts = [step() for _ in range(args.steps)]
+        ks = ctx.kernel_stats(reset=True)
+        st = ctx.stats()
+        good = _sorted_on_device(work, code)
+        ok = ok and good
+        kern = {}
+        for k in ks:
+            if not k["launches"]:
+                continue
+            gbs = (k["bytes"] / (k["total_ms"] * 1e-3) / 1e9) if k["bytes"] and k["total_ms"] > 0 else None
+            kern[k["name"]] = {"ms_per_sort": round(k["total_ms"] / args.steps, 3),
+                               "GB/s": round(gbs, 1) if gbs else None,
+                               "frac": round(gbs / peak, 3) if gbs else None}
+        ms = statistics.median(ts)
+        arrays[kind] = {"n": n, "gkeys_s": round(n / (ms * 1e-3) / 1e9, 3), "ms": round(ms, 3),
+                        "grid_levels": int(st.grid_levels), "grid_passes": int(st.grid_passes),
+                        "splitter_passes": int(st.fallback_passes), "sorted": good,
+                        "kernels": kern}
+        total_keys += n * args.steps
+        total_ms += sum(ts)
+        del src, work
+        torch.cuda.empty_cache()
+    line = {"metric": "Gkeys/s, integer and f32 workloads (2^30 u64, 2^30 u32 Zipf, 2^29 f32)",
+            "value": round(total_keys / (total_ms * 1e-3) / 1e9, 4), "unit": "Gkeys/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(total_ms / (3 * args.steps), 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64/u32/f32", "data": "synthetic",
+            "config": {"workload": "2^30 u64 uniform, 2^30 u32 Zipf(1.0) over 1..2^24, 2^29 f32 Normal",
+                       "k": 256, "cutoff": args.cutoff},
+            "peak_gbs": peak, "peak_source": peak_src, "arrays": arrays}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0 if ok else 1
+
+
 def main():
     args = parse()
     if args.ingest_ncu:
@@ -657,6 +744,8 @@ def main():
         return run_segmented(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "integers":
+        return run_integers(args)
     return run_gb300(args)
 
 
