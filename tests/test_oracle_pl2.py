@@ -129,3 +129,29 @@ def test_pl2_balances_a_skewed_root_better_than_fmcd(dist):
     max_f = max(root_f.counts[: root_f.model.nbuckets])
     max_p = max(root_p.counts[: root_p.model.nbuckets])
     assert max_p * 2 < max_f, (max_p, max_f)
+
+
+@pytest.mark.parametrize("M", [64, 1024])
+@pytest.mark.parametrize("dist", ["uniform", "normal", "lognormal", "exponential"])
+def test_last_half_sweep_leaves_even_knots_at_their_coordinate_minimum(dist, M):
+    # each step ends with the even knots, each moved to the exact minimiser of
+    # the loss along its own coordinate within [y_{j-1}, y_{j+1}]; so moving
+    # one of them by a quarter of its smaller gap, either way, cannot lower
+    # the loss (evaluated independently, in binary64).  Gaps below 1e-5 are
+    # skipped: there the move is close to the binary32 rounding of the knot.
+    x = _sample(dist, S=4000)
+    m, _ = oracle.pl2_fit(x, M, 256)
+    y = oracle.pl2_knots(m).astype(np.float64)
+    L0, _ = oracle.pl2_loss_grad(x, m, y)
+    checked = 0
+    for j in range(2, M - 1, 2):
+        gap = min(y[j] - y[j - 1], y[j + 1] - y[j])
+        if gap < 1e-5:
+            continue
+        for d in (0.25 * gap, -0.25 * gap):
+            z = y.copy()
+            z[j] += d
+            L, _ = oracle.pl2_loss_grad(x, m, z)
+            assert L >= L0 * (1 - 1e-12), (j, d, L, L0)
+        checked += 1
+    assert checked >= M // 8
