@@ -109,7 +109,7 @@ typedef struct iplsTraceRec {
   int64_t off;            /* first key of the subproblem in the whole array */
   int64_t n;              /* keys in the subproblem */
   int32_t level;          /* recursion level (0 = whole array or segment) */
-  int32_t kind;           /* 0 = FMCD linear model, 1 = splitter tree */
+  int32_t kind;           /* 0 = FMCD linear model, 1 = splitter tree, 2 = PL2 */
   int32_t capped;         /* FMCD stopped at its 3D > N break */
   int32_t nbuckets;       /* k, or 2*nsplit+1 for the splitter tree */
   int64_t S;              /* sample size */
@@ -224,23 +224,54 @@ iplsStatus iplsGetTrace(iplsCtx ctx, iplsTraceRec* out, int64_t cap, int64_t* co
  * must not fail for lack of memory half-way).
  *   - n <= 8192 (resident_rmax: 8192 for cfg->cutoff >= 7, 1024*(cutoff+1)
  *     below); a larger n returns IPLS_ERR_ARG with a message naming the
- *     limit.  One block runs the whole IPLS recursion (Ch.2 IPS4o recursion,
- *     Ch.3 FMCD model, Ch.4 parameters) in shared memory; the result equals
- *     iplsSort's on the same keys.
+ *     limit, before any CUDA call.  One block sorts the keys; the result
+ *     equals iplsSort's on the same keys and configuration.
  *   - cfg NULL = iplsDefaultConfig; k, cutoff, root_sample (<= 1024), seed
  *     and exact_only are used.  stream = cudaStream_t (NULL = legacy
- *     default stream).  The call waits for its stream and returns the
- *     device status.
+ *     default stream).
+ *   - The call synchronises its stream (it copies the device status back
+ *     and waits for it), so it cannot be made while that stream is being
+ *     captured into a CUDA graph.
  *   - Its only device scratch is a 256-byte status block in a file-scope
  *     __device__ array of the library, cleared on the stream at the start
  *     of every call.  The first call on each device looks up that array's
- *     address (cudaGetSymbolAddress, with the device current); make it
- *     before capturing the stream into a graph.
+ *     address (cudaGetSymbolAddress, with the device current).
  *   - The status block is shared by every call on a device: calls that
  *     overlap in time (other threads or streams) race on it and must be
  *     serialised by the caller. */
 iplsStatus iplsSortSmallNoAlloc(void* keys, int64_t n, iplsDtype dtype, const iplsConfig* cfg,
                                 void* stream);
+
+/* Copies the PL2 knot values of the grid-level pass records of the last sort
+ * (the records iplsGetTrace lists first, in the same order) to host memory:
+ * (cfg.pl2_leaves + 1) binary32 values y_0..y_M per record, zeros for a pass
+ * whose model is not PL2.  Requires cfg.trace_cap > 0 and cfg.pl2_leaves > 0
+ * (otherwise *count = 0); knots are kept for at most the first 16384 grid
+ * records.  out holds cap records; *count is set to the records written.
+ * (PL2: Ch.2 "Learned Sort" and Ch.3 "Recursive Model Index", a learned
+ * CDF fitted to the sample's empirical CDF.) */
+iplsStatus iplsGetTraceKnots(iplsCtx ctx, float* out, int64_t cap, int64_t* count);
+
+/* The PL2 model's training loss and gradient, computed on the device by the
+ * same forward and backward functions that train PL2 inside the sort (Ch.3:
+ * the mean squared error of a learned CDF against the empirical CDF).
+ *   sample: DEVICE array of S keys of `dtype`, ascending in totalOrder
+ *           (2 <= S <= 4096), the sample the model is fitted on;
+ *   leaves: M, a power of two in [2, 1024];
+ *   knots:  DEVICE array of M + 1 binary32 knot values y_0..y_M;
+ *   out:    DEVICE array of 2(M + 1) + 2 floats, written on `stream`
+ *           (cudaStream_t, NULL = legacy default stream; the call returns
+ *           after enqueueing): out[j] = G_j = sum_i r_i dF(x_i)/dy_j and
+ *           out[M+1+j] = H_j = sum_i (dF(x_i)/dy_j)^2 for j = 0..M, with
+ *           F the model's CDF at sample i and r_i = F(x_i) - (i + 1/2)/S;
+ *           the loss gradient is 2 G_j / S.  out[2M+2] = the loss
+ *           (1/S) sum r_i^2 and out[2M+3] = 1, or all zeros when the
+ *           sample's range cannot carry PL2 (equal or non-finite extremes).
+ * Binary32 throughout, sums over each leaf in sample order.  Allocates
+ * nothing.  IPLS_ERR_ARG for an out-of-range S, leaves or dtype, or a NULL
+ * pointer; IPLS_ERR_CUDA if the launch fails. */
+iplsStatus iplsPL2LossGrad(const void* sample, int64_t S, iplsDtype dtype, int32_t leaves,
+                           const float* knots, float* out, void* stream);
 
 /* Message of the last failure on this thread ("" if none). */
 const char* iplsLastError(void);

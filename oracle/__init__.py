@@ -14,9 +14,10 @@ Parity status of each function (what pins it, in ``tests/test_oracle_pins.py``):
                                  all permutations (n <= 7), multiset hash.
   * ``classify``              -- the worked example of Ch.4 (golden file),
                                  monotonicity property, NaN/inf/-0 cases.
-  * ``fmcd``                  -- brute-force smallest-D search from the
-                                 definition, closed form on arithmetic
-                                 progressions, conflict-degree bound.
+  * ``fmcd``                  -- written from the definition; the one-walk
+                                 O(S) search gives the same D, closed form on
+                                 arithmetic progressions, conflict-degree
+                                 bound.
   * ``partition_pass``        -- histogram sums, permutation, bucket ordering,
                                  the splitter fallback's progress guarantee.
   * ``sample_indices``        -- parity unpinned by the paper (it names no
@@ -101,8 +102,8 @@ def lib():
         L.oracle_sample_size.argtypes = [c.c_int64, c.c_int32, c.c_int32, c.c_int64]
         L.oracle_total_order.argtypes = [c.c_int, c.c_void_p, c.c_int64, c.c_void_p]
         L.oracle_fmcd.argtypes = [c.c_int, c.c_void_p, c.c_int64, c.c_int32, c.POINTER(Model)]
-        L.oracle_fmcd_bruteforce.argtypes = [c.c_int, c.c_void_p, c.c_int64, c.c_int32,
-                                             c.POINTER(Model)]
+        L.oracle_fmcd_incremental.argtypes = [c.c_int, c.c_void_p, c.c_int64, c.c_int32,
+                                              c.POINTER(Model)]
         L.oracle_classify.argtypes = [c.c_int, c.c_void_p, c.c_int64, c.POINTER(Model),
                                       c.c_void_p]
         L.oracle_partition_with_model.argtypes = [c.c_int, c.c_void_p, c.c_int64,
@@ -122,7 +123,13 @@ def lib():
         L.oracle_pl2_classify.argtypes = [c.c_int, c.c_void_p, c.c_int64, c.POINTER(Model),
                                           c.c_void_p, c.c_void_p]
         L.oracle_pl2_loss_grad.argtypes = [c.c_int, c.c_void_p, c.c_int64, c.POINTER(Model),
-                                           c.c_void_p, c.POINTER(c.c_double), c.c_void_p]
+                                           c.c_void_p, c.POINTER(c.c_double), c.c_void_p,
+                                           c.c_void_p]
+        L.oracle_pl2_fit_f64.argtypes = [c.c_int, c.c_void_p, c.c_int64, c.c_int32, c.c_int32,
+                                         c.POINTER(Model), c.c_void_p, c.c_void_p]
+        L.oracle_sort_knots.argtypes = [c.c_int, c.c_void_p, c.c_int64, c.POINTER(Cfg),
+                                        c.c_void_p, c.c_int64, c.POINTER(c.c_int64),
+                                        c.POINTER(c.c_int32), c.c_void_p]
         L.oracle_multiset_hash.restype = None
         L.oracle_multiset_hash.argtypes = [c.c_int, c.c_void_p, c.c_int64,
                                            c.POINTER(c.c_uint64), c.POINTER(c.c_uint64)]
@@ -172,7 +179,8 @@ def total_order(keys: np.ndarray) -> np.ndarray:
 
 
 def fmcd(sorted_sample: np.ndarray, K: int = 256) -> Model:
-    """FMCD, the loop of Listing 1 (Ch.3), binary64."""
+    """FMCD (Ch.3 "Linear Models") from its definition, binary64: the smallest
+    D whose windows of D+1 sample points all span u_d(D)."""
     s = np.ascontiguousarray(sorted_sample)
     m = Model()
     if lib().oracle_fmcd(_code(s), _ptr(s), s.size, K, ctypes.byref(m)) != 0:
@@ -180,11 +188,12 @@ def fmcd(sorted_sample: np.ndarray, K: int = 256) -> Model:
     return m
 
 
-def fmcd_bruteforce(sorted_sample: np.ndarray, K: int = 256) -> Model:
-    """FMCD's result recomputed from its definition (smallest D with P(D))."""
+def fmcd_incremental(sorted_sample: np.ndarray, K: int = 256) -> Model:
+    """FMCD by one walk over the window starts (the O(S) search of Ch.3);
+    must equal fmcd()."""
     s = np.ascontiguousarray(sorted_sample)
     m = Model()
-    if lib().oracle_fmcd_bruteforce(_code(s), _ptr(s), s.size, K, ctypes.byref(m)) != 0:
+    if lib().oracle_fmcd_incremental(_code(s), _ptr(s), s.size, K, ctypes.byref(m)) != 0:
         raise ValueError("FMCD needs N >= 3 and K >= 3")
     return m
 
@@ -237,20 +246,34 @@ def partition_pass(keys: np.ndarray, off: int = 0, level: int = 0, k: int = 256,
     return dst, counts[: m.nbuckets].copy(), m
 
 
+TRACE_DTYPE = np.dtype(Trace)
+
+
 def sort(keys: np.ndarray, k: int = 256, cutoff: int = 32, root_sample: int = 0,
-         seed: int = 0, trace_cap: int = 0, pl2_leaves: int = 0):
+         seed: int = 0, trace_cap: int = 0, pl2_leaves: int = 0, as_array: bool = False,
+         knots: bool = False):
     """Whole IPLS sort (returns a sorted copy, the trace records and the depth).
-    pl2_leaves > 0: subproblems above 8192 keys use the PL2 model."""
+    pl2_leaves > 0: subproblems above 8192 keys use the PL2 model.
+    as_array: the trace as a numpy structured array (TRACE_DTYPE) instead of a
+    list of records (for large traces).  knots: also return the PL2 knots of
+    every record, an array of shape (records, pl2_leaves + 1)."""
     out = np.array(keys, copy=True)
     c = Cfg(k, cutoff, root_sample, seed, pl2_leaves, 0)
-    tr = (Trace * trace_cap)() if trace_cap > 0 else None
+    # np.zeros leaves untouched pages unallocated: a generous cap costs nothing
+    tr = np.zeros(max(trace_cap, 1), TRACE_DTYPE)
+    kn = np.zeros((max(trace_cap, 1), pl2_leaves + 1), np.float32) if knots else None
     cnt = ctypes.c_int64(0)
     lv = ctypes.c_int32(0)
-    rc = lib().oracle_sort(_code(out), _ptr(out), out.size, ctypes.byref(c), tr, trace_cap,
-                           ctypes.byref(cnt), ctypes.byref(lv))
+    rc = lib().oracle_sort_knots(_code(out), _ptr(out), out.size, ctypes.byref(c),
+                                 _ptr(tr) if trace_cap > 0 else None, trace_cap,
+                                 ctypes.byref(cnt), ctypes.byref(lv),
+                                 _ptr(kn) if kn is not None else None)
     if rc != 0:
         raise RuntimeError(f"oracle_sort failed ({rc})")
-    recs = list(tr[: cnt.value]) if tr is not None else []
+    arr = tr[: cnt.value] if trace_cap > 0 else tr[:0]
+    recs = arr if as_array else [Trace.from_buffer_copy(r.tobytes()) for r in arr]
+    if knots:
+        return out, recs, lv.value, kn[: cnt.value]
     return out, recs, lv.value
 
 
@@ -295,15 +318,33 @@ def pl2_knots(m: Model) -> np.ndarray:
     return np.array(m.knots, np.float32)
 
 
-def pl2_loss_grad(sorted_sample: np.ndarray, m: Model, y: np.ndarray):
-    """The PL2 loss and its gradient in the knot values y (for m's leaves)."""
+def pl2_loss_grad(sorted_sample: np.ndarray, m: Model, y: np.ndarray, with_abs: bool = False):
+    """The PL2 loss and its gradient in the knot values y (for m's leaves),
+    binary64.  with_abs: also the per-knot sum of the magnitudes of the
+    gradient's terms."""
     s = np.ascontiguousarray(sorted_sample)
     y = np.ascontiguousarray(y, np.float64)
     loss = ctypes.c_double(0.0)
     grad = np.zeros(y.size, np.float64)
+    absg = np.zeros(y.size, np.float64)
     lib().oracle_pl2_loss_grad(_code(s), _ptr(s), s.size, ctypes.byref(m), _ptr(y),
-                               ctypes.byref(loss), _ptr(grad))
+                               ctypes.byref(loss), _ptr(grad), _ptr(absg))
+    if with_abs:
+        return loss.value, grad, absg
     return loss.value, grad
+
+
+def pl2_fit_f64(sorted_sample: np.ndarray, M: int = 64, K: int = 256):
+    """The PL2 training of pl2_fit carried out in binary64: (model, knots as
+    float64, loss after each step), or None when the range cannot be used."""
+    s = np.ascontiguousarray(sorted_sample)
+    m = Model()
+    losses = np.zeros(PL2_STEPS + 1, np.float64)
+    knots = np.zeros(M + 1, np.float64)
+    if lib().oracle_pl2_fit_f64(_code(s), _ptr(s), s.size, M, K, ctypes.byref(m), _ptr(losses),
+                                _ptr(knots)) != 0:
+        return None
+    return m, knots, losses
 
 
 def std_sort(keys: np.ndarray) -> np.ndarray:

@@ -9,8 +9,9 @@
 // What it computes, and where the paper defines it:
 //   * the partition model F(x) = clamp(floor(a*x + b), 0, k-1)
 //       (Ch.3 "Linear Models", the model equation and the clamping rule);
-//   * FMCD, the Fastest Minimum Conflict Degree fit, literally as the loop of
-//       Listing 1 (Ch.3 "Linear Models"), in binary64;
+//   * FMCD, the Fastest Minimum Conflict Degree fit (Ch.3 "Linear Models"),
+//       from its definition (the smallest conflict-degree parameter D whose
+//       windows all span the bucket width u_d(D)), in binary64;
 //   * the IPLS pass: sample alpha*k-1 random keys with alpha = 0.2 log N and
 //       k = 256, sort the sample, train FMCD, predict the bucket of every key
 //       and move the keys into contiguous bucket regions (Ch.2 IPS4o section,
@@ -23,7 +24,8 @@
 // Readings where the paper is silent or ambiguous (each one is listed, with
 // its reason, in the design notes of the repository):
 //   R1  FMCD arithmetic is binary64, not long double.
-//   R2  The stale u_d at the 3D > N break is kept exactly as the loop has it.
+//   R2  When FMCD stops at 3D > N, the slope keeps the u_d of the D before
+//       the stop (the paper's search leaves before recomputing it).
 //   R3  The model is evaluated in the centred form
 //         b(x) = clamp(floor(fma(A, x (-) x_lo, Bc)), 0, k-1),
 //       x_lo = x[D], Bc = (K - A*(x[N-1-D] (-) x[D])) / 2, which equals
@@ -202,27 +204,40 @@ template <> struct Key<uint64_t> : IntKey<uint64_t> {};
 template <> struct Key<uint32_t> : IntKey<uint32_t> {};
 
 // ---------------------------------------------------------------------------
-// FMCD, the loop of Listing 1 (Ch.3), in binary64 (reading R1).
-// x[0..N) is the sorted sample; K the number of buckets.
+// FMCD (Ch.3 "Linear Models"), in binary64 (reading R1).
+//
+// x[0..N) is the sorted sample and K the number of buckets.  For a conflict
+// degree parameter D the bucket width is u_d(D) = (x[N-1-D] (-) x[D])/(K-2),
+// and D "holds" when every window of D+1 consecutive sample points spans at
+// least u_d(D) (then no bucket of width u_d receives more than D+1 sample
+// points).  FMCD returns the smallest D that holds; it stops looking once
+// 3D > N, and then (reading R2) keeps the u_d of the D before the stop.
+// The slope of the model is A = 1/u_d; the centred intercept is
+// Bc = (K - A*(x[N-1-D] (-) x[D]))/2, and the uncentred intercept of the
+// paper, B = (K - A*(x[N-1-D] + x[D]))/2, is kept for comparison.
 // ---------------------------------------------------------------------------
 template <class T>
-void fmcd_listing(const T* x, int64_t N, int32_t K, OracleModel* m) {
+double fmcd_width(const T* x, int64_t N, int32_t K, int64_t D) {
+  return Key<T>::diff(x[N - 1 - D], x[D]) / (double)(K - 2);
+}
+
+// D holds: every window of D+1 consecutive points spans at least u_d(D).
+template <class T>
+bool fmcd_holds(const T* x, int64_t N, int32_t K, int64_t D) {
+  const double ud = fmcd_width<T>(x, N, K, D);
+  for (int64_t i = 0; i + D < N; ++i)
+    if (!(Key<T>::diff(x[i + D], x[i]) >= ud)) return false;
+  return true;
+}
+
+// The model record for a chosen D (capped: u_d is taken at D-1).
+template <class T>
+void fmcd_model(const T* x, int64_t N, int32_t K, int64_t D, int capped, OracleModel* m) {
   typedef Key<T> KT;
-  const double km2 = (double)(K - 2);
-  int64_t i = 0, D = 1;
-  double ud = KT::diff(x[N - 1 - D], x[D]) / km2;
-  int capped = 0;
-  while (i <= N - 1 - D) {
-    while (i + D < N && KT::diff(x[i + D], x[i]) >= ud) ++i;
-    if (i + D >= N) break;
-    D += 1;
-    if (D * 3 > N) { capped = 1; break; }
-    ud = KT::diff(x[N - 1 - D], x[D]) / km2;
-  }
+  const double ud = fmcd_width<T>(x, N, K, capped ? D - 1 : D);
   const double A = 1.0 / ud;
   const double span = KT::diff(x[N - 1 - D], x[D]);
   const double prod = A * span;
-  const double Bc = ((double)K - prod) / 2.0;
   const double sum = KT::val(x[N - 1 - D]) + KT::val(x[D]);
   const double prod2 = A * sum;
   m->kind = 0;
@@ -231,7 +246,7 @@ void fmcd_listing(const T* x, int64_t N, int32_t K, OracleModel* m) {
   m->D = D;
   m->ud = ud;
   m->A = A;
-  m->Bc = Bc;
+  m->Bc = ((double)K - prod) / 2.0;
   m->B = ((double)K - prod2) / 2.0;
   m->xlo = KT::val(x[D]);
   m->xlo_bits = KT::bits(x[D]);
@@ -239,43 +254,31 @@ void fmcd_listing(const T* x, int64_t N, int32_t K, OracleModel* m) {
   m->nbuckets = K;
 }
 
-// The same result found from the definition rather than the loop: the
-// smallest D >= 1 with 3D <= N such that every window of D+1 consecutive
-// sample points spans at least u_d(D); if no such D exists, the first D with
-// 3D > N, with u_d taken at D-1.  (Equivalence: gap(i,D) grows with D and
-// u_d(D) shrinks with D, so the loop never has to move i backwards.)
+// FMCD from its definition: try D = 1, 2, ... while 3D <= N.
 template <class T>
-void fmcd_bruteforce(const T* x, int64_t N, int32_t K, OracleModel* m) {
-  typedef Key<T> KT;
-  const double km2 = (double)(K - 2);
-  int64_t Dcap = N / 3 + 1;   // smallest D with 3D > N
-  int64_t D = -1;
-  for (int64_t d = 1; d < Dcap; ++d) {
-    double ud = KT::diff(x[N - 1 - d], x[d]) / km2;
-    bool ok = true;
-    for (int64_t i = 0; i + d < N; ++i)
-      if (!(KT::diff(x[i + d], x[i]) >= ud)) { ok = false; break; }
-    if (ok) { D = d; break; }
+void fmcd(const T* x, int64_t N, int32_t K, OracleModel* m) {
+  const int64_t Dstop = N / 3 + 1;  // smallest D with 3D > N
+  for (int64_t D = 1; D < Dstop; ++D)
+    if (fmcd_holds<T>(x, N, K, D)) { fmcd_model<T>(x, N, K, D, 0, m); return; }
+  fmcd_model<T>(x, N, K, Dstop, 1, m);
+}
+
+// The same result by one walk over the window starts, the way the paper's
+// O(S) search finds it: a window that is too narrow for the current D raises
+// D (and u_d) until it is wide enough, and the walk never steps back, since
+// a window's span grows with D while u_d(D) does not (so a window that passed
+// for a smaller D still passes).  Kept only to be checked against fmcd().
+template <class T>
+void fmcd_incremental(const T* x, int64_t N, int32_t K, OracleModel* m) {
+  int64_t D = 1, start = 0;
+  double ud = fmcd_width<T>(x, N, K, D);
+  for (;;) {
+    if (start + D >= N) { fmcd_model<T>(x, N, K, D, 0, m); return; }
+    if (Key<T>::diff(x[start + D], x[start]) >= ud) { ++start; continue; }
+    ++D;
+    if (3 * D > N) { fmcd_model<T>(x, N, K, D, 1, m); return; }
+    ud = fmcd_width<T>(x, N, K, D);
   }
-  int capped = 0;
-  double ud;
-  if (D < 0) {
-    capped = 1;
-    D = Dcap;
-    ud = KT::diff(x[N - 1 - (Dcap - 1)], x[Dcap - 1]) / km2;
-  } else {
-    ud = KT::diff(x[N - 1 - D], x[D]) / km2;
-  }
-  const double A = 1.0 / ud;
-  const double span = KT::diff(x[N - 1 - D], x[D]);
-  const double prod = A * span;
-  m->kind = 0; m->capped = capped; m->S = N; m->D = D; m->ud = ud; m->A = A;
-  m->Bc = ((double)K - prod) / 2.0;
-  const double sum = KT::val(x[N - 1 - D]) + KT::val(x[D]);
-  const double prod2 = A * sum;
-  m->B = ((double)K - prod2) / 2.0;
-  m->xlo = KT::val(x[D]); m->xlo_bits = KT::bits(x[D]);
-  m->nsplit = 0; m->nbuckets = K;
 }
 
 // Model equation of Ch.3 "Linear Models" in the centred form (R3, R4).
@@ -375,20 +378,23 @@ static int bit_length(uint64_t v) {
 }
 
 // Per-sample features of PL2 on the sorted sample: leaf, position in it.
+template <class R>
 struct PL2Feat {
   std::vector<int32_t> leaf;
-  std::vector<float> w;
+  std::vector<R> w;
   std::vector<int64_t> start;  // start[j]: first sample of leaf j; start[M] = S
 };
 
-// Fits PL2 on the sorted sample x[0..S) with M leaves, in binary32 (one
-// rounding per operation, sums in sample order).  Returns false (and leaves
-// m alone) when the sample's range cannot be used: equal or non-finite
-// extremes (the duplicate rule takes over) or a range that does not fit the
-// fixed point (FMCD takes over).
-template <class T>
-bool pl2_fit(const T* x, int64_t S, int32_t M, int32_t K, OracleModel* m, std::vector<float>* knots,
-             PL2Feat* feat_out, std::vector<double>* loss_trace) {
+// Fits PL2 on the sorted sample x[0..S) with M leaves, every operation in
+// the arithmetic type R with one rounding each and every sum in sample order.
+// R = float is the model the sort uses (binary32); R = double is the same
+// training in binary64, kept as a reference for the loss it reaches.
+// Returns false (and leaves m alone) when the sample's range cannot be used:
+// equal or non-finite extremes (the duplicate rule takes over) or a range
+// that does not fit the fixed point (FMCD takes over).
+template <class T, class R>
+bool pl2_train(const T* x, int64_t S, int32_t M, int32_t K, OracleModel* m, std::vector<R>* knots,
+               PL2Feat<R>* feat_out, std::vector<double>* loss_trace) {
   typedef Key<T> KT;
   if (KT::ord(x[0]) == KT::ord(x[S - 1]) || !KT::finite(x[0]) || !KT::finite(x[S - 1])) return false;
   const double range = KT::diff(x[S - 1], x[0]);
@@ -402,17 +408,17 @@ bool pl2_fit(const T* x, int64_t S, int32_t M, int32_t K, OracleModel* m, std::v
   while ((1 << mlog) < M) ++mlog;
   const int64_t umax = X1 - X0;
   const int sh = std::max(0, bit_length((uint64_t)umax) - mlog);
-  PL2Feat f;
+  PL2Feat<R> f;
   f.leaf.resize(S);
   f.w.resize(S);
-  const float inv = std::ldexp(1.0f, -sh);
+  const R inv = std::ldexp((R)1, -sh);
   for (int64_t i = 0; i < S; ++i) {
     bool sat;
     const int64_t U = Fixed<T>::X(x[i], rho, sat) - X0;
     int64_t j = U >> sh;
     if (j > M - 1) j = M - 1;
     f.leaf[i] = (int32_t)j;
-    f.w[i] = (float)(U - (j << sh)) * inv;   // the position the classifier uses
+    f.w[i] = (R)(U - (j << sh)) * inv;   // the position the classifier uses
   }
   // leaf starts: samples are sorted, so leaf j is one index range
   f.start.assign(M + 1, S);
@@ -421,10 +427,10 @@ bool pl2_fit(const T* x, int64_t S, int32_t M, int32_t K, OracleModel* m, std::v
     while (c < S && f.leaf[c] < j) ++c;
     f.start[j] = c;
   }
-  std::vector<float> y(M + 1), tau(S), r(S);
-  for (int64_t i = 0; i < S; ++i) tau[i] = ((float)i + 0.5f) / (float)S;
+  std::vector<R> y(M + 1), tau(S), r(S);
+  for (int64_t i = 0; i < S; ++i) tau[i] = ((R)i + (R)0.5) / (R)S;
   // initial knots: the empirical CDF at the knots
-  for (int32_t j = 0; j <= M; ++j) y[j] = (float)f.start[j] / (float)S;
+  for (int32_t j = 0; j <= M; ++j) y[j] = (R)f.start[j] / (R)S;
   auto loss = [&]() {
     double L = 0.0;
     for (int64_t i = 0; i < S; ++i) L += (double)r[i] * (double)r[i];
@@ -433,10 +439,10 @@ bool pl2_fit(const T* x, int64_t S, int32_t M, int32_t K, OracleModel* m, std::v
   auto forward = [&]() {  // F and the residual of every sample
     for (int64_t i = 0; i < S; ++i) {
       const int32_t a = f.leaf[i];
-      const float t1 = 1.0f - f.w[i];
-      const float p = y[a] * t1;
-      const float q = y[a + 1] * f.w[i];
-      const float F = p + q;
+      const R t1 = (R)1 - f.w[i];
+      const R p = y[a] * t1;
+      const R q = y[a + 1] * f.w[i];
+      const R F = p + q;
       r[i] = F - tau[i];
     }
   };
@@ -456,10 +462,10 @@ bool pl2_fit(const T* x, int64_t S, int32_t M, int32_t K, OracleModel* m, std::v
     for (int parity = 1; parity >= 0; --parity) {
       forward();
       for (int32_t j = parity; j <= M; j += 2) {
-        float g = 0.0f, h = 0.0f;
+        R g = 0, h = 0;
         if (j < M)
           for (int64_t i = f.start[j]; i < f.start[j + 1]; ++i) {
-            const float t1 = 1.0f - f.w[i];
+            const R t1 = (R)1 - f.w[i];
             g = g + r[i] * t1;
             h = h + t1 * t1;
           }
@@ -468,8 +474,8 @@ bool pl2_fit(const T* x, int64_t S, int32_t M, int32_t K, OracleModel* m, std::v
             g = g + r[i] * f.w[i];
             h = h + f.w[i] * f.w[i];
           }
-        if (h > 0.0f) {
-          const float lo = j > 0 ? y[j - 1] : 0.0f, hi = j < M ? y[j + 1] : 1.0f;
+        if (h > (R)0) {
+          const R lo = j > 0 ? y[j - 1] : (R)0, hi = j < M ? y[j + 1] : (R)1;
           y[j] = std::min(std::max(y[j] - g / h, lo), hi);
         }
       }
@@ -487,6 +493,13 @@ bool pl2_fit(const T* x, int64_t S, int32_t M, int32_t K, OracleModel* m, std::v
   *knots = y;
   if (feat_out) *feat_out = f;
   return true;
+}
+
+// The model's training: binary32 (the sort's PL2 model).
+template <class T>
+bool pl2_fit(const T* x, int64_t S, int32_t M, int32_t K, OracleModel* m, std::vector<float>* knots,
+             std::vector<double>* loss_trace) {
+  return pl2_train<T, float>(x, S, M, K, m, knots, nullptr, loss_trace);
 }
 
 // Bucket of key x under a PL2 model: floor(k F(x)) in binary32, clamped to
@@ -533,7 +546,7 @@ int32_t bucket_of(T x, const OracleModel& m, T xlo, const float* knots = nullptr
 template <class T>
 void partition_pass(const T* src, int64_t n, int64_t off, int32_t level,
                     const OracleCfg& cfg, T* dst, int64_t* counts,
-                    OracleModel* m) {
+                    OracleModel* m, std::vector<float>* knots_out = nullptr) {
   typedef Key<T> KT;
   const int64_t S = sample_size(n, level, cfg);
   std::vector<int64_t> idx(S);
@@ -553,7 +566,7 @@ void partition_pass(const T* src, int64_t n, int64_t off, int32_t level,
   // splitter tree on no progress or when a bucket holds more than 4n/k keys
   std::vector<float> knots;
   if (usable && cfg.pl2_leaves > 0 && n > kPL2MinKeys && S <= kPL2MaxSample &&
-      pl2_fit<T>(samp.data(), S, cfg.pl2_leaves, cfg.k, m, &knots, nullptr, nullptr)) {
+      pl2_fit<T>(samp.data(), S, cfg.pl2_leaves, cfg.k, m, &knots, nullptr)) {
     linear = false;
     std::fill(counts, counts + m->nbuckets, 0);
     for (int64_t i = 0; i < n; ++i) counts[b[i] = pl2_bucket<T>(src[i], *m, knots.data())]++;
@@ -564,10 +577,11 @@ void partition_pass(const T* src, int64_t n, int64_t off, int32_t level,
       std::vector<int64_t> base(m->nbuckets + 1, 0);
       for (int32_t j = 0; j < m->nbuckets; ++j) base[j + 1] = base[j] + counts[j];
       for (int64_t i = 0; i < n; ++i) dst[base[b[i]]++] = src[i];
+      if (knots_out) *knots_out = knots;
       return;
     }
   } else if (linear) {
-    fmcd_listing<T>(samp.data(), S, cfg.k, m);
+    fmcd<T>(samp.data(), S, cfg.k, m);
     const bool ok = std::isfinite(m->ud) && m->ud > 0.0 &&
                     std::isfinite(m->A) && std::isfinite(m->Bc);
     if (ok) xlo = samp[m->D]; else linear = false;
@@ -613,9 +627,12 @@ struct Sub { int64_t off, n; };
 // become level L+1 subproblems (Ch.2 IPS4o recursion; Ch.4).
 // `roots` are the level-0 subproblems: the whole array, or independent
 // segments each keyed by its own offset.
+// knots_out (optional): (pl2_leaves + 1) floats per trace record, the knots
+// of that pass's PL2 model (zero for passes of another kind).
 template <class T>
 int ipls_sort(T* keys, int64_t n, const std::vector<Sub>& roots, const OracleCfg& cfg,
-              OracleTrace* trace, int64_t trace_cap, int64_t* trace_count, int32_t* levels_out) {
+              OracleTrace* trace, int64_t trace_cap, int64_t* trace_count, int32_t* levels_out,
+              float* knots_out = nullptr) {
   if (trace_count) *trace_count = 0;
   if (levels_out) *levels_out = 0;
   if (cfg.k < 3 || cfg.k > 256 || cfg.cutoff < 1) return -1;
@@ -638,9 +655,15 @@ int ipls_sort(T* keys, int64_t n, const std::vector<Sub>& roots, const OracleCfg
         base_sort<T>(keys + s.off, s.n);
         continue;
       }
+      std::vector<float> kn;
       partition_pass<T>(src + s.off, s.n, s.off, level, cfg, dst + s.off,
-                        counts.data(), &m);
+                        counts.data(), &m, &kn);
       if (trace && trace_count && *trace_count < trace_cap) {
+        if (knots_out && cfg.pl2_leaves > 0) {
+          float* kr = knots_out + *trace_count * (int64_t)(cfg.pl2_leaves + 1);
+          for (int32_t j = 0; j <= cfg.pl2_leaves; ++j)
+            kr[j] = (m.kind == 2 && j < (int32_t)kn.size()) ? kn[j] : 0.0f;
+        }
         OracleTrace& t = trace[(*trace_count)++];
         t.off = s.off; t.n = s.n; t.level = level; t.pad = 0; t.model = m;
         std::memset(t.counts, 0, sizeof(t.counts));
@@ -711,23 +734,24 @@ int oracle_total_order(int dtype, const void* keys, int64_t n, uint64_t* out) {
   });
 }
 
-// FMCD on an already sorted sample (the loop of Listing 1).
+// FMCD on an already sorted sample (from its definition).
 int oracle_fmcd(int dtype, const void* sorted, int64_t N, int32_t K, OracleModel* m) {
   if (N < 3 || K < 3) return -1;
   std::memset(m, 0, sizeof(*m));
   return dispatch(dtype, [&](auto* tag) {
     typedef std::remove_pointer_t<decltype(tag)> T;
-    fmcd_listing<T>((const T*)sorted, N, K, m);
+    fmcd<T>((const T*)sorted, N, K, m);
     return 0;
   });
 }
 
-int oracle_fmcd_bruteforce(int dtype, const void* sorted, int64_t N, int32_t K, OracleModel* m) {
+// FMCD by the one-walk search (for checking it against the definition).
+int oracle_fmcd_incremental(int dtype, const void* sorted, int64_t N, int32_t K, OracleModel* m) {
   if (N < 3 || K < 3) return -1;
   std::memset(m, 0, sizeof(*m));
   return dispatch(dtype, [&](auto* tag) {
     typedef std::remove_pointer_t<decltype(tag)> T;
-    fmcd_bruteforce<T>((const T*)sorted, N, K, m);
+    fmcd_incremental<T>((const T*)sorted, N, K, m);
     return 0;
   });
 }
@@ -793,6 +817,18 @@ int oracle_sort(int dtype, void* keys, int64_t n, const OracleCfg* cfg,
   });
 }
 
+// oracle_sort that also writes the PL2 knots of every traced pass
+// ((pl2_leaves + 1) floats per record into knots).
+int oracle_sort_knots(int dtype, void* keys, int64_t n, const OracleCfg* cfg,
+                      OracleTrace* trace, int64_t trace_cap, int64_t* trace_count,
+                      int32_t* levels, float* knots) {
+  return dispatch(dtype, [&](auto* tag) {
+    typedef std::remove_pointer_t<decltype(tag)> T;
+    std::vector<Sub> roots(1, Sub{0, n});
+    return ipls_sort<T>((T*)keys, n, roots, *cfg, trace, trace_cap, trace_count, levels, knots);
+  });
+}
+
 // Sorts each segment keys[off[i]..off[i+1]) as its own level-0 subproblem.
 int oracle_sort_segments(int dtype, void* keys, const int64_t* off, int64_t nseg,
                          const OracleCfg* cfg, OracleTrace* trace, int64_t trace_cap,
@@ -822,7 +858,22 @@ int oracle_pl2_fit(int dtype, const void* sorted, int64_t S, int32_t M, int32_t 
     std::memset(m, 0, sizeof(*m));
     std::vector<double> lt;
     std::vector<float> y;
-    if (!pl2_fit<T>((const T*)sorted, S, M, K, m, &y, nullptr, &lt)) return 1;
+    if (!pl2_fit<T>((const T*)sorted, S, M, K, m, &y, &lt)) return 1;
+    for (size_t i = 0; i < lt.size(); ++i) losses[i] = lt[i];
+    for (size_t j = 0; j < y.size(); ++j) knots[j] = y[j];
+    return 0;
+  });
+}
+
+// The same training in binary64 (a reference for the loss the binary32
+// model reaches): its knots (M + 1 doubles) and losses after each step.
+int oracle_pl2_fit_f64(int dtype, const void* sorted, int64_t S, int32_t M, int32_t K, OracleModel* m,
+                       double* losses, double* knots) {
+  return dispatch(dtype, [&](auto* tag) {
+    typedef std::remove_pointer_t<decltype(tag)> T;
+    std::memset(m, 0, sizeof(*m));
+    std::vector<double> lt, y;
+    if (!pl2_train<T, double>((const T*)sorted, S, M, K, m, &y, nullptr, &lt)) return 1;
     for (size_t i = 0; i < lt.size(); ++i) losses[i] = lt[i];
     for (size_t j = 0; j < y.size(); ++j) knots[j] = y[j];
     return 0;
@@ -843,8 +894,10 @@ int oracle_pl2_classify(int dtype, const void* keys, int64_t n, const OracleMode
 // The PL2 loss (1/S) sum (F(x_i) - (i+1/2)/S)^2 and its gradient in the knot
 // values y[0..M], for the leaves and positions a model assigns to the sorted
 // sample (summed in sample order).  For checking training steps.
+// absg (optional): per knot, the sum of the magnitudes of the terms of its
+// gradient, (2/S) sum |r_i| * weight_i (a scale for rounding-error bounds).
 int oracle_pl2_loss_grad(int dtype, const void* sorted, int64_t S, const OracleModel* m,
-                         const double* y, double* loss, double* grad) {
+                         const double* y, double* loss, double* grad, double* absg) {
   return dispatch(dtype, [&](auto* tag) {
     typedef std::remove_pointer_t<decltype(tag)> T;
     const T* x = (const T*)sorted;
@@ -870,6 +923,13 @@ int oracle_pl2_loss_grad(int dtype, const void* sorted, int64_t S, const OracleM
     for (int64_t i = 0; i < S; ++i) {
       grad[leaf[i]] += 2.0 * r[i] * (1.0 - w[i]) / (double)S;
       grad[leaf[i] + 1] += 2.0 * r[i] * w[i] / (double)S;
+    }
+    if (absg) {
+      for (int32_t j = 0; j <= M; ++j) absg[j] = 0.0;
+      for (int64_t i = 0; i < S; ++i) {
+        absg[leaf[i]] += 2.0 * std::fabs(r[i]) * (1.0 - w[i]) / (double)S;
+        absg[leaf[i] + 1] += 2.0 * std::fabs(r[i]) * w[i] / (double)S;
+      }
     }
     return 0;
   });

@@ -86,6 +86,8 @@ struct iplsContext {
   iplsTraceRecDev* trace_grid = nullptr;
   iplsTraceRecDev* trace_res = nullptr;
   int64_t trace_alloc = 0;
+  float* trace_knots = nullptr;       int64_t knot_cap = 0;       // records
+  int knot_leaves = 0;
   int64_t trace_grid_count = 0;
   iplsStats stats{};
   // request queue (iplsSubmit): a worker thread batches pending requests
@@ -360,6 +362,14 @@ iplsStatus sort_impl(iplsCtx c, void* keys, int64_t n, int dtype, const int64_t*
     c->trace_res = (iplsTraceRecDev*)p;
     c->trace_alloc = cfg.trace_cap;
   }
+  if (cfg.trace_cap > 0 && cfg.pl2_leaves > 0 && !c->trace_knots) {
+    const int64_t cap = std::min<int64_t>(cfg.trace_cap, kKnotTraceMax);
+    void* p;
+    IPLS_TRY(dev_alloc(c, &p, (size_t)cap * (cfg.pl2_leaves + 1) * sizeof(float)));
+    c->trace_knots = (float*)p;
+    c->knot_cap = cap;
+    c->knot_leaves = cfg.pl2_leaves;
+  }
   IPLS_CUDA(cudaMemsetAsync(c->run, 0, sizeof(RunStatus), c->stream));
   void* bufs[2] = {keys, c->scratch};
 
@@ -483,6 +493,8 @@ iplsStatus sort_impl(iplsCtx c, void* keys, int64_t n, int dtype, const int64_t*
     a.trace = cfg.trace_cap > 0 ? c->trace_grid : nullptr;
     a.trace_cap = cfg.trace_cap;
     a.trace_base = c->trace_grid_count;
+    a.trace_knots = cfg.trace_cap > 0 ? c->trace_knots : nullptr;
+    a.knot_cap = c->knot_cap;
     const int max_sample = sample_size_host(std::max<int64_t>(max_sub_n, 2), level, cfg.k, cfg.root_sample);
     a.max_sample = max_sample;
     a.pl2_leaves = cfg.pl2_leaves;
@@ -829,6 +841,7 @@ iplsStatus iplsDestroy(iplsCtx c) {
   dev_free(c, c->root_bounds, 2 * sizeof(int64_t));
   dev_free(c, c->trace_grid, (size_t)c->trace_alloc * sizeof(iplsTraceRecDev));
   dev_free(c, c->trace_res, (size_t)c->trace_alloc * sizeof(iplsTraceRecDev));
+  dev_free(c, c->trace_knots, (size_t)c->knot_cap * (c->knot_leaves + 1) * sizeof(float));
   if (c->h_ctl) cudaFreeHost(c->h_ctl);
   if (c->h_run) cudaFreeHost(c->h_run);
   if (c->h_slow) cudaFreeHost(c->h_slow);
@@ -1014,6 +1027,20 @@ iplsStatus iplsGetTrace(iplsCtx c, iplsTraceRec* out, int64_t cap, int64_t* coun
   if (a > 0) IPLS_CUDA(cudaMemcpy(out, c->trace_grid, a * sizeof(iplsTraceRec), cudaMemcpyDeviceToHost));
   if (b > 0) IPLS_CUDA(cudaMemcpy(out + a, c->trace_res, b * sizeof(iplsTraceRec), cudaMemcpyDeviceToHost));
   *count = a + b;
+  return IPLS_OK;
+}
+
+iplsStatus iplsGetTraceKnots(iplsCtx c, float* out, int64_t cap, int64_t* count) {
+  if (!c || !count || (cap > 0 && !out)) return fail(IPLS_ERR_ARG, "bad trace-knot arguments");
+  IPLS_CUDA(cudaStreamSynchronize(c->stream));
+  *count = 0;
+  if (c->cfg.trace_cap <= 0 || c->cfg.pl2_leaves <= 0 || !c->trace_knots) return IPLS_OK;
+  const int64_t ng = std::min(std::min(c->trace_grid_count, c->cfg.trace_cap), c->knot_cap);
+  const int64_t a = std::min(ng, cap);
+  if (a > 0)
+    IPLS_CUDA(cudaMemcpy(out, c->trace_knots, (size_t)a * (c->cfg.pl2_leaves + 1) * sizeof(float),
+                         cudaMemcpyDeviceToHost));
+  *count = a;
   return IPLS_OK;
 }
 

@@ -701,42 +701,45 @@ __device__ __forceinline__ int exponent_of(double r) {
   return e == 0 ? -1022 : e - 1023;
 }
 
-// Block-wide (all threads).  so[0..S) is the sorted sample (order bits).
-// Returns false (m untouched) when the sample's range cannot carry PL2; else
-// the knots y_0..y_M go to kout.  Training is binary32, one rounding per
-// operation.
+// Geometry of a PL2 model from the sorted sample so[0..S) (thread 0 of the
+// block; the result is read after a barrier): the fixed-point scale rho of
+// the sample's range, X0 = X(sample minimum) and the leaf shift sh, so that
+// leaf j = (X - X0) >> sh of M leaves covers the range.  *s_flag = 0 when the
+// range cannot carry PL2 (equal or non-finite extremes, saturation).
 template <class K>
-__device__ bool fit_pl2(const typename KT<K>::Ord* so, int S, int M, int K_, Model* m, float* kout,
-                        PL2Scratch sc, float* y, int* start, int* s_flag, long long* s_x0,
-                        int* s_rho, int* s_sh) {
+__device__ void pl2_geometry(const typename KT<K>::Ord* so, int S, int M, int* s_flag, long long* s_x0,
+                             int* s_rho, int* s_sh) {
   using T = KT<K>;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  if (tid == 0) {
-    *s_flag = 0;
-    const typename T::Bits b0 = T::unord(so[0]), b1 = T::unord(so[S - 1]);
-    if (so[0] != so[S - 1] && !T::special(b0) && !T::special(b1)) {
-      const double range = T::diff(b1, b0);
-      if (range > 0.0 && isfinite(range)) {
-        const int rho = exponent_of(range) - 30;
-        bool s0, s1;
-        const long long X0 = fixed_point<K>(b0, rho, s0), X1 = fixed_point<K>(b1, rho, s1);
-        if (!s0 && !s1) {
-          int mlog = 0;
-          while ((1 << mlog) < M) ++mlog;
-          const unsigned long long umax = (unsigned long long)(X1 - X0);
-          const int bl = umax == 0 ? 0 : 64 - __clzll((long long)umax);
-          *s_sh = bl - mlog > 0 ? bl - mlog : 0;
-          *s_rho = rho;
-          *s_x0 = X0;
-          *s_flag = 1;
-        }
+  *s_flag = 0;
+  const typename T::Bits b0 = T::unord(so[0]), b1 = T::unord(so[S - 1]);
+  if (so[0] != so[S - 1] && !T::special(b0) && !T::special(b1)) {
+    const double range = T::diff(b1, b0);
+    if (range > 0.0 && isfinite(range)) {
+      const int rho = exponent_of(range) - 30;
+      bool s0, s1;
+      const long long X0 = fixed_point<K>(b0, rho, s0), X1 = fixed_point<K>(b1, rho, s1);
+      if (!s0 && !s1) {
+        int mlog = 0;
+        while ((1 << mlog) < M) ++mlog;
+        const unsigned long long umax = (unsigned long long)(X1 - X0);
+        const int bl = umax == 0 ? 0 : 64 - __clzll((long long)umax);
+        *s_sh = bl - mlog > 0 ? bl - mlog : 0;
+        *s_rho = rho;
+        *s_x0 = X0;
+        *s_flag = 1;
       }
     }
   }
-  __syncthreads();
-  if (!*s_flag) return false;
-  const int rho = *s_rho, sh = *s_sh;
-  const long long X0 = *s_x0;
+}
+
+// Per-sample features (block-wide): the leaf of every sample and its position
+// w in [0, 1) inside the leaf, then the first sample of every leaf (start[M]
+// = S).  with_init: the knots start at the empirical CDF, y_j = start_j / S.
+template <class K>
+__device__ void pl2_features(const typename KT<K>::Ord* so, int S, int M, int rho, int sh, long long X0,
+                             PL2Scratch sc, int* start, float* y, bool with_init) {
+  using T = KT<K>;
+  const int tid = threadIdx.x, nt = blockDim.x;
   const float inv = __int_as_float((127 - sh) << 23);  // 2^-sh
   for (int i = tid; i < S; i += nt) {
     bool sat;
@@ -755,33 +758,69 @@ __device__ bool fit_pl2(const typename KT<K>::Ord* so, int S, int M, int K_, Mod
       if (sc.leaf[mid] < j) lo = mid + 1; else hi = mid;
     }
     start[j] = (j == M) ? S : lo;
-    y[j] = __fdiv_rn((float)((j == M) ? S : lo), (float)S);
+    if (with_init) y[j] = __fdiv_rn((float)((j == M) ? S : lo), (float)S);
   }
   __syncthreads();
+}
+
+// Forward (block-wide): the model's CDF at every sample and its residual
+// against the empirical CDF, r_i = F(x_i) - (i + 1/2)/S, binary32.
+__device__ __forceinline__ void pl2_forward(int S, const PL2Scratch& sc, const float* y) {
+  for (int i = threadIdx.x; i < S; i += blockDim.x) {
+    const int a = sc.leaf[i];
+    const float t1 = __fsub_rn(1.0f, sc.w[i]);
+    const float F = __fadd_rn(__fmul_rn(y[a], t1), __fmul_rn(y[a + 1], sc.w[i]));
+    const float tau = __fdiv_rn(__fadd_rn((float)i, 0.5f), (float)S);
+    sc.r[i] = __fsub_rn(F, tau);
+  }
+}
+
+// Backward for knot j (one thread): G_j = sum r_i dF(x_i)/dy_j and H_j =
+// sum (dF(x_i)/dy_j)^2 over the samples of leaf j (weight 1 - w) then of
+// leaf j-1 (weight w), in sample order; the loss gradient is 2 G_j / S and
+// the loss is quadratic in y_j with curvature 2 H_j / S.
+__device__ __forceinline__ void pl2_knot_gh(int j, int M, const PL2Scratch& sc, const int* start, float* G,
+                                            float* H) {
+  float g = 0.0f, h = 0.0f;
+  if (j < M)
+    for (int i = start[j]; i < start[j + 1]; ++i) {
+      const float t1 = __fsub_rn(1.0f, sc.w[i]);
+      g = __fadd_rn(g, __fmul_rn(sc.r[i], t1));
+      h = __fadd_rn(h, __fmul_rn(t1, t1));
+    }
+  if (j > 0)
+    for (int i = start[j - 1]; i < start[j]; ++i) {
+      g = __fadd_rn(g, __fmul_rn(sc.r[i], sc.w[i]));
+      h = __fadd_rn(h, __fmul_rn(sc.w[i], sc.w[i]));
+    }
+  *G = g;
+  *H = h;
+}
+
+// Block-wide (all threads).  so[0..S) is the sorted sample (order bits).
+// Returns false (m untouched) when the sample's range cannot carry PL2; else
+// the knots y_0..y_M go to kout.  Training: kPL2Steps red-black sweeps, each
+// half-sweep a forward pass over the samples and a backward step per knot of
+// one parity (y_j -= G_j / H_j, clamped between its neighbours).
+template <class K>
+__device__ bool fit_pl2(const typename KT<K>::Ord* so, int S, int M, int K_, Model* m, float* kout,
+                        PL2Scratch sc, float* y, int* start, int* s_flag, long long* s_x0,
+                        int* s_rho, int* s_sh) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid == 0) pl2_geometry<K>(so, S, M, s_flag, s_x0, s_rho, s_sh);
+  __syncthreads();
+  if (!*s_flag) return false;
+  const int rho = *s_rho, sh = *s_sh;
+  const long long X0 = *s_x0;
+  pl2_features<K>(so, S, M, rho, sh, X0, sc, start, y, true);
   for (int step = 0; step < kPL2Steps; ++step) {
     for (int parity = 1; parity >= 0; --parity) {
-      for (int i = tid; i < S; i += nt) {  // forward: residual of every sample
-        const int a = sc.leaf[i];
-        const float t1 = __fsub_rn(1.0f, sc.w[i]);
-        const float F = __fadd_rn(__fmul_rn(y[a], t1), __fmul_rn(y[a + 1], sc.w[i]));
-        const float tau = __fdiv_rn(__fadd_rn((float)i, 0.5f), (float)S);
-        sc.r[i] = __fsub_rn(F, tau);
-      }
+      pl2_forward(S, sc, y);
       __syncthreads();
       // the knots of this parity (they read only knots of the other one)
       for (int j = 2 * tid + parity; j <= M; j += 2 * nt) {
-        float g = 0.0f, h = 0.0f;
-        if (j < M)
-          for (int i = start[j]; i < start[j + 1]; ++i) {
-            const float t1 = __fsub_rn(1.0f, sc.w[i]);
-            g = __fadd_rn(g, __fmul_rn(sc.r[i], t1));
-            h = __fadd_rn(h, __fmul_rn(t1, t1));
-          }
-        if (j > 0)
-          for (int i = start[j - 1]; i < start[j]; ++i) {
-            g = __fadd_rn(g, __fmul_rn(sc.r[i], sc.w[i]));
-            h = __fadd_rn(h, __fmul_rn(sc.w[i], sc.w[i]));
-          }
+        float g, h;
+        pl2_knot_gh(j, M, sc, start, &g, &h);
         if (h > 0.0f) {
           const float lo = j > 0 ? y[j - 1] : 0.0f, hi = j < M ? y[j + 1] : 1.0f;
           y[j] = fminf(fmaxf(__fsub_rn(y[j], __fdiv_rn(g, h)), lo), hi);

@@ -31,6 +31,8 @@ constexpr int64_t kPL2MinKeys = 8192;
 constexpr int kPL2MaxSample = 4096;
 constexpr int kPL2Steps = 8;
 constexpr int kPL2MaxLeaves = 1024;
+// Grid-pass trace records whose PL2 knots are kept (iplsGetTraceKnots).
+constexpr int64_t kKnotTraceMax = 16384;
 
 // Linear partition model of one subproblem: b(x) = clamp(floor(fma(A,
 // x (-) x_lo, Bc)), 0, nb-1) (Ch.3 model equation, centred form).
@@ -249,6 +251,8 @@ struct LevelArgs {
   struct iplsTraceRecDev* trace;
   int64_t trace_cap;
   int64_t trace_base;
+  float* trace_knots;    // PL2 knots of grid records (pl2_leaves + 1 each), or NULL
+  int64_t knot_cap;      // records with room in trace_knots
 };
 
 struct ResidentArgs {

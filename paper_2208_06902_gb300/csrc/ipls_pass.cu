@@ -397,6 +397,13 @@ __global__ void __launch_bounds__(256) k_scan(LevelArgs a) {
       r.Bc = m.l.Bc; r.ud = m.l.ud; r.xlo_bits = m.l.xlo_bits; r.nsplit = m.nsplit; r.where = 0;
     }
     r.counts[b] = c;
+    // the PL2 knots of the pass (zeros for another kind of model)
+    if (a.trace_knots && a.pl2_leaves > 0 && a.trace_base + s < a.knot_cap) {
+      const int M1 = a.pl2_leaves + 1;
+      float* kr = a.trace_knots + (size_t)(a.trace_base + s) * M1;
+      const float* kn = a.knots + (size_t)s * M1;
+      for (int j = b; j < M1; j += 256) kr[j] = m.l.kind == kPL2 ? kn[j] : 0.0f;
+    }
   }
   __syncthreads();
   // every splitter-tree pass counts, a homogeneous one too

@@ -58,7 +58,8 @@ class iplsStats(ctypes.Structure):
 _lib = None
 SYMBOLS = ["iplsDefaultConfig", "iplsCreate", "iplsDestroy", "iplsScratchBytes", "iplsSort",
            "iplsSortSegmented", "iplsSortHost", "iplsSubmit", "iplsPoll", "iplsWait",
-           "iplsGetStats", "iplsGetKernelStats", "iplsGetTrace", "iplsLastError"]
+           "iplsGetStats", "iplsGetKernelStats", "iplsGetTrace", "iplsGetTraceKnots",
+           "iplsPL2LossGrad", "iplsSortSmallNoAlloc", "iplsLastError"]
 
 
 def library_path() -> str:
@@ -93,7 +94,9 @@ def load(build_if_missing: bool = True):
     L.iplsPoll.argtypes = [P, c.c_uint64]
     L.iplsWait.argtypes = [P, c.c_uint64, c.c_int64]
     L.iplsGetStats.argtypes = [P, c.POINTER(iplsStats)]
-    L.iplsGetTrace.argtypes = [P, c.POINTER(iplsTraceRec), c.c_int64, c.POINTER(c.c_int64)]
+    L.iplsGetTrace.argtypes = [P, P, c.c_int64, c.POINTER(c.c_int64)]
+    L.iplsGetTraceKnots.argtypes = [P, P, c.c_int64, c.POINTER(c.c_int64)]
+    L.iplsPL2LossGrad.argtypes = [P, c.c_int64, c.c_int, c.c_int32, P, P, P]
     L.iplsLastError.restype = c.c_char_p
     for name in SYMBOLS:
         if name != "iplsLastError":
@@ -196,12 +199,49 @@ def iplsGetStats(ctx: int) -> iplsStats:
     return s
 
 
-def iplsGetTrace(ctx: int, cap: int) -> list:
-    out = (iplsTraceRec * max(cap, 1))()
+TRACE_DTYPE = None
+
+
+def trace_dtype():
+    """numpy structured dtype with the layout of iplsTraceRec."""
+    import numpy as np
+    global TRACE_DTYPE
+    if TRACE_DTYPE is None:
+        TRACE_DTYPE = np.dtype(iplsTraceRec)
+    return TRACE_DTYPE
+
+
+def iplsGetTrace(ctx: int, cap: int, as_array: bool = False):
+    """The trace records of the last sort: a list of iplsTraceRec, or with
+    as_array a numpy structured array of that layout."""
+    import numpy as np
+    out = np.zeros(max(cap, 1), trace_dtype())
     cnt = ctypes.c_int64()
-    _check(load().iplsGetTrace(ctypes.c_void_p(ctx), out, cap, ctypes.byref(cnt)),
-           "iplsGetTrace")
-    return list(out[: cnt.value])
+    _check(load().iplsGetTrace(ctypes.c_void_p(ctx), ctypes.c_void_p(out.ctypes.data), cap,
+                               ctypes.byref(cnt)), "iplsGetTrace")
+    arr = out[: cnt.value]
+    if as_array:
+        return arr
+    return [iplsTraceRec.from_buffer_copy(r.tobytes()) for r in arr]
+
+
+def iplsGetTraceKnots(ctx: int, cap: int, leaves: int):
+    """PL2 knots of the grid-level trace records: array (records, leaves + 1)."""
+    import numpy as np
+    out = np.zeros((max(cap, 1), leaves + 1), np.float32)
+    cnt = ctypes.c_int64()
+    _check(load().iplsGetTraceKnots(ctypes.c_void_p(ctx), ctypes.c_void_p(out.ctypes.data), cap,
+                                    ctypes.byref(cnt)), "iplsGetTraceKnots")
+    return out[: cnt.value]
+
+
+def iplsPL2LossGrad(sample_ptr: int, S: int, dtype: int, leaves: int, knots_ptr: int,
+                    out_ptr: int, stream: int = 0) -> int:
+    """Device PL2 loss and gradient (see include/ipls.h); all pointers are
+    device pointers, out holds 2*(leaves+1)+2 floats."""
+    return _check(load().iplsPL2LossGrad(ctypes.c_void_p(sample_ptr), S, dtype, leaves,
+                                         ctypes.c_void_p(knots_ptr), ctypes.c_void_p(out_ptr),
+                                         ctypes.c_void_p(stream)), "iplsPL2LossGrad")
 
 
 def iplsLastError() -> str:
@@ -241,6 +281,7 @@ class Context:
         self.stream = s
         self.ctx = iplsCreate(cfg, s.cuda_stream)
         self.trace_cap = trace_cap
+        self.pl2_leaves = pl2_leaves
 
     def submit_ptr(self, ptr: int, n: int, dtype: int) -> int:
         """Queues an asynchronous sort of n device keys; returns its ticket."""
@@ -277,8 +318,11 @@ class Context:
     def kernel_stats(self, reset: bool = False) -> list:
         return iplsGetKernelStats(self.ctx, reset)
 
-    def trace(self) -> list:
-        return iplsGetTrace(self.ctx, self.trace_cap)
+    def trace(self, as_array: bool = False):
+        return iplsGetTrace(self.ctx, self.trace_cap, as_array)
+
+    def trace_knots(self):
+        return iplsGetTraceKnots(self.ctx, self.trace_cap, self.pl2_leaves)
 
     def close(self) -> None:
         if getattr(self, "ctx", None):

@@ -155,3 +155,30 @@ def test_last_half_sweep_leaves_even_knots_at_their_coordinate_minimum(dist, M):
             assert L >= L0 * (1 - 1e-12), (j, d, L, L0)
         checked += 1
     assert checked >= M // 8
+
+
+@pytest.mark.parametrize("M", [16, 64, 1024])
+@pytest.mark.parametrize("dtype", [np.float64, np.float32, np.uint64, np.uint32])
+@pytest.mark.parametrize("dist", ["uniform", "normal", "lognormal", "exponential", "mixgauss", "zipf"])
+def test_binary32_training_reaches_the_binary64_loss(dist, dtype, M):
+    """The PL2 model is trained in binary32.  The same training carried out in
+    binary64 is the reference: the binary32 knots, evaluated in binary64,
+    give a loss within 1e-4 (relative) of the binary64 training's final loss,
+    and every knot lies within 2^-12 of its binary64 counterpart -- far below
+    one bucket (1/k = 2^-8 of the CDF), so the precision does not shape the
+    partition."""
+    x = np.sort(datagen.generate(dist, 1 << 20, dtype, seed=3)[:4095])
+    f32 = oracle.pl2_fit(x, M)
+    f64 = oracle.pl2_fit_f64(x, M)
+    assert (f32 is None) == (f64 is None)
+    if f32 is None:
+        return
+    m32, _ = f32
+    m64, y64, losses64 = f64
+    assert (m32.pl2_sh, m32.pl2_rho, m32.pl2_x0) == (m64.pl2_sh, m64.pl2_rho, m64.pl2_x0)
+    y32 = oracle.pl2_knots(m32).astype(np.float64)
+    L32, _ = oracle.pl2_loss_grad(x, m32, y32)
+    L64, _ = oracle.pl2_loss_grad(x, m64, y64)
+    assert math.isclose(L64, losses64[-1], rel_tol=1e-12)
+    assert L32 <= L64 * (1 + 1e-4) + 1e-12, (L32, L64)
+    assert np.abs(y32 - y64).max() <= 2.0 ** -12

@@ -1,14 +1,19 @@
-"""iplsSortSmallNoAlloc: the entry point that sorts without allocating.
+"""iplsSortSmallNoAlloc: the entry point that sorts without allocating, for
+callers that cannot allocate device memory while they sort (a framework
+pool that holds the device's memory, a loop where cudaMalloc could stall
+the device, a pipeline that must not run out of memory half-way).
 
 It is called through the C ABI and compared with iplsSort, the existing
-entry point, on the same keys. Two calls are made back to back, since the
-static status block must be cleared between them. The size limit is checked
-on the host before any CUDA call.
+entry point, on the same keys, and with the oracle's definition of the
+result (std::sort under totalOrder). Two calls are made back to back, since
+the static status block must be cleared between them. The size limit is
+checked on the host before any CUDA call.
 """
 import numpy as np
 import pytest
 
 import datagen
+import oracle
 from gpu_util import CODE, from_dev, to_dev
 
 
@@ -53,10 +58,12 @@ def test_two_calls_in_a_row_equal_iplsSort(dtype):
         p.iplsSort(None, b.data_ptr(), n, CODE[np.dtype(dtype)])
         p.iplsSort(None, b2.data_ptr(), n, CODE[np.dtype(dtype)])
         torch.cuda.synchronize()
-        for got, want in [(a, b), (a2, b2)]:
+        for got, want, src in [(a, b, x), (a2, b2, y)]:
             g = from_dev(got, dtype)
             w = from_dev(want, dtype)
             assert np.array_equal(g.view(np.uint8), w.view(np.uint8)), (dist, n)
+            ref = oracle.std_sort(src)
+            assert np.array_equal(g.view(np.uint8), ref.view(np.uint8)), (dist, n)
 
 
 @pytest.mark.gpu
@@ -78,3 +85,5 @@ def test_other_cutoffs_and_k():
         torch.cuda.synchronize()
         assert np.array_equal(from_dev(a, np.float64).view(np.uint8),
                               from_dev(b, np.float64).view(np.uint8)), (cutoff, k)
+        assert np.array_equal(from_dev(a, np.float64).view(np.uint8),
+                              oracle.std_sort(x).view(np.uint8)), (cutoff, k)
