@@ -22,7 +22,7 @@ def inputs(case):
     return datagen.config3(arg)
 
 
-def run(case, outdir: str, k: int = 256, cutoff: int = 256, trace_cap: int = 4_000_000):
+def run(case, outdir: str, k: int = 256, cutoff: int = 256, trace_cap: int = 1_000_000):
     t0 = time.perf_counter()
     x = inputs(case)
     out, trace, levels = oracle.sort(x, k=k, cutoff=cutoff, trace_cap=trace_cap, as_array=True)

@@ -50,7 +50,7 @@ def test_full_size_passes_equal_the_oracle(case, oracle_runs):
     x = oracle_jobs.inputs(case)
     code = CODE[x.dtype]
     dev = torch.from_numpy(x.view(np.uint8)).cuda()
-    ctx = Context(k=256, cutoff=256, trace_cap=4_000_000)
+    ctx = Context(k=256, cutoff=256, trace_cap=1_000_000)
     ctx.sort_ptr(dev.data_ptr(), x.size, code)
     torch.cuda.synchronize()
     got = dev.cpu().numpy().view(x.dtype)
