@@ -104,6 +104,21 @@ typedef struct iplsKernelStat {
   int64_t bytes;          /* algorithmic bytes moved by those launches */
 } iplsKernelStat;
 
+/* Device time of the grid-level partition passes of one recursion level
+ * (profile = 1), accumulated over calls: grid_ms sums the CUDA-event
+ * durations of that level's grid kernels (fit, classify + histogram, check,
+ * scans, scatter); keys counts the keys those passes moved and bytes their
+ * algorithmic bytes, 2 * w * keys (every moved key read once and written
+ * once, Ch.2 IPS4o partitioning step). */
+typedef struct iplsLevelStat {
+  int32_t level;
+  int32_t pad;
+  int64_t launches;
+  int64_t keys;
+  double grid_ms;
+  int64_t bytes;
+} iplsLevelStat;
+
 /* One partition pass as recorded by the trace (see iplsGetTrace). */
 typedef struct iplsTraceRec {
   int64_t off;            /* first key of the subproblem in the whole array */
@@ -211,6 +226,12 @@ iplsStatus iplsGetStats(iplsCtx ctx, iplsStats* stats);
  * sets *count; reset = 1 clears the accumulators after reading. */
 iplsStatus iplsGetKernelStats(iplsCtx ctx, iplsKernelStat* out, int32_t cap, int32_t* count,
                               int32_t reset);
+
+/* Per-level grid-pass time and bytes accumulated while cfg.profile = 1
+ * (synchronises the stream).  Writes up to cap entries, one per level that
+ * ran grid passes, and sets *count; reset = 1 clears the accumulators. */
+iplsStatus iplsGetLevelStats(iplsCtx ctx, iplsLevelStat* out, int32_t cap, int32_t* count,
+                             int32_t reset);
 
 /* Copies up to cap trace records of the last sort to host memory `out`
  * (requires cfg.trace_cap > 0) and sets *count to the records kept. */

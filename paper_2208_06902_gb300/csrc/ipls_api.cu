@@ -114,10 +114,17 @@ struct iplsContext {
   int scatter_grid[4] = {0, 0, 0, 0};
   int64_t dev_bytes = 0;
   // profiling (cfg.profile): event pairs per launch, resolved at sync points
-  struct Pending { int kind; cudaEvent_t a, b; };
+  struct Pending { int kind; int level; cudaEvent_t a, b; };
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> spare_events;
   int64_t k_launches[16] = {};
+  // per grid level (profile = 1): summed time of the level's grid kernels,
+  // their launches, and the keys (and algorithmic bytes) its passes moved
+  static constexpr int kLevels = 16;
+  double lv_ms[kLevels] = {};
+  int64_t lv_launches[kLevels] = {};
+  int64_t lv_keys[kLevels] = {};
+  int64_t lv_bytes[kLevels] = {};
   double k_ms[16] = {};
   int64_t k_bytes[16] = {};
   // host-buffer sorting
@@ -195,7 +202,7 @@ cudaEvent_t take_event(iplsCtx c) {
 // Launches `fn` (which enqueues exactly one kernel) bracketed by CUDA events
 // when profiling; every launch is counted.
 template <class F>
-cudaError_t timed(iplsCtx c, int kind, F fn) {
+cudaError_t timed(iplsCtx c, int kind, F fn, int level = -1) {
   if (!c->cfg.profile) {
     cudaError_t e = fn();
     return e;
@@ -204,7 +211,7 @@ cudaError_t timed(iplsCtx c, int kind, F fn) {
   if (a) cudaEventRecord(a, c->stream);
   cudaError_t e = fn();
   if (b) cudaEventRecord(b, c->stream);
-  if (a && b) c->pending.push_back({kind, a, b});
+  if (a && b) c->pending.push_back({kind, level, a, b});
   return e;
 }
 
@@ -215,6 +222,10 @@ void resolve_events(iplsCtx c) {
     if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
       c->k_ms[p.kind] += ms;
       c->k_launches[p.kind] += 1;
+      if (p.level >= 0 && p.level < iplsContext::kLevels) {
+        c->lv_ms[p.level] += ms;
+        c->lv_launches[p.level] += 1;
+      }
     } else {
       cudaGetLastError();
     }
@@ -499,13 +510,13 @@ iplsStatus sort_impl(iplsCtx c, void* keys, int64_t n, int dtype, const int64_t*
     a.max_sample = max_sample;
     a.pl2_leaves = cfg.pl2_leaves;
     a.knots = cfg.pl2_leaves > 0 ? X.knots : nullptr;
-    IPLS_CUDA(timed(c, kkFit, [&] { return launch_fit(a, c->stream, max_sample); }));
-    IPLS_CUDA(timed(c, kkHist, [&] { return launch_hist(a, c->stream, 0, occupancy_grid(c, 0, dtype)); }));
-    IPLS_CUDA(timed(c, kkCheck, [&] { return launch_check(a, c->stream, max_sample); }));
-    IPLS_CUDA(timed(c, kkRehist, [&] { return launch_hist(a, c->stream, 1, occupancy_grid(c, 0, dtype)); }));
-    IPLS_CUDA(timed(c, kkScan, [&] { return launch_scan(a, c->stream); }));
-    IPLS_CUDA(timed(c, kkTileScan, [&] { return launch_tilescan(a, c->stream, c->num_sms * 8); }));
-    IPLS_CUDA(timed(c, kkScatter, [&] { return launch_scatter(a, c->stream, occupancy_grid(c, 1, dtype)); }));
+    IPLS_CUDA(timed(c, kkFit, [&] { return launch_fit(a, c->stream, max_sample); }, level));
+    IPLS_CUDA(timed(c, kkHist, [&] { return launch_hist(a, c->stream, 0, occupancy_grid(c, 0, dtype)); }, level));
+    IPLS_CUDA(timed(c, kkCheck, [&] { return launch_check(a, c->stream, max_sample); }, level));
+    IPLS_CUDA(timed(c, kkRehist, [&] { return launch_hist(a, c->stream, 1, occupancy_grid(c, 0, dtype)); }, level));
+    IPLS_CUDA(timed(c, kkScan, [&] { return launch_scan(a, c->stream); }, level));
+    IPLS_CUDA(timed(c, kkTileScan, [&] { return launch_tilescan(a, c->stream, c->num_sms * 8); }, level));
+    IPLS_CUDA(timed(c, kkScatter, [&] { return launch_scatter(a, c->stream, occupancy_grid(c, 1, dtype)); }, level));
     IPLS_CUDA(cudaMemcpyAsync(c->h_ctl, c->ctl, sizeof(LevelCtl), cudaMemcpyDeviceToHost, c->stream));
     IPLS_CUDA(cudaMemcpyAsync(c->h_run, c->run, sizeof(RunStatus), cudaMemcpyDeviceToHost, c->stream));
     IPLS_CUDA(cudaStreamSynchronize(c->stream));
@@ -526,6 +537,10 @@ iplsStatus sort_impl(iplsCtx c, void* keys, int64_t n, int dtype, const int64_t*
     resolve_events(c);
     c->k_bytes[kkHist] += (int64_t)w * lc.keys_level;
     c->k_bytes[kkScatter] += 2 * (int64_t)w * lc.keys_moved;
+    if (level < iplsContext::kLevels) {
+      c->lv_keys[level] += lc.keys_moved;
+      c->lv_bytes[level] += 2 * (int64_t)w * lc.keys_moved;
+    }
     c->stats.grid_levels += 1;
     c->stats.grid_passes += nsub;
     c->stats.fallback_passes += lc.fallback;
@@ -964,6 +979,30 @@ iplsStatus iplsGetKernelStats(iplsCtx c, iplsKernelStat* out, int32_t cap, int32
   if (reset) {
     for (int k = 0; k < 16; ++k) { c->k_launches[k] = 0; c->k_ms[k] = 0.0; c->k_bytes[k] = 0; }
   }
+  return IPLS_OK;
+}
+
+iplsStatus iplsGetLevelStats(iplsCtx c, iplsLevelStat* out, int32_t cap, int32_t* count, int32_t reset) {
+  if (!c || !count || (cap > 0 && !out)) return fail(IPLS_ERR_ARG, "bad level-stats arguments");
+  IPLS_CUDA(cudaStreamSynchronize(c->stream));
+  resolve_events(c);
+  int m = 0;
+  for (int l = 0; l < iplsContext::kLevels && m < cap; ++l) {
+    if (c->lv_launches[l] == 0 && c->lv_keys[l] == 0) continue;
+    out[m].level = l;
+    out[m].pad = 0;
+    out[m].launches = c->lv_launches[l];
+    out[m].keys = c->lv_keys[l];
+    out[m].grid_ms = c->lv_ms[l];
+    out[m].bytes = c->lv_bytes[l];
+    ++m;
+  }
+  *count = m;
+  if (reset)
+    for (int l = 0; l < iplsContext::kLevels; ++l) {
+      c->lv_ms[l] = 0.0;
+      c->lv_launches[l] = c->lv_keys[l] = c->lv_bytes[l] = 0;
+    }
   return IPLS_OK;
 }
 

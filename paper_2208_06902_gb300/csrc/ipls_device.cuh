@@ -73,6 +73,8 @@ template <> struct KT<double> {
   using Ord = unsigned long long;
   static constexpr int W = 8;
   static constexpr int kMant = 52;   // low ord bits linear inside a binade
+  static constexpr int kBias = 1075; // spacing of biased exponent e: 2^(max(e,1) - kBias)
+  static constexpr int kExpMask = 0x7FF;
   __device__ static __forceinline__ Ord ord(Bits b) {
     return (b >> 63) ? ~b : (b | (1ULL << 63));
   }
@@ -99,6 +101,8 @@ template <> struct KT<float> {
   using Ord = unsigned int;
   static constexpr int W = 4;
   static constexpr int kMant = 23;
+  static constexpr int kBias = 150;
+  static constexpr int kExpMask = 0xFF;
   __device__ static __forceinline__ Ord ord(Bits b) { return (b >> 31) ? ~b : (b | 0x80000000u); }
   __device__ static __forceinline__ Bits unord(Ord u) { return (u >> 31) ? (u & 0x7FFFFFFFu) : ~u; }
   __device__ static __forceinline__ double value(Bits b) { return (double)__uint_as_float(b); }
@@ -120,6 +124,8 @@ template <class U, int WB> struct KTInt {
   using Ord = U;
   static constexpr int W = WB;
   static constexpr int kMant = 0;    // integer keys: the value is linear in u
+  static constexpr int kBias = 0;
+  static constexpr int kExpMask = 0;
   __device__ static __forceinline__ Ord ord(Bits b) { return b; }
   __device__ static __forceinline__ Bits unord(Ord u) { return u; }
   __device__ static __forceinline__ double value(Bits b) { return __ull2double_rn((unsigned long long)b); }
@@ -375,6 +381,39 @@ struct FitShared {
   int pad;
 };
 
+// Fields of the same-binade estimate (LinModel::ufast ...).  q is the spacing
+// of the binade of x_lo; ushift is chosen so that in-range keys (model value
+// within nb + |Bc| + 1 of zero) have |D >> ushift| < 2^30 while keys with
+// |D >> ushift| >= 2^30 are certainly clamped.  The bound ucabs covers the
+// truncation by the shift (at most auf), the rounding of Bc and a margin;
+// crel*|v| covers the binary32 roundings of D, auf and the fma (three units
+// of 2^-24 and the binary64 model's own rounding, with room to spare).
+template <class K>
+__device__ void same_binade_model(typename KT<K>::Bits xlo, int nb, double A, double Bc, LinModel* m) {
+  using T = KT<K>;
+  int ok = !T::special(xlo);
+  double q = 1.0;
+  if (T::kMant > 0) {
+    const int e = (int)(((uint64_t)xlo >> T::kMant) & T::kExpMask);
+    q = ldexp(1.0, (e ? e : 1) - T::kBias);
+  }
+  const double aq = __dmul_rn(A, q);  // exact: q is a power of two (unless it underflows)
+  ok = ok && isfinite(aq) && aq >= DBL_MIN;
+  const double width = ok ? __dmul_rn(__ddiv_ru(__dadd_ru((double)nb + 1.0, fabs(Bc)), aq), 1.0 + 0x1.0p-50) : 0.0;
+  ok = ok && isfinite(width);
+  int s = ok ? ilogb(width) + 1 - 29 : 0;
+  if (s < 0) s = 0;
+  const double a2s = ldexp(aq, s);
+  const float auf = __double2float_rn(a2s);
+  ok = ok && s < 64 && auf >= FLT_MIN && isfinite(auf);
+  const float ucabs = __double2float_ru((fabs(Bc) * 0x1.0p-21 + 2.0 * a2s + 0x1.0p-40) * (1.0 + 0x1.0p-20));
+  ok = ok && ucabs < 0x1.0p-8f;
+  m->ufast = ok;
+  m->ushift = s;
+  m->auf = auf;
+  m->ucabs = ucabs;
+}
+
 // One probe: does every window of D+1 consecutive sample points span at
 // least u_d(D)?  The thresholds of the fixed-point test come from the
 // fixed-point span q[N-1-D] - q[D]: with |q(x) - x/2^rho| < 1 and binary64
@@ -459,6 +498,10 @@ __device__ void fit_linear(const typename KT<K>::Ord* so, int N, int K_, LinMode
     m->xlo_bits = 0;
     m->rho = 0;
     m->qlo = 0;
+    m->ufast = 0;
+    m->ushift = 0;
+    m->auf = 0.0f;
+    m->ucabs = 0.0f;
     if (lin) {
       // certified filter: fixed point at rho = L - 61 with |x| < 2^L for every
       // sample key; off when the keys are all zero or so large that a
@@ -532,6 +575,7 @@ __device__ void fit_linear(const typename KT<K>::Ord* so, int N, int K_, LinMode
         m->bcf = __double2float_rn(Bc);
         m->crel = 0x1.0p-21f;
         m->cabs = cabs;
+        same_binade_model<K>(xlo, K_, A, Bc, m);
       }
     }
   }
@@ -594,11 +638,13 @@ __device__ __forceinline__ int classify_exact(typename KT<K>::Bits b, double A, 
 template <class K>
 struct Classifier {
   using Bits = typename KT<K>::Bits;
-  int kind, nb, fast, rho, nsplit;
+  using Ord = typename KT<K>::Ord;
+  int kind, nb, fast, rho, nsplit, ufast, ushift;
   long long qlo;
-  float af, bcf, crel, cabs;
+  float af, bcf, crel, cabs, auf, ucabs;
   double A, Bc;
   Bits xlo;
+  Ord ulo;
   const uint64_t* split;
 
   __device__ __forceinline__ void load(const LinModel& m, int exact_only) {
@@ -614,6 +660,11 @@ struct Classifier {
     A = m.A;
     Bc = m.Bc;
     xlo = (Bits)m.xlo_bits;
+    ulo = KT<K>::ord(xlo);
+    ufast = m.ufast && !exact_only;
+    ushift = m.ushift;
+    auf = m.auf;
+    ucabs = m.ucabs;
     nsplit = 0;
     split = nullptr;
   }
@@ -645,8 +696,44 @@ struct Classifier {
     return -1;
   }
 
+  // The certified binary32 decision on an estimate v with bound del: the
+  // bucket, or -1 when [v - del, v + del] contains a bucket boundary.
+  __device__ __forceinline__ int decide(float v, float del) const {
+    const float hi = v + del, lo = v - del;
+    if (hi < 1.0f) return 0;
+    if (lo >= (float)(nb - 1)) return nb - 1;
+    const float fl = floorf(lo), fh = floorf(hi);
+    if (fl == fh) return __float_as_int(fl + 8388608.0f) - 0x4B000000;
+    return -1;
+  }
+
+  // Same-binade estimate from the order bits u of the key: -1 when the key
+  // is not in x_lo's binade (or not within 2^62 of it, for integers) or the
+  // certified interval contains a bucket boundary.
+  __device__ __forceinline__ int ord_bucket(Ord u) const {
+    using T = KT<K>;
+    long long D;
+    if (T::kMant > 0) {
+      if (((u ^ ulo) >> T::kMant) != 0) return -1;  // another sign or exponent
+      D = (long long)((uint64_t)u - (uint64_t)ulo); // |D| < 2^52: the wrap gives its sign
+    } else {
+      const uint64_t du = (uint64_t)u - (uint64_t)ulo;
+      D = (long long)du;
+      if ((u >= ulo) != (D >= 0)) return -1;        // |u - u_lo| >= 2^63
+    }
+    const long long Ds = D >> ushift;
+    if (Ds >= (1LL << 30)) return nb - 1;
+    if (Ds <= -(1LL << 30)) return 0;
+    const float v = fmaf(auf, __int2float_rn((int)Ds), bcf);
+    return decide(v, fmaf(crel, fabsf(v), ucabs));
+  }
+
   __device__ __forceinline__ int bucket(Bits b) const {
     if (kind == kSplitter) return splitter_bucket((uint64_t)KT<K>::ord(b), split, nsplit);
+    if (ufast) {
+      const int r = ord_bucket(KT<K>::ord(b));
+      if (r >= 0) return r;
+    }
     if (fast) {
       const int r = fast_bucket(b);
       if (r >= 0) return r;
@@ -658,6 +745,10 @@ struct Classifier {
   // the splitter tree or when the estimate is off.
   __device__ __forceinline__ int bucket_or_defer(Bits b) const {
     if (kind == kSplitter) return splitter_bucket((uint64_t)KT<K>::ord(b), split, nsplit);
+    if (ufast) {
+      const int r = ord_bucket(KT<K>::ord(b));
+      if (r >= 0) return r;
+    }
     if (fast) return fast_bucket(b);
     return classify_exact<K>(b, A, Bc, xlo, nb);
   }

@@ -56,6 +56,15 @@ struct LinModel {
   float bcf;      // RN32(Bc)
   float crel;     // certified bound = crel*|v| + cabs
   float cabs;
+  // Same-binade estimate: for a key in the binade of x_lo (integer keys:
+  // within 2^62 of it), x (-) x_lo = (u - u_lo) * q exactly, with u the
+  // totalOrder bits and q the binade's spacing (1 for integers), so the model
+  // value is estimated from D = (u - u_lo) >> ushift as fmaf(auf, D, bcf),
+  // auf = RN32(A * q * 2^ushift), certified by crel*|v| + ucabs.
+  int32_t ufast;
+  int32_t ushift;
+  float auf;
+  float ucabs;
 };
 
 // Full model: the linear part, or unique splitters s_1 < ... < s_m as

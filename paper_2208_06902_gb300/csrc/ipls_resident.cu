@@ -459,8 +459,9 @@ template <class K, int kCap, int kW>
 struct TailSmem {
   typename KT<K>::Ord keys[kCap];
   unsigned char seg[kCap];   // segment (bucket or child) of each position
-  unsigned short wcnt[kW][kMaxK];
-  unsigned int peer[kW][kMaxK];     // lanes of the current step per bucket (kept zero between steps)
+  unsigned short wcnt[kW][kMaxK];   // each warp's offset inside every bucket (stable placement)
+  unsigned int peer[kW][kMaxK];     // per-warp bucket counts, then placement cursors (or, for
+                                    // stable placement, lanes of the current step per bucket)
   int bstart[kMaxK + 1];
   int segb[kMaxK + 1];
   int tot[kMaxK];
@@ -526,15 +527,12 @@ __global__ void __launch_bounds__(kThreads, kCap == kResidentMax ? 2 : 4) k_tail
   if (g.fit >= 0) {
     // the model: a copy in shared memory for the phases after the first
     // barrier; until then every thread reads it from global memory, and each
-    // warp zeroes its own rank counters, so no barrier is needed to start
+    // warp zeroes its own bucket-count row, so no barrier is needed to start
     const TailModel& gm = a.tail_models[g.fit];
     if (threadIdx.x < (int)(sizeof(TailModel) / 8))
       reinterpret_cast<unsigned long long*>(&sh.tm)[threadIdx.x] =
           reinterpret_cast<const unsigned long long*>(&gm)[threadIdx.x];
-    for (int i = lane; i < kMaxK; i += 32) {
-      sh.wcnt[warp][i] = 0;
-      sh.peer[warp][i] = 0u;
-    }
+    for (int i = lane; i < kMaxK; i += 32) sh.peer[warp][i] = 0u;
     if (threadIdx.x == 0) {
       sh.slow_all = 0;
       sh.any_big = 0;
@@ -618,44 +616,30 @@ __global__ void __launch_bounds__(kThreads, kCap == kResidentMax ? 2 : 4) k_tail
           if (j < steps && ((dmask >> j) & 1u)) br[j] = xr[j * 32 + lane];
         __syncwarp();
       }
+      // per-warp bucket counts (one shared atomic per key)
 #pragma unroll
-      for (int j = 0; j < kPT; ++j) {
-        if (j < steps) {
-          const int bk = (int)br[j];
-          // the lanes of this step with the same bucket: one shared OR each
-          const bool valid = bk < kMaxK;
-          const int bq = valid ? bk : 0;
-          if (valid) atomicOr(&sh.peer[warp][bq], 1u << lane);
-          __syncwarp();
-          const unsigned peers = valid ? sh.peer[warp][bq] : 0u;
-          const int lt = __popc(peers & lanemask_lt());
-          const int basec = sh.wcnt[warp][bq];
-          br[j] = ((unsigned)bk << 16) | (unsigned)(basec + lt);
-          __syncwarp();
-          if (valid && lt == 0) {  // the first lane of the bucket
-            sh.wcnt[warp][bq] = (unsigned short)(basec + __popc(peers));
-            sh.peer[warp][bq] = 0u;
-          }
-          __syncwarp();
-        }
-      }
+      for (int j = 0; j < kPT; ++j)
+        if (j < steps && br[j] < (unsigned)kMaxK) atomicAdd(&sh.peer[warp][br[j]], 1u);
       __syncthreads();
       if (threadIdx.x < kMaxK) {
+        // bucket totals; each warp's offset inside the bucket (placement
+        // cursors in peer, the same offsets in wcnt for stable placement)
         const int b = threadIdx.x;
-        int run = 0;
+        unsigned run = 0;
 #pragma unroll
         for (int w = 0; w < kW; ++w) {
-          const int x = sh.wcnt[w][b];
+          const unsigned x = sh.peer[w][b];
+          sh.peer[w][b] = run;
           sh.wcnt[w][b] = (unsigned short)run;
           run += x;
         }
-        sh.tot[b] = run;
+        sh.tot[b] = (int)run;
         // no progress of the linear model: the splitter tree decides (the
         // splitter tree itself always progresses or leaves one equality run)
-        if (run == n && !split_tree) sh.slow_all = 1;
-        if (run > a.cutoff && b < sh.tm.l.nb && !(split_tree && (b & 1))) sh.any_big = 1;
+        if ((int)run == n && !split_tree) sh.slow_all = 1;
+        if ((int)run > a.cutoff && b < sh.tm.l.nb && !(split_tree && (b & 1))) sh.any_big = 1;
       }
-      if (threadIdx.x == 0) {  // the task's key range (after bucket 0's sum)
+      if (threadIdx.x == 0) {  // the task's key range
         Ord lo = ~(Ord)0, hi = 0;
 #pragma unroll
         for (int w = 0; w < kW; ++w) {
@@ -691,12 +675,45 @@ __global__ void __launch_bounds__(kThreads, kCap == kResidentMax ? 2 : 4) k_tail
         __syncthreads();
         const bool tpk = sh.tpk != 0;
         const Ord tlo = sh.tlo;
+        const bool stable = sh.any_big != 0;
+        if (stable) {
+          // a bucket above the cutoff becomes a subproblem of its own, whose
+          // sample is drawn by position: keys keep their input order inside
+          // every bucket (rank within the warp from per-bucket lane masks,
+          // one shared OR per key, after the warp's offset in wcnt)
+          for (int i = lane; i < kMaxK; i += 32) sh.peer[warp][i] = 0u;
+          __syncwarp();
+#pragma unroll
+          for (int j = 0; j < kPT; ++j) {
+            if (j < steps) {
+              const int bk = (int)br[j];
+              const bool valid = bk < kMaxK;
+              const int bq = valid ? bk : 0;
+              if (valid) atomicOr(&sh.peer[warp][bq], 1u << lane);
+              __syncwarp();
+              const unsigned peers = valid ? sh.peer[warp][bq] : 0u;
+              const int lt = __popc(peers & lanemask_lt());
+              const int basec = sh.wcnt[warp][bq];
+              br[j] = ((unsigned)bk << 16) | (unsigned)(basec + lt);
+              __syncwarp();
+              if (valid && lt == 0) {  // the first lane of the bucket
+                sh.wcnt[warp][bq] = (unsigned short)(basec + __popc(peers));
+                sh.peer[warp][bq] = 0u;
+              }
+              __syncwarp();
+            }
+          }
+        }
+        // every bucket is base-cased unless `stable`: the order inside a
+        // bucket does not matter, and a shared cursor per (warp, bucket)
+        // gives each key its place
 #pragma unroll
         for (int j = 0; j < kPT; ++j) {
           if (j < steps) {
-            const int bk = (int)(br[j] >> 16);
+            const int bk = stable ? (int)(br[j] >> 16) : (int)br[j];
             if (bk < kMaxK) {
-              const int p = sh.bstart[bk] + sh.wcnt[warp][bk] + (int)(br[j] & 0xFFFF);
+              const int p = sh.bstart[bk] + (stable ? (int)(br[j] & 0xFFFF)
+                                                    : (int)atomicAdd(&sh.peer[warp][bk], 1u));
               // read again (from cache) rather than held in registers
               const Ord o = T::ord(src[warp * chunk + j * 32 + lane]);
               sh.keys[p] = tpk ? (Ord)((Ord)(o - tlo) << kPosBits) | (Ord)p : o;

@@ -36,6 +36,11 @@ class iplsKernelStat(ctypes.Structure):
                 ("total_ms", ctypes.c_double), ("bytes", ctypes.c_int64)]
 
 
+class iplsLevelStat(ctypes.Structure):
+    _fields_ = [("level", ctypes.c_int32), ("pad", ctypes.c_int32), ("launches", ctypes.c_int64),
+                ("keys", ctypes.c_int64), ("grid_ms", ctypes.c_double), ("bytes", ctypes.c_int64)]
+
+
 class iplsTraceRec(ctypes.Structure):
     _fields_ = [("off", ctypes.c_int64), ("n", ctypes.c_int64), ("level", ctypes.c_int32),
                 ("kind", ctypes.c_int32), ("capped", ctypes.c_int32),
@@ -58,7 +63,8 @@ class iplsStats(ctypes.Structure):
 _lib = None
 SYMBOLS = ["iplsDefaultConfig", "iplsCreate", "iplsDestroy", "iplsScratchBytes", "iplsSort",
            "iplsSortSegmented", "iplsSortHost", "iplsSubmit", "iplsPoll", "iplsWait",
-           "iplsGetStats", "iplsGetKernelStats", "iplsGetTrace", "iplsGetTraceKnots",
+           "iplsGetStats", "iplsGetKernelStats", "iplsGetLevelStats", "iplsGetTrace",
+           "iplsGetTraceKnots",
            "iplsPL2LossGrad", "iplsSortSmallNoAlloc", "iplsLastError"]
 
 
@@ -90,6 +96,8 @@ def load(build_if_missing: bool = True):
     L.iplsSortSmallNoAlloc.argtypes = [P, c.c_int64, c.c_int, c.POINTER(iplsConfig), P]
     L.iplsGetKernelStats.argtypes = [P, c.POINTER(iplsKernelStat), c.c_int32,
                                      c.POINTER(c.c_int32), c.c_int32]
+    L.iplsGetLevelStats.argtypes = [P, c.POINTER(iplsLevelStat), c.c_int32,
+                                    c.POINTER(c.c_int32), c.c_int32]
     L.iplsSubmit.argtypes = [P, P, c.c_int64, c.c_int, c.POINTER(c.c_uint64)]
     L.iplsPoll.argtypes = [P, c.c_uint64]
     L.iplsWait.argtypes = [P, c.c_uint64, c.c_int64]
@@ -175,6 +183,15 @@ def iplsGetKernelStats(ctx: int, reset: bool = False) -> list:
     _check(load().iplsGetKernelStats(ctypes.c_void_p(ctx), out, 32, ctypes.byref(cnt),
                                      1 if reset else 0), "iplsGetKernelStats")
     return [dict(name=r.name.decode(), launches=r.launches, total_ms=r.total_ms,
+                 bytes=r.bytes) for r in out[: cnt.value]]
+
+
+def iplsGetLevelStats(ctx: int, reset: bool = False) -> list:
+    out = (iplsLevelStat * 16)()
+    cnt = ctypes.c_int32()
+    _check(load().iplsGetLevelStats(ctypes.c_void_p(ctx), out, 16, ctypes.byref(cnt),
+                                    1 if reset else 0), "iplsGetLevelStats")
+    return [dict(level=r.level, launches=r.launches, keys=r.keys, grid_ms=r.grid_ms,
                  bytes=r.bytes) for r in out[: cnt.value]]
 
 
@@ -317,6 +334,9 @@ class Context:
 
     def kernel_stats(self, reset: bool = False) -> list:
         return iplsGetKernelStats(self.ctx, reset)
+
+    def level_stats(self, reset: bool = False) -> list:
+        return iplsGetLevelStats(self.ctx, reset)
 
     def trace(self, as_array: bool = False):
         return iplsGetTrace(self.ctx, self.trace_cap, as_array)
