@@ -388,10 +388,19 @@ struct FitShared {
 // truncation by the shift (at most auf), the rounding of Bc and a margin;
 // crel*|v| covers the binary32 roundings of D, auf and the fma (three units
 // of 2^-24 and the binary64 model's own rounding, with room to spare).
+// The estimate is used only when the whole sample (so[0] .. so[N-1]) lies in
+// x_lo's binade, so that most keys take it; otherwise the fixed-point estimate
+// alone serves.
 template <class K>
-__device__ void same_binade_model(typename KT<K>::Bits xlo, int nb, double A, double Bc, LinModel* m) {
+__device__ void same_binade_model(typename KT<K>::Bits xlo, typename KT<K>::Ord s_first,
+                                  typename KT<K>::Ord s_last, int nb, double A, double Bc, LinModel* m) {
   using T = KT<K>;
   int ok = !T::special(xlo);
+  const typename T::Ord ulo = T::ord(xlo);
+  if (T::kMant > 0)
+    ok = ok && ((s_first ^ ulo) >> T::kMant) == 0 && ((s_last ^ ulo) >> T::kMant) == 0;
+  else
+    ok = ok && (uint64_t)(s_last - s_first) < (1ULL << 62);
   double q = 1.0;
   if (T::kMant > 0) {
     const int e = (int)(((uint64_t)xlo >> T::kMant) & T::kExpMask);
@@ -575,7 +584,7 @@ __device__ void fit_linear(const typename KT<K>::Ord* so, int N, int K_, LinMode
         m->bcf = __double2float_rn(Bc);
         m->crel = 0x1.0p-21f;
         m->cabs = cabs;
-        same_binade_model<K>(xlo, K_, A, Bc, m);
+        same_binade_model<K>(xlo, so[0], so[N - 1], K_, A, Bc, m);
       }
     }
   }
