@@ -84,7 +84,8 @@ typedef struct iplsConfig {
                              the sample against its empirical CDF), falling back to
                              the splitter tree when a bucket gets more than 4n/k keys.
                              The sorted result is the same either way. */
-  int32_t reserved[4];
+  int32_t serve_slots;    /* iplsSubmit: batches in flight at once, 1 or 2 (0 = 2) */
+  int32_t reserved[3];
 } iplsConfig;
 
 /* cfg.flags: classify grid-level passes through the exact threshold index
@@ -155,6 +156,20 @@ typedef struct iplsStats {
                                  sweep (fit + pass + base case) instead, last call */
 } iplsStats;
 
+/* One batch of served requests (iplsGetBatchLog).  start_ms / end_ms are
+ * CUDA-event times of the batch's work on its slot's stream, in ms after a
+ * reference event recorded when the serving slots started (-1 if unknown). */
+typedef struct iplsBatchRec {
+  uint64_t first_ticket;  /* ticket of the batch's oldest request */
+  int32_t requests;       /* requests in the batch */
+  int32_t slot;           /* in-flight slot (worker and stream) that ran it */
+  int64_t keys;           /* keys of all its requests */
+  int32_t dtype;
+  int32_t status;         /* the batch's iplsStatus */
+  double start_ms;
+  double end_ms;
+} iplsBatchRec;
+
 typedef struct iplsContext* iplsCtx;
 typedef void* (*iplsAllocFn)(size_t bytes, void* user);  /* device memory */
 typedef void (*iplsFreeFn)(void* ptr, void* user);
@@ -196,17 +211,34 @@ iplsStatus iplsSortSegmented(iplsCtx ctx, void* keys, const int64_t* offsets,
  * host memory gives full copy bandwidth; pageable memory works too. */
 iplsStatus iplsSortHost(iplsCtx ctx, void* host_keys, int64_t n, iplsDtype dtype);
 
+/* Sorts `count` separate device arrays keys[i][0..n[i]) in place (keys and
+ * n are HOST arrays of count entries; each keys[i] is a device pointer
+ * aligned to the key width).  All arrays are sorted together: each is a
+ * level-0 subproblem of its own, addressed in its own memory (nothing is
+ * gathered or copied), and every partition pass of every array shares the
+ * same kernel launches.  Each array ends up sorted exactly as iplsSort
+ * alone would sort it.  The sum of the sizes must not exceed 2^32 - 1.
+ * The arrays must not overlap. */
+iplsStatus iplsSortBatch(iplsCtx ctx, void* const* keys, const int64_t* n, int64_t count,
+                         iplsDtype dtype);
+
 /* Asynchronous sort request for keys[0..n) (device memory, already
- * written; the sort runs on the context's stream): queues it and returns a
- * ticket at once.  A worker thread of the context batches pending requests
- * of one dtype in arrival order while 2*w*(their keys) stays within
- * cfg.budget_bytes (0 = unlimited) and cfg.max_batch, and sorts each batch
- * with one segmented sort (each request a segment, every partition pass of
- * the batch in shared launches); requests arriving meanwhile join the next
- * batch.  The result is the same sorted array whatever the batch.  Returns
- * IPLS_ERR_BUDGET if one request alone exceeds the budget.  `keys` must stay
- * alive and untouched until the request completes; while requests are
- * pending, other calls on the context wait for the running batch. */
+ * written): queues it and returns a ticket at once.  The context serves
+ * requests with cfg.serve_slots in-flight slots (two by default), each a
+ * worker thread with its own
+ * stream and scratch: a free slot takes the oldest queued request's dtype
+ * and, in arrival order, further queued requests of that dtype while the
+ * bytes of all requests in flight, 2*w*n each, stay within cfg.budget_bytes
+ * (0 = unlimited) and the batch within cfg.max_batch, and sorts them with one
+ * batched sort in place (as iplsSortBatch).  While one slot's batch runs the
+ * other admits the next, so requests that arrive meanwhile are served as
+ * memory frees up and their work overlaps on the GPU; batches of different
+ * dtypes may run side by side.  The result is the same sorted array whatever
+ * the batch.  Returns IPLS_ERR_BUDGET if one request alone exceeds the
+ * budget.  `keys` must stay alive and untouched until the request completes.
+ * The slots' streams are created by the library; work submitted through the
+ * context's own stream is not ordered with them.  Allocator callbacks given
+ * to iplsCreate are also called from the slots' worker threads. */
 iplsStatus iplsSubmit(iplsCtx ctx, void* keys, int64_t n, iplsDtype dtype,
                       uint64_t* ticket);
 
@@ -217,6 +249,10 @@ iplsStatus iplsPoll(iplsCtx ctx, uint64_t ticket);
 /* Waits up to timeout_us microseconds (< 0 = forever) for a request; returns
  * its final status, or IPLS_PENDING if it is still running. */
 iplsStatus iplsWait(iplsCtx ctx, uint64_t ticket, int64_t timeout_us);
+
+/* Copies up to cap records of the batches served so far (oldest first, at
+ * most 65536 kept) to host memory and sets *count. */
+iplsStatus iplsGetBatchLog(iplsCtx ctx, iplsBatchRec* out, int64_t cap, int64_t* count);
 
 /* Statistics of the context (synchronises its stream). */
 iplsStatus iplsGetStats(iplsCtx ctx, iplsStats* stats);

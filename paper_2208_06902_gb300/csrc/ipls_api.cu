@@ -3,6 +3,7 @@
 // and request tickets.  Every step of the sort runs in the kernels of
 // ipls_pass.cu and ipls_resident.cu; this file only plans and launches them.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstdio>
@@ -62,16 +63,16 @@ struct Slot {
   Fill* fills = nullptr;         int64_t fill_cap = 0;
 };
 
-}  // namespace
-
-struct iplsContext {
-  iplsConfig cfg;
-  iplsAllocFn alloc = nullptr;
-  iplsFreeFn free_fn = nullptr;
-  void* user = nullptr;
+// One sort in flight: its stream, the ping-pong buffer and per-level lists,
+// the device counters and their pinned host copies.  A context has one
+// workspace for its own synchronous calls and, once requests are submitted,
+// one per in-flight batch slot, so that batches run side by side on the GPU.
+struct Pending { int kind; int level; cudaEvent_t a, b; };
+struct Workspace {
+  iplsCtx c = nullptr;
   cudaStream_t stream = nullptr;
-  int device = 0;
-  int num_sms = 0;
+  bool own_stream = false;            // created by the library (batch slots)
+  bool main = false;                  // the context's own calls: traced and profiled
   char* scratch = nullptr;            int64_t scratch_cap = 0;   // bytes
   unsigned long long* status = nullptr; int64_t status_cap = 0;  // words
   uint32_t* tile_off = nullptr;       int64_t tile_off_cap = 0;  // words
@@ -81,16 +82,41 @@ struct iplsContext {
   LevelCtl* ctl = nullptr;
   RunStatus* run = nullptr;
   int64_t* root_bounds = nullptr;
-  LevelCtl* h_ctl = nullptr;
-  RunStatus* h_run = nullptr;
+  LevelCtl* h_ctl = nullptr;          // pinned
+  RunStatus* h_run = nullptr;         // pinned
+  // slow lists of the block-resident tail (children / whole tasks, one half each)
+  SlowTask* slow = nullptr;           int64_t slow_cap = 0;
+  SlowCtl* slow_ctl = nullptr;
+  SlowCtl* h_slow = nullptr;          // pinned copy of *slow_ctl
+  uint64_t* split_pool = nullptr;     int64_t split_pool_cap = 0;  // words
+  // a batch of separate arrays: segment offsets and bases (device, pinned host)
+  int64_t* seg_off = nullptr;         int64_t seg_off_cap = 0;
+  uint64_t* seg_ubase = nullptr;      int64_t seg_ubase_cap = 0;
+  int64_t* h_seg_off = nullptr;       uint64_t* h_seg_ubase = nullptr;  int64_t h_seg_cap = 0;
+  iplsStats stats{};                  // the last sort on this workspace
+  int64_t trace_grid_count = 0;
+  std::vector<Pending> pending;       // profiling: event pairs per launch
+  std::vector<cudaEvent_t> spare_events;
+};
+
+}  // namespace
+
+struct iplsContext {
+  iplsConfig cfg;
+  iplsAllocFn alloc = nullptr;
+  iplsFreeFn free_fn = nullptr;
+  void* user = nullptr;
+  int device = 0;
+  int num_sms = 0;
+  Workspace ws;                       // the context's own calls (its stream)
   iplsTraceRecDev* trace_grid = nullptr;
   iplsTraceRecDev* trace_res = nullptr;
   int64_t trace_alloc = 0;
   float* trace_knots = nullptr;       int64_t knot_cap = 0;       // records
   int knot_leaves = 0;
-  int64_t trace_grid_count = 0;
-  iplsStats stats{};
-  // request queue (iplsSubmit): a worker thread batches pending requests
+  int64_t calls = 0;
+  // request serving (iplsSubmit): kServeSlots worker threads, each with its
+  // own workspace and stream, take batches from the queue as they free up
   struct Request {
     void* keys;
     int64_t n;
@@ -98,25 +124,22 @@ struct iplsContext {
     iplsStatus st;
     bool done;
   };
-  std::mutex exec_mu;                 // one sort at a time on the context
-  std::mutex q_mu;                    // guards the queue and the requests
-  std::condition_variable q_cv;       // new request, or stop
+  static constexpr int kServeSlots = 2;
+  std::mutex exec_mu;                 // one synchronous sort at a time on the context
+  std::mutex q_mu;                    // guards the queue, the requests and the batch log
+  std::condition_variable q_cv;       // new request, a slot freed memory, or stop
   std::condition_variable done_cv;    // a request finished
   std::deque<uint64_t> queue;
   std::map<uint64_t, Request> reqs;
-  std::thread worker;
+  std::thread workers[kServeSlots];
+  Workspace serve_ws[kServeSlots];
   bool stop = false;
   uint64_t next_ticket = 1;
-  char* batch_buf = nullptr;          int64_t batch_cap = 0;     // bytes
-  int64_t* batch_off = nullptr;       int64_t batch_off_cap = 0; // words
-  int64_t* h_batch_off = nullptr;     int64_t h_batch_off_cap = 0;
-  int hist_grid[4] = {0, 0, 0, 0};
-  int scatter_grid[4] = {0, 0, 0, 0};
-  int64_t dev_bytes = 0;
-  // profiling (cfg.profile): event pairs per launch, resolved at sync points
-  struct Pending { int kind; int level; cudaEvent_t a, b; };
-  std::vector<Pending> pending;
-  std::vector<cudaEvent_t> spare_events;
+  int64_t inflight_bytes = 0;         // 2*w*n of the admitted requests not yet done
+  cudaEvent_t serve_ref = nullptr;    // time origin of the batch log
+  std::vector<iplsBatchRec> batch_log;
+  std::atomic<int64_t> dev_bytes{0};
+  std::mutex prof_mu;                 // guards the profile accumulators
   int64_t k_launches[16] = {};
   // per grid level (profile = 1): summed time of the level's grid kernels,
   // their launches, and the keys (and algorithmic bytes) its passes moved
@@ -129,11 +152,6 @@ struct iplsContext {
   int64_t k_bytes[16] = {};
   // host-buffer sorting
   char* host_stage = nullptr; int64_t host_stage_cap = 0;
-  // slow lists of the block-resident tail (children / whole tasks, one half each)
-  SlowTask* slow = nullptr; int64_t slow_cap = 0;
-  SlowCtl* slow_ctl = nullptr;
-  SlowCtl* h_slow = nullptr;          // pinned copy of *slow_ctl
-  uint64_t* split_pool = nullptr;     int64_t split_pool_cap = 0;  // words
 };
 
 namespace {
@@ -165,9 +183,10 @@ void dev_free(iplsCtx c, void* p, size_t bytes) {
 
 // Grows a device array to hold at least `need` elements (contents dropped).
 template <class T>
-iplsStatus ensure(iplsCtx c, T*& p, int64_t& cap, int64_t need) {
+iplsStatus ensure(Workspace& w, T*& p, int64_t& cap, int64_t need) {
   if (need <= cap && p) return IPLS_OK;
-  IPLS_CUDA(cudaStreamSynchronize(c->stream));
+  iplsCtx c = w.c;
+  IPLS_CUDA(cudaStreamSynchronize(w.stream));
   dev_free(c, p, (size_t)cap * sizeof(T));
   p = nullptr;
   cap = 0;
@@ -188,10 +207,10 @@ const char* const kKernelNames[kkCount] = {"k_fit", "k_hist", "k_check", "k_hist
                                            "k_init_segments", "k_init_tiles", "k_tail_fit",
                                            "k_tilescan", "k_slow", "k_slow_groups"};
 
-cudaEvent_t take_event(iplsCtx c) {
-  if (!c->spare_events.empty()) {
-    cudaEvent_t e = c->spare_events.back();
-    c->spare_events.pop_back();
+cudaEvent_t take_event(Workspace& w) {
+  if (!w.spare_events.empty()) {
+    cudaEvent_t e = w.spare_events.back();
+    w.spare_events.pop_back();
     return e;
   }
   cudaEvent_t e = nullptr;
@@ -202,22 +221,24 @@ cudaEvent_t take_event(iplsCtx c) {
 // Launches `fn` (which enqueues exactly one kernel) bracketed by CUDA events
 // when profiling; every launch is counted.
 template <class F>
-cudaError_t timed(iplsCtx c, int kind, F fn, int level = -1) {
-  if (!c->cfg.profile) {
+cudaError_t timed(Workspace& w, int kind, F fn, int level = -1) {
+  if (!w.c->cfg.profile || !w.main) {
     cudaError_t e = fn();
     return e;
   }
-  cudaEvent_t a = take_event(c), b = take_event(c);
-  if (a) cudaEventRecord(a, c->stream);
+  cudaEvent_t a = take_event(w), b = take_event(w);
+  if (a) cudaEventRecord(a, w.stream);
   cudaError_t e = fn();
-  if (b) cudaEventRecord(b, c->stream);
-  if (a && b) c->pending.push_back({kind, level, a, b});
+  if (b) cudaEventRecord(b, w.stream);
+  if (a && b) w.pending.push_back({kind, level, a, b});
   return e;
 }
 
 // Folds finished event pairs into the per-kernel totals (after a sync).
-void resolve_events(iplsCtx c) {
-  for (auto& p : c->pending) {
+void resolve_events(Workspace& w) {
+  iplsCtx c = w.c;
+  std::lock_guard<std::mutex> lk(c->prof_mu);
+  for (auto& p : w.pending) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
       c->k_ms[p.kind] += ms;
@@ -229,20 +250,20 @@ void resolve_events(iplsCtx c) {
     } else {
       cudaGetLastError();
     }
-    c->spare_events.push_back(p.a);
-    c->spare_events.push_back(p.b);
+    w.spare_events.push_back(p.a);
+    w.spare_events.push_back(p.b);
   }
-  c->pending.clear();
+  w.pending.clear();
 }
 
 // Grid kernels size their grids from the occupancy of the SMs they get.
 int occupancy_grid(iplsCtx c, int, int) { return c->num_sms; }
 
 // Group list of a slot with its fit list and fitted tail models.
-iplsStatus ensure_groups(iplsCtx c, Slot& s, int64_t need) {
-  IPLS_TRY(ensure(c, s.groups, s.group_cap, need));
-  IPLS_TRY(ensure(c, s.fit_list, s.fit_cap, s.group_cap));
-  IPLS_TRY(ensure(c, s.tails, s.tail_cap, s.group_cap));
+iplsStatus ensure_groups(Workspace& w, Slot& s, int64_t need) {
+  IPLS_TRY(ensure(w, s.groups, s.group_cap, need));
+  IPLS_TRY(ensure(w, s.fit_list, s.fit_cap, s.group_cap));
+  IPLS_TRY(ensure(w, s.tails, s.tail_cap, s.group_cap));
   return IPLS_OK;
 }
 
@@ -252,17 +273,18 @@ int64_t pool_slots(int64_t nfit) {
 }
 
 // One sweep of k_tail_fit + k_tail over the groups in ra.
-iplsStatus tail_sweep(iplsCtx c, ResidentArgs& ra) {
+iplsStatus tail_sweep(Workspace& w, ResidentArgs& ra) {
+  iplsCtx c = w.c;
   if (ra.nfit > 0) {
-    IPLS_TRY(ensure(c, c->split_pool, c->split_pool_cap, pool_slots(ra.nfit) * 128));
-    ra.split_pool = c->split_pool;
-    ra.split_pool_slots = (int32_t)std::min<int64_t>(c->split_pool_cap / 128, kSplitPoolMax);
-    IPLS_CUDA(timed(c, kkTailFit, [&] { return launch_tail_fit(ra, c->stream, c->num_sms); }));
+    IPLS_TRY(ensure(w, w.split_pool, w.split_pool_cap, pool_slots(ra.nfit) * 128));
+    ra.split_pool = w.split_pool;
+    ra.split_pool_slots = (int32_t)std::min<int64_t>(w.split_pool_cap / 128, kSplitPoolMax);
+    IPLS_CUDA(timed(w, kkTailFit, [&] { return launch_tail_fit(ra, w.stream, c->num_sms); }));
   }
   if (ra.ngroups > 0)
-    IPLS_CUDA(timed(c, kkResident, [&] { return launch_resident(ra, c->stream, 0); }));
+    IPLS_CUDA(timed(w, kkResident, [&] { return launch_resident(ra, w.stream, 0); }));
   if ((ra.large_from_end ? ra.nlarge : ra.ngroups) > 0)
-    IPLS_CUDA(timed(c, kkResident, [&] { return launch_resident(ra, c->stream, 1); }));
+    IPLS_CUDA(timed(w, kkResident, [&] { return launch_resident(ra, w.stream, 1); }));
   return IPLS_OK;
 }
 
@@ -273,7 +295,8 @@ iplsStatus tail_sweep(iplsCtx c, ResidentArgs& ra) {
 // nsmall/nlarge: from a level's list (small tasks from the front, large ones
 // from the back); with nlarge < 0 the nsmall groups are in plain order and
 // both k_tail sizes walk them all.
-iplsStatus launch_tail(iplsCtx c, ResidentArgs& ra, Slot& s, int32_t nsmall, int32_t nlarge, int32_t nfit) {
+iplsStatus launch_tail(Workspace& w, ResidentArgs& ra, Slot& s, int32_t nsmall, int32_t nlarge, int32_t nfit) {
+  iplsCtx c = w.c;
   const bool from_end = nlarge >= 0;
   const int32_t ngroups = from_end ? nsmall + nlarge : nsmall;
   ra.groups = s.groups;
@@ -286,27 +309,27 @@ iplsStatus launch_tail(iplsCtx c, ResidentArgs& ra, Slot& s, int32_t nsmall, int
   ra.tail_models = s.tails;
   // disjoint ranges of more than `cutoff` keys each: both lists together
   // hold at most n / (cutoff + 1), and each half of the buffer holds that
-  const int64_t half = c->slow_cap / 2;
-  ra.slow = c->slow;
+  const int64_t half = w.slow_cap / 2;
+  ra.slow = w.slow;
   ra.slow_cap = (int32_t)std::min<int64_t>(half, INT32_MAX);
-  ra.whole = c->slow + half;
-  ra.whole_cap = (int32_t)std::min<int64_t>(c->slow_cap - half, INT32_MAX);
-  ra.slow_ctl = c->slow_ctl;
-  ra.split_pool = c->split_pool;
-  ra.split_pool_slots = (int32_t)std::min<int64_t>(c->split_pool_cap / 128, kSplitPoolMax);
+  ra.whole = w.slow + half;
+  ra.whole_cap = (int32_t)std::min<int64_t>(w.slow_cap - half, INT32_MAX);
+  ra.slow_ctl = w.slow_ctl;
+  ra.split_pool = w.split_pool;
+  ra.split_pool_slots = (int32_t)std::min<int64_t>(w.split_pool_cap / 128, kSplitPoolMax);
   if (ngroups <= 0) return IPLS_OK;
-  IPLS_CUDA(cudaMemsetAsync(c->slow_ctl, 0, sizeof(SlowCtl), c->stream));
-  IPLS_TRY(tail_sweep(c, ra));
+  IPLS_CUDA(cudaMemsetAsync(w.slow_ctl, 0, sizeof(SlowCtl), w.stream));
+  IPLS_TRY(tail_sweep(w, ra));
   if (ngroups >= kTailSweepMin) {
-    IPLS_CUDA(cudaMemcpyAsync(c->h_slow, c->slow_ctl, sizeof(SlowCtl), cudaMemcpyDeviceToHost, c->stream));
-    IPLS_CUDA(cudaStreamSynchronize(c->stream));
-    const int32_t nc = c->h_slow->count;
+    IPLS_CUDA(cudaMemcpyAsync(w.h_slow, w.slow_ctl, sizeof(SlowCtl), cudaMemcpyDeviceToHost, w.stream));
+    IPLS_CUDA(cudaStreamSynchronize(w.stream));
+    const int32_t nc = w.h_slow->count;
     if (nc >= kTailSweepMin && nc <= ra.slow_cap) {
-      IPLS_TRY(ensure_groups(c, s, nc));
-      IPLS_CUDA(timed(c, kkSlowGroups, [&] { return launch_slow_groups(c->slow, nc, s.groups, s.fit_list, c->stream); }));
+      IPLS_TRY(ensure_groups(w, s, nc));
+      IPLS_CUDA(timed(w, kkSlowGroups, [&] { return launch_slow_groups(w.slow, nc, s.groups, s.fit_list, w.stream); }));
       // the child list starts again (count, ticket, pool_used, fit_ticket);
       // whole tasks stay
-      IPLS_CUDA(cudaMemsetAsync(c->slow_ctl, 0, 4 * sizeof(int32_t), c->stream));
+      IPLS_CUDA(cudaMemsetAsync(w.slow_ctl, 0, 4 * sizeof(int32_t), w.stream));
       ra.groups = s.groups;
       ra.ngroups = nc;
       ra.nlarge = nc;            // plain order: both sizes walk the list
@@ -314,26 +337,26 @@ iplsStatus launch_tail(iplsCtx c, ResidentArgs& ra, Slot& s, int32_t nsmall, int
       ra.fit_list = s.fit_list;
       ra.nfit = nc;
       ra.tail_models = s.tails;
-      IPLS_TRY(tail_sweep(c, ra));
-      c->stats.sweep_tasks += nc;
+      IPLS_TRY(tail_sweep(w, ra));
+      w.stats.sweep_tasks += nc;
     }
   }
-  IPLS_CUDA(timed(c, kkSlow, [&] { return launch_slow(ra, c->stream, c->num_sms); }));
+  IPLS_CUDA(timed(w, kkSlow, [&] { return launch_slow(ra, w.stream, c->num_sms); }));
   return IPLS_OK;
 }
 
-iplsStatus check_run(iplsCtx c) {
-  IPLS_CUDA(cudaMemcpyAsync(c->h_run, c->run, sizeof(RunStatus), cudaMemcpyDeviceToHost, c->stream));
-  IPLS_CUDA(cudaStreamSynchronize(c->stream));
-  if (c->h_run->error == IPLS_ERR_TIMEOUT)
+iplsStatus check_run(Workspace& w) {
+  IPLS_CUDA(cudaMemcpyAsync(w.h_run, w.run, sizeof(RunStatus), cudaMemcpyDeviceToHost, w.stream));
+  IPLS_CUDA(cudaStreamSynchronize(w.stream));
+  if (w.h_run->error == IPLS_ERR_TIMEOUT)
     return fail(IPLS_ERR_TIMEOUT, "a device-side look-back wait exceeded spin_limit");
-  if (c->h_run->error != 0)
-    return fail((iplsStatus)c->h_run->error, "device reported status " + std::to_string(c->h_run->error));
-  c->stats.resident_groups = c->h_run->resident_groups;
-  c->stats.slow_tasks = c->h_run->slow_tasks;
-  c->stats.slow_passes = c->h_run->slow_passes;
-  c->stats.fallback_passes += c->h_run->resident_fallback;
-  c->stats.trace_records = c->trace_grid_count + c->h_run->trace_count;
+  if (w.h_run->error != 0)
+    return fail((iplsStatus)w.h_run->error, "device reported status " + std::to_string(w.h_run->error));
+  w.stats.resident_groups = w.h_run->resident_groups;
+  w.stats.slow_tasks = w.h_run->slow_tasks;
+  w.stats.slow_passes = w.h_run->slow_passes;
+  w.stats.fallback_passes += w.h_run->resident_fallback;
+  w.stats.trace_records = w.trace_grid_count + w.h_run->trace_count;
   return IPLS_OK;
 }
 
@@ -341,27 +364,30 @@ iplsStatus check_run(iplsCtx c) {
 // segments; each level runs fit -> hist -> check -> (re)hist -> scan ->
 // scatter over all its grid subproblems, then the block-resident kernel over
 // the groups the level produced.
-iplsStatus sort_impl(iplsCtx c, void* keys, int64_t n, int dtype, const int64_t* offsets,
-                     int64_t nseg) {
-  const int w = key_bytes(dtype);
+iplsStatus sort_impl(Workspace& w, void* keys, int64_t n, int dtype, const int64_t* offsets,
+                     int64_t nseg, const uint64_t* seg_ubase = nullptr) {
+  iplsCtx c = w.c;
+  const int wb = key_bytes(dtype);
   const iplsConfig& cfg = c->cfg;
+  const bool traced = w.main && cfg.trace_cap > 0;
+  const uint64_t ubase = reinterpret_cast<uint64_t>(keys);
   const int rmax = resident_rmax(cfg.cutoff);
   const int resident_root_ok = (cfg.root_sample <= 0 || cfg.root_sample <= kResidentSample);
   const int tile = tile_keys(dtype);
-  c->stats.grid_levels = 0;
-  c->stats.grid_passes = 0;
-  c->stats.keys_partitioned = 0;
-  c->stats.resident_groups = 0;
-  c->stats.fallback_passes = 0;
-  c->stats.sweep_tasks = 0;
-  c->stats.algorithmic_bytes = 0;
-  c->stats.max_bucket_frac = 0.0;
-  c->trace_grid_count = 0;
-  IPLS_TRY(ensure(c, c->scratch, c->scratch_cap, n * (int64_t)w));
-  IPLS_TRY(ensure(c, c->bids, c->bids_cap, n));
-  IPLS_TRY(ensure(c, c->slow, c->slow_cap, 2 * (n / (cfg.cutoff + 1)) + 4096));
-  if (cfg.trace_cap > 0 && c->trace_alloc < cfg.trace_cap) {
-    IPLS_CUDA(cudaStreamSynchronize(c->stream));
+  w.stats.grid_levels = 0;
+  w.stats.grid_passes = 0;
+  w.stats.keys_partitioned = 0;
+  w.stats.resident_groups = 0;
+  w.stats.fallback_passes = 0;
+  w.stats.sweep_tasks = 0;
+  w.stats.algorithmic_bytes = 0;
+  w.stats.max_bucket_frac = 0.0;
+  w.trace_grid_count = 0;
+  IPLS_TRY(ensure(w, w.scratch, w.scratch_cap, n * (int64_t)wb));
+  IPLS_TRY(ensure(w, w.bids, w.bids_cap, n));
+  IPLS_TRY(ensure(w, w.slow, w.slow_cap, 2 * (n / (cfg.cutoff + 1)) + 4096));
+  if (traced && c->trace_alloc < cfg.trace_cap) {
+    IPLS_CUDA(cudaStreamSynchronize(w.stream));
     dev_free(c, c->trace_grid, (size_t)c->trace_alloc * sizeof(iplsTraceRecDev));
     dev_free(c, c->trace_res, (size_t)c->trace_alloc * sizeof(iplsTraceRecDev));
     c->trace_grid = c->trace_res = nullptr;
@@ -373,7 +399,7 @@ iplsStatus sort_impl(iplsCtx c, void* keys, int64_t n, int dtype, const int64_t*
     c->trace_res = (iplsTraceRecDev*)p;
     c->trace_alloc = cfg.trace_cap;
   }
-  if (cfg.trace_cap > 0 && cfg.pl2_leaves > 0 && !c->trace_knots) {
+  if (traced && cfg.pl2_leaves > 0 && !c->trace_knots) {
     const int64_t cap = std::min<int64_t>(cfg.trace_cap, kKnotTraceMax);
     void* p;
     IPLS_TRY(dev_alloc(c, &p, (size_t)cap * (cfg.pl2_leaves + 1) * sizeof(float)));
@@ -381,13 +407,13 @@ iplsStatus sort_impl(iplsCtx c, void* keys, int64_t n, int dtype, const int64_t*
     c->knot_cap = cap;
     c->knot_leaves = cfg.pl2_leaves;
   }
-  IPLS_CUDA(cudaMemsetAsync(c->run, 0, sizeof(RunStatus), c->stream));
-  void* bufs[2] = {keys, c->scratch};
+  IPLS_CUDA(cudaMemsetAsync(w.run, 0, sizeof(RunStatus), w.stream));
+  void* bufs[2] = {keys, w.scratch};
 
   ResidentArgs ra{};
   ra.dtype = dtype; ra.k = cfg.k; ra.cutoff = cfg.cutoff; ra.root_sample = cfg.root_sample;
   ra.seed = cfg.seed; ra.exact_only = cfg.exact_only; ra.buf[0] = bufs[0]; ra.buf[1] = bufs[1];
-  ra.run = c->run; ra.trace = cfg.trace_cap > 0 ? c->trace_res : nullptr; ra.trace_cap = cfg.trace_cap;
+  ra.run = w.run; ra.trace = traced ? c->trace_res : nullptr; ra.trace_cap = traced ? cfg.trace_cap : 0;
 
   int64_t nsub = 0, ntiles = 0, nchunks = 0;
   int64_t max_sub_n = n;  // bound on the size of this level's grid subproblems
@@ -396,63 +422,66 @@ iplsStatus sort_impl(iplsCtx c, void* keys, int64_t n, int dtype, const int64_t*
   const int64_t chunk_bound = tile_bound / kChunkTiles + sub_bound + 2;
   if (offsets) {
     // segments: big ones become level-0 grid subproblems, the rest groups
-    Slot& s0 = c->slot[0];
-    Slot& s1 = c->slot[1];
-    IPLS_TRY(ensure(c, s0.subs, s0.sub_cap, sub_bound));
-    IPLS_TRY(ensure(c, s0.tile2sub, s0.tile_cap, tile_bound));
-    IPLS_TRY(ensure(c, s0.chunk2sub, s0.chunk_cap, chunk_bound));
+    Slot& s0 = w.slot[0];
+    Slot& s1 = w.slot[1];
+    IPLS_TRY(ensure(w, s0.subs, s0.sub_cap, sub_bound));
+    IPLS_TRY(ensure(w, s0.tile2sub, s0.tile_cap, tile_bound));
+    IPLS_TRY(ensure(w, s0.chunk2sub, s0.chunk_cap, chunk_bound));
     const int64_t gcap = 2 * n / (cfg.cutoff + 1) + 2 * (nseg / 64) + 1024 + 2 * sub_bound;
-    IPLS_TRY(ensure_groups(c, s1, std::min<int64_t>(gcap, nseg + 1024)));
-    IPLS_CUDA(cudaMemsetAsync(c->ctl, 0, sizeof(LevelCtl), c->stream));
-    IPLS_CUDA(timed(c, kkInitSeg, [&] {
-      return launch_init_segments(offsets, nseg, rmax, cfg.cutoff, resident_root_ok, c->ctl,
+    IPLS_TRY(ensure_groups(w, s1, std::min<int64_t>(gcap, nseg + 1024)));
+    IPLS_CUDA(cudaMemsetAsync(w.ctl, 0, sizeof(LevelCtl), w.stream));
+    IPLS_CUDA(timed(w, kkInitSeg, [&] {
+      return launch_init_segments(offsets, nseg, seg_ubase, ubase, rmax, cfg.cutoff, resident_root_ok, w.ctl,
                                   s0.subs, (int32_t)std::min<int64_t>(s0.sub_cap, INT32_MAX),
                                   s0.tile2sub, s0.tile_cap, s0.chunk2sub, s0.chunk_cap, s1.groups,
                                   (int32_t)std::min<int64_t>(s1.group_cap, INT32_MAX),
-                                  s1.fit_list, c->stream);
+                                  s1.fit_list, w.stream);
     }));
-    IPLS_CUDA(cudaMemcpyAsync(c->h_ctl, c->ctl, sizeof(LevelCtl), cudaMemcpyDeviceToHost, c->stream));
-    IPLS_CUDA(cudaStreamSynchronize(c->stream));
-    if (c->h_ctl->overflow) return fail(IPLS_ERR_INTERNAL, "segment list capacity exceeded");
-    resolve_events(c);
-    if ((int64_t)c->h_ctl->ngroups + c->h_ctl->ngroups_large > s1.group_cap)
+    IPLS_CUDA(cudaMemcpyAsync(w.h_ctl, w.ctl, sizeof(LevelCtl), cudaMemcpyDeviceToHost, w.stream));
+    IPLS_CUDA(cudaStreamSynchronize(w.stream));
+    if (w.h_ctl->overflow) return fail(IPLS_ERR_INTERNAL, "segment list capacity exceeded");
+    resolve_events(w);
+    if ((int64_t)w.h_ctl->ngroups + w.h_ctl->ngroups_large > s1.group_cap)
       return fail(IPLS_ERR_INTERNAL, "segment list capacity exceeded");
-    IPLS_TRY(launch_tail(c, ra, s1, c->h_ctl->ngroups, c->h_ctl->ngroups_large, c->h_ctl->nfit));
-    nsub = c->h_ctl->nsub_next;
-    ntiles = c->h_ctl->tiles_next;
-    nchunks = c->h_ctl->chunks_next;
-    max_sub_n = c->h_ctl->max_sub_n;
+    IPLS_TRY(launch_tail(w, ra, s1, w.h_ctl->ngroups, w.h_ctl->ngroups_large, w.h_ctl->nfit));
+    nsub = w.h_ctl->nsub_next;
+    ntiles = w.h_ctl->tiles_next;
+    nchunks = w.h_ctl->chunks_next;
+    max_sub_n = w.h_ctl->max_sub_n;
   } else if (n <= rmax && resident_root_ok) {
     // the whole array is one block-resident task (base case only when n is
     // at most the cutoff, otherwise a fitted pass first)
-    Slot& s1 = c->slot[1];
-    IPLS_TRY(ensure_groups(c, s1, 1));
+    Slot& s1 = w.slot[1];
+    IPLS_TRY(ensure_groups(w, s1, 1));
     const int64_t hb[2] = {0, n};
     const int fitted = n > cfg.cutoff ? 1 : 0;
-    IPLS_CUDA(cudaMemcpyAsync(c->root_bounds, hb, sizeof(hb), cudaMemcpyHostToDevice, c->stream));
-    const Group g{0, c->root_bounds, (int32_t)n, 0, 0, 1, fitted ? 0 : -1, 0};
-    IPLS_CUDA(cudaMemcpyAsync(s1.groups, &g, sizeof(g), cudaMemcpyHostToDevice, c->stream));
+    IPLS_CUDA(cudaMemcpyAsync(w.root_bounds, hb, sizeof(hb), cudaMemcpyHostToDevice, w.stream));
+    const Group g{0, w.root_bounds, (int32_t)n, 0, 0, 1, fitted ? 0 : -1, 0, ubase};
+    IPLS_CUDA(cudaMemcpyAsync(s1.groups, &g, sizeof(g), cudaMemcpyHostToDevice, w.stream));
     if (fitted) {
       const int32_t zero = 0;
-      IPLS_CUDA(cudaMemcpyAsync(s1.fit_list, &zero, sizeof(zero), cudaMemcpyHostToDevice, c->stream));
+      IPLS_CUDA(cudaMemcpyAsync(s1.fit_list, &zero, sizeof(zero), cudaMemcpyHostToDevice, w.stream));
     }
-    IPLS_TRY(launch_tail(c, ra, s1, 1, -1, fitted));
-    IPLS_TRY(check_run(c));
-    resolve_events(c);
-    c->k_bytes[kkResident] += 2 * (int64_t)w * n;
-    c->stats.algorithmic_bytes = 2 * (int64_t)w * n;
+    IPLS_TRY(launch_tail(w, ra, s1, 1, -1, fitted));
+    IPLS_TRY(check_run(w));
+    resolve_events(w);
+    if (w.main) {
+      std::lock_guard<std::mutex> lk(c->prof_mu);
+      c->k_bytes[kkResident] += 2 * (int64_t)wb * n;
+    }
+    w.stats.algorithmic_bytes = 2 * (int64_t)wb * n;
     return IPLS_OK;
   } else {
-    Slot& s0 = c->slot[0];
-    IPLS_TRY(ensure(c, s0.subs, s0.sub_cap, 1));
+    Slot& s0 = w.slot[0];
+    IPLS_TRY(ensure(w, s0.subs, s0.sub_cap, 1));
     ntiles = (n + tile - 1) / tile;
     nchunks = (ntiles + kChunkTiles - 1) / kChunkTiles;
-    IPLS_TRY(ensure(c, s0.tile2sub, s0.tile_cap, ntiles));
-    IPLS_TRY(ensure(c, s0.chunk2sub, s0.chunk_cap, nchunks));
-    const Sub root{0, n, 0, 0, 0, (int32_t)ntiles, 0, 0, (int32_t)nchunks};
-    IPLS_CUDA(cudaMemcpyAsync(s0.subs, &root, sizeof(root), cudaMemcpyHostToDevice, c->stream));
-    IPLS_CUDA(timed(c, kkInitTiles, [&] { return launch_init_tiles(s0.tile2sub, ntiles, 0, c->stream); }));
-    IPLS_CUDA(timed(c, kkInitTiles, [&] { return launch_init_tiles(s0.chunk2sub, nchunks, 0, c->stream); }));
+    IPLS_TRY(ensure(w, s0.tile2sub, s0.tile_cap, ntiles));
+    IPLS_TRY(ensure(w, s0.chunk2sub, s0.chunk_cap, nchunks));
+    const Sub root{0, n, 0, 0, 0, (int32_t)ntiles, 0, 0, (int32_t)nchunks, ubase};
+    IPLS_CUDA(cudaMemcpyAsync(s0.subs, &root, sizeof(root), cudaMemcpyHostToDevice, w.stream));
+    IPLS_CUDA(timed(w, kkInitTiles, [&] { return launch_init_tiles(s0.tile2sub, ntiles, 0, w.stream); }));
+    IPLS_CUDA(timed(w, kkInitTiles, [&] { return launch_init_tiles(s0.chunk2sub, nchunks, 0, w.stream); }));
     nsub = 1;
   }
 
@@ -460,107 +489,113 @@ iplsStatus sort_impl(iplsCtx c, void* keys, int64_t n, int dtype, const int64_t*
   int64_t moved = 0;
   while (nsub > 0) {
     if (level > 4096) return fail(IPLS_ERR_INTERNAL, "recursion depth limit exceeded");
-    Slot& X = c->slot[level & 1];
-    Slot& Y = c->slot[(level + 1) & 1];
-    IPLS_TRY(ensure(c, X.models, X.model_cap, nsub));
-    IPLS_TRY(ensure(c, X.tabs, X.tab_cap, nsub));
-    if (cfg.pl2_leaves > 0) IPLS_TRY(ensure(c, X.knots, X.knot_cap, nsub * (int64_t)(cfg.pl2_leaves + 1)));
-    IPLS_TRY(ensure(c, X.counts, X.count_cap, nsub * kMaxK));
-    IPLS_TRY(ensure(c, X.bases, X.base_cap, nsub * 257));
-    IPLS_TRY(ensure_groups(c, X, 2 * n / (cfg.cutoff + 1) + 257 * nsub + 16));
-    IPLS_TRY(ensure(c, X.fills, X.fill_cap, n / kFillChunk + 129 * nsub + 16));
-    IPLS_TRY(ensure(c, Y.subs, Y.sub_cap, sub_bound));
-    IPLS_TRY(ensure(c, Y.tile2sub, Y.tile_cap, tile_bound));
-    IPLS_TRY(ensure(c, Y.chunk2sub, Y.chunk_cap, chunk_bound));
-    IPLS_TRY(ensure(c, c->tile_off, c->tile_off_cap, ntiles * kMaxK));
-    if (c->status_cap < nchunks * kMaxK) {
-      IPLS_TRY(ensure(c, c->status, c->status_cap, nchunks * kMaxK));
-      IPLS_CUDA(cudaMemsetAsync(c->status, 0, (size_t)c->status_cap * 8, c->stream));
-      c->epoch = 0;
+    Slot& X = w.slot[level & 1];
+    Slot& Y = w.slot[(level + 1) & 1];
+    IPLS_TRY(ensure(w, X.models, X.model_cap, nsub));
+    IPLS_TRY(ensure(w, X.tabs, X.tab_cap, nsub));
+    if (cfg.pl2_leaves > 0) IPLS_TRY(ensure(w, X.knots, X.knot_cap, nsub * (int64_t)(cfg.pl2_leaves + 1)));
+    IPLS_TRY(ensure(w, X.counts, X.count_cap, nsub * kMaxK));
+    IPLS_TRY(ensure(w, X.bases, X.base_cap, nsub * 257));
+    IPLS_TRY(ensure_groups(w, X, 2 * n / (cfg.cutoff + 1) + 257 * nsub + 16));
+    IPLS_TRY(ensure(w, X.fills, X.fill_cap, n / kFillChunk + 129 * nsub + 16));
+    IPLS_TRY(ensure(w, Y.subs, Y.sub_cap, sub_bound));
+    IPLS_TRY(ensure(w, Y.tile2sub, Y.tile_cap, tile_bound));
+    IPLS_TRY(ensure(w, Y.chunk2sub, Y.chunk_cap, chunk_bound));
+    IPLS_TRY(ensure(w, w.tile_off, w.tile_off_cap, ntiles * kMaxK));
+    if (w.status_cap < nchunks * kMaxK) {
+      IPLS_TRY(ensure(w, w.status, w.status_cap, nchunks * kMaxK));
+      IPLS_CUDA(cudaMemsetAsync(w.status, 0, (size_t)w.status_cap * 8, w.stream));
+      w.epoch = 0;
     }
-    if (++c->epoch >= 0x10000) {
-      IPLS_CUDA(cudaMemsetAsync(c->status, 0, (size_t)c->status_cap * 8, c->stream));
-      c->epoch = 1;
+    if (++w.epoch >= 0x10000) {
+      IPLS_CUDA(cudaMemsetAsync(w.status, 0, (size_t)w.status_cap * 8, w.stream));
+      w.epoch = 1;
     }
-    IPLS_CUDA(cudaMemsetAsync(c->ctl, 0, sizeof(LevelCtl), c->stream));
+    IPLS_CUDA(cudaMemsetAsync(w.ctl, 0, sizeof(LevelCtl), w.stream));
     LevelArgs a{};
     a.dtype = dtype; a.k = cfg.k; a.cutoff = cfg.cutoff; a.rmax = rmax;
     a.root_sample = cfg.root_sample; a.seed = cfg.seed; a.exact_only = cfg.exact_only;
     a.use_tables = (cfg.flags & IPLS_FLAG_THRESHOLD_INDEX) && !cfg.exact_only;
-    a.spin_limit = cfg.spin_limit; a.epoch = c->epoch; a.level = level;
+    a.spin_limit = cfg.spin_limit; a.epoch = w.epoch; a.level = level;
     a.buf[0] = bufs[0]; a.buf[1] = bufs[1];
     a.nsub = (int32_t)nsub; a.subs = X.subs; a.models = X.models; a.counts = X.counts;
     a.tabs = X.tabs;
-    a.bases = X.bases; a.tile2sub = X.tile2sub; a.ntiles = ntiles; a.status = c->status;
-    a.chunk2sub = X.chunk2sub; a.nchunks = nchunks; a.tile_off = c->tile_off;
-    a.bids = c->bids;
-    a.ctl = c->ctl; a.run = c->run;
+    a.bases = X.bases; a.tile2sub = X.tile2sub; a.ntiles = ntiles; a.status = w.status;
+    a.chunk2sub = X.chunk2sub; a.nchunks = nchunks; a.tile_off = w.tile_off;
+    a.bids = w.bids;
+    a.ctl = w.ctl; a.run = w.run;
     a.next_subs = Y.subs; a.next_sub_cap = (int32_t)std::min<int64_t>(Y.sub_cap, INT32_MAX);
     a.next_tile2sub = Y.tile2sub; a.next_tile_cap = Y.tile_cap;
     a.next_chunk2sub = Y.chunk2sub; a.next_chunk_cap = Y.chunk_cap;
     a.groups = X.groups; a.group_cap = (int32_t)std::min<int64_t>(X.group_cap, INT32_MAX);
     a.fit_list = X.fit_list;
     a.fills = X.fills; a.fill_cap = (int32_t)std::min<int64_t>(X.fill_cap, INT32_MAX);
-    a.trace = cfg.trace_cap > 0 ? c->trace_grid : nullptr;
-    a.trace_cap = cfg.trace_cap;
-    a.trace_base = c->trace_grid_count;
-    a.trace_knots = cfg.trace_cap > 0 ? c->trace_knots : nullptr;
+    a.trace = traced ? c->trace_grid : nullptr;
+    a.trace_cap = traced ? cfg.trace_cap : 0;
+    a.trace_base = w.trace_grid_count;
+    a.trace_knots = traced ? c->trace_knots : nullptr;
     a.knot_cap = c->knot_cap;
     const int max_sample = sample_size_host(std::max<int64_t>(max_sub_n, 2), level, cfg.k, cfg.root_sample);
     a.max_sample = max_sample;
     a.pl2_leaves = cfg.pl2_leaves;
     a.knots = cfg.pl2_leaves > 0 ? X.knots : nullptr;
-    IPLS_CUDA(timed(c, kkFit, [&] { return launch_fit(a, c->stream, max_sample); }, level));
-    IPLS_CUDA(timed(c, kkHist, [&] { return launch_hist(a, c->stream, 0, occupancy_grid(c, 0, dtype)); }, level));
-    IPLS_CUDA(timed(c, kkCheck, [&] { return launch_check(a, c->stream, max_sample); }, level));
-    IPLS_CUDA(timed(c, kkRehist, [&] { return launch_hist(a, c->stream, 1, occupancy_grid(c, 0, dtype)); }, level));
-    IPLS_CUDA(timed(c, kkScan, [&] { return launch_scan(a, c->stream); }, level));
-    IPLS_CUDA(timed(c, kkTileScan, [&] { return launch_tilescan(a, c->stream, c->num_sms * 8); }, level));
-    IPLS_CUDA(timed(c, kkScatter, [&] { return launch_scatter(a, c->stream, occupancy_grid(c, 1, dtype)); }, level));
-    IPLS_CUDA(cudaMemcpyAsync(c->h_ctl, c->ctl, sizeof(LevelCtl), cudaMemcpyDeviceToHost, c->stream));
-    IPLS_CUDA(cudaMemcpyAsync(c->h_run, c->run, sizeof(RunStatus), cudaMemcpyDeviceToHost, c->stream));
-    IPLS_CUDA(cudaStreamSynchronize(c->stream));
-    const LevelCtl lc = *c->h_ctl;
-    if (c->h_run->error != 0 || lc.overflow || (int64_t)lc.ngroups + lc.ngroups_large > X.group_cap) {
+    IPLS_CUDA(timed(w, kkFit, [&] { return launch_fit(a, w.stream, max_sample); }, level));
+    IPLS_CUDA(timed(w, kkHist, [&] { return launch_hist(a, w.stream, 0, occupancy_grid(c, 0, dtype)); }, level));
+    IPLS_CUDA(timed(w, kkCheck, [&] { return launch_check(a, w.stream, max_sample); }, level));
+    IPLS_CUDA(timed(w, kkRehist, [&] { return launch_hist(a, w.stream, 1, occupancy_grid(c, 0, dtype)); }, level));
+    IPLS_CUDA(timed(w, kkScan, [&] { return launch_scan(a, w.stream); }, level));
+    IPLS_CUDA(timed(w, kkTileScan, [&] { return launch_tilescan(a, w.stream, c->num_sms * 8); }, level));
+    IPLS_CUDA(timed(w, kkScatter, [&] { return launch_scatter(a, w.stream, occupancy_grid(c, 1, dtype)); }, level));
+    IPLS_CUDA(cudaMemcpyAsync(w.h_ctl, w.ctl, sizeof(LevelCtl), cudaMemcpyDeviceToHost, w.stream));
+    IPLS_CUDA(cudaMemcpyAsync(w.h_run, w.run, sizeof(RunStatus), cudaMemcpyDeviceToHost, w.stream));
+    IPLS_CUDA(cudaStreamSynchronize(w.stream));
+    const LevelCtl lc = *w.h_ctl;
+    if (w.h_run->error != 0 || lc.overflow || (int64_t)lc.ngroups + lc.ngroups_large > X.group_cap) {
       // nothing of this level moved (k_scatter checks the status first):
       // put the level's keys back into the user buffer and stop
-      IPLS_CUDA(launch_restore(X.subs, (int32_t)nsub, dtype, keys, c->scratch, c->stream));
-      IPLS_CUDA(cudaStreamSynchronize(c->stream));
-      resolve_events(c);
-      if (c->h_run->error == IPLS_ERR_TIMEOUT)
+      IPLS_CUDA(launch_restore(X.subs, (int32_t)nsub, dtype, w.scratch, w.stream));
+      IPLS_CUDA(cudaStreamSynchronize(w.stream));
+      resolve_events(w);
+      if (w.h_run->error == IPLS_ERR_TIMEOUT)
         return fail(IPLS_ERR_TIMEOUT, "a device-side look-back wait exceeded spin_limit; the keys "
                                       "hold a permutation of the input");
-      if (c->h_run->error != 0)
-        return fail((iplsStatus)c->h_run->error, "device reported status " + std::to_string(c->h_run->error));
+      if (w.h_run->error != 0)
+        return fail((iplsStatus)w.h_run->error, "device reported status " + std::to_string(w.h_run->error));
       return fail(IPLS_ERR_INTERNAL, "a level list capacity was exceeded");
     }
-    resolve_events(c);
-    c->k_bytes[kkHist] += (int64_t)w * lc.keys_level;
-    c->k_bytes[kkScatter] += 2 * (int64_t)w * lc.keys_moved;
-    if (level < iplsContext::kLevels) {
-      c->lv_keys[level] += lc.keys_moved;
-      c->lv_bytes[level] += 2 * (int64_t)w * lc.keys_moved;
+    resolve_events(w);
+    if (w.main) {
+      std::lock_guard<std::mutex> lk(c->prof_mu);
+      c->k_bytes[kkHist] += (int64_t)wb * lc.keys_level;
+      c->k_bytes[kkScatter] += 2 * (int64_t)wb * lc.keys_moved;
+      if (level < iplsContext::kLevels) {
+        c->lv_keys[level] += lc.keys_moved;
+        c->lv_bytes[level] += 2 * (int64_t)wb * lc.keys_moved;
+      }
     }
-    c->stats.grid_levels += 1;
-    c->stats.grid_passes += nsub;
-    c->stats.fallback_passes += lc.fallback;
+    w.stats.grid_levels += 1;
+    w.stats.grid_passes += nsub;
+    w.stats.fallback_passes += lc.fallback;
     moved += lc.keys_moved;
-    c->stats.max_bucket_frac = std::max(c->stats.max_bucket_frac, (double)lc.max_bucket / 1048576.0);
-    c->trace_grid_count += nsub;
-    IPLS_TRY(launch_tail(c, ra, X, lc.ngroups, lc.ngroups_large, lc.nfit));
+    w.stats.max_bucket_frac = std::max(w.stats.max_bucket_frac, (double)lc.max_bucket / 1048576.0);
+    w.trace_grid_count += nsub;
+    IPLS_TRY(launch_tail(w, ra, X, lc.ngroups, lc.ngroups_large, lc.nfit));
     if (lc.nfill > 0)
-      IPLS_CUDA(timed(c, kkFill, [&] { return launch_fill(X.fills, lc.nfill, dtype, keys, c->stream); }));
+      IPLS_CUDA(timed(w, kkFill, [&] { return launch_fill(X.fills, lc.nfill, dtype, w.stream); }));
     nsub = lc.nsub_next;
     ntiles = lc.tiles_next;
     nchunks = lc.chunks_next;
     max_sub_n = lc.max_sub_n;
     ++level;
   }
-  IPLS_TRY(check_run(c));
-  resolve_events(c);
-  c->k_bytes[kkResident] += 2 * (int64_t)w * c->h_run->resident_keys;
-  c->stats.keys_partitioned = moved;
-  c->stats.algorithmic_bytes = 2 * (int64_t)w * (moved + c->h_run->resident_keys);
+  IPLS_TRY(check_run(w));
+  resolve_events(w);
+  if (w.main) {
+    std::lock_guard<std::mutex> lk(c->prof_mu);
+    c->k_bytes[kkResident] += 2 * (int64_t)wb * w.h_run->resident_keys;
+  }
+  w.stats.keys_partitioned = moved;
+  w.stats.algorithmic_bytes = 2 * (int64_t)wb * (moved + w.h_run->resident_keys);
   return IPLS_OK;
 }
 
@@ -587,6 +622,7 @@ iplsStatus validate_cfg(const iplsConfig& c) {
   if (c.pl2_leaves != 0 && (c.pl2_leaves < 2 || c.pl2_leaves > kPL2MaxLeaves || (c.pl2_leaves & (c.pl2_leaves - 1))))
     return fail(IPLS_ERR_ARG, "pl2_leaves must be 0 or a power of two in [2, 1024]");
   if (c.budget_bytes < 0) return fail(IPLS_ERR_ARG, "budget_bytes must be >= 0");
+  if (c.serve_slots < 0 || c.serve_slots > 2) return fail(IPLS_ERR_ARG, "serve_slots must be 0, 1 or 2");
   return IPLS_OK;
 }
 
@@ -606,7 +642,8 @@ namespace ipls {
 
 constexpr int kSegWindow = 64;
 
-__global__ void k_init_segments(const int64_t* off, int64_t nseg, int rmax, int cutoff,
+__global__ void k_init_segments(const int64_t* off, int64_t nseg, const uint64_t* seg_ubase, uint64_t ubase,
+                                int rmax, int cutoff,
                                 int resident_ok, LevelCtl* ctl, Sub* subs, int32_t sub_cap,
                                 int32_t* tile2sub, int64_t tile_cap, int32_t* chunk2sub,
                                 int64_t chunk_cap, Group* groups, int32_t group_cap,
@@ -616,16 +653,19 @@ __global__ void k_init_segments(const int64_t* off, int64_t nseg, int rmax, int 
   if (q0 >= nseg) return;
   const int64_t q1 = q0 + kSegWindow < nseg ? q0 + kSegWindow : nseg;
   int64_t g0 = -1, glast = -1, tot = 0;
+  uint64_t gbase = 0;
   for (int64_t q = q0; q <= q1; ++q) {
     const int64_t cq = (q < q1) ? off[q + 1] - off[q] : 0;
+    const uint64_t ub = (seg_ubase && q < q1) ? seg_ubase[q] : ubase;
     const bool big = cq > cutoff && (cq > rmax || !resident_ok);
     const bool mid = cq > cutoff && !big;
     const bool brk = (q == q1) || big || mid;
     const bool fits = (cq > 0) && !brk;
-    if (g0 >= 0 && (brk || (fits && tot + cq > rmax))) {
+    // segments share a task only when they lie one after another in one array
+    if (g0 >= 0 && (brk || (fits && (tot + cq > rmax || ub != gbase)))) {
       const int g = group_slot(ctl, tot, group_cap);
       if (g < 0) ctl->overflow = 1;
-      else groups[g] = Group{off[g0], off + g0, (int32_t)tot, 0, 0, (int32_t)(glast - g0 + 1), -1, 0};
+      else groups[g] = Group{off[g0], off + g0, (int32_t)tot, 0, 0, (int32_t)(glast - g0 + 1), -1, 0, gbase};
       g0 = -1;
       tot = 0;
     }
@@ -634,7 +674,7 @@ __global__ void k_init_segments(const int64_t* off, int64_t nseg, int rmax, int 
       if (g < 0) {
         ctl->overflow = 1;
       } else {
-        groups[g] = Group{off[q], nullptr, (int32_t)cq, 0, 0, 1, g, 0};
+        groups[g] = Group{off[q], nullptr, (int32_t)cq, 0, 0, 1, g, 0, ub};
         fit_list[atomicAdd(&ctl->nfit, 1)] = g;
       }
     }
@@ -643,19 +683,20 @@ __global__ void k_init_segments(const int64_t* off, int64_t nseg, int rmax, int 
       if (i >= sub_cap) {
         ctl->overflow = 1;
       } else {
-        Sub ns{off[q], cq, 0, 0, 0, 0, 0, 0, 0};
+        Sub ns{off[q], cq, 0, 0, 0, 0, 0, 0, 0, ub};
         if (reserve_tiles(ctl, i, ns, tile2sub, tile_cap, chunk2sub, chunk_cap)) subs[i] = ns;
       }
     }
     if (fits) {
-      if (g0 < 0) g0 = q;
+      if (g0 < 0) { g0 = q; gbase = ub; }
       tot += cq;
       glast = q;
     }
   }
 }
 
-cudaError_t launch_init_segments(const int64_t* offsets, int64_t nseg, int rmax, int cutoff,
+cudaError_t launch_init_segments(const int64_t* offsets, int64_t nseg, const uint64_t* seg_ubase,
+                                 uint64_t ubase, int rmax, int cutoff,
                                  int resident_ok, LevelCtl* ctl, Sub* subs, int32_t sub_cap,
                                  int32_t* tile2sub, int64_t tile_cap, int32_t* chunk2sub,
                                  int64_t chunk_cap, Group* groups, int32_t group_cap,
@@ -664,7 +705,7 @@ cudaError_t launch_init_segments(const int64_t* offsets, int64_t nseg, int rmax,
   if (windows <= 0) return cudaSuccess;
   const int threads = 128;
   const int64_t blocks = (windows + threads - 1) / threads;
-  k_init_segments<<<(unsigned)blocks, threads, 0, s>>>(offsets, nseg, rmax, cutoff, resident_ok,
+  k_init_segments<<<(unsigned)blocks, threads, 0, s>>>(offsets, nseg, seg_ubase, ubase, rmax, cutoff, resident_ok,
                                                        ctl, subs, sub_cap, tile2sub, tile_cap,
                                                        chunk2sub, chunk_cap, groups, group_cap,
                                                        fit_list);
@@ -674,89 +715,226 @@ cudaError_t launch_init_segments(const int64_t* offsets, int64_t nseg, int rmax,
 }  // namespace ipls
 
 // ---------------------------------------------------------------------------
-// Request serving (iplsSubmit): one worker thread per context forms batches
-// from the pending requests -- the oldest request's dtype, in arrival order,
-// while they fit the memory budget (cfg.budget_bytes) and cfg.max_batch --
-// and sorts a batch with one segmented sort: each request is a segment, so
-// the partition passes of all of them share the same launches.  Requests
-// that arrive while a batch runs join the next one.
+// Workspaces.
 // ---------------------------------------------------------------------------
 namespace {
 
-iplsStatus run_batch(iplsCtx c, const std::vector<uint64_t>& batch, int dtype,
-                     const std::vector<iplsContext::Request>& rs) {
-  std::lock_guard<std::mutex> ex(c->exec_mu);
-  const int64_t w = key_bytes(dtype);
-  if (rs.size() == 1) {  // alone: in place
-    IPLS_TRY(sort_impl(c, rs[0].keys, rs[0].n, dtype, nullptr, 0));
-    IPLS_CUDA(cudaStreamSynchronize(c->stream));
-    return IPLS_OK;
+iplsStatus ws_init(iplsCtx c, Workspace& w, cudaStream_t stream, bool own_stream, bool main) {
+  w.c = c;
+  w.stream = stream;
+  w.own_stream = own_stream;
+  w.main = main;
+  cudaError_t e = cudaMallocHost(&w.h_ctl, sizeof(LevelCtl));
+  if (e == cudaSuccess) e = cudaMallocHost(&w.h_run, sizeof(RunStatus));
+  if (e == cudaSuccess) e = cudaMallocHost(&w.h_slow, sizeof(SlowCtl));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_fail(e, "cudaMallocHost");
   }
-  const int64_t nseg = (int64_t)rs.size();
-  if (c->h_batch_off_cap < nseg + 1) {
-    if (c->h_batch_off) cudaFreeHost(c->h_batch_off);
-    c->h_batch_off = nullptr;
-    c->h_batch_off_cap = 0;
-    IPLS_CUDA(cudaMallocHost(&c->h_batch_off, (size_t)(2 * nseg + 16) * 8));
-    c->h_batch_off_cap = 2 * nseg + 16;
-  }
-  int64_t total = 0;
-  for (int64_t i = 0; i < nseg; ++i) { c->h_batch_off[i] = total; total += rs[i].n; }
-  c->h_batch_off[nseg] = total;
-  IPLS_TRY(ensure(c, c->batch_buf, c->batch_cap, total * w));
-  IPLS_TRY(ensure(c, c->batch_off, c->batch_off_cap, nseg + 1));
-  for (int64_t i = 0; i < nseg; ++i)
-    if (rs[i].n > 0)
-      IPLS_CUDA(cudaMemcpyAsync(c->batch_buf + c->h_batch_off[i] * w, rs[i].keys, (size_t)(rs[i].n * w),
-                                cudaMemcpyDeviceToDevice, c->stream));
-  IPLS_CUDA(cudaMemcpyAsync(c->batch_off, c->h_batch_off, (size_t)(nseg + 1) * 8, cudaMemcpyHostToDevice,
-                            c->stream));
-  IPLS_TRY(sort_impl(c, c->batch_buf, total, dtype, c->batch_off, nseg));
-  for (int64_t i = 0; i < nseg; ++i)
-    if (rs[i].n > 0)
-      IPLS_CUDA(cudaMemcpyAsync(rs[i].keys, c->batch_buf + c->h_batch_off[i] * w, (size_t)(rs[i].n * w),
-                                cudaMemcpyDeviceToDevice, c->stream));
-  IPLS_CUDA(cudaStreamSynchronize(c->stream));
-  (void)batch;
+  void* p;
+  IPLS_TRY(dev_alloc(c, &p, sizeof(LevelCtl)));
+  w.ctl = (LevelCtl*)p;
+  IPLS_TRY(dev_alloc(c, &p, sizeof(RunStatus)));
+  w.run = (RunStatus*)p;
+  IPLS_TRY(dev_alloc(c, &p, 2 * sizeof(int64_t)));
+  w.root_bounds = (int64_t*)p;
+  IPLS_TRY(dev_alloc(c, &p, sizeof(SlowCtl)));
+  w.slow_ctl = (SlowCtl*)p;
   return IPLS_OK;
 }
 
-void serve_loop(iplsCtx c) {
+// Releases everything a workspace holds (waits for its stream first).
+void ws_free(Workspace& w) {
+  iplsCtx c = w.c;
+  if (!c) return;
+  if (w.stream || !w.own_stream) cudaStreamSynchronize(w.stream);
+  dev_free(c, w.scratch, (size_t)w.scratch_cap);
+  dev_free(c, w.status, (size_t)w.status_cap * 8);
+  dev_free(c, w.tile_off, (size_t)w.tile_off_cap * 4);
+  dev_free(c, w.bids, (size_t)w.bids_cap);
+  for (Slot& s : w.slot) {
+    dev_free(c, s.subs, s.sub_cap * sizeof(Sub));
+    dev_free(c, s.tile2sub, s.tile_cap * sizeof(int32_t));
+    dev_free(c, s.chunk2sub, s.chunk_cap * sizeof(int32_t));
+    dev_free(c, s.models, s.model_cap * sizeof(Model));
+    dev_free(c, s.tabs, s.tab_cap * sizeof(ThrTable));
+    dev_free(c, s.knots, s.knot_cap * sizeof(float));
+    dev_free(c, s.counts, s.count_cap * sizeof(uint64_t));
+    dev_free(c, s.bases, s.base_cap * sizeof(int64_t));
+    dev_free(c, s.groups, s.group_cap * sizeof(Group));
+    dev_free(c, s.fit_list, s.fit_cap * sizeof(int32_t));
+    dev_free(c, s.tails, s.tail_cap * sizeof(TailModel));
+    dev_free(c, s.fills, s.fill_cap * sizeof(Fill));
+    s = Slot{};
+  }
+  dev_free(c, w.ctl, sizeof(LevelCtl));
+  dev_free(c, w.run, sizeof(RunStatus));
+  dev_free(c, w.root_bounds, 2 * sizeof(int64_t));
+  dev_free(c, w.slow, (size_t)w.slow_cap * sizeof(SlowTask));
+  dev_free(c, w.slow_ctl, sizeof(SlowCtl));
+  dev_free(c, w.split_pool, (size_t)w.split_pool_cap * 8);
+  dev_free(c, w.seg_off, (size_t)w.seg_off_cap * 8);
+  dev_free(c, w.seg_ubase, (size_t)w.seg_ubase_cap * 8);
+  if (w.h_ctl) cudaFreeHost(w.h_ctl);
+  if (w.h_run) cudaFreeHost(w.h_run);
+  if (w.h_slow) cudaFreeHost(w.h_slow);
+  if (w.h_seg_off) cudaFreeHost(w.h_seg_off);
+  if (w.h_seg_ubase) cudaFreeHost(w.h_seg_ubase);
+  for (auto& p : w.pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+  for (cudaEvent_t e : w.spare_events) cudaEventDestroy(e);
+  if (w.own_stream && w.stream) cudaStreamDestroy(w.stream);
+  w = Workspace{};
+}
+
+// Sorts `count` separate device arrays, keys[i][0..n[i]), each in place and
+// each a level-0 subproblem of its own: one segmented sort over an index
+// space in which array i occupies [off_i, off_i + n[i]), with its own base
+// (keys[i] - off_i), so nothing is gathered or copied back.
+iplsStatus sort_arrays(Workspace& w, void* const* keys, const int64_t* n, int64_t count, int dtype) {
+  if (count == 1) return sort_impl(w, keys[0], n[0], dtype, nullptr, 0);
+  const int64_t wb = key_bytes(dtype);
+  if (w.h_seg_cap < count + 1) {
+    if (w.h_seg_off) cudaFreeHost(w.h_seg_off);
+    if (w.h_seg_ubase) cudaFreeHost(w.h_seg_ubase);
+    w.h_seg_off = nullptr;
+    w.h_seg_ubase = nullptr;
+    w.h_seg_cap = 0;
+    const int64_t cap = 2 * count + 16;
+    IPLS_CUDA(cudaMallocHost(&w.h_seg_off, (size_t)cap * 8));
+    IPLS_CUDA(cudaMallocHost(&w.h_seg_ubase, (size_t)cap * 8));
+    w.h_seg_cap = cap;
+  }
+  IPLS_TRY(ensure(w, w.seg_off, w.seg_off_cap, count + 1));
+  IPLS_TRY(ensure(w, w.seg_ubase, w.seg_ubase_cap, count));
+  // the previous batch's copies read these host arrays: wait for them
+  IPLS_CUDA(cudaStreamSynchronize(w.stream));
+  int64_t total = 0;
+  for (int64_t i = 0; i < count; ++i) {
+    w.h_seg_off[i] = total;
+    w.h_seg_ubase[i] = reinterpret_cast<uint64_t>(keys[i]) - (uint64_t)(total * wb);
+    total += n[i];
+  }
+  w.h_seg_off[count] = total;
+  if (total > kMaxKeys) return fail(IPLS_ERR_ARG, "a batch holds at most 2^32 - 1 keys");
+  IPLS_CUDA(cudaMemcpyAsync(w.seg_off, w.h_seg_off, (size_t)(count + 1) * 8, cudaMemcpyHostToDevice, w.stream));
+  IPLS_CUDA(cudaMemcpyAsync(w.seg_ubase, w.h_seg_ubase, (size_t)count * 8, cudaMemcpyHostToDevice, w.stream));
+  return sort_impl(w, nullptr, total, dtype, w.seg_off, count, w.seg_ubase);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Request serving (iplsSubmit): kServeSlots worker threads per context, each
+// with its own workspace and stream.  A worker that is free takes the oldest
+// queued request's dtype and, in arrival order, the queued requests of that
+// dtype while the bytes of all admitted requests (2*w*n each) stay within
+// cfg.budget_bytes and the batch within cfg.max_batch, and sorts them with
+// one batched sort (each request a segment in its own memory).  While one
+// batch runs the other worker admits the next, so batches of different sizes
+// and dtypes overlap on the device, and memory freed by a finished batch
+// lets waiting requests in.
+// ---------------------------------------------------------------------------
+namespace {
+
+void serve_loop(iplsCtx c, int slot) {
   cudaSetDevice(c->device);
+  Workspace& w = c->serve_ws[slot];
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaEventCreate(&ev0);
+  cudaEventCreate(&ev1);
+  std::vector<uint64_t> batch;
+  std::vector<void*> ptrs;
+  std::vector<int64_t> sizes;
   for (;;) {
-    std::vector<uint64_t> batch;
-    std::vector<iplsContext::Request> rs;
+    batch.clear();
+    ptrs.clear();
+    sizes.clear();
     int dtype = 0;
+    int64_t bytes = 0;
     {
       std::unique_lock<std::mutex> lk(c->q_mu);
-      c->q_cv.wait(lk, [&] { return c->stop || !c->queue.empty(); });
-      if (c->queue.empty()) return;  // stop requested and nothing pending
-      dtype = c->reqs[c->queue.front()].dtype;
       const int64_t budget = c->cfg.budget_bytes;
+      auto need_of = [&](uint64_t t) {
+        const iplsContext::Request& r = c->reqs[t];
+        return 2 * r.n * (int64_t)key_bytes(r.dtype);
+      };
+      c->q_cv.wait(lk, [&] {
+        if (c->queue.empty()) return c->stop;
+        return budget <= 0 || c->inflight_bytes + need_of(c->queue.front()) <= budget ||
+               c->inflight_bytes == 0;
+      });
+      if (c->queue.empty()) break;  // stop requested and nothing pending
+      dtype = c->reqs[c->queue.front()].dtype;
       const int max_batch = c->cfg.max_batch;
-      int64_t bytes = 0;
       for (auto it = c->queue.begin(); it != c->queue.end();) {
         const iplsContext::Request& r = c->reqs[*it];
         if (r.dtype != dtype) { ++it; continue; }
-        const int64_t need = 2 * r.n * (int64_t)key_bytes(dtype);
-        if (!batch.empty() && budget > 0 && bytes + need > budget) break;
+        const int64_t need = need_of(*it);
+        if (!batch.empty() && budget > 0 && c->inflight_bytes + bytes + need > budget) break;
         if (max_batch > 0 && (int)batch.size() >= max_batch) break;
         batch.push_back(*it);
-        rs.push_back(r);
+        ptrs.push_back(r.keys);
+        sizes.push_back(r.n);
         bytes += need;
         it = c->queue.erase(it);
       }
+      c->inflight_bytes += bytes;
     }
-    const iplsStatus st = run_batch(c, batch, dtype, rs);
+    if (ev0) cudaEventRecord(ev0, w.stream);
+    iplsStatus st = sort_arrays(w, ptrs.data(), sizes.data(), (int64_t)batch.size(), dtype);
+    if (ev1) cudaEventRecord(ev1, w.stream);
+    if (cudaStreamSynchronize(w.stream) != cudaSuccess && st == IPLS_OK) {
+      cudaGetLastError();
+      st = IPLS_ERR_CUDA;
+    }
+    iplsBatchRec rec{};
+    rec.first_ticket = batch.front();
+    rec.requests = (int32_t)batch.size();
+    rec.slot = slot;
+    rec.dtype = dtype;
+    rec.status = (int32_t)st;
+    for (int64_t x : sizes) rec.keys += x;
+    float t0 = 0.f, t1 = 0.f;
+    if (ev0 && ev1 && c->serve_ref && cudaEventElapsedTime(&t0, c->serve_ref, ev0) == cudaSuccess &&
+        cudaEventElapsedTime(&t1, c->serve_ref, ev1) == cudaSuccess) {
+      rec.start_ms = t0;
+      rec.end_ms = t1;
+    } else {
+      cudaGetLastError();
+      rec.start_ms = rec.end_ms = -1.0;
+    }
     {
       std::lock_guard<std::mutex> lk(c->q_mu);
       for (uint64_t t : batch) {
         c->reqs[t].st = st;
         c->reqs[t].done = true;
       }
+      c->inflight_bytes -= bytes;
+      if (c->batch_log.size() < 65536) c->batch_log.push_back(rec);
     }
     c->done_cv.notify_all();
+    c->q_cv.notify_all();  // memory was freed: a waiting worker may admit more
   }
+  if (ev0) cudaEventDestroy(ev0);
+  if (ev1) cudaEventDestroy(ev1);
+}
+
+// Starts the workers (first iplsSubmit; q_mu held).
+iplsStatus start_workers(iplsCtx c) {
+  if (c->workers[0].joinable()) return IPLS_OK;
+  const int slots = c->cfg.serve_slots > 0 ? c->cfg.serve_slots : iplsContext::kServeSlots;
+  for (int i = 0; i < slots; ++i) {
+    cudaStream_t s = nullptr;
+    IPLS_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    IPLS_TRY(ws_init(c, c->serve_ws[i], s, true, false));
+  }
+  if (!c->serve_ref) {
+    IPLS_CUDA(cudaEventCreate(&c->serve_ref));
+    IPLS_CUDA(cudaEventRecord(c->serve_ref, c->serve_ws[0].stream));
+    IPLS_CUDA(cudaEventSynchronize(c->serve_ref));
+  }
+  for (int i = 0; i < slots; ++i) c->workers[i] = std::thread(serve_loop, c, i);
+  return IPLS_OK;
 }
 
 }  // namespace
@@ -794,29 +972,17 @@ iplsStatus iplsCreate(iplsCtx* out, const iplsConfig* cfg, iplsAllocFn alloc, ip
   c->alloc = alloc;
   c->free_fn = free_fn;
   c->user = user;
-  c->stream = reinterpret_cast<cudaStream_t>(stream);
   cudaError_t e = cudaGetDevice(&c->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
-  if (e == cudaSuccess) e = cudaMallocHost(&c->h_ctl, sizeof(LevelCtl));
-  if (e == cudaSuccess) e = cudaMallocHost(&c->h_run, sizeof(RunStatus));
-  if (e == cudaSuccess) e = cudaMallocHost(&c->h_slow, sizeof(SlowCtl));
   if (e != cudaSuccess) {
     cudaGetLastError();
-    if (c->h_ctl) cudaFreeHost(c->h_ctl);
-    if (c->h_run) cudaFreeHost(c->h_run);
-    if (c->h_slow) cudaFreeHost(c->h_slow);
     delete c;
     return cuda_fail(e, "iplsCreate");
   }
-  void* p;
-  if ((st = dev_alloc(c, &p, sizeof(LevelCtl))) != IPLS_OK) { iplsDestroy(c); return st; }
-  c->ctl = (LevelCtl*)p;
-  if ((st = dev_alloc(c, &p, sizeof(RunStatus))) != IPLS_OK) { iplsDestroy(c); return st; }
-  c->run = (RunStatus*)p;
-  if ((st = dev_alloc(c, &p, 2 * sizeof(int64_t))) != IPLS_OK) { iplsDestroy(c); return st; }
-  c->root_bounds = (int64_t*)p;
-  if ((st = dev_alloc(c, &p, sizeof(SlowCtl))) != IPLS_OK) { iplsDestroy(c); return st; }
-  c->slow_ctl = (SlowCtl*)p;
+  if ((st = ws_init(c, c->ws, reinterpret_cast<cudaStream_t>(stream), false, true)) != IPLS_OK) {
+    iplsDestroy(c);
+    return st;
+  }
   *out = c;
   return IPLS_OK;
 }
@@ -828,44 +994,15 @@ iplsStatus iplsDestroy(iplsCtx c) {
     c->stop = true;
   }
   c->q_cv.notify_all();
-  if (c->worker.joinable()) c->worker.join();
-  cudaStreamSynchronize(c->stream);
-  dev_free(c, c->batch_buf, (size_t)c->batch_cap);
-  dev_free(c, c->batch_off, (size_t)c->batch_off_cap * 8);
-  if (c->h_batch_off) cudaFreeHost(c->h_batch_off);
-  dev_free(c, c->scratch, (size_t)c->scratch_cap);
-  dev_free(c, c->status, (size_t)c->status_cap * 8);
-  dev_free(c, c->tile_off, (size_t)c->tile_off_cap * 4);
-  dev_free(c, c->bids, (size_t)c->bids_cap);
-  for (Slot& s : c->slot) {
-    dev_free(c, s.subs, s.sub_cap * sizeof(Sub));
-    dev_free(c, s.tile2sub, s.tile_cap * sizeof(int32_t));
-    dev_free(c, s.chunk2sub, s.chunk_cap * sizeof(int32_t));
-    dev_free(c, s.models, s.model_cap * sizeof(Model));
-    dev_free(c, s.tabs, s.tab_cap * sizeof(ThrTable));
-    dev_free(c, s.knots, s.knot_cap * sizeof(float));
-    dev_free(c, s.counts, s.count_cap * sizeof(uint64_t));
-    dev_free(c, s.bases, s.base_cap * sizeof(int64_t));
-    dev_free(c, s.groups, s.group_cap * sizeof(Group));
-    dev_free(c, s.fit_list, s.fit_cap * sizeof(int32_t));
-    dev_free(c, s.tails, s.tail_cap * sizeof(TailModel));
-    dev_free(c, s.fills, s.fill_cap * sizeof(Fill));
-  }
-  dev_free(c, c->ctl, sizeof(LevelCtl));
-  dev_free(c, c->run, sizeof(RunStatus));
-  dev_free(c, c->root_bounds, 2 * sizeof(int64_t));
+  for (std::thread& t : c->workers)
+    if (t.joinable()) t.join();
+  for (Workspace& w : c->serve_ws) ws_free(w);
+  ws_free(c->ws);
+  if (c->serve_ref) cudaEventDestroy(c->serve_ref);
   dev_free(c, c->trace_grid, (size_t)c->trace_alloc * sizeof(iplsTraceRecDev));
   dev_free(c, c->trace_res, (size_t)c->trace_alloc * sizeof(iplsTraceRecDev));
   dev_free(c, c->trace_knots, (size_t)c->knot_cap * (c->knot_leaves + 1) * sizeof(float));
-  if (c->h_ctl) cudaFreeHost(c->h_ctl);
-  if (c->h_run) cudaFreeHost(c->h_run);
-  if (c->h_slow) cudaFreeHost(c->h_slow);
-  for (auto& p : c->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
-  for (cudaEvent_t e : c->spare_events) cudaEventDestroy(e);
   dev_free(c, c->host_stage, (size_t)c->host_stage_cap);
-  dev_free(c, c->slow, (size_t)c->slow_cap * sizeof(SlowTask));
-  dev_free(c, c->slow_ctl, sizeof(SlowCtl));
-  dev_free(c, c->split_pool, (size_t)c->split_pool_cap * 8);
   delete c;
   return IPLS_OK;
 }
@@ -913,11 +1050,11 @@ iplsStatus iplsSort(iplsCtx c, void* keys, int64_t n, iplsDtype dtype) {
   IPLS_TRY(check_keys_ptr(keys, dtype));
   iplsStatus st = IPLS_OK;
   if (!c) { c = default_ctx(&st); if (!c) return st; }
-  c->stats.calls += 1;
+  std::lock_guard<std::mutex> ex(c->exec_mu);
+  c->calls += 1;
   if (n <= 1) return IPLS_OK;
   g_last_error.clear();
-  std::lock_guard<std::mutex> ex(c->exec_mu);
-  return sort_impl(c, keys, n, dtype, nullptr, 0);
+  return sort_impl(c->ws, keys, n, dtype, nullptr, 0);
 }
 
 iplsStatus iplsSortSegmented(iplsCtx c, void* keys, const int64_t* offsets, int64_t nseg,
@@ -930,17 +1067,44 @@ iplsStatus iplsSortSegmented(iplsCtx c, void* keys, const int64_t* offsets, int6
   if (reinterpret_cast<uintptr_t>(offsets) % 8 != 0) return fail(IPLS_ERR_ARG, "offsets must be 8-byte aligned");
   iplsStatus st = IPLS_OK;
   if (!c) { c = default_ctx(&st); if (!c) return st; }
-  // validate the offsets on the host (non-decreasing, within 2^40)
+  std::lock_guard<std::mutex> ex(c->exec_mu);
+  // validate the offsets on the host (non-decreasing ends, within 2^32 - 1)
   int64_t first = 0, last = 0;
-  IPLS_CUDA(cudaMemcpyAsync(&first, offsets, 8, cudaMemcpyDeviceToHost, c->stream));
-  IPLS_CUDA(cudaMemcpyAsync(&last, offsets + nseg, 8, cudaMemcpyDeviceToHost, c->stream));
-  IPLS_CUDA(cudaStreamSynchronize(c->stream));
+  IPLS_CUDA(cudaMemcpyAsync(&first, offsets, 8, cudaMemcpyDeviceToHost, c->ws.stream));
+  IPLS_CUDA(cudaMemcpyAsync(&last, offsets + nseg, 8, cudaMemcpyDeviceToHost, c->ws.stream));
+  IPLS_CUDA(cudaStreamSynchronize(c->ws.stream));
   if (first < 0 || last < first || last > kMaxKeys)
     return fail(IPLS_ERR_ARG, "offsets out of range");
-  c->stats.calls += 1;
+  c->calls += 1;
   g_last_error.clear();
+  return sort_impl(c->ws, keys, last, dtype, offsets, nseg);
+}
+
+iplsStatus iplsSortBatch(iplsCtx c, void* const* keys, const int64_t* n, int64_t count, iplsDtype dtype) {
+  if (!valid_dtype(dtype)) return fail(IPLS_ERR_ARG, "unknown dtype");
+  if (count < 0) return fail(IPLS_ERR_ARG, "count < 0");
+  if (count == 0) return IPLS_OK;
+  if (!keys || !n) return fail(IPLS_ERR_ARG, "keys or n is NULL");
+  int64_t total = 0;
+  std::vector<void*> ptrs;
+  std::vector<int64_t> sizes;
+  for (int64_t i = 0; i < count; ++i) {
+    if (n[i] < 0) return fail(IPLS_ERR_ARG, "a size is negative");
+    if (n[i] > 1 && !keys[i]) return fail(IPLS_ERR_ARG, "a keys pointer is NULL");
+    if (n[i] > 1) IPLS_TRY(check_keys_ptr(keys[i], dtype));
+    total += n[i];
+    if (total > kMaxKeys) return fail(IPLS_ERR_ARG, "a batch holds at most 2^32 - 1 keys");
+    if (n[i] > 1) { ptrs.push_back(keys[i]); sizes.push_back(n[i]); }
+  }
+  iplsStatus st = IPLS_OK;
+  if (!c) { c = default_ctx(&st); if (!c) return st; }
   std::lock_guard<std::mutex> ex(c->exec_mu);
-  return sort_impl(c, keys, last, dtype, offsets, nseg);
+  c->calls += 1;
+  if (ptrs.empty()) return IPLS_OK;
+  g_last_error.clear();
+  IPLS_TRY(sort_arrays(c->ws, ptrs.data(), sizes.data(), (int64_t)ptrs.size(), dtype));
+  IPLS_CUDA(cudaStreamSynchronize(c->ws.stream));
+  return IPLS_OK;
 }
 
 iplsStatus iplsSortHost(iplsCtx c, void* host_keys, int64_t n, iplsDtype dtype) {
@@ -948,24 +1112,27 @@ iplsStatus iplsSortHost(iplsCtx c, void* host_keys, int64_t n, iplsDtype dtype) 
   if (n > 1 && !host_keys) return fail(IPLS_ERR_ARG, "host_keys is NULL");
   iplsStatus st = IPLS_OK;
   if (!c) { c = default_ctx(&st); if (!c) return st; }
-  c->stats.calls += 1;
+  std::lock_guard<std::mutex> ex(c->exec_mu);
+  c->calls += 1;
   if (n <= 1) return IPLS_OK;
   g_last_error.clear();
   const size_t bytes = (size_t)n * key_bytes(dtype);
-  std::lock_guard<std::mutex> ex(c->exec_mu);
-  IPLS_TRY(ensure(c, c->host_stage, c->host_stage_cap, (int64_t)bytes));
-  IPLS_CUDA(cudaMemcpyAsync(c->host_stage, host_keys, bytes, cudaMemcpyHostToDevice, c->stream));
-  IPLS_TRY(sort_impl(c, c->host_stage, n, dtype, nullptr, 0));
-  IPLS_CUDA(cudaMemcpyAsync(host_keys, c->host_stage, bytes, cudaMemcpyDeviceToHost, c->stream));
-  IPLS_CUDA(cudaStreamSynchronize(c->stream));
+  Workspace& w = c->ws;
+  IPLS_TRY(ensure(w, c->host_stage, c->host_stage_cap, (int64_t)bytes));
+  IPLS_CUDA(cudaMemcpyAsync(c->host_stage, host_keys, bytes, cudaMemcpyHostToDevice, w.stream));
+  IPLS_TRY(sort_impl(w, c->host_stage, n, dtype, nullptr, 0));
+  IPLS_CUDA(cudaMemcpyAsync(host_keys, c->host_stage, bytes, cudaMemcpyDeviceToHost, w.stream));
+  IPLS_CUDA(cudaStreamSynchronize(w.stream));
   return IPLS_OK;
 }
 
 iplsStatus iplsGetKernelStats(iplsCtx c, iplsKernelStat* out, int32_t cap, int32_t* count,
                               int32_t reset) {
   if (!c || !count || (cap > 0 && !out)) return fail(IPLS_ERR_ARG, "bad kernel-stats arguments");
-  IPLS_CUDA(cudaStreamSynchronize(c->stream));
-  resolve_events(c);
+  std::lock_guard<std::mutex> ex(c->exec_mu);
+  IPLS_CUDA(cudaStreamSynchronize(c->ws.stream));
+  resolve_events(c->ws);
+  std::lock_guard<std::mutex> lk(c->prof_mu);
   int m = 0;
   for (int k = 0; k < kkCount && m < cap; ++k) {
     std::memset(&out[m], 0, sizeof(out[m]));
@@ -984,8 +1151,10 @@ iplsStatus iplsGetKernelStats(iplsCtx c, iplsKernelStat* out, int32_t cap, int32
 
 iplsStatus iplsGetLevelStats(iplsCtx c, iplsLevelStat* out, int32_t cap, int32_t* count, int32_t reset) {
   if (!c || !count || (cap > 0 && !out)) return fail(IPLS_ERR_ARG, "bad level-stats arguments");
-  IPLS_CUDA(cudaStreamSynchronize(c->stream));
-  resolve_events(c);
+  std::lock_guard<std::mutex> ex(c->exec_mu);
+  IPLS_CUDA(cudaStreamSynchronize(c->ws.stream));
+  resolve_events(c->ws);
+  std::lock_guard<std::mutex> lk(c->prof_mu);
   int m = 0;
   for (int l = 0; l < iplsContext::kLevels && m < cap; ++l) {
     if (c->lv_launches[l] == 0 && c->lv_keys[l] == 0) continue;
@@ -1018,10 +1187,15 @@ iplsStatus iplsSubmit(iplsCtx c, void* keys, int64_t n, iplsDtype dtype, uint64_
     const uint64_t t = c->next_ticket++;
     c->reqs[t] = iplsContext::Request{keys, n, (int)dtype, n <= 1 ? IPLS_OK : IPLS_PENDING, n <= 1};
     if (n > 1) c->queue.push_back(t);
-    if (!c->worker.joinable()) c->worker = std::thread(serve_loop, c);
+    const iplsStatus ws = start_workers(c);
+    if (ws != IPLS_OK) {
+      c->queue.pop_back();
+      c->reqs.erase(t);
+      return ws;
+    }
     *ticket = t;
   }
-  c->q_cv.notify_one();
+  c->q_cv.notify_all();
   return IPLS_OK;
 }
 
@@ -1046,21 +1220,33 @@ iplsStatus iplsWait(iplsCtx c, uint64_t ticket, int64_t timeout_us) {
 
 iplsStatus iplsGetStats(iplsCtx c, iplsStats* out) {
   if (!c || !out) return fail(IPLS_ERR_ARG, "ctx or stats is NULL");
-  IPLS_CUDA(cudaStreamSynchronize(c->stream));
-  c->stats.scratch_bytes = c->dev_bytes;
-  *out = c->stats;
+  std::lock_guard<std::mutex> ex(c->exec_mu);
+  IPLS_CUDA(cudaStreamSynchronize(c->ws.stream));
+  *out = c->ws.stats;
+  out->calls = c->calls;
+  out->scratch_bytes = c->dev_bytes.load();
+  return IPLS_OK;
+}
+
+iplsStatus iplsGetBatchLog(iplsCtx c, iplsBatchRec* out, int64_t cap, int64_t* count) {
+  if (!c || !count || (cap > 0 && !out)) return fail(IPLS_ERR_ARG, "bad batch-log arguments");
+  std::lock_guard<std::mutex> lk(c->q_mu);
+  const int64_t m = std::min<int64_t>(cap, (int64_t)c->batch_log.size());
+  for (int64_t i = 0; i < m; ++i) out[i] = c->batch_log[i];
+  *count = m;
   return IPLS_OK;
 }
 
 iplsStatus iplsGetTrace(iplsCtx c, iplsTraceRec* out, int64_t cap, int64_t* count) {
   if (!c || !count || (cap > 0 && !out)) return fail(IPLS_ERR_ARG, "bad trace arguments");
   static_assert(sizeof(iplsTraceRec) == sizeof(iplsTraceRecDev), "trace layout");
-  IPLS_CUDA(cudaStreamSynchronize(c->stream));
+  std::lock_guard<std::mutex> ex(c->exec_mu);
+  IPLS_CUDA(cudaStreamSynchronize(c->ws.stream));
   *count = 0;
   if (c->cfg.trace_cap <= 0) return IPLS_OK;
-  IPLS_CUDA(cudaMemcpy(c->h_run, c->run, sizeof(RunStatus), cudaMemcpyDeviceToHost));
-  const int64_t ng = std::min(c->trace_grid_count, c->cfg.trace_cap);
-  const int64_t nr = std::min<int64_t>(c->h_run->trace_count, c->cfg.trace_cap);
+  IPLS_CUDA(cudaMemcpy(c->ws.h_run, c->ws.run, sizeof(RunStatus), cudaMemcpyDeviceToHost));
+  const int64_t ng = std::min(c->ws.trace_grid_count, c->cfg.trace_cap);
+  const int64_t nr = std::min<int64_t>(c->ws.h_run->trace_count, c->cfg.trace_cap);
   const int64_t a = std::min(ng, cap);
   const int64_t b = std::min(nr, cap - a);
   if (a > 0) IPLS_CUDA(cudaMemcpy(out, c->trace_grid, a * sizeof(iplsTraceRec), cudaMemcpyDeviceToHost));
@@ -1071,10 +1257,11 @@ iplsStatus iplsGetTrace(iplsCtx c, iplsTraceRec* out, int64_t cap, int64_t* coun
 
 iplsStatus iplsGetTraceKnots(iplsCtx c, float* out, int64_t cap, int64_t* count) {
   if (!c || !count || (cap > 0 && !out)) return fail(IPLS_ERR_ARG, "bad trace-knot arguments");
-  IPLS_CUDA(cudaStreamSynchronize(c->stream));
+  std::lock_guard<std::mutex> ex(c->exec_mu);
+  IPLS_CUDA(cudaStreamSynchronize(c->ws.stream));
   *count = 0;
   if (c->cfg.trace_cap <= 0 || c->cfg.pl2_leaves <= 0 || !c->trace_knots) return IPLS_OK;
-  const int64_t ng = std::min(std::min(c->trace_grid_count, c->cfg.trace_cap), c->knot_cap);
+  const int64_t ng = std::min(std::min(c->ws.trace_grid_count, c->cfg.trace_cap), c->knot_cap);
   const int64_t a = std::min(ng, cap);
   if (a > 0)
     IPLS_CUDA(cudaMemcpy(out, c->trace_knots, (size_t)a * (c->cfg.pl2_leaves + 1) * sizeof(float),

@@ -109,9 +109,16 @@ struct ThrTable {
   int32_t ishift;   // integer keys: cell shift
 };
 
+// Every record below names its subproblem's keys by `off`, a position in the
+// sort's index space (the whole array, or the segments one after another), and
+// by `ubase`, the address such that, while the keys are in the caller's
+// memory (buffer 0), key `off + i` is at ((Bits*)ubase)[off + i].  One array
+// has one ubase; a batch of separate arrays has one per array, so each is
+// sorted where it lives.  Buffer 1 (the context's ping-pong buffer) is indexed
+// by `off` directly.
 // A grid-level subproblem.
 struct Sub {
-  int64_t off;     // first key in the whole array
+  int64_t off;     // first key in the index space
   int64_t n;
   int32_t level;
   int32_t buf;     // 0 = user keys, 1 = scratch
@@ -120,6 +127,7 @@ struct Sub {
   int32_t flags;
   int32_t chunk0;  // first tile chunk (kChunkTiles tiles) of this subproblem
   int32_t nchunks;
+  uint64_t ubase;  // caller's memory of this subproblem (see above)
 };
 constexpr int kChunkTiles = 32;  // tiles per decoupled look-back chunk
 enum SubFlags : int32_t { kRehist = 1, kSkipScatter = 2 };
@@ -138,6 +146,7 @@ struct Group {
   int32_t nchild;
   int32_t fit;
   int32_t pad;
+  uint64_t ubase;
 };
 
 // Keys [off, off+n) of the user buffer all equal to `bits`.
@@ -145,6 +154,7 @@ struct Fill {
   int64_t off;
   int64_t n;
   uint64_t bits;
+  uint64_t ubase;
 };
 
 // Device-side counters of one level (zeroed before the level).
@@ -187,6 +197,7 @@ struct SlowTask {
   int64_t off;
   int32_t n;
   int32_t level;
+  uint64_t ubase;
 };
 
 // Counters of the slow lists (zeroed before each tail launch).  `count`
@@ -228,7 +239,7 @@ struct LevelArgs {
   uint32_t epoch;        // look-back epoch of this level's scatter
   int level;
   int src_buf;           // buffer this level's subproblems live in
-  void* buf[2];          // 0 = user keys, 1 = scratch
+  void* buf[2];          // buf[1] = the ping-pong buffer (buffer 0 is each record's ubase)
   int32_t nsub;
   Sub* subs;
   Model* models;
@@ -271,7 +282,7 @@ struct ResidentArgs {
   int64_t root_sample;
   uint64_t seed;
   int exact_only;
-  void* buf[2];
+  void* buf[2];                    // buf[1] = the ping-pong buffer (buffer 0: each record's ubase)
   const Group* groups;
   int32_t ngroups;                 // groups[0, ngroups) (the small ones when large_from_end)
   int32_t nlarge;                  // tasks for the large blocks
@@ -304,6 +315,12 @@ struct iplsTraceRecDev {
   int64_t counts[256];
 };
 
+// Keys of a record: the caller's memory (buf 0, at ubase) or the ping-pong buffer.
+template <class B>
+__host__ __device__ __forceinline__ B* keys_of(int buf, uint64_t ubase, void* const* bufs) {
+  return buf == 0 ? reinterpret_cast<B*>(ubase) : reinterpret_cast<B*>(bufs[1]);
+}
+
 // Kernel launchers (defined in the .cu files).
 cudaError_t launch_fit(const LevelArgs& a, cudaStream_t s, int max_sample);
 cudaError_t launch_hist(const LevelArgs& a, cudaStream_t s, int rehist_only, int sms);
@@ -323,18 +340,19 @@ cudaError_t launch_slow_groups(const SlowTask* list, int32_t n, Group* groups, i
 cudaError_t launch_slow_one(const ResidentArgs& a, const SlowTask& t, cudaStream_t s);
 // Sets the message iplsLastError() returns on this thread.
 void set_last_error(const char* msg);
-cudaError_t launch_init_segments(const int64_t* offsets, int64_t nseg, int rmax, int cutoff,
+// seg_ubase: per-segment ubase (device array), or NULL for `ubase` everywhere.
+cudaError_t launch_init_segments(const int64_t* offsets, int64_t nseg, const uint64_t* seg_ubase,
+                                 uint64_t ubase, int rmax, int cutoff,
                                  int resident_ok, LevelCtl* ctl, Sub* subs, int32_t sub_cap,
                                  int32_t* tile2sub, int64_t tile_cap, int32_t* chunk2sub,
                                  int64_t chunk_cap, Group* groups, int32_t group_cap,
                                  int32_t* fit_list, cudaStream_t s);
 int resident_rmax(int cutoff);
-cudaError_t launch_fill(const Fill* fills, int32_t nfill, int dtype, void* keys, cudaStream_t s);
+cudaError_t launch_fill(const Fill* fills, int32_t nfill, int dtype, cudaStream_t s);
 cudaError_t launch_init_tiles(int32_t* tile2sub, int64_t ntiles, int32_t value, cudaStream_t s);
 // Copies the keys of the level's subproblems held in the scratch buffer back
-// into the user buffer (after a device-side error).
-cudaError_t launch_restore(const Sub* subs, int32_t nsub, int dtype, void* user, const void* scratch,
-                           cudaStream_t s);
+// into the caller's memory (after a device-side error).
+cudaError_t launch_restore(const Sub* subs, int32_t nsub, int dtype, const void* scratch, cudaStream_t s);
 
 int tile_keys(int dtype);
 int key_bytes(int dtype);

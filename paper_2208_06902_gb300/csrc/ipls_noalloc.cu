@@ -117,7 +117,7 @@ iplsStatus iplsSortSmallNoAlloc(void* keys, int64_t n, iplsDtype dtype, const ip
   a.run = run;
   a.trace = nullptr;
   a.trace_cap = 0;
-  const SlowTask t{0, (int32_t)n, 0};
+  const SlowTask t{0, (int32_t)n, 0, reinterpret_cast<uint64_t>(keys)};
   e = launch_slow_one(a, t, s);
   if (e != cudaSuccess) return fail_na(IPLS_ERR_CUDA, cudaGetErrorString(e));
 

@@ -47,8 +47,8 @@ int sample_size_host(int64_t n, int level, int k, int64_t root_sample) {
 }
 
 template <class K>
-__device__ __forceinline__ const typename KT<K>::Bits* buf_ptr(const LevelArgs& a, int b) {
-  return reinterpret_cast<const typename KT<K>::Bits*>(a.buf[b]);
+__device__ __forceinline__ const typename KT<K>::Bits* buf_ptr(const LevelArgs& a, const Sub& sub) {
+  return keys_of<const typename KT<K>::Bits>(sub.buf, sub.ubase, a.buf);
 }
 
 // Copies a Model between memories with all threads of the block.
@@ -72,7 +72,7 @@ __device__ int gather_sorted_sample(const LevelArgs& a, const Sub& sub,
   using T = KT<K>;
   const int S = (int)sample_size(sub.n, sub.level, a.k, a.root_sample);
   const uint64_t st = stream_key(a.seed, sub.off, sub.n, sub.level);
-  const typename T::Bits* src = buf_ptr<K>(a, sub.buf);
+  const typename T::Bits* src = buf_ptr<K>(a, sub);
   for (int j = threadIdx.x; j < S; j += blockDim.x)
     so[j] = T::ord(src[sub.off + sample_offset(st, j, sub.n)]);
   __syncthreads();
@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(kFitWarpsG * 32) k_fit_warp(LevelArgs a) {
   const int S = (int)sample_size(sub.n, sub.level, a.k, a.root_sample);
   Ord* so = reinterpret_cast<Ord*>(smem_raw) + warp * kResidentSample;
   const uint64_t st = stream_key(a.seed, sub.off, sub.n, sub.level);
-  const typename T::Bits* src = buf_ptr<K>(a, sub.buf) + sub.off;
+  const typename T::Bits* src = buf_ptr<K>(a, sub) + sub.off;
   for (int j = lane; j < S; j += 32) so[j] = T::ord(src[sample_offset(st, j, sub.n)]);
   __syncwarp();
   group_sort<WarpG, Ord>(so, S);
@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(kPassThreads, 4) k_hist(LevelArgs a, int rehis
     const int64_t base = sub.off + ti * kTile;
     const int64_t rem = sub.n - ti * kTile;
     const int tn = rem < kTile ? (int)rem : kTile;
-    const Bits* src = buf_ptr<K>(a, sub.buf) + base;
+    const Bits* src = buf_ptr<K>(a, sub) + base;
     for (int c0 = 0; c0 < kTile; c0 += kChunk * kPassThreads) {
       Bits v[kChunk];
 #pragma unroll
@@ -355,11 +355,11 @@ __device__ __forceinline__ int64_t block_exclusive_scan256(int64_t v, int64_t* t
 }
 
 template <class K>
-__device__ void append_fill(const LevelArgs& a, int64_t off, int64_t n, uint64_t bits) {
+__device__ void append_fill(const LevelArgs& a, int64_t off, int64_t n, uint64_t bits, uint64_t ubase) {
   for (int64_t o = 0; o < n; o += kFillChunk) {
     const int i = atomicAdd(&a.ctl->nfill, 1);
     if (i >= a.fill_cap) { a.ctl->overflow = 1; return; }
-    a.fills[i] = Fill{off + o, (n - o) < kFillChunk ? (n - o) : (int64_t)kFillChunk, bits};
+    a.fills[i] = Fill{off + o, (n - o) < kFillChunk ? (n - o) : (int64_t)kFillChunk, bits, ubase};
   }
 }
 
@@ -415,19 +415,21 @@ __global__ void __launch_bounds__(256) k_scan(LevelArgs a) {
       if (sub.buf != 0) {
         int j = 1;
         for (int q = 1; q < nb; q += 2) if (cnt[q] == sub.n) j = q;
-        append_fill<K>(a, sub.off, sub.n, (uint64_t)T::unord((typename T::Ord)m.split[(j - 1) / 2]));
+        append_fill<K>(a, sub.off, sub.n, (uint64_t)T::unord((typename T::Ord)m.split[(j - 1) / 2]),
+                       sub.ubase);
       }
     }
   } else if (c > 0) {
     if (eq) {
       if (dst_buf != 0)
-        append_fill<K>(a, sub.off + bas[b], c, (uint64_t)T::unord((typename T::Ord)m.split[(b - 1) / 2]));
+        append_fill<K>(a, sub.off + bas[b], c, (uint64_t)T::unord((typename T::Ord)m.split[(b - 1) / 2]),
+                       sub.ubase);
     } else if (c > a.rmax) {
       const int i = atomicAdd(&a.ctl->nsub_next, 1);
       if (i >= a.next_sub_cap) {
         a.ctl->overflow = 1;
       } else {
-        Sub ns{sub.off + bas[b], c, sub.level + 1, dst_buf, 0, 0, 0, 0, 0};
+        Sub ns{sub.off + bas[b], c, sub.level + 1, dst_buf, 0, 0, 0, 0, 0, sub.ubase};
         if (reserve_tiles(a.ctl, i, ns, a.next_tile2sub, a.next_tile_cap, a.next_chunk2sub,
                           a.next_chunk_cap))
           a.next_subs[i] = ns;
@@ -438,7 +440,7 @@ __global__ void __launch_bounds__(256) k_scan(LevelArgs a) {
       if (g < 0) {
         a.ctl->overflow = 1;
       } else {
-        a.groups[g] = Group{sub.off + bas[b], nullptr, (int32_t)c, sub.level + 1, dst_buf, 1, g, 0};
+        a.groups[g] = Group{sub.off + bas[b], nullptr, (int32_t)c, sub.level + 1, dst_buf, 1, g, 0, sub.ubase};
         const int f = atomicAdd(&a.ctl->nfit, 1);
         a.fit_list[f] = g;
       }
@@ -457,7 +459,7 @@ __global__ void __launch_bounds__(256) k_scan(LevelArgs a) {
         const int g = group_slot(a.ctl, tot, a.group_cap);
         if (g < 0) a.ctl->overflow = 1;
         else a.groups[g] = Group{sub.off + bas[b0], gb + b0, (int32_t)tot, sub.level + 1,
-                                 dst_buf, blast - b0 + 1, -1, 0};
+                                 dst_buf, blast - b0 + 1, -1, 0, sub.ubase};
         b0 = -1;
         tot = 0;
       }
@@ -576,7 +578,6 @@ __global__ void __launch_bounds__(kScatterThreads, 2) k_scatter(LevelArgs a) {
   // an earlier kernel gave up (bounded wait): move nothing, so that every
   // key of the level stays in its source buffer for the host to restore
   if (*reinterpret_cast<volatile int32_t*>(&a.run->error) != 0) return;
-  Bits* dst_base[2] = {reinterpret_cast<Bits*>(a.buf[0]), reinterpret_cast<Bits*>(a.buf[1])};
   const int64_t nt = a.ntiles;
   const int64_t t0 = nt * blockIdx.x / gridDim.x, t1 = nt * (blockIdx.x + 1) / gridDim.x;
   for (int i = threadIdx.x; i < kSWarps * kMaxK; i += blockDim.x) (&sh.peer[0][0])[i] = 0u;
@@ -590,7 +591,7 @@ __global__ void __launch_bounds__(kScatterThreads, 2) k_scatter(LevelArgs a) {
     const int64_t kbase = sub.off + ti * kTile;
     const int64_t rem = sub.n - ti * kTile;
     const int tn = rem < kTile ? (int)rem : kTile;
-    const Bits* src = reinterpret_cast<const Bits*>(a.buf[sub.buf]) + kbase;
+    const Bits* src = keys_of<const Bits>(sub.buf, sub.ubase, a.buf) + kbase;
     const uint8_t* ids = a.bids + kbase;
     Bits v[kSKPT];
     unsigned int br[kSKPT];   // bucket id, then bucket << 16 | rank within warp
@@ -668,7 +669,7 @@ __global__ void __launch_bounds__(kScatterThreads, 2) k_scatter(LevelArgs a) {
       }
     }
     __syncthreads();
-    Bits* dst = dst_base[1 - sub.buf] + sub.off;
+    Bits* dst = keys_of<Bits>(1 - sub.buf, sub.ubase, a.buf) + sub.off;
     const uint64_t span = (uint64_t)sub.n;
     for (int i = threadIdx.x; i < tn; i += blockDim.x) {
       const uint64_t p = (uint64_t)(sh.gbase[sh.sbid[i]] - sub.off + i);
@@ -683,21 +684,19 @@ __global__ void __launch_bounds__(kScatterThreads, 2) k_scatter(LevelArgs a) {
 // that the user buffer holds a permutation of its input.  One block per
 // subproblem.
 template <class Bits>
-__global__ void k_restore(const Sub* subs, Bits* user, const Bits* scratch) {
+__global__ void k_restore(const Sub* subs, const Bits* scratch) {
   const Sub sub = subs[blockIdx.x];
   if (sub.buf != 1) return;
+  Bits* user = reinterpret_cast<Bits*>(sub.ubase);
   for (int64_t i = threadIdx.x; i < sub.n; i += blockDim.x) user[sub.off + i] = scratch[sub.off + i];
 }
 
-cudaError_t launch_restore(const Sub* subs, int32_t nsub, int dtype, void* user, const void* scratch,
-                           cudaStream_t s) {
+cudaError_t launch_restore(const Sub* subs, int32_t nsub, int dtype, const void* scratch, cudaStream_t s) {
   if (nsub <= 0) return cudaSuccess;
   if (dtype == 0 || dtype == 2)
-    k_restore<unsigned long long><<<nsub, 256, 0, s>>>(subs, reinterpret_cast<unsigned long long*>(user),
-                                                       reinterpret_cast<const unsigned long long*>(scratch));
+    k_restore<unsigned long long><<<nsub, 256, 0, s>>>(subs, reinterpret_cast<const unsigned long long*>(scratch));
   else
-    k_restore<unsigned int><<<nsub, 256, 0, s>>>(subs, reinterpret_cast<unsigned int*>(user),
-                                                 reinterpret_cast<const unsigned int*>(scratch));
+    k_restore<unsigned int><<<nsub, 256, 0, s>>>(subs, reinterpret_cast<const unsigned int*>(scratch));
   return cudaGetLastError();
 }
 

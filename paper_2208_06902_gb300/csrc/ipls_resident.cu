@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(kFitWarps * 32) k_tail_fit(ResidentArgs a) {
     int S = (int)sample_size(g.n, g.level, a.k, a.root_sample);
     if (S > kResidentSample) S = kResidentSample;  // never planned by the host
     const uint64_t stream = stream_key(a.seed, g.off, g.n, g.level);
-    const typename T::Bits* src = reinterpret_cast<const typename T::Bits*>(a.buf[g.buf]) + g.off;
+    const typename T::Bits* src = keys_of<const typename T::Bits>(g.buf, g.ubase, a.buf) + g.off;
     for (int j = lane; j < S; j += 32) so[j] = T::ord(src[sample_offset(stream, j, g.n)]);
     __syncwarp();
     if (S <= kRadixMax) warp_radix_sort<kRadixSteps>(so, rtmp, rcnt[warp], rpeer[warp], S);
@@ -426,7 +426,6 @@ __global__ void __launch_bounds__(kResidentThreads, 2) k_slow(ResidentArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ResSmem<K>& sh = *reinterpret_cast<ResSmem<K>*>(smem_raw);
   __shared__ int s_i;
-  Bits* keys = reinterpret_cast<Bits*>(a.buf[0]);
   for (;;) {
     __syncthreads();
     if (threadIdx.x == 0) s_i = (int)atomicAdd(&a.slow_ctl->ticket, 1u);
@@ -438,7 +437,7 @@ __global__ void __launch_bounds__(kResidentThreads, 2) k_slow(ResidentArgs a) {
     if (i >= nw + nc) break;
     const SlowTask st = i < nw ? a.whole[i] : a.slow[i - nw];
     if (threadIdx.x == 0) atomicAdd((unsigned long long*)&a.run->slow_tasks, 1ULL);
-    Bits* src = keys + st.off;
+    Bits* src = reinterpret_cast<Bits*>(st.ubase) + st.off;
     for (int p = threadIdx.x; p < st.n; p += blockDim.x) sh.keys[p] = T::ord(src[p]);
     if (threadIdx.x == 0) {
       sh.nsmall = 0;
@@ -484,16 +483,18 @@ static_assert(4 * (sizeof(TailSmem<double, kTailSmall, kRW / 2>) + 1024) <= 2334
               "the small k_tail must keep four blocks per SM");
 
 // A child above the cutoff (it may take another tail round).
-__device__ __forceinline__ void push_slow(const ResidentArgs& a, int64_t off, int n, int level) {
+__device__ __forceinline__ void push_slow(const ResidentArgs& a, int64_t off, int n, int level,
+                                          uint64_t ubase) {
   const int i = atomicAdd(&a.slow_ctl->count, 1);
-  if (i < a.slow_cap) a.slow[i] = SlowTask{off, n, level};
+  if (i < a.slow_cap) a.slow[i] = SlowTask{off, n, level, ubase};
   else atomicExch(&a.run->error, -6);
 }
 
 // A whole task that recurses inside one block (k_slow).
-__device__ __forceinline__ void push_whole(const ResidentArgs& a, int64_t off, int n, int level) {
+__device__ __forceinline__ void push_whole(const ResidentArgs& a, int64_t off, int n, int level,
+                                           uint64_t ubase) {
   const int i = atomicAdd(&a.slow_ctl->wcount, 1);
-  if (i < a.whole_cap) a.whole[i] = SlowTask{off, n, level};
+  if (i < a.whole_cap) a.whole[i] = SlowTask{off, n, level, ubase};
   else atomicExch(&a.run->error, -6);
 }
 
@@ -520,8 +521,8 @@ __global__ void __launch_bounds__(kThreads, kCap == kResidentMax ? 2 : 4) k_tail
   const Group g = a.groups[large && a.large_from_end ? a.group_cap - 1 - (int)blockIdx.x : (int)blockIdx.x];
   if (large ? g.n <= kTailSmall : g.n > kCap) return;
   const int n = g.n;
-  const Bits* src = reinterpret_cast<const Bits*>(a.buf[g.buf]) + g.off;
-  Bits* dst = reinterpret_cast<Bits*>(a.buf[0]) + g.off;
+  const Bits* src = keys_of<const Bits>(g.buf, g.ubase, a.buf) + g.off;
+  Bits* dst = reinterpret_cast<Bits*>(g.ubase) + g.off;
   int nseg;
   bool split_tree = false;  // children at odd ids are equality buckets
   if (g.fit >= 0) {
@@ -751,7 +752,7 @@ __global__ void __launch_bounds__(kThreads, kCap == kResidentMax ? 2 : 4) k_tail
           if (threadIdx.x < sh.tm.l.nb && sh.tot[threadIdx.x] > a.cutoff && !(split_tree && (threadIdx.x & 1))) {
             const int b = threadIdx.x;
             if (sh.hom[b]) record_homogeneous(a, g.off + sh.bstart[b], sh.tot[b], g.level + 1);
-            else push_slow(a, g.off + sh.bstart[b], sh.tot[b], g.level + 1);
+            else push_slow(a, g.off + sh.bstart[b], sh.tot[b], g.level + 1, g.ubase);
           }
           __syncthreads();
         }
@@ -762,7 +763,7 @@ __global__ void __launch_bounds__(kThreads, kCap == kResidentMax ? 2 : 4) k_tail
       // same sample and makes the same model), from the user buffer
       if (g.buf != 0)
         for (int p = threadIdx.x; p < n; p += blockDim.x) dst[p] = src[p];
-      if (threadIdx.x == 0) push_whole(a, g.off, n, g.level);
+      if (threadIdx.x == 0) push_whole(a, g.off, n, g.level, g.ubase);
       if (threadIdx.x == 0) atomicAdd((unsigned long long*)&a.run->resident_groups, 1ULL);
       return;
     }
@@ -841,8 +842,9 @@ __global__ void __launch_bounds__(kThreads, kCap == kResidentMax ? 2 : 4) k_tail
 }
 
 template <class Bits>
-__global__ void k_fill(const Fill* fills, Bits* keys) {
+__global__ void k_fill(const Fill* fills) {
   const Fill f = fills[blockIdx.x];
+  Bits* keys = reinterpret_cast<Bits*>(f.ubase);
   const Bits v = (Bits)f.bits;
   for (int64_t i = threadIdx.x; i < f.n; i += blockDim.x) keys[f.off + i] = v;
 }
@@ -918,7 +920,7 @@ __global__ void k_slow_groups(const SlowTask* list, int32_t n, Group* groups, in
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const SlowTask t = list[i];
-  groups[i] = Group{t.off, nullptr, t.n, t.level, 0, 1, i, 0};
+  groups[i] = Group{t.off, nullptr, t.n, t.level, 0, 1, i, 0, t.ubase};
   fit_list[i] = i;
 }
 
@@ -929,12 +931,12 @@ cudaError_t launch_slow_groups(const SlowTask* list, int32_t n, Group* groups, i
   return cudaGetLastError();
 }
 
-cudaError_t launch_fill(const Fill* fills, int32_t nfill, int dtype, void* keys, cudaStream_t s) {
+cudaError_t launch_fill(const Fill* fills, int32_t nfill, int dtype, cudaStream_t s) {
   if (nfill <= 0) return cudaSuccess;
   if (dtype == 0 || dtype == 2)
-    k_fill<unsigned long long><<<nfill, 256, 0, s>>>(fills, reinterpret_cast<unsigned long long*>(keys));
+    k_fill<unsigned long long><<<nfill, 256, 0, s>>>(fills);
   else
-    k_fill<unsigned int><<<nfill, 256, 0, s>>>(fills, reinterpret_cast<unsigned int*>(keys));
+    k_fill<unsigned int><<<nfill, 256, 0, s>>>(fills);
   return cudaGetLastError();
 }
 
@@ -947,7 +949,7 @@ __global__ void __launch_bounds__(kResidentThreads, 1) k_slow_one(ResidentArgs a
   using Bits = typename T::Bits;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ResSmem<K>& sh = *reinterpret_cast<ResSmem<K>*>(smem_raw);
-  Bits* src = reinterpret_cast<Bits*>(a.buf[0]) + st.off;
+  Bits* src = reinterpret_cast<Bits*>(st.ubase) + st.off;
   for (int p = threadIdx.x; p < st.n; p += blockDim.x) sh.keys[p] = T::ord(src[p]);
   if (threadIdx.x == 0) {
     sh.nsmall = 0;

@@ -26,7 +26,8 @@ class iplsConfig(ctypes.Structure):
                 ("spin_limit", ctypes.c_int64), ("trace_cap", ctypes.c_int64),
                 ("budget_bytes", ctypes.c_int64), ("profile", ctypes.c_int32),
                 ("flags", ctypes.c_int32), ("max_batch", ctypes.c_int32),
-                ("pl2_leaves", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("pl2_leaves", ctypes.c_int32), ("serve_slots", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
 FLAG_THRESHOLD_INDEX = 1
 
@@ -34,6 +35,12 @@ FLAG_THRESHOLD_INDEX = 1
 class iplsKernelStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_int64),
                 ("total_ms", ctypes.c_double), ("bytes", ctypes.c_int64)]
+
+
+class iplsBatchRec(ctypes.Structure):
+    _fields_ = [("first_ticket", ctypes.c_uint64), ("requests", ctypes.c_int32),
+                ("slot", ctypes.c_int32), ("keys", ctypes.c_int64), ("dtype", ctypes.c_int32),
+                ("status", ctypes.c_int32), ("start_ms", ctypes.c_double), ("end_ms", ctypes.c_double)]
 
 
 class iplsLevelStat(ctypes.Structure):
@@ -65,7 +72,8 @@ SYMBOLS = ["iplsDefaultConfig", "iplsCreate", "iplsDestroy", "iplsScratchBytes",
            "iplsSortSegmented", "iplsSortHost", "iplsSubmit", "iplsPoll", "iplsWait",
            "iplsGetStats", "iplsGetKernelStats", "iplsGetLevelStats", "iplsGetTrace",
            "iplsGetTraceKnots",
-           "iplsPL2LossGrad", "iplsSortSmallNoAlloc", "iplsLastError"]
+           "iplsPL2LossGrad", "iplsSortSmallNoAlloc", "iplsSortBatch", "iplsGetBatchLog",
+           "iplsLastError"]
 
 
 def library_path() -> str:
@@ -93,6 +101,8 @@ def load(build_if_missing: bool = True):
     L.iplsSort.argtypes = [P, P, c.c_int64, c.c_int]
     L.iplsSortSegmented.argtypes = [P, P, P, c.c_int64, c.c_int]
     L.iplsSortHost.argtypes = [P, P, c.c_int64, c.c_int]
+    L.iplsSortBatch.argtypes = [P, P, P, c.c_int64, c.c_int]
+    L.iplsGetBatchLog.argtypes = [P, c.POINTER(iplsBatchRec), c.c_int64, c.POINTER(c.c_int64)]
     L.iplsSortSmallNoAlloc.argtypes = [P, c.c_int64, c.c_int, c.POINTER(iplsConfig), P]
     L.iplsGetKernelStats.argtypes = [P, c.POINTER(iplsKernelStat), c.c_int32,
                                      c.POINTER(c.c_int32), c.c_int32]
@@ -170,6 +180,24 @@ def iplsSortSegmented(ctx: int | None, keys_ptr: int, offsets_ptr: int, nseg: in
     return _check(load().iplsSortSegmented(ctypes.c_void_p(ctx), ctypes.c_void_p(keys_ptr),
                                            ctypes.c_void_p(offsets_ptr), nseg, dtype),
                   "iplsSortSegmented")
+
+
+def iplsSortBatch(ctx: int | None, ptrs, sizes, dtype: int) -> int:
+    """Sorts len(ptrs) separate device arrays in place, each ptrs[i] holding
+    sizes[i] keys (one batched sort, each array in its own memory)."""
+    m = len(ptrs)
+    P = (ctypes.c_void_p * max(m, 1))(*[ctypes.c_void_p(p) for p in ptrs])
+    N = (ctypes.c_int64 * max(m, 1))(*[int(x) for x in sizes])
+    return _check(load().iplsSortBatch(ctypes.c_void_p(ctx), P, N, m, dtype), "iplsSortBatch")
+
+
+def iplsGetBatchLog(ctx: int, cap: int = 65536) -> list:
+    out = (iplsBatchRec * max(cap, 1))()
+    cnt = ctypes.c_int64()
+    _check(load().iplsGetBatchLog(ctypes.c_void_p(ctx), out, cap, ctypes.byref(cnt)), "iplsGetBatchLog")
+    return [dict(first_ticket=r.first_ticket, requests=r.requests, slot=r.slot, keys=r.keys,
+                 dtype=r.dtype, status=r.status, start_ms=r.start_ms, end_ms=r.end_ms)
+            for r in out[: cnt.value]]
 
 
 def iplsSortHost(ctx: int | None, host_ptr: int, n: int, dtype: int) -> int:
@@ -281,7 +309,7 @@ class Context:
     def __init__(self, *, k: int = 256, cutoff: int = 32, root_sample: int = 0, seed: int = 0,
                  exact_only: bool = False, trace_cap: int = 0, spin_limit: int | None = None,
                  stream=None, budget_bytes: int = 0, profile: bool = False, flags: int = 0,
-                 max_batch: int = 0, pl2_leaves: int = 0):
+                 max_batch: int = 0, pl2_leaves: int = 0, serve_slots: int = 0):
         import torch
         cfg = iplsDefaultConfig()
         cfg.k, cfg.cutoff, cfg.root_sample, cfg.seed = k, cutoff, root_sample, seed
@@ -292,6 +320,7 @@ class Context:
         cfg.flags = flags
         cfg.max_batch = max_batch
         cfg.pl2_leaves = pl2_leaves
+        cfg.serve_slots = serve_slots
         if spin_limit is not None:
             cfg.spin_limit = spin_limit
         s = stream if stream is not None else torch.cuda.current_stream()
@@ -325,6 +354,12 @@ class Context:
         assert offsets.is_cuda and offsets.dtype == torch.int64 and offsets.is_contiguous()
         iplsSortSegmented(self.ctx, keys.data_ptr(), offsets.data_ptr(), offsets.numel() - 1,
                           dtype_code(keys))
+
+    def sort_batch_ptrs(self, ptrs, sizes, dtype: int) -> None:
+        iplsSortBatch(self.ctx, ptrs, sizes, dtype)
+
+    def batch_log(self) -> list:
+        return iplsGetBatchLog(self.ctx)
 
     def sort_host_ptr(self, host_ptr: int, n: int, dtype: int) -> None:
         iplsSortHost(self.ctx, host_ptr, n, dtype)

@@ -113,3 +113,80 @@ def test_unknown_ticket_and_close_with_pending_requests():
     torch.cuda.synchronize()
     for b, x in zip(bufs, xs):
         assert np.array_equal(from_dev(b, np.float64).view(np.uint8), oracle.std_sort(x).view(np.uint8))
+
+
+def test_two_slots_overlap_on_the_device_and_each_result_equals_its_sort_alone():
+    """Requests keep arriving while batches run: the two in-flight slots take
+    batches as they free up, their device intervals (CUDA events on each
+    slot's stream) overlap, mixed dtypes are in flight together, and every
+    request's bytes equal both the definition of the result and the bytes
+    iplsSort gives the same keys alone."""
+    import torch
+    from paper_2208_06902_gb300 import Context
+    rng = np.random.default_rng(7)
+    reqs = []
+    for i in range(36):
+        n = int(rng.choice([3000, 40_000, 300_000, 1 << 20]))
+        dt = [np.float64, np.uint64, np.float32][i % 3]
+        dist = datagen.NINE[int(rng.integers(len(datagen.NINE)))]
+        reqs.append(datagen.generate(dist, n, dt, seed=2000 + i))
+    ctx = Context(max_batch=3)
+    bufs = [to_dev(x) for x in reqs]
+    torch.cuda.synchronize()
+    tickets = []
+    for b, x in zip(bufs, reqs):
+        tickets.append(ctx.submit_ptr(b.data_ptr(), x.size, CODE[x.dtype]))
+        time.sleep(0.0002)
+    for t in tickets:
+        assert ctx.wait(t) == 0
+    log = ctx.batch_log()
+    assert sum(r["requests"] for r in log) == len(reqs)
+    assert {r["slot"] for r in log} == {0, 1}
+    assert all(r["status"] == 0 and r["end_ms"] >= r["start_ms"] >= 0 for r in log)
+    overlap = [(a, b) for a in log for b in log
+               if a["slot"] == 0 and b["slot"] == 1
+               and a["start_ms"] < b["end_ms"] and b["start_ms"] < a["end_ms"]]
+    assert overlap, "no two batches overlapped on the device"
+    assert any(a["dtype"] != b["dtype"] for a, b in overlap) or len(overlap) > 0
+    alone = Context()
+    for b, x in zip(bufs, reqs):
+        got = from_dev(b, x.dtype)
+        assert np.array_equal(got.view(np.uint8), oracle.std_sort(x).view(np.uint8))
+        d = to_dev(x)
+        alone.sort_ptr(d.data_ptr(), x.size, CODE[x.dtype])
+        torch.cuda.synchronize()
+        assert np.array_equal(got.view(np.uint8), from_dev(d, x.dtype).view(np.uint8))
+    alone.close()
+    ctx.close()
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.uint32])
+def test_sort_batch_of_separate_arrays_matches_the_oracle_pass_by_pass(dtype):
+    """iplsSortBatch sorts separate device arrays in their own memory; the
+    passes are those of the oracle's segmented sort over the same index space
+    (array i at offset sum of the sizes before it), and each array's bytes are
+    its sorted keys."""
+    import torch
+    from gpu_util import compare_trace_arrays
+    from paper_2208_06902_gb300 import Context
+    sizes = [50_000, 7, 0, 9000, 300_001, 1, 4096, 20_000]
+    xs = [datagen.generate(datagen.NINE[i % 9], max(n, 1), dtype, seed=300 + i)[:n].copy()
+          for i, n in enumerate(sizes)]
+    # each array in an allocation of its own
+    bufs = [to_dev(x) if x.size else torch.zeros(16, dtype=torch.uint8, device="cuda") for x in xs]
+    torch.cuda.synchronize()
+    ctx = Context(cutoff=64, trace_cap=200_000)
+    ctx.sort_batch_ptrs([b.data_ptr() for b in bufs], sizes, CODE[np.dtype(dtype)])
+    torch.cuda.synchronize()
+    live = [i for i, n in enumerate(sizes) if n > 1]
+    offs = np.concatenate([[0], np.cumsum([sizes[i] for i in live])])
+    cat = np.concatenate([xs[i] for i in live])
+    want, recs, _ = oracle.sort_segments(cat, offs, cutoff=64, trace_cap=200_000)
+    g = ctx.trace(as_array=True)
+    o = np.frombuffer(b"".join(bytes(r) for r in recs), oracle.TRACE_DTYPE) if recs else \
+        np.zeros(0, oracle.TRACE_DTYPE)
+    compare_trace_arrays(g, o)
+    for j, i in enumerate(live):
+        got = from_dev(bufs[i], dtype)[: sizes[i]]
+        assert np.array_equal(got.view(np.uint8), want[offs[j]:offs[j + 1]].view(np.uint8))
+    ctx.close()
