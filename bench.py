@@ -59,7 +59,8 @@ def parse():
     p.add_argument("--profile-stats", metavar="JSON",
                    help="profiling run: sort W+K arrays, write the per-kernel launches and "
                         "algorithmic bytes of ALL of them to JSON, print no bench line")
-    p.add_argument("--workload", default="single", choices=["single", "segmented", "serve", "integers"],
+    p.add_argument("--workload", default="single",
+                   choices=["single", "segmented", "serve", "integers", "uniform2p20"],
                    help="single: the 2^28 arrays (headline); segmented: a batch of "
                         "200,000 uneven segments in one call vs one call per segment; "
                         "serve: Poisson-arriving requests, batched vs one at a time")
@@ -68,6 +69,10 @@ def parse():
                    help="offered load as a fraction of the one-at-a-time service rate")
     p.add_argument("--max-request-log10", type=float, default=6.0)
     p.add_argument("--segments", type=int, default=200_000)
+    p.add_argument("--graph", action="store_true",
+                   help="segmented: device-driven levels captured into a CUDA graph")
+    p.add_argument("--stated-size", action="store_true",
+                   help="segmented: the size law as stated (about 1.26e9 keys), not rescaled to 2^log2n")
     p.add_argument("--budget-gb", type=int, default=64,
                    help="serve: device-memory budget of the requests in flight (GiB)")
     p.add_argument("--tuned", metavar="JSON", help="autotuner table; picks k and cutoff")
@@ -507,8 +512,9 @@ def run_segmented(args):
     ipls.load()
     dev = torch.device("cuda", 0)
     sizes = datagen.segment_sizes(args.segments)
-    scale = (1 << args.log2n) / float(sizes.sum())
-    sizes = np.maximum(np.rint(sizes * scale), 16).astype(np.int64)
+    if not args.stated_size:
+        scale = (1 << args.log2n) / float(sizes.sum())
+        sizes = np.maximum(np.rint(sizes * scale), 16).astype(np.int64)
     keys, offsets, _ = datagen.segmented(sizes)
     n = int(offsets[-1])
     k, cutoff = 256, args.cutoff
@@ -520,7 +526,8 @@ def run_segmented(args):
     off = torch.from_numpy(offsets).to(dev)
     work = torch.empty_like(src)
     stream = torch.cuda.current_stream()
-    ctx = ipls.Context(k=k, cutoff=cutoff, stream=stream)
+    flags = ipls.ipls.FLAG_GRAPH if args.graph else 0
+    ctx = ipls.Context(k=k, cutoff=cutoff, stream=stream, flags=flags)
 
     def batch():
         work.copy_(src)
@@ -550,16 +557,38 @@ def run_segmented(args):
     t_each = a.elapsed_time(b)
     same = bool(torch.equal(got, work))
     ms = statistics.median(t_batch)
+    # per-call time of a small segmented sort (one 4096-key segment), host
+    # wall clock around the call, without and with the captured graph
+    overhead = {}
+    small = torch.from_numpy(datagen.generate("normal", 4096, np.float64, seed=9).view(np.uint8)).to(dev)
+    soff = torch.tensor([0, 4096], dtype=torch.int64, device=dev)
+    sw = torch.empty_like(small)
+    for name, fl in (("host_levels", 0), ("graph", ipls.ipls.FLAG_GRAPH)):
+        c2 = ipls.Context(k=k, cutoff=cutoff, stream=stream, flags=fl)
+        for _ in range(5):
+            sw.copy_(small)
+            ipls.iplsSortSegmented(c2.ctx, sw.data_ptr(), soff.data_ptr(), 1, ipls.F64)
+        torch.cuda.synchronize()
+        reps = 200
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            ipls.iplsSortSegmented(c2.ctx, sw.data_ptr(), soff.data_ptr(), 1, ipls.F64)
+        torch.cuda.synchronize()
+        overhead[name] = round((time.perf_counter() - t0) / reps * 1e6, 1)
+        c2.close()
     line = {"metric": "Gkeys/s, segmented batch sort (one call, all segments)",
             "value": round(n / (ms * 1e-3) / 1e9, 4), "unit": "Gkeys/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": f"{sizes.size} segments, {n} f64 keys in total",
-                       "sizes": "LogNormal(median 2048, sigma 1.5) clamped to [16, 4194304], "
-                                f"rescaled to sum ~2^{args.log2n}",
+                       "sizes": "LogNormal(median 2048, sigma 1.5) clamped to [16, 4194304]"
+                                + (" as stated (no rescale)" if args.stated_size
+                                   else f", rescaled to sum ~2^{args.log2n}"),
                        "median_segment": int(np.median(sizes)), "max_segment": int(sizes.max()),
-                       "k": k, "cutoff": cutoff, "tuned": bool(args.tuned)},
+                       "k": k, "cutoff": cutoff, "tuned": bool(args.tuned),
+                       "graph": bool(args.graph)},
+            "call_us_4096_keys": overhead,
             "per_segment_calls": {"value": round(n / (t_each * 1e-3) / 1e9, 4), "unit": "Gkeys/s",
                                   "ms": round(t_each, 1), "calls": int(sizes.size)},
             "speedup_vs_per_segment": round(t_each / ms, 2),
@@ -693,6 +722,52 @@ def run_serve(args):
     return 0 if same else 1
 
 
+def run_uniform2p20(args):
+    """The small single-array workload: 2^20 f64 keys U[0,1) from seed 0, a
+    root sample of 2^14 keys, k = 256, base-case cutoff 32, sorted K times
+    (the input restored between sorts).  Reports Gkeys/s and the per-call
+    device time; the output is checked against the serial oracle."""
+    import numpy as np
+    import torch
+
+    import datagen
+    import oracle
+    torch.cuda.set_device(0)
+    import paper_2208_06902_gb300 as ipls
+    ipls.load()
+    dev = torch.device("cuda", 0)
+    x = datagen.config1(1 << 20, seed=0)
+    src = torch.from_numpy(x.view(np.uint8)).to(dev)
+    work = torch.empty_like(src)
+    stream = torch.cuda.current_stream()
+    ctx = ipls.Context(cutoff=32, root_sample=1 << 14, stream=stream)
+    ts = []
+    for i in range(args.warmup + args.steps):
+        work.copy_(src)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.sort_ptr(work.data_ptr(), x.size, ipls.F64)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            ts.append(a.elapsed_time(b))
+    want, _, _ = oracle.sort(x, cutoff=32, root_sample=1 << 14)
+    same = bool(np.array_equal(work.cpu().numpy(), want.view(np.uint8)))
+    ms = statistics.median(ts)
+    line = {"metric": "Gkeys/s sorting 2^20 f64 uniform keys (IPLS, cutoff 32)",
+            "value": round(x.size / (ms * 1e-3) / 1e9, 4), "unit": "Gkeys/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "2^20 f64 U[0,1), seed 0, root sample 2^14, k 256, cutoff 32",
+                       "l2": "input (8 MiB) fits in L2: restored from a copy before every sort"},
+            "equals_oracle": same}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0 if same else 1
+
+
 def _sorted_on_device(t, code) -> bool:
     """Non-decreasing in totalOrder, checked on the device."""
     import torch
@@ -792,6 +867,8 @@ def main():
         return run_serve(args)
     if args.workload == "integers":
         return run_integers(args)
+    if args.workload == "uniform2p20":
+        return run_uniform2p20(args)
     return run_gb300(args)
 
 

@@ -93,6 +93,15 @@ typedef struct iplsConfig {
  * speed; off by default). */
 #define IPLS_FLAG_THRESHOLD_INDEX 1
 
+/* cfg.flags: iplsSortSegmented runs its recursion levels without host round
+ * trips -- every kernel reads its level's counts from device memory -- and
+ * captures them into a CUDA graph, replayed while the keys pointer, offsets
+ * pointer, segment count and total stay the same (deeper recursion than the
+ * graph holds continues level by level from the host).  Buffers are sized
+ * for the worst case up front, so the context holds more scratch.  Same
+ * sorted result. */
+#define IPLS_FLAG_GRAPH 2
+
 /* Accumulated device time of one kernel of the library (profile = 1).
  * bytes = algorithmic bytes: keys read + keys written by the launches, in
  * bytes (the classify/histogram sweep reads every live key once, the scatter

@@ -278,21 +278,25 @@ def sort(keys: np.ndarray, k: int = 256, cutoff: int = 32, root_sample: int = 0,
 
 
 def sort_segments(keys: np.ndarray, offsets, k: int = 256, cutoff: int = 32,
-                  root_sample: int = 0, seed: int = 0, trace_cap: int = 0, pl2_leaves: int = 0):
+                  root_sample: int = 0, seed: int = 0, trace_cap: int = 0, pl2_leaves: int = 0,
+                  as_array: bool = False):
     """IPLS on each segment keys[off[i]:off[i+1]], each a level-0 subproblem
-    keyed by its own offset (returns sorted copy, trace records, depth)."""
+    keyed by its own offset (returns sorted copy, trace records, depth).
+    as_array: the trace as a numpy structured array (TRACE_DTYPE)."""
     out = np.array(keys, copy=True)
     off = np.ascontiguousarray(offsets, np.int64)
     c = Cfg(k, cutoff, root_sample, seed, pl2_leaves, 0)
-    tr = (Trace * trace_cap)() if trace_cap > 0 else None
+    tr = np.zeros(max(trace_cap, 1), TRACE_DTYPE)
     cnt = ctypes.c_int64(0)
     lv = ctypes.c_int32(0)
     rc = lib().oracle_sort_segments(_code(out), _ptr(out), _ptr(off), off.size - 1,
-                                    ctypes.byref(c), tr, trace_cap, ctypes.byref(cnt),
+                                    ctypes.byref(c), ctypes.cast(_ptr(tr), ctypes.POINTER(Trace))
+                                    if trace_cap > 0 else None, trace_cap, ctypes.byref(cnt),
                                     ctypes.byref(lv))
     if rc != 0:
         raise RuntimeError(f"oracle_sort_segments failed ({rc})")
-    recs = list(tr[: cnt.value]) if tr is not None else []
+    arr = tr[: cnt.value] if trace_cap > 0 else tr[:0]
+    recs = arr if as_array else [Trace.from_buffer_copy(r.tobytes()) for r in arr]
     return out, recs, lv.value
 
 

@@ -26,6 +26,9 @@ thread_local std::string g_last_error;
 
 // Offsets inside a bucket are kept in 32 bits per tile.
 constexpr int64_t kMaxKeys = (int64_t(1) << 32) - 1;
+// Device-driven levels enqueued at most (deeper recursion continues with
+// host-driven levels).
+constexpr int kDevLevelsMax = 8;
 
 iplsStatus fail(iplsStatus st, const std::string& msg) {
   g_last_error = msg;
@@ -97,6 +100,23 @@ struct Workspace {
   int64_t trace_grid_count = 0;
   std::vector<Pending> pending;       // profiling: event pairs per launch
   std::vector<cudaEvent_t> spare_events;
+  // device-driven levels: one LevelCtl per level (entry 0: the segment
+  // lists), their pinned copy, the grid trace counter, and the captured
+  // graph of the last segmented call with its key
+  LevelCtl* ctl_arr = nullptr;
+  LevelCtl* h_ctl_arr = nullptr;
+  long long* trace_ctr = nullptr;
+  long long* h_trace_ctr = nullptr;
+  bool capturing = false;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  struct GraphKey {
+    void* keys; const int64_t* offsets; const uint64_t* ubase; int64_t n, nseg; int dtype, levels;
+    bool operator==(const GraphKey& o) const {
+      return keys == o.keys && offsets == o.offsets && ubase == o.ubase && n == o.n && nseg == o.nseg &&
+             dtype == o.dtype && levels == o.levels;
+    }
+  } gkey{};
 };
 
 }  // namespace
@@ -123,6 +143,7 @@ struct iplsContext {
     int dtype;
     iplsStatus st;
     bool done;
+    std::string msg;     // the failure's message (set on the worker thread)
   };
   static constexpr int kServeSlots = 2;
   std::mutex exec_mu;                 // one synchronous sort at a time on the context
@@ -222,7 +243,7 @@ cudaEvent_t take_event(Workspace& w) {
 // when profiling; every launch is counted.
 template <class F>
 cudaError_t timed(Workspace& w, int kind, F fn, int level = -1) {
-  if (!w.c->cfg.profile || !w.main) {
+  if (!w.c->cfg.profile || !w.main || w.capturing) {
     cudaError_t e = fn();
     return e;
   }
@@ -282,9 +303,9 @@ iplsStatus tail_sweep(Workspace& w, ResidentArgs& ra) {
     IPLS_CUDA(timed(w, kkTailFit, [&] { return launch_tail_fit(ra, w.stream, c->num_sms); }));
   }
   if (ra.ngroups > 0)
-    IPLS_CUDA(timed(w, kkResident, [&] { return launch_resident(ra, w.stream, 0); }));
+    IPLS_CUDA(timed(w, kkResident, [&] { return launch_resident(ra, w.stream, 0, c->num_sms); }));
   if ((ra.large_from_end ? ra.nlarge : ra.ngroups) > 0)
-    IPLS_CUDA(timed(w, kkResident, [&] { return launch_resident(ra, w.stream, 1); }));
+    IPLS_CUDA(timed(w, kkResident, [&] { return launch_resident(ra, w.stream, 1, c->num_sms); }));
   return IPLS_OK;
 }
 
@@ -360,6 +381,218 @@ iplsStatus check_run(Workspace& w) {
   return IPLS_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Device-driven levels (segmented sorts, cfg.flags & IPLS_FLAG_GRAPH): every
+// buffer is sized for the worst case first, then the levels are enqueued
+// with no host round trip -- each kernel reads its level's counts from the
+// LevelCtl the previous level left on the device and loops over them with a
+// fixed grid -- so that the whole sequence can be captured into a CUDA graph
+// and replayed.  One readback at the end gives the statistics, any error,
+// and whether the recursion needs more levels than were enqueued.
+// ---------------------------------------------------------------------------
+struct DevCaps {
+  int64_t sub, tile, chunk, group, fill;
+};
+
+DevCaps dev_caps(const iplsConfig& cfg, int64_t n, int64_t nseg, int dtype) {
+  const int rmax = resident_rmax(cfg.cutoff);
+  DevCaps d;
+  d.sub = n / (rmax + 1) + 2;
+  d.tile = n / tile_keys(dtype) + d.sub + 2;
+  d.chunk = d.tile / kChunkTiles + d.sub + 2;
+  d.group = 2 * n / (cfg.cutoff + 1) + 257 * d.sub + 16 + nseg + 1024;
+  d.fill = n / kFillChunk + 129 * d.sub + 16;
+  return d;
+}
+
+// Subproblems a slot can hold in every per-subproblem array, and tiles and
+// chunks the level arrays can hold (arrays grown by earlier calls may differ
+// in capacity).
+int64_t slot_sub_limit(const Workspace& w, const Slot& X) {
+  const iplsConfig& cfg = w.c->cfg;
+  int64_t m = std::min(X.sub_cap, X.model_cap);
+  m = std::min(m, X.count_cap / kMaxK);
+  m = std::min(m, X.base_cap / 257);
+  if (cfg.flags & IPLS_FLAG_THRESHOLD_INDEX) m = std::min(m, X.tab_cap);
+  if (cfg.pl2_leaves > 0) m = std::min(m, X.knot_cap / (cfg.pl2_leaves + 1));
+  return std::min<int64_t>(m, INT32_MAX);
+}
+int64_t slot_tile_limit(const Workspace& w, const Slot& X) {
+  return std::min(X.tile_cap, w.tile_off_cap / kMaxK);
+}
+int64_t slot_chunk_limit(const Workspace& w, const Slot& X) {
+  return std::min(X.chunk_cap, w.status_cap / kMaxK);
+}
+
+iplsStatus device_prepare(Workspace& w, int64_t n, int64_t nseg, int dtype) {
+  iplsCtx c = w.c;
+  const iplsConfig& cfg = c->cfg;
+  const DevCaps d = dev_caps(cfg, n, nseg, dtype);
+  IPLS_TRY(ensure(w, w.scratch, w.scratch_cap, n * (int64_t)key_bytes(dtype)));
+  IPLS_TRY(ensure(w, w.bids, w.bids_cap, n));
+  IPLS_TRY(ensure(w, w.slow, w.slow_cap, 2 * (n / (cfg.cutoff + 1)) + 4096));
+  for (Slot& X : w.slot) {
+    IPLS_TRY(ensure(w, X.subs, X.sub_cap, d.sub));
+    IPLS_TRY(ensure(w, X.tile2sub, X.tile_cap, d.tile));
+    IPLS_TRY(ensure(w, X.chunk2sub, X.chunk_cap, d.chunk));
+    IPLS_TRY(ensure(w, X.models, X.model_cap, d.sub));
+    IPLS_TRY(ensure(w, X.tabs, X.tab_cap, (cfg.flags & IPLS_FLAG_THRESHOLD_INDEX) ? d.sub : 1));
+    if (cfg.pl2_leaves > 0) IPLS_TRY(ensure(w, X.knots, X.knot_cap, d.sub * (int64_t)(cfg.pl2_leaves + 1)));
+    IPLS_TRY(ensure(w, X.counts, X.count_cap, d.sub * kMaxK));
+    IPLS_TRY(ensure(w, X.bases, X.base_cap, d.sub * 257));
+    IPLS_TRY(ensure_groups(w, X, d.group));
+    IPLS_TRY(ensure(w, X.fills, X.fill_cap, d.fill));
+  }
+  IPLS_TRY(ensure(w, w.tile_off, w.tile_off_cap, d.tile * kMaxK));
+  IPLS_TRY(ensure(w, w.status, w.status_cap, d.chunk * kMaxK));
+  IPLS_TRY(ensure(w, w.split_pool, w.split_pool_cap, pool_slots(d.group) * 128));
+  if (!w.ctl_arr) {
+    void* p;
+    IPLS_TRY(dev_alloc(c, &p, (kDevLevelsMax + 1) * sizeof(LevelCtl)));
+    w.ctl_arr = (LevelCtl*)p;
+    IPLS_TRY(dev_alloc(c, &p, sizeof(long long)));
+    w.trace_ctr = (long long*)p;
+    IPLS_CUDA(cudaMallocHost(&w.h_ctl_arr, (kDevLevelsMax + 1) * sizeof(LevelCtl)));
+    IPLS_CUDA(cudaMallocHost(&w.h_trace_ctr, sizeof(long long)));
+  }
+  return IPLS_OK;
+}
+
+// The tail of one device-driven level: its groups in slot s, counted in
+// *gcnt; a second sweep over the children above the cutoff when there are
+// at least kTailSweepMin of them; k_slow for the rest.
+iplsStatus launch_tail_dev(Workspace& w, ResidentArgs ra, Slot& s, LevelCtl* gcnt) {
+  iplsCtx c = w.c;
+  const int32_t cap = (int32_t)std::min<int64_t>(std::min(s.group_cap, std::min(s.fit_cap, s.tail_cap)), INT32_MAX);
+  ra.groups = s.groups;
+  ra.ngroups = cap;
+  ra.nlarge = cap;
+  ra.group_cap = cap;
+  ra.large_from_end = 1;
+  ra.fit_list = s.fit_list;
+  ra.nfit = cap;
+  ra.tail_models = s.tails;
+  ra.gcnt = gcnt;
+  ra.device_counts = 1;
+  ra.sweep = 0;
+  const int64_t half = w.slow_cap / 2;
+  ra.slow = w.slow;
+  ra.slow_cap = (int32_t)std::min<int64_t>(half, INT32_MAX);
+  ra.whole = w.slow + half;
+  ra.whole_cap = (int32_t)std::min<int64_t>(w.slow_cap - half, INT32_MAX);
+  ra.slow_ctl = w.slow_ctl;
+  ra.split_pool = w.split_pool;
+  ra.split_pool_slots = (int32_t)std::min<int64_t>(w.split_pool_cap / 128, kSplitPoolMax);
+  IPLS_CUDA(cudaMemsetAsync(w.slow_ctl, 0, sizeof(SlowCtl), w.stream));
+  IPLS_CUDA(timed(w, kkTailFit, [&] { return launch_tail_fit(ra, w.stream, c->num_sms); }));
+  IPLS_CUDA(timed(w, kkResident, [&] { return launch_resident(ra, w.stream, 0, c->num_sms); }));
+  IPLS_CUDA(timed(w, kkResident, [&] { return launch_resident(ra, w.stream, 1, c->num_sms); }));
+  IPLS_CUDA(timed(w, kkSlowGroups, [&] {
+    return launch_sweep_groups(w.slow, w.slow_ctl, ra.slow_cap, s.groups, s.fit_list, cap, w.stream);
+  }));
+  ResidentArgs rb = ra;
+  rb.sweep = 1;
+  rb.large_from_end = 0;
+  IPLS_CUDA(timed(w, kkTailFit, [&] { return launch_tail_fit(rb, w.stream, c->num_sms); }));
+  IPLS_CUDA(timed(w, kkResident, [&] { return launch_resident(rb, w.stream, 0, c->num_sms); }));
+  IPLS_CUDA(timed(w, kkResident, [&] { return launch_resident(rb, w.stream, 1, c->num_sms); }));
+  IPLS_CUDA(timed(w, kkSlow, [&] { return launch_slow(ra, w.stream, c->num_sms); }));
+  return IPLS_OK;
+}
+
+// Enqueues the segment lists and `levels` device-driven levels (buffers from
+// device_prepare; no allocation and no host synchronisation), then copies
+// the level counters, the run status and the trace counter to pinned memory.
+iplsStatus device_enqueue(Workspace& w, int64_t n, int dtype, const int64_t* offsets, int64_t nseg,
+                          const uint64_t* seg_ubase, uint64_t ubase, int levels) {
+  iplsCtx c = w.c;
+  const iplsConfig& cfg = c->cfg;
+  const bool traced = w.main && cfg.trace_cap > 0;
+  const int rmax = resident_rmax(cfg.cutoff);
+  const int resident_root_ok = (cfg.root_sample <= 0 || cfg.root_sample <= kResidentSample);
+  IPLS_CUDA(cudaMemsetAsync(w.run, 0, sizeof(RunStatus), w.stream));
+  IPLS_CUDA(cudaMemsetAsync(w.ctl_arr, 0, (size_t)(levels + 1) * sizeof(LevelCtl), w.stream));
+  IPLS_CUDA(cudaMemsetAsync(w.trace_ctr, 0, sizeof(long long), w.stream));
+  ResidentArgs ra{};
+  ra.dtype = dtype; ra.k = cfg.k; ra.cutoff = cfg.cutoff; ra.root_sample = cfg.root_sample;
+  ra.seed = cfg.seed; ra.exact_only = cfg.exact_only; ra.buf[0] = nullptr; ra.buf[1] = w.scratch;
+  ra.run = w.run; ra.trace = traced ? c->trace_res : nullptr; ra.trace_cap = traced ? cfg.trace_cap : 0;
+  Slot& s0 = w.slot[0];
+  Slot& s1 = w.slot[1];
+  IPLS_CUDA(timed(w, kkInitSeg, [&] {
+    return launch_init_segments(offsets, nseg, seg_ubase, ubase, rmax, cfg.cutoff, resident_root_ok, &w.ctl_arr[0],
+                                s0.subs, (int32_t)slot_sub_limit(w, s0), s0.tile2sub,
+                                slot_tile_limit(w, s0), s0.chunk2sub, slot_chunk_limit(w, s0), s1.groups,
+                                (int32_t)std::min<int64_t>(std::min(s1.group_cap, std::min(s1.fit_cap, s1.tail_cap)),
+                                                           INT32_MAX),
+                                s1.fit_list, w.stream);
+  }));
+  IPLS_TRY(launch_tail_dev(w, ra, s1, &w.ctl_arr[0]));
+  for (int level = 0; level < levels; ++level) {
+    // the largest sample of the level: that of an n-key subproblem (level 0
+    // may have its own root sample size)
+    const int sample_bound = sample_size_host(std::max<int64_t>(n, 2), level == 0 ? 0 : 1, cfg.k, cfg.root_sample);
+    Slot& X = w.slot[level & 1];
+    Slot& Y = w.slot[(level + 1) & 1];
+    // look-back words start from zero at every level (epoch 1 throughout),
+    // so a replayed graph never meets words of an earlier replay
+    IPLS_CUDA(cudaMemsetAsync(w.status, 0, (size_t)w.status_cap * 8, w.stream));
+    LevelArgs a{};
+    a.dtype = dtype; a.k = cfg.k; a.cutoff = cfg.cutoff; a.rmax = rmax;
+    a.root_sample = cfg.root_sample; a.seed = cfg.seed; a.exact_only = cfg.exact_only;
+    a.use_tables = (cfg.flags & IPLS_FLAG_THRESHOLD_INDEX) && !cfg.exact_only;
+    a.spin_limit = cfg.spin_limit; a.epoch = 1; a.level = level;
+    a.buf[0] = nullptr; a.buf[1] = w.scratch;
+    a.nsub = (int32_t)slot_sub_limit(w, X);
+    a.subs = X.subs; a.models = X.models; a.counts = X.counts; a.tabs = X.tabs; a.bases = X.bases;
+    a.tile2sub = X.tile2sub; a.ntiles = slot_tile_limit(w, X); a.chunk2sub = X.chunk2sub;
+    a.nchunks = slot_chunk_limit(w, X);
+    a.status = w.status; a.tile_off = w.tile_off; a.bids = w.bids;
+    a.ctl = &w.ctl_arr[level + 1]; a.run = w.run; a.cnt = &w.ctl_arr[level];
+    a.next_subs = Y.subs; a.next_sub_cap = (int32_t)slot_sub_limit(w, Y);
+    a.next_tile2sub = Y.tile2sub; a.next_tile_cap = slot_tile_limit(w, Y);
+    a.next_chunk2sub = Y.chunk2sub; a.next_chunk_cap = slot_chunk_limit(w, Y);
+    a.groups = X.groups;
+    a.group_cap = (int32_t)std::min<int64_t>(std::min(X.group_cap, std::min(X.fit_cap, X.tail_cap)), INT32_MAX);
+    a.fit_list = X.fit_list;
+    a.fills = X.fills; a.fill_cap = (int32_t)std::min<int64_t>(X.fill_cap, INT32_MAX);
+    a.trace = traced ? c->trace_grid : nullptr;
+    a.trace_cap = traced ? cfg.trace_cap : 0;
+    a.trace_base = 0;
+    a.trace_ctr = traced ? w.trace_ctr : nullptr;
+    a.trace_knots = traced ? c->trace_knots : nullptr;
+    a.knot_cap = c->knot_cap;
+    a.max_sample = sample_bound;
+    a.pl2_leaves = cfg.pl2_leaves;
+    a.knots = cfg.pl2_leaves > 0 ? X.knots : nullptr;
+    const int sms = c->num_sms;
+    IPLS_CUDA(timed(w, kkFit, [&] { return launch_fit(a, w.stream, sample_bound, sms); }, level));
+    IPLS_CUDA(timed(w, kkHist, [&] { return launch_hist(a, w.stream, 0, sms); }, level));
+    IPLS_CUDA(timed(w, kkCheck, [&] { return launch_check(a, w.stream, sample_bound, sms); }, level));
+    IPLS_CUDA(timed(w, kkRehist, [&] { return launch_hist(a, w.stream, 1, sms); }, level));
+    IPLS_CUDA(timed(w, kkScan, [&] { return launch_scan(a, w.stream, sms); }, level));
+    IPLS_CUDA(timed(w, kkTileScan, [&] { return launch_tilescan(a, w.stream, sms * 8); }, level));
+    IPLS_CUDA(timed(w, kkScatter, [&] { return launch_scatter(a, w.stream, sms); }, level));
+    IPLS_TRY(launch_tail_dev(w, ra, X, &w.ctl_arr[level + 1]));
+    IPLS_CUDA(timed(w, kkFill, [&] {
+      return launch_fill(X.fills, a.fill_cap, dtype, w.stream, &w.ctl_arr[level + 1], sms * 8, w.run);
+    }));
+  }
+  IPLS_CUDA(cudaMemcpyAsync(w.h_ctl_arr, w.ctl_arr, (size_t)(levels + 1) * sizeof(LevelCtl),
+                            cudaMemcpyDeviceToHost, w.stream));
+  IPLS_CUDA(cudaMemcpyAsync(w.h_run, w.run, sizeof(RunStatus), cudaMemcpyDeviceToHost, w.stream));
+  IPLS_CUDA(cudaMemcpyAsync(w.h_trace_ctr, w.trace_ctr, sizeof(long long), cudaMemcpyDeviceToHost, w.stream));
+  return IPLS_OK;
+}
+
+// Levels enqueued for n keys: one per factor of about 2^8 above the
+// block-resident size, plus one.
+int device_levels_for(int64_t n) {
+  int L = 1;
+  for (int64_t m = n; m > 8192 && L < kDevLevelsMax; m >>= 8) ++L;
+  return L;
+}
+
 // The level loop.  Level-0 subproblems are either the whole array or the
 // segments; each level runs fit -> hist -> check -> (re)hist -> scan ->
 // scatter over all its grid subproblems, then the block-resident kernel over
@@ -420,7 +653,94 @@ iplsStatus sort_impl(Workspace& w, void* keys, int64_t n, int dtype, const int64
   const int64_t sub_bound = n / (rmax + 1) + 2;
   const int64_t tile_bound = n / tile + sub_bound + 2;
   const int64_t chunk_bound = tile_bound / kChunkTiles + sub_bound + 2;
-  if (offsets) {
+  int start_level = 0;
+  int64_t moved = 0;
+  if (offsets && (cfg.flags & IPLS_FLAG_GRAPH)) {
+    // device-driven levels, captured once into a CUDA graph per (buffers,
+    // sizes) and replayed
+    const int levels = device_levels_for(n);
+    IPLS_TRY(device_prepare(w, n, nseg, dtype));
+    const Workspace::GraphKey key{keys, offsets, seg_ubase, n, nseg, dtype, levels};
+    if (!(w.graph && w.gkey == key)) {
+      if (w.graph) {
+        cudaGraphExecDestroy(w.graph);
+        w.graph = nullptr;
+      }
+      if (!w.cap_stream) IPLS_CUDA(cudaStreamCreateWithFlags(&w.cap_stream, cudaStreamNonBlocking));
+      IPLS_CUDA(cudaStreamSynchronize(w.stream));
+      const cudaStream_t keep = w.stream;
+      w.stream = w.cap_stream;
+      w.capturing = true;
+      cudaError_t e = cudaStreamBeginCapture(w.stream, cudaStreamCaptureModeRelaxed);
+      iplsStatus st = IPLS_OK;
+      if (e == cudaSuccess) st = device_enqueue(w, n, dtype, offsets, nseg, seg_ubase, ubase, levels);
+      cudaGraph_t g = nullptr;
+      const cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(w.stream, &g) : e;
+      w.stream = keep;
+      w.capturing = false;
+      if (st != IPLS_OK) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return st;
+      }
+      if (e2 != cudaSuccess) return cuda_fail(e2, "capturing the segmented sort");
+      e = cudaGraphInstantiate(&w.graph, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        w.graph = nullptr;
+        return cuda_fail(e, "cudaGraphInstantiate");
+      }
+      w.gkey = key;
+    }
+    IPLS_CUDA(cudaGraphLaunch(w.graph, w.stream));
+    IPLS_CUDA(cudaStreamSynchronize(w.stream));
+    const LevelCtl* H = w.h_ctl_arr;
+    const int64_t sub_cap = std::min(w.slot[0].sub_cap, w.slot[1].sub_cap);
+    auto nsub_at = [&](int L) { return std::min<int64_t>(H[L].nsub_next, sub_cap); };
+    if (w.h_run->error_level > 0) {
+      // the level whose scatter stopped keeps its keys where its records say:
+      // those in the ping-pong buffer go back to the caller's memory
+      const int L = w.h_run->error_level - 1;
+      IPLS_CUDA(launch_restore(w.slot[L & 1].subs, (int32_t)nsub_at(L), dtype, w.scratch, w.stream));
+      IPLS_CUDA(cudaStreamSynchronize(w.stream));
+      if (w.h_run->error == IPLS_ERR_TIMEOUT)
+        return fail(IPLS_ERR_TIMEOUT, "a device-side look-back wait exceeded spin_limit; the keys "
+                                      "hold a permutation of the input");
+      return fail((iplsStatus)w.h_run->error, "device reported status " + std::to_string(w.h_run->error));
+    }
+    for (int L = 0; L <= levels; ++L) {
+      if (!H[L].overflow) continue;
+      // level L-1 listed more than fits: nothing after its scatter ran
+      if (L > 0) {
+        IPLS_CUDA(launch_restore(w.slot[(L - 1) & 1].subs, (int32_t)nsub_at(L - 1), dtype, w.scratch, w.stream));
+        IPLS_CUDA(cudaStreamSynchronize(w.stream));
+      }
+      return fail(IPLS_ERR_INTERNAL, "a level list capacity was exceeded");
+    }
+    for (int L = 0; L < levels; ++L) {
+      const int64_t ns = nsub_at(L);
+      if (ns == 0) break;
+      w.stats.grid_levels += 1;
+      w.stats.grid_passes += ns;
+      w.stats.fallback_passes += H[L + 1].fallback;
+      moved += H[L + 1].keys_moved;
+      w.stats.max_bucket_frac = std::max(w.stats.max_bucket_frac, (double)H[L + 1].max_bucket / 1048576.0);
+      if (w.main) {
+        std::lock_guard<std::mutex> lk(c->prof_mu);
+        c->k_bytes[kkHist] += (int64_t)wb * H[L + 1].keys_level;
+        c->k_bytes[kkScatter] += 2 * (int64_t)wb * H[L + 1].keys_moved;
+      }
+    }
+    if (traced) w.trace_grid_count = *w.h_trace_ctr;
+    nsub = nsub_at(levels);
+    ntiles = H[levels].tiles_next;
+    nchunks = H[levels].chunks_next;
+    max_sub_n = H[levels].max_sub_n;
+    start_level = levels;
+    // the host-driven levels that follow start from clean look-back words
+    IPLS_CUDA(cudaMemsetAsync(w.status, 0, (size_t)w.status_cap * 8, w.stream));
+    w.epoch = 1;
+  } else if (offsets) {
     // segments: big ones become level-0 grid subproblems, the rest groups
     Slot& s0 = w.slot[0];
     Slot& s1 = w.slot[1];
@@ -485,8 +805,7 @@ iplsStatus sort_impl(Workspace& w, void* keys, int64_t n, int dtype, const int64
     nsub = 1;
   }
 
-  int level = 0;
-  int64_t moved = 0;
+  int level = start_level;
   while (nsub > 0) {
     if (level > 4096) return fail(IPLS_ERR_INTERNAL, "recursion depth limit exceeded");
     Slot& X = w.slot[level & 1];
@@ -539,11 +858,11 @@ iplsStatus sort_impl(Workspace& w, void* keys, int64_t n, int dtype, const int64
     a.max_sample = max_sample;
     a.pl2_leaves = cfg.pl2_leaves;
     a.knots = cfg.pl2_leaves > 0 ? X.knots : nullptr;
-    IPLS_CUDA(timed(w, kkFit, [&] { return launch_fit(a, w.stream, max_sample); }, level));
+    IPLS_CUDA(timed(w, kkFit, [&] { return launch_fit(a, w.stream, max_sample, c->num_sms); }, level));
     IPLS_CUDA(timed(w, kkHist, [&] { return launch_hist(a, w.stream, 0, occupancy_grid(c, 0, dtype)); }, level));
-    IPLS_CUDA(timed(w, kkCheck, [&] { return launch_check(a, w.stream, max_sample); }, level));
+    IPLS_CUDA(timed(w, kkCheck, [&] { return launch_check(a, w.stream, max_sample, c->num_sms); }, level));
     IPLS_CUDA(timed(w, kkRehist, [&] { return launch_hist(a, w.stream, 1, occupancy_grid(c, 0, dtype)); }, level));
-    IPLS_CUDA(timed(w, kkScan, [&] { return launch_scan(a, w.stream); }, level));
+    IPLS_CUDA(timed(w, kkScan, [&] { return launch_scan(a, w.stream, c->num_sms); }, level));
     IPLS_CUDA(timed(w, kkTileScan, [&] { return launch_tilescan(a, w.stream, c->num_sms * 8); }, level));
     IPLS_CUDA(timed(w, kkScatter, [&] { return launch_scatter(a, w.stream, occupancy_grid(c, 1, dtype)); }, level));
     IPLS_CUDA(cudaMemcpyAsync(w.h_ctl, w.ctl, sizeof(LevelCtl), cudaMemcpyDeviceToHost, w.stream));
@@ -675,7 +994,9 @@ __global__ void k_init_segments(const int64_t* off, int64_t nseg, const uint64_t
         ctl->overflow = 1;
       } else {
         groups[g] = Group{off[q], nullptr, (int32_t)cq, 0, 0, 1, g, 0, ub};
-        fit_list[atomicAdd(&ctl->nfit, 1)] = g;
+        const int f = atomicAdd(&ctl->nfit, 1);
+        if (f < group_cap) fit_list[f] = g;
+        else ctl->overflow = 1;
       }
     }
     if (big) {
@@ -780,6 +1101,12 @@ void ws_free(Workspace& w) {
   if (w.h_slow) cudaFreeHost(w.h_slow);
   if (w.h_seg_off) cudaFreeHost(w.h_seg_off);
   if (w.h_seg_ubase) cudaFreeHost(w.h_seg_ubase);
+  dev_free(c, w.ctl_arr, (kDevLevelsMax + 1) * sizeof(LevelCtl));
+  dev_free(c, w.trace_ctr, sizeof(long long));
+  if (w.h_ctl_arr) cudaFreeHost(w.h_ctl_arr);
+  if (w.h_trace_ctr) cudaFreeHost(w.h_trace_ctr);
+  if (w.graph) cudaGraphExecDestroy(w.graph);
+  if (w.cap_stream) cudaStreamDestroy(w.cap_stream);
   for (auto& p : w.pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
   for (cudaEvent_t e : w.spare_events) cudaEventDestroy(e);
   if (w.own_stream && w.stream) cudaStreamDestroy(w.stream);
@@ -908,6 +1235,7 @@ void serve_loop(iplsCtx c, int slot) {
       for (uint64_t t : batch) {
         c->reqs[t].st = st;
         c->reqs[t].done = true;
+        if (st != IPLS_OK) c->reqs[t].msg = g_last_error;
       }
       c->inflight_bytes -= bytes;
       if (c->batch_log.size() < 65536) c->batch_log.push_back(rec);
@@ -1185,7 +1513,7 @@ iplsStatus iplsSubmit(iplsCtx c, void* keys, int64_t n, iplsDtype dtype, uint64_
   {
     std::lock_guard<std::mutex> lk(c->q_mu);
     const uint64_t t = c->next_ticket++;
-    c->reqs[t] = iplsContext::Request{keys, n, (int)dtype, n <= 1 ? IPLS_OK : IPLS_PENDING, n <= 1};
+    c->reqs[t] = iplsContext::Request{keys, n, (int)dtype, n <= 1 ? IPLS_OK : IPLS_PENDING, n <= 1, {}};
     if (n > 1) c->queue.push_back(t);
     const iplsStatus ws = start_workers(c);
     if (ws != IPLS_OK) {
@@ -1204,6 +1532,7 @@ iplsStatus iplsPoll(iplsCtx c, uint64_t ticket) {
   std::lock_guard<std::mutex> lk(c->q_mu);
   auto it = c->reqs.find(ticket);
   if (it == c->reqs.end()) return fail(IPLS_ERR_ARG, "unknown ticket");
+  if (it->second.done && it->second.st != IPLS_OK) g_last_error = it->second.msg;
   return it->second.done ? it->second.st : IPLS_PENDING;
 }
 
@@ -1215,6 +1544,7 @@ iplsStatus iplsWait(iplsCtx c, uint64_t ticket, int64_t timeout_us) {
   auto done = [&] { return it->second.done; };
   if (timeout_us < 0) c->done_cv.wait(lk, done);
   else c->done_cv.wait_for(lk, std::chrono::microseconds(timeout_us), done);
+  if (it->second.done && it->second.st != IPLS_OK) g_last_error = it->second.msg;
   return it->second.done ? it->second.st : IPLS_PENDING;
 }
 

@@ -181,6 +181,9 @@ struct LevelCtl {
 struct RunStatus {
   int32_t error;         // 0 or a negative iplsStatus
   int32_t where;         // which wait gave up (diagnostics)
+  int32_t error_level;   // 1 + the first grid level whose scatter moved nothing
+                         // because of an error (0: none)
+  int32_t pad;
   int64_t trace_count;
   int64_t resident_passes;
   int64_t resident_fallback;
@@ -209,7 +212,7 @@ struct SlowCtl {
   int32_t pool_used;   // splitter-pool slots taken by this tail sweep
   int32_t fit_ticket;  // next task of k_tail_fit's persistent warps
   int32_t wcount;
-  int32_t pad;
+  int32_t sweep;       // device-driven levels: tasks of the second sweep (0: none)
 };
 
 // Splitters of a tail task whose tree has more than kTailSplit of them (one
@@ -273,6 +276,13 @@ struct LevelArgs {
   int64_t trace_base;
   float* trace_knots;    // PL2 knots of grid records (pl2_leaves + 1 each), or NULL
   int64_t knot_cap;      // records with room in trace_knots
+  // Device-driven levels (no host round trip between levels): when cnt is
+  // set, this level's subproblem, tile and chunk counts are the previous
+  // level's nsub_next, tiles_next and chunks_next (written by k_scan or
+  // k_init_segments), capped by nsub, ntiles and nchunks, which are then
+  // capacities; a level after an overflow or a device error does nothing.
+  const LevelCtl* cnt;
+  long long* trace_ctr;  // device-driven levels: next free grid trace record
 };
 
 struct ResidentArgs {
@@ -302,7 +312,36 @@ struct ResidentArgs {
   RunStatus* run;
   struct iplsTraceRecDev* trace;   // block-resident passes append here
   int64_t trace_cap;
+  // Device-driven levels: the group counts are those gcnt (the level's
+  // LevelCtl) holds, or for a second sweep (sweep = 1) slow_ctl->sweep; the
+  // kernels then loop over the tasks with a fixed grid.
+  LevelCtl* gcnt;
+  int32_t sweep;
+  int32_t device_counts;
 };
+
+// Tasks of a tail launch: host-given counts, or (device-driven levels) the
+// counts the level's k_scan left in *gcnt -- none once the level overflowed,
+// a device error was raised, or the two ends of the group list met (which
+// marks the level as overflowed for the host to see).
+__device__ __forceinline__ int32_t tail_count(const ResidentArgs& a, bool large) {
+  if (!a.device_counts) return (large && a.large_from_end) ? a.nlarge : a.ngroups;
+  // a level whose scatter stopped on an error has nothing to finish
+  if (*reinterpret_cast<const volatile int32_t*>(&a.run->error_level) != 0) return 0;
+  if (a.sweep) return *reinterpret_cast<const volatile int32_t*>(&a.slow_ctl->sweep);
+  const volatile LevelCtl* g = a.gcnt;
+  if (g->overflow) return 0;
+  if ((int64_t)g->ngroups + g->ngroups_large > a.group_cap) {
+    a.gcnt->overflow = 1;
+    return 0;
+  }
+  return large ? g->ngroups_large : g->ngroups;
+}
+__device__ __forceinline__ int32_t tail_nfit(const ResidentArgs& a) {
+  if (!a.device_counts) return a.nfit;
+  if (a.sweep) return tail_count(a, false);
+  return tail_count(a, false) > 0 || tail_count(a, true) > 0 ? a.gcnt->nfit : 0;
+}
 
 // Same layout as iplsTraceRec in the public header.
 struct iplsTraceRecDev {
@@ -315,6 +354,32 @@ struct iplsTraceRecDev {
   int64_t counts[256];
 };
 
+// Counts of a level (device-driven levels read them from the device).
+__device__ __forceinline__ bool level_dead(const LevelArgs& a) {
+  // (after an error the level still launches its scatter, which moves
+  // nothing and records that it stopped there)
+  return a.cnt && (*reinterpret_cast<const volatile int32_t*>(&a.cnt->overflow) != 0 ||
+                   *reinterpret_cast<const volatile int32_t*>(&a.run->error_level) != 0);
+}
+__device__ __forceinline__ int32_t level_nsub(const LevelArgs& a) {
+  if (!a.cnt) return a.nsub;
+  if (level_dead(a)) return 0;
+  const int32_t v = a.cnt->nsub_next;
+  return v < a.nsub ? v : a.nsub;
+}
+__device__ __forceinline__ int64_t level_ntiles(const LevelArgs& a) {
+  if (!a.cnt) return a.ntiles;
+  if (level_dead(a)) return 0;
+  const int64_t v = a.cnt->tiles_next;
+  return v < a.ntiles ? v : a.ntiles;
+}
+__device__ __forceinline__ int64_t level_nchunks(const LevelArgs& a) {
+  if (!a.cnt) return a.nchunks;
+  if (level_dead(a)) return 0;
+  const int64_t v = a.cnt->chunks_next;
+  return v < a.nchunks ? v : a.nchunks;
+}
+
 // Keys of a record: the caller's memory (buf 0, at ubase) or the ping-pong buffer.
 template <class B>
 __host__ __device__ __forceinline__ B* keys_of(int buf, uint64_t ubase, void* const* bufs) {
@@ -322,15 +387,15 @@ __host__ __device__ __forceinline__ B* keys_of(int buf, uint64_t ubase, void* co
 }
 
 // Kernel launchers (defined in the .cu files).
-cudaError_t launch_fit(const LevelArgs& a, cudaStream_t s, int max_sample);
+cudaError_t launch_fit(const LevelArgs& a, cudaStream_t s, int max_sample, int sms);
 cudaError_t launch_hist(const LevelArgs& a, cudaStream_t s, int rehist_only, int sms);
-cudaError_t launch_check(const LevelArgs& a, cudaStream_t s, int max_sample);
-cudaError_t launch_scan(const LevelArgs& a, cudaStream_t s);
+cudaError_t launch_check(const LevelArgs& a, cudaStream_t s, int max_sample, int sms);
+cudaError_t launch_scan(const LevelArgs& a, cudaStream_t s, int sms);
 cudaError_t launch_tilescan(const LevelArgs& a, cudaStream_t s, int grid);
 cudaError_t launch_scatter(const LevelArgs& a, cudaStream_t s, int sms);
 cudaError_t launch_tail_fit(const ResidentArgs& a, cudaStream_t s, int sms);
 // large = 0: tasks of up to 4096 keys (256-thread blocks); 1: the rest.
-cudaError_t launch_resident(const ResidentArgs& a, cudaStream_t s, int large);
+cudaError_t launch_resident(const ResidentArgs& a, cudaStream_t s, int large, int sms);
 cudaError_t launch_slow(const ResidentArgs& a, cudaStream_t s, int sms);
 // groups[i] = the fitted tail task of list[i], fit_list[i] = i (i < n).
 cudaError_t launch_slow_groups(const SlowTask* list, int32_t n, Group* groups, int32_t* fit_list,
@@ -348,7 +413,16 @@ cudaError_t launch_init_segments(const int64_t* offsets, int64_t nseg, const uin
                                  int64_t chunk_cap, Group* groups, int32_t group_cap,
                                  int32_t* fit_list, cudaStream_t s);
 int resident_rmax(int cutoff);
-cudaError_t launch_fill(const Fill* fills, int32_t nfill, int dtype, cudaStream_t s);
+// cnt (device-driven levels): nfill is then a capacity and the count is
+// cnt->nfill (nothing once the level overflowed).
+cudaError_t launch_fill(const Fill* fills, int32_t nfill, int dtype, cudaStream_t s,
+                        const LevelCtl* cnt = nullptr, int grid = 0, const RunStatus* run = nullptr);
+// Device-driven second sweep: when the first sweep queued at least
+// kTailSweepMin children (and the list fits), turns them into the sweep's
+// groups, sets ctl->sweep to their number and restarts the child list;
+// otherwise sets ctl->sweep = 0 and leaves them to k_slow.
+cudaError_t launch_sweep_groups(const SlowTask* list, SlowCtl* ctl, int32_t list_cap, Group* groups,
+                                int32_t* fit_list, int32_t group_cap, cudaStream_t s);
 cudaError_t launch_init_tiles(int32_t* tile2sub, int64_t ntiles, int32_t value, cudaStream_t s);
 // Copies the keys of the level's subproblems held in the scratch buffer back
 // into the caller's memory (after a device-side error).

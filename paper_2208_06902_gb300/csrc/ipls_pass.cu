@@ -88,8 +88,8 @@ __device__ int gather_sorted_sample(const LevelArgs& a, const Sub& sub,
 // (eight fits per block would leave most SMs idle).
 constexpr int kFitWarpsG = 8;
 constexpr int kWarpFitMin = 1024;
-__host__ __device__ __forceinline__ bool warp_fits(const LevelArgs& a) {
-  return !a.use_tables && a.nsub >= kWarpFitMin;
+__host__ __device__ __forceinline__ bool warp_fits(const LevelArgs& a, int32_t nsub) {
+  return !a.use_tables && nsub >= kWarpFitMin;
 }
 // Subproblems that take PL2 (when enabled) are fitted by a block.
 __device__ __forceinline__ bool takes_pl2(const LevelArgs& a, const Sub& sub, int S) {
@@ -97,9 +97,9 @@ __device__ __forceinline__ bool takes_pl2(const LevelArgs& a, const Sub& sub, in
   // in which every sample does; it reserves no PL2 scratch)
   return a.pl2_leaves > 0 && sub.n > kPL2MinKeys && S <= kPL2MaxSample && a.max_sample <= kPL2MaxSample;
 }
-__device__ __forceinline__ bool fit_by_warp(const LevelArgs& a, const Sub& sub) {
+__device__ __forceinline__ bool fit_by_warp(const LevelArgs& a, const Sub& sub, int32_t nsub) {
   const int S = (int)sample_size(sub.n, sub.level, a.k, a.root_sample);
-  return warp_fits(a) && S <= kResidentSample && !takes_pl2(a, sub, S);
+  return warp_fits(a, nsub) && S <= kResidentSample && !takes_pl2(a, sub, S);
 }
 
 template <class K>
@@ -110,10 +110,10 @@ __global__ void __launch_bounds__(kFitWarpsG * 32) k_fit_warp(LevelArgs a) {
   __shared__ FitShared fs[kFitWarpsG];
   __shared__ Model mod[kFitWarpsG];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int s = blockIdx.x * kFitWarpsG + warp;
-  if (s >= a.nsub) return;
+  const int32_t nsub = level_nsub(a);
+  for (int s = blockIdx.x * kFitWarpsG + warp; s < nsub; s += gridDim.x * kFitWarpsG) {
   const Sub sub = a.subs[s];
-  if (!fit_by_warp(a, sub)) return;
+  if (!fit_by_warp(a, sub, nsub)) continue;
   const int S = (int)sample_size(sub.n, sub.level, a.k, a.root_sample);
   Ord* so = reinterpret_cast<Ord*>(smem_raw) + warp * kResidentSample;
   const uint64_t st = stream_key(a.seed, sub.off, sub.n, sub.level);
@@ -128,9 +128,11 @@ __global__ void __launch_bounds__(kFitWarpsG * 32) k_fit_warp(LevelArgs a) {
   for (int i = lane; i < (int)(sizeof(Model) / 8); i += 32) md[i] = ms[i];
   for (int b = lane; b < kMaxK; b += 32) a.counts[(size_t)s * kMaxK + b] = 0;
   if (lane == 0) {
-    a.tabs[s].ok = 0;
+    if (a.use_tables) a.tabs[s].ok = 0;
     a.subs[s].flags = 0;
     atomicAdd((unsigned long long*)&a.ctl->keys_level, (unsigned long long)sub.n);
+  }
+  __syncwarp();
   }
 }
 
@@ -144,9 +146,11 @@ __global__ void __launch_bounds__(kFitThreads) k_fit(LevelArgs a) {
   __shared__ ThrTable tab;
   __shared__ int scan_tmp[kL1Max];
   Ord* so = reinterpret_cast<Ord*>(smem);
-  const int s = blockIdx.x;
+  const int32_t nsub = level_nsub(a);
+  for (int s = blockIdx.x; s < nsub; s += gridDim.x) {
+  __syncthreads();  // the previous subproblem is done with shared memory
   const Sub sub = a.subs[s];
-  if (fit_by_warp(a, sub)) return;  // k_fit_warp fits this one
+  if (fit_by_warp(a, sub, nsub)) continue;  // k_fit_warp fits this one
   const int S = gather_sorted_sample<K>(a, sub, so);
   bool pl2 = false;
   if (takes_pl2(a, sub, S)) {
@@ -167,13 +171,14 @@ __global__ void __launch_bounds__(kFitThreads) k_fit(LevelArgs a) {
   if (sm.l.kind == kLinear && a.use_tables) {
     build_thr_table<K>(sm.l, &tab, scan_tmp);
     copy_table(&a.tabs[s], &tab);
-  } else if (threadIdx.x == 0) {
+  } else if (threadIdx.x == 0 && a.use_tables) {
     a.tabs[s].ok = 0;
   }
   for (int b = threadIdx.x; b < kMaxK; b += blockDim.x) a.counts[(size_t)s * kMaxK + b] = 0;
   if (threadIdx.x == 0) {
     a.subs[s].flags = 0;
     atomicAdd((unsigned long long*)&a.ctl->keys_level, (unsigned long long)sub.n);
+  }
   }
 }
 
@@ -193,7 +198,7 @@ __global__ void __launch_bounds__(kPassThreads, 4) k_hist(LevelArgs a, int rehis
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int i = threadIdx.x; i < kWarps * kMaxK; i += blockDim.x) (&hist[0][0])[i] = 0;
   for (int i = threadIdx.x; i < kMaxK; i += blockDim.x) acc[i] = 0;
-  const int64_t nt = a.ntiles;
+  const int64_t nt = level_ntiles(a);
   const int64_t t0 = nt * blockIdx.x / gridDim.x, t1 = nt * (blockIdx.x + 1) / gridDim.x;
   int cur = -1;
   bool use_tab = false;
@@ -307,7 +312,9 @@ __global__ void __launch_bounds__(kFitThreads) k_check(LevelArgs a) {
   __shared__ Model sm;
   __shared__ int s_redo;
   Ord* so = reinterpret_cast<Ord*>(smem);
-  const int s = blockIdx.x;
+  const int32_t nsub = level_nsub(a);
+  for (int s = blockIdx.x; s < nsub; s += gridDim.x) {
+  __syncthreads();  // the previous subproblem is done with shared memory
   const Sub sub = a.subs[s];
   if (threadIdx.x == 0) s_redo = 0;
   __syncthreads();
@@ -323,7 +330,7 @@ __global__ void __launch_bounds__(kFitThreads) k_check(LevelArgs a) {
     }
   }
   __syncthreads();
-  if (!s_redo) return;
+  if (!s_redo) continue;
   copy_model(&sm, &gm);
   __syncthreads();
   const int S = gather_sorted_sample<K>(a, sub, so);
@@ -331,9 +338,10 @@ __global__ void __launch_bounds__(kFitThreads) k_check(LevelArgs a) {
   copy_model(&a.models[s], &sm);
   for (int b = threadIdx.x; b < kMaxK; b += blockDim.x) a.counts[(size_t)s * kMaxK + b] = 0;
   if (threadIdx.x == 0) {
-    a.tabs[s].ok = 0;
+    if (a.use_tables) a.tabs[s].ok = 0;
     a.subs[s].flags |= kRehist;
     atomicAdd(&a.ctl->nrehist, 1);
+  }
   }
 }
 
@@ -370,7 +378,11 @@ __global__ void __launch_bounds__(256) k_scan(LevelArgs a) {
   __shared__ int64_t cnt[256];
   __shared__ int64_t bas[257];
   __shared__ int s_skip;
-  const int s = blockIdx.x, b = threadIdx.x;
+  __shared__ long long s_rec;
+  const int b = threadIdx.x;
+  const int32_t nsub = level_nsub(a);
+  for (int s = blockIdx.x; s < nsub; s += gridDim.x) {
+  __syncthreads();  // the previous subproblem is done with shared memory
   const Sub sub = a.subs[s];
   const Model& m = a.models[s];
   const int nb = m.l.nb;
@@ -381,16 +393,23 @@ __global__ void __launch_bounds__(256) k_scan(LevelArgs a) {
   const int64_t ex = block_exclusive_scan256(c, tmp);
   bas[b] = ex;
   if (b == 255) bas[256] = ex + c;
-  if (b == 0) s_skip = 0;
+  if (b == 0) {
+    s_skip = 0;
+    // trace record of this pass: trace_base + s, or (device-driven levels)
+    // the next free record
+    s_rec = a.trace_cap <= 0 ? 0
+            : a.trace_ctr ? (long long)atomicAdd((unsigned long long*)a.trace_ctr, 1ULL)
+                          : a.trace_base + s;
+  }
   __syncthreads();
   int64_t* gb = a.bases + (size_t)s * 257;
   gb[b] = bas[b];
   if (b == 0) gb[256] = bas[256];
   const bool eq = splitter && (b & 1) && b < nb;
   if (eq && c == sub.n) s_skip = 1;
-  // trace: this level's grid passes own records trace_base + s
-  if (a.trace_cap > 0 && a.trace_base + s < a.trace_cap) {
-    iplsTraceRecDev& r = a.trace[a.trace_base + s];
+  const long long rec = s_rec;
+  if (a.trace_cap > 0 && rec < a.trace_cap) {
+    iplsTraceRecDev& r = a.trace[rec];
     if (b == 0) {
       r.off = sub.off; r.n = sub.n; r.level = sub.level; r.kind = m.l.kind;
       r.capped = m.l.capped; r.nbuckets = nb; r.S = m.l.S; r.D = m.l.D; r.A = m.l.A;
@@ -398,9 +417,9 @@ __global__ void __launch_bounds__(256) k_scan(LevelArgs a) {
     }
     r.counts[b] = c;
     // the PL2 knots of the pass (zeros for another kind of model)
-    if (a.trace_knots && a.pl2_leaves > 0 && a.trace_base + s < a.knot_cap) {
+    if (a.trace_knots && a.pl2_leaves > 0 && rec < a.knot_cap) {
       const int M1 = a.pl2_leaves + 1;
-      float* kr = a.trace_knots + (size_t)(a.trace_base + s) * M1;
+      float* kr = a.trace_knots + (size_t)rec * M1;
       const float* kn = a.knots + (size_t)s * M1;
       for (int j = b; j < M1; j += 256) kr[j] = m.l.kind == kPL2 ? kn[j] : 0.0f;
     }
@@ -442,7 +461,8 @@ __global__ void __launch_bounds__(256) k_scan(LevelArgs a) {
       } else {
         a.groups[g] = Group{sub.off + bas[b], nullptr, (int32_t)c, sub.level + 1, dst_buf, 1, g, 0, sub.ubase};
         const int f = atomicAdd(&a.ctl->nfit, 1);
-        a.fit_list[f] = g;
+        if (f < a.group_cap) a.fit_list[f] = g;
+        else a.ctl->overflow = 1;
       }
     }
   }
@@ -474,7 +494,7 @@ __global__ void __launch_bounds__(256) k_scan(LevelArgs a) {
     for (int q = 0; q < nb; ++q) mx = cnt[q] > mx ? cnt[q] : mx;
     const long long frac = (long long)((double)mx * 1048576.0 / (double)sub.n);
     atomicMax((unsigned long long*)&a.ctl->max_bucket, (unsigned long long)frac);
-  }
+  }  }
 }
 
 // ---------------------------------------------------------------------------
@@ -499,12 +519,13 @@ __global__ void __launch_bounds__(256) k_tilescan(LevelArgs a) {
   __shared__ int s_c;
   const int b = threadIdx.x;
   const unsigned long long ep = (unsigned long long)(a.epoch & 0xFFFF) << 48;
+  const int64_t nchunks = level_nchunks(a);
   for (;;) {
     __syncthreads();
     if (b == 0) s_c = (int)atomicAdd(&a.ctl->ticket, 1u);
     __syncthreads();
     const int c = s_c;
-    if (c >= a.nchunks) break;
+    if (c >= nchunks) break;
     const Sub sub = a.subs[a.chunk2sub[c]];
     if (sub.flags & kSkipScatter) continue;
     const int ci = c - sub.chunk0;
@@ -577,8 +598,12 @@ __global__ void __launch_bounds__(kScatterThreads, 2) k_scatter(LevelArgs a) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // an earlier kernel gave up (bounded wait): move nothing, so that every
   // key of the level stays in its source buffer for the host to restore
-  if (*reinterpret_cast<volatile int32_t*>(&a.run->error) != 0) return;
-  const int64_t nt = a.ntiles;
+  if (*reinterpret_cast<volatile int32_t*>(&a.run->error) != 0) {
+    // the first level that moved nothing (its keys are where its records say)
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(&a.run->error_level, 0, a.level + 1);
+    return;
+  }
+  const int64_t nt = level_ntiles(a);
   const int64_t t0 = nt * blockIdx.x / gridDim.x, t1 = nt * (blockIdx.x + 1) / gridDim.x;
   for (int i = threadIdx.x; i < kSWarps * kMaxK; i += blockDim.x) (&sh.peer[0][0])[i] = 0u;
   for (int64_t t = t0; t < t1; ++t) {
@@ -721,35 +746,54 @@ static cudaError_t by_dtype(int dtype, F f) {
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_fit(const LevelArgs& a, cudaStream_t s, int max_sample) {
+// The dynamic shared memory of k_fit and k_check depends on the level's
+// largest sample; their limit is set once to the largest any call can ask
+// for (a root sample of 16384 keys), never lowered, since it is a property of
+// the kernel shared by every thread and stream of the process.
+constexpr int kRootSampleMax = 16384;
+template <class K>
+size_t fit_smem_max() {
+  return (size_t)kRootSampleMax * sizeof(typename KT<K>::Ord);
+}
+
+// Device-driven levels (a.cnt set) launch a fixed grid over the level's
+// capacity; the kernels loop over the subproblems the device counted.
+static int64_t loop_grid(const LevelArgs& a, int64_t per_block, int64_t fixed) {
+  const int64_t need = (a.nsub + per_block - 1) / per_block;
+  return a.cnt ? (need < fixed ? need : fixed) : need;
+}
+
+cudaError_t launch_fit(const LevelArgs& a, cudaStream_t s, int max_sample, int sms) {
   if (a.nsub <= 0) return cudaSuccess;
   return by_dtype(a.dtype, [&](auto* tag) {
     using K = std::remove_pointer_t<decltype(tag)>;
     using Ord = typename KT<K>::Ord;
-    if (warp_fits(a)) {
+    if (a.cnt || warp_fits(a, a.nsub)) {
       const size_t wsmem = (size_t)kFitWarpsG * kResidentSample * sizeof(Ord);
       cudaFuncSetAttribute(k_fit_warp<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem);
-      k_fit_warp<K><<<(a.nsub + kFitWarpsG - 1) / kFitWarpsG, kFitWarpsG * 32, wsmem, s>>>(a);
+      k_fit_warp<K><<<(unsigned)loop_grid(a, kFitWarpsG, (int64_t)sms * 4), kFitWarpsG * 32, wsmem, s>>>(a);
       const cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) return e;
-      if (max_sample <= kResidentSample && a.pl2_leaves == 0) return cudaSuccess;  // all went to warps
+      if (!a.cnt && max_sample <= kResidentSample && a.pl2_leaves == 0) return cudaSuccess;  // all went to warps
     }
     size_t smem = (size_t)max_sample * sizeof(Ord);
     if (a.pl2_leaves > 0 && max_sample <= kPL2MaxSample)
       smem = ((smem + 15) & ~(size_t)15) + (size_t)kPL2MaxSample * 12;
-    cudaFuncSetAttribute(k_fit<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_fit<K><<<a.nsub, kFitThreads, smem, s>>>(a);
+    if (smem > fit_smem_max<K>()) return cudaErrorInvalidValue;
+    cudaFuncSetAttribute(k_fit<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fit_smem_max<K>());
+    k_fit<K><<<(unsigned)loop_grid(a, 1, (int64_t)sms * 2), kFitThreads, smem, s>>>(a);
     return cudaGetLastError();
   });
 }
 
-cudaError_t launch_check(const LevelArgs& a, cudaStream_t s, int max_sample) {
+cudaError_t launch_check(const LevelArgs& a, cudaStream_t s, int max_sample, int sms) {
   if (a.nsub <= 0) return cudaSuccess;
   return by_dtype(a.dtype, [&](auto* tag) {
     using K = std::remove_pointer_t<decltype(tag)>;
     const size_t smem = (size_t)max_sample * sizeof(typename KT<K>::Ord);
-    cudaFuncSetAttribute(k_check<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_check<K><<<a.nsub, kFitThreads, smem, s>>>(a);
+    if (smem > fit_smem_max<K>()) return cudaErrorInvalidValue;
+    cudaFuncSetAttribute(k_check<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fit_smem_max<K>());
+    k_check<K><<<(unsigned)loop_grid(a, 1, (int64_t)sms * 2), kFitThreads, smem, s>>>(a);
     return cudaGetLastError();
   });
 }
@@ -774,11 +818,11 @@ cudaError_t launch_hist(const LevelArgs& a, cudaStream_t s, int rehist_only, int
   });
 }
 
-cudaError_t launch_scan(const LevelArgs& a, cudaStream_t s) {
+cudaError_t launch_scan(const LevelArgs& a, cudaStream_t s, int sms) {
   if (a.nsub <= 0) return cudaSuccess;
   return by_dtype(a.dtype, [&](auto* tag) {
     using K = std::remove_pointer_t<decltype(tag)>;
-    k_scan<K><<<a.nsub, 256, 0, s>>>(a);
+    k_scan<K><<<(unsigned)loop_grid(a, 1, (int64_t)sms * 8), 256, 0, s>>>(a);
     return cudaGetLastError();
   });
 }

@@ -29,6 +29,8 @@
 //
 // The paper's base case is SkaSort for n <= 2^12 (Ch.4); any exact sort
 // gives the same, unique result.
+#include <algorithm>
+
 #include "ipls_device.cuh"
 
 namespace ipls {
@@ -61,6 +63,7 @@ __global__ void __launch_bounds__(kFitWarps * 32) k_tail_fit(ResidentArgs a) {
   __shared__ TailModel tm[kFitWarps];
   __shared__ unsigned rcnt[kFitWarps][256], rpeer[kFitWarps][256];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int32_t nfit = tail_nfit(a);
   for (int i = lane; i < 256; i += 32) rpeer[warp][i] = 0u;
   unsigned char* slot = smem_raw + (size_t)warp * fit_slot_bytes<Ord>();
   Ord* so = reinterpret_cast<Ord*>(slot);
@@ -71,7 +74,7 @@ __global__ void __launch_bounds__(kFitWarps * 32) k_tail_fit(ResidentArgs a) {
     int task = 0;
     if (lane == 0) task = atomicAdd(&a.slow_ctl->fit_ticket, 1);
     task = __shfl_sync(0xffffffffu, task, 0);
-    if (task >= a.nfit) break;
+    if (task >= nfit) break;
     const Group g = a.groups[a.fit_list[task]];
     int S = (int)sample_size(g.n, g.level, a.k, a.root_sample);
     if (S > kResidentSample) S = kResidentSample;  // never planned by the host
@@ -506,19 +509,19 @@ static_assert(kResidentMax <= (1 << kPosBits), "positions must fit the packed wo
 
 // kThreads threads, tasks of at most kCap keys; the small size takes tasks
 // of up to kTailSmall keys, the large one the rest (each skips the other's).
+// One task: the group at list position gi (all threads of the block).
 template <class K, int kThreads, int kCap>
-__global__ void __launch_bounds__(kThreads, kCap == kResidentMax ? 2 : 4) k_tail(ResidentArgs a) {
+__device__ __forceinline__ void tail_task(const ResidentArgs& a, int gi, unsigned char* smem_raw) {
   using T = KT<K>;
   using Bits = typename T::Bits;
   using Ord = typename T::Ord;
   constexpr int kW = kThreads / 32;     // warps
   constexpr int kPT = kCap / kThreads;  // keys per thread
   constexpr Ord kSpan = (Ord)1 << (sizeof(Ord) * 8 - kPosBits);
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   TailSmem<K, kCap, kW>& sh = *reinterpret_cast<TailSmem<K, kCap, kW>*>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool large = kCap == kResidentMax;
-  const Group g = a.groups[large && a.large_from_end ? a.group_cap - 1 - (int)blockIdx.x : (int)blockIdx.x];
+  const Group g = a.groups[large && a.large_from_end ? a.group_cap - 1 - gi : gi];
   if (large ? g.n <= kTailSmall : g.n > kCap) return;
   const int n = g.n;
   const Bits* src = keys_of<const Bits>(g.buf, g.ubase, a.buf) + g.off;
@@ -841,12 +844,30 @@ __global__ void __launch_bounds__(kThreads, kCap == kResidentMax ? 2 : 4) k_tail
   }
 }
 
+// kThreads threads, tasks of at most kCap keys; the small size takes tasks
+// of up to kTailSmall keys, the large one the rest (each skips the other's).
+// One block per task when the host sized the grid; a fixed grid looping over
+// the tasks on device-driven levels.
+template <class K, int kThreads, int kCap>
+__global__ void __launch_bounds__(kThreads, kCap == kResidentMax ? 2 : 4) k_tail(ResidentArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int32_t count = tail_count(a, kCap == kResidentMax);
+  for (int gi = blockIdx.x; gi < count; gi += gridDim.x) {
+    tail_task<K, kThreads, kCap>(a, gi, smem_raw);
+    __syncthreads();  // the task is done with shared memory
+  }
+}
+
 template <class Bits>
-__global__ void k_fill(const Fill* fills) {
-  const Fill f = fills[blockIdx.x];
+__global__ void k_fill(const Fill* fills, const LevelCtl* cnt, int32_t cap, const RunStatus* run) {
+  int32_t nf = cap;
+  if (cnt) nf = (cnt->overflow || run->error_level) ? 0 : (cnt->nfill < cap ? cnt->nfill : cap);
+  for (int32_t fi = blockIdx.x; fi < nf; fi += gridDim.x) {
+  const Fill f = fills[fi];
   Bits* keys = reinterpret_cast<Bits*>(f.ubase);
   const Bits v = (Bits)f.bits;
   for (int64_t i = threadIdx.x; i < f.n; i += blockDim.x) keys[f.off + i] = v;
+  }
 }
 
 template <class F>
@@ -878,17 +899,19 @@ cudaError_t launch_tail_fit(const ResidentArgs& a, cudaStream_t s, int sms) {
   });
 }
 
-cudaError_t launch_resident(const ResidentArgs& a, cudaStream_t s, int large) {
+cudaError_t launch_resident(const ResidentArgs& a, cudaStream_t s, int large, int sms) {
   return by_dtype_r(a.dtype, [&](auto* tag) {
     using K = std::remove_pointer_t<decltype(tag)>;
     // tasks of up to kTailSmall keys in the small blocks, the rest in the
-    // large ones (every block of the other size returns at once)
+    // large ones; on device-driven levels the counts are capacities and a
+    // fixed grid (eight rounds of resident blocks) loops over the tasks
     if (!large) {
       if (a.ngroups <= 0) return cudaSuccess;
       const size_t ss = sizeof(TailSmem<K, kTailSmall, kRW / 2>);
       cudaFuncSetAttribute(k_tail<K, kResidentThreads / 2, kTailSmall>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
-      k_tail<K, kResidentThreads / 2, kTailSmall><<<a.ngroups, kResidentThreads / 2, ss, s>>>(a);
+      const int g = a.device_counts ? std::min(a.ngroups, sms * 4 * 8) : a.ngroups;
+      k_tail<K, kResidentThreads / 2, kTailSmall><<<g, kResidentThreads / 2, ss, s>>>(a);
       return cudaGetLastError();
     }
     const size_t sl = sizeof(TailSmem<K, kResidentMax, kRW>);
@@ -896,7 +919,8 @@ cudaError_t launch_resident(const ResidentArgs& a, cudaStream_t s, int large) {
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sl);
     const int nl = a.large_from_end ? a.nlarge : a.ngroups;
     if (nl <= 0) return cudaSuccess;
-    k_tail<K, kResidentThreads, kResidentMax><<<nl, kResidentThreads, sl, s>>>(a);
+    const int g = a.device_counts ? std::min(nl, sms * 2 * 8) : nl;
+    k_tail<K, kResidentThreads, kResidentMax><<<g, kResidentThreads, sl, s>>>(a);
     return cudaGetLastError();
   });
 }
@@ -931,12 +955,47 @@ cudaError_t launch_slow_groups(const SlowTask* list, int32_t n, Group* groups, i
   return cudaGetLastError();
 }
 
-cudaError_t launch_fill(const Fill* fills, int32_t nfill, int dtype, cudaStream_t s) {
+__global__ void __launch_bounds__(1024) k_sweep_groups(const SlowTask* list, SlowCtl* ctl, int32_t list_cap,
+                                                      Group* groups, int32_t* fit_list, int32_t group_cap) {
+  __shared__ int32_t s_n;
+  if (threadIdx.x == 0) {
+    int32_t n = ctl->count;
+    if (n < kTailSweepMin || n > list_cap || n > group_cap) n = 0;
+    s_n = n;
+  }
+  __syncthreads();
+  const int32_t n = s_n;
+  for (int32_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const SlowTask t = list[i];
+    groups[i] = Group{t.off, nullptr, t.n, t.level, 0, 1, i, 0, t.ubase};
+    fit_list[i] = i;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ctl->sweep = n;
+    if (n > 0) {  // the child list starts again; whole tasks stay
+      ctl->count = 0;
+      ctl->ticket = 0;
+      ctl->pool_used = 0;
+      ctl->fit_ticket = 0;
+    }
+  }
+}
+
+cudaError_t launch_sweep_groups(const SlowTask* list, SlowCtl* ctl, int32_t list_cap, Group* groups,
+                                int32_t* fit_list, int32_t group_cap, cudaStream_t s) {
+  k_sweep_groups<<<1, 1024, 0, s>>>(list, ctl, list_cap, groups, fit_list, group_cap);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill(const Fill* fills, int32_t nfill, int dtype, cudaStream_t s, const LevelCtl* cnt,
+                        int grid, const RunStatus* run) {
   if (nfill <= 0) return cudaSuccess;
+  const int g = cnt ? (grid < nfill ? grid : nfill) : nfill;
   if (dtype == 0 || dtype == 2)
-    k_fill<unsigned long long><<<nfill, 256, 0, s>>>(fills);
+    k_fill<unsigned long long><<<g, 256, 0, s>>>(fills, cnt, nfill, run);
   else
-    k_fill<unsigned int><<<nfill, 256, 0, s>>>(fills);
+    k_fill<unsigned int><<<g, 256, 0, s>>>(fills, cnt, nfill, run);
   return cudaGetLastError();
 }
 

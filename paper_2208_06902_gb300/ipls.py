@@ -30,6 +30,7 @@ class iplsConfig(ctypes.Structure):
                 ("reserved", ctypes.c_int32 * 3)]
 
 FLAG_THRESHOLD_INDEX = 1
+FLAG_GRAPH = 2
 
 
 class iplsKernelStat(ctypes.Structure):

@@ -181,11 +181,8 @@ def test_sort_batch_of_separate_arrays_matches_the_oracle_pass_by_pass(dtype):
     live = [i for i, n in enumerate(sizes) if n > 1]
     offs = np.concatenate([[0], np.cumsum([sizes[i] for i in live])])
     cat = np.concatenate([xs[i] for i in live])
-    want, recs, _ = oracle.sort_segments(cat, offs, cutoff=64, trace_cap=200_000)
-    g = ctx.trace(as_array=True)
-    o = np.frombuffer(b"".join(bytes(r) for r in recs), oracle.TRACE_DTYPE) if recs else \
-        np.zeros(0, oracle.TRACE_DTYPE)
-    compare_trace_arrays(g, o)
+    want, o, _ = oracle.sort_segments(cat, offs, cutoff=64, trace_cap=200_000, as_array=True)
+    compare_trace_arrays(ctx.trace(as_array=True), o)
     for j, i in enumerate(live):
         got = from_dev(bufs[i], dtype)[: sizes[i]]
         assert np.array_equal(got.view(np.uint8), want[offs[j]:offs[j + 1]].view(np.uint8))
