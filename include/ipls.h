@@ -85,7 +85,9 @@ typedef struct iplsConfig {
                              the splitter tree when a bucket gets more than 4n/k keys.
                              The sorted result is the same either way. */
   int32_t serve_slots;    /* iplsSubmit: batches in flight at once, 1 or 2 (0 = 2) */
-  int32_t reserved[3];
+  int32_t pl2_depth;      /* with pl2_leaves: PL2 only at recursion levels below this
+                             (default 1: the whole array or each segment; 0 = every level) */
+  int32_t reserved[2];
 } iplsConfig;
 
 /* cfg.flags: classify grid-level passes through the exact threshold index

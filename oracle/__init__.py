@@ -51,7 +51,7 @@ KIND_LINEAR, KIND_SPLITTER = 0, 1
 class Cfg(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int32), ("cutoff", ctypes.c_int32),
                 ("root_sample", ctypes.c_int64), ("seed", ctypes.c_uint64),
-                ("pl2_leaves", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("pl2_leaves", ctypes.c_int32), ("pl2_depth", ctypes.c_int32)]
 
 
 class Model(ctypes.Structure):
@@ -150,8 +150,8 @@ def _ptr(a: np.ndarray):
 
 
 def cfg(k: int = 256, cutoff: int = 32, root_sample: int = 0, seed: int = 0,
-        pl2_leaves: int = 0) -> Cfg:
-    return Cfg(k, cutoff, root_sample, seed, pl2_leaves, 0)
+        pl2_leaves: int = 0, pl2_depth: int = 1) -> Cfg:
+    return Cfg(k, cutoff, root_sample, seed, pl2_leaves, pl2_depth)
 
 
 def mix64(z: int) -> int:
@@ -251,14 +251,15 @@ TRACE_DTYPE = np.dtype(Trace)
 
 def sort(keys: np.ndarray, k: int = 256, cutoff: int = 32, root_sample: int = 0,
          seed: int = 0, trace_cap: int = 0, pl2_leaves: int = 0, as_array: bool = False,
-         knots: bool = False):
+         knots: bool = False, pl2_depth: int = 1):
     """Whole IPLS sort (returns a sorted copy, the trace records and the depth).
-    pl2_leaves > 0: subproblems above 8192 keys use the PL2 model.
+    pl2_leaves > 0: subproblems above 8192 keys at levels below pl2_depth
+    (0: every level) use the PL2 model.
     as_array: the trace as a numpy structured array (TRACE_DTYPE) instead of a
     list of records (for large traces).  knots: also return the PL2 knots of
     every record, an array of shape (records, pl2_leaves + 1)."""
     out = np.array(keys, copy=True)
-    c = Cfg(k, cutoff, root_sample, seed, pl2_leaves, 0)
+    c = Cfg(k, cutoff, root_sample, seed, pl2_leaves, pl2_depth)
     # np.zeros leaves untouched pages unallocated: a generous cap costs nothing
     tr = np.zeros(max(trace_cap, 1), TRACE_DTYPE)
     kn = np.zeros((max(trace_cap, 1), pl2_leaves + 1), np.float32) if knots else None
@@ -279,13 +280,13 @@ def sort(keys: np.ndarray, k: int = 256, cutoff: int = 32, root_sample: int = 0,
 
 def sort_segments(keys: np.ndarray, offsets, k: int = 256, cutoff: int = 32,
                   root_sample: int = 0, seed: int = 0, trace_cap: int = 0, pl2_leaves: int = 0,
-                  as_array: bool = False):
+                  as_array: bool = False, pl2_depth: int = 1):
     """IPLS on each segment keys[off[i]:off[i+1]], each a level-0 subproblem
     keyed by its own offset (returns sorted copy, trace records, depth).
     as_array: the trace as a numpy structured array (TRACE_DTYPE)."""
     out = np.array(keys, copy=True)
     off = np.ascontiguousarray(offsets, np.int64)
-    c = Cfg(k, cutoff, root_sample, seed, pl2_leaves, 0)
+    c = Cfg(k, cutoff, root_sample, seed, pl2_leaves, pl2_depth)
     tr = np.zeros(max(trace_cap, 1), TRACE_DTYPE)
     cnt = ctypes.c_int64(0)
     lv = ctypes.c_int32(0)

@@ -72,9 +72,9 @@ struct OracleCfg {
   int64_t root_sample;  // sample size at level 0; 0 = the alpha*k-1 formula
   uint64_t seed;        // seed of the sampling stream
   int32_t pl2_leaves;   // 0: FMCD everywhere; else PL2 with this many leaves
-                        // (a power of two, 2..64) for subproblems of more
+                        // (a power of two, 2..1024) for subproblems of more
                         // than kPL2MinKeys keys
-  int32_t pad;
+  int32_t pl2_depth;    // PL2 only at levels below this (0: at every level)
 };
 
 // PL2 is used for subproblems larger than this (smaller ones keep FMCD).
@@ -566,6 +566,7 @@ void partition_pass(const T* src, int64_t n, int64_t off, int32_t level,
   // splitter tree on no progress or when a bucket holds more than 4n/k keys
   std::vector<float> knots;
   if (usable && cfg.pl2_leaves > 0 && n > kPL2MinKeys && S <= kPL2MaxSample &&
+      (cfg.pl2_depth == 0 || level < cfg.pl2_depth) &&
       pl2_fit<T>(samp.data(), S, cfg.pl2_leaves, cfg.k, m, &knots, nullptr)) {
     linear = false;
     std::fill(counts, counts + m->nbuckets, 0);

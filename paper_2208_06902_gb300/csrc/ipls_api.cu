@@ -461,7 +461,12 @@ iplsStatus device_prepare(Workspace& w, int64_t n, int64_t nseg, int dtype) {
 // The tail of one device-driven level: its groups in slot s, counted in
 // *gcnt; a second sweep over the children above the cutoff when there are
 // at least kTailSweepMin of them; k_slow for the rest.
-iplsStatus launch_tail_dev(Workspace& w, ResidentArgs ra, Slot& s, LevelCtl* gcnt) {
+// max_task: the largest task the groups can hold (tasks above kTailSmall
+// keys need the large k_tail); sweep: whether a second sweep can occur (it
+// needs kTailSweepMin children above the cutoff).  Launches that the sizes
+// rule out are left out of the graph.
+iplsStatus launch_tail_dev(Workspace& w, ResidentArgs ra, Slot& s, LevelCtl* gcnt, int64_t max_task,
+                           bool sweep) {
   iplsCtx c = w.c;
   const int32_t cap = (int32_t)std::min<int64_t>(std::min(s.group_cap, std::min(s.fit_cap, s.tail_cap)), INT32_MAX);
   ra.groups = s.groups;
@@ -483,19 +488,22 @@ iplsStatus launch_tail_dev(Workspace& w, ResidentArgs ra, Slot& s, LevelCtl* gcn
   ra.slow_ctl = w.slow_ctl;
   ra.split_pool = w.split_pool;
   ra.split_pool_slots = (int32_t)std::min<int64_t>(w.split_pool_cap / 128, kSplitPoolMax);
+  const bool large = max_task > kTailSmall;
   IPLS_CUDA(cudaMemsetAsync(w.slow_ctl, 0, sizeof(SlowCtl), w.stream));
   IPLS_CUDA(timed(w, kkTailFit, [&] { return launch_tail_fit(ra, w.stream, c->num_sms); }));
   IPLS_CUDA(timed(w, kkResident, [&] { return launch_resident(ra, w.stream, 0, c->num_sms); }));
-  IPLS_CUDA(timed(w, kkResident, [&] { return launch_resident(ra, w.stream, 1, c->num_sms); }));
-  IPLS_CUDA(timed(w, kkSlowGroups, [&] {
-    return launch_sweep_groups(w.slow, w.slow_ctl, ra.slow_cap, s.groups, s.fit_list, cap, w.stream);
-  }));
-  ResidentArgs rb = ra;
-  rb.sweep = 1;
-  rb.large_from_end = 0;
-  IPLS_CUDA(timed(w, kkTailFit, [&] { return launch_tail_fit(rb, w.stream, c->num_sms); }));
-  IPLS_CUDA(timed(w, kkResident, [&] { return launch_resident(rb, w.stream, 0, c->num_sms); }));
-  IPLS_CUDA(timed(w, kkResident, [&] { return launch_resident(rb, w.stream, 1, c->num_sms); }));
+  if (large) IPLS_CUDA(timed(w, kkResident, [&] { return launch_resident(ra, w.stream, 1, c->num_sms); }));
+  if (sweep) {
+    IPLS_CUDA(timed(w, kkSlowGroups, [&] {
+      return launch_sweep_groups(w.slow, w.slow_ctl, ra.slow_cap, s.groups, s.fit_list, cap, w.stream);
+    }));
+    ResidentArgs rb = ra;
+    rb.sweep = 1;
+    rb.large_from_end = 0;
+    IPLS_CUDA(timed(w, kkTailFit, [&] { return launch_tail_fit(rb, w.stream, c->num_sms); }));
+    IPLS_CUDA(timed(w, kkResident, [&] { return launch_resident(rb, w.stream, 0, c->num_sms); }));
+    if (large) IPLS_CUDA(timed(w, kkResident, [&] { return launch_resident(rb, w.stream, 1, c->num_sms); }));
+  }
   IPLS_CUDA(timed(w, kkSlow, [&] { return launch_slow(ra, w.stream, c->num_sms); }));
   return IPLS_OK;
 }
@@ -527,7 +535,9 @@ iplsStatus device_enqueue(Workspace& w, int64_t n, int dtype, const int64_t* off
                                                            INT32_MAX),
                                 s1.fit_list, w.stream);
   }));
-  IPLS_TRY(launch_tail_dev(w, ra, s1, &w.ctl_arr[0]));
+  // the second sweep needs kTailSweepMin children above the cutoff
+  const bool sweep = n >= (int64_t)kTailSweepMin * (cfg.cutoff + 1);
+  IPLS_TRY(launch_tail_dev(w, ra, s1, &w.ctl_arr[0], std::min<int64_t>(n, rmax), sweep));
   for (int level = 0; level < levels; ++level) {
     // the largest sample of the level: that of an n-key subproblem (level 0
     // may have its own root sample size)
@@ -564,6 +574,7 @@ iplsStatus device_enqueue(Workspace& w, int64_t n, int dtype, const int64_t* off
     a.knot_cap = c->knot_cap;
     a.max_sample = sample_bound;
     a.pl2_leaves = cfg.pl2_leaves;
+    a.pl2_depth = cfg.pl2_depth;
     a.knots = cfg.pl2_leaves > 0 ? X.knots : nullptr;
     const int sms = c->num_sms;
     IPLS_CUDA(timed(w, kkFit, [&] { return launch_fit(a, w.stream, sample_bound, sms); }, level));
@@ -573,7 +584,7 @@ iplsStatus device_enqueue(Workspace& w, int64_t n, int dtype, const int64_t* off
     IPLS_CUDA(timed(w, kkScan, [&] { return launch_scan(a, w.stream, sms); }, level));
     IPLS_CUDA(timed(w, kkTileScan, [&] { return launch_tilescan(a, w.stream, sms * 8); }, level));
     IPLS_CUDA(timed(w, kkScatter, [&] { return launch_scatter(a, w.stream, sms); }, level));
-    IPLS_TRY(launch_tail_dev(w, ra, X, &w.ctl_arr[level + 1]));
+    IPLS_TRY(launch_tail_dev(w, ra, X, &w.ctl_arr[level + 1], rmax, sweep));
     IPLS_CUDA(timed(w, kkFill, [&] {
       return launch_fill(X.fills, a.fill_cap, dtype, w.stream, &w.ctl_arr[level + 1], sms * 8, w.run);
     }));
@@ -585,11 +596,12 @@ iplsStatus device_enqueue(Workspace& w, int64_t n, int dtype, const int64_t* off
   return IPLS_OK;
 }
 
-// Levels enqueued for n keys: one per factor of about 2^8 above the
-// block-resident size, plus one.
-int device_levels_for(int64_t n) {
+// Levels enqueued for n keys: none when every segment fits a block-resident
+// task, else one per factor of about 2^8 above that size, plus one.
+int device_levels_for(int64_t n, int rmax) {
+  if (n <= rmax) return 0;
   int L = 1;
-  for (int64_t m = n; m > 8192 && L < kDevLevelsMax; m >>= 8) ++L;
+  for (int64_t m = n; m > rmax && L < kDevLevelsMax; m >>= 8) ++L;
   return L;
 }
 
@@ -658,7 +670,7 @@ iplsStatus sort_impl(Workspace& w, void* keys, int64_t n, int dtype, const int64
   if (offsets && (cfg.flags & IPLS_FLAG_GRAPH)) {
     // device-driven levels, captured once into a CUDA graph per (buffers,
     // sizes) and replayed
-    const int levels = device_levels_for(n);
+    const int levels = device_levels_for(n, rmax);
     IPLS_TRY(device_prepare(w, n, nseg, dtype));
     const Workspace::GraphKey key{keys, offsets, seg_ubase, n, nseg, dtype, levels};
     if (!(w.graph && w.gkey == key)) {
@@ -857,6 +869,7 @@ iplsStatus sort_impl(Workspace& w, void* keys, int64_t n, int dtype, const int64
     const int max_sample = sample_size_host(std::max<int64_t>(max_sub_n, 2), level, cfg.k, cfg.root_sample);
     a.max_sample = max_sample;
     a.pl2_leaves = cfg.pl2_leaves;
+    a.pl2_depth = cfg.pl2_depth;
     a.knots = cfg.pl2_leaves > 0 ? X.knots : nullptr;
     IPLS_CUDA(timed(w, kkFit, [&] { return launch_fit(a, w.stream, max_sample, c->num_sms); }, level));
     IPLS_CUDA(timed(w, kkHist, [&] { return launch_hist(a, w.stream, 0, occupancy_grid(c, 0, dtype)); }, level));
@@ -942,6 +955,7 @@ iplsStatus validate_cfg(const iplsConfig& c) {
     return fail(IPLS_ERR_ARG, "pl2_leaves must be 0 or a power of two in [2, 1024]");
   if (c.budget_bytes < 0) return fail(IPLS_ERR_ARG, "budget_bytes must be >= 0");
   if (c.serve_slots < 0 || c.serve_slots > 2) return fail(IPLS_ERR_ARG, "serve_slots must be 0, 1 or 2");
+  if (c.pl2_depth < 0) return fail(IPLS_ERR_ARG, "pl2_depth must be >= 0");
   return IPLS_OK;
 }
 
@@ -1284,6 +1298,7 @@ iplsStatus iplsDefaultConfig(iplsConfig* cfg) {
   cfg->spin_limit = int64_t(1) << 26;
   cfg->trace_cap = 0;
   cfg->budget_bytes = 0;
+  cfg->pl2_depth = 1;
   return IPLS_OK;
 }
 

@@ -213,6 +213,7 @@ struct SlowCtl {
   int32_t fit_ticket;  // next task of k_tail_fit's persistent warps
   int32_t wcount;
   int32_t sweep;       // device-driven levels: tasks of the second sweep (0: none)
+  int32_t tticket[2];  // device-driven levels: next task of the small / large k_tail
 };
 
 // Splitters of a tail task whose tree has more than kTailSplit of them (one
@@ -236,6 +237,7 @@ struct LevelArgs {
   int exact_only;
   int use_tables;        // build and use the exact threshold index
   int pl2_leaves;        // 0, or PL2 leaves for subproblems above kPL2MinKeys
+  int pl2_depth;         // PL2 only at levels below this (0: every level)
   float* knots;          // [nsub][pl2_leaves + 1] PL2 knot values (when pl2_leaves > 0)
   int max_sample;        // largest sample of the level (k_fit's shared-memory layout)
   int64_t spin_limit;

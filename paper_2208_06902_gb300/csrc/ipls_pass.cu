@@ -95,7 +95,8 @@ __host__ __device__ __forceinline__ bool warp_fits(const LevelArgs& a, int32_t n
 __device__ __forceinline__ bool takes_pl2(const LevelArgs& a, const Sub& sub, int S) {
   // (a level whose largest sample exceeds kPL2MaxSample is a level-0 launch
   // in which every sample does; it reserves no PL2 scratch)
-  return a.pl2_leaves > 0 && sub.n > kPL2MinKeys && S <= kPL2MaxSample && a.max_sample <= kPL2MaxSample;
+  return a.pl2_leaves > 0 && sub.n > kPL2MinKeys && S <= kPL2MaxSample && a.max_sample <= kPL2MaxSample &&
+         (a.pl2_depth == 0 || sub.level < a.pl2_depth);
 }
 __device__ __forceinline__ bool fit_by_warp(const LevelArgs& a, const Sub& sub, int32_t nsub) {
   const int S = (int)sample_size(sub.n, sub.level, a.k, a.root_sample);

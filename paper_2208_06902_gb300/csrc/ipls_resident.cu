@@ -851,10 +851,24 @@ __device__ __forceinline__ void tail_task(const ResidentArgs& a, int gi, unsigne
 template <class K, int kThreads, int kCap>
 __global__ void __launch_bounds__(kThreads, kCap == kResidentMax ? 2 : 4) k_tail(ResidentArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int32_t count = tail_count(a, kCap == kResidentMax);
-  for (int gi = blockIdx.x; gi < count; gi += gridDim.x) {
+  constexpr bool large = kCap == kResidentMax;
+  const int32_t count = tail_count(a, large);
+  if (!a.device_counts) {
+    for (int gi = blockIdx.x; gi < count; gi += gridDim.x) {
+      tail_task<K, kThreads, kCap>(a, gi, smem_raw);
+      __syncthreads();  // the task is done with shared memory
+    }
+    return;
+  }
+  // device-driven levels: one wave of blocks takes the tasks from a ticket
+  __shared__ int s_gi;
+  for (;;) {
+    if (threadIdx.x == 0) s_gi = atomicAdd(&a.slow_ctl->tticket[large ? 1 : 0], 1);
+    __syncthreads();
+    const int gi = s_gi;
+    if (gi >= count) break;
     tail_task<K, kThreads, kCap>(a, gi, smem_raw);
-    __syncthreads();  // the task is done with shared memory
+    __syncthreads();  // the task is done with shared memory (and s_gi read)
   }
 }
 
@@ -903,14 +917,14 @@ cudaError_t launch_resident(const ResidentArgs& a, cudaStream_t s, int large, in
   return by_dtype_r(a.dtype, [&](auto* tag) {
     using K = std::remove_pointer_t<decltype(tag)>;
     // tasks of up to kTailSmall keys in the small blocks, the rest in the
-    // large ones; on device-driven levels the counts are capacities and a
-    // fixed grid (eight rounds of resident blocks) loops over the tasks
+    // large ones; on device-driven levels the counts are capacities and one
+    // wave of resident blocks takes the tasks from a ticket
     if (!large) {
       if (a.ngroups <= 0) return cudaSuccess;
       const size_t ss = sizeof(TailSmem<K, kTailSmall, kRW / 2>);
       cudaFuncSetAttribute(k_tail<K, kResidentThreads / 2, kTailSmall>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
-      const int g = a.device_counts ? std::min(a.ngroups, sms * 4 * 8) : a.ngroups;
+      const int g = a.device_counts ? std::min(a.ngroups, sms * 4) : a.ngroups;
       k_tail<K, kResidentThreads / 2, kTailSmall><<<g, kResidentThreads / 2, ss, s>>>(a);
       return cudaGetLastError();
     }
@@ -919,7 +933,7 @@ cudaError_t launch_resident(const ResidentArgs& a, cudaStream_t s, int large, in
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sl);
     const int nl = a.large_from_end ? a.nlarge : a.ngroups;
     if (nl <= 0) return cudaSuccess;
-    const int g = a.device_counts ? std::min(nl, sms * 2 * 8) : nl;
+    const int g = a.device_counts ? std::min(nl, sms * 2) : nl;
     k_tail<K, kResidentThreads, kResidentMax><<<g, kResidentThreads, sl, s>>>(a);
     return cudaGetLastError();
   });
@@ -978,6 +992,8 @@ __global__ void __launch_bounds__(1024) k_sweep_groups(const SlowTask* list, Slo
       ctl->ticket = 0;
       ctl->pool_used = 0;
       ctl->fit_ticket = 0;
+      ctl->tticket[0] = 0;
+      ctl->tticket[1] = 0;
     }
   }
 }

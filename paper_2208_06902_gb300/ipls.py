@@ -27,7 +27,7 @@ class iplsConfig(ctypes.Structure):
                 ("budget_bytes", ctypes.c_int64), ("profile", ctypes.c_int32),
                 ("flags", ctypes.c_int32), ("max_batch", ctypes.c_int32),
                 ("pl2_leaves", ctypes.c_int32), ("serve_slots", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 3)]
+                ("pl2_depth", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 FLAG_THRESHOLD_INDEX = 1
 FLAG_GRAPH = 2
@@ -310,7 +310,8 @@ class Context:
     def __init__(self, *, k: int = 256, cutoff: int = 32, root_sample: int = 0, seed: int = 0,
                  exact_only: bool = False, trace_cap: int = 0, spin_limit: int | None = None,
                  stream=None, budget_bytes: int = 0, profile: bool = False, flags: int = 0,
-                 max_batch: int = 0, pl2_leaves: int = 0, serve_slots: int = 0):
+                 max_batch: int = 0, pl2_leaves: int = 0, serve_slots: int = 0,
+                 pl2_depth: int = 1):
         import torch
         cfg = iplsDefaultConfig()
         cfg.k, cfg.cutoff, cfg.root_sample, cfg.seed = k, cutoff, root_sample, seed
@@ -322,6 +323,7 @@ class Context:
         cfg.max_batch = max_batch
         cfg.pl2_leaves = pl2_leaves
         cfg.serve_slots = serve_slots
+        cfg.pl2_depth = pl2_depth
         if spin_limit is not None:
             cfg.spin_limit = spin_limit
         s = stream if stream is not None else torch.cuda.current_stream()

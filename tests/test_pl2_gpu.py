@@ -47,16 +47,36 @@ def test_pl2_passes_match_the_oracle(dtype, dist, leaves):
 
 @pytest.mark.parametrize("leaves", [2, 16, 64, 256, 1024])
 def test_pl2_grid_levels_match_the_oracle(leaves):
+    # pl2_depth 0: PL2 at every level above 8192 keys, so that knots of
+    # several passes are compared
     x = datagen.generate("lognormal", 1 << 22, np.float64, seed=32)
     want, recs, _, kn = oracle.sort(x, cutoff=256, trace_cap=300_000, pl2_leaves=leaves,
-                                    as_array=True, knots=True)
-    got, ctx = gpu_sort(x, cutoff=256, trace_cap=300_000, pl2_leaves=leaves)
+                                    as_array=True, knots=True, pl2_depth=0)
+    got, ctx = gpu_sort(x, cutoff=256, trace_cap=300_000, pl2_leaves=leaves, pl2_depth=0)
     assert _same(got, want)
     kg = ctx.trace_knots()
     g = ctx.trace(as_array=True)
     compare_trace_arrays(g, recs, kg, kn)
     assert ctx.stats().grid_levels >= 2
     assert (g["kind"][: len(kg)] == 2).sum() >= 2  # knots of several PL2 passes compared
+
+
+@pytest.mark.parametrize("dist", ["lognormal", "exponential", "normal", "mixgauss"])
+def test_pl2_at_the_root_balances_better_than_fmcd_on_the_gpu(dist):
+    """What the trained model gains: on skewed keys (2^22 f64) the PL2 root
+    pass (64 leaves, the top level only) puts fewer keys into its largest
+    bucket than FMCD's linear model does, and the whole sort needs no more
+    grid-level passes; both give the same sorted bytes."""
+    x = datagen.generate(dist, 1 << 22, np.float64, seed=33)
+    a, ca = gpu_sort(x, cutoff=256, trace_cap=300_000)
+    b, cb = gpu_sort(x, cutoff=256, trace_cap=300_000, pl2_leaves=64, pl2_depth=1)
+    assert _same(a, b)
+    ra = [r for r in ca.trace() if r.level == 0][0]
+    rb = [r for r in cb.trace() if r.level == 0][0]
+    assert rb.kind == 2 and ra.kind != 2
+    assert max(rb.counts[: rb.nbuckets]) < max(ra.counts[: ra.nbuckets])
+    assert cb.stats().grid_passes <= ca.stats().grid_passes
+    assert cb.stats().max_bucket_frac < ca.stats().max_bucket_frac
 
 
 def test_dense_cluster_takes_the_splitter_tree_on_the_gpu():
