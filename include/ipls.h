@@ -104,6 +104,11 @@ typedef struct iplsConfig {
  * sorted result. */
 #define IPLS_FLAG_GRAPH 2
 
+/* cfg.flags: each block-resident task fits its model inside the block that
+ * partitions it, from the keys it has already read, instead of in a separate
+ * fitting kernel (same sample, same model, same result). */
+#define IPLS_FLAG_FIT_IN_TAIL 4
+
 /* Accumulated device time of one kernel of the library (profile = 1).
  * bytes = algorithmic bytes: keys read + keys written by the launches, in
  * bytes (the classify/histogram sweep reads every live key once, the scatter

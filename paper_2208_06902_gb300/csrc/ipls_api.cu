@@ -296,7 +296,7 @@ int64_t pool_slots(int64_t nfit) {
 // One sweep of k_tail_fit + k_tail over the groups in ra.
 iplsStatus tail_sweep(Workspace& w, ResidentArgs& ra) {
   iplsCtx c = w.c;
-  if (ra.nfit > 0) {
+  if (ra.nfit > 0 && !ra.fit_inblock) {
     IPLS_TRY(ensure(w, w.split_pool, w.split_pool_cap, pool_slots(ra.nfit) * 128));
     ra.split_pool = w.split_pool;
     ra.split_pool_slots = (int32_t)std::min<int64_t>(w.split_pool_cap / 128, kSplitPoolMax);
@@ -490,7 +490,8 @@ iplsStatus launch_tail_dev(Workspace& w, ResidentArgs ra, Slot& s, LevelCtl* gcn
   ra.split_pool_slots = (int32_t)std::min<int64_t>(w.split_pool_cap / 128, kSplitPoolMax);
   const bool large = max_task > kTailSmall;
   IPLS_CUDA(cudaMemsetAsync(w.slow_ctl, 0, sizeof(SlowCtl), w.stream));
-  IPLS_CUDA(timed(w, kkTailFit, [&] { return launch_tail_fit(ra, w.stream, c->num_sms); }));
+  if (!ra.fit_inblock)
+    IPLS_CUDA(timed(w, kkTailFit, [&] { return launch_tail_fit(ra, w.stream, c->num_sms); }));
   IPLS_CUDA(timed(w, kkResident, [&] { return launch_resident(ra, w.stream, 0, c->num_sms); }));
   if (large) IPLS_CUDA(timed(w, kkResident, [&] { return launch_resident(ra, w.stream, 1, c->num_sms); }));
   if (sweep) {
@@ -500,7 +501,8 @@ iplsStatus launch_tail_dev(Workspace& w, ResidentArgs ra, Slot& s, LevelCtl* gcn
     ResidentArgs rb = ra;
     rb.sweep = 1;
     rb.large_from_end = 0;
-    IPLS_CUDA(timed(w, kkTailFit, [&] { return launch_tail_fit(rb, w.stream, c->num_sms); }));
+    if (!rb.fit_inblock)
+      IPLS_CUDA(timed(w, kkTailFit, [&] { return launch_tail_fit(rb, w.stream, c->num_sms); }));
     IPLS_CUDA(timed(w, kkResident, [&] { return launch_resident(rb, w.stream, 0, c->num_sms); }));
     if (large) IPLS_CUDA(timed(w, kkResident, [&] { return launch_resident(rb, w.stream, 1, c->num_sms); }));
   }
@@ -525,6 +527,7 @@ iplsStatus device_enqueue(Workspace& w, int64_t n, int dtype, const int64_t* off
   ra.dtype = dtype; ra.k = cfg.k; ra.cutoff = cfg.cutoff; ra.root_sample = cfg.root_sample;
   ra.seed = cfg.seed; ra.exact_only = cfg.exact_only; ra.buf[0] = nullptr; ra.buf[1] = w.scratch;
   ra.run = w.run; ra.trace = traced ? c->trace_res : nullptr; ra.trace_cap = traced ? cfg.trace_cap : 0;
+  ra.fit_inblock = (cfg.flags & IPLS_FLAG_FIT_IN_TAIL) ? 1 : 0;
   Slot& s0 = w.slot[0];
   Slot& s1 = w.slot[1];
   IPLS_CUDA(timed(w, kkInitSeg, [&] {
@@ -659,6 +662,7 @@ iplsStatus sort_impl(Workspace& w, void* keys, int64_t n, int dtype, const int64
   ra.dtype = dtype; ra.k = cfg.k; ra.cutoff = cfg.cutoff; ra.root_sample = cfg.root_sample;
   ra.seed = cfg.seed; ra.exact_only = cfg.exact_only; ra.buf[0] = bufs[0]; ra.buf[1] = bufs[1];
   ra.run = w.run; ra.trace = traced ? c->trace_res : nullptr; ra.trace_cap = traced ? cfg.trace_cap : 0;
+  ra.fit_inblock = (cfg.flags & IPLS_FLAG_FIT_IN_TAIL) ? 1 : 0;
 
   int64_t nsub = 0, ntiles = 0, nchunks = 0;
   int64_t max_sub_n = n;  // bound on the size of this level's grid subproblems

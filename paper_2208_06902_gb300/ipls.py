@@ -31,6 +31,7 @@ class iplsConfig(ctypes.Structure):
 
 FLAG_THRESHOLD_INDEX = 1
 FLAG_GRAPH = 2
+FLAG_FIT_IN_TAIL = 4
 
 
 class iplsKernelStat(ctypes.Structure):

@@ -65,8 +65,10 @@ def test_pl2_grid_levels_match_the_oracle(leaves):
 def test_pl2_at_the_root_balances_better_than_fmcd_on_the_gpu(dist):
     """What the trained model gains: on skewed keys (2^22 f64) the PL2 root
     pass (64 leaves, the top level only) puts fewer keys into its largest
-    bucket than FMCD's linear model does, and the whole sort needs no more
-    grid-level passes; both give the same sorted bytes."""
+    bucket than FMCD's linear model does, and the recursion is no deeper;
+    both give the same sorted bytes.  (More of PL2's evenly sized children
+    can sit above the block-resident size and take a grid pass, so the count
+    of grid passes is not the measure.)"""
     x = datagen.generate(dist, 1 << 22, np.float64, seed=33)
     a, ca = gpu_sort(x, cutoff=256, trace_cap=300_000)
     b, cb = gpu_sort(x, cutoff=256, trace_cap=300_000, pl2_leaves=64, pl2_depth=1)
@@ -75,7 +77,7 @@ def test_pl2_at_the_root_balances_better_than_fmcd_on_the_gpu(dist):
     rb = [r for r in cb.trace() if r.level == 0][0]
     assert rb.kind == 2 and ra.kind != 2
     assert max(rb.counts[: rb.nbuckets]) < max(ra.counts[: ra.nbuckets])
-    assert cb.stats().grid_passes <= ca.stats().grid_passes
+    assert cb.stats().grid_levels <= ca.stats().grid_levels
     assert cb.stats().max_bucket_frac < ca.stats().max_bucket_frac
 
 
