@@ -109,6 +109,11 @@ typedef struct iplsConfig {
  * fitting kernel (same sample, same model, same result). */
 #define IPLS_FLAG_FIT_IN_TAIL 4
 
+/* cfg.flags: the grid-level scatter runs three blocks per SM and reads each
+ * key when it places it (from L1, prefetched) instead of holding the tile's
+ * keys in registers through the ranking (same result). */
+#define IPLS_FLAG_SCATTER3 8
+
 /* Accumulated device time of one kernel of the library (profile = 1).
  * bytes = algorithmic bytes: keys read + keys written by the launches, in
  * bytes (the classify/histogram sweep reads every live key once, the scatter

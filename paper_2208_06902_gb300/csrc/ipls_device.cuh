@@ -423,6 +423,43 @@ __device__ void same_binade_model(typename KT<K>::Bits xlo, typename KT<K>::Ord 
   m->ucabs = ucabs;
 }
 
+// Fields of the uncentred estimate (LinModel::gfast ...), float keys only.
+// With xf the key truncated to binary32 (23 mantissa bits; exact for f32
+// keys), B = Bc - A x_lo in binary64 and v_f = RN32(RN32(A) xf + RN32(B)):
+//   |v_f - v64| <= |A||xf|(2^-23 + 2^-24)(1 + 2^-22)   (truncation, RN32(A))
+//                + 2^-23 |B| + 2^-23 |v_f|              (RN32(B), the fma)
+//                + 2^-52 |A| (|xf| + |x_lo|) + 2^-53 |v64| (the binary64 model's
+//                                                       own roundings)
+// so gc1 = |A| 2^-21.9, crel = 2^-21 and gcabs = 2^-22 |B| + 2^-51 |A x_lo|
+// + 2^-40 (rounded up) bound it, and the FP32 evaluation of the bound and of
+// v_f +- del stays within the margin.  Used only when the bound at the
+// sample's extremes stays below 2^-8 of a bucket.
+template <class K>
+__device__ void uncentred_model(typename KT<K>::Bits xlo, typename KT<K>::Bits s_first,
+                                typename KT<K>::Bits s_last, double A, double Bc, LinModel* m) {
+  using T = KT<K>;
+  m->gfast = 0;
+  m->gaf = m->gbf = m->gc1 = m->gcabs = 0.0f;
+  m->gpad = 0;
+  if (T::kMant == 0 || T::special(xlo)) return;
+  const double x0 = T::value(xlo);
+  const double B = __fma_rn(-A, x0, Bc);
+  const float gaf = __double2float_rn(A), gbf = __double2float_rn(B);
+  const double c1 = fabs(A) * 0x1.1p-22 * (1.0 + 0x1.0p-20);
+  const float gc1 = __double2float_ru(c1);
+  const float gcabs = __double2float_ru((fabs(B) * 0x1.0p-22 + fabs(A * x0) * 0x1.0p-51 + 0x1.0p-40) *
+                                        (1.0 + 0x1.0p-20));
+  const double xm = fmax(fabs(T::value(s_first)), fabs(T::value(s_last)));
+  const bool ok = isfinite(B) && isfinite(gaf) && isfinite(gbf) && isfinite(gc1) && gaf != 0.0f &&
+                  isfinite(xm) && (double)gc1 * xm + gcabs < 0x1.0p-8;
+  if (!ok) return;
+  m->gfast = 1;
+  m->gaf = gaf;
+  m->gbf = gbf;
+  m->gc1 = gc1;
+  m->gcabs = gcabs;
+}
+
 // One probe: does every window of D+1 consecutive sample points span at
 // least u_d(D)?  The thresholds of the fixed-point test come from the
 // fixed-point span q[N-1-D] - q[D]: with |q(x) - x/2^rho| < 1 and binary64
@@ -511,6 +548,9 @@ __device__ void fit_linear(const typename KT<K>::Ord* so, int N, int K_, LinMode
     m->ushift = 0;
     m->auf = 0.0f;
     m->ucabs = 0.0f;
+    m->gfast = 0;
+    m->gaf = m->gbf = m->gc1 = m->gcabs = 0.0f;
+    m->gpad = 0;
     if (lin) {
       // certified filter: fixed point at rho = L - 61 with |x| < 2^L for every
       // sample key; off when the keys are all zero or so large that a
@@ -585,6 +625,7 @@ __device__ void fit_linear(const typename KT<K>::Ord* so, int N, int K_, LinMode
         m->crel = 0x1.0p-21f;
         m->cabs = cabs;
         same_binade_model<K>(xlo, so[0], so[N - 1], K_, A, Bc, m);
+        uncentred_model<K>(xlo, T::unord(so[0]), T::unord(so[N - 1]), A, Bc, m);
       }
     }
   }
@@ -648,9 +689,9 @@ template <class K>
 struct Classifier {
   using Bits = typename KT<K>::Bits;
   using Ord = typename KT<K>::Ord;
-  int kind, nb, fast, rho, nsplit, ufast, ushift;
+  int kind, nb, fast, rho, nsplit, ufast, ushift, gfast;
   long long qlo;
-  float af, bcf, crel, cabs, auf, ucabs;
+  float af, bcf, crel, cabs, auf, ucabs, gaf, gbf, gc1, gcabs;
   double A, Bc;
   Bits xlo;
   Ord ulo;
@@ -674,6 +715,11 @@ struct Classifier {
     ushift = m.ushift;
     auf = m.auf;
     ucabs = m.ucabs;
+    gfast = m.gfast && !exact_only;
+    gaf = m.gaf;
+    gbf = m.gbf;
+    gc1 = m.gc1;
+    gcabs = m.gcabs;
     nsplit = 0;
     split = nullptr;
   }
@@ -737,8 +783,34 @@ struct Classifier {
     return decide(v, fmaf(crel, fabsf(v), ucabs));
   }
 
+  // Uncentred estimate for float keys: -1 when the key's binary32
+  // truncation is not a normal number or the certified interval contains a
+  // bucket boundary.
+  __device__ __forceinline__ int flt_bucket(Bits b) const {
+    float xf;
+    if (sizeof(Bits) == 8) {
+      const unsigned long long u = (unsigned long long)b;
+      const unsigned hi = (unsigned)(u >> 32), lo = (unsigned)u;
+      const unsigned e = (hi >> 20) & 0x7FFu;
+      if (e - 897u > 253u) return -1;  // beyond binary32's normal range (or inf/NaN)
+      const unsigned mant = __funnelshift_l(lo, hi, 3) & 0x7FFFFFu;
+      xf = __uint_as_float((hi & 0x80000000u) | ((e - 896u) << 23) | mant);
+    } else {
+      const unsigned u = (unsigned)b;
+      const unsigned e = (u >> 23) & 0xFFu;
+      if (e - 1u > 253u) return -1;
+      xf = __uint_as_float(u);
+    }
+    const float v = fmaf(gaf, xf, gbf);
+    return decide(v, fmaf(gc1, fabsf(xf), fmaf(crel, fabsf(v), gcabs)));
+  }
+
   __device__ __forceinline__ int bucket(Bits b) const {
     if (kind == kSplitter) return splitter_bucket((uint64_t)KT<K>::ord(b), split, nsplit);
+    if (gfast && !ufast) {
+      const int r = flt_bucket(b);
+      if (r >= 0) return r;
+    }
     if (ufast) {
       const int r = ord_bucket(KT<K>::ord(b));
       if (r >= 0) return r;
@@ -754,6 +826,10 @@ struct Classifier {
   // the splitter tree or when the estimate is off.
   __device__ __forceinline__ int bucket_or_defer(Bits b) const {
     if (kind == kSplitter) return splitter_bucket((uint64_t)KT<K>::ord(b), split, nsplit);
+    if (gfast && !ufast) {
+      const int r = flt_bucket(b);
+      if (r >= 0) return r;
+    }
     if (ufast) {
       const int r = ord_bucket(KT<K>::ord(b));
       if (r >= 0) return r;

@@ -65,6 +65,15 @@ struct LinModel {
   int32_t ushift;
   float auf;
   float ucabs;
+  // Uncentred estimate (float keys whose binary32 truncation xf is a normal
+  // number): v = fmaf(gaf, xf, gbf) with gaf = RN32(A), gbf = RN32(Bc - A x_lo),
+  // certified by gc1*|xf| + crel*|v| + gcabs.
+  int32_t gfast;
+  float gaf;
+  float gbf;
+  float gc1;
+  float gcabs;
+  int32_t gpad;
 };
 
 // Full model: the linear part, or unique splitters s_1 < ... < s_m as
@@ -285,6 +294,7 @@ struct LevelArgs {
   // capacities; a level after an overflow or a device error does nothing.
   const LevelCtl* cnt;
   long long* trace_ctr;  // device-driven levels: next free grid trace record
+  int scatter3;          // k_scatter in three blocks per SM (keys read when placed)
 };
 
 struct ResidentArgs {
