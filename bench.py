@@ -76,8 +76,8 @@ def parse():
     p.add_argument("--budget-gb", type=int, default=64,
                    help="serve: device-memory budget of the requests in flight (GiB)")
     p.add_argument("--tuned", metavar="JSON", help="autotuner table; picks k and cutoff")
-    p.add_argument("--fit-in-tail", action="store_true",
-                   help="block-resident tasks fit their models in the partitioning block")
+    p.add_argument("--scatter3", action="store_true",
+                   help="grid scatter in three blocks per SM (keys read when placed)")
     p.add_argument("--pl2", type=int, default=0,
                    help="PL2 leaves for subproblems above 8192 keys (0: FMCD, the paper's IPLS)")
     p.add_argument("--ingest-ncu", nargs=2, metavar=("CSV", "STATS_JSON"),
@@ -325,8 +325,9 @@ def run_gb300(args):
     pristine = {d: torch.from_numpy(inputs[d].view(np.uint8)).to(dev) for d in dists}
     work = torch.empty(n * 8, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
+    flags = ipls.ipls.FLAG_SCATTER3 if args.scatter3 else 0
     ctx = ipls.Context(cutoff=args.cutoff, profile=True, stream=stream, pl2_leaves=args.pl2,
-                       flags=ipls.ipls.FLAG_FIT_IN_TAIL if args.fit_in_tail else 0)
+                       flags=flags)
 
     def step(i, timed):
         d = dists[i % len(dists)]
@@ -475,7 +476,7 @@ def run_gb300(args):
                                          "states 32): a tuned choice; the sorted output is "
                                          "the same, only the pass trace differs",
                        "model": f"PL2, {args.pl2} leaves, top level" if args.pl2 else "FMCD",
-                       "tail_fit": "in the partitioning block" if args.fit_in_tail else "separate kernel",
+                       "scatter_blocks_per_sm": 3 if args.scatter3 else 2,
                        "sample": "alpha*k-1 keys, alpha = 0.2*floor(log2 n)",
                        "l2": f"flushed: a {n * 8 >> 20} MiB input-restore copy runs between "
                              "timed steps (inputs larger than L2 from 2^25 keys)",

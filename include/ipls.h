@@ -104,11 +104,6 @@ typedef struct iplsConfig {
  * sorted result. */
 #define IPLS_FLAG_GRAPH 2
 
-/* cfg.flags: each block-resident task fits its model inside the block that
- * partitions it, from the keys it has already read, instead of in a separate
- * fitting kernel (same sample, same model, same result). */
-#define IPLS_FLAG_FIT_IN_TAIL 4
-
 /* cfg.flags: the grid-level scatter runs three blocks per SM and reads each
  * key when it places it (from L1, prefetched) instead of holding the tile's
  * keys in registers through the ranking (same result). */

@@ -296,7 +296,7 @@ int64_t pool_slots(int64_t nfit) {
 // One sweep of k_tail_fit + k_tail over the groups in ra.
 iplsStatus tail_sweep(Workspace& w, ResidentArgs& ra) {
   iplsCtx c = w.c;
-  if (ra.nfit > 0 && !ra.fit_inblock) {
+  if (ra.nfit > 0) {
     IPLS_TRY(ensure(w, w.split_pool, w.split_pool_cap, pool_slots(ra.nfit) * 128));
     ra.split_pool = w.split_pool;
     ra.split_pool_slots = (int32_t)std::min<int64_t>(w.split_pool_cap / 128, kSplitPoolMax);
@@ -490,8 +490,7 @@ iplsStatus launch_tail_dev(Workspace& w, ResidentArgs ra, Slot& s, LevelCtl* gcn
   ra.split_pool_slots = (int32_t)std::min<int64_t>(w.split_pool_cap / 128, kSplitPoolMax);
   const bool large = max_task > kTailSmall;
   IPLS_CUDA(cudaMemsetAsync(w.slow_ctl, 0, sizeof(SlowCtl), w.stream));
-  if (!ra.fit_inblock)
-    IPLS_CUDA(timed(w, kkTailFit, [&] { return launch_tail_fit(ra, w.stream, c->num_sms); }));
+  IPLS_CUDA(timed(w, kkTailFit, [&] { return launch_tail_fit(ra, w.stream, c->num_sms); }));
   IPLS_CUDA(timed(w, kkResident, [&] { return launch_resident(ra, w.stream, 0, c->num_sms); }));
   if (large) IPLS_CUDA(timed(w, kkResident, [&] { return launch_resident(ra, w.stream, 1, c->num_sms); }));
   if (sweep) {
@@ -501,8 +500,7 @@ iplsStatus launch_tail_dev(Workspace& w, ResidentArgs ra, Slot& s, LevelCtl* gcn
     ResidentArgs rb = ra;
     rb.sweep = 1;
     rb.large_from_end = 0;
-    if (!rb.fit_inblock)
-      IPLS_CUDA(timed(w, kkTailFit, [&] { return launch_tail_fit(rb, w.stream, c->num_sms); }));
+    IPLS_CUDA(timed(w, kkTailFit, [&] { return launch_tail_fit(rb, w.stream, c->num_sms); }));
     IPLS_CUDA(timed(w, kkResident, [&] { return launch_resident(rb, w.stream, 0, c->num_sms); }));
     if (large) IPLS_CUDA(timed(w, kkResident, [&] { return launch_resident(rb, w.stream, 1, c->num_sms); }));
   }
@@ -527,7 +525,6 @@ iplsStatus device_enqueue(Workspace& w, int64_t n, int dtype, const int64_t* off
   ra.dtype = dtype; ra.k = cfg.k; ra.cutoff = cfg.cutoff; ra.root_sample = cfg.root_sample;
   ra.seed = cfg.seed; ra.exact_only = cfg.exact_only; ra.buf[0] = nullptr; ra.buf[1] = w.scratch;
   ra.run = w.run; ra.trace = traced ? c->trace_res : nullptr; ra.trace_cap = traced ? cfg.trace_cap : 0;
-  ra.fit_inblock = (cfg.flags & IPLS_FLAG_FIT_IN_TAIL) ? 1 : 0;
   Slot& s0 = w.slot[0];
   Slot& s1 = w.slot[1];
   IPLS_CUDA(timed(w, kkInitSeg, [&] {
@@ -663,7 +660,6 @@ iplsStatus sort_impl(Workspace& w, void* keys, int64_t n, int dtype, const int64
   ra.dtype = dtype; ra.k = cfg.k; ra.cutoff = cfg.cutoff; ra.root_sample = cfg.root_sample;
   ra.seed = cfg.seed; ra.exact_only = cfg.exact_only; ra.buf[0] = bufs[0]; ra.buf[1] = bufs[1];
   ra.run = w.run; ra.trace = traced ? c->trace_res : nullptr; ra.trace_cap = traced ? cfg.trace_cap : 0;
-  ra.fit_inblock = (cfg.flags & IPLS_FLAG_FIT_IN_TAIL) ? 1 : 0;
 
   int64_t nsub = 0, ntiles = 0, nchunks = 0;
   int64_t max_sub_n = n;  // bound on the size of this level's grid subproblems
@@ -786,20 +782,10 @@ iplsStatus sort_impl(Workspace& w, void* keys, int64_t n, int dtype, const int64
     nchunks = w.h_ctl->chunks_next;
     max_sub_n = w.h_ctl->max_sub_n;
   } else if (n <= rmax && resident_root_ok) {
-    // the whole array is one block-resident task (base case only when n is
-    // at most the cutoff, otherwise a fitted pass first)
-    Slot& s1 = w.slot[1];
-    IPLS_TRY(ensure_groups(w, s1, 1));
-    const int64_t hb[2] = {0, n};
-    const int fitted = n > cfg.cutoff ? 1 : 0;
-    IPLS_CUDA(cudaMemcpyAsync(w.root_bounds, hb, sizeof(hb), cudaMemcpyHostToDevice, w.stream));
-    const Group g{0, w.root_bounds, (int32_t)n, 0, 0, 1, fitted ? 0 : -1, 0, ubase};
-    IPLS_CUDA(cudaMemcpyAsync(s1.groups, &g, sizeof(g), cudaMemcpyHostToDevice, w.stream));
-    if (fitted) {
-      const int32_t zero = 0;
-      IPLS_CUDA(cudaMemcpyAsync(s1.fit_list, &zero, sizeof(zero), cudaMemcpyHostToDevice, w.stream));
-    }
-    IPLS_TRY(launch_tail(w, ra, s1, 1, -1, fitted));
+    // the whole array fits one block: one launch runs the whole recursion in
+    // shared memory (the same sample, models and passes as the tail kernels)
+    const SlowTask t{0, (int32_t)n, 0, ubase};
+    IPLS_CUDA(timed(w, kkSlow, [&] { return launch_slow_one(ra, t, w.stream); }));
     IPLS_TRY(check_run(w));
     resolve_events(w);
     if (w.main) {

@@ -330,7 +330,6 @@ struct ResidentArgs {
   LevelCtl* gcnt;
   int32_t sweep;
   int32_t device_counts;
-  int32_t fit_inblock;   // 1: k_tail fits its tasks itself (no k_tail_fit, no pool)
 };
 
 // Tasks of a tail launch: host-given counts, or (device-driven levels) the

@@ -469,8 +469,7 @@ struct TailSmem {
   int tot[kMaxK];
   int hom[kMaxK];
   TailModel tm;
-  FitShared fs;          // the in-block fit's state
-  uint64_t split[128];   // a tree too large for the record, from the pool (or fitted here)
+  uint64_t split[128];   // a tree too large for the record, from the pool
   typename KT<K>::Ord seglo[kMaxK];  // smallest key of each base-cased segment
   unsigned char segpk[kMaxK];        // 1: the segment is ranked on packed words
   typename KT<K>::Ord wlo[kW], whi[kW];    // per-warp key range of a fitted task
@@ -511,49 +510,7 @@ static_assert(kResidentMax <= (1 << kPosBits), "positions must fit the packed wo
 // kThreads threads, tasks of at most kCap keys; the small size takes tasks
 // of up to kTailSmall keys, the large one the rest (each skips the other's).
 // One task: the group at list position gi (all threads of the block).
-// The model of a fitted tail task computed by its own block (all threads):
-// the task's keys staged in input order, the sample gathered from them (the
-// same positions as every other fit of this subproblem), sorted, FMCD; the
-// splitter tree from the same sample when FMCD cannot split (Ch.3 "Linear
-// Models", "Decision Trees").  Kept out of line so that its registers do not
-// add to those of the partitioning loops.
-template <class K, int kCap, int kW>
-__device__ __noinline__ void tail_fit_in_block(TailSmem<K, kCap, kW>& sh, const ResidentArgs& a, const Group& g,
-                                               const typename KT<K>::Bits* src, int n) {
-  using T = KT<K>;
-  using Ord = typename T::Ord;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) sh.keys[i] = T::ord(src[i]);
-  int S = (int)sample_size(n, g.level, a.k, a.root_sample);
-  if (S > kResidentSample) S = kResidentSample;  // never planned by the host
-  static_assert(sizeof(sh.peer) >= kResidentSample * sizeof(Ord), "the sample must fit the count rows");
-  Ord* samp = reinterpret_cast<Ord*>(&sh.peer[0][0]);
-  const uint64_t stream = stream_key(a.seed, g.off, n, g.level);
-  __syncthreads();
-  for (int j = threadIdx.x; j < S; j += blockDim.x) samp[j] = sh.keys[sample_offset(stream, j, n)];
-  __syncthreads();
-  block_sort(samp, S);
-  fit_linear<BlockG, K>(samp, S, a.k, &sh.tm.l, sh.fs);
-  if (threadIdx.x == 0) {
-    sh.tm.nsplit = 0;
-    sh.tm.pool = -1;
-    if (sh.tm.l.kind == kSplitter) {
-      const int want = (a.k - 1) / 2;
-      int cnt = 0;
-      for (int i = 0; i < want; ++i) {
-        const uint64_t u = (uint64_t)samp[(int64_t)(i + 1) * S / (want + 1)];
-        if (cnt == 0 || sh.split[cnt - 1] != u) sh.split[cnt++] = u;
-      }
-      sh.tm.nsplit = cnt;
-      sh.tm.l.nb = 2 * cnt + 1;
-      sh.tm.l.fast = 0;
-    }
-    sh.slow_all = 0;
-    sh.any_big = 0;
-  }
-  __syncthreads();
-}
-
-template <class K, int kThreads, int kCap, bool kFitHere>
+template <class K, int kThreads, int kCap>
 __device__ __forceinline__ void tail_task(const ResidentArgs& a, int gi, unsigned char* smem_raw) {
   using T = KT<K>;
   using Bits = typename T::Bits;
@@ -572,42 +529,30 @@ __device__ __forceinline__ void tail_task(const ResidentArgs& a, int gi, unsigne
   int nseg;
   bool split_tree = false;  // children at odd ids are equality buckets
   if (g.fit >= 0) {
-    bool slow = false;
-    const uint64_t* splits;
-    const TailModel* gmp;
-    if (kFitHere) {
-      tail_fit_in_block<K, kCap, kW>(sh, a, g, src, n);
-      for (int i = lane; i < kMaxK; i += 32) sh.peer[warp][i] = 0u;  // the sample area is free again
-      __syncwarp();
-      gmp = &sh.tm;
-      split_tree = sh.tm.l.kind == kSplitter;
+    // the model: a copy in shared memory for the phases after the first
+    // barrier; until then every thread reads it from global memory, and each
+    // warp zeroes its own bucket-count row, so no barrier is needed to start
+    const TailModel& gm = a.tail_models[g.fit];
+    if (threadIdx.x < (int)(sizeof(TailModel) / 8))
+      reinterpret_cast<unsigned long long*>(&sh.tm)[threadIdx.x] =
+          reinterpret_cast<const unsigned long long*>(&gm)[threadIdx.x];
+    for (int i = lane; i < kMaxK; i += 32) sh.peer[warp][i] = 0u;
+    if (threadIdx.x == 0) {
+      sh.slow_all = 0;
+      sh.any_big = 0;
+    }
+    __syncwarp();
+    const TailModel* gmp = &gm;
+    split_tree = gm.l.kind == kSplitter;
+    // a large splitter tree comes from its pool slot; without one the task
+    // recurses in k_slow
+    bool slow = split_tree && gm.nsplit > kTailSplit && gm.pool < 0;
+    const uint64_t* splits = gm.split;
+    if (split_tree && gm.nsplit > kTailSplit && !slow) {
+      for (int i = threadIdx.x; i < gm.nsplit; i += blockDim.x)
+        sh.split[i] = a.split_pool[(size_t)gm.pool * 128 + i];
+      __syncthreads();
       splits = sh.split;
-    } else {
-      // the model: a copy in shared memory for the phases after the first
-      // barrier; until then every thread reads it from global memory, and
-      // each warp zeroes its own bucket-count row, so no barrier is needed
-      const TailModel& gm = a.tail_models[g.fit];
-      if (threadIdx.x < (int)(sizeof(TailModel) / 8))
-        reinterpret_cast<unsigned long long*>(&sh.tm)[threadIdx.x] =
-            reinterpret_cast<const unsigned long long*>(&gm)[threadIdx.x];
-      for (int i = lane; i < kMaxK; i += 32) sh.peer[warp][i] = 0u;
-      if (threadIdx.x == 0) {
-        sh.slow_all = 0;
-        sh.any_big = 0;
-      }
-      __syncwarp();
-      gmp = &gm;
-      split_tree = gm.l.kind == kSplitter;
-      // a large splitter tree comes from its pool slot; without one the task
-      // recurses in k_slow
-      slow = split_tree && gm.nsplit > kTailSplit && gm.pool < 0;
-      splits = gm.split;
-      if (split_tree && gm.nsplit > kTailSplit && !slow) {
-        for (int i = threadIdx.x; i < gm.nsplit; i += blockDim.x)
-          sh.split[i] = a.split_pool[(size_t)gm.pool * 128 + i];
-        __syncthreads();
-        splits = sh.split;
-      }
     }
     const int nsplit = gmp->nsplit;
     if (!slow) {
@@ -904,27 +849,27 @@ __device__ __forceinline__ void tail_task(const ResidentArgs& a, int gi, unsigne
 // of up to kTailSmall keys, the large one the rest (each skips the other's).
 // One block per task when the host sized the grid; a fixed grid looping over
 // the tasks on device-driven levels.
-// kFitHere: the tasks' models are fitted in the block (IPLS_FLAG_FIT_IN_TAIL),
-// a separate instantiation so that the other keeps its registers.
-template <class K, int kThreads, int kCap, bool kFitHere>
+// kThreads threads, tasks of at most kCap keys; the small size takes tasks
+// of up to kTailSmall keys, the large one the rest (each skips the other's).
+// Host-driven levels: one block per task.  Device-driven levels (kTicket):
+// one wave of blocks takes the tasks from a ticket.
+template <class K, int kThreads, int kCap, bool kTicket>
 __global__ void __launch_bounds__(kThreads, kCap == kResidentMax ? 2 : 4) k_tail(ResidentArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int s_gi;
   constexpr bool large = kCap == kResidentMax;
+  if (!kTicket) {
+    tail_task<K, kThreads, kCap>(a, blockIdx.x, smem_raw);
+    return;
+  }
+  __shared__ int s_gi;
   const int32_t count = tail_count(a, large);
-  // one block per task when the host sized the grid; on device-driven
-  // levels one wave of blocks takes the tasks from a ticket
-  int gi = blockIdx.x;
   for (;;) {
-    if (a.device_counts) {
-      if (threadIdx.x == 0) s_gi = atomicAdd(&a.slow_ctl->tticket[large ? 1 : 0], 1);
-      __syncthreads();
-      gi = s_gi;
-    }
+    if (threadIdx.x == 0) s_gi = atomicAdd(&a.slow_ctl->tticket[large ? 1 : 0], 1);
+    __syncthreads();
+    const int gi = s_gi;
     if (gi >= count) break;
-    tail_task<K, kThreads, kCap, kFitHere>(a, gi, smem_raw);
+    tail_task<K, kThreads, kCap>(a, gi, smem_raw);
     __syncthreads();  // the task is done with shared memory (and s_gi read)
-    if (!a.device_counts) gi += gridDim.x;
   }
 }
 
@@ -969,7 +914,7 @@ cudaError_t launch_tail_fit(const ResidentArgs& a, cudaStream_t s, int sms) {
   });
 }
 
-template <class K, bool kFitHere>
+template <class K, bool kTicket>
 static cudaError_t launch_resident_t(const ResidentArgs& a, cudaStream_t s, int large, int sms) {
   // tasks of up to kTailSmall keys in the small blocks, the rest in the
   // large ones; on device-driven levels the counts are capacities and one
@@ -977,27 +922,27 @@ static cudaError_t launch_resident_t(const ResidentArgs& a, cudaStream_t s, int 
   if (!large) {
     if (a.ngroups <= 0) return cudaSuccess;
     const size_t ss = sizeof(TailSmem<K, kTailSmall, kRW / 2>);
-    cudaFuncSetAttribute(k_tail<K, kResidentThreads / 2, kTailSmall, kFitHere>,
+    cudaFuncSetAttribute(k_tail<K, kResidentThreads / 2, kTailSmall, kTicket>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
     const int g = a.device_counts ? std::min(a.ngroups, sms * 4) : a.ngroups;
-    k_tail<K, kResidentThreads / 2, kTailSmall, kFitHere><<<g, kResidentThreads / 2, ss, s>>>(a);
+    k_tail<K, kResidentThreads / 2, kTailSmall, kTicket><<<g, kResidentThreads / 2, ss, s>>>(a);
     return cudaGetLastError();
   }
   const size_t sl = sizeof(TailSmem<K, kResidentMax, kRW>);
-  cudaFuncSetAttribute(k_tail<K, kResidentThreads, kResidentMax, kFitHere>,
+  cudaFuncSetAttribute(k_tail<K, kResidentThreads, kResidentMax, kTicket>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sl);
   const int nl = a.large_from_end ? a.nlarge : a.ngroups;
   if (nl <= 0) return cudaSuccess;
   const int g = a.device_counts ? std::min(nl, sms * 2) : nl;
-  k_tail<K, kResidentThreads, kResidentMax, kFitHere><<<g, kResidentThreads, sl, s>>>(a);
+  k_tail<K, kResidentThreads, kResidentMax, kTicket><<<g, kResidentThreads, sl, s>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_resident(const ResidentArgs& a, cudaStream_t s, int large, int sms) {
   return by_dtype_r(a.dtype, [&](auto* tag) {
     using K = std::remove_pointer_t<decltype(tag)>;
-    return a.fit_inblock ? launch_resident_t<K, true>(a, s, large, sms)
-                         : launch_resident_t<K, false>(a, s, large, sms);
+    return a.device_counts ? launch_resident_t<K, true>(a, s, large, sms)
+                           : launch_resident_t<K, false>(a, s, large, sms);
   });
 }
 
