@@ -69,6 +69,9 @@ def parse():
                    help="offered load as a fraction of the one-at-a-time service rate")
     p.add_argument("--max-request-log10", type=float, default=6.0)
     p.add_argument("--segments", type=int, default=200_000)
+    p.add_argument("--autotune", action="store_true",
+                   help="segmented: tune (k, cutoff, graph, PL2) on another instance of the "
+                        "workload first, then time the tuned and the default configuration")
     p.add_argument("--graph", action="store_true",
                    help="segmented: device-driven levels captured into a CUDA graph")
     p.add_argument("--stated-size", action="store_true",
@@ -76,8 +79,6 @@ def parse():
     p.add_argument("--budget-gb", type=int, default=64,
                    help="serve: device-memory budget of the requests in flight (GiB)")
     p.add_argument("--tuned", metavar="JSON", help="autotuner table; picks k and cutoff")
-    p.add_argument("--scatter3", action="store_true",
-                   help="grid scatter in three blocks per SM (keys read when placed)")
     p.add_argument("--pl2", type=int, default=0,
                    help="PL2 leaves for subproblems above 8192 keys (0: FMCD, the paper's IPLS)")
     p.add_argument("--ingest-ncu", nargs=2, metavar=("CSV", "STATS_JSON"),
@@ -325,9 +326,7 @@ def run_gb300(args):
     pristine = {d: torch.from_numpy(inputs[d].view(np.uint8)).to(dev) for d in dists}
     work = torch.empty(n * 8, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
-    flags = ipls.ipls.FLAG_SCATTER3 if args.scatter3 else 0
-    ctx = ipls.Context(cutoff=args.cutoff, profile=True, stream=stream, pl2_leaves=args.pl2,
-                       flags=flags)
+    ctx = ipls.Context(cutoff=args.cutoff, profile=True, stream=stream, pl2_leaves=args.pl2)
 
     def step(i, timed):
         d = dists[i % len(dists)]
@@ -476,7 +475,6 @@ def run_gb300(args):
                                          "states 32): a tuned choice; the sorted output is "
                                          "the same, only the pass trace differs",
                        "model": f"PL2, {args.pl2} leaves, top level" if args.pl2 else "FMCD",
-                       "scatter_blocks_per_sm": 3 if args.scatter3 else 2,
                        "sample": "alpha*k-1 keys, alpha = 0.2*floor(log2 n)",
                        "l2": f"flushed: a {n * 8 >> 20} MiB input-restore copy runs between "
                              "timed steps (inputs larger than L2 from 2^25 keys)",
@@ -532,7 +530,62 @@ def run_segmented(args):
     work = torch.empty_like(src)
     stream = torch.cuda.current_stream()
     flags = ipls.ipls.FLAG_GRAPH if args.graph else 0
-    ctx = ipls.Context(k=k, cutoff=cutoff, stream=stream, flags=flags)
+    tuning = None
+    default_gkeys = None
+    if args.autotune:
+        from paper_2208_06902_gb300 import autotune
+        # a tuning instance of the same workload (other seeds), same size
+        tsz = datagen.segment_sizes(args.segments, seed=14)
+        if not args.stated_size:
+            tsz = np.maximum(np.rint(tsz * ((1 << args.log2n) / float(tsz.sum()))), 16).astype(np.int64)
+        tkeys, toff, _ = datagen.segmented(tsz, seed=15)
+        tsrc = torch.from_numpy(tkeys.view(np.uint8)).to(dev)
+        toffd = torch.from_numpy(toff).to(dev)
+        twork = torch.empty_like(tsrc)
+        ctxs = {}
+
+        def run_cfg(cfg):
+            key = tuple(sorted(cfg.items()))
+            if key not in ctxs:
+                for c_ in ctxs.values():
+                    c_.close()
+                ctxs.clear()
+                ctxs[key] = ipls.Context(stream=stream, **cfg)
+            twork.copy_(tsrc)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ipls.iplsSortSegmented(ctxs[key].ctx, twork.data_ptr(), toffd.data_ptr(), tsz.size, ipls.F64)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1)
+
+        cands = [dict(k=kk, cutoff=cc, flags=ff, pl2_leaves=pp) for kk in (64, 128, 256)
+                 for cc in (64, 128, 256, 512) for ff in (0, ipls.ipls.FLAG_GRAPH) for pp in (0, 64)]
+        tuning = autotune.tune_workload(run_cfg, cands, reps=3, log=lambda *a: None)
+        for c_ in ctxs.values():
+            c_.close()
+        del tsrc, twork
+        best = tuning["best"]
+        # the default configuration on the bench instance, for comparison
+        dctx = ipls.Context(k=256, cutoff=args.cutoff, stream=stream, flags=flags)
+        dts = []
+        for i in range(args.warmup + args.steps):
+            work.copy_(src)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ipls.iplsSortSegmented(dctx.ctx, work.data_ptr(), off.data_ptr(), sizes.size, ipls.F64)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if i >= args.warmup:
+                dts.append(e0.elapsed_time(e1))
+        dctx.close()
+        default_gkeys = round(n / (statistics.median(dts) * 1e-3) / 1e9, 4)
+        k, cutoff, flags = best["k"], best["cutoff"], best["flags"]
+        ctx = ipls.Context(stream=stream, **best)
+    else:
+        ctx = ipls.Context(k=k, cutoff=cutoff, stream=stream, flags=flags)
 
     def batch():
         work.copy_(src)
@@ -592,7 +645,11 @@ def run_segmented(args):
                                    else f", rescaled to sum ~2^{args.log2n}"),
                        "median_segment": int(np.median(sizes)), "max_segment": int(sizes.max()),
                        "k": k, "cutoff": cutoff, "tuned": bool(args.tuned),
-                       "graph": bool(args.graph)},
+                       "graph": bool(flags & ipls.ipls.FLAG_GRAPH)},
+            "autotune": ({"best": tuning["best"], "tuning_instance_ms": tuning["ms"],
+                          "candidates": len(tuning["all"]), "default_gkeys_s": default_gkeys,
+                          "default": {"k": 256, "cutoff": args.cutoff, "flags": 0, "pl2_leaves": 0}}
+                         if tuning else None),
             "call_us_4096_keys": overhead,
             "per_segment_calls": {"value": round(n / (t_each * 1e-3) / 1e9, 4), "unit": "Gkeys/s",
                                   "ms": round(t_each, 1), "calls": int(sizes.size)},

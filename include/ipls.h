@@ -104,11 +104,6 @@ typedef struct iplsConfig {
  * sorted result. */
 #define IPLS_FLAG_GRAPH 2
 
-/* cfg.flags: the grid-level scatter runs three blocks per SM and reads each
- * key when it places it (from L1, prefetched) instead of holding the tile's
- * keys in registers through the ranking (same result). */
-#define IPLS_FLAG_SCATTER3 8
-
 /* Accumulated device time of one kernel of the library (profile = 1).
  * bytes = algorithmic bytes: keys read + keys written by the launches, in
  * bytes (the classify/histogram sweep reads every live key once, the scatter

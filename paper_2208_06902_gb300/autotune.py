@@ -1,10 +1,17 @@
 """Autotuner for the sort's run parameters, by measurement on this GPU.
 
-The sorted output is unique (ascending totalOrder), so the base-case cutoff
-and the buckets per pass k change only the speed and the pass trace, never
-the result. ``tune`` times a grid of (k, cutoff) on seeded synthetic arrays
-of each size class and dtype and keeps the fastest. ``tuned_config`` looks
-a size up in the resulting table, which ``save``/``load`` keep as JSON.
+The sorted output is unique (ascending totalOrder), so the base-case cutoff,
+the buckets per pass k, the partition model (FMCD, or PL2 at the top level)
+and the graph mode of segmented sorts change only the speed and the pass
+trace, never the result.
+
+- ``tune`` times a grid of (k, cutoff, PL2 leaves) on seeded synthetic arrays
+  of each size class and dtype (normal, lognormal and Zipf keys) and keeps
+  the fastest; ``tuned_config`` looks a size up in the resulting table,
+  which ``save``/``load`` keep as JSON.
+- ``tune_workload`` times candidate configurations on a whole workload (for
+  example a segmented batch of uneven segments) through a caller-supplied
+  runner and keeps the fastest.
 
     python -m paper_2208_06902_gb300.autotune --out table.json
 """
@@ -18,7 +25,8 @@ import time
 DTYPE_NAMES = {0: "f64", 1: "f32", 2: "u64", 3: "u32"}
 DEFAULT_SIZES = [1 << 12, 1 << 16, 1 << 20, 1 << 24, 1 << 27]
 DEFAULT_CUTOFFS = [32, 64, 128, 256, 512, 1024]
-DEFAULT_KS = [128, 256]
+DEFAULT_KS = [64, 128, 256]
+DEFAULT_PL2 = [0, 64]
 
 
 def tuned_config(n: int, dtype: int, table: dict) -> dict:
@@ -32,7 +40,7 @@ def tuned_config(n: int, dtype: int, table: dict) -> dict:
         if s <= n:
             pick = s
     r = rows[str(pick)]
-    return {"k": int(r["k"]), "cutoff": int(r["cutoff"])}
+    return {"k": int(r["k"]), "cutoff": int(r["cutoff"]), "pl2_leaves": int(r.get("pl2_leaves", 0))}
 
 
 def save(table: dict, path: str) -> None:
@@ -47,19 +55,38 @@ def load(path: str) -> dict:
 
 
 def _inputs(n: int, dtype: int):
-    """Two seeded arrays per size class: Normal(0,1) and Zipf, as dtype."""
+    """Three seeded arrays per size class: Normal(0,1), LogNormal(0,0.5) (or
+    raw 64-bit draws for integers) and Zipf, as dtype."""
     import numpy as np
 
     import datagen
     np_t = {0: np.float64, 1: np.float32, 2: np.uint64, 3: np.uint32}[dtype]
     if dtype in (0, 1):
-        return [datagen.generate("normal", n, np_t, 21), datagen.generate("zipf", n, np_t, 22)]
-    return [datagen.generate("raw64", n, np_t, 21), datagen.generate("zipf", n, np_t, 22)]
+        return [datagen.generate("normal", n, np_t, 21), datagen.generate("lognormal", n, np_t, 23),
+                datagen.generate("zipf", n, np_t, 22)]
+    return [datagen.generate("raw64", n, np_t, 21), datagen.generate("lognormal", n, np_t, 23),
+            datagen.generate("zipf", n, np_t, 22)]
+
+
+def tune_workload(run, candidates, reps: int = 3, log=print) -> dict:
+    """Times every candidate configuration (a dict of Context keywords) with
+    ``run(cfg) -> ms`` (the caller's workload, one timed execution; the
+    first call of each candidate is a warm-up) and returns {"best": cfg,
+    "ms": best time, "all": [(cfg, ms), ...]}."""
+    results = []
+    for cfg in candidates:
+        run(cfg)
+        ms = sorted(run(cfg) for _ in range(reps))[reps // 2]
+        results.append((cfg, round(ms, 4)))
+        log(f"{cfg}: {ms:.3f} ms")
+    best = min(results, key=lambda r: r[1])
+    return {"best": best[0], "ms": best[1], "all": results}
 
 
 def tune(sizes=DEFAULT_SIZES, dtypes=(0, 1, 2, 3), cutoffs=DEFAULT_CUTOFFS, ks=DEFAULT_KS,
-         reps: int = 3, log=print) -> dict:
-    """Times every (k, cutoff) on each size class and dtype; returns the table."""
+         pl2=DEFAULT_PL2, reps: int = 3, log=print) -> dict:
+    """Times every (k, cutoff, PL2 leaves) on each size class and dtype;
+    returns the table."""
     import numpy as np
     import torch
 
@@ -73,31 +100,31 @@ def tune(sizes=DEFAULT_SIZES, dtypes=(0, 1, 2, 3), cutoffs=DEFAULT_CUTOFFS, ks=D
                       for a in _inputs(n, dtype)]
             work = torch.empty_like(arrays[0])
             best = None
-            for k in ks:
-                for cutoff in cutoffs:
-                    ctx = ipls.Context(k=k, cutoff=cutoff)
-                    total = 0.0
-                    for rep in range(reps + 1):
-                        for a in arrays:
-                            work.copy_(a)
-                            s0 = torch.cuda.Event(enable_timing=True)
-                            s1 = torch.cuda.Event(enable_timing=True)
-                            s0.record()
-                            ctx.sort_ptr(work.data_ptr(), n, dtype)
-                            s1.record()
-                            torch.cuda.synchronize()
-                            if rep > 0:  # the first round allocates scratch
-                                total += s0.elapsed_time(s1)
-                    ctx.close()
-                    ms = total / (reps * len(arrays))
-                    if best is None or ms < best["ms"]:
-                        best = {"k": k, "cutoff": cutoff, "ms": round(ms, 4),
-                                "gkeys_s": round(n / (ms * 1e-3) / 1e9, 3)}
+            for k, cutoff, leaves in [(k, c, p) for k in ks for c in cutoffs for p in pl2]:
+                ctx = ipls.Context(k=k, cutoff=cutoff, pl2_leaves=leaves)
+                total = 0.0
+                for rep in range(reps + 1):
+                    for a in arrays:
+                        work.copy_(a)
+                        s0 = torch.cuda.Event(enable_timing=True)
+                        s1 = torch.cuda.Event(enable_timing=True)
+                        s0.record()
+                        ctx.sort_ptr(work.data_ptr(), n, dtype)
+                        s1.record()
+                        torch.cuda.synchronize()
+                        if rep > 0:  # the first round allocates scratch
+                            total += s0.elapsed_time(s1)
+                ctx.close()
+                ms = total / (reps * len(arrays))
+                if best is None or ms < best["ms"]:
+                    best = {"k": k, "cutoff": cutoff, "pl2_leaves": leaves, "ms": round(ms, 4),
+                            "gkeys_s": round(n / (ms * 1e-3) / 1e9, 3)}
             rows[str(n)] = best
             log(f"{DTYPE_NAMES[dtype]} n={n}: {best}")
         entries[DTYPE_NAMES[dtype]] = rows
     return {"device": torch.cuda.get_device_name(dev), "reps": reps, "cutoffs": list(cutoffs),
-            "ks": list(ks), "created": time.strftime("%Y-%m-%d %H:%M:%S"), "entries": entries}
+            "ks": list(ks), "pl2": list(pl2), "created": time.strftime("%Y-%m-%d %H:%M:%S"),
+            "entries": entries}
 
 
 def main(argv=None) -> int:

@@ -575,7 +575,6 @@ iplsStatus device_enqueue(Workspace& w, int64_t n, int dtype, const int64_t* off
     a.max_sample = sample_bound;
     a.pl2_leaves = cfg.pl2_leaves;
     a.pl2_depth = cfg.pl2_depth;
-    a.scatter3 = (cfg.flags & IPLS_FLAG_SCATTER3) ? 1 : 0;
     a.knots = cfg.pl2_leaves > 0 ? X.knots : nullptr;
     const int sms = c->num_sms;
     IPLS_CUDA(timed(w, kkFit, [&] { return launch_fit(a, w.stream, sample_bound, sms); }, level));
@@ -861,7 +860,6 @@ iplsStatus sort_impl(Workspace& w, void* keys, int64_t n, int dtype, const int64
     a.max_sample = max_sample;
     a.pl2_leaves = cfg.pl2_leaves;
     a.pl2_depth = cfg.pl2_depth;
-    a.scatter3 = (cfg.flags & IPLS_FLAG_SCATTER3) ? 1 : 0;
     a.knots = cfg.pl2_leaves > 0 ? X.knots : nullptr;
     IPLS_CUDA(timed(w, kkFit, [&] { return launch_fit(a, w.stream, max_sample, c->num_sms); }, level));
     IPLS_CUDA(timed(w, kkHist, [&] { return launch_hist(a, w.stream, 0, occupancy_grid(c, 0, dtype)); }, level));

@@ -807,12 +807,11 @@ struct Classifier {
 
   __device__ __forceinline__ int bucket(Bits b) const {
     if (kind == kSplitter) return splitter_bucket((uint64_t)KT<K>::ord(b), split, nsplit);
-    if (gfast && !ufast) {
-      const int r = flt_bucket(b);
-      if (r >= 0) return r;
-    }
     if (ufast) {
       const int r = ord_bucket(KT<K>::ord(b));
+      if (r >= 0) return r;
+    } else if (gfast) {
+      const int r = flt_bucket(b);
       if (r >= 0) return r;
     }
     if (fast) {
@@ -826,12 +825,11 @@ struct Classifier {
   // the splitter tree or when the estimate is off.
   __device__ __forceinline__ int bucket_or_defer(Bits b) const {
     if (kind == kSplitter) return splitter_bucket((uint64_t)KT<K>::ord(b), split, nsplit);
-    if (gfast && !ufast) {
-      const int r = flt_bucket(b);
-      if (r >= 0) return r;
-    }
     if (ufast) {
       const int r = ord_bucket(KT<K>::ord(b));
+      if (r >= 0) return r;
+    } else if (gfast) {
+      const int r = flt_bucket(b);
       if (r >= 0) return r;
     }
     if (fast) return fast_bucket(b);

@@ -294,7 +294,6 @@ struct LevelArgs {
   // capacities; a level after an overflow or a device error does nothing.
   const LevelCtl* cnt;
   long long* trace_ctr;  // device-driven levels: next free grid trace record
-  int scatter3;          // k_scatter in three blocks per SM (keys read when placed)
 };
 
 struct ResidentArgs {

@@ -590,11 +590,8 @@ struct ScatterSmem {
 
 // Stable scatter of every tile of the level: each block owns a contiguous
 // range of tiles; 512 threads, 8 keys each, read straight into registers.
-// kBlocks: blocks per SM the registers allow.  With 3 the keys are not held
-// in registers through the ranking: the tile is prefetched into L1 at the
-// start and each key is read when it is placed.
-template <class K, int kBlocks>
-__global__ void __launch_bounds__(kScatterThreads, kBlocks) k_scatter(LevelArgs a) {
+template <class K>
+__global__ void __launch_bounds__(kScatterThreads, 2) k_scatter(LevelArgs a) {
   using T = KT<K>;
   using Bits = typename T::Bits;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -622,17 +619,12 @@ __global__ void __launch_bounds__(kScatterThreads, kBlocks) k_scatter(LevelArgs 
     const int tn = rem < kTile ? (int)rem : kTile;
     const Bits* src = keys_of<const Bits>(sub.buf, sub.ubase, a.buf) + kbase;
     const uint8_t* ids = a.bids + kbase;
-    constexpr bool kHold = kBlocks < 3;
-    Bits v[kHold ? kSKPT : 1];
+    Bits v[kSKPT];
     unsigned int br[kSKPT];   // bucket id, then bucket << 16 | rank within warp
 #pragma unroll
     for (int j = 0; j < kSKPT; ++j) {
       const int i = warp * kSKPW + j * 32 + lane;
-      if (kHold) {
-        v[kHold ? j : 0] = (i < tn) ? src[i] : Bits(0);
-      } else if (i < tn) {
-        asm volatile("prefetch.global.L1 [%0];" ::"l"(src + i));
-      }
+      v[j] = (i < tn) ? src[i] : Bits(0);
       br[j] = (i < tn) ? (unsigned)ids[i] : (unsigned)kMaxK;
     }
     __syncthreads();  // wcnt zeroed
@@ -698,7 +690,7 @@ __global__ void __launch_bounds__(kScatterThreads, kBlocks) k_scatter(LevelArgs 
       const int bk = (int)(br[j] >> 16);
       if (bk < kMaxK) {
         const int lp = sh.tile_start[bk] + sh.wcnt[warp][bk] + (int)(br[j] & 0xFFFF);
-        sh.stage[lp] = kHold ? v[kHold ? j : 0] : src[warp * kSKPW + j * 32 + lane];
+        sh.stage[lp] = v[j];
         sh.sbid[lp] = (unsigned char)bk;
       }
     }
@@ -844,21 +836,16 @@ cudaError_t launch_tilescan(const LevelArgs& a, cudaStream_t s, int grid) {
   return cudaGetLastError();
 }
 
-template <class K, int kBlocks>
-static cudaError_t launch_scatter_t(const LevelArgs& a, cudaStream_t s, int grid) {
-  const size_t smem = sizeof(ScatterSmem<K>);
-  cudaFuncSetAttribute(k_scatter<K, kBlocks>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  int g = resident_blocks((const void*)k_scatter<K, kBlocks>, kScatterThreads, smem, grid);
-  if (g > a.ntiles) g = (int)a.ntiles;
-  k_scatter<K, kBlocks><<<g, kScatterThreads, smem, s>>>(a);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_scatter(const LevelArgs& a, cudaStream_t s, int grid) {
   if (a.ntiles <= 0) return cudaSuccess;
   return by_dtype(a.dtype, [&](auto* tag) {
     using K = std::remove_pointer_t<decltype(tag)>;
-    return a.scatter3 ? launch_scatter_t<K, 3>(a, s, grid) : launch_scatter_t<K, 2>(a, s, grid);
+    const size_t smem = sizeof(ScatterSmem<K>);
+    cudaFuncSetAttribute(k_scatter<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int g = resident_blocks((const void*)k_scatter<K>, kScatterThreads, smem, grid);
+    if (g > a.ntiles) g = (int)a.ntiles;
+    k_scatter<K><<<g, kScatterThreads, smem, s>>>(a);
+    return cudaGetLastError();
   });
 }
 

@@ -31,7 +31,6 @@ class iplsConfig(ctypes.Structure):
 
 FLAG_THRESHOLD_INDEX = 1
 FLAG_GRAPH = 2
-FLAG_SCATTER3 = 8
 
 
 class iplsKernelStat(ctypes.Structure):

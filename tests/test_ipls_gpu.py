@@ -224,13 +224,3 @@ def test_lookback_timeout_leaves_a_permutation():
     got, _ = gpu_sort(x)
     assert _same(got, want)
 
-
-@pytest.mark.parametrize("dtype", DTYPES)
-@pytest.mark.parametrize("dist", ["normal", "zipf", "twodups"])
-def test_scatter_in_three_blocks_gives_the_oracle_passes(dtype, dist):
-    # IPLS_FLAG_SCATTER3: the grid scatter reads each key when it places it
-    x = datagen.generate(dist, 300_017, dtype, seed=23)
-    want, recs, _ = oracle.sort(x, cutoff=32, trace_cap=100_000)
-    got, ctx = gpu_sort(x, cutoff=32, trace_cap=100_000, flags=8)
-    assert _same(got, want)
-    compare_traces(ctx.trace(), recs)
