@@ -297,6 +297,8 @@ __global__ void __launch_bounds__(kPassThreads, 4) k_hist(LevelArgs a, int rehis
       th[b] = tot;
       acc[b] += tot;
     }
+    // the rows are zero again before any warp counts the next tile
+    __syncthreads();
   }
   __syncthreads();
   if (cur >= 0) {

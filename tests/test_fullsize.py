@@ -73,3 +73,25 @@ def test_2p28_f64_distributions(dist):
 @pytest.mark.parametrize("kind,code", [("u64", 2), ("u32", 3), ("f32", 1)])
 def test_integer_and_f32_full_sizes(kind, code):
     _check(datagen.config3(kind), code)
+
+
+def test_repeated_full_size_sorts_are_exact():
+    """Back-to-back sorts of 2^28 f64 exponential keys, each in a new context
+    right after the host-to-device copy: every output is the sorted input
+    (a histogram race between tiles of one subproblem once lost counts in
+    some of these runs and left a non-permutation)."""
+    from paper_2208_06902_gb300 import Context
+    x = datagen.config2("exponential", 1 << 28)
+    want = None
+    for _ in range(4):
+        dev = torch.from_numpy(x.view(np.uint8)).cuda()
+        ctx = Context(k=256, cutoff=256)
+        ctx.sort_ptr(dev.data_ptr(), x.size, 0)
+        torch.cuda.synchronize()
+        out = _total_order_key(dev.view(torch.float64), 0)
+        if want is None:
+            want = torch.sort(_total_order_key(torch.from_numpy(x.view(np.uint8)).cuda()
+                                               .view(torch.float64), 0)).values
+        assert torch.equal(out, want)
+        ctx.close()
+        del dev, out
