@@ -692,6 +692,10 @@ struct Classifier {
   int kind, nb, fast, rho, nsplit, ufast, ushift, gfast;
   long long qlo;
   float af, bcf, crel, cabs, auf, ucabs, gaf, gbf, gc1, gcabs;
+  float nbm1f;      // nb - 1 as binary32
+  float aufs;       // auf with the sign of x_lo's binade folded in (float keys)
+  unsigned xl32, xh32;  // x_lo's bits, low and high words
+  bool neg_binade;  // x_lo is negative (float keys)
   double A, Bc;
   Bits xlo;
   Ord ulo;
@@ -720,6 +724,11 @@ struct Classifier {
     gbf = m.gbf;
     gc1 = m.gc1;
     gcabs = m.gcabs;
+    nbm1f = (float)(nb - 1);
+    neg_binade = KT<K>::kMant > 0 && KT<K>::negative(xlo);
+    aufs = neg_binade ? -auf : auf;
+    xl32 = (unsigned)(unsigned long long)xlo;
+    xh32 = (unsigned)((unsigned long long)xlo >> 32);
     nsplit = 0;
     split = nullptr;
   }
@@ -803,6 +812,96 @@ struct Classifier {
     }
     const float v = fmaf(gaf, xf, gbf);
     return decide(v, fmaf(gc1, fabsf(xf), fmaf(crel, fabsf(v), gcabs)));
+  }
+
+  // decide() without branches: the bucket (valid when ok) and whether the
+  // certified interval [v - del, v + del] holds no bucket boundary.  Both
+  // ends are floored and clamped to [0, nb - 1] (clamp∘floor is monotone),
+  // so equal results decide every point of the interval, the clamped ends
+  // included.  v and del are finite here (keys they would not be finite
+  // for are excluded by the caller's range checks).
+  __device__ __forceinline__ int decide_bf(float v, float del, bool& ok) const {
+    const float fl = fminf(fmaxf(floorf(v - del), 0.0f), nbm1f);
+    const float fh = fminf(fmaxf(floorf(v + del), 0.0f), nbm1f);
+    ok = fl == fh;
+    return __float2int_rz(fl);
+  }
+
+  // ord_bucket() without branches, on the key's own bits.  Float keys: in
+  // x_lo's binade the totalOrder difference is the raw-bits difference, with
+  // its sign flipped for negative binades (folded into aufs); the shift
+  // truncates toward -inf either way, within the same bound.  A shifted
+  // difference beyond int32 lies far outside the model's range (|D >> s| >=
+  // 2^31 > 2^30): clamped by its sign.  ok = false for a key outside the
+  // binade (integers: whose difference from x_lo overflows) or whose
+  // interval holds a boundary.
+  __device__ __forceinline__ int ord_bf(Bits b, bool& ok) const {
+    using T = KT<K>;
+    if (T::kMant == 23) {
+      // binary32: |bits - x_lo bits| < 2^23 in the binade
+      const unsigned u = (unsigned)b, x = (unsigned)xlo;
+      const bool in = ((u ^ x) >> 23) == 0;
+      const int ds = (int)(u - x) >> ushift;
+      const float v = fmaf(aufs, __int2float_rn(ds), bcf);
+      bool okd;
+      const int r = decide_bf(v, fmaf(crel, fabsf(v), ucabs), okd);
+      ok = in && okd;
+      return r;
+    }
+    unsigned dl, dh;
+    bool in;
+    if (T::kMant == 52) {
+      // binary64 on 32-bit halves: same binade iff the top 12 bits agree
+      const unsigned bl = (unsigned)(unsigned long long)b, bh = (unsigned)((unsigned long long)b >> 32);
+      in = ((bh ^ xh32) >> 20) == 0;
+      asm("sub.cc.u32 %0, %2, %3;\n\tsubc.u32 %1, %4, %5;" : "=r"(dl), "=r"(dh) : "r"(bl), "r"(xl32), "r"(bh), "r"(xh32));
+    } else {
+      const uint64_t du = (uint64_t)b - (uint64_t)ulo;
+      dl = (unsigned)du;
+      dh = (unsigned)(du >> 32);
+      in = ((uint64_t)b >= (uint64_t)ulo) == ((long long)du >= 0);
+    }
+    // the low word of D >> s, and whether D >> s fits in it
+    int ds;
+    bool fits;
+    if (ushift < 32) {
+      ds = (int)__funnelshift_r(dl, dh, ushift);
+      fits = ((int)dh >> ushift) == (ds >> 31);
+    } else {
+      ds = (int)dh >> (ushift - 32);
+      fits = true;
+    }
+    const float v = fmaf(aufs, __int2float_rn(ds), bcf);
+    bool okd;
+    int r = decide_bf(v, fmaf(crel, fabsf(v), ucabs), okd);
+    const bool above = ((int)dh >= 0) != neg_binade;  // the key's value is above x_lo's
+    r = fits ? r : (above ? nb - 1 : 0);
+    ok = in && (okd || !fits);
+    return r;
+  }
+
+  // flt_bucket() without branches.
+  __device__ __forceinline__ int flt_bf(Bits b, bool& ok) const {
+    float xf;
+    bool in;
+    if (sizeof(Bits) == 8) {
+      const unsigned long long u = (unsigned long long)b;
+      const unsigned hi = (unsigned)(u >> 32), lo = (unsigned)u;
+      const unsigned e = (hi >> 20) & 0x7FFu;
+      in = e - 897u <= 253u;
+      const unsigned mant = __funnelshift_l(lo, hi, 3) & 0x7FFFFFu;
+      xf = __uint_as_float((hi & 0x80000000u) | ((e - 896u) << 23) | mant);
+    } else {
+      const unsigned u = (unsigned)b;
+      const unsigned e = (u >> 23) & 0xFFu;
+      in = e - 1u <= 253u;
+      xf = __uint_as_float(u);
+    }
+    const float v = fmaf(gaf, xf, gbf);
+    bool okd;
+    const int r = decide_bf(v, fmaf(gc1, fabsf(xf), fmaf(crel, fabsf(v), gcabs)), okd);
+    ok = in && okd;
+    return r;
   }
 
   __device__ __forceinline__ int bucket(Bits b) const {

@@ -184,6 +184,11 @@ __global__ void __launch_bounds__(kFitThreads) k_fit(LevelArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// How k_hist classifies the keys of a subproblem: the branch-free
+// same-binade or uncentred estimate of a linear model, or the general
+// dispatch (fixed-point estimate, splitter tree, PL2, binary64 only).
+constexpr int kPathGeneric = 0, kPathOrd = 1, kPathFlt = 2;
+
 template <class K>
 __global__ void __launch_bounds__(kPassThreads, 4) k_hist(LevelArgs a, int rehist_only) {
   using T = KT<K>;
@@ -203,6 +208,7 @@ __global__ void __launch_bounds__(kPassThreads, 4) k_hist(LevelArgs a, int rehis
   const int64_t t0 = nt * blockIdx.x / gridDim.x, t1 = nt * (blockIdx.x + 1) / gridDim.x;
   int cur = -1;
   bool use_tab = false;
+  int path = kPathGeneric;
   Classifier<K> cls;
   for (int64_t t = t0; t < t1; ++t) {
     const int s = a.tile2sub[t];
@@ -223,6 +229,7 @@ __global__ void __launch_bounds__(kPassThreads, 4) k_hist(LevelArgs a, int rehis
       __syncthreads();
       cls.load(sm, a.exact_only);
       use_tab = a.use_tables && sm.l.kind == kLinear && tab.ok;
+      path = sm.l.kind != kLinear ? kPathGeneric : cls.ufast ? kPathOrd : cls.gfast ? kPathFlt : kPathGeneric;
       if (sm.l.kind == kPL2) {
         pl2_tables(sm, a.knots + (size_t)s * (a.pl2_leaves + 1), pl_yf, pl_lo, threadIdx.x, blockDim.x);
         __syncthreads();
@@ -255,16 +262,35 @@ __global__ void __launch_bounds__(kPassThreads, 4) k_hist(LevelArgs a, int rehis
         }
       } else {
         unsigned dmask = 0;  // steps whose key needs the binary64 model
+        if (path != kPathGeneric) {
+          // the estimate of the whole subproblem, without branches; keys it
+          // cannot decide go to the binary64 batch below
 #pragma unroll
-        for (int j = 0; j < kChunk; ++j) {
-          const int i = c0 + j * kPassThreads + threadIdx.x;
-          if (i < tn) {
-            const int bk = sm.l.kind == kPL2 ? pl2_bucket<K>(v[j], sm, pl_yf, pl_lo) : cls.bucket_or_defer(v[j]);
-            if (bk >= 0) {
-              ids[i] = (uint8_t)bk;
-              atomicAdd(&hist[warp][bk], 1u);
-            } else {
-              dmask |= 1u << j;
+          for (int j = 0; j < kChunk; ++j) {
+            const int i = c0 + j * kPassThreads + threadIdx.x;
+            if (i < tn) {
+              bool ok;
+              const int bk = path == kPathOrd ? cls.ord_bf(v[j], ok) : cls.flt_bf(v[j], ok);
+              if (ok) {
+                ids[i] = (uint8_t)bk;
+                atomicAdd(&hist[warp][bk], 1u);
+              } else {
+                dmask |= 1u << j;
+              }
+            }
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < kChunk; ++j) {
+            const int i = c0 + j * kPassThreads + threadIdx.x;
+            if (i < tn) {
+              const int bk = sm.l.kind == kPL2 ? pl2_bucket<K>(v[j], sm, pl_yf, pl_lo) : cls.bucket_or_defer(v[j]);
+              if (bk >= 0) {
+                ids[i] = (uint8_t)bk;
+                atomicAdd(&hist[warp][bk], 1u);
+              } else {
+                dmask |= 1u << j;
+              }
             }
           }
         }
