@@ -429,7 +429,7 @@ iplsStatus device_prepare(Workspace& w, int64_t n, int64_t nseg, int dtype) {
   const iplsConfig& cfg = c->cfg;
   const DevCaps d = dev_caps(cfg, n, nseg, dtype);
   IPLS_TRY(ensure(w, w.scratch, w.scratch_cap, n * (int64_t)key_bytes(dtype)));
-  IPLS_TRY(ensure(w, w.bids, w.bids_cap, n));
+  IPLS_TRY(ensure(w, w.bids, w.bids_cap, n + 16));
   IPLS_TRY(ensure(w, w.slow, w.slow_cap, 2 * (n / (cfg.cutoff + 1)) + 4096));
   for (Slot& X : w.slot) {
     IPLS_TRY(ensure(w, X.subs, X.sub_cap, d.sub));
@@ -629,7 +629,7 @@ iplsStatus sort_impl(Workspace& w, void* keys, int64_t n, int dtype, const int64
   w.stats.max_bucket_frac = 0.0;
   w.trace_grid_count = 0;
   IPLS_TRY(ensure(w, w.scratch, w.scratch_cap, n * (int64_t)wb));
-  IPLS_TRY(ensure(w, w.bids, w.bids_cap, n));
+  IPLS_TRY(ensure(w, w.bids, w.bids_cap, n + 16));
   IPLS_TRY(ensure(w, w.slow, w.slow_cap, 2 * (n / (cfg.cutoff + 1)) + 4096));
   if (traced && c->trace_alloc < cfg.trace_cap) {
     IPLS_CUDA(cudaStreamSynchronize(w.stream));

@@ -880,6 +880,72 @@ struct Classifier {
     return r;
   }
 
+  // A refinement of bucket bk for ordering inside it: an index in [0, 8)
+  // that never decreases as the key grows among the keys of bucket bk --
+  // the eighth of [bk, bk + 1) the estimate of path 1 (same-binade) or 2
+  // (uncentred) puts the key in, clamped; a key that estimate does not
+  // cover takes the end it lies on (below or above x_lo's binade, beyond
+  // int32 after the shift, or outside binary32's normal range, where zero
+  // and the tiny values sit between the negative and the positive keys).
+  // It only orders keys inside their (exact) bucket, so it needs no
+  // certificate.
+  __device__ __forceinline__ int sub8(Bits b, int bk, int path) const {
+    using T = KT<K>;
+    float v;
+    if (path == 1) {
+      bool cover;
+      if (T::kMant == 23) {
+        const unsigned u = (unsigned)b, x = (unsigned)xlo;
+        cover = ((u ^ x) >> 23) == 0;
+        v = fmaf(aufs, __int2float_rn((int)(u - x) >> ushift), bcf);
+      } else {
+        unsigned dl, dh;
+        bool in;
+        if (T::kMant == 52) {
+          const unsigned bl = (unsigned)(unsigned long long)b, bh = (unsigned)((unsigned long long)b >> 32);
+          in = ((bh ^ xh32) >> 20) == 0;
+          asm("sub.cc.u32 %0, %2, %3;\n\tsubc.u32 %1, %4, %5;" : "=r"(dl), "=r"(dh) : "r"(bl), "r"(xl32), "r"(bh), "r"(xh32));
+        } else {
+          const uint64_t du = (uint64_t)b - (uint64_t)ulo;
+          dl = (unsigned)du;
+          dh = (unsigned)(du >> 32);
+          in = ((uint64_t)b >= (uint64_t)ulo) == ((long long)du >= 0);
+        }
+        int ds;
+        bool fits;
+        if (ushift < 32) {
+          ds = (int)__funnelshift_r(dl, dh, ushift);
+          fits = ((int)dh >> ushift) == (ds >> 31);
+        } else {
+          ds = (int)dh >> (ushift - 32);
+          fits = true;
+        }
+        cover = in && fits;
+        v = fmaf(aufs, __int2float_rn(ds), bcf);
+      }
+      if (!cover) return T::ord(b) < ulo ? 0 : 7;
+    } else {
+      float xf;
+      if (sizeof(Bits) == 8) {
+        const unsigned long long u = (unsigned long long)b;
+        const unsigned hi = (unsigned)(u >> 32), lo = (unsigned)u;
+        const unsigned e = (hi >> 20) & 0x7FFu;
+        const float inf = __uint_as_float((hi & 0x80000000u) | 0x7F800000u);
+        const unsigned mant = __funnelshift_l(lo, hi, 3) & 0x7FFFFFu;
+        xf = e < 897u ? 0.0f
+             : e > 1150u ? inf
+                         : __uint_as_float((hi & 0x80000000u) | ((e - 896u) << 23) | mant);
+      } else {
+        const unsigned u = (unsigned)b;
+        const unsigned e = (u >> 23) & 0xFFu;
+        xf = e == 0u ? 0.0f : e == 255u ? __uint_as_float((u & 0x80000000u) | 0x7F800000u) : __uint_as_float(u);
+      }
+      v = fmaf(gaf, xf, gbf);
+    }
+    const float t = fminf(fmaxf(floorf((v - (float)bk) * 8.0f), 0.0f), 7.0f);
+    return (int)t;
+  }
+
   // flt_bucket() without branches.
   __device__ __forceinline__ int flt_bf(Bits b, bool& ok) const {
     float xf;

@@ -460,7 +460,9 @@ __global__ void __launch_bounds__(kResidentThreads, 2) k_slow(ResidentArgs a) {
 template <class K, int kCap, int kW>
 struct TailSmem {
   typename KT<K>::Ord keys[kCap];
-  unsigned char seg[kCap];   // segment (bucket or child) of each position
+  // segment of each position: a bucket or child, or (large tasks) a bucket
+  // eighth (bucket * 8 + refinement)
+  typename std::conditional<kCap == kResidentMax, unsigned short, unsigned char>::type seg[kCap];
   unsigned short wcnt[kW][kMaxK];   // each warp's offset inside every bucket (stable placement)
   unsigned int peer[kW][kMaxK];     // per-warp bucket counts, then placement cursors (or, for
                                     // stable placement, lanes of the current step per bucket)
@@ -507,6 +509,36 @@ __device__ __forceinline__ void push_whole(const ResidentArgs& a, int64_t off, i
 constexpr int kPosBits = 13;
 static_assert(kResidentMax <= (1 << kPosBits), "positions must fit the packed word");
 
+// Large tail tasks cut their buckets into eighths only when the keys fill
+// at least this many buckets.
+constexpr int kFineMinBuckets = 64;
+
+// Number of words in keys[s, e) below kp (the rank of a packed word in its
+// segment; packed words are distinct).  Two (8-byte) or four (4-byte)
+// words per shared-memory load; the array is 16-byte aligned.
+template <class Ord>
+__device__ __forceinline__ int count_below(const Ord* keys, int s, int e, Ord kp) {
+  int cnt = 0;
+  int r = s;
+  if (sizeof(Ord) == 8) {
+    if ((r & 1) && r < e) cnt += keys[r++] < kp ? 1 : 0;
+#pragma unroll 2
+    for (; r + 2 <= e; r += 2) {
+      const ulonglong2 w = *reinterpret_cast<const ulonglong2*>(keys + r);
+      cnt += ((Ord)w.x < kp ? 1 : 0) + ((Ord)w.y < kp ? 1 : 0);
+    }
+  } else {
+    for (; (r & 3) && r < e; ++r) cnt += keys[r] < kp ? 1 : 0;
+#pragma unroll 2
+    for (; r + 4 <= e; r += 4) {
+      const uint4 w = *reinterpret_cast<const uint4*>(keys + r);
+      cnt += ((Ord)w.x < kp ? 1 : 0) + ((Ord)w.y < kp ? 1 : 0) + ((Ord)w.z < kp ? 1 : 0) + ((Ord)w.w < kp ? 1 : 0);
+    }
+  }
+  for (; r < e; ++r) cnt += keys[r] < kp ? 1 : 0;
+  return cnt;
+}
+
 // kThreads threads, tasks of at most kCap keys; the small size takes tasks
 // of up to kTailSmall keys, the large one the rest (each skips the other's).
 // One task: the group at list position gi (all threads of the block).
@@ -528,6 +560,8 @@ __device__ __forceinline__ void tail_task(const ResidentArgs& a, int gi, unsigne
   Bits* dst = reinterpret_cast<Bits*>(g.ubase) + g.off;
   int nseg;
   bool split_tree = false;  // children at odd ids are equality buckets
+  bool fine = false;        // segments are bucket eighths (starts in fstart)
+  unsigned* const fstart = &sh.peer[0][0];
   if (g.fit >= 0) {
     // the model: a copy in shared memory for the phases after the first
     // barrier; until then every thread reads it from global memory, and each
@@ -571,20 +605,43 @@ __device__ __forceinline__ void tail_task(const ResidentArgs& a, int gi, unsigne
       // task's key range on the side
       unsigned dmask = 0;
       Ord klo = ~(Ord)0, khi = 0;
+      // a linear model with a same-binade or uncentred estimate is evaluated
+      // without branches (undecided keys are deferred); the rest through the
+      // general dispatch
+      const int path = split_tree || gmp->l.kind != kLinear ? 0 : cls.ufast ? 1 : cls.gfast ? 2 : 0;
+      if (path != 0) {
 #pragma unroll
-      for (int j = 0; j < kPT; ++j) {
-        if (j < steps) {
-          const int i = warp * chunk + j * 32 + lane;
-          int bk = kMaxK;
-          if (i < n) {
-            const Ord o = T::ord(v[j]);
-            klo = o < klo ? o : klo;
-            khi = o > khi ? o : khi;
-            bk = split_tree ? splitter_bucket((uint64_t)o, splits, nsplit)
-                            : cls.bucket_or_defer(v[j]);
-            if (bk < 0) dmask |= 1u << j;
+        for (int j = 0; j < kPT; ++j) {
+          if (j < steps) {
+            const int i = warp * chunk + j * 32 + lane;
+            int bk = kMaxK;
+            if (i < n) {
+              const Ord o = T::ord(v[j]);
+              klo = o < klo ? o : klo;
+              khi = o > khi ? o : khi;
+              bool ok;
+              bk = path == 1 ? cls.ord_bf(v[j], ok) : cls.flt_bf(v[j], ok);
+              if (!ok) dmask |= 1u << j;
+            }
+            br[j] = (unsigned)bk;
           }
-          br[j] = (unsigned)bk;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < kPT; ++j) {
+          if (j < steps) {
+            const int i = warp * chunk + j * 32 + lane;
+            int bk = kMaxK;
+            if (i < n) {
+              const Ord o = T::ord(v[j]);
+              klo = o < klo ? o : klo;
+              khi = o > khi ? o : khi;
+              bk = split_tree ? splitter_bucket((uint64_t)o, splits, nsplit)
+                              : cls.bucket_or_defer(v[j]);
+              if (bk < 0) dmask |= 1u << j;
+            }
+            br[j] = (unsigned)bk;
+          }
         }
       }
 #pragma unroll
@@ -654,7 +711,9 @@ __device__ __forceinline__ void tail_task(const ResidentArgs& a, int gi, unsigne
         sh.tlo = lo;
         sh.tpk = (Ord)(hi - lo) < kSpan ? 1 : 0;
       }
-      __syncthreads();
+      // non-empty buckets (keys spread over few buckets are mostly copies
+      // of few values, which eighths would not separate)
+      const int nonempty = __syncthreads_count(threadIdx.x < kMaxK && sh.tot[threadIdx.x] > 0);
       slow = sh.slow_all != 0;
       if (!slow) {
         if (warp == 0) {
@@ -709,20 +768,71 @@ __device__ __forceinline__ void tail_task(const ResidentArgs& a, int gi, unsigne
             }
           }
         }
-        // every bucket is base-cased unless `stable`: the order inside a
-        // bucket does not matter, and a shared cursor per (warp, bucket)
-        // gives each key its place
+        // large tasks of a linear model with an estimate: every bucket is
+        // cut into eighths by a refinement that never decreases inside the
+        // bucket, so that the base case ranks each key among about an
+        // eighth of its bucket
+        fine = kCap == kResidentMax && path != 0 && !stable && nonempty >= kFineMinBuckets;
+        if (fine) {
+          unsigned* const fcur = reinterpret_cast<unsigned*>(&sh.wcnt[0][0]);
+          static_assert(kCap != kResidentMax || sizeof(sh.wcnt) >= kMaxK * 8 * sizeof(unsigned), "eighth cursors must fit");
+          static_assert(kCap != kResidentMax || sizeof(sh.peer) >= (kMaxK * 8 + 1) * sizeof(unsigned), "eighth starts must fit");
+          for (int i = threadIdx.x; i < kMaxK * 8; i += kThreads) fcur[i] = 0u;
+          __syncthreads();
 #pragma unroll
-        for (int j = 0; j < kPT; ++j) {
-          if (j < steps) {
-            const int bk = stable ? (int)(br[j] >> 16) : (int)br[j];
-            if (bk < kMaxK) {
-              const int p = sh.bstart[bk] + (stable ? (int)(br[j] & 0xFFFF)
-                                                    : (int)atomicAdd(&sh.peer[warp][bk], 1u));
-              // read again (from cache) rather than held in registers
-              const Ord o = T::ord(src[warp * chunk + j * 32 + lane]);
-              sh.keys[p] = tpk ? (Ord)((Ord)(o - tlo) << kPosBits) | (Ord)p : o;
-              sh.seg[p] = (unsigned char)bk;
+          for (int j = 0; j < kPT; ++j) {
+            if (j < steps) {
+              const int bk = (int)br[j];
+              unsigned id = 0xFFFFu;
+              if (bk < kMaxK) {
+                id = (unsigned)(bk * 8 + cls.sub8(src[warp * chunk + j * 32 + lane], bk, path));
+                atomicAdd(&fcur[id], 1u);
+              }
+              br[j] = id;
+            }
+          }
+          __syncthreads();
+          if (threadIdx.x < kMaxK) {
+            const int b = threadIdx.x;
+            unsigned run = (unsigned)sh.bstart[b];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              const unsigned c = fcur[b * 8 + q];
+              fcur[b * 8 + q] = run;
+              fstart[b * 8 + q] = run;
+              run += c;
+            }
+          }
+          if (threadIdx.x == 0) fstart[kMaxK * 8] = (unsigned)n;
+          __syncthreads();
+#pragma unroll
+          for (int j = 0; j < kPT; ++j) {
+            if (j < steps) {
+              const unsigned id = br[j];
+              if (id < (unsigned)(kMaxK * 8)) {
+                const int p = (int)atomicAdd(&fcur[id], 1u);
+                const Ord o = T::ord(src[warp * chunk + j * 32 + lane]);
+                sh.keys[p] = tpk ? (Ord)((Ord)(o - tlo) << kPosBits) | (Ord)p : o;
+                sh.seg[p] = (unsigned short)id;
+              }
+            }
+          }
+        } else {
+          // every bucket is base-cased unless `stable`: the order inside a
+          // bucket does not matter, and a shared cursor per (warp, bucket)
+          // gives each key its place
+#pragma unroll
+          for (int j = 0; j < kPT; ++j) {
+            if (j < steps) {
+              const int bk = stable ? (int)(br[j] >> 16) : (int)br[j];
+              if (bk < kMaxK) {
+                const int p = sh.bstart[bk] + (stable ? (int)(br[j] & 0xFFFF)
+                                                      : (int)atomicAdd(&sh.peer[warp][bk], 1u));
+                // read again (from cache) rather than held in registers
+                const Ord o = T::ord(src[warp * chunk + j * 32 + lane]);
+                sh.keys[p] = tpk ? (Ord)((Ord)(o - tlo) << kPosBits) | (Ord)p : o;
+                sh.seg[p] = (unsigned char)bk;
+              }
             }
           }
         }
@@ -816,18 +926,13 @@ __device__ __forceinline__ void tail_task(const ResidentArgs& a, int gi, unsigne
   }
   for (int p = threadIdx.x; p < n; p += blockDim.x) {
     const int q = sh.seg[p];
-    const int s = sh.segb[q], e = sh.segb[q + 1];
+    const int s = fine ? (int)fstart[q] : sh.segb[q], e = fine ? (int)fstart[q + 1] : sh.segb[q + 1];
     const Ord kp = sh.keys[p];
     const bool based = e - s <= cutoff && !(split_tree && (q & 1));
     int d = p;
     Ord out = kp;
     if (task_pk || (g.fit < 0 && sh.segpk[q])) {
-      if (based) {
-        int cnt = 0;
-#pragma unroll 4
-        for (int r = s; r < e; ++r) cnt += sh.keys[r] < kp ? 1 : 0;
-        d = s + cnt;
-      }
+      if (based) d = s + count_below(sh.keys, s, e, kp);
       out = (Ord)((task_pk ? sh.tlo : sh.seglo[q]) + (kp >> kPosBits));
     } else if (based) {
       int cnt = 0;
