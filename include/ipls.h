@@ -222,6 +222,19 @@ iplsStatus iplsSortSegmented(iplsCtx ctx, void* keys, const int64_t* offsets,
  * host memory gives full copy bandwidth; pageable memory works too. */
 iplsStatus iplsSortHost(iplsCtx ctx, void* host_keys, int64_t n, iplsDtype dtype);
 
+/* Sorts `count` separate HOST arrays host_keys[i][0..n[i]) in place, one
+ * after another, with the copies overlapped: while array i is sorted on the
+ * device, array i+1 is copied in and array i-1 copied out, on two copy
+ * streams of the context, through three context-owned device buffers of the
+ * largest n[i] keys each.  host_keys and n are host arrays of count
+ * entries; the arrays must not overlap.  Each array ends up exactly as
+ * iplsSortHost leaves it.  The copies overlap only for pinned (page-locked)
+ * host memory; pageable memory gives the same result without overlap.  The
+ * call returns when every array is back in host memory; on an error the
+ * arrays not yet copied back keep their input. */
+iplsStatus iplsSortHostBatch(iplsCtx ctx, void* const* host_keys, const int64_t* n, int64_t count,
+                             iplsDtype dtype);
+
 /* Sorts `count` separate device arrays keys[i][0..n[i]) in place (keys and
  * n are HOST arrays of count entries; each keys[i] is a device pointer
  * aligned to the key width).  All arrays are sorted together: each is a

@@ -173,6 +173,11 @@ struct iplsContext {
   int64_t k_bytes[16] = {};
   // host-buffer sorting
   char* host_stage = nullptr; int64_t host_stage_cap = 0;
+  // pipelined host batches: three device buffers in rotation (one arriving,
+  // one being sorted, one leaving), a copy stream each way, their events
+  char* pipe_buf[3] = {}; int64_t pipe_cap[3] = {};
+  cudaStream_t h2d = nullptr, d2h = nullptr;
+  cudaEvent_t in_ev[3] = {}, sorted_ev[3] = {}, out_ev[3] = {};
 };
 
 namespace {
@@ -1336,6 +1341,14 @@ iplsStatus iplsDestroy(iplsCtx c) {
   dev_free(c, c->trace_res, (size_t)c->trace_alloc * sizeof(iplsTraceRecDev));
   dev_free(c, c->trace_knots, (size_t)c->knot_cap * (c->knot_leaves + 1) * sizeof(float));
   dev_free(c, c->host_stage, (size_t)c->host_stage_cap);
+  for (int k = 0; k < 3; ++k) {
+    dev_free(c, c->pipe_buf[k], (size_t)c->pipe_cap[k]);
+    if (c->in_ev[k]) cudaEventDestroy(c->in_ev[k]);
+    if (c->sorted_ev[k]) cudaEventDestroy(c->sorted_ev[k]);
+    if (c->out_ev[k]) cudaEventDestroy(c->out_ev[k]);
+  }
+  if (c->h2d) cudaStreamDestroy(c->h2d);
+  if (c->d2h) cudaStreamDestroy(c->d2h);
   delete c;
   return IPLS_OK;
 }
@@ -1456,6 +1469,72 @@ iplsStatus iplsSortHost(iplsCtx c, void* host_keys, int64_t n, iplsDtype dtype) 
   IPLS_TRY(sort_impl(w, c->host_stage, n, dtype, nullptr, 0));
   IPLS_CUDA(cudaMemcpyAsync(host_keys, c->host_stage, bytes, cudaMemcpyDeviceToHost, w.stream));
   IPLS_CUDA(cudaStreamSynchronize(w.stream));
+  return IPLS_OK;
+}
+
+iplsStatus iplsSortHostBatch(iplsCtx c, void* const* host_keys, const int64_t* n, int64_t count,
+                             iplsDtype dtype) {
+  if (!valid_dtype(dtype)) return fail(IPLS_ERR_ARG, "unknown dtype");
+  if (count < 0) return fail(IPLS_ERR_ARG, "count < 0");
+  if (count == 0) return IPLS_OK;
+  if (!host_keys || !n) return fail(IPLS_ERR_ARG, "host_keys or n is NULL");
+  int64_t max_n = 0;
+  for (int64_t i = 0; i < count; ++i) {
+    IPLS_TRY(check_common(n[i], dtype));
+    if (n[i] > 1 && !host_keys[i]) return fail(IPLS_ERR_ARG, "host_keys[i] is NULL");
+    max_n = std::max(max_n, n[i]);
+  }
+  iplsStatus st = IPLS_OK;
+  if (!c) { c = default_ctx(&st); if (!c) return st; }
+  std::lock_guard<std::mutex> ex(c->exec_mu);
+  c->calls += count;
+  g_last_error.clear();
+  const int wb = key_bytes(dtype);
+  Workspace& w = c->ws;
+  for (int k = 0; k < 3; ++k) IPLS_TRY(ensure(w, c->pipe_buf[k], c->pipe_cap[k], max_n * wb));
+  if (!c->h2d) {
+    IPLS_CUDA(cudaStreamCreateWithFlags(&c->h2d, cudaStreamNonBlocking));
+    IPLS_CUDA(cudaStreamCreateWithFlags(&c->d2h, cudaStreamNonBlocking));
+    for (int k = 0; k < 3; ++k) {
+      IPLS_CUDA(cudaEventCreateWithFlags(&c->in_ev[k], cudaEventDisableTiming));
+      IPLS_CUDA(cudaEventCreateWithFlags(&c->sorted_ev[k], cudaEventDisableTiming));
+      IPLS_CUDA(cudaEventCreateWithFlags(&c->out_ev[k], cudaEventDisableTiming));
+    }
+  }
+  // array i uses buffer i % 3; its copy in may start once array i - 3 has
+  // left that buffer, its sort once it has arrived, its copy out once it is
+  // sorted.  The copies in and out of neighbouring arrays run on their own
+  // streams while array i is sorted.
+  auto copy_in = [&](int64_t i) -> cudaError_t {
+    const int k = (int)(i % 3);
+    cudaError_t e = cudaSuccess;
+    if (i >= 3) e = cudaStreamWaitEvent(c->h2d, c->out_ev[k], 0);
+    if (e == cudaSuccess && n[i] > 1)
+      e = cudaMemcpyAsync(c->pipe_buf[k], host_keys[i], (size_t)n[i] * wb, cudaMemcpyHostToDevice, c->h2d);
+    if (e == cudaSuccess) e = cudaEventRecord(c->in_ev[k], c->h2d);
+    return e;
+  };
+  iplsStatus result = IPLS_OK;
+  cudaError_t e = copy_in(0);
+  for (int64_t i = 0; i < count && e == cudaSuccess && result == IPLS_OK; ++i) {
+    const int k = (int)(i % 3);
+    if (i + 1 < count) e = copy_in(i + 1);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(w.stream, c->in_ev[k], 0);
+    if (e != cudaSuccess) break;
+    if (n[i] > 1) result = sort_impl(w, c->pipe_buf[k], n[i], dtype, nullptr, 0);
+    if (result != IPLS_OK) break;
+    e = cudaEventRecord(c->sorted_ev[k], w.stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->d2h, c->sorted_ev[k], 0);
+    if (e == cudaSuccess && n[i] > 1)
+      e = cudaMemcpyAsync(host_keys[i], c->pipe_buf[k], (size_t)n[i] * wb, cudaMemcpyDeviceToHost, c->d2h);
+    if (e == cudaSuccess) e = cudaEventRecord(c->out_ev[k], c->d2h);
+  }
+  // every copy this call queued has finished before it returns
+  const cudaError_t e1 = cudaStreamSynchronize(c->h2d);
+  const cudaError_t e2 = cudaStreamSynchronize(c->d2h);
+  if (result != IPLS_OK) return result;
+  if (e == cudaSuccess) e = e1 != cudaSuccess ? e1 : e2;
+  if (e != cudaSuccess) return cuda_fail(e, "iplsSortHostBatch");
   return IPLS_OK;
 }
 

@@ -70,7 +70,7 @@ class iplsStats(ctypes.Structure):
 
 _lib = None
 SYMBOLS = ["iplsDefaultConfig", "iplsCreate", "iplsDestroy", "iplsScratchBytes", "iplsSort",
-           "iplsSortSegmented", "iplsSortHost", "iplsSubmit", "iplsPoll", "iplsWait",
+           "iplsSortSegmented", "iplsSortHost", "iplsSortHostBatch", "iplsSubmit", "iplsPoll", "iplsWait",
            "iplsGetStats", "iplsGetKernelStats", "iplsGetLevelStats", "iplsGetTrace",
            "iplsGetTraceKnots",
            "iplsPL2LossGrad", "iplsSortSmallNoAlloc", "iplsSortBatch", "iplsGetBatchLog",
@@ -103,6 +103,7 @@ def load(build_if_missing: bool = True):
     L.iplsSortSegmented.argtypes = [P, P, P, c.c_int64, c.c_int]
     L.iplsSortHost.argtypes = [P, P, c.c_int64, c.c_int]
     L.iplsSortBatch.argtypes = [P, P, P, c.c_int64, c.c_int]
+    L.iplsSortHostBatch.argtypes = [P, P, P, c.c_int64, c.c_int]
     L.iplsGetBatchLog.argtypes = [P, c.POINTER(iplsBatchRec), c.c_int64, c.POINTER(c.c_int64)]
     L.iplsSortSmallNoAlloc.argtypes = [P, c.c_int64, c.c_int, c.POINTER(iplsConfig), P]
     L.iplsGetKernelStats.argtypes = [P, c.POINTER(iplsKernelStat), c.c_int32,
@@ -190,6 +191,15 @@ def iplsSortBatch(ctx: int | None, ptrs, sizes, dtype: int) -> int:
     P = (ctypes.c_void_p * max(m, 1))(*[ctypes.c_void_p(p) for p in ptrs])
     N = (ctypes.c_int64 * max(m, 1))(*[int(x) for x in sizes])
     return _check(load().iplsSortBatch(ctypes.c_void_p(ctx), P, N, m, dtype), "iplsSortBatch")
+
+
+def iplsSortHostBatch(ctx: int | None, ptrs, sizes, dtype: int) -> int:
+    """Sorts len(ptrs) separate host arrays in place, each ptrs[i] holding
+    sizes[i] keys, with the copies in and out overlapped with the sorts."""
+    m = len(ptrs)
+    P = (ctypes.c_void_p * max(m, 1))(*[ctypes.c_void_p(p) for p in ptrs])
+    N = (ctypes.c_int64 * max(m, 1))(*[int(x) for x in sizes])
+    return _check(load().iplsSortHostBatch(ctypes.c_void_p(ctx), P, N, m, dtype), "iplsSortHostBatch")
 
 
 def iplsGetBatchLog(ctx: int, cap: int = 65536) -> list:
@@ -366,6 +376,9 @@ class Context:
 
     def sort_host_ptr(self, host_ptr: int, n: int, dtype: int) -> None:
         iplsSortHost(self.ctx, host_ptr, n, dtype)
+
+    def sort_host_batch_ptrs(self, ptrs, sizes, dtype: int) -> None:
+        iplsSortHostBatch(self.ctx, ptrs, sizes, dtype)
 
     def stats(self) -> iplsStats:
         return iplsGetStats(self.ctx)
