@@ -42,6 +42,17 @@ def test_host_side_validation_without_gpu():
     assert "aligned" in p.iplsLastError()
     assert lib.iplsSortSegmented(None, None, None, -1, 0) == -1
     assert lib.iplsSortSegmented(None, None, None, 0, 0) == 0   # nothing to do
+    # host batches: count, dtype, NULL arrays and sizes are checked first
+    P = (ctypes.c_void_p * 2)(None, None)
+    N = (ctypes.c_int64 * 2)(10, 5)
+    assert lib.iplsSortHostBatch(None, P, N, 0, 0) == 0           # nothing to do
+    assert lib.iplsSortHostBatch(None, P, N, -1, 0) == -1
+    assert lib.iplsSortHostBatch(None, P, N, 2, 9) == -1          # unknown dtype
+    assert lib.iplsSortHostBatch(None, None, N, 2, 0) == -1
+    assert lib.iplsSortHostBatch(None, P, N, 2, 0) == -1          # NULL array of 10 keys
+    assert "NULL" in p.iplsLastError()
+    N2 = (ctypes.c_int64 * 2)(2**32, 1)
+    assert lib.iplsSortHostBatch(None, P, N2, 2, 0) == -1         # above 2^32 - 1 keys
     cfg = p.iplsDefaultConfig()
     assert (cfg.k, cfg.cutoff, cfg.sync) == (256, 32, 1)
     n = p.iplsScratchBytes(None, 1 << 28, 0)
