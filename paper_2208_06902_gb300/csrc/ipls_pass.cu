@@ -188,6 +188,7 @@ __global__ void __launch_bounds__(kFitThreads) k_fit(LevelArgs a) {
 // same-binade or uncentred estimate of a linear model, or the general
 // dispatch (fixed-point estimate, splitter tree, PL2, binary64 only).
 constexpr int kPathGeneric = 0, kPathOrd = 1, kPathFlt = 2;
+constexpr int kHistGrab = 4;  // tiles k_hist takes per ticket
 
 template <class K>
 __global__ void __launch_bounds__(kPassThreads, 4) k_hist(LevelArgs a, int rehist_only) {
@@ -205,12 +206,34 @@ __global__ void __launch_bounds__(kPassThreads, 4) k_hist(LevelArgs a, int rehis
   for (int i = threadIdx.x; i < kWarps * kMaxK; i += blockDim.x) (&hist[0][0])[i] = 0;
   for (int i = threadIdx.x; i < kMaxK; i += blockDim.x) acc[i] = 0;
   const int64_t nt = level_ntiles(a);
-  const int64_t t0 = nt * blockIdx.x / gridDim.x, t1 = nt * (blockIdx.x + 1) / gridDim.x;
   int cur = -1;
   bool use_tab = false;
   int path = kPathGeneric;
   Classifier<K> cls;
-  for (int64_t t = t0; t < t1; ++t) {
+  // groups of kHistGrab tiles from a level-wide ticket: tiles of some
+  // subproblems classify slower (the general dispatch, deferred keys), and
+  // a fixed share per block would leave the level waiting for the slowest
+  // (the re-histogram pass, which skips most tiles, keeps one fixed range
+  // per block)
+  unsigned* const ticket = &a.ctl->hist_ticket[0];
+  __shared__ long long s_tg;
+  bool first = true;
+  for (;;) {
+  __syncthreads();  // the previous group is done before the ticket is read again
+  if (!rehist_only && threadIdx.x == 0) s_tg = (long long)atomicAdd(ticket, (unsigned)kHistGrab);
+  __syncthreads();
+  int64_t tg, tge;
+  if (rehist_only) {
+    if (!first) break;
+    first = false;
+    tg = nt * blockIdx.x / gridDim.x;
+    tge = nt * (blockIdx.x + 1) / gridDim.x;
+  } else {
+    tg = s_tg;
+    if (tg >= nt) break;
+    tge = tg + kHistGrab < nt ? tg + kHistGrab : nt;
+  }
+  for (int64_t t = tg; t < tge; ++t) {
     const int s = a.tile2sub[t];
     if (s != cur) {
       __syncthreads();
@@ -325,6 +348,7 @@ __global__ void __launch_bounds__(kPassThreads, 4) k_hist(LevelArgs a, int rehis
     }
     // the rows are zero again before any warp counts the next tile
     __syncthreads();
+  }
   }
   __syncthreads();
   if (cur >= 0) {
