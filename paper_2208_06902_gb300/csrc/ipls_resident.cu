@@ -479,6 +479,7 @@ struct TailSmem {
   int tpk;                           // 1: the fitted task's keys are placed packed
   int slow_all;
   int any_big;   // some bucket above the cutoff would be queued
+  int any_mid;   // some bucket (bit 0) or eighth (bit 1) of kSameMin+1 .. cutoff keys
   long long rec;
 };
 // two (four) blocks per SM, each with its 1 KB of reserved shared memory
@@ -513,6 +514,15 @@ static_assert(kResidentMax <= (1 << kPosBits), "positions must fit the packed wo
 // at least this many buckets.
 constexpr int kFineMinBuckets = 64;
 
+// Base case: a segment of more than this many keys is first checked for
+// copies of one key, which keep their places (any order of equal keys gives
+// the same bytes); ranking them by counting would cost the square of the
+// segment's size.  The mark is bit 31 of the segment's start (starts are
+// below 2^13), so that the base case reads it with the bounds.
+constexpr int kSameMin = 32;
+constexpr unsigned kSameBit = 0x80000000u;
+constexpr unsigned kStartMask = 0x7FFFFFFFu;
+
 // Number of words in keys[s, e) below kp (the rank of a packed word in its
 // segment; packed words are distinct).  Two (8-byte) or four (4-byte)
 // words per shared-memory load; the array is 16-byte aligned.
@@ -537,6 +547,20 @@ __device__ __forceinline__ int count_below(const Ord* keys, int s, int e, Ord kp
   }
   for (; r < e; ++r) cnt += keys[r] < kp ? 1 : 0;
   return cnt;
+}
+
+// 1 when keys[s, e) hold two different keys (compared after a right shift
+// by `shift`, which drops the position bits of packed words).  Stops at the
+// first difference.
+template <class Ord>
+__device__ __forceinline__ int differs(const Ord* keys, int s, int e, int shift) {
+  const Ord k0 = keys[s];
+  int r = s + 1;
+  for (; r + 4 <= e; r += 4)
+    if (((keys[r] ^ k0) | (keys[r + 1] ^ k0) | (keys[r + 2] ^ k0) | (keys[r + 3] ^ k0)) >> shift) return 1;
+  for (; r < e; ++r)
+    if ((keys[r] ^ k0) >> shift) return 1;
+  return 0;
 }
 
 // kThreads threads, tasks of at most kCap keys; the small size takes tasks
@@ -574,6 +598,7 @@ __device__ __forceinline__ void tail_task(const ResidentArgs& a, int gi, unsigne
     if (threadIdx.x == 0) {
       sh.slow_all = 0;
       sh.any_big = 0;
+      sh.any_mid = 0;
     }
     __syncwarp();
     const TailModel* gmp = &gm;
@@ -700,6 +725,7 @@ __device__ __forceinline__ void tail_task(const ResidentArgs& a, int gi, unsigne
         // splitter tree itself always progresses or leaves one equality run)
         if ((int)run == n && !split_tree) sh.slow_all = 1;
         if ((int)run > a.cutoff && b < sh.tm.l.nb && !(split_tree && (b & 1))) sh.any_big = 1;
+        if ((int)run > kSameMin && (int)run <= a.cutoff) sh.any_mid = 1;
       }
       if (threadIdx.x == 0) {  // the task's key range
         Ord lo = ~(Ord)0, hi = 0;
@@ -795,13 +821,16 @@ __device__ __forceinline__ void tail_task(const ResidentArgs& a, int gi, unsigne
           if (threadIdx.x < kMaxK) {
             const int b = threadIdx.x;
             unsigned run = (unsigned)sh.bstart[b];
+            bool mid = false;
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
               const unsigned c = fcur[b * 8 + q];
               fcur[b * 8 + q] = run;
               fstart[b * 8 + q] = run;
               run += c;
+              mid = mid || c > (unsigned)kSameMin;
             }
+            if (mid) sh.any_mid = 3;
           }
           if (threadIdx.x == 0) fstart[kMaxK * 8] = (unsigned)n;
           __syncthreads();
@@ -901,9 +930,9 @@ __device__ __forceinline__ void tail_task(const ResidentArgs& a, int gi, unsigne
   const bool task_pk = g.fit >= 0 && sh.tpk != 0;
   if (g.fit < 0) {
     for (int q = threadIdx.x; q < nseg; q += blockDim.x) {
-      const int s = sh.segb[q], e = sh.segb[q + 1];
       Ord mn = 0;
-      bool pk = false;
+      bool pk = false, eq = false;
+      const int s = sh.segb[q] & (int)kStartMask, e = sh.segb[q + 1] & (int)kStartMask;
       if (e - s >= 2 && e - s <= cutoff) {
         mn = sh.keys[s];
         Ord mx = mn;
@@ -913,9 +942,12 @@ __device__ __forceinline__ void tail_task(const ResidentArgs& a, int gi, unsigne
           mx = k > mx ? k : mx;
         }
         pk = (Ord)(mx - mn) < kSpan;
+        eq = mx == mn;
       }
       sh.seglo[q] = mn;
       sh.segpk[q] = pk ? 1 : 0;
+      // only this thread writes segb[q]; readers mask the mark off
+      if (eq) sh.segb[q] = s | (int)kSameBit;
     }
     __syncthreads();
     for (int p = threadIdx.x; p < n; p += blockDim.x) {
@@ -923,12 +955,25 @@ __device__ __forceinline__ void tail_task(const ResidentArgs& a, int gi, unsigne
       if (sh.segpk[q]) sh.keys[p] = (Ord)((Ord)(sh.keys[p] - sh.seglo[q]) << kPosBits) | (Ord)p;
     }
     __syncthreads();
+  } else if (sh.any_mid & (fine ? 2 : 1)) {
+    // segments of kSameMin+1 .. cutoff keys that hold copies of one key
+    const int ncell = fine ? kMaxK * 8 : nseg;
+    const int sshift = task_pk ? kPosBits : 0;
+    unsigned* const st = fine ? fstart : reinterpret_cast<unsigned*>(sh.segb);
+    for (int q = threadIdx.x; q < ncell; q += blockDim.x) {
+      const int s = (int)(st[q] & kStartMask), e = (int)(st[q + 1] & kStartMask);
+      if (e - s > kSameMin && e - s <= cutoff && !differs(sh.keys, s, e, sshift)) st[q] = (unsigned)s | kSameBit;
+    }
+    __syncthreads();
   }
   for (int p = threadIdx.x; p < n; p += blockDim.x) {
     const int q = sh.seg[p];
-    const int s = fine ? (int)fstart[q] : sh.segb[q], e = fine ? (int)fstart[q + 1] : sh.segb[q + 1];
+    const unsigned s0 = fine ? fstart[q] : (unsigned)sh.segb[q];
+    const int s = (int)(s0 & kStartMask);
+    const int e = (int)((fine ? fstart[q + 1] : (unsigned)sh.segb[q + 1]) & kStartMask);
     const Ord kp = sh.keys[p];
-    const bool based = e - s <= cutoff && !(split_tree && (q & 1));
+    // copies of one key keep their places
+    const bool based = e - s <= cutoff && !(split_tree && (q & 1)) && !(s0 & kSameBit);
     int d = p;
     Ord out = kp;
     if (task_pk || (g.fit < 0 && sh.segpk[q])) {
@@ -950,10 +995,6 @@ __device__ __forceinline__ void tail_task(const ResidentArgs& a, int gi, unsigne
   }
 }
 
-// kThreads threads, tasks of at most kCap keys; the small size takes tasks
-// of up to kTailSmall keys, the large one the rest (each skips the other's).
-// One block per task when the host sized the grid; a fixed grid looping over
-// the tasks on device-driven levels.
 // kThreads threads, tasks of at most kCap keys; the small size takes tasks
 // of up to kTailSmall keys, the large one the rest (each skips the other's).
 // Host-driven levels: one block per task.  Device-driven levels (kTicket):
