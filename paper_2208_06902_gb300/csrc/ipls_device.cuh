@@ -249,12 +249,74 @@ __device__ void group_sort(T* a, int n) {
 template <class T>
 __device__ __forceinline__ void block_sort(T* a, int n) { group_sort<BlockG, T>(a, n); }
 
+// One stable counting-sort pass of a warp radix sort: src[0..n) by the 8-bit
+// digit ((key - lo) >> shift) & 255 into dst.  The in-warp rank of a key
+// among the keys of its step with the same digit comes from a shared OR of
+// lane bits; cnt holds the digit counts, peer is zero on entry and on exit.
+template <int kSteps, class Ord>
+__device__ __forceinline__ void radix_pass(const Ord* src, Ord* dst, unsigned* cnt, unsigned* peer, int n,
+                                           Ord lo, int shift) {
+  const int lane = threadIdx.x & 31;
+  for (int i = lane; i < 256; i += 32) cnt[i] = 0;
+  __syncwarp();
+  unsigned rk[kSteps];  // digit << 16 | rank among the equal digits before it
+#pragma unroll
+  for (int t = 0; t < kSteps; ++t) {
+    if (t * 32 < n) {
+      const int i = t * 32 + lane;
+      const bool valid = i < n;
+      const int d = valid ? (int)(((src[i] - lo) >> shift) & 255) : 0;
+      if (valid) atomicOr(&peer[d], 1u << lane);
+      __syncwarp();
+      const unsigned pm = valid ? peer[d] : 0u;
+      const int lt = __popc(pm & lanemask_lt());
+      const unsigned base = cnt[d];
+      rk[t] = ((unsigned)d << 16) | (base + (unsigned)lt);
+      __syncwarp();
+      if (valid && lt == 0) {
+        cnt[d] = base + (unsigned)__popc(pm);
+        peer[d] = 0u;
+      }
+      __syncwarp();
+    }
+  }
+  {  // exclusive scan of the 256 digit counts, 8 per lane
+    unsigned loc[8], sum = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) { loc[q] = cnt[lane * 8 + q]; sum += loc[q]; }
+    unsigned incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned x = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += x;
+    }
+    unsigned run = incl - sum;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) { cnt[lane * 8 + q] = run; run += loc[q]; }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int t = 0; t < kSteps; ++t) {
+    if (t * 32 < n) {
+      const int i = t * 32 + lane;
+      if (i < n) dst[cnt[rk[t] >> 16] + (rk[t] & 0xFFFFu)] = src[i];
+    }
+  }
+  __syncwarp();
+}
+
+// Digits of the first try of warp_radix_sort (the highest ones).
+constexpr int kRadixTop = 3;
+
 // LSD radix sort of a[0..n) (n <= 32*kSteps) by one warp, on 8-bit digits of
 // (key - min): a sample drawn from one subproblem spans a narrow range, so
 // few passes are needed (none when all keys are equal).  tmp holds n more
 // keys; cnt and peer are 256 words each, peer zero on entry and on exit.
-// Each pass is a stable counting sort; the in-warp rank of a key among the
-// keys of its step with the same digit comes from a shared OR of lane bits.
+// The passes run over the kRadixTop highest digits that some key sets
+// first; keys whose top digits differ are then in order, and when every
+// key is at most its right neighbour the array is sorted.  Otherwise (two
+// keys that agree on the top digits were left out of order) every digit is
+// sorted again, from the lowest.
 template <int kSteps, class Ord>
 __device__ void warp_radix_sort(Ord* a, Ord* tmp, unsigned* cnt, unsigned* peer, int n) {
   const int lane = threadIdx.x & 31;
@@ -280,58 +342,28 @@ __device__ void warp_radix_sort(Ord* a, Ord* tmp, unsigned* cnt, unsigned* peer,
   const int passes = (bits + 7) / 8;
   Ord* src = a;
   Ord* dst = tmp;
-  for (int p = 0; p < passes; ++p) {
-    const int shift = 8 * p;
-    if (((vary >> shift) & 255) == 0) continue;
-    for (int i = lane; i < 256; i += 32) cnt[i] = 0;
-    __syncwarp();
-    unsigned rk[kSteps];  // digit << 16 | rank among the equal digits before it
-#pragma unroll
-    for (int t = 0; t < kSteps; ++t) {
-      if (t * 32 < n) {
-        const int i = t * 32 + lane;
-        const bool valid = i < n;
-        const int d = valid ? (int)(((src[i] - lo) >> shift) & 255) : 0;
-        if (valid) atomicOr(&peer[d], 1u << lane);
-        __syncwarp();
-        const unsigned pm = valid ? peer[d] : 0u;
-        const int lt = __popc(pm & lanemask_lt());
-        const unsigned base = cnt[d];
-        rk[t] = ((unsigned)d << 16) | (base + (unsigned)lt);
-        __syncwarp();
-        if (valid && lt == 0) {
-          cnt[d] = base + (unsigned)__popc(pm);
-          peer[d] = 0u;
-        }
-        __syncwarp();
-      }
+  // the lowest of the kRadixTop highest digits that some key sets
+  int p0 = 0;
+  for (int p = passes - 1, live = 0; p >= 0; --p) {
+    if (((vary >> (8 * p)) & 255) == 0) continue;
+    if (++live == kRadixTop) {
+      p0 = p;
+      break;
     }
-    {  // exclusive scan of the 256 digit counts, 8 per lane
-      unsigned loc[8], sum = 0;
-#pragma unroll
-      for (int q = 0; q < 8; ++q) { loc[q] = cnt[lane * 8 + q]; sum += loc[q]; }
-      unsigned incl = sum;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const unsigned x = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += x;
-      }
-      unsigned run = incl - sum;
-#pragma unroll
-      for (int q = 0; q < 8; ++q) { cnt[lane * 8 + q] = run; run += loc[q]; }
+  }
+  for (;;) {
+    for (int p = p0; p < passes; ++p) {
+      if (((vary >> (8 * p)) & 255) == 0) continue;
+      radix_pass<kSteps>(src, dst, cnt, peer, n, lo, 8 * p);
+      Ord* sw = src;
+      src = dst;
+      dst = sw;
     }
-    __syncwarp();
-#pragma unroll
-    for (int t = 0; t < kSteps; ++t) {
-      if (t * 32 < n) {
-        const int i = t * 32 + lane;
-        if (i < n) dst[cnt[rk[t] >> 16] + (rk[t] & 0xFFFFu)] = src[i];
-      }
-    }
-    __syncwarp();
-    Ord* sw = src;
-    src = dst;
-    dst = sw;
+    if (p0 == 0) break;
+    bool bad = false;
+    for (int i = lane; i + 1 < n; i += 32) bad = bad || src[i] > src[i + 1];
+    if (!__any_sync(0xffffffffu, bad)) break;
+    p0 = 0;
   }
   if (src != a) {
     for (int i = lane; i < n; i += 32) a[i] = src[i];
