@@ -183,7 +183,7 @@ struct LevelCtl {
   int64_t keys_moved;    // keys scattered by this level's grid passes
   int64_t keys_level;    // keys in this level's grid subproblems
   int64_t max_sub_n;     // largest grid subproblem created for the next level
-  uint32_t hist_ticket[2];  // [0]: next tile group of k_hist; [1]: unused
+  uint32_t tile_ticket[2];  // next tile group of [0] k_hist, [1] k_scatter
 };
 
 // Run-wide device status (persists across levels of one call).

@@ -189,6 +189,7 @@ __global__ void __launch_bounds__(kFitThreads) k_fit(LevelArgs a) {
 // dispatch (fixed-point estimate, splitter tree, PL2, binary64 only).
 constexpr int kPathGeneric = 0, kPathOrd = 1, kPathFlt = 2;
 constexpr int kHistGrab = 4;  // tiles k_hist takes per ticket
+constexpr int kScatterGrab = 4;  // tiles k_scatter takes per ticket
 
 template <class K>
 __global__ void __launch_bounds__(kPassThreads, 4) k_hist(LevelArgs a, int rehist_only) {
@@ -215,7 +216,7 @@ __global__ void __launch_bounds__(kPassThreads, 4) k_hist(LevelArgs a, int rehis
   // a fixed share per block would leave the level waiting for the slowest
   // (the re-histogram pass, which skips most tiles, keeps one fixed range
   // per block)
-  unsigned* const ticket = &a.ctl->hist_ticket[0];
+  unsigned* const ticket = &a.ctl->tile_ticket[0];
   __shared__ long long s_tg;
   bool first = true;
   for (;;) {
@@ -657,9 +658,20 @@ __global__ void __launch_bounds__(kScatterThreads, 2) k_scatter(LevelArgs a) {
     return;
   }
   const int64_t nt = level_ntiles(a);
-  const int64_t t0 = nt * blockIdx.x / gridDim.x, t1 = nt * (blockIdx.x + 1) / gridDim.x;
   for (int i = threadIdx.x; i < kSWarps * kMaxK; i += blockDim.x) (&sh.peer[0][0])[i] = 0u;
-  for (int64_t t = t0; t < t1; ++t) {
+  // groups of kScatterGrab tiles from a level-wide ticket: tiles of skipped
+  // subproblems cost nothing and the last tile of a subproblem is short, so
+  // a fixed share per block would leave the level waiting for the slowest
+  unsigned* const ticket = &a.ctl->tile_ticket[1];
+  __shared__ long long s_tg;
+  for (;;) {
+  __syncthreads();  // the previous group is done before the ticket is read again
+  if (threadIdx.x == 0) s_tg = (long long)atomicAdd(ticket, (unsigned)kScatterGrab);
+  __syncthreads();
+  const int64_t tg = s_tg;
+  if (tg >= nt) break;
+  const int64_t tge = tg + kScatterGrab < nt ? tg + kScatterGrab : nt;
+  for (int64_t t = tg; t < tge; ++t) {
     const int s = a.tile2sub[t];
     const Sub sub = a.subs[s];
     if (sub.flags & kSkipScatter) continue;
@@ -753,6 +765,7 @@ __global__ void __launch_bounds__(kScatterThreads, 2) k_scatter(LevelArgs a) {
       const uint64_t p = (uint64_t)(sh.gbase[sh.sbid[i]] - sub.off + i);
       if (p < span) dst[p] = sh.stage[i];
     }
+  }
   }
 }
 
